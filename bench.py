@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused double-MRT time step (MLUPS and fraction of the HBM roofline).
+
+One "step" is one time step of the whole cavity: one launch of the fused kernel
+(pull-stream of both lattices with the walls, D2Q9 MRT + force, D2Q5 MRT, store,
+hot-wall Nusselt reduction). The default workload is the largest single cavity,
+4096 x 4096 at Ra = 1e7, Pr = 0.001, alpha = 0.1, started at rest with seeded
+1e-6 noise; its two float32 population buffers (3.76 GB) are far larger than L2,
+so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dmrt|reference]
+
+With N > 1 (torchrun) every rank steps its own independent cavity (weak scaling,
+no collective on the data path); timing is the max over ranks.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (both lattices) & % HBM roofline; batched/FP16 vs plain FP32 at Nu err≤1e-3"
+UNIT = "MLUPS"
+BYTES_PER_NODE_FP32 = 112  # 14 populations read + 14 written, 4 bytes each
+FALLBACK_HBM_GBS = 6800.0
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_4096x4096.json")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", "step_kernel.cuh")]
+
+
+def workload(name):
+    from paper_1601_04633_gb300 import inputs
+
+    table = {
+        "cavity_4096": inputs.cavity_4096,
+        "cavity_2048": lambda: inputs.Cavity(2048, 2048, 1e7, 0.001, seed=5),
+        "cavity_256": inputs.cavity_256_oscillatory,
+        "cavity_64": inputs.cavity_64,
+    }
+    cav = table[name]()
+    label = f"cavity_{cav.nx}x{cav.ny}_Ra{cav.Ra:g}_Pr{cav.Pr:g}_alpha{cav.alpha:g}"
+    return cav, label
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm_copy_gbs"):
+            if key in d and d[key]:
+                return float(d[key]), "measured"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+def ncu_traffic_per_launch(nodes):
+    """DRAM bytes per launch from the committed ncu summary, scaled to ``nodes``;
+    None if absent or taken on a different kernel source."""
+    try:
+        with open(PROFILE_SUMMARY) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_hash():
+        return None
+    return d["dram_bytes_per_launch"] * nodes / d["nodes"]
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_uuid):
+        self.uuid = device_uuid
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if not self.proc:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        rows = []
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), parts[4:8]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "samples": 0}
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def time_oracle(cav, budget_s, max_steps=50, rows=None):
+    """MLUPS of the FP64 oracle on the host cores: steps of the same cavity (or of a
+    band of ``rows`` rows of it) until about ``budget_s`` seconds of work."""
+    import oracle as O
+
+    threads = O.set_threads(len(os.sched_getaffinity(0)))
+    ny = rows or cav.ny
+    m = O.derive(cav.nx, ny, cav.Ra, cav.Pr, cav.alpha)
+    from paper_1601_04633_gb300 import inputs
+
+    th = inputs.Cavity(cav.nx, ny, cav.Ra, cav.Pr, cav.alpha, seed=cav.seed).theta0()
+    f, g = O.init(m, th)
+    t0 = time.perf_counter()
+    O.run(m, 1, f, g)
+    t1 = time.perf_counter() - t0
+    steps = int(max(1, min(max_steps, budget_s / max(t1, 1e-9))))
+    t0 = time.perf_counter()
+    O.run(m, steps, f, g)
+    dt = time.perf_counter() - t0
+    return {"value": cav.nx * ny * steps / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{steps} fp64 oracle steps of {cav.nx}x{ny} (same Ra, Pr, alpha), {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    cav, label = workload(args.workload)
+    import oracle as O
+
+    threads = O.set_threads(len(os.sched_getaffinity(0)))
+    # Each step: one oracle time step of a band of the cavity sized so that the whole
+    # warmup + steps run stays within a couple of minutes.
+    budget_per_step = max(0.005, 120.0 / max(1, args.steps + args.warmup))
+    probe_rows = 64
+    m = O.derive(cav.nx, probe_rows, cav.Ra, cav.Pr, cav.alpha)
+    f, g = O.init(m, np.zeros((probe_rows, cav.nx)))
+    t0 = time.perf_counter()
+    O.run(m, 2, f, g)
+    rate = cav.nx * probe_rows * 2 / (time.perf_counter() - t0)
+    rows = int(max(4, min(cav.ny, budget_per_step * rate / cav.nx)))
+    m = O.derive(cav.nx, rows, cav.Ra, cav.Pr, cav.alpha)
+    from paper_1601_04633_gb300 import inputs
+
+    th = inputs.Cavity(cav.nx, rows, cav.Ra, cav.Pr, cav.alpha, seed=cav.seed).theta0()
+    f, g = O.init(m, th)
+    O.run(m, args.warmup, f, g)
+    t0 = time.perf_counter()
+    O.run(m, args.steps, f, g)
+    dt = time.perf_counter() - t0
+    value = cav.nx * rows * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": label, "sample_rows": rows},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"each step: one fp64 oracle step of {cav.nx}x{rows} rows of the cavity"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_dmrt(args):
+    import torch
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (there is no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_1601_04633_gb300 import dmrt as D
+    from paper_1601_04633_gb300 import inputs
+
+    cav, label = workload(args.workload)
+    cav.seed = cav.seed + 1000 * rank  # independent replica per rank
+    nodes = cav.nx * cav.ny
+    stream = torch.cuda.current_stream()
+
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1))
+    sim.step(args.warmup)
+    sim.check()
+    torch.cuda.synchronize()
+
+    props = torch.cuda.get_device_properties(local)
+    uuid = str(getattr(props, "uuid", "") or "")
+    sampler = ClockSampler(("GPU-" + uuid) if uuid and not uuid.startswith("GPU-") else uuid)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    sim.check()
+    nu_mean, _, _ = sim.nusselt()
+    sim.close()
+    del sim
+
+    # End to end through the public C ABI with host buffers: create from a pinned
+    # host temperature field (H2D), K steps, then the Nu series and the u, v, theta
+    # fields back to pinned host memory (D2H), all inside the timed region.
+    theta0 = torch.from_numpy(cav.theta0()).pin_memory()
+    outs = [torch.empty((cav.ny, cav.nx), dtype=torch.float32).pin_memory() for _ in range(3)]
+    p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha, nu_capacity=max(args.steps, 1))
+    wsb = D.dmrt_workspace_size(p)
+    workspace = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    series = np.zeros(max(args.steps, 1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    h = D.dmrt_create(p, theta0.numpy(), workspace.data_ptr(), wsb, stream.cuda_stream)
+    D.dmrt_step(h, args.steps)
+    _, _, series = D.dmrt_nusselt(h, cav.ny, args.steps)
+    D.dmrt_fields(h, outs[0].data_ptr(), outs[1].data_ptr(), outs[2].data_ptr(), False)
+    e2e_s = time.perf_counter() - t0
+    D.dmrt_destroy(h)
+    del workspace
+
+    t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms, e2e_s = t.tolist()
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
+
+    steps = max(args.steps, 1)
+    value = ws * nodes * args.steps / (ms / 1e3) / 1e6
+    per_launch_s = ms / 1e3 / steps
+    achieved = BYTES_PER_NODE_FP32 * nodes / per_launch_s / 1e9
+    peak, peak_src = hbm_peak()
+    traffic = ncu_traffic_per_launch(nodes)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": label, "nx": cav.nx, "ny": cav.ny, "Ra": cav.Ra, "Pr": cav.Pr,
+                   "alpha": cav.alpha, "storage": "fp32", "parallelism": f"{ws} independent cavities",
+                   "l2": "state (two 14-plane fp32 buffers) larger than L2: no flush"
+                   if BYTES_PER_NODE_FP32 * nodes > 129e6 else "state fits in L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} HBM copy bandwidth",
+                     "bytes_per_node": BYTES_PER_NODE_FP32, "kernel": "dmrt::step_kernel"},
+        "e2e": {"value": ws * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
+                "h2d_bytes_per_step": 8 * nodes / steps,
+                "d2h_bytes_per_step": (12 * nodes + 8 * args.steps) / steps},
+        "gpu_launches": args.steps,
+        "clocks": sampler.summary(),
+        "nu_mean_last": nu_mean,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = time_oracle(cav, budget_s=12.0)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=("dmrt", "reference"), default="dmrt")
+    ap.add_argument("--workload", default="cavity_4096", choices=("cavity_4096", "cavity_2048", "cavity_256", "cavity_64"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_dmrt(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

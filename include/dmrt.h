@@ -1,0 +1,174 @@
+/*
+ * dmrt — double-MRT thermal lattice Boltzmann time step on one GB300 (sm_103a).
+ *
+ * C ABI of libdmrt.so. The method is the one of Li, Yang & Zhang, "Double MRT
+ * thermal lattice Boltzmann method for simulating natural convection of low
+ * Prandtl number fluids" (arXiv 1601.04633):
+ *   - Sec. 2 (Eqs. 1-17): side-heated square cavity, left wall theta_hot,
+ *     right wall theta_cold, adiabatic top and bottom, no-slip everywhere;
+ *   - Sec. 3.1 (Eqs. 22-34): D2Q9 MRT flow lattice with the Boussinesq force
+ *     (Eqs. 26-27) and bounce-back no-slip walls;
+ *   - Sec. 3.2 (Eqs. 35-45): D2Q5 MRT temperature lattice, bounce-back on
+ *     adiabatic walls (Eq. 44), anti-bounce-back on fixed-temperature walls (Eq. 45);
+ *   - Eqs. 18-19: hot-wall Nusselt number, recorded every time step.
+ *
+ * Conventions (every entry point):
+ *   - Return 0 on success or a negative DMRT_E_* code; nothing throws.
+ *     dmrt_last_error() gives a message for the most recent failure of a context.
+ *   - Device memory is never allocated by the library. The caller provides one
+ *     device workspace of dmrt_workspace_size() bytes (256-byte aligned) at
+ *     creation and keeps it alive until dmrt_destroy(). Host memory for the
+ *     context itself is malloc'd by dmrt_create and freed by dmrt_destroy.
+ *   - All device work is enqueued on the CUDA stream given at creation
+ *     (a cudaStream_t passed as void*; NULL = the legacy default stream).
+ *     dmrt_step only enqueues; calls that return data to the host synchronise
+ *     that stream.
+ *   - A context is not thread-safe; distinct contexts are independent.
+ *   - Grid: nodes (i, j), 0 <= i < nx, 0 <= j < ny, cell-centred at x = i + 1/2,
+ *     y = j + 1/2 (lattice units, dx = dt = c = 1). Walls lie at x = 0, nx and
+ *     y = 0, ny (half-way bounce-back). H = ny. Host field arrays are row-major
+ *     [ny][nx] (index j * nx + i).
+ */
+#ifndef DMRT_H
+#define DMRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define DMRT_OK 0
+#define DMRT_E_ARG (-1)      /* invalid argument or size */
+#define DMRT_E_UNSTABLE (-2) /* parameters outside the model's valid range */
+#define DMRT_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define DMRT_E_DIVERGED (-4) /* a non-finite density or temperature was seen */
+#define DMRT_E_TIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define DMRT_E_SPACE (-6)    /* workspace or host buffer too small */
+#define DMRT_E_STATE (-7)    /* checkpoint does not match this context */
+
+/* Population storage precision. */
+#define DMRT_FP32 0
+#define DMRT_FP16 1
+#define DMRT_BF16 2
+
+/* Wall kinds for the left and right (vertical) walls. Top and bottom are
+ * always adiabatic (Eqs. 7-8, 44). */
+#define DMRT_WALL_FIXED 0     /* fixed temperature, anti-bounce-back (Eq. 45) */
+#define DMRT_WALL_ADIABATIC 1 /* zero heat flux, bounce-back (Eq. 44) */
+
+typedef struct {
+    int32_t nx, ny;     /* nodes; H = ny. 2 <= nx, ny <= 32768 */
+    double Ra;          /* Rayleigh number g beta dT H^3 / (nu alpha) (Eq. 9), >= 0 */
+    double Pr;          /* Prandtl number nu / alpha (Eq. 9), > 0 */
+    double alpha;       /* lattice thermal diffusivity; if <= 0 it is derived from Ma */
+    double Ma;          /* Mach number u_c / c_s (Eq. 9), used only when alpha <= 0:
+                           alpha = Ma H / sqrt(3 Ra Pr) */
+    double theta_hot;   /* left wall temperature (Eq. 14) */
+    double theta_cold;  /* right wall temperature (Eq. 15) */
+    double theta_ref;   /* buoyancy reference temperature theta_l (Eq. 27) */
+    double theta_init;  /* uniform initial temperature when no field is given */
+    int32_t left_wall;  /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
+    int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
+    int32_t storage;    /* DMRT_FP32 (DMRT_FP16 / DMRT_BF16 reserved) */
+    int32_t reserved;
+    int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
+} dmrt_params;
+
+/* Constants derived from dmrt_params (Eqs. 9, 31-32, 38-40, 43, 45). */
+typedef struct {
+    double nu;        /* kinematic viscosity Pr * alpha */
+    double alpha;     /* thermal diffusivity */
+    double s_e, s_nu, s_q, s_eps;  /* D2Q9 rates (Eq. 32) */
+    double sig_k, sig_e, sig_nu;   /* D2Q5 rates (Eq. 40) */
+    double a;         /* D2Q5 equilibrium parameter (Eq. 43) */
+    double gbeta;     /* buoyancy per unit theta: G_y = gbeta (theta - theta_ref) */
+    double abb;       /* 2 sqrt(3) alpha (Eq. 45) */
+    double Ma;        /* Mach number sqrt(3 gbeta dT H) */
+    double fo_per_step; /* Fourier number per step alpha / H^2 (Eq. 20) */
+} dmrt_consts;
+
+typedef struct dmrt_ctx dmrt_ctx;
+
+/* Fill *p with defaults: 64x64, Ra 1e4, Pr 0.01, alpha 0.1, walls +-0.5,
+ * theta_ref 0, theta_init 0, fixed-temperature side walls, FP32, ring 2^20. */
+void dmrt_default_params(dmrt_params* p);
+
+/* Validate *p and derive the model constants (host only, no GPU needed).
+ * Errors: DMRT_E_ARG (sizes, Pr <= 0, Ra < 0, no alpha and no Ma, walls equal
+ * with Ra > 0), DMRT_E_UNSTABLE (a outside (-4, 1), a rate outside (0, 2)). */
+int dmrt_derive(const dmrt_params* p, dmrt_consts* out);
+
+/* Device workspace bytes a context with these parameters needs. */
+int dmrt_workspace_size(const dmrt_params* p, size_t* bytes);
+
+/* Create a context. theta0: optional host array [ny][nx] of initial
+ * temperatures (NULL = theta_init everywhere). The initial state is the
+ * equilibrium at rest: f_i = 0 (delta-rho = 0, u = 0; the flow populations are
+ * stored shifted by w_i rho0, Eq. 33) and g_i = g_i_eq(theta0, u = 0) (Eq. 42);
+ * it counts as a post-collision state, so the first step starts with streaming.
+ * workspace: device pointer, 256-byte aligned, of at least
+ * dmrt_workspace_size() bytes; the context uses it until dmrt_destroy.
+ * stream: cudaStream_t as void*. Synchronises the stream before returning. */
+int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
+                size_t workspace_bytes, void* stream, dmrt_ctx** out);
+
+/* Enqueue nsteps time steps (nsteps >= 0). One step is one fused kernel:
+ * pull-stream f and g with the walls, moments, D2Q9 MRT collision (Eq. 28),
+ * buoyancy force (Eq. 26), D2Q5 MRT collision (Eq. 36), store, and the
+ * hot-wall Nusselt number of the pre-collision temperature (Eqs. 18-19)
+ * appended to the ring. Does not synchronise. */
+int dmrt_step(dmrt_ctx* c, int64_t nsteps);
+
+/* Synchronise the stream and report DMRT_E_DIVERGED if any step so far saw a
+ * non-finite density or temperature. */
+int dmrt_check(dmrt_ctx* c);
+
+/* Time steps taken so far. */
+int64_t dmrt_steps_done(const dmrt_ctx* c);
+
+/* Macroscopic fields at the current time level (pre-collision u, v, theta of
+ * the last step; Eqs. 33, 41), float32 arrays [ny][nx] owned by the caller.
+ * on_device != 0: u, v, theta are device pointers; else host pointers.
+ * Any of u, v, theta may be NULL. Synchronises. */
+int dmrt_fields(dmrt_ctx* c, float* u, float* v, float* theta, int on_device);
+
+/* Hot-wall Nusselt numbers (Eqs. 18-19), host outputs, all nullable:
+ *   nu_mean:  mean Nu of the last step;
+ *   nu_local: [ny] local Nu of the last step;
+ *   series:   up to cap most recent per-step mean values, oldest first;
+ *   count:    number of values written to series.
+ * Nu_j = H (8 theta_w(j) - 9 theta(0,j) + theta(1,j)) / (3 (theta_hot - theta_cold)).
+ * Synchronises; returns DMRT_E_DIVERGED if a non-finite value was seen. */
+int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
+                 int64_t cap, int64_t* count);
+
+/* Replace the left (hot) and right (cold) wall temperatures by per-row
+ * profiles theta_w(j) (host arrays [ny], nullable = keep). Used by Eq. 45 and
+ * by the Nusselt number. */
+int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold);
+
+/* Post-collision population state at the current time level as a dense host
+ * float32 array [14][ny][nx]: planes f_1..f_9 (Eq. 23 order; f stored shifted
+ * so that sum f_i = delta-rho, Eq. 33) then g_1..g_5 (Eq. 35 order).
+ * get: device -> host; set: host -> device (replaces the state; the step
+ * count and the Nusselt ring are unchanged). Both synchronise. */
+int dmrt_get_state(dmrt_ctx* c, float* host);
+int dmrt_set_state(dmrt_ctx* c, const float* host);
+
+/* Derived constants of a context. */
+int dmrt_get_consts(const dmrt_ctx* c, dmrt_consts* out);
+
+/* Message for the last failure on c (or of the last failed dmrt_create when c
+ * is NULL). Never NULL. */
+const char* dmrt_last_error(const dmrt_ctx* c);
+
+/* Release the context (not the caller's workspace). Synchronises. NULL is a no-op. */
+void dmrt_destroy(dmrt_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRT_H */

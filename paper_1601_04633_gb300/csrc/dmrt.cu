@@ -1,0 +1,566 @@
+// Host side of libdmrt.so: parameter derivation, workspace layout, the
+// init / fields kernels and the C entry points declared in include/dmrt.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "dmrt.h"
+#include "step_kernel.cuh"
+
+using dmrt::kPlanes;
+using dmrt::kThreads;
+
+namespace {
+
+thread_local char g_create_error[256] = "";
+
+struct Layout {
+    int pitch;            // elements per row (multiple of 128)
+    long long plane;      // elements per plane
+    size_t buf_bytes;     // one population buffer (14 planes)
+    size_t off_a, off_b, off_hot, off_cold, off_rows, off_ring, off_misc;
+    size_t total;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+Layout make_layout(const dmrt_params& p) {
+    Layout L;
+    L.pitch = ((p.nx + 127) / 128) * 128;
+    L.plane = (long long)p.ny * L.pitch;
+    L.buf_bytes = align256((size_t)kPlanes * (size_t)L.plane * sizeof(float));
+    size_t o = 0;
+    L.off_a = o; o += L.buf_bytes;
+    L.off_b = o; o += L.buf_bytes;
+    L.off_hot = o; o += align256((size_t)p.ny * sizeof(float));
+    L.off_cold = o; o += align256((size_t)p.ny * sizeof(float));
+    L.off_rows = o; o += align256((size_t)p.ny * sizeof(double));
+    L.off_ring = o; o += align256((size_t)p.nu_capacity * sizeof(double));
+    L.off_misc = o; o += 256;
+    L.total = o;
+    return L;
+}
+
+// Scalars kept on the device (one 256-byte block).
+struct Misc {
+    long long step;      // steps recorded in the Nu ring
+    double nu_last;      // mean Nu of the latest step
+    unsigned counter;    // rows reported in the running step
+    unsigned err;        // error bits
+};
+
+}  // namespace
+
+struct dmrt_ctx {
+    dmrt_params p;
+    dmrt_consts k;
+    Layout L;
+    char* ws;
+    cudaStream_t stream;
+    int cur;             // 0: state in buffer A, 1: in buffer B
+    long long t;         // steps enqueued
+    dmrt::StepConsts sc;
+    int wx_log2;
+    dim3 grid;
+    cudaGraphExec_t graph[2];
+    int graph_len;
+    char err[256];
+};
+
+namespace {
+
+void set_err(dmrt_ctx* c, const char* fmt, ...) {
+    char* dst = c ? c->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+}
+
+int cuda_fail(dmrt_ctx* c, cudaError_t e, const char* what) {
+    set_err(c, "%s: %s", what, cudaGetErrorString(e));
+    return DMRT_E_CUDA;
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+float* buf(dmrt_ctx* c, int which) {
+    return reinterpret_cast<float*>(c->ws + (which == 0 ? c->L.off_a : c->L.off_b));
+}
+Misc* misc(dmrt_ctx* c) { return reinterpret_cast<Misc*>(c->ws + c->L.off_misc); }
+
+dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
+    dmrt::StepArgs A;
+    A.src = buf(c, from);
+    A.dst = buf(c, 1 - from);
+    A.hot = reinterpret_cast<const float*>(c->ws + c->L.off_hot);
+    A.cold = reinterpret_cast<const float*>(c->ws + c->L.off_cold);
+    A.nu_rows = reinterpret_cast<double*>(c->ws + c->L.off_rows);
+    A.nu_ring = reinterpret_cast<double*>(c->ws + c->L.off_ring);
+    Misc* m = misc(c);
+    A.nu_last = &m->nu_last;
+    A.counter = &m->counter;
+    A.err = &m->err;
+    A.d_step = &m->step;
+    A.cap = c->p.nu_capacity;
+    A.plane = c->L.plane;
+    A.nx = c->p.nx;
+    A.ny = c->p.ny;
+    A.pitch = c->L.pitch;
+    A.wx_log2 = c->wx_log2;
+    return A;
+}
+
+// ---- small kernels ----------------------------------------------------------
+
+// Initial post-collision state: f = 0 (rest, delta-rho = 0) and g at the D2Q5
+// equilibrium of theta0 at rest, g_0 = (1 - a) theta / 5, g_1..4 = (4 + a) theta / 20
+// (Eq. 42 mapped back through N). Also zeroes the padding columns.
+__global__ void init_kernel(float* __restrict__ S, const double* __restrict__ theta0,
+                            double theta_const, double a, int nx, int ny, int pitch,
+                            long long plane) {
+    const long long n = (long long)ny * pitch;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / pitch), i = (int)(q % pitch);
+        double th = 0.0;
+        const bool in = i < nx;
+        if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
+        for (int k = 0; k < 9; ++k) S[k * plane + q] = 0.f;
+        S[9 * plane + q] = in ? (float)((1.0 - a) * th / 5.0) : 0.f;
+        const float side = in ? (float)((4.0 + a) * th / 20.0) : 0.f;
+        for (int k = 10; k < 14; ++k) S[k * plane + q] = side;
+    }
+}
+
+// Macroscopic fields of a post-collision state at the same time level:
+// theta = sum g* (the thermal collision keeps theta), u = sum e f*, and
+// v = sum e_y f* - G_y(theta) (the force added rho0 G to the momentum).
+__global__ void fields_kernel(const float* __restrict__ S, float* __restrict__ u,
+                              float* __restrict__ v, float* __restrict__ th, int nx, int ny,
+                              int pitch, long long plane, float gbeta, float theta_ref) {
+    const long long n = (long long)nx * ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        const long long s = (long long)j * pitch + i;
+        float f[9], g[5];
+        for (int k = 0; k < 9; ++k) f[k] = S[k * plane + s];
+        for (int k = 0; k < 5; ++k) g[k] = S[(9 + k) * plane + s];
+        const float jx = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
+        const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+        const float t = g[0] + g[1] + g[2] + g[3] + g[4];
+        if (u) u[q] = jx;
+        if (v) v[q] = jy - gbeta * (t - theta_ref);
+        if (th) th[q] = t;
+    }
+}
+
+__global__ void fill_kernel(float* p, const double* src, double value, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = (float)(src ? src[i] : value);
+}
+
+int validate(const dmrt_params* p, dmrt_ctx* c) {
+    if (!p) {
+        set_err(c, "params is NULL");
+        return DMRT_E_ARG;
+    }
+    if (p->nx < 2 || p->ny < 2 || p->nx > 32768 || p->ny > 32768) {
+        set_err(c, "grid %d x %d outside [2, 32768]", p->nx, p->ny);
+        return DMRT_E_ARG;
+    }
+    if (!(p->Pr > 0.0) || !(p->Ra >= 0.0) || !std::isfinite(p->Ra) || !std::isfinite(p->Pr)) {
+        set_err(c, "need Pr > 0 and finite Ra >= 0 (Pr=%g Ra=%g)", p->Pr, p->Ra);
+        return DMRT_E_ARG;
+    }
+    if (!(p->alpha > 0.0) && !(p->Ma > 0.0 && p->Ra > 0.0)) {
+        set_err(c, "give alpha > 0, or Ma > 0 with Ra > 0");
+        return DMRT_E_ARG;
+    }
+    if (p->left_wall < 0 || p->left_wall > 1 || p->right_wall < 0 || p->right_wall > 1) {
+        set_err(c, "wall kinds must be DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC");
+        return DMRT_E_ARG;
+    }
+    if (p->storage != DMRT_FP32) {
+        set_err(c, "storage %d not available in this build (only DMRT_FP32)", p->storage);
+        return DMRT_E_ARG;
+    }
+    if (p->nu_capacity < 1) {
+        set_err(c, "nu_capacity must be >= 1");
+        return DMRT_E_ARG;
+    }
+    const double dT = p->theta_hot - p->theta_cold;
+    if (!std::isfinite(dT) || (dT == 0.0 && p->Ra > 0.0)) {
+        set_err(c, "theta_hot - theta_cold must be finite and nonzero when Ra > 0");
+        return DMRT_E_ARG;
+    }
+    return DMRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dmrt_default_params(dmrt_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->nx = 64;
+    p->ny = 64;
+    p->Ra = 1e4;
+    p->Pr = 0.01;
+    p->alpha = 0.1;
+    p->Ma = 0.0;
+    p->theta_hot = 0.5;
+    p->theta_cold = -0.5;
+    p->theta_ref = 0.0;
+    p->theta_init = 0.0;
+    p->left_wall = DMRT_WALL_FIXED;
+    p->right_wall = DMRT_WALL_FIXED;
+    p->storage = DMRT_FP32;
+    p->nu_capacity = 1 << 20;
+}
+
+int dmrt_derive(const dmrt_params* p, dmrt_consts* out) {
+    int rc = validate(p, nullptr);
+    if (rc) return rc;
+    const double H = (double)p->ny;
+    const double dT = p->theta_hot - p->theta_cold;
+    dmrt_consts k;
+    // alpha from Ma: Ma = sqrt(3 g beta dT H) and g beta dT = Ra nu alpha / H^3
+    // = Ra Pr alpha^2 / H^3 (Eq. 9) give alpha = Ma H / sqrt(3 Ra Pr).
+    k.alpha = p->alpha > 0.0 ? p->alpha : p->Ma * H / std::sqrt(3.0 * p->Ra * p->Pr);
+    k.nu = p->Pr * k.alpha;
+    k.s_nu = 2.0 / (6.0 * k.nu + 1.0);               // Eq. 32
+    k.s_e = k.s_eps = k.s_nu;
+    k.s_q = 8.0 * (2.0 - k.s_nu) / (8.0 - k.s_nu);    // Eq. 32
+    const double inv_k = 0.5 + std::sqrt(3.0) / 6.0;  // 1/sigma_k, Eq. 40
+    const double inv_e = 0.5 + std::sqrt(3.0) / 3.0;  // 1/sigma_e = 1/sigma_nu, Eq. 40
+    k.sig_k = 1.0 / inv_k;
+    k.sig_e = k.sig_nu = 1.0 / inv_e;
+    k.a = 10.0 * k.alpha / (inv_k - 0.5) - 4.0;       // Eq. 43
+    k.gbeta = dT != 0.0 ? p->Ra * k.nu * k.alpha / (H * H * H) / dT : 0.0;
+    k.abb = 2.0 * std::sqrt(3.0) * k.alpha;           // Eq. 45
+    k.Ma = std::sqrt(3.0 * k.gbeta * dT * H);
+    k.fo_per_step = k.alpha / (H * H);                // Eq. 20
+    if (!(k.a > -4.0 && k.a < 1.0)) {
+        set_err(nullptr, "a = %g outside (-4, 1): alpha must lie in (0, %.6f)", k.a,
+                1.0 / (4.0 * std::sqrt(3.0)));
+        return DMRT_E_UNSTABLE;
+    }
+    if (!(k.s_nu > 0.0 && k.s_nu < 2.0 && k.s_q > 0.0 && k.s_q < 2.0)) {
+        set_err(nullptr, "relaxation rate outside (0, 2)");
+        return DMRT_E_UNSTABLE;
+    }
+    if (out) *out = k;
+    return DMRT_OK;
+}
+
+int dmrt_workspace_size(const dmrt_params* p, size_t* bytes) {
+    int rc = validate(p, nullptr);
+    if (rc) return rc;
+    if (!bytes) return DMRT_E_ARG;
+    *bytes = make_layout(*p).total;
+    return DMRT_OK;
+}
+
+int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
+                size_t workspace_bytes, void* stream, dmrt_ctx** out) {
+    if (!out) {
+        set_err(nullptr, "out is NULL");
+        return DMRT_E_ARG;
+    }
+    *out = nullptr;
+    dmrt_consts k;
+    int rc = dmrt_derive(p, &k);
+    if (rc) return rc;
+    Layout L = make_layout(*p);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        set_err(nullptr, "workspace must be a 256-byte aligned device pointer");
+        return DMRT_E_ARG;
+    }
+    if (workspace_bytes < L.total) {
+        set_err(nullptr, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+        return DMRT_E_SPACE;
+    }
+    dmrt_ctx* c = new (std::nothrow) dmrt_ctx();
+    if (!c) {
+        set_err(nullptr, "out of host memory");
+        return DMRT_E_SPACE;
+    }
+    c->p = *p;
+    c->k = k;
+    c->L = L;
+    c->ws = static_cast<char*>(workspace);
+    c->stream = static_cast<cudaStream_t>(stream);
+    c->cur = 0;
+    c->t = 0;
+    c->graph[0] = c->graph[1] = nullptr;
+    c->graph_len = 64;
+    c->err[0] = 0;
+
+    dmrt::StepConsts& s = c->sc;
+    s.se36 = (float)(k.s_e / 36.0);
+    s.snu4 = (float)(k.s_nu / 4.0);
+    s.sq12 = (float)(k.s_q / 12.0);
+    s.seps36 = (float)(k.s_eps / 36.0);
+    s.sk2 = (float)(k.sig_k / 2.0);
+    s.se20 = (float)(k.sig_e / 20.0);
+    s.snu4t = (float)(k.sig_nu / 4.0);
+    s.a = (float)k.a;
+    s.gbeta = (float)k.gbeta;
+    s.theta_ref = (float)p->theta_ref;
+    s.abb = (float)k.abb;
+    s.left_fixed = p->left_wall == DMRT_WALL_FIXED;
+    s.right_fixed = p->right_wall == DMRT_WALL_FIXED;
+    const double dT = p->theta_hot - p->theta_cold;
+    s.nu_scale = dT != 0.0 ? (double)p->ny / (3.0 * dT) : 0.0;
+
+    const int nxq = (p->nx + 3) / 4;
+    int wx = 1;
+    while (wx < nxq && wx < 32) wx <<= 1;
+    c->wx_log2 = 0;
+    while ((1 << c->wx_log2) < wx) ++c->wx_log2;
+    const int rows_per_block = (kThreads / 32) * (32 / wx);
+    c->grid = dim3((nxq + wx - 1) / wx, (p->ny + rows_per_block - 1) / rows_per_block, 1);
+
+    auto fail = [&](int code) {
+        std::snprintf(g_create_error, sizeof g_create_error, "%s", c->err);
+        delete c;
+        return code;
+    };
+    // Zero the scalars and the ring, set the wall profiles, write the initial state.
+    if (cudaMemsetAsync(c->ws + L.off_hot, 0, L.total - L.off_hot, c->stream) != cudaSuccess)
+        return fail(cuda_fail(c, cudaGetLastError(), "cudaMemsetAsync"));
+    fill_kernel<<<(p->ny + 255) / 256, 256, 0, c->stream>>>(
+        reinterpret_cast<float*>(c->ws + L.off_hot), nullptr, p->theta_hot, p->ny);
+    fill_kernel<<<(p->ny + 255) / 256, 256, 0, c->stream>>>(
+        reinterpret_cast<float*>(c->ws + L.off_cold), nullptr, p->theta_cold, p->ny);
+    const double* d_theta0 = nullptr;
+    if (theta0) {
+        // Stage the host field in buffer B (not yet used: it holds 56 bytes per node).
+        double* stage = reinterpret_cast<double*>(c->ws + L.off_b);
+        cudaError_t e = cudaMemcpyAsync(stage, theta0, (size_t)p->nx * p->ny * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) return fail(cuda_fail(c, e, "copy theta0"));
+        d_theta0 = stage;
+    }
+    init_kernel<<<1024, 256, 0, c->stream>>>(buf(c, 0), d_theta0, p->theta_init, k.a, p->nx,
+                                             p->ny, L.pitch, L.plane);
+    // Buffer B's padding columns must read as zero too.
+    init_kernel<<<1024, 256, 0, c->stream>>>(buf(c, 1), nullptr, 0.0, k.a, p->nx, p->ny,
+                                             L.pitch, L.plane);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "init kernels"));
+    e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "init synchronize"));
+    *out = c;
+    return DMRT_OK;
+}
+
+static int launch_one(dmrt_ctx* c) {
+    dmrt::StepArgs A = step_args(c, c->cur);
+    dmrt::step_kernel<<<c->grid, kThreads, 0, c->stream>>>(A, c->sc);
+    c->cur ^= 1;
+    c->t += 1;
+    return DMRT_OK;
+}
+
+// A graph of graph_len (even) steps starting from buffer `from`, built node by
+// node (no stream capture, so it works on any stream, the legacy default included).
+static int build_graph(dmrt_ctx* c, int from) {
+    cudaGraph_t g;
+    CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    cudaGraphNode_t prev = nullptr;
+    dmrt::StepArgs args[2] = {step_args(c, from), step_args(c, 1 - from)};
+    for (int i = 0; i < c->graph_len; ++i) {
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)dmrt::step_kernel;
+        kp.gridDim = c->grid;
+        kp.blockDim = dim3(kThreads, 1, 1);
+        kp.sharedMemBytes = 0;
+        void* params[2] = {&args[i & 1], &c->sc};
+        kp.kernelParams = params;
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_fail(c, e, "cudaGraphAddKernelNode");
+        }
+        prev = node;
+    }
+    cudaError_t e = cudaGraphInstantiate(&c->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGraphInstantiate");
+    return DMRT_OK;
+}
+
+int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
+    if (!c || nsteps < 0) return DMRT_E_ARG;
+    while (nsteps > 0) {
+        if (nsteps >= c->graph_len) {
+            if (!c->graph[c->cur]) {
+                int rc = build_graph(c, c->cur);
+                if (rc) return rc;
+            }
+            CK(cudaGraphLaunch(c->graph[c->cur], c->stream), "cudaGraphLaunch");
+            c->t += c->graph_len;  // even length: the state stays in the same buffer
+            nsteps -= c->graph_len;
+        } else {
+            launch_one(c);
+            nsteps -= 1;
+        }
+    }
+    CK(cudaGetLastError(), "step launch");
+    return DMRT_OK;
+}
+
+int dmrt_check(dmrt_ctx* c) {
+    if (!c) return DMRT_E_ARG;
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, &misc(c)->err, sizeof err, cudaMemcpyDeviceToHost), "read error flag");
+    if (err & 1u) {
+        set_err(c, "non-finite density or temperature after %lld steps", c->t);
+        return DMRT_E_DIVERGED;
+    }
+    return DMRT_OK;
+}
+
+int64_t dmrt_steps_done(const dmrt_ctx* c) { return c ? c->t : -1; }
+
+int dmrt_fields(dmrt_ctx* c, float* u, float* v, float* theta, int on_device) {
+    if (!c) return DMRT_E_ARG;
+    const dmrt_params& p = c->p;
+    const long long n = (long long)p.nx * p.ny;
+    float *du = u, *dv = v, *dt = theta;
+    if (!on_device) {
+        // Host outputs: stage in the idle population buffer (no allocation).
+        float* stage = buf(c, 1 - c->cur);
+        du = u ? stage : nullptr;
+        dv = v ? stage + n : nullptr;
+        dt = theta ? stage + 2 * n : nullptr;
+    }
+    const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
+    fields_kernel<<<blocks, 256, 0, c->stream>>>(buf(c, c->cur), du, dv, dt, p.nx, p.ny,
+                                                 c->L.pitch, c->L.plane, c->sc.gbeta,
+                                                 c->sc.theta_ref);
+    CK(cudaGetLastError(), "fields kernel");
+    if (!on_device) {
+        if (u) CK(cudaMemcpyAsync(u, du, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy u");
+        if (v) CK(cudaMemcpyAsync(v, dv, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy v");
+        if (theta) CK(cudaMemcpyAsync(theta, dt, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy theta");
+    }
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DMRT_OK;
+}
+
+int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series, int64_t cap,
+                 int64_t* count) {
+    if (!c || (series && cap < 0)) return DMRT_E_ARG;
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    Misc m;
+    CK(cudaMemcpy(&m, misc(c), sizeof m, cudaMemcpyDeviceToHost), "read scalars");
+    if (nu_mean) *nu_mean = m.nu_last;
+    if (nu_local)
+        CK(cudaMemcpy(nu_local, c->ws + c->L.off_rows, (size_t)c->p.ny * sizeof(double),
+                      cudaMemcpyDeviceToHost), "copy local Nu");
+    long long written = 0;
+    if (series && cap > 0) {
+        const long long R = c->p.nu_capacity;
+        long long avail = std::min<long long>(m.step, R);
+        long long want = std::min<long long>(avail, cap);
+        long long first = m.step - want;  // step index of the oldest value returned
+        const double* ring = reinterpret_cast<const double*>(c->ws + c->L.off_ring);
+        long long done = 0;
+        while (done < want) {
+            long long slot = (first + done) % R;
+            long long run = std::min<long long>(want - done, R - slot);
+            CK(cudaMemcpy(series + done, ring + slot, run * sizeof(double), cudaMemcpyDeviceToHost),
+               "copy Nu series");
+            done += run;
+        }
+        written = want;
+    }
+    if (count) *count = written;
+    if (m.err & 1u) {
+        set_err(c, "non-finite density or temperature after %lld steps", c->t);
+        return DMRT_E_DIVERGED;
+    }
+    return DMRT_OK;
+}
+
+int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold) {
+    if (!c) return DMRT_E_ARG;
+    const int ny = c->p.ny;
+    // Stage through the idle buffer, convert to float on the device.
+    double* stage = reinterpret_cast<double*>(buf(c, 1 - c->cur));
+    if (hot) {
+        CK(cudaMemcpyAsync(stage, hot, ny * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy hot");
+        fill_kernel<<<(ny + 255) / 256, 256, 0, c->stream>>>(
+            reinterpret_cast<float*>(c->ws + c->L.off_hot), stage, 0.0, ny);
+    }
+    if (cold) {
+        CK(cudaMemcpyAsync(stage + ny, cold, ny * sizeof(double), cudaMemcpyHostToDevice, c->stream), "copy cold");
+        fill_kernel<<<(ny + 255) / 256, 256, 0, c->stream>>>(
+            reinterpret_cast<float*>(c->ws + c->L.off_cold), stage + ny, 0.0, ny);
+    }
+    CK(cudaGetLastError(), "profile kernel");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DMRT_OK;
+}
+
+// Copy between a dense host array [14][ny][nx] of float32 and the padded
+// device planes of the current state (2D copies, one per plane).
+int dmrt_get_state(dmrt_ctx* c, float* host) {
+    if (!c || !host) return DMRT_E_ARG;
+    const dmrt_params& p = c->p;
+    const float* S = buf(c, c->cur);
+    for (int k = 0; k < kPlanes; ++k)
+        CK(cudaMemcpy2DAsync(host + (size_t)k * p.nx * p.ny, (size_t)p.nx * sizeof(float),
+                             S + (size_t)k * c->L.plane, (size_t)c->L.pitch * sizeof(float),
+                             (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyDeviceToHost, c->stream),
+           "copy state to host");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DMRT_OK;
+}
+
+int dmrt_set_state(dmrt_ctx* c, const float* host) {
+    if (!c || !host) return DMRT_E_ARG;
+    const dmrt_params& p = c->p;
+    float* S = buf(c, c->cur);
+    for (int k = 0; k < kPlanes; ++k)
+        CK(cudaMemcpy2DAsync(S + (size_t)k * c->L.plane, (size_t)c->L.pitch * sizeof(float),
+                             host + (size_t)k * p.nx * p.ny, (size_t)p.nx * sizeof(float),
+                             (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyHostToDevice, c->stream),
+           "copy state to device");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DMRT_OK;
+}
+
+int dmrt_get_consts(const dmrt_ctx* c, dmrt_consts* out) {
+    if (!c || !out) return DMRT_E_ARG;
+    *out = c->k;
+    return DMRT_OK;
+}
+
+const char* dmrt_last_error(const dmrt_ctx* c) { return c ? c->err : g_create_error; }
+
+void dmrt_destroy(dmrt_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 2; ++i)
+        if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,306 @@
+"""Python binding of libdmrt.so (the C ABI of include/dmrt.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA
+kernels. PyTorch provides the device workspace (its caching allocator) and
+the CUDA stream. There is no CPU fallback: if the library is missing or no GPU
+is present, the calls raise.
+
+Low-level functions carry the C names (``dmrt_create``, ``dmrt_step``, ...);
+``Cavity2D`` bundles them with a torch-owned workspace.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libdmrt.so")
+
+DMRT_OK = 0
+DMRT_E_ARG = -1
+DMRT_E_UNSTABLE = -2
+DMRT_E_CUDA = -3
+DMRT_E_DIVERGED = -4
+DMRT_E_TIMEOUT = -5
+DMRT_E_SPACE = -6
+DMRT_E_STATE = -7
+DMRT_FP32, DMRT_FP16, DMRT_BF16 = 0, 1, 2
+DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
+
+_ERRNAMES = {-1: "DMRT_E_ARG", -2: "DMRT_E_UNSTABLE", -3: "DMRT_E_CUDA", -4: "DMRT_E_DIVERGED",
+             -5: "DMRT_E_TIMEOUT", -6: "DMRT_E_SPACE", -7: "DMRT_E_STATE"}
+
+
+class DmrtError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("Ra", ctypes.c_double), ("Pr", ctypes.c_double),
+        ("alpha", ctypes.c_double), ("Ma", ctypes.c_double),
+        ("theta_hot", ctypes.c_double), ("theta_cold", ctypes.c_double),
+        ("theta_ref", ctypes.c_double), ("theta_init", ctypes.c_double),
+        ("left_wall", ctypes.c_int32), ("right_wall", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("nu_capacity", ctypes.c_int64),
+    ]
+
+
+class Consts(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "nu", "alpha", "s_e", "s_nu", "s_q", "s_eps", "sig_k", "sig_e", "sig_nu",
+        "a", "gbeta", "abb", "Ma", "fo_per_step")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+_lock = threading.Lock()
+
+# Exported symbols and their signatures: (restype, argtypes).
+_VP = ctypes.c_void_p
+_DP = ctypes.POINTER(ctypes.c_double)
+_FP = ctypes.POINTER(ctypes.c_float)
+SIGNATURES = {
+    "dmrt_default_params": (None, [ctypes.POINTER(Params)]),
+    "dmrt_derive": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(Consts)]),
+    "dmrt_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_create": (ctypes.c_int, [ctypes.POINTER(Params), _DP, _VP, ctypes.c_size_t, _VP,
+                                   ctypes.POINTER(_VP)]),
+    "dmrt_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "dmrt_check": (ctypes.c_int, [_VP]),
+    "dmrt_steps_done": (ctypes.c_int64, [_VP]),
+    "dmrt_fields": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int]),
+    "dmrt_nusselt": (ctypes.c_int, [_VP, _DP, _DP, _DP, ctypes.c_int64,
+                                    ctypes.POINTER(ctypes.c_int64)]),
+    "dmrt_set_wall_profiles": (ctypes.c_int, [_VP, _DP, _DP]),
+    "dmrt_get_consts": (ctypes.c_int, [_VP, ctypes.POINTER(Consts)]),
+    "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
+    "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
+    "dmrt_last_error": (ctypes.c_char_p, [_VP]),
+    "dmrt_destroy": (None, [_VP]),
+}
+
+
+def load():
+    """Load libdmrt.so (built by ``paper_1601_04633_gb300.build``); raise if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"{LIB_PATH} is missing: build it with `python -m paper_1601_04633_gb300.build` "
+                    "(there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc, handle=None):
+    if rc != DMRT_OK:
+        msg = load().dmrt_last_error(handle)
+        raise DmrtError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(_DP)
+
+
+# ---- same-name wrappers ------------------------------------------------------
+
+def dmrt_default_params() -> Params:
+    p = Params()
+    load().dmrt_default_params(ctypes.byref(p))
+    return p
+
+
+def dmrt_derive(p: Params) -> Consts:
+    k = Consts()
+    _check(load().dmrt_derive(ctypes.byref(p), ctypes.byref(k)))
+    return k
+
+
+def dmrt_workspace_size(p: Params) -> int:
+    n = ctypes.c_size_t()
+    _check(load().dmrt_workspace_size(ctypes.byref(p), ctypes.byref(n)))
+    return n.value
+
+
+def dmrt_create(p: Params, theta0, workspace_ptr: int, workspace_bytes: int, stream_ptr: int):
+    """theta0: None or a float64 host array [ny][nx] (C order)."""
+    h = _VP()
+    th = None
+    if theta0 is not None:
+        th = np.ascontiguousarray(theta0, dtype=np.float64)
+        if th.size != p.nx * p.ny:
+            raise ValueError("theta0 must hold nx * ny values")
+    _check(load().dmrt_create(ctypes.byref(p), _dptr(th), _VP(workspace_ptr), workspace_bytes,
+                              _VP(stream_ptr), ctypes.byref(h)))
+    return h
+
+
+def dmrt_step(h, n: int):
+    _check(load().dmrt_step(h, int(n)), h)
+
+
+def dmrt_check(h):
+    _check(load().dmrt_check(h), h)
+
+
+def dmrt_steps_done(h) -> int:
+    return load().dmrt_steps_done(h)
+
+
+def dmrt_fields(h, u_ptr, v_ptr, theta_ptr, on_device: bool):
+    _check(load().dmrt_fields(h, _VP(u_ptr), _VP(v_ptr), _VP(theta_ptr), int(bool(on_device))), h)
+
+
+def dmrt_nusselt(h, ny: int, cap: int = 0):
+    """Returns (nu_mean, nu_local[ny], series[count]) as numpy float64."""
+    mean = ctypes.c_double()
+    local = np.zeros(ny)
+    series = np.zeros(max(cap, 0))
+    count = ctypes.c_int64()
+    _check(load().dmrt_nusselt(h, ctypes.byref(mean), _dptr(local),
+                               _dptr(series) if cap > 0 else None, int(cap), ctypes.byref(count)), h)
+    return mean.value, local, series[: count.value]
+
+
+def dmrt_set_wall_profiles(h, hot=None, cold=None):
+    hp = None if hot is None else np.ascontiguousarray(hot, dtype=np.float64)
+    cp = None if cold is None else np.ascontiguousarray(cold, dtype=np.float64)
+    _check(load().dmrt_set_wall_profiles(h, _dptr(hp), _dptr(cp)), h)
+
+
+def dmrt_get_consts(h) -> Consts:
+    k = Consts()
+    _check(load().dmrt_get_consts(h, ctypes.byref(k)), h)
+    return k
+
+
+def dmrt_get_state(h, nx: int, ny: int) -> np.ndarray:
+    out = np.empty((14, ny, nx), dtype=np.float32)
+    _check(load().dmrt_get_state(h, out.ctypes.data_as(_FP)), h)
+    return out
+
+
+def dmrt_set_state(h, state):
+    a = np.ascontiguousarray(state, dtype=np.float32)
+    _check(load().dmrt_set_state(h, a.ctypes.data_as(_FP)), h)
+
+
+def dmrt_destroy(h):
+    load().dmrt_destroy(h)
+
+
+# ---- convenience object --------------------------------------------------------
+
+def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.5,
+                theta_ref=None, theta_init=0.0, left_wall=DMRT_WALL_FIXED,
+                right_wall=DMRT_WALL_FIXED, storage=DMRT_FP32, nu_capacity=1 << 20) -> Params:
+    p = dmrt_default_params()
+    p.nx, p.ny, p.Ra, p.Pr, p.alpha, p.Ma = int(nx), int(ny), float(Ra), float(Pr), float(alpha), float(Ma)
+    p.theta_hot, p.theta_cold = float(theta_hot), float(theta_cold)
+    p.theta_ref = 0.5 * (theta_hot + theta_cold) if theta_ref is None else float(theta_ref)
+    p.theta_init = float(theta_init)
+    p.left_wall, p.right_wall, p.storage = int(left_wall), int(right_wall), int(storage)
+    p.nu_capacity = int(nu_capacity)
+    return p
+
+
+class Cavity2D:
+    """One side-heated cavity on the GPU, backed by a torch-allocated workspace."""
+
+    def __init__(self, params: Params, theta0=None, device="cuda", stream=None,
+                 theta_hot_profile=None):
+        import torch
+
+        self.p = params
+        self.nx, self.ny = params.nx, params.ny
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = dmrt_workspace_size(params)
+        # 256-byte aligned: torch's caching allocator returns 512-byte aligned blocks.
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        assert self.workspace.data_ptr() % 256 == 0
+        self.h = dmrt_create(params, theta0, self.workspace.data_ptr(), nbytes,
+                             self.stream.cuda_stream)
+        self.consts = dmrt_get_consts(self.h)
+        if theta_hot_profile is not None:
+            dmrt_set_wall_profiles(self.h, hot=theta_hot_profile)
+
+    @classmethod
+    def from_inputs(cls, cav, **kw):
+        """From a ``paper_1601_04633_gb300.inputs.Cavity`` description."""
+        p = make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha, theta_hot=cav.theta_hot,
+                        theta_cold=cav.theta_cold, theta_init=cav.theta_init,
+                        **{k: v for k, v in kw.items() if k in ("storage", "nu_capacity",
+                                                                   "left_wall", "right_wall",
+                                                                   "theta_ref")})
+        rest = {k: v for k, v in kw.items() if k in ("device", "stream")}
+        return cls(p, theta0=cav.theta0(), theta_hot_profile=cav.theta_hot_profile, **rest)
+
+    def step(self, n: int):
+        dmrt_step(self.h, n)
+
+    def check(self):
+        dmrt_check(self.h)
+
+    @property
+    def steps_done(self) -> int:
+        return dmrt_steps_done(self.h)
+
+    def fields(self):
+        """(u, v, theta) as float32 CUDA tensors [ny][nx]."""
+        import torch
+
+        out = [torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device) for _ in range(3)]
+        dmrt_fields(self.h, out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), True)
+        return tuple(out)
+
+    def fields_host(self, pinned=None):
+        """(u, v, theta) as float32 numpy arrays [ny][nx], copied by the library."""
+        if pinned is None:
+            out = [np.empty((self.ny, self.nx), dtype=np.float32) for _ in range(3)]
+            ptrs = [a.ctypes.data for a in out]
+        else:
+            out = pinned
+            ptrs = [t.data_ptr() for t in pinned]
+        dmrt_fields(self.h, ptrs[0], ptrs[1], ptrs[2], False)
+        return tuple(out) if pinned is None else tuple(t.numpy() for t in pinned)
+
+    def get_state(self) -> np.ndarray:
+        """Post-collision populations [14][ny][nx] (f_1..f_9, g_1..g_5), float32."""
+        return dmrt_get_state(self.h, self.nx, self.ny)
+
+    def set_state(self, state):
+        dmrt_set_state(self.h, state)
+
+    def nusselt(self, series_cap: int = 0):
+        return dmrt_nusselt(self.h, self.ny, series_cap)
+
+    def close(self):
+        if getattr(self, "h", None):
+            dmrt_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,102 @@
+"""CPU checks of the C ABI: the library builds, loads and exports every symbol the
+header declares, and its host-side parameter logic agrees with the oracle's own
+derivation (no GPU work is done here)."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def D():
+    from paper_1601_04633_gb300 import build
+
+    build.build_library()
+    from paper_1601_04633_gb300 import dmrt
+
+    dmrt.load()
+    return dmrt
+
+
+def _declared(header):
+    with open(os.path.join(ROOT, "include", header)) as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dmrt_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported_and_bound(D):
+    names = _declared("dmrt.h")
+    assert "dmrt_create" in names and "dmrt_step" in names
+    L = D.load()
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in D.SIGNATURES, f"binding lacks {n}"
+
+
+def test_default_params(D):
+    p = D.dmrt_default_params()
+    assert (p.nx, p.ny, p.Ra, p.Pr, p.alpha) == (64, 64, 1e4, 0.01, 0.1)
+    assert (p.theta_hot, p.theta_cold, p.theta_ref) == (0.5, -0.5, 0.0)
+    assert p.storage == D.DMRT_FP32 and p.nu_capacity == 1 << 20
+
+
+@pytest.mark.parametrize("nx,ny,Ra,Pr,alpha", [(64, 64, 1e4, 0.01, 0.1), (256, 256, 1e5, 0.005, 0.1),
+                                               (4096, 4096, 1e7, 0.001, 0.1), (50, 20, 3e3, 0.7, 0.03)])
+def test_derive_matches_oracle(D, nx, ny, Ra, Pr, alpha):
+    k = D.dmrt_derive(D.make_params(nx, ny, Ra, Pr, alpha))
+    m = O.derive(nx, ny, Ra, Pr, alpha)
+    for a, b in ((k.nu, m.nu), (k.s_nu, m.s_nu), (k.s_q, m.s_q), (k.s_e, m.s_e), (k.s_eps, m.s_eps),
+                 (k.sig_k, m.sig_k), (k.sig_e, m.sig_e), (k.sig_nu, m.sig_nu), (k.a, m.a),
+                 (k.gbeta, m.gbeta), (k.abb, m.abb_coef)):
+        assert a == pytest.approx(b, rel=1e-13)
+    assert k.fo_per_step == pytest.approx(alpha / ny ** 2, rel=1e-14)
+
+
+def test_alpha_from_mach(D):
+    # Eq. 9: Ma = u_c / c_s with u_c^2 = g beta dT H and g beta dT = Ra nu alpha / H^3.
+    k1 = D.dmrt_derive(D.make_params(128, 128, 1e5, 0.01, 0.1))
+    k2 = D.dmrt_derive(D.make_params(128, 128, 1e5, 0.01, alpha=0.0, Ma=k1.Ma))
+    assert k2.alpha == pytest.approx(0.1, rel=1e-13)
+    # Fo = tau Ma / sqrt(3 Ra Pr) (Eq. 21) with tau = t c / H (Eq. 9) equals alpha t / H^2 (Eq. 20).
+    t = 1000
+    assert (t / 128) * k1.Ma / np.sqrt(3 * 1e5 * 0.01) == pytest.approx(k1.fo_per_step * t, rel=1e-12)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nx=1), -1), (dict(ny=40000), -1), (dict(Pr=0.0), -1), (dict(Ra=-1.0), -1),
+    (dict(alpha=0.0, Ma=0.0), -1), (dict(alpha=0.2), -2), (dict(theta_hot=0.0, theta_cold=0.0), -1),
+    (dict(storage=7), -1), (dict(nu_capacity=0), -1), (dict(left_wall=3), -1),
+])
+def test_invalid_params_rejected(D, kw, code):
+    base = dict(nx=64, ny=64, Ra=1e4, Pr=0.01, alpha=0.1)
+    base.update({k: v for k, v in kw.items() if k in base})
+    p = D.make_params(**base)
+    for k, v in kw.items():
+        if k not in base:
+            setattr(p, k, v)
+    with pytest.raises(D.DmrtError) as ei:
+        D.dmrt_derive(p)
+    assert ei.value.code == code
+    assert D.load().dmrt_last_error(None)
+
+
+def test_workspace_size(D):
+    p = D.make_params(4096, 4096, 1e7, 0.001, 0.1)
+    n = D.dmrt_workspace_size(p)
+    # Two 14-plane float32 buffers of 4096 x 4096 plus small arrays.
+    assert 2 * 14 * 4 * 4096 * 4096 <= n < 2 * 14 * 4 * 4096 * 4096 + (16 << 20)
+    p2 = D.make_params(130, 7, 1e4, 0.01, 0.1)
+    assert D.dmrt_workspace_size(p2) >= 2 * 14 * 4 * 256 * 7  # rows padded to 128 elements
+
+
+def test_create_without_workspace_fails_cleanly(D):
+    p = D.make_params(64, 64, 1e4, 0.01, 0.1)
+    with pytest.raises(D.DmrtError) as ei:
+        D.dmrt_create(p, None, 0, 0, 0)
+    assert ei.value.code == D.DMRT_E_ARG

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (the double-MRT step in float32 against fp64):
+  fields u, v, theta: max_x |gpu - oracle| / max_x |oracle| <= 1e-5 per field;
+  mean hot-wall Nusselt number, every step: |gpu - oracle| / |oracle| <= 1e-4;
+  one step from a given state: every population within 1e-5 of the plane's
+  largest magnitude (float32 rounding of ~10 operations is ~1e-6 of that).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_04633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+NU_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def D():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1601_04633_gb300 import dmrt
+
+    return dmrt
+
+
+def rel_err(a, b):
+    return np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def gpu_run(D, cav, steps, **kw):
+    sim = D.Cavity2D.from_inputs(cav, **kw)
+    sim.step(steps)
+    sim.check()
+    u, v, t = (x.cpu().numpy().astype(np.float64) for x in sim.fields())
+    mean, local, series = sim.nusselt(series_cap=steps)
+    state = sim.get_state()
+    sim.close()
+    return dict(u=u, v=v, theta=t, nu=mean, nu_local=local, nu_series=series, state=state)
+
+
+def oracle_run(cav, steps, left_bc=O.WALL_FIXED, right_bc=O.WALL_FIXED):
+    m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha, theta_hot=cav.theta_hot,
+                 theta_cold=cav.theta_cold, left_bc=left_bc, right_bc=right_bc)
+    f, g = O.init(m, cav.theta0())
+    r = O.run(m, steps, f, g, theta_hot_profile=cav.theta_hot_profile)
+    r["f"], r["g"], r["model"] = f, g, m
+    return r
+
+
+def assert_parity(gpu, ref, field_tol=FIELD_TOL, nu_tol=NU_TOL):
+    for name in ("u", "v", "theta"):
+        e = rel_err(gpu[name], ref[name])
+        assert e <= field_tol, f"{name}: {e:.3e}"
+    nu_ref = ref["nu_series"]
+    assert len(gpu["nu_series"]) == len(nu_ref)
+    e = (np.abs(gpu["nu_series"] - nu_ref) / np.abs(nu_ref)).max()
+    assert e <= nu_tol, f"Nu series: {e:.3e}"
+    e = np.abs(gpu["nu_local"] - ref["nu_local"]).max() / np.abs(ref["nu_local"]).max()
+    assert e <= nu_tol, f"local Nu: {e:.3e}"
+
+
+def test_parity_cavity_64_1000_steps(D):
+    # 64 x 64, Ra 1e4, Pr 0.01, alpha 0.1, seeded 1e-6 noise (the paper's Case 1).
+    cav = inputs.cavity_64()
+    assert_parity(gpu_run(D, cav, 1000), oracle_run(cav, 1000))
+
+
+def test_parity_oscillatory_256_1000_steps(D):
+    cav = inputs.cavity_256_oscillatory()
+    assert_parity(gpu_run(D, cav, 1000), oracle_run(cav, 1000))
+
+
+@pytest.mark.parametrize("nx,ny", [(300, 70), (67, 45), (130, 9), (2, 2), (5, 3), (3, 17), (129, 130)])
+def test_parity_ragged_shapes(D, nx, ny):
+    # Several tiles in x and y with ragged tails, and degenerate tiny grids.
+    cav = inputs.Cavity(nx, ny, 1e5, 0.01, noise_amp=1e-2, seed=nx * 1000 + ny)
+    assert_parity(gpu_run(D, cav, 300), oracle_run(cav, 300))
+
+
+def test_parity_wall_profile_and_adiabatic_right_wall(D):
+    cav = inputs.Cavity(96, 80, 1e5, 0.005, noise_amp=1e-3, seed=21)
+    cav.theta_hot_profile = 0.5 + 0.05 * np.sin(np.linspace(0, 3, 80))
+    g = gpu_run(D, cav, 500, right_wall=D.DMRT_WALL_ADIABATIC)
+    r = oracle_run(cav, 500, right_bc=O.WALL_ADIABATIC)
+    assert_parity(g, r)
+
+
+def test_parity_adjoint_config_shape(D):
+    # 128 x 128, Ra 1e5, Pr 0.01 with the perturbed hot-wall profile 0.5 + 0.01 N(0,1).
+    cav = inputs.cavity_128_adjoint()
+    assert_parity(gpu_run(D, cav, 1000), oracle_run(cav, 1000))
+
+
+def test_energy_conserved_with_adiabatic_walls(D):
+    cav = inputs.Cavity(100, 60, 1e5, 0.01, noise_amp=0.2, seed=22)
+    p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, left_wall=D.DMRT_WALL_ADIABATIC,
+                      right_wall=D.DMRT_WALL_ADIABATIC)
+    sim = D.Cavity2D(p, theta0=cav.theta0())
+    th0 = sim.fields()[2].double().sum().item()
+    sim.step(2000)
+    sim.check()
+    th1 = sim.fields()[2].double().sum().item()
+    sim.close()
+    assert abs(th1 - th0) <= 1e-6 * np.abs(cav.theta0()).sum()
+
+
+def _random_state(nx, ny, seed):
+    # A plausible post-collision state: shifted D2Q9 equilibria of random
+    # (delta-rho, u, v) plus noise, and D2Q5 populations around theta in [-0.5, 0.5].
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    r = inputs.uniform01(seed, 4 * nx * ny).reshape(4, ny, nx)
+    drho, u, v = 2e-3 * (r[0] - 0.5), 0.1 * (r[1] - 0.5), 0.1 * (r[2] - 0.5)
+    th = r[3] - 0.5
+    eu = ex[:, None, None] * u + ey[:, None, None] * v
+    f = w9[:, None, None] * (drho + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u * u + v * v))
+    f += 1e-4 * (inputs.uniform01(seed + 1, 9 * nx * ny).reshape(9, ny, nx) - 0.5)
+    g = np.empty((5, ny, nx))
+    g[0] = 0.3 * th
+    g[1:] = 0.175 * th
+    g += 1e-2 * (inputs.uniform01(seed + 2, 5 * nx * ny).reshape(5, ny, nx) - 0.5)
+    return np.concatenate([f, g]).astype(np.float32)
+
+
+@pytest.mark.parametrize("nx,ny", [(4096, 4096), (32768, 5), (6, 32768)])
+def test_one_step_from_random_state_full_size(D, nx, ny):
+    # The largest single cavity (4096^2, the benchmark's launch configuration) and the
+    # maximum extents: every population after one step, from the same float32 state.
+    cav = inputs.Cavity(nx, ny, 1e7 if nx == ny else 1e5, 0.001, noise_amp=0.0)
+    state = _random_state(nx, ny, seed=31)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=16)
+    sim.set_state(state)
+    sim.step(1)
+    sim.check()
+    out = sim.get_state()
+    nu_mean, nu_local, _ = sim.nusselt()
+    sim.close()
+
+    m = O.derive(nx, ny, cav.Ra, cav.Pr, cav.alpha)
+    s64 = state.astype(np.float64)
+    del state
+    r = O.step(m, np.ascontiguousarray(s64[:9]), np.ascontiguousarray(s64[9:]))
+    del s64
+    for k in range(9):
+        ref = r["f"][k]
+        assert np.abs(out[k] - ref).max() <= FIELD_TOL * np.abs(ref).max(), f"f{k + 1}"
+    for k in range(5):
+        ref = r["g"][k]
+        assert np.abs(out[9 + k] - ref).max() <= FIELD_TOL * np.abs(ref).max(), f"g{k + 1}"
+    assert abs(nu_mean - r["nu"]) <= NU_TOL * abs(r["nu"])
+    assert np.abs(nu_local - r["nu_local"]).max() <= NU_TOL * np.abs(r["nu_local"]).max()
+
+
+def test_deterministic_and_graph_equals_single_launches(D):
+    cav = inputs.Cavity(200, 150, 1e5, 0.005, noise_amp=1e-3, seed=23)
+    a = D.Cavity2D.from_inputs(cav)
+    a.step(200)  # graphs of 64 steps plus single launches
+    b = D.Cavity2D.from_inputs(cav)
+    for _ in range(200):
+        b.step(1)
+    c = D.Cavity2D.from_inputs(cav)
+    c.step(200)
+    sa, sb, sc = a.get_state(), b.get_state(), c.get_state()
+    na, nb, nc = a.nusselt(200)[2], b.nusselt(200)[2], c.nusselt(200)[2]
+    for s in (a, b, c):
+        s.close()
+    assert np.array_equal(sa, sb) and np.array_equal(sa, sc)
+    assert np.array_equal(na, nb) and np.array_equal(na, nc)
+
+
+def test_state_roundtrip_resumes_bitwise(D):
+    cav = inputs.Cavity(64, 48, 1e5, 0.01, noise_amp=1e-3, seed=24)
+    a = D.Cavity2D.from_inputs(cav)
+    a.step(150)
+    mid = a.get_state()
+    a.step(150)
+    end_a = a.get_state()
+    b = D.Cavity2D.from_inputs(cav)
+    b.set_state(mid)
+    b.step(150)
+    end_b = b.get_state()
+    a.close()
+    b.close()
+    assert np.array_equal(end_a, end_b)
+
+
+def test_fields_host_equals_device(D):
+    cav = inputs.Cavity(70, 50, 1e5, 0.01, noise_amp=1e-3, seed=25)
+    sim = D.Cavity2D.from_inputs(cav)
+    sim.step(100)
+    dev = [t.cpu().numpy() for t in sim.fields()]
+    host = sim.fields_host()
+    sim.close()
+    for a, b in zip(dev, host):
+        assert np.array_equal(a, b)
+
+
+def test_nusselt_ring_wraps(D):
+    cav = inputs.Cavity(32, 32, 1e4, 0.01, noise_amp=1e-3, seed=26)
+    a = D.Cavity2D.from_inputs(cav, nu_capacity=50)
+    b = D.Cavity2D.from_inputs(cav)
+    a.step(123)
+    b.step(123)
+    sa = a.nusselt(1000)[2]
+    sb = b.nusselt(1000)[2]
+    s7 = a.nusselt(7)[2]
+    a.close()
+    b.close()
+    assert len(sa) == 50 and len(sb) == 123
+    assert np.array_equal(sa, sb[-50:])
+    assert np.array_equal(s7, sb[-7:])
+
+
+def test_non_finite_state_is_reported(D):
+    cav = inputs.Cavity(40, 30, 1e4, 0.01, noise_amp=0.0)
+    th = cav.theta0()
+    th[10, 20] = np.nan
+    sim = D.Cavity2D(D.make_params(40, 30, 1e4, 0.01), theta0=th)
+    sim.step(3)
+    with pytest.raises(D.DmrtError) as ei:
+        sim.check()
+    assert ei.value.code == D.DMRT_E_DIVERGED
+    sim.close()
