@@ -45,7 +45,7 @@ extern "C" {
 #define DMRT_E_UNSTABLE (-2) /* parameters outside the model's valid range */
 #define DMRT_E_CUDA (-3)     /* a CUDA runtime call failed */
 #define DMRT_E_DIVERGED (-4) /* a non-finite density or temperature was seen */
-#define DMRT_E_TIMEOUT (-5)  /* a bounded device-side wait ran out */
+#define DMRT_E_TIMEOUT (-5)  /* a bounded device-side wait ran out (2 s per wait) */
 #define DMRT_E_SPACE (-6)    /* workspace or host buffer too small */
 #define DMRT_E_STATE (-7)    /* checkpoint does not match this context */
 
@@ -53,6 +53,17 @@ extern "C" {
 #define DMRT_FP32 0
 #define DMRT_FP16 1
 #define DMRT_BF16 2
+
+/* Step kernel variants. Both compute the same step; they differ only in how
+ * the populations reach the registers. DIRECT: 128-bit loads straight from
+ * global memory, x-shifts by warp shuffles. TMA: a persistent kernel that
+ * stages (strip x row-block) tiles in shared memory with 3-D tensor copies
+ * through a multi-stage mbarrier pipeline. AUTO picks TMA for grids wider
+ * than 496 nodes, DIRECT otherwise. (R, S) tiles compiled in: (1,4) (1,6)
+ * (2,2) (2,3) (2,4) (4,2) (4,3). */
+#define DMRT_KERNEL_AUTO 0
+#define DMRT_KERNEL_DIRECT 1
+#define DMRT_KERNEL_TMA 2
 
 /* Wall kinds for the left and right (vertical) walls. Top and bottom are
  * always adiabatic (Eqs. 7-8, 44). */
@@ -73,8 +84,10 @@ typedef struct {
     int32_t left_wall;  /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t storage;    /* DMRT_FP32 (DMRT_FP16 / DMRT_BF16 reserved) */
-    int32_t reserved;
+    int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
+    int32_t tma_rows;   /* TMA kernel: rows per work item (0 = default 2) */
+    int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default 3) */
 } dmrt_params;
 
 /* Constants derived from dmrt_params (Eqs. 9, 31-32, 38-40, 43, 45). */

@@ -1,6 +1,8 @@
 // Host side of libdmrt.so: parameter derivation, workspace layout, the
 // init / fields kernels and the C entry points declared in include/dmrt.h.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -10,10 +12,12 @@
 #include <new>
 
 #include "dmrt.h"
-#include "step_kernel.cuh"
+#include "step_direct.cuh"
+#include "step_tma.cuh"
 
+using dmrt::plane_f;
+using dmrt::plane_g;
 using dmrt::kPlanes;
-using dmrt::kThreads;
 
 namespace {
 
@@ -65,8 +69,17 @@ struct dmrt_ctx {
     int cur;             // 0: state in buffer A, 1: in buffer B
     long long t;         // steps enqueued
     dmrt::StepConsts sc;
+    int kernel;          // DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA (resolved)
+    // direct kernel
     int wx_log2;
     dim3 grid;
+    // TMA kernel
+    int R, S;
+    dmrt::TmaGeo geo;
+    int tma_grid;
+    size_t tma_smem;
+    const void* tma_func;
+    CUtensorMap map6[2], map4[2];  // per source buffer: 6-plane and 4-plane boxes
     cudaGraphExec_t graph[2];
     int graph_len;
     char err[256];
@@ -135,10 +148,10 @@ __global__ void init_kernel(float* __restrict__ S, const double* __restrict__ th
         double th = 0.0;
         const bool in = i < nx;
         if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
-        for (int k = 0; k < 9; ++k) S[k * plane + q] = 0.f;
-        S[9 * plane + q] = in ? (float)((1.0 - a) * th / 5.0) : 0.f;
+        for (int k = 0; k < 9; ++k) S[plane_f(k) * plane + q] = 0.f;
+        S[plane_g(0) * plane + q] = in ? (float)((1.0 - a) * th / 5.0) : 0.f;
         const float side = in ? (float)((4.0 + a) * th / 20.0) : 0.f;
-        for (int k = 10; k < 14; ++k) S[k * plane + q] = side;
+        for (int k = 1; k < 5; ++k) S[plane_g(k) * plane + q] = side;
     }
 }
 
@@ -154,8 +167,8 @@ __global__ void fields_kernel(const float* __restrict__ S, float* __restrict__ u
         const int j = (int)(q / nx), i = (int)(q % nx);
         const long long s = (long long)j * pitch + i;
         float f[9], g[5];
-        for (int k = 0; k < 9; ++k) f[k] = S[k * plane + s];
-        for (int k = 0; k < 5; ++k) g[k] = S[(9 + k) * plane + s];
+        for (int k = 0; k < 9; ++k) f[k] = S[plane_f(k) * plane + s];
+        for (int k = 0; k < 5; ++k) g[k] = S[plane_g(k) * plane + s];
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
         const float t = g[0] + g[1] + g[2] + g[3] + g[4];
@@ -168,6 +181,105 @@ __global__ void fields_kernel(const float* __restrict__ S, float* __restrict__ u
 __global__ void fill_kernel(float* p, const double* src, double value, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = (float)(src ? src[i] : value);
+}
+
+// Host state arrays are ordered f_1..f_9, g_1..g_5; the device planes are grouped.
+int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
+
+// TMA tile shapes compiled in: R rows per item, S pipeline stages.
+struct TmaVariant {
+    int R, S;
+    const void* func;
+};
+const TmaVariant kTmaVariants[] = {
+    {1, 4, (const void*)dmrt::step_tma_kernel<1, 4>}, {1, 6, (const void*)dmrt::step_tma_kernel<1, 6>},
+    {2, 2, (const void*)dmrt::step_tma_kernel<2, 2>}, {2, 3, (const void*)dmrt::step_tma_kernel<2, 3>},
+    {2, 4, (const void*)dmrt::step_tma_kernel<2, 4>}, {4, 2, (const void*)dmrt::step_tma_kernel<4, 2>},
+    {4, 3, (const void*)dmrt::step_tma_kernel<4, 3>},
+};
+constexpr int kDefaultR = 2, kDefaultS = 3;
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+    }
+    return fn;
+}
+
+// 3-D view {pitch, ny, 14} of one population buffer with boxes {256, R, planes}.
+int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes) {
+    auto enc = tensor_map_encoder();
+    if (!enc) {
+        set_err(c, "cuTensorMapEncodeTiled is not available from the driver");
+        return DMRT_E_CUDA;
+    }
+    cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->p.ny, (cuuint64_t)kPlanes};
+    cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * sizeof(float),
+                             (cuuint64_t)c->L.plane * sizeof(float)};
+    cuuint32_t box[3] = {(cuuint32_t)dmrt::kTmaBox, (cuuint32_t)c->R, (cuuint32_t)planes};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_err(c, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return DMRT_E_CUDA;
+    }
+    return DMRT_OK;
+}
+
+// Resolve the kernel variant and prepare its launch configuration.
+int setup_kernel(dmrt_ctx* c) {
+    const dmrt_params& p = c->p;
+    int want = p.kernel;
+    int R = p.tma_rows > 0 ? p.tma_rows : kDefaultR;
+    int S = p.tma_stages > 0 ? p.tma_stages : kDefaultS;
+    if (want == DMRT_KERNEL_AUTO)
+        want = (p.nx > 2 * dmrt::kTmaStrip && p.ny >= 4 * R) ? DMRT_KERNEL_TMA : DMRT_KERNEL_DIRECT;
+    c->kernel = want;
+    c->R = R;
+    c->S = S;
+    c->tma_func = nullptr;
+    if (want != DMRT_KERNEL_TMA) return DMRT_OK;
+    for (const TmaVariant& v : kTmaVariants)
+        if (v.R == R && v.S == S) c->tma_func = v.func;
+    if (!c->tma_func) {
+        set_err(c, "no TMA tile with %d rows and %d stages is compiled in", R, S);
+        return DMRT_E_ARG;
+    }
+    if (p.ny < R) {
+        set_err(c, "TMA kernel needs ny >= %d", R);
+        return DMRT_E_ARG;
+    }
+    c->geo.n_strips = (p.nx + dmrt::kTmaStrip - 1) / dmrt::kTmaStrip;
+    c->geo.n_rowblocks = (p.ny + R - 1) / R;
+    c->tma_smem = dmrt::tma_smem_bytes(R, S);
+    CK(cudaFuncSetAttribute(c->tma_func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->tma_smem),
+       "set TMA kernel shared memory");
+    int dev = 0, sms = 0, per_sm = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->tma_func, 64 * R, c->tma_smem),
+       "occupancy");
+    if (per_sm < 1) {
+        set_err(c, "TMA tile %dx%d does not fit on an SM", R, S);
+        return DMRT_E_ARG;
+    }
+    const long long items = (long long)c->geo.n_strips * c->geo.n_rowblocks;
+    c->tma_grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+    for (int b = 0; b < 2; ++b) {
+        int rc = encode_map(c, &c->map6[b], buf(c, b), 6);
+        if (rc) return rc;
+        rc = encode_map(c, &c->map4[b], buf(c, b), 4);
+        if (rc) return rc;
+    }
+    return DMRT_OK;
 }
 
 int validate(const dmrt_params* p, dmrt_ctx* c) {
@@ -193,6 +305,10 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
     }
     if (p->storage != DMRT_FP32) {
         set_err(c, "storage %d not available in this build (only DMRT_FP32)", p->storage);
+        return DMRT_E_ARG;
+    }
+    if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_TMA) {
+        set_err(c, "kernel must be DMRT_KERNEL_AUTO, _DIRECT or _TMA");
         return DMRT_E_ARG;
     }
     if (p->nu_capacity < 1) {
@@ -227,7 +343,10 @@ void dmrt_default_params(dmrt_params* p) {
     p->left_wall = DMRT_WALL_FIXED;
     p->right_wall = DMRT_WALL_FIXED;
     p->storage = DMRT_FP32;
+    p->kernel = DMRT_KERNEL_AUTO;
     p->nu_capacity = 1 << 20;
+    p->tma_rows = 0;
+    p->tma_stages = 0;
 }
 
 int dmrt_derive(const dmrt_params* p, dmrt_consts* out) {
@@ -330,7 +449,7 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     while (wx < nxq && wx < 32) wx <<= 1;
     c->wx_log2 = 0;
     while ((1 << c->wx_log2) < wx) ++c->wx_log2;
-    const int rows_per_block = (kThreads / 32) * (32 / wx);
+    const int rows_per_block = (dmrt::kDirectThreads / 32) * (32 / wx);
     c->grid = dim3((nxq + wx - 1) / wx, (p->ny + rows_per_block - 1) / rows_per_block, 1);
 
     auto fail = [&](int code) {
@@ -338,6 +457,8 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
         delete c;
         return code;
     };
+    int rc2 = setup_kernel(c);
+    if (rc2) return fail(rc2);
     // Zero the scalars and the ring, set the wall profiles, write the initial state.
     if (cudaMemsetAsync(c->ws + L.off_hot, 0, L.total - L.off_hot, c->stream) != cudaSuccess)
         return fail(cuda_fail(c, cudaGetLastError(), "cudaMemsetAsync"));
@@ -367,9 +488,23 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     return DMRT_OK;
 }
 
+// One step from buffer `from` to the other one.
+static int launch_step(dmrt_ctx* c, int from) {
+    dmrt::StepArgs A = step_args(c, from);
+    if (c->kernel == DMRT_KERNEL_TMA) {
+        void* params[5] = {&c->map6[from], &c->map4[from], &A, &c->sc, &c->geo};
+        cudaError_t e = cudaLaunchKernel(c->tma_func, dim3(c->tma_grid), dim3(64 * c->R), params,
+                                         c->tma_smem, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "TMA step launch");
+    } else {
+        dmrt::step_direct_kernel<<<c->grid, dmrt::kDirectThreads, 0, c->stream>>>(A, c->sc);
+    }
+    return DMRT_OK;
+}
+
 static int launch_one(dmrt_ctx* c) {
-    dmrt::StepArgs A = step_args(c, c->cur);
-    dmrt::step_kernel<<<c->grid, kThreads, 0, c->stream>>>(A, c->sc);
+    int rc = launch_step(c, c->cur);
+    if (rc) return rc;
     c->cur ^= 1;
     c->t += 1;
     return DMRT_OK;
@@ -383,13 +518,23 @@ static int build_graph(dmrt_ctx* c, int from) {
     cudaGraphNode_t prev = nullptr;
     dmrt::StepArgs args[2] = {step_args(c, from), step_args(c, 1 - from)};
     for (int i = 0; i < c->graph_len; ++i) {
+        const int src = (i & 1) ? 1 - from : from;
         cudaKernelNodeParams kp = {};
-        kp.func = (void*)dmrt::step_kernel;
-        kp.gridDim = c->grid;
-        kp.blockDim = dim3(kThreads, 1, 1);
-        kp.sharedMemBytes = 0;
-        void* params[2] = {&args[i & 1], &c->sc};
-        kp.kernelParams = params;
+        void* dparams[2] = {&args[i & 1], &c->sc};
+        void* tparams[5] = {&c->map6[src], &c->map4[src], &args[i & 1], &c->sc, &c->geo};
+        if (c->kernel == DMRT_KERNEL_TMA) {
+            kp.func = const_cast<void*>(c->tma_func);
+            kp.gridDim = dim3(c->tma_grid);
+            kp.blockDim = dim3(64 * c->R);
+            kp.sharedMemBytes = (unsigned)c->tma_smem;
+            kp.kernelParams = tparams;
+        } else {
+            kp.func = (void*)dmrt::step_direct_kernel;
+            kp.gridDim = c->grid;
+            kp.blockDim = dim3(dmrt::kDirectThreads);
+            kp.sharedMemBytes = 0;
+            kp.kernelParams = dparams;
+        }
         cudaGraphNode_t node;
         cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
         if (e != cudaSuccess) {
@@ -416,7 +561,8 @@ int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
             c->t += c->graph_len;  // even length: the state stays in the same buffer
             nsteps -= c->graph_len;
         } else {
-            launch_one(c);
+            int rc = launch_one(c);
+            if (rc) return rc;
             nsteps -= 1;
         }
     }
@@ -429,7 +575,11 @@ int dmrt_check(dmrt_ctx* c) {
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     unsigned err = 0;
     CK(cudaMemcpy(&err, &misc(c)->err, sizeof err, cudaMemcpyDeviceToHost), "read error flag");
-    if (err & 1u) {
+    if (err & dmrt::kErrTimeout) {
+        set_err(c, "a bounded device-side wait expired after %lld steps", c->t);
+        return DMRT_E_TIMEOUT;
+    }
+    if (err & dmrt::kErrNonFinite) {
         set_err(c, "non-finite density or temperature after %lld steps", c->t);
         return DMRT_E_DIVERGED;
     }
@@ -492,7 +642,11 @@ int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
         written = want;
     }
     if (count) *count = written;
-    if (m.err & 1u) {
+    if (m.err & dmrt::kErrTimeout) {
+        set_err(c, "a bounded device-side wait expired after %lld steps", c->t);
+        return DMRT_E_TIMEOUT;
+    }
+    if (m.err & dmrt::kErrNonFinite) {
         set_err(c, "non-finite density or temperature after %lld steps", c->t);
         return DMRT_E_DIVERGED;
     }
@@ -527,7 +681,7 @@ int dmrt_get_state(dmrt_ctx* c, float* host) {
     const float* S = buf(c, c->cur);
     for (int k = 0; k < kPlanes; ++k)
         CK(cudaMemcpy2DAsync(host + (size_t)k * p.nx * p.ny, (size_t)p.nx * sizeof(float),
-                             S + (size_t)k * c->L.plane, (size_t)c->L.pitch * sizeof(float),
+                             S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
                              (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyDeviceToHost, c->stream),
            "copy state to host");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
@@ -539,7 +693,7 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
     const dmrt_params& p = c->p;
     float* S = buf(c, c->cur);
     for (int k = 0; k < kPlanes; ++k)
-        CK(cudaMemcpy2DAsync(S + (size_t)k * c->L.plane, (size_t)c->L.pitch * sizeof(float),
+        CK(cudaMemcpy2DAsync(S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
                              host + (size_t)k * p.nx * p.ny, (size_t)p.nx * sizeof(float),
                              (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyHostToDevice, c->stream),
            "copy state to device");

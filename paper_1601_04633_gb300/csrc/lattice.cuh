@@ -1,0 +1,241 @@
+// Shared device pieces of the double-MRT step (Li, Yang & Zhang, arXiv 1601.04633,
+// Sec. 3): the population layout, per-launch arguments, the per-node collision
+// with the buoyancy force, and the fused hot-wall Nusselt reduction.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dmrt {
+
+constexpr int kPlanes = 14;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Populations are stored as 14 planes [ny][pitch] (structure of arrays; pitch a
+// multiple of 128 elements, padding columns kept at zero). The planes are
+// grouped by the y component of their lattice velocity, so that the pull of one
+// output row reads three contiguous plane groups from three rows:
+//   Z (e_y =  0, source row j):     f1 f2 f4 g1 g2 g4   -> planes 0..5
+//   P (e_y = +1, source row j - 1): f3 f6 f7 g3         -> planes 6..9
+//   N (e_y = -1, source row j + 1): f5 f8 f9 g5         -> planes 10..13
+// (paper numbering, Eqs. 23 and 35). plane_f(k) / plane_g(k) give the plane of
+// the 0-based direction k.
+__host__ __device__ constexpr int plane_f(int k) {
+    return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 6 : k == 3 ? 2 : k == 4 ? 10 : k == 5 ? 7 : k == 6 ? 8 : k == 7 ? 11 : 12;
+}
+__host__ __device__ constexpr int plane_g(int k) {
+    return k == 0 ? 3 : k == 1 ? 4 : k == 2 ? 9 : k == 3 ? 5 : 13;
+}
+constexpr int kGroupZ = 0, kGroupP = 6, kGroupN = 10;
+
+// Relaxation constants pre-divided by the squared norms of the rows of the
+// transforms (D2Q9: 9,6,6,36,4,4,12,12,36; D2Q5: 5,2,2,20,4), so that
+// f* = f - sum_k M[k][i] d_k with d_k = rate_k (m_k - m_k_eq) / norm_k.
+struct StepConsts {
+    float se36, snu4, sq12, seps36;  // D2Q9: s_e/36, s_nu/4, s_q/12, s_eps/36
+    float sk2, se20, snu4t;          // D2Q5: sigma_k/2, sigma_e/20, sigma_nu/4
+    float a;                         // D2Q5 equilibrium parameter (Eq. 43)
+    float gbeta, theta_ref;          // G_y = gbeta (theta - theta_ref) (Eq. 27)
+    float abb;                       // 2 sqrt(3) alpha (Eq. 45)
+    int left_fixed, right_fixed;     // 1 = anti-bounce-back wall, 0 = adiabatic
+    double nu_scale;                 // H / (3 (theta_hot - theta_cold))
+};
+
+struct StepArgs {
+    const float* __restrict__ src;  // post-collision state at time t
+    float* __restrict__ dst;        // post-collision state at time t + 1
+    const float* __restrict__ hot;  // [ny] left-wall temperature
+    const float* __restrict__ cold; // [ny] right-wall temperature
+    double* nu_rows;                // [ny] local Nu of the latest step
+    double* nu_ring;                // [cap] mean Nu per step
+    double* nu_last;                // mean Nu of the latest step
+    unsigned* counter;              // rows reported in the current step
+    unsigned* err;                  // bit 0: non-finite value; bit 1: wait timed out
+    long long* d_step;              // steps recorded so far
+    long long cap;
+    long long plane;  // elements per plane = ny * pitch
+    int nx, ny, pitch;
+    int wx_log2;      // direct kernel: lanes per row segment = 1 << wx_log2
+};
+
+constexpr unsigned kErrNonFinite = 1u;
+constexpr unsigned kErrTimeout = 2u;
+
+__device__ __forceinline__ float4 ldg4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+template <int E>
+__device__ __forceinline__ float& comp(float4& v) {
+    if constexpr (E == 0) return v.x;
+    else if constexpr (E == 1) return v.y;
+    else if constexpr (E == 2) return v.z;
+    else return v.w;
+}
+
+__device__ __forceinline__ void set_comp(float4& v, int e, float val) {
+    v.x = (e == 0) ? val : v.x;
+    v.y = (e == 1) ? val : v.y;
+    v.z = (e == 2) ? val : v.z;
+    v.w = (e == 3) ? val : v.w;
+}
+
+// Collision + force + thermal collision of one node, in place.
+// f[0..8]: D2Q9 populations (shifted: they sum to delta-rho, Eq. 33),
+// g[0..4]: D2Q5 populations. Directions: f1..f4 = (1,0),(0,1),(-1,0),(0,-1),
+// f5..f8 = (1,1),(-1,1),(-1,-1),(1,-1); g1..g4 as f1..f4 (0-based indices).
+__device__ __forceinline__ void collide_node(float (&f)[9], float (&g)[5], const StepConsts& K,
+                                             float& rho_out, float& theta_out) {
+    // Moments m = M f (Eq. 30), with rho0 = 1 so u = jx, v = jy (Eq. 33).
+    const float a13 = f[1] - f[3], a24 = f[2] - f[4];
+    const float s13 = f[1] + f[3], s24 = f[2] + f[4];
+    const float a56 = f[5] - f[6], a78 = f[7] - f[8];
+    const float s56 = f[5] + f[6], s78 = f[7] + f[8];
+    const float s1234 = s13 + s24, s5678 = s56 + s78;
+    const float rho = f[0] + s1234 + s5678;
+    const float u = a13 + a56 - a78;
+    const float v = a24 + s56 - s78;
+    const float e = -4.f * f[0] - s1234 + 2.f * s5678;
+    const float pxx = s13 - s24;
+    const float pxy = (f[5] + f[7]) - (f[6] + f[8]);
+    const float qx = -2.f * a13 + a56 - a78;
+    const float qy = -2.f * a24 + s56 - s78;
+    const float eps = 4.f * f[0] - 2.f * s1234 + s5678;
+    const float uu = u * u + v * v;
+    // Non-equilibrium parts (Eq. 34, m4_eq = -2 drho + 3 |u|^2), scaled.
+    const float d3 = K.se36 * (e + 2.f * rho - 3.f * uu);
+    const float d4 = K.snu4 * (pxx - (u * u - v * v));
+    const float d5 = K.snu4 * (pxy - u * v);
+    const float d6 = K.sq12 * (qx + u);
+    const float d7 = K.sq12 * (qy + v);
+    const float d8 = K.seps36 * (eps - rho + 3.f * uu);
+
+    const float theta = g[0] + g[1] + g[2] + g[3] + g[4];  // Eq. 41
+
+    // Buoyancy force (Eqs. 26-27): F_i = 3 (e_i - u).G f_i_eq(rho0 = 1, u),
+    // G = (0, gbeta (theta - theta_ref)).
+    const float c3 = 3.f * K.gbeta * (theta - K.theta_ref);
+    const float base = 1.f - 1.5f * uu;
+    const float cv_m = c3 * (-v), cv_p = c3 * (1.f - v), cv_n = c3 * (-1.f - v);
+    const float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+    const float u3 = 3.f * u, v3 = 3.f * v, uu45 = 4.5f * u * u, vv45 = 4.5f * v * v;
+    const float upv = u + v, umv = u - v;
+    const float qp = base + 4.5f * upv * upv, qm = base + 4.5f * umv * umv;
+    const float F0 = cv_m * (4.f / 9.f) * base;
+    const float F1 = cv_m * w1 * (base + u3 + uu45);
+    const float F2 = cv_p * w1 * (base + v3 + vv45);
+    const float F3 = cv_m * w1 * (base - u3 + uu45);
+    const float F4 = cv_n * w1 * (base - v3 + vv45);
+    const float F5 = cv_p * w5 * (qp + 3.f * upv);
+    const float F6 = cv_p * w5 * (qm - 3.f * umv);
+    const float F7 = cv_n * w5 * (qp - 3.f * upv);
+    const float F8 = cv_n * w5 * (qm + 3.f * umv);
+
+    // f* = f - M^-1 S (m - m_eq) + F, with M^-1 = M^T diag(1/norm) (Eq. 28).
+    f[0] = f[0] + 4.f * d3 - 4.f * d8 + F0;
+    f[1] = f[1] + d3 - d4 + 2.f * d6 + 2.f * d8 + F1;
+    f[2] = f[2] + d3 + d4 + 2.f * d7 + 2.f * d8 + F2;
+    f[3] = f[3] + d3 - d4 - 2.f * d6 + 2.f * d8 + F3;
+    f[4] = f[4] + d3 + d4 - 2.f * d7 + 2.f * d8 + F4;
+    f[5] = f[5] - 2.f * d3 - d5 - d6 - d7 - d8 + F5;
+    f[6] = f[6] - 2.f * d3 + d5 + d6 - d7 - d8 + F6;
+    f[7] = f[7] - 2.f * d3 - d5 + d6 + d7 - d8 + F7;
+    f[8] = f[8] - 2.f * d3 + d5 - d6 + d7 - d8 + F8;
+
+    // D2Q5: n = N g (Eq. 37, fifth row (0,1,-1,1,-1)), n_eq = (theta, u theta,
+    // v theta, a theta, 0) (Eq. 42), g* = g - N^-1 Q (n - n_eq) (Eq. 36).
+    const float n1 = g[1] - g[3];
+    const float n2 = g[2] - g[4];
+    const float n3 = -4.f * g[0] + (g[1] + g[2] + g[3] + g[4]);
+    const float n4 = (g[1] + g[3]) - (g[2] + g[4]);
+    const float e1 = K.sk2 * (n1 - u * theta);
+    const float e2 = K.sk2 * (n2 - v * theta);
+    const float e3 = K.se20 * (n3 - K.a * theta);
+    const float e4 = K.snu4t * n4;
+    g[0] = g[0] + 4.f * e3;
+    g[1] = g[1] - e1 - e3 - e4;
+    g[2] = g[2] - e2 - e3 + e4;
+    g[3] = g[3] + e1 - e3 - e4;
+    g[4] = g[4] + e2 - e3 + e4;
+
+    rho_out = rho;
+    theta_out = theta;
+}
+
+// Collide node E of four (F, Gq hold the pulled populations of 4 nodes) in
+// place; invalid nodes (padding) are zeroed so the padding stays zero.
+template <int E>
+__device__ __forceinline__ void node_update(float4 (&F)[9], float4 (&Gq)[5], const StepConsts& K,
+                                            float (&theta4)[4], bool valid, bool& bad) {
+    float f[9], g[5];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f[k] = comp<E>(F[k]);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) g[k] = comp<E>(Gq[k]);
+    float rho, theta;
+    collide_node(f, g, K, rho, theta);
+    if (valid) {
+        bad |= !(fabsf(rho) < 1e30f) || !(fabsf(theta) < 1e30f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) f[k] = 0.f;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) g[k] = 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) comp<E>(F[k]) = f[k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) comp<E>(Gq[k]) = g[k];
+    theta4[E] = theta;
+}
+
+__device__ __forceinline__ void collide_quad(float4 (&F)[9], float4 (&Gq)[5], const StepConsts& K,
+                                             float (&theta4)[4], int nvalid, bool& bad) {
+    node_update<0>(F, Gq, K, theta4, nvalid > 0, bad);
+    node_update<1>(F, Gq, K, theta4, nvalid > 1, bad);
+    node_update<2>(F, Gq, K, theta4, nvalid > 2, bad);
+    node_update<3>(F, Gq, K, theta4, nvalid > 3, bad);
+}
+
+// Store a collided quad (4 nodes from x0 of row j) to the destination planes.
+__device__ __forceinline__ void store_quad(const StepArgs& A, int j, int x0, const float4 (&F)[9],
+                                           const float4 (&Gq)[5]) {
+    float* D = A.dst + (size_t)j * A.pitch + x0;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) *reinterpret_cast<float4*>(D + plane_f(k) * A.plane) = F[k];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) *reinterpret_cast<float4*>(D + plane_g(k) * A.plane) = Gq[k];
+}
+
+// Hot-wall Nusselt number (Eqs. 18-19). Called by all 32 lanes of a warp; the
+// lane with has_nu holds row j's local value. The warp that completes the
+// count of ny rows sums them in a fixed order (lane-strided, then a butterfly),
+// so the mean does not depend on which warps arrive first, and appends it to
+// the ring.
+__device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j, double nuj) {
+    const int lane = threadIdx.x & 31;
+    if (has_nu) {
+        A.nu_rows[j] = nuj;
+        __threadfence();
+    }
+    const unsigned n_here = __popc(__ballot_sync(kFull, has_nu));
+    unsigned before = 0;
+    if (lane == 0 && n_here) before = atomicAdd(A.counter, n_here);
+    before = __shfl_sync(kFull, before, 0);
+    if (n_here && before + n_here == (unsigned)A.ny) {
+        __threadfence();
+        double s = 0.0;
+        for (int r = lane; r < A.ny; r += 32) s += __ldcg(A.nu_rows + r);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0) {
+            const double mean = s / (double)A.ny;
+            const long long t = *A.d_step;
+            A.nu_ring[t % A.cap] = mean;
+            *A.nu_last = mean;
+            *A.d_step = t + 1;
+            *A.counter = 0u;
+        }
+    }
+}
+
+}  // namespace dmrt

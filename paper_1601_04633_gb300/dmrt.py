@@ -29,6 +29,7 @@ DMRT_E_SPACE = -6
 DMRT_E_STATE = -7
 DMRT_FP32, DMRT_FP16, DMRT_BF16 = 0, 1, 2
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
+DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA = 0, 1, 2
 
 _ERRNAMES = {-1: "DMRT_E_ARG", -2: "DMRT_E_UNSTABLE", -3: "DMRT_E_CUDA", -4: "DMRT_E_DIVERGED",
              -5: "DMRT_E_TIMEOUT", -6: "DMRT_E_SPACE", -7: "DMRT_E_STATE"}
@@ -48,8 +49,9 @@ class Params(ctypes.Structure):
         ("theta_hot", ctypes.c_double), ("theta_cold", ctypes.c_double),
         ("theta_ref", ctypes.c_double), ("theta_init", ctypes.c_double),
         ("left_wall", ctypes.c_int32), ("right_wall", ctypes.c_int32),
-        ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("storage", ctypes.c_int32), ("kernel", ctypes.c_int32),
         ("nu_capacity", ctypes.c_int64),
+        ("tma_rows", ctypes.c_int32), ("tma_stages", ctypes.c_int32),
     ]
 
 
@@ -212,7 +214,8 @@ def dmrt_destroy(h):
 
 def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.5,
                 theta_ref=None, theta_init=0.0, left_wall=DMRT_WALL_FIXED,
-                right_wall=DMRT_WALL_FIXED, storage=DMRT_FP32, nu_capacity=1 << 20) -> Params:
+                right_wall=DMRT_WALL_FIXED, storage=DMRT_FP32, nu_capacity=1 << 20,
+                kernel=DMRT_KERNEL_AUTO, tma_rows=0, tma_stages=0) -> Params:
     p = dmrt_default_params()
     p.nx, p.ny, p.Ra, p.Pr, p.alpha, p.Ma = int(nx), int(ny), float(Ra), float(Pr), float(alpha), float(Ma)
     p.theta_hot, p.theta_cold = float(theta_hot), float(theta_cold)
@@ -220,6 +223,7 @@ def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.
     p.theta_init = float(theta_init)
     p.left_wall, p.right_wall, p.storage = int(left_wall), int(right_wall), int(storage)
     p.nu_capacity = int(nu_capacity)
+    p.kernel, p.tma_rows, p.tma_stages = int(kernel), int(tma_rows), int(tma_stages)
     return p
 
 
@@ -251,7 +255,8 @@ class Cavity2D:
                         theta_cold=cav.theta_cold, theta_init=cav.theta_init,
                         **{k: v for k, v in kw.items() if k in ("storage", "nu_capacity",
                                                                    "left_wall", "right_wall",
-                                                                   "theta_ref")})
+                                                                   "theta_ref", "kernel",
+                                                                   "tma_rows", "tma_stages")})
         rest = {k: v for k, v in kw.items() if k in ("device", "stream")}
         return cls(p, theta0=cav.theta0(), theta_hot_profile=cav.theta_hot_profile, **rest)
 

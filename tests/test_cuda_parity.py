@@ -67,10 +67,15 @@ def assert_parity(gpu, ref, field_tol=FIELD_TOL, nu_tol=NU_TOL):
     assert e <= nu_tol, f"local Nu: {e:.3e}"
 
 
-def test_parity_cavity_64_1000_steps(D):
+KERNELS = [1, 2]  # DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA
+KERNEL_IDS = ["direct", "tma"]
+
+
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
+def test_parity_cavity_64_1000_steps(D, kernel):
     # 64 x 64, Ra 1e4, Pr 0.01, alpha 0.1, seeded 1e-6 noise (the paper's Case 1).
     cav = inputs.cavity_64()
-    assert_parity(gpu_run(D, cav, 1000), oracle_run(cav, 1000))
+    assert_parity(gpu_run(D, cav, 1000, kernel=kernel), oracle_run(cav, 1000))
 
 
 def test_parity_oscillatory_256_1000_steps(D):
@@ -78,17 +83,25 @@ def test_parity_oscillatory_256_1000_steps(D):
     assert_parity(gpu_run(D, cav, 1000), oracle_run(cav, 1000))
 
 
-@pytest.mark.parametrize("nx,ny", [(300, 70), (67, 45), (130, 9), (2, 2), (5, 3), (3, 17), (129, 130)])
-def test_parity_ragged_shapes(D, nx, ny):
-    # Several tiles in x and y with ragged tails, and degenerate tiny grids.
-    cav = inputs.Cavity(nx, ny, 1e5, 0.01, noise_amp=1e-2, seed=nx * 1000 + ny)
-    assert_parity(gpu_run(D, cav, 300), oracle_run(cav, 300))
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
+@pytest.mark.parametrize("nx,ny", [(300, 70), (67, 45), (130, 9), (2, 2), (5, 3), (3, 17), (129, 130),
+                                   (600, 33), (497, 12)])
+def test_parity_ragged_shapes(D, nx, ny, kernel):
+    # Several tiles in x and y with ragged tails, and degenerate tiny grids. Ra is
+    # chosen for Ma = 0.1 (Ma = sqrt(3) alpha sqrt(Ra Pr) / H, from Eq. 9): the
+    # method is a low-Mach scheme, and a fixed Ra in a few-row box would drive
+    # Ma far above 0.3, where no lattice Boltzmann result is meaningful.
+    Pr, alpha, Ma = 0.01, 0.1, 0.1
+    Ra = (Ma * ny / (np.sqrt(3) * alpha)) ** 2 / Pr
+    cav = inputs.Cavity(nx, ny, Ra, Pr, alpha, noise_amp=1e-2, seed=nx * 1000 + ny)
+    assert_parity(gpu_run(D, cav, 300, kernel=kernel), oracle_run(cav, 300))
 
 
-def test_parity_wall_profile_and_adiabatic_right_wall(D):
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
+def test_parity_wall_profile_and_adiabatic_right_wall(D, kernel):
     cav = inputs.Cavity(96, 80, 1e5, 0.005, noise_amp=1e-3, seed=21)
     cav.theta_hot_profile = 0.5 + 0.05 * np.sin(np.linspace(0, 3, 80))
-    g = gpu_run(D, cav, 500, right_wall=D.DMRT_WALL_ADIABATIC)
+    g = gpu_run(D, cav, 500, right_wall=D.DMRT_WALL_ADIABATIC, kernel=kernel)
     r = oracle_run(cav, 500, right_bc=O.WALL_ADIABATIC)
     assert_parity(g, r)
 
@@ -131,13 +144,14 @@ def _random_state(nx, ny, seed):
     return np.concatenate([f, g]).astype(np.float32)
 
 
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
 @pytest.mark.parametrize("nx,ny", [(4096, 4096), (32768, 5), (6, 32768)])
-def test_one_step_from_random_state_full_size(D, nx, ny):
+def test_one_step_from_random_state_full_size(D, nx, ny, kernel):
     # The largest single cavity (4096^2, the benchmark's launch configuration) and the
     # maximum extents: every population after one step, from the same float32 state.
     cav = inputs.Cavity(nx, ny, 1e7 if nx == ny else 1e5, 0.001, noise_amp=0.0)
     state = _random_state(nx, ny, seed=31)
-    sim = D.Cavity2D.from_inputs(cav, nu_capacity=16)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=16, kernel=kernel)
     sim.set_state(state)
     sim.step(1)
     sim.check()
@@ -160,14 +174,15 @@ def test_one_step_from_random_state_full_size(D, nx, ny):
     assert np.abs(nu_local - r["nu_local"]).max() <= NU_TOL * np.abs(r["nu_local"]).max()
 
 
-def test_deterministic_and_graph_equals_single_launches(D):
-    cav = inputs.Cavity(200, 150, 1e5, 0.005, noise_amp=1e-3, seed=23)
-    a = D.Cavity2D.from_inputs(cav)
+@pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
+def test_deterministic_and_graph_equals_single_launches(D, kernel):
+    cav = inputs.Cavity(700, 150, 1e5, 0.005, noise_amp=1e-3, seed=23)
+    a = D.Cavity2D.from_inputs(cav, kernel=kernel)
     a.step(200)  # graphs of 64 steps plus single launches
-    b = D.Cavity2D.from_inputs(cav)
+    b = D.Cavity2D.from_inputs(cav, kernel=kernel)
     for _ in range(200):
         b.step(1)
-    c = D.Cavity2D.from_inputs(cav)
+    c = D.Cavity2D.from_inputs(cav, kernel=kernel)
     c.step(200)
     sa, sb, sc = a.get_state(), b.get_state(), c.get_state()
     na, nb, nc = a.nusselt(200)[2], b.nusselt(200)[2], c.nusselt(200)[2]
@@ -175,6 +190,30 @@ def test_deterministic_and_graph_equals_single_launches(D):
         s.close()
     assert np.array_equal(sa, sb) and np.array_equal(sa, sc)
     assert np.array_equal(na, nb) and np.array_equal(na, nc)
+
+
+TMA_TILES = [(1, 4), (1, 6), (2, 2), (2, 3), (2, 4), (4, 2), (4, 3)]
+
+
+def test_all_kernel_variants_agree_bitwise(D):
+    # Every variant computes the same per-node arithmetic on the same pulled values:
+    # the direct kernel and every compiled TMA tile give identical bits, including
+    # the Nusselt series, over several steps from a random state.
+    nx, ny, steps = 1000, 301, 5
+    cav = inputs.Cavity(nx, ny, 1e6, 0.005, noise_amp=0.0)
+    state = _random_state(nx, ny, seed=41)
+    outs = []
+    for kernel, (R, S) in [(1, (0, 0))] + [(2, t) for t in TMA_TILES]:
+        sim = D.Cavity2D.from_inputs(cav, kernel=kernel, tma_rows=R, tma_stages=S)
+        sim.set_state(state)
+        sim.step(steps)
+        sim.check()
+        outs.append((sim.get_state(), sim.nusselt(steps)[2], (kernel, R, S)))
+        sim.close()
+    ref_state, ref_nu, _ = outs[0]
+    for st, nu, tag in outs[1:]:
+        assert np.array_equal(st, ref_state), tag
+        assert np.array_equal(nu, ref_nu), tag
 
 
 def test_state_roundtrip_resumes_bitwise(D):
