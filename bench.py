@@ -35,7 +35,8 @@ UNIT = "MLUPS"
 BYTES_PER_NODE_FP32 = 112  # 14 populations read + 14 written, 4 bytes each
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_4096x4096.json")
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", "step_kernel.cuh")]
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", f)
+                  for f in ("lattice.cuh", "step_tma.cuh", "step_direct.cuh")]
 
 
 def workload(name):
@@ -234,7 +235,9 @@ def run_dmrt(args):
     nodes = cav.nx * cav.ny
     stream = torch.cuda.current_stream()
 
-    sim = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1))
+    kw = dict(kernel=args.kernel, tma_rows=args.tma_rows, tma_stages=args.tma_stages)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1), **kw)
+    launch = dict(sim.launch)
     sim.step(args.warmup)
     sim.check()
     torch.cuda.synchronize()
@@ -265,7 +268,7 @@ def run_dmrt(args):
     # fields back to pinned host memory (D2H), all inside the timed region.
     theta0 = torch.from_numpy(cav.theta0()).pin_memory()
     outs = [torch.empty((cav.ny, cav.nx), dtype=torch.float32).pin_memory() for _ in range(3)]
-    p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha, nu_capacity=max(args.steps, 1))
+    p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha, nu_capacity=max(args.steps, 1), **kw)
     wsb = D.dmrt_workspace_size(p)
     workspace = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     series = np.zeros(max(args.steps, 1))
@@ -301,12 +304,14 @@ def run_dmrt(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": label, "nx": cav.nx, "ny": cav.ny, "Ra": cav.Ra, "Pr": cav.Pr,
                    "alpha": cav.alpha, "storage": "fp32", "parallelism": f"{ws} independent cavities",
+                   "launch": launch,
                    "l2": "state (two 14-plane fp32 buffers) larger than L2: no flush"
                    if BYTES_PER_NODE_FP32 * nodes > 129e6 else "state fits in L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} HBM copy bandwidth",
-                     "bytes_per_node": BYTES_PER_NODE_FP32, "kernel": "dmrt::step_kernel"},
+                     "bytes_per_node": BYTES_PER_NODE_FP32,
+                     "kernel": "dmrt::step_tma_kernel" if launch["kernel"] == 2 else "dmrt::step_direct_kernel"},
         "e2e": {"value": ws * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes / steps,
                 "d2h_bytes_per_step": (12 * nodes + 8 * args.steps) / steps},
@@ -330,6 +335,9 @@ def main():
     ap.add_argument("--impl", choices=("dmrt", "reference"), default="dmrt")
     ap.add_argument("--workload", default="cavity_4096", choices=("cavity_4096", "cavity_2048", "cavity_256", "cavity_64"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 direct, 2 TMA")
+    ap.add_argument("--tma-rows", type=int, default=0)
+    ap.add_argument("--tma-stages", type=int, default=0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

@@ -59,8 +59,11 @@ extern "C" {
  * global memory, x-shifts by warp shuffles. TMA: a persistent kernel that
  * stages (strip x row-block) tiles in shared memory with 3-D tensor copies
  * through a multi-stage mbarrier pipeline. AUTO picks TMA for grids wider
- * than 496 nodes, DIRECT otherwise. (R, S) tiles compiled in: (1,4) (1,6)
- * (2,2) (2,3) (2,4) (4,2) (4,3). */
+ * than 496 nodes, DIRECT otherwise. TMA tiles compiled in, as (nodes per
+ * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
+ * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)
+ * (4,2); NPT 1 with (1,2) (1,3) (1,4) (1,5) (2,2) (2,3) (3,2) (4,2) (4,3).
+ * Default (1, 4, 2). */
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
@@ -86,8 +89,10 @@ typedef struct {
     int32_t storage;    /* DMRT_FP32 (DMRT_FP16 / DMRT_BF16 reserved) */
     int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
-    int32_t tma_rows;   /* TMA kernel: rows per work item (0 = default 2) */
-    int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default 3) */
+    int32_t tma_rows;   /* TMA kernel: rows per work item (0 = default 4) */
+    int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default 2) */
+    int32_t tma_npt;    /* TMA kernel: nodes per thread, 4, 2 or 1 (0 = default 1) */
+    int32_t reserved;
 } dmrt_params;
 
 /* Constants derived from dmrt_params (Eqs. 9, 31-32, 38-40, 43, 45). */
@@ -170,6 +175,16 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold);
  * count and the Nusselt ring are unchanged). Both synchronise. */
 int dmrt_get_state(dmrt_ctx* c, float* host);
 int dmrt_set_state(dmrt_ctx* c, const float* host);
+
+/* Launch configuration a context resolved to (for reports and tuning). */
+typedef struct {
+    int32_t kernel;       /* DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
+    int32_t tma_npt, tma_rows, tma_stages;
+    int32_t grid, block;  /* blocks per step launch, threads per block */
+    int64_t smem_bytes;   /* dynamic shared memory per block */
+    int32_t graph_steps;  /* steps per captured CUDA graph */
+} dmrt_launch;
+int dmrt_get_launch(const dmrt_ctx* c, dmrt_launch* out);
 
 /* Derived constants of a context. */
 int dmrt_get_consts(const dmrt_ctx* c, dmrt_consts* out);

@@ -14,6 +14,7 @@
 #include "dmrt.h"
 #include "step_direct.cuh"
 #include "step_tma.cuh"
+#include "tma_variants.h"
 
 using dmrt::plane_f;
 using dmrt::plane_g;
@@ -74,7 +75,7 @@ struct dmrt_ctx {
     int wx_log2;
     dim3 grid;
     // TMA kernel
-    int R, S;
+    int npt, R, S, tma_block;
     dmrt::TmaGeo geo;
     int tma_grid;
     size_t tma_smem;
@@ -186,18 +187,19 @@ __global__ void fill_kernel(float* p, const double* src, double value, int n) {
 // Host state arrays are ordered f_1..f_9, g_1..g_5; the device planes are grouped.
 int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
 
-// TMA tile shapes compiled in: R rows per item, S pipeline stages.
-struct TmaVariant {
-    int R, S;
-    const void* func;
-};
-const TmaVariant kTmaVariants[] = {
-    {1, 4, (const void*)dmrt::step_tma_kernel<1, 4>}, {1, 6, (const void*)dmrt::step_tma_kernel<1, 6>},
-    {2, 2, (const void*)dmrt::step_tma_kernel<2, 2>}, {2, 3, (const void*)dmrt::step_tma_kernel<2, 3>},
-    {2, 4, (const void*)dmrt::step_tma_kernel<2, 4>}, {4, 2, (const void*)dmrt::step_tma_kernel<4, 2>},
-    {4, 3, (const void*)dmrt::step_tma_kernel<4, 3>},
-};
-constexpr int kDefaultR = 2, kDefaultS = 3;
+constexpr int kDefaultNpt = 1, kDefaultR = 4, kDefaultS = 2;
+
+const dmrt::TmaVariant* find_tma_variant(int npt, int R, int S) {
+    const dmrt::TmaVariant* (*lists[3])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
+                                                dmrt::tma_variants_npt1};
+    for (auto list : lists) {
+        int n = 0;
+        const dmrt::TmaVariant* v = list(&n);
+        for (int i = 0; i < n; ++i)
+            if (v[i].npt == npt && v[i].R == R && v[i].S == S) return &v[i];
+    }
+    return nullptr;
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -238,21 +240,29 @@ int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes) {
 int setup_kernel(dmrt_ctx* c) {
     const dmrt_params& p = c->p;
     int want = p.kernel;
+    int npt = p.tma_npt > 0 ? p.tma_npt : kDefaultNpt;
     int R = p.tma_rows > 0 ? p.tma_rows : kDefaultR;
     int S = p.tma_stages > 0 ? p.tma_stages : kDefaultS;
+    if (p.tma_rows <= 0 && p.ny < R) {
+        // Fewer rows than the default tile: one row per item.
+        R = 1;
+        if (p.tma_stages <= 0) S = npt == 1 ? 2 : 3;
+    }
     if (want == DMRT_KERNEL_AUTO)
         want = (p.nx > 2 * dmrt::kTmaStrip && p.ny >= 4 * R) ? DMRT_KERNEL_TMA : DMRT_KERNEL_DIRECT;
     c->kernel = want;
+    c->npt = npt;
     c->R = R;
     c->S = S;
     c->tma_func = nullptr;
     if (want != DMRT_KERNEL_TMA) return DMRT_OK;
-    for (const TmaVariant& v : kTmaVariants)
-        if (v.R == R && v.S == S) c->tma_func = v.func;
-    if (!c->tma_func) {
-        set_err(c, "no TMA tile with %d rows and %d stages is compiled in", R, S);
+    const dmrt::TmaVariant* v = find_tma_variant(npt, R, S);
+    if (!v) {
+        set_err(c, "no TMA tile with %d nodes/thread, %d rows, %d stages is compiled in", npt, R, S);
         return DMRT_E_ARG;
     }
+    c->tma_func = v->func;
+    c->tma_block = R * (256 / npt);
     if (p.ny < R) {
         set_err(c, "TMA kernel needs ny >= %d", R);
         return DMRT_E_ARG;
@@ -265,7 +275,7 @@ int setup_kernel(dmrt_ctx* c) {
     int dev = 0, sms = 0, per_sm = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
-    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->tma_func, 64 * R, c->tma_smem),
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->tma_func, c->tma_block, c->tma_smem),
        "occupancy");
     if (per_sm < 1) {
         set_err(c, "TMA tile %dx%d does not fit on an SM", R, S);
@@ -347,6 +357,7 @@ void dmrt_default_params(dmrt_params* p) {
     p->nu_capacity = 1 << 20;
     p->tma_rows = 0;
     p->tma_stages = 0;
+    p->tma_npt = 0;
 }
 
 int dmrt_derive(const dmrt_params* p, dmrt_consts* out) {
@@ -493,7 +504,7 @@ static int launch_step(dmrt_ctx* c, int from) {
     dmrt::StepArgs A = step_args(c, from);
     if (c->kernel == DMRT_KERNEL_TMA) {
         void* params[5] = {&c->map6[from], &c->map4[from], &A, &c->sc, &c->geo};
-        cudaError_t e = cudaLaunchKernel(c->tma_func, dim3(c->tma_grid), dim3(64 * c->R), params,
+        cudaError_t e = cudaLaunchKernel(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), params,
                                          c->tma_smem, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "TMA step launch");
     } else {
@@ -525,7 +536,7 @@ static int build_graph(dmrt_ctx* c, int from) {
         if (c->kernel == DMRT_KERNEL_TMA) {
             kp.func = const_cast<void*>(c->tma_func);
             kp.gridDim = dim3(c->tma_grid);
-            kp.blockDim = dim3(64 * c->R);
+            kp.blockDim = dim3(c->tma_block);
             kp.sharedMemBytes = (unsigned)c->tma_smem;
             kp.kernelParams = tparams;
         } else {
@@ -698,6 +709,26 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
                              (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyHostToDevice, c->stream),
            "copy state to device");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DMRT_OK;
+}
+
+int dmrt_get_launch(const dmrt_ctx* c, dmrt_launch* out) {
+    if (!c || !out) return DMRT_E_ARG;
+    out->kernel = c->kernel;
+    if (c->kernel == DMRT_KERNEL_TMA) {
+        out->tma_npt = c->npt;
+        out->tma_rows = c->R;
+        out->tma_stages = c->S;
+        out->grid = c->tma_grid;
+        out->block = c->tma_block;
+        out->smem_bytes = (int64_t)c->tma_smem;
+    } else {
+        out->tma_npt = out->tma_rows = out->tma_stages = 0;
+        out->grid = (int32_t)(c->grid.x * c->grid.y);
+        out->block = dmrt::kDirectThreads;
+        out->smem_bytes = 0;
+    }
+    out->graph_steps = c->graph_len;
     return DMRT_OK;
 }
 

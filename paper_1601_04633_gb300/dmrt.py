@@ -52,6 +52,7 @@ class Params(ctypes.Structure):
         ("storage", ctypes.c_int32), ("kernel", ctypes.c_int32),
         ("nu_capacity", ctypes.c_int64),
         ("tma_rows", ctypes.c_int32), ("tma_stages", ctypes.c_int32),
+        ("tma_npt", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -59,6 +60,16 @@ class Consts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "nu", "alpha", "s_e", "s_nu", "s_q", "s_eps", "sig_k", "sig_e", "sig_nu",
         "a", "gbeta", "abb", "Ma", "fo_per_step")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Launch(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("tma_npt", ctypes.c_int32), ("tma_rows", ctypes.c_int32),
+                ("tma_stages", ctypes.c_int32),
+                ("grid", ctypes.c_int32), ("block", ctypes.c_int32), ("smem_bytes", ctypes.c_int64),
+                ("graph_steps", ctypes.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -85,6 +96,7 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int64)]),
     "dmrt_set_wall_profiles": (ctypes.c_int, [_VP, _DP, _DP]),
     "dmrt_get_consts": (ctypes.c_int, [_VP, ctypes.POINTER(Consts)]),
+    "dmrt_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
@@ -195,6 +207,12 @@ def dmrt_get_consts(h) -> Consts:
     return k
 
 
+def dmrt_get_launch(h) -> Launch:
+    k = Launch()
+    _check(load().dmrt_get_launch(h, ctypes.byref(k)), h)
+    return k
+
+
 def dmrt_get_state(h, nx: int, ny: int) -> np.ndarray:
     out = np.empty((14, ny, nx), dtype=np.float32)
     _check(load().dmrt_get_state(h, out.ctypes.data_as(_FP)), h)
@@ -215,7 +233,7 @@ def dmrt_destroy(h):
 def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.5,
                 theta_ref=None, theta_init=0.0, left_wall=DMRT_WALL_FIXED,
                 right_wall=DMRT_WALL_FIXED, storage=DMRT_FP32, nu_capacity=1 << 20,
-                kernel=DMRT_KERNEL_AUTO, tma_rows=0, tma_stages=0) -> Params:
+                kernel=DMRT_KERNEL_AUTO, tma_rows=0, tma_stages=0, tma_npt=0) -> Params:
     p = dmrt_default_params()
     p.nx, p.ny, p.Ra, p.Pr, p.alpha, p.Ma = int(nx), int(ny), float(Ra), float(Pr), float(alpha), float(Ma)
     p.theta_hot, p.theta_cold = float(theta_hot), float(theta_cold)
@@ -224,6 +242,7 @@ def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.
     p.left_wall, p.right_wall, p.storage = int(left_wall), int(right_wall), int(storage)
     p.nu_capacity = int(nu_capacity)
     p.kernel, p.tma_rows, p.tma_stages = int(kernel), int(tma_rows), int(tma_stages)
+    p.tma_npt = int(tma_npt)
     return p
 
 
@@ -245,6 +264,7 @@ class Cavity2D:
         self.h = dmrt_create(params, theta0, self.workspace.data_ptr(), nbytes,
                              self.stream.cuda_stream)
         self.consts = dmrt_get_consts(self.h)
+        self.launch = dmrt_get_launch(self.h).as_dict()
         if theta_hot_profile is not None:
             dmrt_set_wall_profiles(self.h, hot=theta_hot_profile)
 
@@ -256,7 +276,8 @@ class Cavity2D:
                         **{k: v for k, v in kw.items() if k in ("storage", "nu_capacity",
                                                                    "left_wall", "right_wall",
                                                                    "theta_ref", "kernel",
-                                                                   "tma_rows", "tma_stages")})
+                                                                   "tma_rows", "tma_stages",
+                                                                   "tma_npt")})
         rest = {k: v for k, v in kw.items() if k in ("device", "stream")}
         return cls(p, theta0=cav.theta0(), theta_hot_profile=cav.theta_hot_profile, **rest)
 

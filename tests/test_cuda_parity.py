@@ -192,7 +192,9 @@ def test_deterministic_and_graph_equals_single_launches(D, kernel):
     assert np.array_equal(na, nb) and np.array_equal(na, nc)
 
 
-TMA_TILES = [(1, 4), (1, 6), (2, 2), (2, 3), (2, 4), (4, 2), (4, 3)]
+TMA_TILES = ([(4, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (2, 2), (2, 3), (2, 4), (4, 2), (4, 3)]]
+             + [(2, r, s) for r, s in [(1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (4, 2)]]
+             + [(1, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (3, 2), (4, 2), (4, 3)]])
 
 
 def test_all_kernel_variants_agree_bitwise(D):
@@ -203,12 +205,12 @@ def test_all_kernel_variants_agree_bitwise(D):
     cav = inputs.Cavity(nx, ny, 1e6, 0.005, noise_amp=0.0)
     state = _random_state(nx, ny, seed=41)
     outs = []
-    for kernel, (R, S) in [(1, (0, 0))] + [(2, t) for t in TMA_TILES]:
-        sim = D.Cavity2D.from_inputs(cav, kernel=kernel, tma_rows=R, tma_stages=S)
+    for kernel, (npt, R, S) in [(1, (0, 0, 0))] + [(2, t) for t in TMA_TILES]:
+        sim = D.Cavity2D.from_inputs(cav, kernel=kernel, tma_rows=R, tma_stages=S, tma_npt=npt)
         sim.set_state(state)
         sim.step(steps)
         sim.check()
-        outs.append((sim.get_state(), sim.nusselt(steps)[2], (kernel, R, S)))
+        outs.append((sim.get_state(), sim.nusselt(steps)[2], (kernel, npt, R, S)))
         sim.close()
     ref_state, ref_nu, _ = outs[0]
     for st, nu, tag in outs[1:]:
