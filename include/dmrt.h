@@ -176,6 +176,44 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold);
 int dmrt_get_state(dmrt_ctx* c, float* host);
 int dmrt_set_state(dmrt_ctx* c, const float* host);
 
+/* ---- One step without any device allocation (the paper has no counterpart) ----
+ *
+ * For callers that cannot allocate device memory where they step a cavity: code
+ * running while a framework owns all device memory and hands out only input and
+ * output buffers, real-time loops in which a cudaMalloc would synchronise the
+ * device, or plug-in hosts that forbid allocation inside their callbacks.
+ * dmrt_step_noalloc advances one time step (the same fused step as dmrt_step,
+ * run by the direct-load kernel) from src to dst and allocates nothing: the
+ * scratch the step needs (per-row Nusselt values, the arrival counter of the
+ * fused reduction, the wall temperatures, the error word) lives in one
+ * file-scope device array of 16 * DMRT_NOALLOC_MAX_NY + 256 bytes (about 128 KB)
+ * that every GPU which loads the library holds until the process exits.
+ *
+ *   p:          problem parameters, as for dmrt_create (kernel and tma_* ignored);
+ *               ny must not exceed DMRT_NOALLOC_MAX_NY (else DMRT_E_ARG, with the
+ *               reason in dmrt_last_error(NULL)).
+ *   src, dst:   distinct 16-byte aligned device buffers, each 14 * ny * pitch
+ *               floats, pitch = nx rounded up to a multiple of 128: the
+ *               post-collision populations at time t (read) and t + 1 (written),
+ *               14 planes [ny][pitch] in the order (paper numbering)
+ *               f1 f2 f4 g1 g2 g4 f3 f6 f7 g3 f5 f8 f9 g5. Padding columns are
+ *               ignored on input.
+ *   theta_hot, theta_cold: device float arrays [ny] of wall temperatures, or NULL
+ *               for the constant theta_hot / theta_cold of p.
+ *   nu_mean:    device pointer to one double that receives the step's mean
+ *               hot-wall Nusselt number (Eqs. 18-19), or NULL.
+ *   stream:     cudaStream_t as void*; the call only enqueues work on it.
+ *
+ * The first call on a device looks up the array's device address (host code
+ * only sees a host-side stand-in for it), so make that first call before any
+ * stream capture. Every call shares the array and clears what must start at
+ * zero; calls that overlap on the GPU (other streams, other threads) race on it,
+ * so order them. Non-finite values are not reported by this call. */
+#define DMRT_NOALLOC_MAX_NY 8192
+int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* dst,
+                      const float* theta_hot, const float* theta_cold, double* nu_mean,
+                      void* stream);
+
 /* Launch configuration a context resolved to (for reports and tuning). */
 typedef struct {
     int32_t kernel;       /* DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */

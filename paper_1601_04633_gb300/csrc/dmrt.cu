@@ -61,6 +61,10 @@ struct Misc {
 
 }  // namespace
 
+void dmrt_internal_set_error(const char* msg) {
+    std::snprintf(g_create_error, sizeof g_create_error, "%s", msg);
+}
+
 struct dmrt_ctx {
     dmrt_params p;
     dmrt_consts k;

@@ -75,7 +75,8 @@ __device__ __forceinline__ float4 pull_finish(const PlaneLoad& L, int j, int x0,
     return yin ? out : v;
 }
 
-__global__ void __launch_bounds__(kDirectThreads, 4) step_direct_kernel(StepArgs A, StepConsts K) {
+// Internal linkage: every translation unit that launches it compiles its own copy.
+static __global__ void __launch_bounds__(kDirectThreads, 4) step_direct_kernel(StepArgs A, StepConsts K) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     Geo G;

@@ -30,6 +30,15 @@ DMRT_E_STATE = -7
 DMRT_FP32, DMRT_FP16, DMRT_BF16 = 0, 1, 2
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
 DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA = 0, 1, 2
+DMRT_NOALLOC_MAX_NY = 8192
+# Device plane order of the population buffers: entry d is the index, in the host
+# order f1..f9, g1..g5 (paper numbering), of device plane d.
+DEVICE_PLANE_ORDER = (0, 1, 3, 9, 10, 12, 2, 5, 6, 11, 4, 7, 8, 13)
+
+
+def device_pitch(nx: int) -> int:
+    """Elements per row of a device population plane."""
+    return (int(nx) + 127) // 128 * 128
 
 _ERRNAMES = {-1: "DMRT_E_ARG", -2: "DMRT_E_UNSTABLE", -3: "DMRT_E_CUDA", -4: "DMRT_E_DIVERGED",
              -5: "DMRT_E_TIMEOUT", -6: "DMRT_E_SPACE", -7: "DMRT_E_STATE"}
@@ -99,6 +108,7 @@ SIGNATURES = {
     "dmrt_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
+    "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
     "dmrt_destroy": (None, [_VP]),
 }
@@ -222,6 +232,13 @@ def dmrt_get_state(h, nx: int, ny: int) -> np.ndarray:
 def dmrt_set_state(h, state):
     a = np.ascontiguousarray(state, dtype=np.float32)
     _check(load().dmrt_set_state(h, a.ctypes.data_as(_FP)), h)
+
+
+def dmrt_step_noalloc(p: Params, src_ptr: int, dst_ptr: int, nu_mean_ptr: int, stream_ptr: int,
+                      hot_ptr: int = 0, cold_ptr: int = 0):
+    """One step between caller-owned device buffers, with no device allocation."""
+    _check(load().dmrt_step_noalloc(ctypes.byref(p), _VP(src_ptr), _VP(dst_ptr), _VP(hot_ptr or None),
+                                    _VP(cold_ptr or None), _VP(nu_mean_ptr or None), _VP(stream_ptr)))
 
 
 def dmrt_destroy(h):
