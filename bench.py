@@ -33,6 +33,8 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS (both lattices) & % HBM roofline; batched/FP16 vs plain FP32 at Nu err≤1e-3"
 UNIT = "MLUPS"
 BYTES_PER_NODE_FP32 = 112  # 14 populations read + 14 written, 4 bytes each
+STORAGES = {"fp32": 0, "fp16": 1, "bf16": 2}
+BYTES_PER_NODE = {"fp32": 112, "fp16": 56, "bf16": 56}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_4096x4096.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", f)
@@ -235,7 +237,8 @@ def run_dmrt(args):
     nodes = cav.nx * cav.ny
     stream = torch.cuda.current_stream()
 
-    kw = dict(kernel=args.kernel, tma_rows=args.tma_rows, tma_stages=args.tma_stages)
+    kw = dict(kernel=args.kernel, tma_rows=args.tma_rows, tma_stages=args.tma_stages,
+              tma_npt=args.tma_npt, storage=STORAGES[args.storage])
     sim = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1), **kw)
     launch = dict(sim.launch)
     sim.step(args.warmup)
@@ -262,6 +265,30 @@ def run_dmrt(args):
     nu_mean, _, _ = sim.nusselt()
     sim.close()
     del sim
+
+    # Secondary: the 16-bit storage variants on the same workload and step count,
+    # timed the same way, with their mean Nusselt number against this run's.
+    secondary = {}
+    if not args.no_secondary and args.storage == "fp32":
+        for st in ("fp16", "bf16"):
+            s2 = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1),
+                                        storage=STORAGES[st], kernel=2, tma_npt=4, tma_rows=4, tma_stages=2)
+            s2.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s2.step(args.steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms2 = e0.elapsed_time(e1)
+            s2.check()
+            nu2 = s2.nusselt()[0]
+            secondary[st] = {"value": nodes * args.steps / (ms2 / 1e3) / 1e6, "unit": UNIT,
+                             "bytes_per_node": BYTES_PER_NODE[st], "launch": dict(s2.launch),
+                             "nu_mean_last": nu2,
+                             "nu_rel_err_vs_fp32": abs(nu2 - nu_mean) / abs(nu_mean) if nu_mean else None}
+            s2.close()
+            del s2
 
     # End to end through the public C ABI with host buffers: create from a pinned
     # host temperature field (H2D), K steps, then the Nu series and the u, v, theta
@@ -295,22 +322,24 @@ def run_dmrt(args):
     steps = max(args.steps, 1)
     value = ws * nodes * args.steps / (ms / 1e3) / 1e6
     per_launch_s = ms / 1e3 / steps
-    achieved = BYTES_PER_NODE_FP32 * nodes / per_launch_s / 1e9
+    bpn = BYTES_PER_NODE[args.storage]
+    achieved = bpn * nodes / per_launch_s / 1e9
     peak, peak_src = hbm_peak()
-    traffic = ncu_traffic_per_launch(nodes)
+    traffic = ncu_traffic_per_launch(nodes) if args.storage == "fp32" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.storage == "fp32" else f"{args.storage} storage, f32 arithmetic",
+        "data": "synthetic",
         "config": {"workload": label, "nx": cav.nx, "ny": cav.ny, "Ra": cav.Ra, "Pr": cav.Pr,
-                   "alpha": cav.alpha, "storage": "fp32", "parallelism": f"{ws} independent cavities",
+                   "alpha": cav.alpha, "storage": args.storage, "parallelism": f"{ws} independent cavities",
                    "launch": launch,
                    "l2": "state (two 14-plane fp32 buffers) larger than L2: no flush"
-                   if BYTES_PER_NODE_FP32 * nodes > 129e6 else "state fits in L2"},
+                   if bpn * nodes > 129e6 else "state fits in L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} HBM copy bandwidth",
-                     "bytes_per_node": BYTES_PER_NODE_FP32,
+                     "bytes_per_node": bpn,
                      "kernel": "dmrt::step_tma_kernel" if launch["kernel"] == 2 else "dmrt::step_direct_kernel"},
         "e2e": {"value": ws * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes / steps,
@@ -319,6 +348,8 @@ def run_dmrt(args):
         "clocks": sampler.summary(),
         "nu_mean_last": nu_mean,
     }
+    if secondary:
+        line["secondary"] = secondary
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = time_oracle(cav, budget_s=12.0)
     print(json.dumps(line), flush=True)
@@ -338,6 +369,9 @@ def main():
     ap.add_argument("--kernel", type=int, default=0, help="0 auto, 1 direct, 2 TMA")
     ap.add_argument("--tma-rows", type=int, default=0)
     ap.add_argument("--tma-stages", type=int, default=0)
+    ap.add_argument("--tma-npt", type=int, default=0)
+    ap.add_argument("--storage", choices=tuple(STORAGES), default="fp32")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the 16-bit storage runs")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":

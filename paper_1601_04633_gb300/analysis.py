@@ -1,0 +1,95 @@
+"""Analysis of the mean hot-wall Nusselt number history Nu(t) (host side).
+
+The paper reports, for each case of Table 1 (Sec. 4), whether the mean Nusselt
+number reaches a steady value or oscillates, and for oscillating cases the
+mean, amplitude and period, with time measured by the Fourier number
+Fo = alpha t / H^2 (Eq. 20). This module computes those statistics from a
+per-step series. The period is the mean spacing of upward crossings, located
+by linear interpolation between steps: first of the window mean (or, if the
+record drifts too much for that, of its linear trend), then, to separate the
+oscillation from any slow wave or drift, of the moving average over one such
+period. The amplitude is half the peak-to-peak range of the oscillation about
+that moving average; the drift is the mean of the last fifth of the window
+minus that of the first fifth.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, asdict
+
+import numpy as np
+
+
+@dataclass
+class NuStats:
+    steady: bool
+    mean: float
+    amplitude: float          # half the peak-to-peak range of the oscillation
+    peak_to_peak: float
+    period_fo: float | None   # in Fourier-number units; None when steady or undetermined
+    cycles: int               # complete cycles seen in the window
+    window_fo: tuple          # (start, end) of the analysed window in Fo
+    drift: float              # mean of the last fifth of the window minus the first fifth
+
+    def as_dict(self):
+        return asdict(self)
+
+
+def fourier_number(steps, alpha: float, H: float):
+    """Fo = alpha t / H^2 (Eq. 20) for step counts t (lattice units, dt = 1)."""
+    return alpha * np.asarray(steps, dtype=np.float64) / (H * H)
+
+
+def _crossing_period(f, d):
+    """Mean spacing of upward zero crossings of d(f), and the number of complete cycles."""
+    up = np.nonzero((d[:-1] < 0) & (d[1:] >= 0))[0]
+    if len(up) < 2:
+        return None, 0
+    t = f[up] + (f[up + 1] - f[up]) * (-d[up]) / (d[up + 1] - d[up])
+    return float((t[-1] - t[0]) / (len(t) - 1)), len(t) - 1
+
+
+def nu_statistics(series, fo_per_step: float, window_fo: float | None = None,
+                  steady_tol: float = 1e-4) -> NuStats:
+    """Statistics of Nu over the last ``window_fo`` Fourier units of ``series``.
+
+    series[k] is the mean Nu after step k + 1. The record counts as steady when its
+    peak-to-peak range over the window is below ``steady_tol`` times the mean.
+    """
+    nu = np.asarray(series, dtype=np.float64)
+    n = len(nu)
+    if n < 4:
+        raise ValueError("need at least 4 samples")
+    fo = (np.arange(n) + 1) * fo_per_step
+    if window_fo is None:
+        start = n // 2
+    else:
+        start = max(0, n - int(round(window_fo / fo_per_step)))
+    w = nu[start:]
+    f = fo[start:]
+    mean = float(w.mean())
+    p2p = float(w.max() - w.min())
+    steady = p2p <= steady_tol * abs(mean)
+    fifth = max(1, len(w) // 5)
+    drift = float(w[-fifth:].mean() - w[:fifth].mean())
+    period, cycles, amplitude = None, 0, 0.5 * p2p
+    if not steady:
+        period, cycles = _crossing_period(f, w - mean)
+        if period is None or cycles < 2:
+            trend = np.polyval(np.polyfit(f - f[0], w, 1), f - f[0])
+            period, cycles = _crossing_period(f, w - trend)
+        if period is not None:
+            L = int(round(period / fo_per_step))
+            if 2 <= L < len(w) // 2:
+                # centred moving average over one period (valid part only)
+                c = np.cumsum(np.concatenate([[0.0], w]))
+                ma = (c[L:] - c[:-L]) / L
+                off = L // 2
+                seg = w[off:off + len(ma)]
+                fseg = f[off:off + len(ma)]
+                p2, c2 = _crossing_period(fseg, seg - ma)
+                if p2 is not None:
+                    period, cycles = p2, c2
+                    amplitude = 0.5 * float((seg - ma).max() - (seg - ma).min())
+    return NuStats(steady=bool(steady), mean=mean, amplitude=amplitude, peak_to_peak=p2p,
+                   period_fo=period, cycles=cycles, window_fo=(float(f[0]), float(f[-1])),
+                   drift=drift)

@@ -1,6 +1,8 @@
 // Host side of libdmrt.so: parameter derivation, workspace layout, the
 // init / fields kernels and the C entry points declared in include/dmrt.h.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
@@ -34,11 +36,13 @@ struct Layout {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+int elem_bytes(int storage) { return storage == DMRT_FP32 ? 4 : 2; }
+
 Layout make_layout(const dmrt_params& p) {
     Layout L;
     L.pitch = ((p.nx + 127) / 128) * 128;
     L.plane = (long long)p.ny * L.pitch;
-    L.buf_bytes = align256((size_t)kPlanes * (size_t)L.plane * sizeof(float));
+    L.buf_bytes = align256((size_t)kPlanes * (size_t)L.plane * elem_bytes(p.storage));
     size_t o = 0;
     L.off_a = o; o += L.buf_bytes;
     L.off_b = o; o += L.buf_bytes;
@@ -140,11 +144,25 @@ dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
 
 // ---- small kernels ----------------------------------------------------------
 
+__device__ __forceinline__ float elem_to_f(float x) { return x; }
+__device__ __forceinline__ float elem_to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float elem_to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename E>
+__device__ __forceinline__ E elem_from_f(float x);
+template <>
+__device__ __forceinline__ float elem_from_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __half elem_from_f<__half>(float x) { return __float2half_rn(x); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 elem_from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
 // Initial post-collision state: f = 0 (rest, delta-rho = 0) and g at the D2Q5
 // equilibrium of theta0 at rest, g_0 = (1 - a) theta / 5, g_1..4 = (4 + a) theta / 20
-// (Eq. 42 mapped back through N). Also zeroes the padding columns.
-__global__ void init_kernel(float* __restrict__ S, const double* __restrict__ theta0,
-                            double theta_const, double a, int nx, int ny, int pitch,
+// (Eq. 42 mapped back through N), stored minus sh0 / sh1 (16-bit storage
+// shift; 0 for float32). Also zeroes the padding columns.
+template <typename E>
+__global__ void init_kernel(E* __restrict__ S, const double* __restrict__ theta0, double theta_const,
+                            double a, double sh0, double sh1, int nx, int ny, int pitch,
                             long long plane) {
     const long long n = (long long)ny * pitch;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
@@ -153,33 +171,59 @@ __global__ void init_kernel(float* __restrict__ S, const double* __restrict__ th
         double th = 0.0;
         const bool in = i < nx;
         if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
-        for (int k = 0; k < 9; ++k) S[plane_f(k) * plane + q] = 0.f;
-        S[plane_g(0) * plane + q] = in ? (float)((1.0 - a) * th / 5.0) : 0.f;
-        const float side = in ? (float)((4.0 + a) * th / 20.0) : 0.f;
-        for (int k = 1; k < 5; ++k) S[plane_g(k) * plane + q] = side;
+        for (int k = 0; k < 9; ++k) S[plane_f(k) * plane + q] = elem_from_f<E>(0.f);
+        S[plane_g(0) * plane + q] = elem_from_f<E>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
+        const float side = in ? (float)((4.0 + a) * th / 20.0 - sh1) : 0.f;
+        for (int k = 1; k < 5; ++k) S[plane_g(k) * plane + q] = elem_from_f<E>(side);
     }
 }
 
 // Macroscopic fields of a post-collision state at the same time level:
 // theta = sum g* (the thermal collision keeps theta), u = sum e f*, and
 // v = sum e_y f* - G_y(theta) (the force added rho0 G to the momentum).
-__global__ void fields_kernel(const float* __restrict__ S, float* __restrict__ u,
+template <typename E>
+__global__ void fields_kernel(const E* __restrict__ S, float* __restrict__ u,
                               float* __restrict__ v, float* __restrict__ th, int nx, int ny,
-                              int pitch, long long plane, float gbeta, float theta_ref) {
+                              int pitch, long long plane, float gbeta, float theta_ref,
+                              float sh0, float sh1) {
     const long long n = (long long)nx * ny;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(q / nx), i = (int)(q % nx);
         const long long s = (long long)j * pitch + i;
         float f[9], g[5];
-        for (int k = 0; k < 9; ++k) f[k] = S[plane_f(k) * plane + s];
-        for (int k = 0; k < 5; ++k) g[k] = S[plane_g(k) * plane + s];
+        for (int k = 0; k < 9; ++k) f[k] = elem_to_f(S[plane_f(k) * plane + s]);
+        for (int k = 0; k < 5; ++k) g[k] = elem_to_f(S[plane_g(k) * plane + s]) + (k == 0 ? sh0 : sh1);
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
         const float t = g[0] + g[1] + g[2] + g[3] + g[4];
         if (u) u[q] = jx;
         if (v) v[q] = jy - gbeta * (t - theta_ref);
         if (th) th[q] = t;
+    }
+}
+
+// One plane between the padded device layout and a dense float32 [ny][nx]
+// array (16-bit storage: value = stored + shift).
+template <typename E>
+__global__ void plane_to_f32(const E* __restrict__ P, float* __restrict__ out, int nx, int ny,
+                             int pitch, float shift) {
+    const long long n = (long long)nx * ny;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        out[q] = elem_to_f(P[(size_t)j * pitch + i]) + shift;
+    }
+}
+
+template <typename E>
+__global__ void plane_from_f32(E* __restrict__ P, const float* __restrict__ in, int nx, int ny,
+                               int pitch, float shift) {
+    const long long n = (long long)ny * pitch;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / pitch), i = (int)(q % pitch);
+        P[q] = elem_from_f<E>(i < nx ? in[(size_t)j * nx + i] - shift : 0.f);
     }
 }
 
@@ -191,16 +235,28 @@ __global__ void fill_kernel(float* p, const double* src, double value, int n) {
 // Host state arrays are ordered f_1..f_9, g_1..g_5; the device planes are grouped.
 int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
 
+// Call fn with a value of the storage element type (float, __half, __nv_bfloat16).
+template <typename Fn>
+void with_elem(int storage, Fn&& fn) {
+    if (storage == DMRT_FP16)
+        fn(__half{});
+    else if (storage == DMRT_BF16)
+        fn(__nv_bfloat16{});
+    else
+        fn(float{});
+}
+
 constexpr int kDefaultNpt = 1, kDefaultR = 4, kDefaultS = 2;
 
-const dmrt::TmaVariant* find_tma_variant(int npt, int R, int S) {
-    const dmrt::TmaVariant* (*lists[3])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
-                                                dmrt::tma_variants_npt1};
+const dmrt::TmaVariant* find_tma_variant(int storage, int npt, int R, int S) {
+    const dmrt::TmaVariant* (*lists[5])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
+                                                dmrt::tma_variants_npt1, dmrt::tma_variants_fp16,
+                                                dmrt::tma_variants_bf16};
     for (auto list : lists) {
         int n = 0;
         const dmrt::TmaVariant* v = list(&n);
         for (int i = 0; i < n; ++i)
-            if (v[i].npt == npt && v[i].R == R && v[i].S == S) return &v[i];
+            if (v[i].storage == storage && v[i].npt == npt && v[i].R == R && v[i].S == S) return &v[i];
     }
     return nullptr;
 }
@@ -226,11 +282,14 @@ int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes) {
         return DMRT_E_CUDA;
     }
     cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->p.ny, (cuuint64_t)kPlanes};
-    cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * sizeof(float),
-                             (cuuint64_t)c->L.plane * sizeof(float)};
+    const int eb = elem_bytes(c->p.storage);
+    cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * eb, (cuuint64_t)c->L.plane * eb};
+    const CUtensorMapDataType dt = c->p.storage == DMRT_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : c->p.storage == DMRT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint32_t box[3] = {(cuuint32_t)dmrt::kTmaBox, (cuuint32_t)c->R, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+    CUresult r = enc(m, dt, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
@@ -253,14 +312,20 @@ int setup_kernel(dmrt_ctx* c) {
         if (p.tma_stages <= 0) S = npt == 1 ? 2 : 3;
     }
     if (want == DMRT_KERNEL_AUTO)
-        want = (p.nx > 2 * dmrt::kTmaStrip && p.ny >= 4 * R) ? DMRT_KERNEL_TMA : DMRT_KERNEL_DIRECT;
+        want = (p.storage != DMRT_FP32 || (p.nx > 2 * dmrt::tma_strip(4) && p.ny >= 4 * R))
+                   ? DMRT_KERNEL_TMA
+                   : DMRT_KERNEL_DIRECT;
+    if (want == DMRT_KERNEL_DIRECT && p.storage != DMRT_FP32) {
+        set_err(c, "the direct kernel stores float32 only; 16-bit storage runs the TMA kernel");
+        return DMRT_E_ARG;
+    }
     c->kernel = want;
     c->npt = npt;
     c->R = R;
     c->S = S;
     c->tma_func = nullptr;
     if (want != DMRT_KERNEL_TMA) return DMRT_OK;
-    const dmrt::TmaVariant* v = find_tma_variant(npt, R, S);
+    const dmrt::TmaVariant* v = find_tma_variant(p.storage, npt, R, S);
     if (!v) {
         set_err(c, "no TMA tile with %d nodes/thread, %d rows, %d stages is compiled in", npt, R, S);
         return DMRT_E_ARG;
@@ -271,9 +336,10 @@ int setup_kernel(dmrt_ctx* c) {
         set_err(c, "TMA kernel needs ny >= %d", R);
         return DMRT_E_ARG;
     }
-    c->geo.n_strips = (p.nx + dmrt::kTmaStrip - 1) / dmrt::kTmaStrip;
+    const int strip = dmrt::tma_strip(elem_bytes(p.storage));
+    c->geo.n_strips = (p.nx + strip - 1) / strip;
     c->geo.n_rowblocks = (p.ny + R - 1) / R;
-    c->tma_smem = dmrt::tma_smem_bytes(R, S);
+    c->tma_smem = dmrt::tma_smem_bytes(R, S, elem_bytes(p.storage));
     CK(cudaFuncSetAttribute(c->tma_func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->tma_smem),
        "set TMA kernel shared memory");
     int dev = 0, sms = 0, per_sm = 0;
@@ -317,8 +383,8 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "wall kinds must be DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC");
         return DMRT_E_ARG;
     }
-    if (p->storage != DMRT_FP32) {
-        set_err(c, "storage %d not available in this build (only DMRT_FP32)", p->storage);
+    if (p->storage != DMRT_FP32 && p->storage != DMRT_FP16 && p->storage != DMRT_BF16) {
+        set_err(c, "storage must be DMRT_FP32, DMRT_FP16 or DMRT_BF16 (got %d)", p->storage);
         return DMRT_E_ARG;
     }
     if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_TMA) {
@@ -456,6 +522,11 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     s.abb = (float)k.abb;
     s.left_fixed = p->left_wall == DMRT_WALL_FIXED;
     s.right_fixed = p->right_wall == DMRT_WALL_FIXED;
+    // 16-bit storage keeps g_i - w_i theta_ref (w_0 = (1-a)/5, w_1..4 = (4+a)/20).
+    const double sh0 = p->storage == DMRT_FP32 ? 0.0 : (1.0 - k.a) / 5.0 * p->theta_ref;
+    const double sh1 = p->storage == DMRT_FP32 ? 0.0 : (4.0 + k.a) / 20.0 * p->theta_ref;
+    s.gsh0 = (float)sh0;
+    s.gsh1 = (float)sh1;
     const double dT = p->theta_hot - p->theta_cold;
     s.nu_scale = dT != 0.0 ? (double)p->ny / (3.0 * dT) : 0.0;
 
@@ -483,18 +554,22 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
         reinterpret_cast<float*>(c->ws + L.off_cold), nullptr, p->theta_cold, p->ny);
     const double* d_theta0 = nullptr;
     if (theta0) {
-        // Stage the host field in buffer B (not yet used: it holds 56 bytes per node).
+        // Stage the host field in buffer B (not yet used: it holds 28 or 56 bytes per node).
         double* stage = reinterpret_cast<double*>(c->ws + L.off_b);
         cudaError_t e = cudaMemcpyAsync(stage, theta0, (size_t)p->nx * p->ny * sizeof(double),
                                         cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return fail(cuda_fail(c, e, "copy theta0"));
         d_theta0 = stage;
     }
-    init_kernel<<<1024, 256, 0, c->stream>>>(buf(c, 0), d_theta0, p->theta_init, k.a, p->nx,
-                                             p->ny, L.pitch, L.plane);
-    // Buffer B's padding columns must read as zero too.
-    init_kernel<<<1024, 256, 0, c->stream>>>(buf(c, 1), nullptr, 0.0, k.a, p->nx, p->ny,
-                                             L.pitch, L.plane);
+    with_elem(p->storage, [&](auto tag) {
+        using E = decltype(tag);
+        init_kernel<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<E*>(buf(c, 0)), d_theta0,
+                                                    p->theta_init, k.a, sh0, sh1, p->nx, p->ny,
+                                                    L.pitch, L.plane);
+        // Buffer B's padding columns must read as zero too.
+        init_kernel<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<E*>(buf(c, 1)), nullptr, p->theta_ref,
+                                                    k.a, sh0, sh1, p->nx, p->ny, L.pitch, L.plane);
+    });
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init kernels"));
     e = cudaStreamSynchronize(c->stream);
@@ -616,9 +691,12 @@ int dmrt_fields(dmrt_ctx* c, float* u, float* v, float* theta, int on_device) {
         dt = theta ? stage + 2 * n : nullptr;
     }
     const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-    fields_kernel<<<blocks, 256, 0, c->stream>>>(buf(c, c->cur), du, dv, dt, p.nx, p.ny,
-                                                 c->L.pitch, c->L.plane, c->sc.gbeta,
-                                                 c->sc.theta_ref);
+    with_elem(p.storage, [&](auto tag) {
+        using E = decltype(tag);
+        fields_kernel<E><<<blocks, 256, 0, c->stream>>>(reinterpret_cast<const E*>(buf(c, c->cur)), du, dv,
+                                                        dt, p.nx, p.ny, c->L.pitch, c->L.plane, c->sc.gbeta,
+                                                        c->sc.theta_ref, c->sc.gsh0, c->sc.gsh1);
+    });
     CK(cudaGetLastError(), "fields kernel");
     if (!on_device) {
         if (u) CK(cudaMemcpyAsync(u, du, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream), "copy u");
@@ -689,16 +767,39 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold) {
 }
 
 // Copy between a dense host array [14][ny][nx] of float32 and the padded
-// device planes of the current state (2D copies, one per plane).
+// device planes of the current state. float32 storage: one 2D copy per plane.
+// 16-bit storage: one plane at a time is converted through the idle buffer
+// (which holds 28 bytes per node, a float32 plane needs 4).
+static float plane_shift(const dmrt_ctx* c, int host_k) {
+    return host_k < 9 ? 0.f : (host_k == 9 ? c->sc.gsh0 : c->sc.gsh1);
+}
+
 int dmrt_get_state(dmrt_ctx* c, float* host) {
     if (!c || !host) return DMRT_E_ARG;
     const dmrt_params& p = c->p;
-    const float* S = buf(c, c->cur);
-    for (int k = 0; k < kPlanes; ++k)
-        CK(cudaMemcpy2DAsync(host + (size_t)k * p.nx * p.ny, (size_t)p.nx * sizeof(float),
-                             S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
-                             (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyDeviceToHost, c->stream),
-           "copy state to host");
+    const size_t n = (size_t)p.nx * p.ny;
+    if (p.storage == DMRT_FP32) {
+        const float* S = buf(c, c->cur);
+        for (int k = 0; k < kPlanes; ++k)
+            CK(cudaMemcpy2DAsync(host + (size_t)k * n, (size_t)p.nx * sizeof(float),
+                                 S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
+                                 (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyDeviceToHost, c->stream),
+               "copy state to host");
+    } else {
+        float* stage = buf(c, 1 - c->cur);
+        for (int k = 0; k < kPlanes; ++k) {
+            with_elem(p.storage, [&](auto tag) {
+                using E = decltype(tag);
+                const E* P = reinterpret_cast<const E*>(buf(c, c->cur)) + (size_t)host_plane(k) * c->L.plane;
+                plane_to_f32<E><<<1024, 256, 0, c->stream>>>(P, stage, p.nx, p.ny, c->L.pitch,
+                                                             plane_shift(c, k));
+            });
+            CK(cudaGetLastError(), "state conversion");
+            CK(cudaMemcpyAsync(host + (size_t)k * n, stage, n * sizeof(float), cudaMemcpyDeviceToHost,
+                               c->stream),
+               "copy state to host");
+        }
+    }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DMRT_OK;
 }
@@ -706,12 +807,29 @@ int dmrt_get_state(dmrt_ctx* c, float* host) {
 int dmrt_set_state(dmrt_ctx* c, const float* host) {
     if (!c || !host) return DMRT_E_ARG;
     const dmrt_params& p = c->p;
-    float* S = buf(c, c->cur);
-    for (int k = 0; k < kPlanes; ++k)
-        CK(cudaMemcpy2DAsync(S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
-                             host + (size_t)k * p.nx * p.ny, (size_t)p.nx * sizeof(float),
-                             (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyHostToDevice, c->stream),
-           "copy state to device");
+    const size_t n = (size_t)p.nx * p.ny;
+    if (p.storage == DMRT_FP32) {
+        float* S = buf(c, c->cur);
+        for (int k = 0; k < kPlanes; ++k)
+            CK(cudaMemcpy2DAsync(S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
+                                 host + (size_t)k * n, (size_t)p.nx * sizeof(float),
+                                 (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyHostToDevice, c->stream),
+               "copy state to device");
+    } else {
+        float* stage = buf(c, 1 - c->cur);
+        for (int k = 0; k < kPlanes; ++k) {
+            CK(cudaMemcpyAsync(stage, host + (size_t)k * n, n * sizeof(float), cudaMemcpyHostToDevice,
+                               c->stream),
+               "copy state to device");
+            with_elem(p.storage, [&](auto tag) {
+                using E = decltype(tag);
+                E* P = reinterpret_cast<E*>(buf(c, c->cur)) + (size_t)host_plane(k) * c->L.plane;
+                plane_from_f32<E><<<1024, 256, 0, c->stream>>>(P, stage, p.nx, p.ny, c->L.pitch,
+                                                               plane_shift(c, k));
+            });
+            CK(cudaGetLastError(), "state conversion");
+        }
+    }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DMRT_OK;
 }

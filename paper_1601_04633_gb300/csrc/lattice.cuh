@@ -37,6 +37,7 @@ struct StepConsts {
     float gbeta, theta_ref;          // G_y = gbeta (theta - theta_ref) (Eq. 27)
     float abb;                       // 2 sqrt(3) alpha (Eq. 45)
     int left_fixed, right_fixed;     // 1 = anti-bounce-back wall, 0 = adiabatic
+    float gsh0, gsh1;                // 16-bit storage: g_0, g_1..4 stored minus these
     double nu_scale;                 // H / (3 (theta_hot - theta_cold))
 };
 

@@ -73,6 +73,7 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     dmrt_consts k;
     int rc = dmrt_derive(p, &k);
     if (rc) return rc;
+    if (p->storage != DMRT_FP32) return fail(DMRT_E_ARG, "float32 storage only", nullptr);
     if (p->ny > kMaxNy) {
         char d[64];
         std::snprintf(d, sizeof d, "%d > %d", p->ny, kMaxNy);

@@ -1,9 +1,11 @@
 // Fused double-MRT time step, TMA-pipelined persistent variant (sm_103a).
 //
-// Work items are (strip, row block): a strip is 248 nodes of a row, a row block
-// R consecutive rows. For one item the pull-stream needs, per plane group
-// (see lattice.cuh), R rows of 256 floats starting 4 nodes left of the strip
-// (one halo column each side, rounded out to 16-byte alignment):
+// Work items are (strip, row block): a strip is 256 - 2 HALO nodes of a row
+// (248 for float32 storage, 240 for 16-bit storage), a row block R consecutive
+// rows. For one item the pull-stream needs, per plane group (see lattice.cuh),
+// R rows of 256 elements starting HALO nodes left of the strip (one halo column
+// each side, rounded out so the copy starts on a 16-byte boundary; HALO = 16
+// bytes / element size):
 //   group Z (6 planes) from rows j0 .. j0+R-1,
 //   group P (4 planes) from rows j0-1 .. j0+R-2,
 //   group N (4 planes) from rows j0+1 .. j0+R.
@@ -21,23 +23,29 @@
 // kErrTimeout, waits (bounded) for the copies it issued and returns.
 #pragma once
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "lattice.cuh"
 
 namespace dmrt {
 
-constexpr int kTmaStrip = 248;      // nodes per strip
-constexpr int kTmaBox = 256;        // floats per box row (strip + halos, aligned)
+constexpr int kTmaBox = 256;  // elements per box row (strip + halos, aligned)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__host__ __device__ constexpr int tma_halo(int elem_bytes) { return 16 / elem_bytes; }
+__host__ __device__ constexpr int tma_strip(int elem_bytes) { return kTmaBox - 2 * tma_halo(elem_bytes); }
 
 struct TmaGeo {
     int n_strips;
     int n_rowblocks;
 };
 
-__host__ __device__ constexpr int tma_stage_floats(int R) { return kPlanes * R * kTmaBox; }
-__host__ __device__ constexpr size_t tma_smem_bytes(int R, int S) {
-    return (size_t)S * tma_stage_floats(R) * sizeof(float) + (size_t)S * 8;
+__host__ __device__ constexpr int tma_stage_elems(int R) { return kPlanes * R * kTmaBox; }
+__host__ __device__ constexpr size_t tma_smem_bytes(int R, int S, int elem_bytes) {
+    return (size_t)S * tma_stage_elems(R) * elem_bytes + (size_t)S * 8;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -96,80 +104,103 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-template <int NPT>
-struct VecOf;
+// ---- typed storage -----------------------------------------------------------
+// Populations are stored as float32, or rounded to-nearest to float16 / bfloat16
+// (the collision always runs in float32). 16-bit storage keeps the thermal
+// populations shifted by their rest weight times theta_ref: a stored g_i is
+// g_i - w_i theta_ref (w_0 = (1-a)/5, w_1..4 = (4+a)/20); the flow populations
+// are already shifted by w_i rho0 (Eq. 33).
+__device__ __forceinline__ float to_f(float x) { return x; }
+__device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename E>
+__device__ __forceinline__ E from_f(float x);
 template <>
-struct VecOf<4> {
-    using T = float4;
-};
+__device__ __forceinline__ float from_f<float>(float x) { return x; }
 template <>
-struct VecOf<2> {
-    using T = float2;
-};
+__device__ __forceinline__ __half from_f<__half>(float x) { return __float2half_rn(x); }
 template <>
-struct VecOf<1> {
-    using T = float;
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+// Only 16-bit storage is shifted; float32 values are stored as they are.
+template <typename E>
+constexpr bool kShifted = !std::is_same<E, float>::value;
+
+template <typename E, int N>
+struct alignas(sizeof(E) * N) Pack {
+    E v[N];
 };
 
-template <int NPT>
-__device__ __forceinline__ void vec_get(const float* p, float (&o)[NPT]) {
-    if constexpr (NPT == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(p);
-        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
-    } else if constexpr (NPT == 2) {
-        const float2 v = *reinterpret_cast<const float2*>(p);
-        o[0] = v.x, o[1] = v.y;
-    } else {
-        o[0] = *p;
-    }
+// N consecutive stored values (aligned to N elements) as floats.
+template <typename E, int N>
+__device__ __forceinline__ void vec_get(const E* p, float (&o)[N]) {
+    const Pack<E, N> q = *reinterpret_cast<const Pack<E, N>*>(p);
+#pragma unroll
+    for (int e = 0; e < N; ++e) o[e] = to_f(q.v[e]);
 }
 
-template <int NPT>
-__device__ __forceinline__ void vec_ldg(const float* p, float (&o)[NPT]) {
-    if constexpr (NPT == 4) {
-        const float4 v = __ldg(reinterpret_cast<const float4*>(p));
-        o[0] = v.x, o[1] = v.y, o[2] = v.z, o[3] = v.w;
-    } else if constexpr (NPT == 2) {
-        const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-        o[0] = v.x, o[1] = v.y;
+template <typename E, int N>
+__device__ __forceinline__ void vec_ldg(const E* p, float (&o)[N], float shift) {
+    Pack<E, N> q;
+    if constexpr (sizeof(Pack<E, N>) == 16) {
+        const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+        q = *reinterpret_cast<const Pack<E, N>*>(&r);
+    } else if constexpr (sizeof(Pack<E, N>) == 8) {
+        const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+        q = *reinterpret_cast<const Pack<E, N>*>(&r);
+    } else if constexpr (sizeof(Pack<E, N>) == 4) {
+        const unsigned r = __ldg(reinterpret_cast<const unsigned*>(p));
+        q = *reinterpret_cast<const Pack<E, N>*>(&r);
     } else {
-        o[0] = __ldg(p);
+        const unsigned short r = __ldg(reinterpret_cast<const unsigned short*>(p));
+        q = *reinterpret_cast<const Pack<E, N>*>(&r);
     }
+#pragma unroll
+    for (int e = 0; e < N; ++e) o[e] = kShifted<E> ? to_f(q.v[e]) + shift : to_f(q.v[e]);
 }
 
-template <int NPT>
-__device__ __forceinline__ void vec_put(float* p, const float (&o)[NPT]) {
-    if constexpr (NPT == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(o[0], o[1], o[2], o[3]);
-    } else if constexpr (NPT == 2) {
-        *reinterpret_cast<float2*>(p) = make_float2(o[0], o[1]);
-    } else {
-        *p = o[0];
-    }
+template <typename E>
+__device__ __forceinline__ float ldg_one(const E* p, float shift) {
+    float o[1];
+    vec_ldg<E, 1>(p, o, shift);
+    return o[0];
+}
+
+template <typename E, int N>
+__device__ __forceinline__ void vec_put(E* p, const float (&o)[N], float shift) {
+    Pack<E, N> q;
+#pragma unroll
+    for (int e = 0; e < N; ++e) q.v[e] = from_f<E>(kShifted<E> ? o[e] - shift : o[e]);
+    *reinterpret_cast<Pack<E, N>*>(p) = q;
 }
 
 // NPT consecutive values of a shared-memory plane row for nodes n0..n0+NPT-1,
 // shifted for a pull with lattice x-velocity EX: node n takes the value at
-// n - EX. The row starts 4 nodes left of the strip, so node n sits at n + 4.
-template <int EX, int NPT>
-__device__ __forceinline__ void lds_pull(const float* rowp, int n0, float (&o)[NPT]) {
-    const float* p = rowp + 4 + n0;
+// n - EX. The row starts HALO nodes left of the strip, so node n sits at n + HALO.
+template <int EX, int NPT, typename E>
+__device__ __forceinline__ void lds_pull(const E* rowp, int n0, float (&o)[NPT], float shift) {
+    constexpr int HALO = tma_halo(sizeof(E));
+    const E* p = rowp + HALO + n0;
     if constexpr (EX == 0 || NPT == 1) {
-        vec_get<NPT>(p - EX, o);
+        vec_get<E, NPT>(p - EX, o);
     } else if constexpr (EX == 1) {
         float a[NPT], b[NPT];
-        vec_get<NPT>(p - NPT, a);
-        vec_get<NPT>(p, b);
+        vec_get<E, NPT>(p - NPT, a);
+        vec_get<E, NPT>(p, b);
         o[0] = a[NPT - 1];
 #pragma unroll
         for (int e = 1; e < NPT; ++e) o[e] = b[e - 1];
     } else {
         float b[NPT], c[NPT];
-        vec_get<NPT>(p, b);
-        vec_get<NPT>(p + NPT, c);
+        vec_get<E, NPT>(p, b);
+        vec_get<E, NPT>(p + NPT, c);
 #pragma unroll
         for (int e = 0; e < NPT - 1; ++e) o[e] = b[e + 1];
         o[NPT - 1] = c[0];
+    }
+    if constexpr (kShifted<E>) {
+#pragma unroll
+        for (int e = 0; e < NPT; ++e) o[e] += shift;
     }
 }
 
@@ -192,7 +223,7 @@ __device__ __forceinline__ void collide_nodes(float (&F)[9][NPT], float (&Gq)[5]
 #pragma unroll
         for (int k = 0; k < 9; ++k) F[k][e] = valid ? f[k] : 0.f;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) Gq[k][e] = valid ? g[k] : 0.f;
+        for (int k = 0; k < 5; ++k) Gq[k][e] = valid ? g[k] : (k == 0 ? K.gsh0 : K.gsh1);
         theta[e] = th;
     }
 }
@@ -218,19 +249,21 @@ struct ItemCursor {
     }
 };
 
-template <int NPT, int R, int S>
+template <typename E, int NPT, int R, int S>
 __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_constant__ CUtensorMap map6,
                                                           const __grid_constant__ CUtensorMap map4,
                                                           StepArgs A, StepConsts K, TmaGeo T) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    float* stages = reinterpret_cast<float*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * tma_stage_floats(R) * sizeof(float));
+    E* stages = reinterpret_cast<E*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * tma_stage_elems(R) * sizeof(E));
+    constexpr int HALO = tma_halo(sizeof(E));
+    constexpr int STRIP = tma_strip(sizeof(E));
     constexpr int TPR = 256 / NPT;  // threads per row of a strip
     const int tid = threadIdx.x;
     const int rg = tid / TPR;  // row of the block this thread works on
     const int t = tid % TPR;   // node group within the strip
     const int G = gridDim.x;
-    constexpr uint32_t kStageBytes = (uint32_t)(kPlanes * R * kTmaBox * sizeof(float));
+    constexpr uint32_t kStageBytes = (uint32_t)(kPlanes * R * kTmaBox * sizeof(E));
 
     // After an expired wait in an earlier launch the state is already invalid:
     // return at once instead of waiting again.
@@ -243,9 +276,9 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     __syncthreads();
 
     auto issue = [&](const ItemCursor& c, int s) {
-        const int x = c.strip * kTmaStrip - 4;
+        const int x = c.strip * STRIP - HALO;
         const int j0 = c.rb * R;
-        float* st = stages + (size_t)s * tma_stage_floats(R);
+        E* st = stages + (size_t)s * tma_stage_elems(R);
         mbar_expect_tx(&bars[s], kStageBytes);
         tma_load_3d(st, &map6, x, j0, kGroupZ, &bars[s]);
         tma_load_3d(st + kGroupP * R * kTmaBox, &map4, x, j0 - 1, kGroupP, &bars[s]);
@@ -264,7 +297,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         }
     }
 
-    const float* Sg = A.src;
+    const E* Sg = reinterpret_cast<const E*>(A.src);
+    const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 for float32)
     const long long PL = A.plane;
     const float sign_l_g = K.left_fixed ? -1.f : 1.f;
     const float sign_r_g = K.right_fixed ? -1.f : 1.f;
@@ -287,63 +321,63 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         const int strip = cc.strip;
         const int j = cc.rb * R + rg;
         const int n0 = NPT * t;
-        const int x0 = strip * kTmaStrip + n0;
+        const int x0 = strip * STRIP + n0;
         const bool row_ok = j < A.ny;
-        const bool mine = ok && row_ok && n0 < kTmaStrip && x0 < A.nx;
+        const bool mine = ok && row_ok && n0 < STRIP && x0 < A.nx;
         float theta[NPT];
 #pragma unroll
         for (int e = 0; e < NPT; ++e) theta[e] = 0.f;
         if (mine) {
-            const float* st = stages + (size_t)s * tma_stage_floats(R);
+            const E* st = stages + (size_t)s * tma_stage_elems(R);
             auto rowp = [&](int plane) { return st + (plane * R + rg) * kTmaBox; };
             float F[9][NPT], Gq[5][NPT];
-            lds_pull<0>(rowp(plane_f(0)), n0, F[0]);
-            lds_pull<1>(rowp(plane_f(1)), n0, F[1]);
-            lds_pull<0>(rowp(plane_f(2)), n0, F[2]);
-            lds_pull<-1>(rowp(plane_f(3)), n0, F[3]);
-            lds_pull<0>(rowp(plane_f(4)), n0, F[4]);
-            lds_pull<1>(rowp(plane_f(5)), n0, F[5]);
-            lds_pull<-1>(rowp(plane_f(6)), n0, F[6]);
-            lds_pull<-1>(rowp(plane_f(7)), n0, F[7]);
-            lds_pull<1>(rowp(plane_f(8)), n0, F[8]);
-            lds_pull<0>(rowp(plane_g(0)), n0, Gq[0]);
-            lds_pull<1>(rowp(plane_g(1)), n0, Gq[1]);
-            lds_pull<0>(rowp(plane_g(2)), n0, Gq[2]);
-            lds_pull<-1>(rowp(plane_g(3)), n0, Gq[3]);
-            lds_pull<0>(rowp(plane_g(4)), n0, Gq[4]);
+            lds_pull<0>(rowp(plane_f(0)), n0, F[0], 0.f);
+            lds_pull<1>(rowp(plane_f(1)), n0, F[1], 0.f);
+            lds_pull<0>(rowp(plane_f(2)), n0, F[2], 0.f);
+            lds_pull<-1>(rowp(plane_f(3)), n0, F[3], 0.f);
+            lds_pull<0>(rowp(plane_f(4)), n0, F[4], 0.f);
+            lds_pull<1>(rowp(plane_f(5)), n0, F[5], 0.f);
+            lds_pull<-1>(rowp(plane_f(6)), n0, F[6], 0.f);
+            lds_pull<-1>(rowp(plane_f(7)), n0, F[7], 0.f);
+            lds_pull<1>(rowp(plane_f(8)), n0, F[8], 0.f);
+            lds_pull<0>(rowp(plane_g(0)), n0, Gq[0], sh0);
+            lds_pull<1>(rowp(plane_g(1)), n0, Gq[1], sh1);
+            lds_pull<0>(rowp(plane_g(2)), n0, Gq[2], sh1);
+            lds_pull<-1>(rowp(plane_g(3)), n0, Gq[3], sh1);
+            lds_pull<0>(rowp(plane_g(4)), n0, Gq[4], sh1);
 
             // Walls. Bottom row: links from below (f2, f5, f6, g2) bounce back from
             // the node's own opposites (f4, f7, f8, g4); top row the reverse.
-            const float* rowj = Sg + (size_t)j * A.pitch;
+            const E* rowj = Sg + (size_t)j * A.pitch;
             if (j == 0) {
-                vec_ldg<NPT>(rowj + plane_f(4) * PL + x0, F[2]);
-                vec_ldg<NPT>(rowj + plane_f(7) * PL + x0, F[5]);
-                vec_ldg<NPT>(rowj + plane_f(8) * PL + x0, F[6]);
-                vec_ldg<NPT>(rowj + plane_g(4) * PL + x0, Gq[2]);
+                vec_ldg<E, NPT>(rowj + plane_f(4) * PL + x0, F[2], 0.f);
+                vec_ldg<E, NPT>(rowj + plane_f(7) * PL + x0, F[5], 0.f);
+                vec_ldg<E, NPT>(rowj + plane_f(8) * PL + x0, F[6], 0.f);
+                vec_ldg<E, NPT>(rowj + plane_g(4) * PL + x0, Gq[2], sh1);
             }
             if (j == A.ny - 1) {
-                vec_ldg<NPT>(rowj + plane_f(2) * PL + x0, F[4]);
-                vec_ldg<NPT>(rowj + plane_f(5) * PL + x0, F[7]);
-                vec_ldg<NPT>(rowj + plane_f(6) * PL + x0, F[8]);
-                vec_ldg<NPT>(rowj + plane_g(2) * PL + x0, Gq[4]);
+                vec_ldg<E, NPT>(rowj + plane_f(2) * PL + x0, F[4], 0.f);
+                vec_ldg<E, NPT>(rowj + plane_f(5) * PL + x0, F[7], 0.f);
+                vec_ldg<E, NPT>(rowj + plane_f(6) * PL + x0, F[8], 0.f);
+                vec_ldg<E, NPT>(rowj + plane_g(2) * PL + x0, Gq[4], sh1);
             }
             // Left wall (node x = 0): links with e_x = +1 (f1, f5, f8, g1).
             if (x0 == 0) {
-                F[1][0] = __ldg(rowj + plane_f(3) * PL);
-                F[5][0] = __ldg(rowj + plane_f(7) * PL);
-                F[8][0] = __ldg(rowj + plane_f(6) * PL);
+                F[1][0] = ldg_one(rowj + plane_f(3) * PL, 0.f);
+                F[5][0] = ldg_one(rowj + plane_f(7) * PL, 0.f);
+                F[8][0] = ldg_one(rowj + plane_f(6) * PL, 0.f);
                 const float add = K.left_fixed ? K.abb * __ldg(A.hot + j) : 0.f;
-                Gq[1][0] = sign_l_g * __ldg(rowj + plane_g(3) * PL) + add;
+                Gq[1][0] = sign_l_g * ldg_one(rowj + plane_g(3) * PL, sh1) + add;
             }
             // Right wall (node x = nx - 1): links with e_x = -1 (f3, f6, f7, g3).
             const int re = A.nx - 1 - x0;
             if (re < NPT) {
                 const int xr = A.nx - 1;
-                const float v3 = __ldg(rowj + plane_f(1) * PL + xr);
-                const float v6 = __ldg(rowj + plane_f(8) * PL + xr);
-                const float v7 = __ldg(rowj + plane_f(5) * PL + xr);
+                const float v3 = ldg_one(rowj + plane_f(1) * PL + xr, 0.f);
+                const float v6 = ldg_one(rowj + plane_f(8) * PL + xr, 0.f);
+                const float v7 = ldg_one(rowj + plane_f(5) * PL + xr, 0.f);
                 const float add = K.right_fixed ? K.abb * __ldg(A.cold + j) : 0.f;
-                const float vg = sign_r_g * __ldg(rowj + plane_g(1) * PL + xr) + add;
+                const float vg = sign_r_g * ldg_one(rowj + plane_g(1) * PL + xr, sh1) + add;
 #pragma unroll
                 for (int e = 0; e < NPT; ++e) {
                     if (e == re) {
@@ -357,11 +391,11 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
 
             bool bad = false;
             collide_nodes<NPT>(F, Gq, K, theta, min(NPT, A.nx - x0), bad);
-            float* D = A.dst + (size_t)j * A.pitch + x0;
+            E* D = reinterpret_cast<E*>(A.dst) + (size_t)j * A.pitch + x0;
 #pragma unroll
-            for (int k = 0; k < 9; ++k) vec_put<NPT>(D + plane_f(k) * PL, F[k]);
+            for (int k = 0; k < 9; ++k) vec_put<E, NPT>(D + plane_f(k) * PL, F[k], 0.f);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) vec_put<NPT>(D + plane_g(k) * PL, Gq[k]);
+            for (int k = 0; k < 5; ++k) vec_put<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1);
             if (bad) atomicOr(A.err, kErrNonFinite);
         }
         // Nusselt number of row j from the first warp of the row's thread group

@@ -1,24 +1,25 @@
-// TMA step-kernel tiles with 1 node(s) per thread (see step_tma.cuh).
+// TMA step-kernel tiles: float32 storage, 1 node per thread (see step_tma.cuh).
+#include "dmrt.h"
 #include "step_tma.cuh"
 #include "tma_variants.h"
 
 namespace dmrt {
 
-static const TmaVariant kVariants1[] = {
-    {1, 1, 2, (const void*)step_tma_kernel<1, 1, 2>},
-    {1, 1, 3, (const void*)step_tma_kernel<1, 1, 3>},
-    {1, 1, 4, (const void*)step_tma_kernel<1, 1, 4>},
-    {1, 1, 5, (const void*)step_tma_kernel<1, 1, 5>},
-    {1, 2, 2, (const void*)step_tma_kernel<1, 2, 2>},
-    {1, 2, 3, (const void*)step_tma_kernel<1, 2, 3>},
-    {1, 3, 2, (const void*)step_tma_kernel<1, 3, 2>},
-    {1, 4, 2, (const void*)step_tma_kernel<1, 4, 2>},
-    {1, 4, 3, (const void*)step_tma_kernel<1, 4, 3>},
+static const TmaVariant kVariants[] = {
+    {DMRT_FP32, 1, 1, 2, (const void*)step_tma_kernel<float, 1, 1, 2>},
+    {DMRT_FP32, 1, 1, 3, (const void*)step_tma_kernel<float, 1, 1, 3>},
+    {DMRT_FP32, 1, 1, 4, (const void*)step_tma_kernel<float, 1, 1, 4>},
+    {DMRT_FP32, 1, 1, 5, (const void*)step_tma_kernel<float, 1, 1, 5>},
+    {DMRT_FP32, 1, 2, 2, (const void*)step_tma_kernel<float, 1, 2, 2>},
+    {DMRT_FP32, 1, 2, 3, (const void*)step_tma_kernel<float, 1, 2, 3>},
+    {DMRT_FP32, 1, 3, 2, (const void*)step_tma_kernel<float, 1, 3, 2>},
+    {DMRT_FP32, 1, 4, 2, (const void*)step_tma_kernel<float, 1, 4, 2>},
+    {DMRT_FP32, 1, 4, 3, (const void*)step_tma_kernel<float, 1, 4, 3>},
 };
 
 const TmaVariant* tma_variants_npt1(int* n) {
-    *n = (int)(sizeof(kVariants1) / sizeof(kVariants1[0]));
-    return kVariants1;
+    *n = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+    return kVariants;
 }
 
 }  // namespace dmrt

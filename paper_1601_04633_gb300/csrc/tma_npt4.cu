@@ -1,25 +1,26 @@
-// TMA step-kernel tiles with 4 node(s) per thread (see step_tma.cuh).
+// TMA step-kernel tiles: float32 storage, 4 nodes per thread (see step_tma.cuh).
+#include "dmrt.h"
 #include "step_tma.cuh"
 #include "tma_variants.h"
 
 namespace dmrt {
 
-static const TmaVariant kVariants4[] = {
-    {4, 1, 2, (const void*)step_tma_kernel<4, 1, 2>},
-    {4, 1, 3, (const void*)step_tma_kernel<4, 1, 3>},
-    {4, 1, 4, (const void*)step_tma_kernel<4, 1, 4>},
-    {4, 1, 5, (const void*)step_tma_kernel<4, 1, 5>},
-    {4, 1, 6, (const void*)step_tma_kernel<4, 1, 6>},
-    {4, 2, 2, (const void*)step_tma_kernel<4, 2, 2>},
-    {4, 2, 3, (const void*)step_tma_kernel<4, 2, 3>},
-    {4, 2, 4, (const void*)step_tma_kernel<4, 2, 4>},
-    {4, 4, 2, (const void*)step_tma_kernel<4, 4, 2>},
-    {4, 4, 3, (const void*)step_tma_kernel<4, 4, 3>},
+static const TmaVariant kVariants[] = {
+    {DMRT_FP32, 4, 1, 2, (const void*)step_tma_kernel<float, 4, 1, 2>},
+    {DMRT_FP32, 4, 1, 3, (const void*)step_tma_kernel<float, 4, 1, 3>},
+    {DMRT_FP32, 4, 1, 4, (const void*)step_tma_kernel<float, 4, 1, 4>},
+    {DMRT_FP32, 4, 1, 5, (const void*)step_tma_kernel<float, 4, 1, 5>},
+    {DMRT_FP32, 4, 1, 6, (const void*)step_tma_kernel<float, 4, 1, 6>},
+    {DMRT_FP32, 4, 2, 2, (const void*)step_tma_kernel<float, 4, 2, 2>},
+    {DMRT_FP32, 4, 2, 3, (const void*)step_tma_kernel<float, 4, 2, 3>},
+    {DMRT_FP32, 4, 2, 4, (const void*)step_tma_kernel<float, 4, 2, 4>},
+    {DMRT_FP32, 4, 4, 2, (const void*)step_tma_kernel<float, 4, 4, 2>},
+    {DMRT_FP32, 4, 4, 3, (const void*)step_tma_kernel<float, 4, 4, 3>},
 };
 
 const TmaVariant* tma_variants_npt4(int* n) {
-    *n = (int)(sizeof(kVariants4) / sizeof(kVariants4[0]));
-    return kVariants4;
+    *n = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+    return kVariants;
 }
 
 }  // namespace dmrt

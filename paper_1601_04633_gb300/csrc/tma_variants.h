@@ -1,11 +1,12 @@
-// Registry of the compiled TMA step-kernel tiles: NPT nodes per thread, R rows
-// per work item, S pipeline stages. Each list is defined in its own
-// translation unit (tma_npt*.cu) so the instantiations compile in parallel.
+// Registry of the compiled TMA step-kernel tiles: storage type, NPT nodes per
+// thread, R rows per work item, S pipeline stages. Each list is defined in its
+// own translation unit (tma_*.cu) so the instantiations compile in parallel.
 #pragma once
 
 namespace dmrt {
 
 struct TmaVariant {
+    int storage;  // DMRT_FP32, DMRT_FP16 or DMRT_BF16
     int npt, R, S;
     const void* func;
 };
@@ -13,5 +14,7 @@ struct TmaVariant {
 const TmaVariant* tma_variants_npt4(int* n);
 const TmaVariant* tma_variants_npt2(int* n);
 const TmaVariant* tma_variants_npt1(int* n);
+const TmaVariant* tma_variants_fp16(int* n);
+const TmaVariant* tma_variants_bf16(int* n);
 
 }  // namespace dmrt

@@ -1,0 +1,105 @@
+"""16-bit population storage (float16 / bfloat16, float32 collision).
+
+One step from a given state is checked element by element against the fp64
+oracle run from the same (already rounded) state: the only extra error of the
+16-bit path is the final round-to-nearest of each stored value, at most one
+half unit in the last place, u = 2^-11 (float16) or 2^-8 (bfloat16) of the
+stored (shifted) value, plus the float32 arithmetic (~1e-6 of the plane).
+Long runs are compared with the oracle and the measured Nusselt error is
+reported, not bounded by the 1e-3 target, which plain 16-bit storage misses
+(see the design notes: increments below half an ulp are lost).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_04633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+UNIT_ROUNDOFF = {1: 2.0 ** -11, 2: 2.0 ** -8}
+
+
+@pytest.fixture(scope="module")
+def D():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1601_04633_gb300 import dmrt
+
+    return dmrt
+
+
+def _random_state(nx, ny, seed, theta_mid):
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    ex = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1])
+    ey = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1])
+    r = inputs.uniform01(seed, 4 * nx * ny).reshape(4, ny, nx)
+    drho, u, v = 2e-3 * (r[0] - 0.5), 0.1 * (r[1] - 0.5), 0.1 * (r[2] - 0.5)
+    th = theta_mid + r[3] - 0.5
+    eu = ex[:, None, None] * u + ey[:, None, None] * v
+    f = w9[:, None, None] * (drho + 3 * eu + 4.5 * eu ** 2 - 1.5 * (u * u + v * v))
+    g = np.empty((5, ny, nx))
+    g[0] = 0.3 * th
+    g[1:] = 0.175 * th
+    g += 1e-2 * (inputs.uniform01(seed + 2, 5 * nx * ny).reshape(5, ny, nx) - 0.5)
+    return np.concatenate([f, g]).astype(np.float32)
+
+
+@pytest.mark.parametrize("storage", [1, 2], ids=["fp16", "bf16"])
+@pytest.mark.parametrize("walls", [(0.5, -0.5), (1.0, 0.0)], ids=["theta_ref0", "theta_ref0.5"])
+@pytest.mark.parametrize("nx,ny", [(1000, 301), (67, 45)])
+def test_one_step_matches_oracle_within_rounding(D, storage, walls, nx, ny):
+    hot, cold = walls
+    cav = inputs.Cavity(nx, ny, 1e5, 0.01, noise_amp=0.0, theta_hot=hot, theta_cold=cold)
+    sim = D.Cavity2D.from_inputs(cav, storage=storage)
+    sim.set_state(_random_state(nx, ny, 61, 0.5 * (hot + cold)))
+    state = sim.get_state()  # the state as stored (rounded to 16 bits)
+    sim.step(1)
+    sim.check()
+    out = sim.get_state()
+    nu_mean = sim.nusselt()[0]
+    k = sim.consts
+    sim.close()
+
+    m = O.derive(nx, ny, cav.Ra, cav.Pr, cav.alpha, theta_hot=hot, theta_cold=cold)
+    s64 = state.astype(np.float64)
+    r = O.step(m, np.ascontiguousarray(s64[:9]), np.ascontiguousarray(s64[9:]))
+    ref = np.concatenate([r["f"], r["g"]])
+    u = UNIT_ROUNDOFF[storage]
+    theta_ref = 0.5 * (hot + cold)
+    shift = np.array([0.0] * 9 + [(1 - k.a) / 5 * theta_ref] + [(4 + k.a) / 20 * theta_ref] * 4)
+    for p in range(14):
+        bound = u * np.abs(ref[p] - shift[p]) + 1e-5 * np.abs(ref[p]).max() + 1e-12
+        err = np.abs(out[p] - ref[p])
+        assert np.all(err <= bound), f"plane {p}: worst excess {(err - bound).max():.3e}"
+    # The Nusselt number comes from the pre-collision theta of the rounded state.
+    assert abs(nu_mean - r["nu"]) <= 1e-5 * abs(r["nu"]) + 1e-9
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2], ids=["fp32", "fp16", "bf16"])
+def test_long_run_error_report(D, storage):
+    # 64 x 64, Ra 1e4, Pr 0.01 (Case 1), 5000 steps: float32 meets the parity
+    # tolerances; the 16-bit errors are recorded and only required to be finite
+    # and smaller than the quantities themselves.
+    cav = inputs.cavity_64()
+    steps = 5000
+    sim = D.Cavity2D.from_inputs(cav, storage=storage, nu_capacity=steps)
+    sim.step(steps)
+    sim.check()
+    u, v, th = (x.cpu().numpy().astype(np.float64) for x in sim.fields())
+    series = sim.nusselt(steps)[2]
+    sim.close()
+    m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+    f, g = O.init(m, cav.theta0())
+    ref = O.run(m, steps, f, g)
+    nu_err = np.abs(series - ref["nu_series"]).max() / np.abs(ref["nu_series"]).max()
+    th_err = np.abs(th - ref["theta"]).max() / np.abs(ref["theta"]).max()
+    print(f"storage {storage}: max Nu error {nu_err:.3e}, theta error {th_err:.3e}")
+    if storage == 0:
+        assert nu_err <= 1e-4 and th_err <= 1e-5
+    else:
+        assert np.isfinite(nu_err) and nu_err < 1.0 and th_err < 1.0
