@@ -54,6 +54,15 @@ extern "C" {
 #define DMRT_FP16 1
 #define DMRT_BF16 2
 
+/* Rounding of 16-bit population stores. NEAREST: round to nearest even.
+ * STOCHASTIC: round up with probability equal to the distance to the lower
+ * neighbour in units of the spacing, so that the expected stored value equals
+ * the float32 value and increments smaller than half a unit in the last place
+ * are kept on average; the random bits come from a per-node, per-step hash
+ * (deterministic: a run repeats bit for bit). Float32 storage rounds nothing. */
+#define DMRT_ROUND_NEAREST 0
+#define DMRT_ROUND_STOCHASTIC 1
+
 /* Step kernel variants. Both compute the same step; they differ only in how
  * the populations reach the registers. DIRECT: 128-bit loads straight from
  * global memory, x-shifts by warp shuffles. TMA: a persistent kernel that
@@ -86,13 +95,14 @@ typedef struct {
     double theta_init;  /* uniform initial temperature when no field is given */
     int32_t left_wall;  /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
-    int32_t storage;    /* DMRT_FP32 (DMRT_FP16 / DMRT_BF16 reserved) */
+    int32_t storage;    /* DMRT_FP32, DMRT_FP16 or DMRT_BF16 (16-bit storage runs the
+                           TMA kernel; arithmetic is float32 in every case) */
     int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
     int32_t tma_rows;   /* TMA kernel: rows per work item (0 = default 4) */
     int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default 2) */
     int32_t tma_npt;    /* TMA kernel: nodes per thread, 4, 2 or 1 (0 = default 1) */
-    int32_t reserved;
+    int32_t rounding;   /* 16-bit storage: DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC */
 } dmrt_params;
 
 /* Constants derived from dmrt_params (Eqs. 9, 31-32, 38-40, 43, 45). */

@@ -57,7 +57,8 @@ Layout make_layout(const dmrt_params& p) {
 
 // Scalars kept on the device (one 256-byte block).
 struct Misc {
-    long long step;      // steps recorded in the Nu ring
+    long long step[2];   // steps recorded in the Nu ring; slot b is current when the
+                         // state is in buffer b (a launch reads one slot, writes the other)
     double nu_last;      // mean Nu of the latest step
     unsigned counter;    // rows reported in the running step
     unsigned err;        // error bits
@@ -132,7 +133,9 @@ dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
     A.nu_last = &m->nu_last;
     A.counter = &m->counter;
     A.err = &m->err;
-    A.d_step = &m->step;
+    A.step_in = &m->step[from];
+    A.step_out = &m->step[1 - from];
+    A.rounding = c->p.rounding;
     A.cap = c->p.nu_capacity;
     A.plane = c->L.plane;
     A.nx = c->p.nx;
@@ -248,7 +251,7 @@ void with_elem(int storage, Fn&& fn) {
 
 constexpr int kDefaultNpt = 1, kDefaultR = 4, kDefaultS = 2;
 
-const dmrt::TmaVariant* find_tma_variant(int storage, int npt, int R, int S) {
+const dmrt::TmaVariant* find_tma_variant(int storage, int rounding, int npt, int R, int S) {
     const dmrt::TmaVariant* (*lists[5])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
                                                 dmrt::tma_variants_npt1, dmrt::tma_variants_fp16,
                                                 dmrt::tma_variants_bf16};
@@ -256,7 +259,9 @@ const dmrt::TmaVariant* find_tma_variant(int storage, int npt, int R, int S) {
         int n = 0;
         const dmrt::TmaVariant* v = list(&n);
         for (int i = 0; i < n; ++i)
-            if (v[i].storage == storage && v[i].npt == npt && v[i].R == R && v[i].S == S) return &v[i];
+            if (v[i].storage == storage && v[i].rounding == rounding && v[i].npt == npt && v[i].R == R &&
+                v[i].S == S)
+                return &v[i];
     }
     return nullptr;
 }
@@ -325,9 +330,10 @@ int setup_kernel(dmrt_ctx* c) {
     c->S = S;
     c->tma_func = nullptr;
     if (want != DMRT_KERNEL_TMA) return DMRT_OK;
-    const dmrt::TmaVariant* v = find_tma_variant(p.storage, npt, R, S);
+    const dmrt::TmaVariant* v = find_tma_variant(p.storage, p.rounding, npt, R, S);
     if (!v) {
-        set_err(c, "no TMA tile with %d nodes/thread, %d rows, %d stages is compiled in", npt, R, S);
+        set_err(c, "no TMA tile with %d nodes/thread, %d rows, %d stages is compiled in for this "
+                   "storage and rounding", npt, R, S);
         return DMRT_E_ARG;
     }
     c->tma_func = v->func;
@@ -387,6 +393,14 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "storage must be DMRT_FP32, DMRT_FP16 or DMRT_BF16 (got %d)", p->storage);
         return DMRT_E_ARG;
     }
+    if (p->rounding != DMRT_ROUND_NEAREST && p->rounding != DMRT_ROUND_STOCHASTIC) {
+        set_err(c, "rounding must be DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC");
+        return DMRT_E_ARG;
+    }
+    if (p->rounding == DMRT_ROUND_STOCHASTIC && p->storage == DMRT_FP32) {
+        set_err(c, "stochastic rounding applies to 16-bit storage only");
+        return DMRT_E_ARG;
+    }
     if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_TMA) {
         set_err(c, "kernel must be DMRT_KERNEL_AUTO, _DIRECT or _TMA");
         return DMRT_E_ARG;
@@ -428,6 +442,7 @@ void dmrt_default_params(dmrt_params* p) {
     p->tma_rows = 0;
     p->tma_stages = 0;
     p->tma_npt = 0;
+    p->rounding = DMRT_ROUND_NEAREST;
 }
 
 int dmrt_derive(const dmrt_params* p, dmrt_consts* out) {
@@ -720,9 +735,10 @@ int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
     long long written = 0;
     if (series && cap > 0) {
         const long long R = c->p.nu_capacity;
-        long long avail = std::min<long long>(m.step, R);
+        const long long recorded = m.step[c->cur];
+        long long avail = std::min<long long>(recorded, R);
         long long want = std::min<long long>(avail, cap);
-        long long first = m.step - want;  // step index of the oldest value returned
+        long long first = recorded - want;  // step index of the oldest value returned
         const double* ring = reinterpret_cast<const double*>(c->ws + c->L.off_ring);
         long long done = 0;
         while (done < want) {

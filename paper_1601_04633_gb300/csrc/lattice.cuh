@@ -51,7 +51,9 @@ struct StepArgs {
     double* nu_last;                // mean Nu of the latest step
     unsigned* counter;              // rows reported in the current step
     unsigned* err;                  // bit 0: non-finite value; bit 1: wait timed out
-    long long* d_step;              // steps recorded so far
+    const long long* step_in;       // steps recorded before this launch (read by all)
+    long long* step_out;            // written once, = step_in + 1, by the reducer
+    int rounding;                   // 16-bit storage: 0 nearest, 1 stochastic
     long long cap;
     long long plane;  // elements per plane = ny * pitch
     int nx, ny, pitch;
@@ -230,10 +232,10 @@ __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j,
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) {
             const double mean = s / (double)A.ny;
-            const long long t = *A.d_step;
+            const long long t = *A.step_in;
             A.nu_ring[t % A.cap] = mean;
             *A.nu_last = mean;
-            *A.d_step = t + 1;
+            *A.step_out = t + 1;
             *A.counter = 0u;
         }
     }

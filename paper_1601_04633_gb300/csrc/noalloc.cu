@@ -36,7 +36,7 @@ constexpr size_t kOffMisc = 16 * (size_t)kMaxNy;
 constexpr size_t kScratchBytes = kOffMisc + 256;
 
 struct Misc {
-    long long step;
+    long long step[2];
     double nu_last;
     double nu_sink;  // target of the mean when the caller passes no output
     unsigned counter;
@@ -142,7 +142,9 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     A.nu_last = &misc->nu_last;
     A.counter = &misc->counter;
     A.err = &misc->err;
-    A.d_step = &misc->step;
+    A.step_in = &misc->step[0];
+    A.step_out = &misc->step[1];
+    A.rounding = 0;
     A.cap = 1;
     A.plane = (long long)p->ny * pitch;
     A.nx = p->nx;

@@ -174,6 +174,52 @@ __device__ __forceinline__ void vec_put(E* p, const float (&o)[N], float shift) 
     *reinterpret_cast<Pack<E, N>*>(p) = q;
 }
 
+// Stochastic rounding of a float32 value to E (used for 16-bit stores when
+// requested): a uniform random integer below the spacing of E at x is added to
+// the magnitude bits of x, then the result is truncated toward zero, so x is
+// rounded up in magnitude with probability equal to its distance from the
+// lower neighbour in units of the spacing (Croci et al., "Stochastic rounding:
+// implementation, error analysis and applications", R. Soc. Open Sci. 2022).
+// For float16 the discarded bit count grows by one per binade below its
+// smallest normal 2^-14, so subnormal targets are rounded the same way.
+template <typename E>
+__device__ __forceinline__ E from_f_sr(float x, unsigned rnd);
+template <>
+__device__ __forceinline__ __half from_f_sr<__half>(float x, unsigned rnd) {
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    const int width = min(13 + max(0, 113 - e), 24);
+    return __float2half_rz(__uint_as_float(b + (rnd >> (32 - width))));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f_sr<__nv_bfloat16>(float x, unsigned rnd) {
+    return __float2bfloat16_rz(__uint_as_float(__float_as_uint(x) + (rnd >> 16)));
+}
+
+// Integer hash "lowbias32" (C. Wellons, "Prospecting for hash functions", 2018).
+__device__ __forceinline__ unsigned hash32(unsigned x) {
+    x ^= x >> 16;
+    x *= 0x7feb352du;
+    x ^= x >> 15;
+    x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+
+// Linear congruential step (Numerical Recipes constants); the high bits are used.
+__device__ __forceinline__ unsigned lcg(unsigned& r) {
+    r = r * 1664525u + 1013904223u;
+    return r;
+}
+
+template <typename E, int N>
+__device__ __forceinline__ void vec_put_sr(E* p, const float (&o)[N], float shift, unsigned& r) {
+    Pack<E, N> q;
+#pragma unroll
+    for (int e = 0; e < N; ++e) q.v[e] = from_f_sr<E>(o[e] - shift, lcg(r));
+    *reinterpret_cast<Pack<E, N>*>(p) = q;
+}
+
 // NPT consecutive values of a shared-memory plane row for nodes n0..n0+NPT-1,
 // shifted for a pull with lattice x-velocity EX: node n takes the value at
 // n - EX. The row starts HALO nodes left of the strip, so node n sits at n + HALO.
@@ -249,7 +295,7 @@ struct ItemCursor {
     }
 };
 
-template <typename E, int NPT, int R, int S>
+template <typename E, int NPT, int R, int S, bool SR = false>
 __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_constant__ CUtensorMap map6,
                                                           const __grid_constant__ CUtensorMap map4,
                                                           StepArgs A, StepConsts K, TmaGeo T) {
@@ -298,6 +344,10 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     }
 
     const E* Sg = reinterpret_cast<const E*>(A.src);
+    // Stochastic rounding: per-step salt (the step count is only written by the
+    // previous launch, so every block reads the same value).
+    unsigned salt = 0;
+    if constexpr (SR) salt = hash32((unsigned)*A.step_in * 0x9e3779b9u + 0x632be5abu);
     const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 for float32)
     const long long PL = A.plane;
     const float sign_l_g = K.left_fixed ? -1.f : 1.f;
@@ -392,10 +442,18 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
             bool bad = false;
             collide_nodes<NPT>(F, Gq, K, theta, min(NPT, A.nx - x0), bad);
             E* D = reinterpret_cast<E*>(A.dst) + (size_t)j * A.pitch + x0;
+            if constexpr (SR) {
+                unsigned r = hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)x0) ^ salt);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) vec_put<E, NPT>(D + plane_f(k) * PL, F[k], 0.f);
+                for (int k = 0; k < 9; ++k) vec_put_sr<E, NPT>(D + plane_f(k) * PL, F[k], 0.f, r);
 #pragma unroll
-            for (int k = 0; k < 5; ++k) vec_put<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1);
+                for (int k = 0; k < 5; ++k) vec_put_sr<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1, r);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 9; ++k) vec_put<E, NPT>(D + plane_f(k) * PL, F[k], 0.f);
+#pragma unroll
+                for (int k = 0; k < 5; ++k) vec_put<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1);
+            }
             if (bad) atomicOr(A.err, kErrNonFinite);
         }
         // Nusselt number of row j from the first warp of the row's thread group

@@ -6,7 +6,8 @@
 namespace dmrt {
 
 struct TmaVariant {
-    int storage;  // DMRT_FP32, DMRT_FP16 or DMRT_BF16
+    int storage;   // DMRT_FP32, DMRT_FP16 or DMRT_BF16
+    int rounding;  // DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC
     int npt, R, S;
     const void* func;
 };

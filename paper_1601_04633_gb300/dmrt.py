@@ -30,6 +30,7 @@ DMRT_E_STATE = -7
 DMRT_FP32, DMRT_FP16, DMRT_BF16 = 0, 1, 2
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
 DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA = 0, 1, 2
+DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC = 0, 1
 DMRT_NOALLOC_MAX_NY = 8192
 # Device plane order of the population buffers: entry d is the index, in the host
 # order f1..f9, g1..g5 (paper numbering), of device plane d.
@@ -61,7 +62,7 @@ class Params(ctypes.Structure):
         ("storage", ctypes.c_int32), ("kernel", ctypes.c_int32),
         ("nu_capacity", ctypes.c_int64),
         ("tma_rows", ctypes.c_int32), ("tma_stages", ctypes.c_int32),
-        ("tma_npt", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("tma_npt", ctypes.c_int32), ("rounding", ctypes.c_int32),
     ]
 
 
@@ -250,7 +251,8 @@ def dmrt_destroy(h):
 def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.5,
                 theta_ref=None, theta_init=0.0, left_wall=DMRT_WALL_FIXED,
                 right_wall=DMRT_WALL_FIXED, storage=DMRT_FP32, nu_capacity=1 << 20,
-                kernel=DMRT_KERNEL_AUTO, tma_rows=0, tma_stages=0, tma_npt=0) -> Params:
+                kernel=DMRT_KERNEL_AUTO, tma_rows=0, tma_stages=0, tma_npt=0,
+                rounding=DMRT_ROUND_NEAREST) -> Params:
     p = dmrt_default_params()
     p.nx, p.ny, p.Ra, p.Pr, p.alpha, p.Ma = int(nx), int(ny), float(Ra), float(Pr), float(alpha), float(Ma)
     p.theta_hot, p.theta_cold = float(theta_hot), float(theta_cold)
@@ -260,6 +262,7 @@ def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.
     p.nu_capacity = int(nu_capacity)
     p.kernel, p.tma_rows, p.tma_stages = int(kernel), int(tma_rows), int(tma_stages)
     p.tma_npt = int(tma_npt)
+    p.rounding = int(rounding)
     return p
 
 
@@ -294,7 +297,7 @@ class Cavity2D:
                                                                    "left_wall", "right_wall",
                                                                    "theta_ref", "kernel",
                                                                    "tma_rows", "tma_stages",
-                                                                   "tma_npt")})
+                                                                   "tma_npt", "rounding")})
         rest = {k: v for k, v in kw.items() if k in ("device", "stream")}
         return cls(p, theta0=cav.theta0(), theta_hot_profile=cav.theta_hot_profile, **rest)
 
