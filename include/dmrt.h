@@ -244,6 +244,56 @@ const char* dmrt_last_error(const dmrt_ctx* c);
 /* Release the context (not the caller's workspace). Synchronises. NULL is a no-op. */
 void dmrt_destroy(dmrt_ctx* c);
 
+/* ---- Batched sweep: many independent cavities per launch ----------------------
+ *
+ * Steps n independent side-heated cavities (any sizes and parameters, float32
+ * storage) with one launch per time step of a persistent TMA kernel over the
+ * concatenated work items of all cavities, replayed from CUDA graphs. Each
+ * member is also an ordinary context (dmrt_batch_context), so dmrt_fields,
+ * dmrt_nusselt, dmrt_get_state, ... work on it, and stepping the members one
+ * by one with dmrt_step is the sequential alternative. The paper's four cases
+ * (Table 1) are such a sweep over (Ra, Pr). */
+typedef struct dmrt_batch dmrt_batch;
+
+/* Tile of the batched kernel: nodes per thread, rows per item, pipeline stages
+ * (0 = default 1, 4, 2), and steps per CUDA graph (0 = 64; must be even).
+ * Compiled tiles (npt, R, S): (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,2,2) (2,4,2)
+ * (4,1,4) (4,4,2). */
+typedef struct {
+    int32_t tma_npt, tma_rows, tma_stages, graph_steps;
+} dmrt_batch_opts;
+
+/* Device workspace for a batch of n cavities (the members' workspaces plus the
+ * kernel's tables). Errors as dmrt_derive for any member; DMRT_E_ARG for n < 1
+ * or 16-bit storage. */
+int dmrt_batch_workspace_size(const dmrt_params* arr, int32_t n, size_t* bytes);
+
+/* Create a batch. arr: n parameter sets; theta0: NULL, or n host pointers (each
+ * NULL or an [ny][nx] initial temperature field); opts: NULL for defaults;
+ * workspace: 256-byte aligned device memory of dmrt_batch_workspace_size()
+ * bytes, kept alive by the caller until dmrt_batch_destroy. Synchronises. */
+int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* theta0,
+                      const dmrt_batch_opts* opts, void* workspace, size_t workspace_bytes,
+                      void* stream, dmrt_batch** out);
+
+/* Enqueue nsteps time steps of every member. DMRT_E_STATE if a member was
+ * stepped on its own by an odd number of steps since the last batch step. */
+int dmrt_batch_step(dmrt_batch* b, int64_t nsteps);
+
+/* Synchronise; DMRT_E_TIMEOUT or DMRT_E_DIVERGED (first member concerned). */
+int dmrt_batch_check(dmrt_batch* b);
+
+int32_t dmrt_batch_size(const dmrt_batch* b);
+
+/* Member i as a context (borrowed: do not destroy it), or NULL. */
+dmrt_ctx* dmrt_batch_context(dmrt_batch* b, int32_t i);
+
+int dmrt_batch_get_launch(const dmrt_batch* b, dmrt_launch* out);
+const char* dmrt_batch_last_error(const dmrt_batch* b);
+
+/* Release the batch and its member contexts (not the workspace). */
+void dmrt_batch_destroy(dmrt_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

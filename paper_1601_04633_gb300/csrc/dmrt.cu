@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "dmrt.h"
 #include "step_direct.cuh"
@@ -280,7 +281,7 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 }
 
 // 3-D view {pitch, ny, 14} of one population buffer with boxes {256, R, planes}.
-int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes) {
+int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes, int rows, int width = dmrt::kTmaBox) {
     auto enc = tensor_map_encoder();
     if (!enc) {
         set_err(c, "cuTensorMapEncodeTiled is not available from the driver");
@@ -292,7 +293,7 @@ int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes) {
     const CUtensorMapDataType dt = c->p.storage == DMRT_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : c->p.storage == DMRT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                                : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    cuuint32_t box[3] = {(cuuint32_t)dmrt::kTmaBox, (cuuint32_t)c->R, (cuuint32_t)planes};
+    cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(m, dt, 3, base, dims, strides, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -360,9 +361,9 @@ int setup_kernel(dmrt_ctx* c) {
     const long long items = (long long)c->geo.n_strips * c->geo.n_rowblocks;
     c->tma_grid = (int)std::min<long long>(items, (long long)sms * per_sm);
     for (int b = 0; b < 2; ++b) {
-        int rc = encode_map(c, &c->map6[b], buf(c, b), 6);
+        int rc = encode_map(c, &c->map6[b], buf(c, b), 6, c->R);
         if (rc) return rc;
-        rc = encode_map(c, &c->map4[b], buf(c, b), 4);
+        rc = encode_map(c, &c->map4[b], buf(c, b), 4, c->R);
         if (rc) return rc;
     }
     return DMRT_OK;
@@ -884,6 +885,363 @@ void dmrt_destroy(dmrt_ctx* c) {
     for (int i = 0; i < 2; ++i)
         if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
     delete c;
+}
+
+}  // extern "C"
+
+// ---- batched sweep ------------------------------------------------------------
+
+struct dmrt_batch {
+    int n;
+    std::vector<dmrt_ctx*> sub;
+    char* ws;
+    cudaStream_t stream;
+    dmrt::BatchCavity* d_cav;
+    CUtensorMap* d_maps;
+    unsigned* d_err;
+    int total_items;
+    int npt, R, S, grid, block;
+    size_t smem;
+    const void* func;
+    int parity;
+    long long t;
+    cudaGraphExec_t graph[2];
+    int graph_len;
+    char err[256];
+};
+
+namespace {
+
+struct BatchLayout {
+    std::vector<size_t> off, bytes;
+    size_t off_cav, off_maps, off_err, total;
+};
+
+int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
+    if (!arr || n < 1 || n > 65536) {
+        set_err(nullptr, "batch needs 1 <= n <= 65536 cavities");
+        return DMRT_E_ARG;
+    }
+    L->off.resize(n);
+    L->bytes.resize(n);
+    size_t o = 0;
+    for (int i = 0; i < n; ++i) {
+        int rc = validate(&arr[i], nullptr);
+        if (rc) return rc;
+        if (arr[i].storage != DMRT_FP32) {
+            set_err(nullptr, "batched sweep: cavity %d: float32 storage only", i);
+            return DMRT_E_ARG;
+        }
+        L->off[i] = o;
+        L->bytes[i] = make_layout(arr[i]).total;
+        o += align256(L->bytes[i]);
+    }
+    L->off_cav = o;
+    o += align256((size_t)n * sizeof(dmrt::BatchCavity));
+    L->off_maps = o;
+    o += align256((size_t)n * 4 * sizeof(CUtensorMap));
+    L->off_err = o;
+    o += 256;
+    L->total = o;
+    return DMRT_OK;
+}
+
+void batch_set_err(dmrt_batch* b, const char* fmt, ...) {
+    char* dst = b ? b->err : g_create_error;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(dst, 256, fmt, ap);
+    va_end(ap);
+}
+
+int batch_cuda_fail(dmrt_batch* b, cudaError_t e, const char* what) {
+    batch_set_err(b, "%s: %s", what, cudaGetErrorString(e));
+    return DMRT_E_CUDA;
+}
+
+#define BCK(call, what)                                              \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return batch_cuda_fail(b, e_, what);  \
+    } while (0)
+
+int batch_launch(dmrt_batch* b, int parity) {
+    void* params[6] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &parity, &b->d_err};
+    BCK(cudaLaunchKernel(b->func, dim3(b->grid), dim3(b->block), params, b->smem, b->stream),
+        "batch step launch");
+    return DMRT_OK;
+}
+
+int batch_build_graph(dmrt_batch* b, int from) {
+    cudaGraph_t g;
+    BCK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    cudaGraphNode_t prev = nullptr;
+    int par[2] = {from, 1 - from};
+    for (int i = 0; i < b->graph_len; ++i) {
+        cudaKernelNodeParams kp = {};
+        void* params[6] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &par[i & 1], &b->d_err};
+        kp.func = const_cast<void*>(b->func);
+        kp.gridDim = dim3(b->grid);
+        kp.blockDim = dim3(b->block);
+        kp.sharedMemBytes = (unsigned)b->smem;
+        kp.kernelParams = params;
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return batch_cuda_fail(b, e, "cudaGraphAddKernelNode");
+        }
+        prev = node;
+    }
+    cudaError_t e = cudaGraphInstantiate(&b->graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return batch_cuda_fail(b, e, "cudaGraphInstantiate");
+    return DMRT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmrt_batch_workspace_size(const dmrt_params* arr, int32_t n, size_t* bytes) {
+    BatchLayout L;
+    int rc = batch_layout(arr, n, &L);
+    if (rc) return rc;
+    if (!bytes) return DMRT_E_ARG;
+    *bytes = L.total;
+    return DMRT_OK;
+}
+
+int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* theta0,
+                      const dmrt_batch_opts* opts, void* workspace, size_t workspace_bytes,
+                      void* stream, dmrt_batch** out) {
+    if (!out) {
+        set_err(nullptr, "out is NULL");
+        return DMRT_E_ARG;
+    }
+    *out = nullptr;
+    BatchLayout L;
+    int rc = batch_layout(arr, n, &L);
+    if (rc) return rc;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
+        set_err(nullptr, "workspace must be a 256-byte aligned device pointer");
+        return DMRT_E_ARG;
+    }
+    if (workspace_bytes < L.total) {
+        set_err(nullptr, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+        return DMRT_E_SPACE;
+    }
+    const int npt = opts && opts->tma_npt > 0 ? opts->tma_npt : 1;
+    const int R = opts && opts->tma_rows > 0 ? opts->tma_rows : 4;
+    const int S = opts && opts->tma_stages > 0 ? opts->tma_stages : 2;
+    const int glen = opts && opts->graph_steps > 0 ? opts->graph_steps : 64;
+    if (glen % 2) {
+        set_err(nullptr, "graph_steps must be even");
+        return DMRT_E_ARG;
+    }
+    int nv = 0;
+    const dmrt::TmaVariant* vars = dmrt::tma_variants_batch(&nv);
+    const void* func = nullptr;
+    for (int i = 0; i < nv; ++i)
+        if (vars[i].npt == npt && vars[i].R == R && vars[i].S == S) func = vars[i].func;
+    if (!func) {
+        set_err(nullptr, "no batched tile with %d nodes/thread, %d rows, %d stages is compiled in", npt, R, S);
+        return DMRT_E_ARG;
+    }
+    dmrt_batch* b = new (std::nothrow) dmrt_batch();
+    if (!b) {
+        set_err(nullptr, "out of host memory");
+        return DMRT_E_SPACE;
+    }
+    b->n = n;
+    b->ws = static_cast<char*>(workspace);
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->npt = npt;
+    b->R = R;
+    b->S = S;
+    b->func = func;
+    b->parity = 0;
+    b->t = 0;
+    b->graph[0] = b->graph[1] = nullptr;
+    b->graph_len = glen;
+    b->err[0] = 0;
+    auto fail = [&](int code) {
+        std::snprintf(g_create_error, sizeof g_create_error, "%s", b->err[0] ? b->err : g_create_error);
+        for (dmrt_ctx* c : b->sub) dmrt_destroy(c);
+        delete b;
+        return code;
+    };
+    // Members: ordinary contexts on slices of the workspace.
+    for (int i = 0; i < n; ++i) {
+        dmrt_ctx* c = nullptr;
+        rc = dmrt_create(&arr[i], theta0 ? theta0[i] : nullptr, b->ws + L.off[i], L.bytes[i], stream, &c);
+        if (rc) {
+            char msg[256];
+            std::snprintf(msg, sizeof msg, "cavity %d: %.200s", i, g_create_error);
+            std::snprintf(b->err, sizeof b->err, "%s", msg);
+            return fail(rc);
+        }
+        b->sub.push_back(c);
+    }
+    // Device tables: per-cavity arguments and tensor maps (boxes of R rows).
+    std::vector<dmrt::BatchCavity> cav(n);
+    std::vector<CUtensorMap> maps((size_t)n * 4);
+    long long items = 0;
+    const int block = R * (256 / npt);
+    const int quantum = 32 * npt;                          // strip widths keep warps in one row
+    const int w_max = (dmrt::kTmaBox - 8) / quantum * quantum;
+    for (int i = 0; i < n; ++i) {
+        dmrt_ctx* c = b->sub[i];
+        std::memset(&cav[i], 0, sizeof cav[i]);
+        cav[i].args[0] = step_args(c, 0);
+        cav[i].args[1] = step_args(c, 1);
+        cav[i].K = c->sc;
+        const int ns = (c->p.nx + w_max - 1) / w_max;
+        const int W = ((c->p.nx + ns - 1) / ns + quantum - 1) / quantum * quantum;
+        const int WB = W + 8;
+        const int tpr = W / npt;
+        // Rows per item: bounded by the block's threads and by the stage, which
+        // must also hold up to 2 x 124 bytes of 128-byte alignment padding.
+        const int stage_elems = dmrt::tma_stage_elems(R);
+        int RC = std::max(1, std::min(block / tpr, R * dmrt::kTmaBox / WB));
+        auto round128 = [](int elems) { return (elems * 4 + 127) / 128 * 128 / 4; };
+        while (RC > 1 && round128(6 * RC * WB) + round128(4 * RC * WB) + 4 * RC * WB > stage_elems) --RC;
+        cav[i].offP = round128(6 * RC * WB);
+        cav[i].offN = cav[i].offP + round128(4 * RC * WB);
+        cav[i].n_strips = (c->p.nx + W - 1) / W;
+        cav[i].n_rowblocks = (c->p.ny + RC - 1) / RC;
+        cav[i].item_base = (int)items;
+        cav[i].W = W;
+        cav[i].WB = WB;
+        cav[i].RC = RC;
+        cav[i].tpr = tpr;
+        cav[i].stage_bytes = (unsigned)(kPlanes * RC * WB * sizeof(float));
+        items += (long long)cav[i].n_strips * cav[i].n_rowblocks;
+        for (int bf = 0; bf < 2; ++bf) {
+            rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 0], buf(c, bf), 6, RC, WB);
+            if (!rc) rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 1], buf(c, bf), 4, RC, WB);
+            if (rc) {
+                std::snprintf(b->err, sizeof b->err, "cavity %d: %.200s", i, c->err);
+                return fail(rc);
+            }
+        }
+    }
+    if (items > 0x7fffffff) {
+        batch_set_err(b, "batch has too many work items");
+        return fail(DMRT_E_ARG);
+    }
+    b->total_items = (int)items;
+    b->d_cav = reinterpret_cast<dmrt::BatchCavity*>(b->ws + L.off_cav);
+    b->d_maps = reinterpret_cast<CUtensorMap*>(b->ws + L.off_maps);
+    b->d_err = reinterpret_cast<unsigned*>(b->ws + L.off_err);
+    cudaError_t e = cudaMemcpyAsync(b->d_cav, cav.data(), cav.size() * sizeof(cav[0]), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(maps[0]), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 256, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch tables"));
+    // Launch shape: persistent grid of resident blocks.
+    b->block = R * (256 / npt);
+    b->smem = dmrt::tma_smem_bytes(R, S, 4);
+    int dev = 0, sms = 0, per_sm = 0;
+    e = cudaFuncSetAttribute(b->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, b->func, b->block, b->smem);
+    if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch launch shape"));
+    if (per_sm < 1) {
+        batch_set_err(b, "batched tile does not fit on an SM");
+        return fail(DMRT_E_ARG);
+    }
+    b->grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+    *out = b;
+    return DMRT_OK;
+}
+
+int dmrt_batch_step(dmrt_batch* b, int64_t nsteps) {
+    if (!b || nsteps < 0) return DMRT_E_ARG;
+    for (int i = 0; i < b->n; ++i) {
+        if (b->sub[i]->cur != b->parity) {
+            batch_set_err(b, "cavity %d was stepped on its own by an odd number of steps since the last "
+                             "batch step; step it once more first", i);
+            return DMRT_E_STATE;
+        }
+    }
+    long long done = 0;
+    while (done < nsteps) {
+        if (nsteps - done >= b->graph_len) {
+            if (!b->graph[b->parity]) {
+                int rc = batch_build_graph(b, b->parity);
+                if (rc) return rc;
+            }
+            BCK(cudaGraphLaunch(b->graph[b->parity], b->stream), "cudaGraphLaunch");
+            done += b->graph_len;  // even: parity unchanged
+        } else {
+            int rc = batch_launch(b, b->parity);
+            if (rc) return rc;
+            b->parity ^= 1;
+            done += 1;
+        }
+    }
+    BCK(cudaGetLastError(), "batch step launch");
+    b->t += nsteps;
+    for (dmrt_ctx* c : b->sub) {
+        c->cur = b->parity;
+        c->t += nsteps;
+    }
+    return DMRT_OK;
+}
+
+int dmrt_batch_check(dmrt_batch* b) {
+    if (!b) return DMRT_E_ARG;
+    BCK(cudaStreamSynchronize(b->stream), "synchronize");
+    unsigned err = 0;
+    BCK(cudaMemcpy(&err, b->d_err, sizeof err, cudaMemcpyDeviceToHost), "read error flag");
+    if (err & dmrt::kErrTimeout) {
+        batch_set_err(b, "a bounded device-side wait expired");
+        return DMRT_E_TIMEOUT;
+    }
+    for (int i = 0; i < b->n; ++i) {
+        int rc = dmrt_check(b->sub[i]);
+        if (rc) {
+            batch_set_err(b, "cavity %d: %.200s", i, b->sub[i]->err);
+            return rc;
+        }
+    }
+    return DMRT_OK;
+}
+
+int32_t dmrt_batch_size(const dmrt_batch* b) { return b ? b->n : 0; }
+
+dmrt_ctx* dmrt_batch_context(dmrt_batch* b, int32_t i) {
+    if (!b || i < 0 || i >= b->n) return nullptr;
+    return b->sub[i];
+}
+
+int dmrt_batch_get_launch(const dmrt_batch* b, dmrt_launch* out) {
+    if (!b || !out) return DMRT_E_ARG;
+    out->kernel = DMRT_KERNEL_TMA;
+    out->tma_npt = b->npt;
+    out->tma_rows = b->R;
+    out->tma_stages = b->S;
+    out->grid = b->grid;
+    out->block = b->block;
+    out->smem_bytes = (int64_t)b->smem;
+    out->graph_steps = b->graph_len;
+    return DMRT_OK;
+}
+
+const char* dmrt_batch_last_error(const dmrt_batch* b) { return b ? b->err : g_create_error; }
+
+void dmrt_batch_destroy(dmrt_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    for (dmrt_ctx* c : b->sub) dmrt_destroy(c);
+    delete b;
 }
 
 }  // extern "C"

@@ -274,6 +274,128 @@ __device__ __forceinline__ void collide_nodes(float (&F)[9][NPT], float (&Gq)[5]
     }
 }
 
+// Pull, collide and store one work item (strip, row block) from its shared-
+// memory stage `st`, and report the Nusselt number of the rows it owns in the
+// first strip. Called by every thread of the block (the Nusselt report is a
+// warp collective); `ok` is false when the stage's wait expired.
+// Geometry: strips of W nodes, shared-memory rows of WB elements (HALO left
+// of the strip), RC rows per item, plane groups P and N starting offP / offN
+// elements into the stage (group Z at 0); compile-time constants in the
+// single-cavity kernel, per-cavity values in the batched one.
+template <typename E, int NPT, bool SR>
+__device__ __forceinline__ void process_item(const E* st, const StepArgs& A, const StepConsts& K,
+                                             int strip, int rb, int rg, int t, bool ok,
+                                             unsigned salt, int W, int WB, int RC, int offP, int offN) {
+    const E* Sg = reinterpret_cast<const E*>(A.src);
+    const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 for float32)
+    const long long PL = A.plane;
+    const float sign_l_g = K.left_fixed ? -1.f : 1.f;
+    const float sign_r_g = K.right_fixed ? -1.f : 1.f;
+    const int j = rb * RC + rg;
+    const int n0 = NPT * t;
+    const int x0 = strip * W + n0;
+    const bool row_ok = j < A.ny;
+    const bool mine = ok && row_ok && rg < RC && n0 < W && x0 < A.nx;
+    float theta[NPT];
+#pragma unroll
+    for (int e = 0; e < NPT; ++e) theta[e] = 0.f;
+    if (mine) {
+        auto rowp = [&](int plane) {
+            const int g0 = plane >= kGroupN ? kGroupN : plane >= kGroupP ? kGroupP : kGroupZ;
+            const int off = plane >= kGroupN ? offN : plane >= kGroupP ? offP : 0;
+            return st + off + ((plane - g0) * RC + rg) * WB;
+        };
+        float F[9][NPT], Gq[5][NPT];
+        lds_pull<0>(rowp(plane_f(0)), n0, F[0], 0.f);
+        lds_pull<1>(rowp(plane_f(1)), n0, F[1], 0.f);
+        lds_pull<0>(rowp(plane_f(2)), n0, F[2], 0.f);
+        lds_pull<-1>(rowp(plane_f(3)), n0, F[3], 0.f);
+        lds_pull<0>(rowp(plane_f(4)), n0, F[4], 0.f);
+        lds_pull<1>(rowp(plane_f(5)), n0, F[5], 0.f);
+        lds_pull<-1>(rowp(plane_f(6)), n0, F[6], 0.f);
+        lds_pull<-1>(rowp(plane_f(7)), n0, F[7], 0.f);
+        lds_pull<1>(rowp(plane_f(8)), n0, F[8], 0.f);
+        lds_pull<0>(rowp(plane_g(0)), n0, Gq[0], sh0);
+        lds_pull<1>(rowp(plane_g(1)), n0, Gq[1], sh1);
+        lds_pull<0>(rowp(plane_g(2)), n0, Gq[2], sh1);
+        lds_pull<-1>(rowp(plane_g(3)), n0, Gq[3], sh1);
+        lds_pull<0>(rowp(plane_g(4)), n0, Gq[4], sh1);
+
+        // Walls. Bottom row: links from below (f2, f5, f6, g2) bounce back from
+        // the node's own opposites (f4, f7, f8, g4); top row the reverse.
+        const E* rowj = Sg + (size_t)j * A.pitch;
+        if (j == 0) {
+            vec_ldg<E, NPT>(rowj + plane_f(4) * PL + x0, F[2], 0.f);
+            vec_ldg<E, NPT>(rowj + plane_f(7) * PL + x0, F[5], 0.f);
+            vec_ldg<E, NPT>(rowj + plane_f(8) * PL + x0, F[6], 0.f);
+            vec_ldg<E, NPT>(rowj + plane_g(4) * PL + x0, Gq[2], sh1);
+        }
+        if (j == A.ny - 1) {
+            vec_ldg<E, NPT>(rowj + plane_f(2) * PL + x0, F[4], 0.f);
+            vec_ldg<E, NPT>(rowj + plane_f(5) * PL + x0, F[7], 0.f);
+            vec_ldg<E, NPT>(rowj + plane_f(6) * PL + x0, F[8], 0.f);
+            vec_ldg<E, NPT>(rowj + plane_g(2) * PL + x0, Gq[4], sh1);
+        }
+        // Left wall (node x = 0): links with e_x = +1 (f1, f5, f8, g1).
+        if (x0 == 0) {
+            F[1][0] = ldg_one(rowj + plane_f(3) * PL, 0.f);
+            F[5][0] = ldg_one(rowj + plane_f(7) * PL, 0.f);
+            F[8][0] = ldg_one(rowj + plane_f(6) * PL, 0.f);
+            const float add = K.left_fixed ? K.abb * __ldg(A.hot + j) : 0.f;
+            Gq[1][0] = sign_l_g * ldg_one(rowj + plane_g(3) * PL, sh1) + add;
+        }
+        // Right wall (node x = nx - 1): links with e_x = -1 (f3, f6, f7, g3).
+        const int re = A.nx - 1 - x0;
+        if (re < NPT) {
+            const int xr = A.nx - 1;
+            const float v3 = ldg_one(rowj + plane_f(1) * PL + xr, 0.f);
+            const float v6 = ldg_one(rowj + plane_f(8) * PL + xr, 0.f);
+            const float v7 = ldg_one(rowj + plane_f(5) * PL + xr, 0.f);
+            const float add = K.right_fixed ? K.abb * __ldg(A.cold + j) : 0.f;
+            const float vg = sign_r_g * ldg_one(rowj + plane_g(1) * PL + xr, sh1) + add;
+#pragma unroll
+            for (int e = 0; e < NPT; ++e) {
+                if (e == re) {
+                    F[3][e] = v3;
+                    F[6][e] = v6;
+                    F[7][e] = v7;
+                    Gq[3][e] = vg;
+                }
+            }
+        }
+
+        bool bad = false;
+        collide_nodes<NPT>(F, Gq, K, theta, min(NPT, A.nx - x0), bad);
+        E* D = reinterpret_cast<E*>(A.dst) + (size_t)j * A.pitch + x0;
+        if constexpr (SR) {
+            unsigned r = hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)x0) ^ salt);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) vec_put_sr<E, NPT>(D + plane_f(k) * PL, F[k], 0.f, r);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) vec_put_sr<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1, r);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) vec_put<E, NPT>(D + plane_f(k) * PL, F[k], 0.f);
+#pragma unroll
+            for (int k = 0; k < 5; ++k) vec_put<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1);
+        }
+        if (bad) atomicOr(A.err, kErrNonFinite);
+    }
+    // Nusselt number of row j from the first warp of the row's thread group
+    // in the first strip; nodes 0 and 1 sit in lane 0 (or lanes 0 and 1).
+    if (strip == 0 && t < 32) {
+        float th1 = NPT > 1 ? theta[NPT > 1 ? 1 : 0] : 0.f;
+        if constexpr (NPT == 1) th1 = __shfl_down_sync(kFull, theta[0], 1);
+        const bool has_nu = mine && t == 0;
+        double nuj = 0.0;
+        if (has_nu) {
+            const double tw = (double)__ldg(A.hot + j);
+            nuj = K.nu_scale * (8.0 * tw - 9.0 * (double)theta[0] + (double)th1);
+        }
+        nu_report(A, has_nu, j, nuj);
+    }
+}
+
 // Position in the block's sequence of work items blockIdx.x, blockIdx.x + G,
 // blockIdx.x + 2G, ... with item = rowblock * n_strips + strip, advanced
 // without divisions (they would cost as much as a node's arithmetic).
@@ -343,15 +465,10 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         }
     }
 
-    const E* Sg = reinterpret_cast<const E*>(A.src);
     // Stochastic rounding: per-step salt (the step count is only written by the
     // previous launch, so every block reads the same value).
     unsigned salt = 0;
     if constexpr (SR) salt = hash32((unsigned)*A.step_in * 0x9e3779b9u + 0x632be5abu);
-    const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 for float32)
-    const long long PL = A.plane;
-    const float sign_l_g = K.left_fixed ? -1.f : 1.f;
-    const float sign_r_g = K.right_fixed ? -1.f : 1.f;
     bool timed_out = false;
     ItemCursor cc;  // consumer: the item being computed
     cc.init(blockIdx.x, G, T.n_strips);
@@ -368,107 +485,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         }
         const bool ok = mbar_wait_bounded(&bars[s], phase);
 
-        const int strip = cc.strip;
-        const int j = cc.rb * R + rg;
-        const int n0 = NPT * t;
-        const int x0 = strip * STRIP + n0;
-        const bool row_ok = j < A.ny;
-        const bool mine = ok && row_ok && n0 < STRIP && x0 < A.nx;
-        float theta[NPT];
-#pragma unroll
-        for (int e = 0; e < NPT; ++e) theta[e] = 0.f;
-        if (mine) {
-            const E* st = stages + (size_t)s * tma_stage_elems(R);
-            auto rowp = [&](int plane) { return st + (plane * R + rg) * kTmaBox; };
-            float F[9][NPT], Gq[5][NPT];
-            lds_pull<0>(rowp(plane_f(0)), n0, F[0], 0.f);
-            lds_pull<1>(rowp(plane_f(1)), n0, F[1], 0.f);
-            lds_pull<0>(rowp(plane_f(2)), n0, F[2], 0.f);
-            lds_pull<-1>(rowp(plane_f(3)), n0, F[3], 0.f);
-            lds_pull<0>(rowp(plane_f(4)), n0, F[4], 0.f);
-            lds_pull<1>(rowp(plane_f(5)), n0, F[5], 0.f);
-            lds_pull<-1>(rowp(plane_f(6)), n0, F[6], 0.f);
-            lds_pull<-1>(rowp(plane_f(7)), n0, F[7], 0.f);
-            lds_pull<1>(rowp(plane_f(8)), n0, F[8], 0.f);
-            lds_pull<0>(rowp(plane_g(0)), n0, Gq[0], sh0);
-            lds_pull<1>(rowp(plane_g(1)), n0, Gq[1], sh1);
-            lds_pull<0>(rowp(plane_g(2)), n0, Gq[2], sh1);
-            lds_pull<-1>(rowp(plane_g(3)), n0, Gq[3], sh1);
-            lds_pull<0>(rowp(plane_g(4)), n0, Gq[4], sh1);
-
-            // Walls. Bottom row: links from below (f2, f5, f6, g2) bounce back from
-            // the node's own opposites (f4, f7, f8, g4); top row the reverse.
-            const E* rowj = Sg + (size_t)j * A.pitch;
-            if (j == 0) {
-                vec_ldg<E, NPT>(rowj + plane_f(4) * PL + x0, F[2], 0.f);
-                vec_ldg<E, NPT>(rowj + plane_f(7) * PL + x0, F[5], 0.f);
-                vec_ldg<E, NPT>(rowj + plane_f(8) * PL + x0, F[6], 0.f);
-                vec_ldg<E, NPT>(rowj + plane_g(4) * PL + x0, Gq[2], sh1);
-            }
-            if (j == A.ny - 1) {
-                vec_ldg<E, NPT>(rowj + plane_f(2) * PL + x0, F[4], 0.f);
-                vec_ldg<E, NPT>(rowj + plane_f(5) * PL + x0, F[7], 0.f);
-                vec_ldg<E, NPT>(rowj + plane_f(6) * PL + x0, F[8], 0.f);
-                vec_ldg<E, NPT>(rowj + plane_g(2) * PL + x0, Gq[4], sh1);
-            }
-            // Left wall (node x = 0): links with e_x = +1 (f1, f5, f8, g1).
-            if (x0 == 0) {
-                F[1][0] = ldg_one(rowj + plane_f(3) * PL, 0.f);
-                F[5][0] = ldg_one(rowj + plane_f(7) * PL, 0.f);
-                F[8][0] = ldg_one(rowj + plane_f(6) * PL, 0.f);
-                const float add = K.left_fixed ? K.abb * __ldg(A.hot + j) : 0.f;
-                Gq[1][0] = sign_l_g * ldg_one(rowj + plane_g(3) * PL, sh1) + add;
-            }
-            // Right wall (node x = nx - 1): links with e_x = -1 (f3, f6, f7, g3).
-            const int re = A.nx - 1 - x0;
-            if (re < NPT) {
-                const int xr = A.nx - 1;
-                const float v3 = ldg_one(rowj + plane_f(1) * PL + xr, 0.f);
-                const float v6 = ldg_one(rowj + plane_f(8) * PL + xr, 0.f);
-                const float v7 = ldg_one(rowj + plane_f(5) * PL + xr, 0.f);
-                const float add = K.right_fixed ? K.abb * __ldg(A.cold + j) : 0.f;
-                const float vg = sign_r_g * ldg_one(rowj + plane_g(1) * PL + xr, sh1) + add;
-#pragma unroll
-                for (int e = 0; e < NPT; ++e) {
-                    if (e == re) {
-                        F[3][e] = v3;
-                        F[6][e] = v6;
-                        F[7][e] = v7;
-                        Gq[3][e] = vg;
-                    }
-                }
-            }
-
-            bool bad = false;
-            collide_nodes<NPT>(F, Gq, K, theta, min(NPT, A.nx - x0), bad);
-            E* D = reinterpret_cast<E*>(A.dst) + (size_t)j * A.pitch + x0;
-            if constexpr (SR) {
-                unsigned r = hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)x0) ^ salt);
-#pragma unroll
-                for (int k = 0; k < 9; ++k) vec_put_sr<E, NPT>(D + plane_f(k) * PL, F[k], 0.f, r);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) vec_put_sr<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1, r);
-            } else {
-#pragma unroll
-                for (int k = 0; k < 9; ++k) vec_put<E, NPT>(D + plane_f(k) * PL, F[k], 0.f);
-#pragma unroll
-                for (int k = 0; k < 5; ++k) vec_put<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1);
-            }
-            if (bad) atomicOr(A.err, kErrNonFinite);
-        }
-        // Nusselt number of row j from the first warp of the row's thread group
-        // in the first strip; nodes 0 and 1 sit in lane 0 (or lanes 0 and 1).
-        if (strip == 0 && t < 32) {
-            float th1 = NPT > 1 ? theta[NPT > 1 ? 1 : 0] : 0.f;
-            if constexpr (NPT == 1) th1 = __shfl_down_sync(kFull, theta[0], 1);
-            const bool has_nu = mine && t == 0;
-            double nuj = 0.0;
-            if (has_nu) {
-                const double tw = (double)__ldg(A.hot + j);
-                nuj = K.nu_scale * (8.0 * tw - 9.0 * (double)theta[0] + (double)th1);
-            }
-            nu_report(A, has_nu, j, nuj);
-        }
+        process_item<E, NPT, SR>(stages + (size_t)s * tma_stage_elems(R), A, K, cc.strip, cc.rb, rg,
+                                 t, ok, salt, STRIP, kTmaBox, R, kGroupP * R * kTmaBox, kGroupN * R * kTmaBox);
         // All threads are done with stage s; a timeout anywhere ends the block.
         if (__syncthreads_or(!ok)) {
             timed_out = true;
@@ -483,6 +501,138 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     if (timed_out && tid == 0) {
         atomicOr(A.err, kErrTimeout);
         // Let the copies this block issued land before its shared memory is released.
+        for (int q = k; q < issued; ++q) mbar_wait_bounded(&bars[q % S], (uint32_t)((q / S) & 1));
+    }
+}
+
+// ---- batched sweep ------------------------------------------------------------
+// One launch steps every cavity of a batch. The work items of all cavities
+// form one list, cavity after cavity (strip fastest, then row block); each
+// block of the persistent grid takes one contiguous chunk of it, so consecutive
+// items of a block mostly belong to one cavity. The producer and the
+// consumers walk the same cursor through the chunk (the consumers S - 1 items
+// behind), so no item descriptor has to pass through shared memory.
+// Float32 storage only.
+// Each cavity has its own strip geometry: strips of W nodes (a multiple of
+// 32 NPT, so that every warp stays within one row), boxes WB = W + 8 elements
+// wide and RC rows tall (as many rows as the block's threads and the stage's
+// shared memory allow), so narrow cavities keep the block's lanes busy.
+struct BatchCavity {
+    StepArgs args[2];  // by source buffer: args[b] reads buffer b, writes 1 - b
+    StepConsts K;
+    int n_strips, n_rowblocks;
+    int item_base;     // index of the cavity's first item in the batch list
+    int W, WB, RC;     // strip width, box width, rows per item
+    int tpr;           // threads per row = W / NPT
+    int offP, offN;    // stage offsets (elements) of plane groups P and N, 128-byte aligned
+    unsigned stage_bytes;
+    int pad2;
+};
+
+struct BatchCursor {
+    int c, strip, rb;
+    __device__ __forceinline__ void init(const BatchCavity* __restrict__ cav, int n_cav, int item) {
+        int lo = 0, hi = n_cav - 1;  // last cavity whose item_base <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cav[mid].item_base <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        c = lo;
+        const int local = item - cav[c].item_base;
+        const int ns = cav[c].n_strips;
+        strip = local % ns;
+        rb = local / ns;
+    }
+    __device__ __forceinline__ void advance(const BatchCavity* __restrict__ cav) {
+        if (++strip == cav[c].n_strips) {
+            strip = 0;
+            if (++rb == cav[c].n_rowblocks) {
+                rb = 0;
+                ++c;
+            }
+        }
+    }
+};
+
+template <int NPT, int R, int S>
+__global__ void __launch_bounds__(R * (256 / NPT))
+    step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
+                          int n_cav, int total_items, int parity, unsigned* batch_err) {
+    using E = float;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    E* stages = reinterpret_cast<E*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * tma_stage_elems(R) * sizeof(E));
+    constexpr int HALO = tma_halo(sizeof(E));
+    const int tid = threadIdx.x;
+
+    if (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout) return;
+
+    const int first = (int)((long long)blockIdx.x * total_items / gridDim.x);
+    const int last = (int)((long long)(blockIdx.x + 1) * total_items / gridDim.x);
+    const int count = last - first;
+    if (count <= 0) return;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // maps[(c * 2 + buffer) * 2 + 0]: 6-plane boxes, [... + 1]: 4-plane boxes.
+    auto issue = [&](const BatchCursor& q, int s) {
+        const BatchCavity& bc = cav[q.c];
+        const int x = q.strip * bc.W - HALO;
+        const int j0 = q.rb * bc.RC;
+        const CUtensorMap* m = maps + ((size_t)q.c * 2 + parity) * 2;
+        E* st = stages + (size_t)s * tma_stage_elems(R);
+        mbar_expect_tx(&bars[s], bc.stage_bytes);
+        tma_load_3d(st, m, x, j0, kGroupZ, &bars[s]);
+        tma_load_3d(st + bc.offP, m + 1, x, j0 - 1, kGroupP, &bars[s]);
+        tma_load_3d(st + bc.offN, m + 1, x, j0 + 1, kGroupN, &bars[s]);
+    };
+
+    BatchCursor pc;
+    pc.init(cav, n_cav, first);
+    int issued = 0;
+    if (tid == 0) {
+        for (int q = 0; q < S - 1 && q < count; ++q) {
+            issue(pc, q);
+            pc.advance(cav);
+            issued = q + 1;
+        }
+    }
+    BatchCursor cc;
+    cc.init(cav, n_cav, first);
+    bool timed_out = false;
+    int k = 0, s = 0;
+    uint32_t phase = 0;
+    for (; k < count; ++k) {
+        if (tid == 0 && k + S - 1 < count) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(pc, s == 0 ? S - 1 : s - 1);
+            pc.advance(cav);
+            issued = k + S;
+        }
+        const bool ok = mbar_wait_bounded(&bars[s], phase);
+        const BatchCavity& bc = cav[cc.c];
+        const int tpr = bc.tpr;
+        const int rg = tid / tpr;
+        const int t = tid - rg * tpr;
+        process_item<E, NPT, false>(stages + (size_t)s * tma_stage_elems(R), bc.args[parity], bc.K,
+                                    cc.strip, cc.rb, rg, t, ok, 0u, bc.W, bc.WB, bc.RC, bc.offP, bc.offN);
+        if (__syncthreads_or(!ok)) {
+            timed_out = true;
+            break;
+        }
+        cc.advance(cav);
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
+        }
+    }
+    if (timed_out && tid == 0) {
+        atomicOr(batch_err, kErrTimeout);
         for (int q = k; q < issued; ++q) mbar_wait_bounded(&bars[q % S], (uint32_t)((q / S) & 1));
     }
 }

@@ -17,5 +17,6 @@ const TmaVariant* tma_variants_npt2(int* n);
 const TmaVariant* tma_variants_npt1(int* n);
 const TmaVariant* tma_variants_fp16(int* n);
 const TmaVariant* tma_variants_bf16(int* n);
+const TmaVariant* tma_variants_batch(int* n);  // batched sweep kernels
 
 }  // namespace dmrt

@@ -85,6 +85,11 @@ class Launch(ctypes.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("tma_npt", ctypes.c_int32), ("tma_rows", ctypes.c_int32),
+                ("tma_stages", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 
@@ -111,6 +116,18 @@ SIGNATURES = {
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
+    "dmrt_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
+                                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.POINTER(_DP),
+                                         ctypes.POINTER(BatchOpts), _VP, ctypes.c_size_t, _VP,
+                                         ctypes.POINTER(_VP)]),
+    "dmrt_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "dmrt_batch_check": (ctypes.c_int, [_VP]),
+    "dmrt_batch_size": (ctypes.c_int32, [_VP]),
+    "dmrt_batch_context": (_VP, [_VP, ctypes.c_int32]),
+    "dmrt_batch_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
+    "dmrt_batch_last_error": (ctypes.c_char_p, [_VP]),
+    "dmrt_batch_destroy": (None, [_VP]),
     "dmrt_destroy": (None, [_VP]),
 }
 
@@ -136,6 +153,13 @@ def load():
 def _check(rc, handle=None):
     if rc != DMRT_OK:
         msg = load().dmrt_last_error(handle)
+        raise DmrtError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def _check_batch(rc, b=None):
+    if rc != DMRT_OK:
+        msg = load().dmrt_batch_last_error(b)
         raise DmrtError(rc, msg.decode() if msg else "")
     return rc
 
@@ -344,6 +368,89 @@ class Cavity2D:
         if getattr(self, "h", None):
             dmrt_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Member(Cavity2D):
+    """A batch member as a context (borrowed: the batch owns it)."""
+
+    def __init__(self, batch, i, params):
+        self.p = params
+        self.nx, self.ny = params.nx, params.ny
+        self.device = batch.device
+        self.stream = batch.stream
+        self.h = _VP(load().dmrt_batch_context(batch.b, i))
+        self.consts = dmrt_get_consts(self.h)
+        self.launch = dmrt_get_launch(self.h).as_dict()
+
+    def close(self):
+        self.h = None
+
+
+class Batch:
+    """Independent cavities stepped together by the batched kernel (one launch
+    per time step); ``members[i]`` exposes each as a context."""
+
+    def __init__(self, params_list, theta0_list=None, opts=None, device="cuda", stream=None):
+        import torch
+
+        n = len(params_list)
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        arr = (Params * n)(*params_list)
+        nbytes = ctypes.c_size_t()
+        _check_batch(load().dmrt_batch_workspace_size(arr, n, ctypes.byref(nbytes)))
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        keep = []
+        th_ptrs = None
+        if theta0_list is not None:
+            th_ptrs = (_DP * n)()
+            for i, th in enumerate(theta0_list):
+                if th is not None:
+                    a = np.ascontiguousarray(th, dtype=np.float64)
+                    keep.append(a)
+                    th_ptrs[i] = a.ctypes.data_as(_DP)
+        o = None
+        if opts is not None:
+            o = BatchOpts(*[int(opts.get(k, 0)) for k in ("tma_npt", "tma_rows", "tma_stages", "graph_steps")])
+        b = _VP()
+        _check_batch(load().dmrt_batch_create(arr, n, th_ptrs, ctypes.byref(o) if o else None,
+                                              _VP(self.workspace.data_ptr()), nbytes.value,
+                                              _VP(self.stream.cuda_stream), ctypes.byref(b)))
+        self.b = b
+        self.n = n
+        lk = Launch()
+        _check_batch(load().dmrt_batch_get_launch(b, ctypes.byref(lk)), b)
+        self.launch = lk.as_dict()
+        self.members = [_Member(self, i, params_list[i]) for i in range(n)]
+
+    @classmethod
+    def from_inputs(cls, cavities, opts=None, nu_capacity=1 << 16, **kw):
+        ps = [make_params(c.nx, c.ny, c.Ra, c.Pr, c.alpha, theta_hot=c.theta_hot, theta_cold=c.theta_cold,
+                          theta_init=c.theta_init, nu_capacity=nu_capacity) for c in cavities]
+        return cls(ps, [c.theta0() for c in cavities], opts=opts, **kw)
+
+    @property
+    def nodes(self) -> int:
+        return sum(m.nx * m.ny for m in self.members)
+
+    def step(self, n: int):
+        _check_batch(load().dmrt_batch_step(self.b, int(n)), self.b)
+
+    def check(self):
+        _check_batch(load().dmrt_batch_check(self.b), self.b)
+
+    def close(self):
+        if getattr(self, "b", None):
+            for m in self.members:
+                m.close()
+            load().dmrt_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

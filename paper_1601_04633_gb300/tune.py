@@ -1,0 +1,137 @@
+"""Autotuner for the step kernels' tile shape (nodes per thread, rows per work
+item, pipeline stages) and CUDA-graph length.
+
+Each candidate is timed on the actual workload with CUDA events after a short
+warm-up, and the fastest is returned; results can be cached in a JSON file
+keyed by the workload's shapes and the GPU name. Tuning never changes results:
+every tile computes bit-identical steps.
+
+    python -m paper_1601_04633_gb300.tune --batch      # the 64-cavity sweep
+    python -m paper_1601_04633_gb300.tune --single 4096
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+
+# Compiled tiles (see include/dmrt.h).
+BATCH_TILES = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 2, 2), (2, 4, 2), (4, 1, 4), (4, 4, 2)]
+SINGLE_TILES_FP32 = ([(1, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (3, 2), (4, 2), (4, 3)]]
+                     + [(2, r, s) for r, s in [(1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (4, 2)]]
+                     + [(4, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (2, 2), (2, 3), (2, 4),
+                                              (4, 2), (4, 3)]])
+SINGLE_TILES_16 = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (1, 4, 4), (2, 2, 2), (2, 4, 2), (2, 4, 3), (4, 4, 2)]
+SINGLE_TILES_16_SR = [(1, 1, 2), (1, 4, 2), (2, 2, 2), (4, 4, 2)]
+
+
+def _time_steps(step, steps, warmup):
+    import torch
+
+    step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def _key(kind, shapes, extra=""):
+    import torch
+
+    h = hashlib.sha256(json.dumps([kind, shapes, extra]).encode()).hexdigest()[:16]
+    return f"{torch.cuda.get_device_name()}|{kind}|{h}"
+
+
+def _cache_get(path, key):
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        return json.load(fh).get(key)
+
+
+def _cache_put(path, key, value):
+    if not path:
+        return
+    d = {}
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+    d[key] = value
+    tmp = path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(d, fh, indent=1)
+    os.replace(tmp, path)
+
+
+def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None):
+    """Pick the batched kernel's tile for these cavities. Returns
+    {"opts": {...}, "mlups": best, "trials": [...]}."""
+    from . import dmrt as D
+
+    key = _key("batch", [(c.nx, c.ny) for c in cavities], str(steps))
+    hit = _cache_get(cache, key)
+    if hit:
+        return hit
+    nodes = sum(c.nx * c.ny for c in cavities)
+    trials = []
+    for npt, R, S in (tiles or BATCH_TILES):
+        for g in graph_steps:
+            opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g)
+            b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + 8)
+            sec = _time_steps(b.step, steps, warmup)
+            b.check()
+            b.close()
+            trials.append({"opts": opts, "mlups": nodes * steps / sec / 1e6})
+    best = max(trials, key=lambda r: r["mlups"])
+    out = {"opts": best["opts"], "mlups": best["mlups"], "trials": trials}
+    _cache_put(cache, key, out)
+    return out
+
+
+def tune_single(cav, storage=0, rounding=0, steps=200, warmup=20, tiles=None, cache=None):
+    """Pick the single-cavity TMA tile. Returns {"kw": {...}, "mlups": best, "trials": [...]}."""
+    from . import dmrt as D
+
+    if tiles is None:
+        tiles = SINGLE_TILES_FP32 if storage == 0 else (SINGLE_TILES_16_SR if rounding else SINGLE_TILES_16)
+    key = _key("single", [(cav.nx, cav.ny)], f"{storage}-{rounding}-{steps}")
+    hit = _cache_get(cache, key)
+    if hit:
+        return hit
+    trials = []
+    for npt, R, S in tiles:
+        kw = dict(kernel=D.DMRT_KERNEL_TMA, tma_npt=npt, tma_rows=R, tma_stages=S, storage=storage,
+                  rounding=rounding)
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=steps + warmup + 8, **kw)
+        sec = _time_steps(sim.step, steps, warmup)
+        sim.check()
+        sim.close()
+        trials.append({"kw": kw, "mlups": cav.nx * cav.ny * steps / sec / 1e6})
+    best = max(trials, key=lambda r: r["mlups"])
+    out = {"kw": best["kw"], "mlups": best["mlups"], "trials": trials}
+    _cache_put(cache, key, out)
+    return out
+
+
+def main():
+    from . import inputs
+
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--single", type=int, default=0, help="side of a square cavity")
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--cache", default=None)
+    args = ap.parse_args()
+    if args.batch:
+        print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, cache=args.cache), indent=1))
+    if args.single:
+        cav = inputs.Cavity(args.single, args.single, 1e7, 0.001, seed=5)
+        print(json.dumps(tune_single(cav, steps=args.steps, cache=args.cache), indent=1))
+
+
+if __name__ == "__main__":
+    main()

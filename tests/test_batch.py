@@ -1,0 +1,113 @@
+"""Batched sweep: many independent cavities stepped by one launch per time step.
+
+The batched kernel runs the same per-node arithmetic as the single-cavity
+kernels on the same pulled values, so every member must match, bit for bit,
+the same cavity stepped on its own; a sampled subset of the 64-cavity sweep is
+also checked against the fp64 oracle with the parity tolerances.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_04633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELD_TOL = 1e-5
+NU_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def D():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1601_04633_gb300 import dmrt
+
+    return dmrt
+
+
+def _uneven():
+    # Uneven shapes (ragged strips and row blocks), Ra for Ma <= 0.1, three Prandtl numbers.
+    shapes = [(128, 128), (200, 150), (67, 45), (300, 70), (33, 257), (500, 9), (2, 2)]
+    out = []
+    for k, (nx, ny) in enumerate(shapes):
+        Pr = (0.001, 0.005, 0.01)[k % 3]
+        Ra = min(1e6, (0.08 * ny / (np.sqrt(3) * 0.1)) ** 2 / Pr)
+        out.append(inputs.Cavity(nx, ny, Ra, Pr, noise_amp=1e-3, seed=100 + k))
+    return out
+
+
+@pytest.mark.parametrize("tile", [(1, 4, 2), (1, 1, 2), (2, 2, 2), (4, 4, 2), (4, 1, 4)])
+def test_batch_members_match_single_contexts_bitwise(D, tile):
+    cavs = _uneven()
+    npt, R, S = tile
+    b = D.Batch.from_inputs(cavs, opts=dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=16),
+                            nu_capacity=128)
+    b.step(37)  # graphs of 16 steps plus single launches
+    b.check()
+    for i, cav in enumerate(cavs):
+        single = D.Cavity2D.from_inputs(cav, nu_capacity=128)
+        single.step(37)
+        single.check()
+        m = b.members[i]
+        assert m.steps_done == 37
+        assert np.array_equal(m.get_state(), single.get_state()), i
+        assert np.array_equal(m.nusselt(37)[2], single.nusselt(37)[2]), i
+        single.close()
+    b.close()
+
+
+def test_batch_parity_rule_and_member_stepping(D):
+    cavs = _uneven()[:3]
+    b = D.Batch.from_inputs(cavs, nu_capacity=64)
+    b.step(4)
+    b.members[1].step(1)  # stepped on its own: the batch must refuse until it is even again
+    with pytest.raises(D.DmrtError) as ei:
+        b.step(1)
+    assert ei.value.code == D.DMRT_E_STATE
+    b.members[1].step(1)
+    b.step(3)
+    b.check()
+    ref = D.Cavity2D.from_inputs(cavs[1], nu_capacity=64)
+    ref.step(9)
+    assert np.array_equal(b.members[1].get_state(), ref.get_state())
+    assert b.members[0].steps_done == 7 and b.members[1].steps_done == 9
+    ref.close()
+    b.close()
+
+
+def test_sweep_of_64_cavities_sampled_against_oracle(D):
+    # The 64-cavity sweep (sides 128..384, Ra log-uniform in [1e4, 1e6], Pr in
+    # {0.001, 0.005, 0.01}); 300 steps; three members against the oracle.
+    cavs = inputs.batch_sweep()
+    steps = 300
+    b = D.Batch.from_inputs(cavs, nu_capacity=steps)
+    b.step(steps)
+    b.check()
+    for i in (0, 17, 63):
+        cav = cavs[i]
+        m = b.members[i]
+        u, v, th = (x.cpu().numpy().astype(np.float64) for x in m.fields())
+        series = m.nusselt(steps)[2]
+        mo = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+        f, g = O.init(mo, cav.theta0())
+        ref = O.run(mo, steps, f, g)
+        for name, a in (("u", u), ("v", v), ("theta", th)):
+            err = np.abs(a - ref[name]).max() / np.abs(ref[name]).max()
+            assert err <= FIELD_TOL, (i, name, err)
+        nu_err = (np.abs(series - ref["nu_series"]) / np.abs(ref["nu_series"])).max()
+        assert nu_err <= NU_TOL, (i, nu_err)
+    b.close()
+
+
+def test_autotuner_picks_a_compiled_tile(D):
+    from paper_1601_04633_gb300 import tune
+
+    cavs = _uneven()[:4]
+    r = tune.tune_batch(cavs, steps=20, warmup=4, tiles=[(1, 4, 2), (2, 2, 2)])
+    assert r["opts"]["tma_npt"] in (1, 2) and len(r["trials"]) == 2
+    assert all(t["mlups"] > 0 for t in r["trials"])
