@@ -90,6 +90,9 @@ def lib():
             L.orc_run.argtypes = [mp, ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.orc_run.restype = ctypes.c_int
             L.orc_fields_from_post.argtypes = [mp, dp, dp, dp, dp, dp]
+            L.orc_collide_vjp.argtypes = [mp, dp, dp, dp, dp]
+            L.orc_adjoint.argtypes = [mp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp, dp, dp]
+            L.orc_adjoint.restype = ctypes.c_int
             L.orc_set_threads.argtypes = [ctypes.c_int]
             L.orc_set_threads.restype = ctypes.c_int
             _lib = L
@@ -256,3 +259,41 @@ def fields_from_post(model: Model, fs, gs):
     u, v, t = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
     lib().orc_fields_from_post(ctypes.byref(model), _p(fs), _p(gs), _p(u), _p(v), _p(t))
     return u, v, t
+
+
+def collide_vjp(model: Model, x, lam):
+    """nu = C'(x)^T lam for one node (x, lam: 14 values, f then g) and lam . dC/dgbeta."""
+    x = _vec(x, 14)
+    lam = _vec(lam, 14)
+    nu = np.zeros(14)
+    dgb = ctypes.c_double(0.0)
+    lib().orc_collide_vjp(ctypes.byref(model), _p(x), _p(lam), _p(nu),
+                          ctypes.cast(ctypes.byref(dgb), ctypes.POINTER(ctypes.c_double)))
+    return nu, dgb.value
+
+
+def adjoint(model: Model, nsteps: int, avg_last: int, f0, g0, theta_hot_profile=None):
+    """J = mean hot-wall Nu over the last avg_last of nsteps steps from (f0, g0), and
+    (dJ/dtheta_w[ny], dJ/dgbeta). Keeps every forward state: small grids only."""
+    ny = model.ny
+    hp = _profile(theta_hot_profile, ny)
+    if hp is None:
+        hp = np.full(ny, model.theta_hot)
+    J = ctypes.c_double()
+    dth = np.zeros(ny)
+    dgb = ctypes.c_double()
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib().orc_adjoint(ctypes.byref(model), int(nsteps), int(avg_last),
+                           _p(np.ascontiguousarray(f0, dtype=np.float64)),
+                           _p(np.ascontiguousarray(g0, dtype=np.float64)), _p(hp),
+                           ctypes.cast(ctypes.byref(J), dp), _p(dth), ctypes.cast(ctypes.byref(dgb), dp))
+    if rc:
+        raise RuntimeError(f"orc_adjoint failed rc={rc}")
+    return J.value, dth, dgb.value
+
+
+def objective(model: Model, nsteps: int, avg_last: int, theta0, theta_hot_profile=None):
+    """J (as in ``adjoint``) from a forward run started at rest with temperature theta0."""
+    f, g = init(model, theta0)
+    r = run(model, nsteps, f, g, theta_hot_profile=theta_hot_profile)
+    return float(r["nu_series"][-avg_last:].mean())

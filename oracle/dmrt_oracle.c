@@ -36,6 +36,7 @@
  *     second-order one-sided derivative through the wall value and the first
  *     two node values (Eq. 18), mean over rows (Eq. 19, midpoint rule).
  */
+#include <complex.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -454,6 +455,199 @@ void orc_fields_from_post(const orc_model *md, const double *fs, const double *g
             v[q] = (jy - md->rho0 * Gy) / md->rho0;
             theta[q] = t;
         }
+}
+
+
+/* ---------------------------------------------------------------------- */
+/* Discrete adjoint of the step (test infrastructure for the GPU adjoint).  */
+/*
+ * Objective: J = sum_k w_k Nu(k), with Nu(k) the mean hot-wall Nusselt number
+ * of step k (Eqs. 18-19) and w_k = 1 / avg_last for the last avg_last steps.
+ * Parameters: the hot-wall temperature profile theta_w(j) (Eq. 45 and the Nu
+ * stencil) and the buoyancy scale gbeta (Eq. 27; Ra enters only through it).
+ *
+ * Reverse sweep, step k = N..1, with all forward states kept:
+ *   nu     = C'(q_k)^T lambda_k + w_k dNu(k)/dq_k      (q_k: pulled state of step k)
+ *   lambda_{k-1} = P^T nu                              (transposed streaming, walls)
+ * The local Jacobian C' of the collision (Eqs. 26-36) is formed column by
+ * column by complex-step differentiation (Squire & Trapp, SIAM Rev. 1998):
+ * dC/dx_m = Im C(x + i h e_m) / h, exact to rounding for this polynomial map.
+ */
+typedef double complex cplx;
+
+static void collide_cx(const orc_model *md, const cplx f[9], const cplx g[5], cplx gbeta,
+                       cplx fout[9], cplx gout[5]) {
+    double rates9[9] = {md->s_rho, md->s_j,  md->s_j,  md->s_e, md->s_nu,
+                        md->s_nu,  md->s_q,  md->s_q,  md->s_eps};
+    double rates5[5] = {md->sig_0, md->sig_k, md->sig_k, md->sig_e, md->sig_nu};
+    static const double W9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9,
+                                 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    cplx drho = 0, jx = 0, jy = 0, theta = 0;
+    for (int k = 0; k < 9; ++k) {
+        drho += f[k];
+        jx += f[k] * EX9[k];
+        jy += f[k] * EY9[k];
+    }
+    for (int k = 0; k < 5; ++k) theta += g[k];
+    double rho0 = md->rho0;
+    cplx u = jx / rho0, v = jy / rho0, uu = u * u + v * v;
+    cplx m[9], meq[9], mstar[9];
+    for (int r = 0; r < 9; ++r) {
+        m[r] = 0;
+        for (int k = 0; k < 9; ++k) m[r] += M9[r][k] * f[k];
+    }
+    meq[0] = drho;
+    meq[1] = rho0 * u;
+    meq[2] = rho0 * v;
+    meq[3] = -2.0 * drho + 3.0 * rho0 * uu;
+    meq[4] = rho0 * (u * u - v * v);
+    meq[5] = rho0 * u * v;
+    meq[6] = -rho0 * u;
+    meq[7] = -rho0 * v;
+    meq[8] = drho - 3.0 * rho0 * uu;
+    for (int r = 0; r < 9; ++r) mstar[r] = m[r] - rates9[r] * (m[r] - meq[r]);
+    double cs2 = 1.0 / 3.0, p = rho0 * cs2;
+    cplx Gy = gbeta * (theta - md->theta_ref);
+    for (int r = 0; r < 9; ++r) {
+        cplx acc = 0;
+        for (int k = 0; k < 9; ++k) acc += M9inv[r][k] * mstar[k];
+        cplx eu = EX9[r] * u + EY9[r] * v;
+        cplx feq = W9[r] * rho0 * (1.0 + eu / cs2 + eu * eu / (2.0 * cs2 * cs2) - uu / (2.0 * cs2));
+        fout[r] = acc + Gy * (EY9[r] - v) / p * feq;
+    }
+    cplx n[5], neq[5], nstar[5];
+    for (int r = 0; r < 5; ++r) {
+        n[r] = 0;
+        for (int k = 0; k < 5; ++k) n[r] += N5[r][k] * g[k];
+    }
+    neq[0] = theta;
+    neq[1] = u * theta;
+    neq[2] = v * theta;
+    neq[3] = md->a * theta;
+    neq[4] = 0;
+    for (int r = 0; r < 5; ++r) nstar[r] = n[r] - rates5[r] * (n[r] - neq[r]);
+    for (int r = 0; r < 5; ++r) {
+        cplx acc = 0;
+        for (int k = 0; k < 5; ++k) acc += N5inv[r][k] * nstar[k];
+        gout[r] = acc;
+    }
+}
+
+/* Jacobian-transpose product at one node: nu = C'(x)^T lam (x = 9 f then 5 g),
+ * and *dgb += lam . dC/dgbeta. */
+void orc_collide_vjp(const orc_model *md, const double x[14], const double lam[14], double nu[14],
+                     double *dgb) {
+    const double h = 1e-30;
+    ensure_inverses();
+    for (int col = 0; col <= 14; ++col) {
+        cplx f[9], g[5], fo[9], go[5];
+        for (int k = 0; k < 9; ++k) f[k] = x[k];
+        for (int k = 0; k < 5; ++k) g[k] = x[9 + k];
+        cplx gb = md->gbeta;
+        if (col < 9) f[col] += I * h;
+        else if (col < 14) g[col - 9] += I * h;
+        else gb += I * h;
+        collide_cx(md, f, g, gb, fo, go);
+        double acc = 0.0;
+        for (int k = 0; k < 9; ++k) acc += lam[k] * cimag(fo[k]) / h;
+        for (int k = 0; k < 5; ++k) acc += lam[9 + k] * cimag(go[k]) / h;
+        if (col < 14) nu[col] = acc;
+        else *dgb += acc;
+    }
+}
+
+int orc_adjoint(const orc_model *md, int64_t nsteps, int64_t avg_last, const double *f0,
+                const double *g0, const double *theta_hot_prof, double *J, double *dJ_dthw,
+                double *dJ_dgbeta) {
+    int nx = md->nx, ny = md->ny;
+    size_t n = (size_t)nx * ny, sz = 14 * n;
+    if (nsteps < 1 || avg_last < 1 || avg_last > nsteps) return -1;
+    double *S = (double *)malloc((size_t)(nsteps + 1) * sz * sizeof(double));
+    double *q = (double *)malloc(sz * sizeof(double));
+    double *lam = (double *)calloc(sz, sizeof(double));
+    double *nu = (double *)malloc(sz * sizeof(double));
+    double *lprev = (double *)malloc(sz * sizeof(double));
+    if (!S || !q || !lam || !nu || !lprev) {
+        free(S); free(q); free(lam); free(nu); free(lprev);
+        return -2;
+    }
+    ensure_inverses();
+    const double scale = md->dT != 0.0 ? md->H / (3.0 * md->dT) : 0.0;
+    memcpy(S, f0, 9 * n * sizeof(double));
+    memcpy(S + 9 * n, g0, 5 * n * sizeof(double));
+    double Jacc = 0.0;
+    for (int64_t k = 1; k <= nsteps; ++k) {
+        double *prev = S + (size_t)(k - 1) * sz, *next = S + (size_t)k * sz, nu_k;
+        orc_step(md, prev, prev + 9 * n, theta_hot_prof, NULL, next, next + 9 * n, NULL, NULL, NULL,
+                 NULL, &nu_k);
+        if (k > nsteps - avg_last) Jacc += nu_k / (double)avg_last;
+    }
+    *J = Jacc;
+    for (int j = 0; j < ny; ++j) dJ_dthw[j] = 0.0;
+    double dgb = 0.0;
+    for (int64_t k = nsteps; k >= 1; --k) {
+        const double *prev = S + (size_t)(k - 1) * sz;
+        const double w = (k > nsteps - avg_last) ? 1.0 / (double)avg_last : 0.0;
+        orc_stream(md, prev, prev + 9 * n, theta_hot_prof, NULL, q, q + 9 * n);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                double x[14], l[14], o[14];
+                for (int c = 0; c < 14; ++c) {
+                    x[c] = q[(size_t)c * n + (size_t)j * nx + i];
+                    l[c] = lam[(size_t)c * n + (size_t)j * nx + i];
+                }
+                orc_collide_vjp(md, x, l, o, &dgb);
+                for (int c = 0; c < 14; ++c) nu[(size_t)c * n + (size_t)j * nx + i] = o[c];
+            }
+        /* Nu(k) = (1/ny) sum_j scale (8 theta_w(j) - 9 theta(0,j) + theta(1,j)), theta = sum g. */
+        if (w != 0.0)
+            for (int j = 0; j < ny; ++j) {
+                for (int c = 9; c < 14; ++c) {
+                    nu[(size_t)c * n + (size_t)j * nx + 0] += w * (-9.0 * scale) / ny;
+                    nu[(size_t)c * n + (size_t)j * nx + 1] += w * scale / ny;
+                }
+                dJ_dthw[j] += w * 8.0 * scale / ny;
+            }
+        /* Transposed streaming: every pulled entry goes back to where it came from. */
+        for (size_t c = 0; c < sz; ++c) lprev[c] = 0.0;
+        for (int k9 = 0; k9 < 9; ++k9) {
+            int kb = opposite9(k9);
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int si = i - EX9[k9], sj = j - EY9[k9];
+                    double val = nu[(size_t)k9 * n + (size_t)j * nx + i];
+                    if (si >= 0 && si < nx && sj >= 0 && sj < ny)
+                        lprev[(size_t)k9 * n + (size_t)sj * nx + si] += val;
+                    else
+                        lprev[(size_t)kb * n + (size_t)j * nx + i] += val;
+                }
+        }
+        for (int k5 = 0; k5 < 5; ++k5) {
+            int kb = opposite5(k5);
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i) {
+                    int si = i - EX5[k5], sj = j - EY5[k5];
+                    double val = nu[(size_t)(9 + k5) * n + (size_t)j * nx + i];
+                    if (si >= 0 && si < nx && sj >= 0 && sj < ny) {
+                        lprev[(size_t)(9 + k5) * n + (size_t)sj * nx + si] += val;
+                        continue;
+                    }
+                    int bc = si < 0 ? md->left_bc : si >= nx ? md->right_bc : ORC_WALL_ADIABATIC;
+                    if (bc == ORC_WALL_FIXED) {
+                        lprev[(size_t)(9 + kb) * n + (size_t)j * nx + i] -= val; /* Eq. 45 */
+                        if (si < 0) dJ_dthw[j] += md->abb_coef * val;
+                    } else {
+                        lprev[(size_t)(9 + kb) * n + (size_t)j * nx + i] += val; /* Eq. 44 */
+                    }
+                }
+        }
+        double *tmp = lam;
+        lam = lprev;
+        lprev = tmp;
+    }
+    *dJ_dgbeta = dgb;
+    free(S); free(q); free(lam); free(nu); free(lprev);
+    return 0;
 }
 
 int orc_set_threads(int n) {

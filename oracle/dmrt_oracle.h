@@ -46,6 +46,14 @@ int orc_run(const orc_model *md, int64_t nsteps, double *fs, double *gs,
             double *nu_local);
 void orc_fields_from_post(const orc_model *md, const double *fs, const double *gs,
                           double *u, double *v, double *theta);
+/* Discrete adjoint (all forward states kept: small grids). J = mean over the last
+ * avg_last steps of the mean hot-wall Nu; gradients w.r.t. the hot-wall profile
+ * (ny values) and gbeta. f0/g0: initial post-collision state. */
+void orc_collide_vjp(const orc_model *md, const double x[14], const double lam[14], double nu[14],
+                     double *dgb);
+int orc_adjoint(const orc_model *md, int64_t nsteps, int64_t avg_last, const double *f0,
+                const double *g0, const double *theta_hot_prof, double *J, double *dJ_dthw,
+                double *dJ_dgbeta);
 int orc_set_threads(int n); /* OpenMP threads over rows; returns the count in use */
 int orc_abi_version(void);
 
