@@ -244,6 +244,28 @@ const char* dmrt_last_error(const dmrt_ctx* c);
 /* Release the context (not the caller's workspace). Synchronises. NULL is a no-op. */
 void dmrt_destroy(dmrt_ctx* c);
 
+/* ---- Discrete adjoint ---------------------------------------------------------
+ *
+ * Gradient of J = mean hot-wall Nusselt number (Eqs. 18-19) over the last
+ * avg_last of nsteps steps, with respect to the hot-wall temperature profile
+ * theta_w(j) (which enters Eq. 45 and the Nusselt stencil) and to Ra (which
+ * enters through the buoyancy scale of Eq. 27), by a hand-written reverse
+ * (transposed collide-stream) kernel: the exact adjoint of the discrete
+ * float32 step, with the gradients accumulated in float64. Memory: sqrt(N)
+ * checkpoints of the state plus a sqrt(N)-step segment that is recomputed from
+ * its checkpoint before being swept backwards.
+ *
+ * dmrt_adjoint starts from the context's current state and wall profiles,
+ * advances the context by nsteps (its state, step count and Nusselt ring are
+ * those of a dmrt_step(c, nsteps) call), and returns J, dJ/dtheta_w (host
+ * array [ny]) and dJ/dRa (each output nullable). Float32 storage only;
+ * nu_capacity >= avg_last. workspace: device memory of
+ * dmrt_adjoint_workspace_size() bytes, 256-byte aligned, used only during the
+ * call. Synchronises; DMRT_E_DIVERGED if the forward run diverged. */
+int dmrt_adjoint_workspace_size(const dmrt_ctx* c, int64_t nsteps, size_t* bytes);
+int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace, size_t workspace_bytes,
+                 double* J, double* dJ_dthetaw, double* dJ_dRa);
+
 /* ---- Batched sweep: many independent cavities per launch ----------------------
  *
  * Steps n independent side-heated cavities (any sizes and parameters, float32

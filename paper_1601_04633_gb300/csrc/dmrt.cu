@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dmrt.h"
+#include "adjoint.cuh"
 #include "step_direct.cuh"
 #include "step_tma.cuh"
 #include "tma_variants.h"
@@ -1242,6 +1243,157 @@ void dmrt_batch_destroy(dmrt_batch* b) {
         if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
     for (dmrt_ctx* c : b->sub) dmrt_destroy(c);
     delete b;
+}
+
+}  // extern "C"
+
+// ---- discrete adjoint ------------------------------------------------------------
+
+namespace {
+
+struct AdjLayout {
+    long long K, C;  // checkpoint interval and count
+    size_t state;    // bytes of one state
+    size_t off_ckpt, off_seg, off_nu0, off_nu1, off_dthw, off_misc, off_rows, total;
+};
+
+AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
+    AdjLayout L;
+    L.K = (long long)std::ceil(std::sqrt((double)N));
+    if (L.K < 1) L.K = 1;
+    L.C = (N + L.K - 1) / L.K;
+    L.state = align256((size_t)kPlanes * (size_t)c->L.plane * sizeof(float));
+    size_t o = 0;
+    L.off_ckpt = o; o += (size_t)L.C * L.state;
+    L.off_seg = o; o += (size_t)L.K * L.state;
+    L.off_nu0 = o; o += L.state;
+    L.off_nu1 = o; o += L.state;
+    L.off_dthw = o; o += align256((size_t)c->p.ny * sizeof(double));
+    L.off_misc = o; o += 256;
+    L.off_rows = o; o += align256((size_t)c->p.ny * sizeof(double) + 8);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dmrt_adjoint_workspace_size(const dmrt_ctx* c, int64_t nsteps, size_t* bytes) {
+    if (!c || !bytes || nsteps < 1) return DMRT_E_ARG;
+    *bytes = adjoint_layout(c, nsteps).total;
+    return DMRT_OK;
+}
+
+int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace, size_t workspace_bytes,
+                 double* J, double* dJ_dthetaw, double* dJ_dRa) {
+    if (!c) return DMRT_E_ARG;
+    if (nsteps < 1 || avg_last < 1 || avg_last > nsteps) {
+        set_err(c, "need 1 <= avg_last <= nsteps");
+        return DMRT_E_ARG;
+    }
+    if (c->p.storage != DMRT_FP32) {
+        set_err(c, "the adjoint needs float32 storage");
+        return DMRT_E_ARG;
+    }
+    if (avg_last > c->p.nu_capacity) {
+        set_err(c, "nu_capacity (%lld) must hold the %lld averaged steps", (long long)c->p.nu_capacity,
+                (long long)avg_last);
+        return DMRT_E_ARG;
+    }
+    const AdjLayout AL = adjoint_layout(c, nsteps);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < AL.total) {
+        set_err(c, "adjoint workspace: need %zu bytes, 256-byte aligned", AL.total);
+        return DMRT_E_SPACE;
+    }
+    char* w = static_cast<char*>(workspace);
+    auto ckpt = [&](long long q) { return reinterpret_cast<float*>(w + AL.off_ckpt + (size_t)q * AL.state); };
+    auto slot = [&](long long q) { return reinterpret_cast<float*>(w + AL.off_seg + (size_t)q * AL.state); };
+    const size_t copy_bytes = (size_t)kPlanes * (size_t)c->L.plane * sizeof(float);
+    const long long N = nsteps, K = AL.K;
+
+    // Forward pass with checkpoints every K steps; J from the Nusselt ring.
+    CK(cudaMemcpyAsync(ckpt(0), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    for (long long q = 0; q < AL.C; ++q) {
+        const long long n = std::min(K, N - q * K);
+        int rc = dmrt_step(c, n);
+        if (rc) return rc;
+        if (q + 1 < AL.C)
+            CK(cudaMemcpyAsync(ckpt(q + 1), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream),
+               "checkpoint");
+    }
+    std::vector<double> series((size_t)avg_last);
+    int64_t got = 0;
+    int rc = dmrt_nusselt(c, nullptr, nullptr, series.data(), avg_last, &got);
+    if (rc) return rc;
+    double jsum = 0.0;
+    for (int64_t q = 0; q < got; ++q) jsum += series[(size_t)q];
+    if (J) *J = jsum / (double)avg_last;
+
+    // Reverse sweep, segment by segment from the last.
+    float* nu_a = reinterpret_cast<float*>(w + AL.off_nu0);
+    float* nu_b = reinterpret_cast<float*>(w + AL.off_nu1);
+    double* dthw = reinterpret_cast<double*>(w + AL.off_dthw);
+    Misc* scratch = reinterpret_cast<Misc*>(w + AL.off_misc);
+    CK(cudaMemsetAsync(nu_a, 0, copy_bytes, c->stream), "zero adjoint");
+    CK(cudaMemsetAsync(w + AL.off_dthw, 0, AL.off_rows - AL.off_dthw, c->stream), "zero gradients");
+    double* dgb = &scratch->nu_last;  // the scratch block's double doubles as dJ/dgbeta
+    dmrt::StepArgs RA = step_args(c, 0);  // recompute: Nusselt output into scratch
+    RA.nu_rows = reinterpret_cast<double*>(w + AL.off_rows);
+    RA.nu_ring = reinterpret_cast<double*>(w + AL.off_rows) + c->p.ny;
+    RA.nu_last = RA.nu_ring;
+    RA.counter = &scratch->counter;
+    RA.err = &scratch->err;
+    RA.step_in = &scratch->step[0];
+    RA.step_out = &scratch->step[1];
+    RA.cap = 1;
+    dmrt::AdjArgs AA;
+    AA.hot = reinterpret_cast<const float*>(c->ws + c->L.off_hot);
+    AA.cold = reinterpret_cast<const float*>(c->ws + c->L.off_cold);
+    AA.dthw = dthw;
+    AA.dgbeta = dgb;
+    AA.plane = c->L.plane;
+    AA.nx = c->p.nx;
+    AA.ny = c->p.ny;
+    AA.pitch = c->L.pitch;
+    AA.nu_wall = (float)(-9.0 * c->sc.nu_scale / c->p.ny);
+    AA.nu_next = (float)(c->sc.nu_scale / c->p.ny);
+    AA.gather_only = 0;
+    const dim3 agrid((c->p.nx + 127) / 128, c->p.ny);
+    for (long long q = AL.C - 1; q >= 0; --q) {
+        const long long start = q * K, end = std::min(start + K, N), len = end - start;
+        for (long long t = 1; t < len; ++t) {  // s_{start + t} into slot t
+            RA.src = t == 1 ? ckpt(q) : slot(t - 1);
+            RA.dst = slot(t);
+            dmrt::step_direct_kernel<<<c->grid, dmrt::kDirectThreads, 0, c->stream>>>(RA, c->sc);
+        }
+        for (long long k = end; k > start; --k) {
+            AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(k - 1 - start);
+            AA.nu_in = nu_a;
+            AA.nu_out = nu_b;
+            AA.w = (k > N - avg_last) ? (float)(1.0 / (double)avg_last) : 0.f;
+            dmrt::adjoint_step_kernel<<<agrid, 128, 0, c->stream>>>(AA, c->sc);
+            std::swap(nu_a, nu_b);
+        }
+        CK(cudaGetLastError(), "adjoint launch");
+    }
+    AA.nu_in = nu_a;  // nu_1: the anti-bounce-back term of step 1
+    AA.gather_only = 1;
+    dmrt::adjoint_step_kernel<<<agrid, 128, 0, c->stream>>>(AA, c->sc);
+    CK(cudaGetLastError(), "adjoint launch");
+    std::vector<double> g((size_t)c->p.ny);
+    double dgbeta = 0.0;
+    CK(cudaMemcpyAsync(g.data(), dthw, g.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read dJ/dtheta_w");
+    CK(cudaMemcpyAsync(&dgbeta, dgb, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read dJ/dgbeta");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    // The Nusselt stencil's own theta_w term, 8 scale / ny per averaged step.
+    const double direct = 8.0 * c->sc.nu_scale / (double)c->p.ny;
+    if (dJ_dthetaw)
+        for (int j = 0; j < c->p.ny; ++j) dJ_dthetaw[j] = g[(size_t)j] + direct;
+    // gbeta = Ra nu alpha / (H^3 dT), so dJ/dRa = dJ/dgbeta * nu alpha / (H^3 dT).
+    const double H = (double)c->p.ny, dT = c->p.theta_hot - c->p.theta_cold;
+    if (dJ_dRa) *dJ_dRa = dT != 0.0 ? dgbeta * c->k.nu * c->k.alpha / (H * H * H * dT) : 0.0;
+    return dmrt_check(c);
 }
 
 }  // extern "C"

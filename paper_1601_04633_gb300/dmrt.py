@@ -115,6 +115,8 @@ SIGNATURES = {
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
+    "dmrt_adjoint_workspace_size": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _DP, _DP, _DP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
     "dmrt_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
@@ -354,6 +356,22 @@ class Cavity2D:
         dmrt_fields(self.h, ptrs[0], ptrs[1], ptrs[2], False)
         return tuple(out) if pinned is None else tuple(t.numpy() for t in pinned)
 
+    def adjoint(self, nsteps: int, avg_last: int):
+        """Advance nsteps and return (J, dJ/dtheta_w [ny], dJ/dRa): J = mean hot-wall Nu
+        over the last avg_last steps. The adjoint workspace is allocated with torch."""
+        import torch
+
+        nbytes = ctypes.c_size_t()
+        _check(load().dmrt_adjoint_workspace_size(self.h, int(nsteps), ctypes.byref(nbytes)), self.h)
+        ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        J = ctypes.c_double()
+        dth = np.zeros(self.ny)
+        dRa = ctypes.c_double()
+        _check(load().dmrt_adjoint(self.h, int(nsteps), int(avg_last), _VP(ws.data_ptr()), nbytes.value,
+                                   ctypes.byref(J), _dptr(dth), ctypes.byref(dRa)), self.h)
+        del ws
+        return J.value, dth, dRa.value
+
     def get_state(self) -> np.ndarray:
         """Post-collision populations [14][ny][nx] (f_1..f_9, g_1..g_5), float32."""
         return dmrt_get_state(self.h, self.nx, self.ny)
@@ -457,3 +475,39 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def _nusselt_objective_class():
+    import torch
+
+    class NusseltObjective(torch.autograd.Function):
+        """J(theta_w, Ra) = mean hot-wall Nusselt number over the last ``avg_last`` of
+        ``nsteps`` steps of a cavity started from ``cavity`` (an ``inputs.Cavity``), as
+        a differentiable function of the hot-wall profile theta_w [ny] and Ra; the
+        backward pass returns the discrete adjoint's gradients."""
+
+        @staticmethod
+        def forward(ctx, theta_w, Ra, cavity, nsteps, avg_last):
+            import copy
+
+            cav = copy.copy(cavity)
+            cav.Ra = float(Ra.detach().cpu())
+            cav.theta_hot_profile = theta_w.detach().cpu().double().numpy()
+            sim = Cavity2D.from_inputs(cav, nu_capacity=max(int(avg_last), 1))
+            J, dth, dRa = sim.adjoint(int(nsteps), int(avg_last))
+            sim.close()
+            ctx.save_for_backward(torch.as_tensor(dth, dtype=theta_w.dtype, device=theta_w.device),
+                                  torch.as_tensor(dRa, dtype=Ra.dtype, device=Ra.device))
+            return torch.as_tensor(J, dtype=theta_w.dtype, device=theta_w.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            dth, dRa = ctx.saved_tensors
+            return gJ * dth, gJ * dRa, None, None, None
+
+    return NusseltObjective
+
+
+def nusselt_objective(theta_w, Ra, cavity, nsteps: int, avg_last: int):
+    """Differentiable J(theta_w, Ra) (see ``NusseltObjective``)."""
+    return _nusselt_objective_class().apply(theta_w, Ra, cavity, nsteps, avg_last)

@@ -1,0 +1,110 @@
+"""Discrete adjoint on the GPU: gradients of the mean hot-wall Nusselt number with
+respect to the hot-wall temperature profile and Ra.
+
+Checked against the fp64 oracle adjoint (small grids, every component) and
+against central finite differences of the fp64 oracle forward run on the
+128 x 128, Ra = 1e5, Pr = 0.01 cavity with a perturbed hot-wall profile
+(h = 1e-3 absolute for theta_w, 1e-3 relative for Ra), to 1e-4 relative.
+The float32 forward and the fp64 finite differences differ by the float32
+trajectory error (~1e-6 of the fields), far inside that tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1601_04633_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def D():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1601_04633_gb300 import dmrt
+
+    return dmrt
+
+
+@pytest.mark.parametrize("nx,ny,Ra,steps,avg", [(24, 20, 1e5, 60, 20), (33, 17, 3e4, 45, 45), (300, 12, 2e3, 30, 7)])
+def test_adjoint_matches_oracle_adjoint(D, nx, ny, Ra, steps, avg):
+    cav = inputs.Cavity(nx, ny, Ra, 0.01, noise_amp=1e-2, seed=nx + ny)
+    cav.theta_hot_profile = 0.5 + 0.03 * np.sin(np.arange(ny))
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=steps)
+    J, dth, dRa = sim.adjoint(steps, avg)
+    sim.close()
+    m = O.derive(nx, ny, Ra, 0.01, 0.1)
+    f0, g0 = O.init(m, cav.theta0())
+    Jo, dtho, dgbo = O.adjoint(m, steps, avg, f0, g0, theta_hot_profile=cav.theta_hot_profile)
+    dRao = dgbo * m.gbeta / Ra
+    assert J == pytest.approx(Jo, rel=1e-5)
+    assert np.abs(dth - dtho).max() <= REL * np.abs(dtho).max()
+    assert dRa == pytest.approx(dRao, rel=REL)
+
+
+def test_adjoint_advances_like_a_forward_run(D):
+    cav = inputs.Cavity(130, 40, 1e5, 0.005, noise_amp=1e-3, seed=5)
+    a = D.Cavity2D.from_inputs(cav, nu_capacity=500)
+    b = D.Cavity2D.from_inputs(cav, nu_capacity=500)
+    J, _, _ = a.adjoint(301, 100)
+    b.step(301)
+    assert a.steps_done == b.steps_done == 301
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert J == pytest.approx(b.nusselt(100)[2].mean(), rel=1e-14)
+    a.close()
+    b.close()
+
+
+def test_adjoint_config_128_against_finite_differences(D):
+    # 128 x 128, Ra 1e5, Pr 0.01, hot wall 0.5 + 0.01 N(0, 1), 10000 steps, J over the last 2000.
+    cav = inputs.cavity_128_adjoint()
+    steps, avg = 10000, 2000
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=avg)
+    J, dth, dRa = sim.adjoint(steps, avg)
+    sim.close()
+    O.set_threads(0)
+    m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+    th0 = cav.theta0()
+
+    def Jo(profile, model=m):
+        return O.objective(model, steps, avg, th0, profile)
+
+    assert J == pytest.approx(Jo(cav.theta_hot_profile), rel=1e-5)
+    h = 1e-3
+    # A random direction in theta_w, and two single components.
+    v = inputs.normal(77, cav.ny)
+    v /= np.linalg.norm(v)
+    fd = (Jo(cav.theta_hot_profile + h * v) - Jo(cav.theta_hot_profile - h * v)) / (2 * h)
+    assert dth @ v == pytest.approx(fd, rel=REL)
+    for jrow in (3, 64):
+        e = np.zeros(cav.ny)
+        e[jrow] = 1.0
+        fd = (Jo(cav.theta_hot_profile + h * e) - Jo(cav.theta_hot_profile - h * e)) / (2 * h)
+        assert dth[jrow] == pytest.approx(fd, rel=REL, abs=REL * np.abs(dth).max())
+    mp = O.derive(cav.nx, cav.ny, cav.Ra * (1 + h), cav.Pr, cav.alpha)
+    mm = O.derive(cav.nx, cav.ny, cav.Ra * (1 - h), cav.Pr, cav.alpha)
+    fd = (Jo(cav.theta_hot_profile, mp) - Jo(cav.theta_hot_profile, mm)) / (2 * h * cav.Ra)
+    assert dRa == pytest.approx(fd, rel=REL)
+
+
+def test_autograd_function(D):
+    import torch
+
+    cav = inputs.Cavity(48, 40, 1e5, 0.01, noise_amp=1e-3, seed=8)
+    theta_w = torch.full((40,), 0.5, dtype=torch.float64, requires_grad=True)
+    Ra = torch.tensor(1e5, dtype=torch.float64, requires_grad=True)
+    J = D.nusselt_objective(theta_w, Ra, cav, 200, 50)
+    (2.0 * J).backward()
+    sim = D.Cavity2D.from_inputs(inputs.Cavity(48, 40, 1e5, 0.01, noise_amp=1e-3, seed=8), nu_capacity=50)
+    D.dmrt_set_wall_profiles(sim.h, hot=np.full(40, 0.5))
+    Jr, dth, dRa = sim.adjoint(200, 50)
+    sim.close()
+    assert float(J.detach()) == pytest.approx(Jr, rel=1e-12)
+    assert np.allclose(theta_w.grad.numpy(), 2.0 * dth, rtol=1e-12, atol=0)
+    assert float(Ra.grad) == pytest.approx(2.0 * dRa, rel=1e-12)
