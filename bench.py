@@ -334,7 +334,29 @@ def run_dmrt(args):
             "sequential_value": bnodes * bsteps / (ms_s / 1e3) / 1e6, "tile": tuned["opts"],
             "roofline_frac": bnodes * 112 / (ms_b / 1e3 / bsteps) / 1e9 / hbm_peak()[0],
             "nu_max_rel_diff_vs_sequential": max(abs(a - b_) / abs(b_) for a, b_ in zip(nu_b, nu_s)),
+            "tuner_trials": [{"tile": t["opts"], "mlups": round(t["mlups"])} for t in tuned["trials"]],
         }
+
+        # Discrete adjoint (128 x 128, Ra 1e5, Pr 0.01, hot wall 0.5 + 0.01 N(0,1), 10000 steps,
+        # J = mean Nu of the last 2000): wall time against the plain forward run.
+        acav = inputs.cavity_128_adjoint()
+        fwd = D.Cavity2D.from_inputs(acav, nu_capacity=2000)
+        fwd.step(16)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fwd.step(10000)
+        fwd.check()
+        t_fwd = time.perf_counter() - t0
+        fwd.close()
+        adj = D.Cavity2D.from_inputs(acav, nu_capacity=2000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Jv, dth, dRa = adj.adjoint(10000, 2000)
+        t_adj = time.perf_counter() - t0
+        adj.close()
+        secondary["adjoint"] = {"workload": "cavity 128x128 Ra 1e5 Pr 0.01, 10000 steps, J over last 2000",
+                                "forward_s": t_fwd, "adjoint_s": t_adj, "ratio": t_adj / t_fwd,
+                                "J": Jv, "dJ_dRa": dRa, "dJ_dthetaw_norm": float(np.linalg.norm(dth))}
 
     # End to end through the public C ABI with host buffers: create from a pinned
     # host temperature field (H2D), K steps, then the Nu series and the u, v, theta

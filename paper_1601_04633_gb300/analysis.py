@@ -4,9 +4,10 @@ The paper reports, for each case of Table 1 (Sec. 4), whether the mean Nusselt
 number reaches a steady value or oscillates, and for oscillating cases the
 mean, amplitude and period, with time measured by the Fourier number
 Fo = alpha t / H^2 (Eq. 20). This module computes those statistics from a
-per-step series. The period is the mean spacing of upward crossings, located
-by linear interpolation between steps: first of the window mean (or, if the
-record drifts too much for that, of its linear trend), then, to separate the
+per-step series. The period is that of the dominant spectral peak; a second
+estimate is the mean spacing of upward crossings, located by linear
+interpolation between steps: first of the window mean (or, if the record
+drifts too much for that, of its linear trend), then, to separate the
 oscillation from any slow wave or drift, of the moving average over one such
 period. The amplitude is half the peak-to-peak range of the oscillation about
 that moving average; the drift is the mean of the last fifth of the window
@@ -19,13 +20,41 @@ from dataclasses import dataclass, asdict
 import numpy as np
 
 
+def dominant_period(f, x, min_samples=5, max_fraction=1.0 / 3.0):
+    """Period (in the units of f) of the largest spectral peak of x(f): linear trend
+    removed, Hann window, zero-padded 8x FFT, parabolic interpolation of the
+    log-magnitude around the peak. Periods shorter than ``min_samples`` samples
+    or longer than ``max_fraction`` of the record are ignored. None if no peak."""
+    x = np.asarray(x, dtype=np.float64)
+    n = len(x)
+    if n < 16:
+        return None
+    dt = float(f[1] - f[0])
+    t = np.arange(n)
+    x = x - np.polyval(np.polyfit(t, x, 1), t)
+    X = np.abs(np.fft.rfft(x * np.hanning(n), n=8 * n))
+    fr = np.fft.rfftfreq(8 * n, d=dt)
+    ok = (fr > 1.0 / (max_fraction * n * dt)) & (fr < 1.0 / (min_samples * dt))
+    if not ok.any() or X[ok].max() <= 0:
+        return None
+    k = int(np.nonzero(ok)[0][np.argmax(X[ok])])
+    if 0 < k < len(X) - 1 and X[k - 1] > 0 and X[k + 1] > 0:
+        a, b, c = np.log(X[k - 1]), np.log(X[k]), np.log(X[k + 1])
+        shift = 0.5 * (a - c) / (a - 2 * b + c) if (a - 2 * b + c) != 0 else 0.0
+    else:
+        shift = 0.0
+    freq = fr[k] + shift * (fr[1] - fr[0])
+    return float(1.0 / freq) if freq > 0 else None
+
+
 @dataclass
 class NuStats:
     steady: bool
     mean: float
     amplitude: float          # half the peak-to-peak range of the oscillation
     peak_to_peak: float
-    period_fo: float | None   # in Fourier-number units; None when steady or undetermined
+    period_fo: float | None   # dominant spectral period in Fo; None when steady
+    crossing_period_fo: float | None  # mean spacing of upward crossings (see above)
     cycles: int               # complete cycles seen in the window
     window_fo: tuple          # (start, end) of the analysed window in Fo
     drift: float              # mean of the last fifth of the window minus the first fifth
@@ -49,11 +78,12 @@ def _crossing_period(f, d):
 
 
 def nu_statistics(series, fo_per_step: float, window_fo: float | None = None,
-                  steady_tol: float = 1e-4) -> NuStats:
+                  steady_tol: float = 1e-3) -> NuStats:
     """Statistics of Nu over the last ``window_fo`` Fourier units of ``series``.
 
-    series[k] is the mean Nu after step k + 1. The record counts as steady when its
-    peak-to-peak range over the window is below ``steady_tol`` times the mean.
+    series[k] is the mean Nu after step k + 1. The record counts as steady when the
+    peak-to-peak range of its residual about a cubic fit over the window is below
+    ``steady_tol`` times the mean (a settled or monotonically settling record).
     """
     nu = np.asarray(series, dtype=np.float64)
     n = len(nu)
@@ -68,7 +98,11 @@ def nu_statistics(series, fo_per_step: float, window_fo: float | None = None,
     f = fo[start:]
     mean = float(w.mean())
     p2p = float(w.max() - w.min())
-    steady = p2p <= steady_tol * abs(mean)
+    tt = (f - f[0]) / max(f[-1] - f[0], 1e-300)
+    resid = w - np.polyval(np.polyfit(tt, w, 3), tt)
+    # steady, or converging without oscillating: the record leaves only a tiny
+    # residual about a smooth (cubic) trend over the window
+    steady = float(resid.max() - resid.min()) <= steady_tol * abs(mean)
     fifth = max(1, len(w) // 5)
     drift = float(w[-fifth:].mean() - w[:fifth].mean())
     period, cycles, amplitude = None, 0, 0.5 * p2p
@@ -90,6 +124,7 @@ def nu_statistics(series, fo_per_step: float, window_fo: float | None = None,
                 if p2 is not None:
                     period, cycles = p2, c2
                     amplitude = 0.5 * float((seg - ma).max() - (seg - ma).min())
-    return NuStats(steady=bool(steady), mean=mean, amplitude=amplitude, peak_to_peak=p2p,
-                   period_fo=period, cycles=cycles, window_fo=(float(f[0]), float(f[-1])),
-                   drift=drift)
+    spectral = None if steady else dominant_period(f, w)
+    return NuStats(steady=bool(steady), mean=mean, amplitude=amplitude if not steady else 0.0,
+                   peak_to_peak=p2p, period_fo=spectral, crossing_period_fo=period if not steady else None,
+                   cycles=cycles if not steady else 0, window_fo=(float(f[0]), float(f[-1])), drift=drift)
