@@ -33,8 +33,13 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS (both lattices) & % HBM roofline; batched/FP16 vs plain FP32 at Nu err≤1e-3"
 UNIT = "MLUPS"
 BYTES_PER_NODE_FP32 = 112  # 14 populations read + 14 written, 4 bytes each
-STORAGES = {"fp32": 0, "fp16": 1, "bf16": 2}
-BYTES_PER_NODE = {"fp32": 112, "fp16": 56, "bf16": 56}
+# storage mode -> (storage, rounding); bytes moved per node and step (read + write)
+STORAGES = {"fp32": (0, 0), "fp16": (1, 0), "bf16": (2, 0), "fp16_sr": (1, 1), "bf16_sr": (2, 1),
+            "mixed": (3, 0), "mixed_sr": (3, 1)}
+BYTES_PER_NODE = {"fp32": 112, "fp16": 56, "bf16": 56, "fp16_sr": 56, "bf16_sr": 56, "mixed": 76,
+                  "mixed_sr": 76}
+# Tiles (nodes per thread, rows, stages) of the secondary storage runs.
+SECONDARY_TILES = {"fp16": (4, 4, 2), "bf16": (4, 4, 2), "fp16_sr": (4, 4, 2), "mixed_sr": (1, 4, 2)}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_4096x4096.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", f)
@@ -238,7 +243,7 @@ def run_dmrt(args):
     stream = torch.cuda.current_stream()
 
     kw = dict(kernel=args.kernel, tma_rows=args.tma_rows, tma_stages=args.tma_stages,
-              tma_npt=args.tma_npt, storage=STORAGES[args.storage])
+              tma_npt=args.tma_npt, storage=STORAGES[args.storage][0], rounding=STORAGES[args.storage][1])
     sim = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1), **kw)
     launch = dict(sim.launch)
     sim.step(args.warmup)
@@ -266,13 +271,14 @@ def run_dmrt(args):
     sim.close()
     del sim
 
-    # Secondary: the 16-bit storage variants on the same workload and step count,
-    # timed the same way, with their mean Nusselt number against this run's.
+    # Secondary: the 16-bit and mixed storage variants on the same workload and
+    # step count, timed the same way, with their mean Nusselt number against this run's.
     secondary = {}
     if not args.no_secondary and args.storage == "fp32":
-        for st in ("fp16", "bf16"):
+        for st, (npt, rows, stages) in SECONDARY_TILES.items():
             s2 = D.Cavity2D.from_inputs(cav, nu_capacity=max(args.steps + args.warmup, 1),
-                                        storage=STORAGES[st], kernel=2, tma_npt=4, tma_rows=4, tma_stages=2)
+                                        storage=STORAGES[st][0], rounding=STORAGES[st][1], kernel=2,
+                                        tma_npt=npt, tma_rows=rows, tma_stages=stages)
             s2.step(args.warmup)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -49,10 +49,14 @@ extern "C" {
 #define DMRT_E_SPACE (-6)    /* workspace or host buffer too small */
 #define DMRT_E_STATE (-7)    /* checkpoint does not match this context */
 
-/* Population storage precision. */
+/* Population storage precision. MIXED: the flow populations f in float16 and
+ * the thermal populations g in float32 (38 bytes per node and buffer instead of
+ * 56); the rounding mode applies to the float16 flow stores. 16-bit and mixed
+ * storage have no counterpart in the paper (which stores double). */
 #define DMRT_FP32 0
 #define DMRT_FP16 1
 #define DMRT_BF16 2
+#define DMRT_MIXED 3
 
 /* Rounding of 16-bit population stores. NEAREST: round to nearest even.
  * STOCHASTIC: round up with probability equal to the distance to the lower
@@ -72,7 +76,10 @@ extern "C" {
  * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
  * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)
  * (4,2); NPT 1 with (1,2) (1,3) (1,4) (1,5) (2,2) (2,3) (3,2) (4,2) (4,3).
- * Default (1, 4, 2). */
+ * Default (1, 4, 2). FP16 / BF16 storage, rounding to nearest: (1,1,2)
+ * (1,2,2) (1,4,2) (1,4,3) (1,4,4) (2,2,2) (2,4,2) (2,4,3) (4,4,2); stochastic:
+ * (1,1,2) (1,4,2) (2,2,2) (4,4,2). MIXED storage, nearest: (1,1,2) (1,2,2)
+ * (1,4,2) (2,2,2); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,2,2) (2,4,2). */
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
@@ -95,14 +102,15 @@ typedef struct {
     double theta_init;  /* uniform initial temperature when no field is given */
     int32_t left_wall;  /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
-    int32_t storage;    /* DMRT_FP32, DMRT_FP16 or DMRT_BF16 (16-bit storage runs the
-                           TMA kernel; arithmetic is float32 in every case) */
+    int32_t storage;    /* DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (16-bit and mixed
+                           storage run the TMA kernel; arithmetic is float32 in every case) */
     int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
     int32_t tma_rows;   /* TMA kernel: rows per work item (0 = default 4) */
     int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default 2) */
     int32_t tma_npt;    /* TMA kernel: nodes per thread, 4, 2 or 1 (0 = default 1) */
-    int32_t rounding;   /* 16-bit storage: DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC */
+    int32_t rounding;   /* 16-bit stores (all populations for FP16 / BF16, the flow
+                           populations for MIXED): DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC */
 } dmrt_params;
 
 /* Constants derived from dmrt_params (Eqs. 9, 31-32, 38-40, 43, 45). */

@@ -31,20 +31,24 @@ thread_local char g_create_error[256] = "";
 struct Layout {
     int pitch;            // elements per row (multiple of 128)
     long long plane;      // elements per plane
-    size_t buf_bytes;     // one population buffer (14 planes)
+    size_t buf_bytes;     // one population buffer (14 planes; mixed storage: 9 float16
+                          // flow planes, then 5 float32 thermal planes)
     size_t off_a, off_b, off_hot, off_cold, off_rows, off_ring, off_misc;
     size_t total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-int elem_bytes(int storage) { return storage == DMRT_FP32 ? 4 : 2; }
+// Bytes per stored flow (f) and thermal (g) population.
+int f_bytes(int storage) { return storage == DMRT_FP32 ? 4 : 2; }
+int g_bytes(int storage) { return storage == DMRT_FP32 || storage == DMRT_MIXED ? 4 : 2; }
+bool g_16bit(int storage) { return storage == DMRT_FP16 || storage == DMRT_BF16; }
 
 Layout make_layout(const dmrt_params& p) {
     Layout L;
     L.pitch = ((p.nx + 127) / 128) * 128;
     L.plane = (long long)p.ny * L.pitch;
-    L.buf_bytes = align256((size_t)kPlanes * (size_t)L.plane * elem_bytes(p.storage));
+    L.buf_bytes = align256((size_t)L.plane * (9 * f_bytes(p.storage) + 5 * g_bytes(p.storage)));
     size_t o = 0;
     L.off_a = o; o += L.buf_bytes;
     L.off_b = o; o += L.buf_bytes;
@@ -91,7 +95,7 @@ struct dmrt_ctx {
     int tma_grid;
     size_t tma_smem;
     const void* tma_func;
-    CUtensorMap map6[2], map4[2];  // per source buffer: 6-plane and 4-plane boxes
+    CUtensorMap maps[2][3];  // per source buffer: the step kernel's three tensor maps
     cudaGraphExec_t graph[2];
     int graph_len;
     char err[256];
@@ -161,14 +165,32 @@ __device__ __forceinline__ __half elem_from_f<__half>(float x) { return __float2
 template <>
 __device__ __forceinline__ __nv_bfloat16 elem_from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
+// Flow and thermal plane bases of a population buffer in layout L.
+template <typename L, typename B>
+__device__ __forceinline__ auto* f_base(B* S) {
+    using Ef = typename L::Ef;
+    using T = typename std::conditional<std::is_const<B>::value, const Ef, Ef>::type;
+    return reinterpret_cast<T*>(S);
+}
+template <typename L, typename B>
+__device__ __forceinline__ auto* g_base(B* S, long long plane) {
+    using Eg = typename L::Eg;
+    using T = typename std::conditional<std::is_const<B>::value, const Eg, Eg>::type;
+    return reinterpret_cast<T*>(S + (L::kSplit ? (size_t)9 * plane * sizeof(typename L::Ef) : 0));
+}
+
 // Initial post-collision state: f = 0 (rest, delta-rho = 0) and g at the D2Q5
 // equilibrium of theta0 at rest, g_0 = (1 - a) theta / 5, g_1..4 = (4 + a) theta / 20
-// (Eq. 42 mapped back through N), stored minus sh0 / sh1 (16-bit storage
+// (Eq. 42 mapped back through N), stored minus sh0 / sh1 (16-bit thermal storage
 // shift; 0 for float32). Also zeroes the padding columns.
-template <typename E>
-__global__ void init_kernel(E* __restrict__ S, const double* __restrict__ theta0, double theta_const,
+template <typename L>
+__global__ void init_kernel(unsigned char* __restrict__ S, const double* __restrict__ theta0, double theta_const,
                             double a, double sh0, double sh1, int nx, int ny, int pitch,
                             long long plane) {
+    using Ef = typename L::Ef;
+    using Eg = typename L::Eg;
+    Ef* Sf = f_base<L>(S);
+    Eg* Sg = g_base<L>(S, plane);
     const long long n = (long long)ny * pitch;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
@@ -176,29 +198,31 @@ __global__ void init_kernel(E* __restrict__ S, const double* __restrict__ theta0
         double th = 0.0;
         const bool in = i < nx;
         if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
-        for (int k = 0; k < 9; ++k) S[plane_f(k) * plane + q] = elem_from_f<E>(0.f);
-        S[plane_g(0) * plane + q] = elem_from_f<E>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
+        for (int k = 0; k < 9; ++k) Sf[L::pf(k) * plane + q] = elem_from_f<Ef>(0.f);
+        Sg[L::pg(0) * plane + q] = elem_from_f<Eg>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
         const float side = in ? (float)((4.0 + a) * th / 20.0 - sh1) : 0.f;
-        for (int k = 1; k < 5; ++k) S[plane_g(k) * plane + q] = elem_from_f<E>(side);
+        for (int k = 1; k < 5; ++k) Sg[L::pg(k) * plane + q] = elem_from_f<Eg>(side);
     }
 }
 
 // Macroscopic fields of a post-collision state at the same time level:
 // theta = sum g* (the thermal collision keeps theta), u = sum e f*, and
 // v = sum e_y f* - G_y(theta) (the force added rho0 G to the momentum).
-template <typename E>
-__global__ void fields_kernel(const E* __restrict__ S, float* __restrict__ u,
+template <typename L>
+__global__ void fields_kernel(const unsigned char* __restrict__ S, float* __restrict__ u,
                               float* __restrict__ v, float* __restrict__ th, int nx, int ny,
                               int pitch, long long plane, float gbeta, float theta_ref,
                               float sh0, float sh1) {
+    const auto* Sf = f_base<L>(S);
+    const auto* Sg = g_base<L>(S, plane);
     const long long n = (long long)nx * ny;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(q / nx), i = (int)(q % nx);
         const long long s = (long long)j * pitch + i;
         float f[9], g[5];
-        for (int k = 0; k < 9; ++k) f[k] = elem_to_f(S[plane_f(k) * plane + s]);
-        for (int k = 0; k < 5; ++k) g[k] = elem_to_f(S[plane_g(k) * plane + s]) + (k == 0 ? sh0 : sh1);
+        for (int k = 0; k < 9; ++k) f[k] = elem_to_f(Sf[L::pf(k) * plane + s]);
+        for (int k = 0; k < 5; ++k) g[k] = elem_to_f(Sg[L::pg(k) * plane + s]) + (k == 0 ? sh0 : sh1);
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
         const float t = g[0] + g[1] + g[2] + g[3] + g[4];
@@ -240,7 +264,7 @@ __global__ void fill_kernel(float* p, const double* src, double value, int n) {
 // Host state arrays are ordered f_1..f_9, g_1..g_5; the device planes are grouped.
 int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
 
-// Call fn with a value of the storage element type (float, __half, __nv_bfloat16).
+// Call fn with a value of the element type of a one-type storage (float, __half, __nv_bfloat16).
 template <typename Fn>
 void with_elem(int storage, Fn&& fn) {
     if (storage == DMRT_FP16)
@@ -251,12 +275,38 @@ void with_elem(int storage, Fn&& fn) {
         fn(float{});
 }
 
+// Call fn with the population layout of a storage mode.
+template <typename Fn>
+void with_layout(int storage, Fn&& fn) {
+    if (storage == DMRT_FP16)
+        fn(dmrt::OneType<__half>{});
+    else if (storage == DMRT_BF16)
+        fn(dmrt::OneType<__nv_bfloat16>{});
+    else if (storage == DMRT_MIXED)
+        fn(dmrt::Split<__half, float>{});
+    else
+        fn(dmrt::OneType<float>{});
+}
+
+// Byte offset of host-order plane k (f_1..f_9, g_1..g_5) in a population
+// buffer, and the one-type storage its elements have.
+size_t plane_offset(const dmrt_params& p, long long plane, int k) {
+    if (p.storage == DMRT_MIXED)
+        return k < 9 ? (size_t)dmrt::split_f(k) * plane * 2
+                     : (size_t)9 * plane * 2 + (size_t)dmrt::split_g(k - 9) * plane * 4;
+    return (size_t)host_plane(k) * plane * f_bytes(p.storage);
+}
+int plane_storage(const dmrt_params& p, int k) {
+    if (p.storage == DMRT_MIXED) return k < 9 ? DMRT_FP16 : DMRT_FP32;
+    return p.storage;
+}
+
 constexpr int kDefaultNpt = 1, kDefaultR = 4, kDefaultS = 2;
 
 const dmrt::TmaVariant* find_tma_variant(int storage, int rounding, int npt, int R, int S) {
-    const dmrt::TmaVariant* (*lists[5])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
+    const dmrt::TmaVariant* (*lists[6])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
                                                 dmrt::tma_variants_npt1, dmrt::tma_variants_fp16,
-                                                dmrt::tma_variants_bf16};
+                                                dmrt::tma_variants_bf16, dmrt::tma_variants_mixed};
     for (auto list : lists) {
         int n = 0;
         const dmrt::TmaVariant* v = list(&n);
@@ -281,19 +331,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// 3-D view {pitch, ny, 14} of one population buffer with boxes {256, R, planes}.
-int encode_map(dmrt_ctx* c, CUtensorMap* m, float* base, int planes, int rows, int width = dmrt::kTmaBox) {
+// 3-D view {pitch, ny, nplanes} of planes of element type `storage` (FP32,
+// FP16 or BF16) starting at base, with boxes {width, rows, planes}.
+int encode_map(dmrt_ctx* c, CUtensorMap* m, void* base, int storage, int nplanes, int planes, int rows,
+               int width = dmrt::kTmaBox) {
     auto enc = tensor_map_encoder();
     if (!enc) {
         set_err(c, "cuTensorMapEncodeTiled is not available from the driver");
         return DMRT_E_CUDA;
     }
-    cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->p.ny, (cuuint64_t)kPlanes};
-    const int eb = elem_bytes(c->p.storage);
+    cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->p.ny, (cuuint64_t)nplanes};
+    const int eb = f_bytes(storage);
     cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * eb, (cuuint64_t)c->L.plane * eb};
-    const CUtensorMapDataType dt = c->p.storage == DMRT_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                   : c->p.storage == DMRT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const CUtensorMapDataType dt = storage == DMRT_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : storage == DMRT_FP16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     cuuint32_t box[3] = {(cuuint32_t)width, (cuuint32_t)rows, (cuuint32_t)planes};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = enc(m, dt, 3, base, dims, strides, box, estr,
@@ -323,7 +375,7 @@ int setup_kernel(dmrt_ctx* c) {
                    ? DMRT_KERNEL_TMA
                    : DMRT_KERNEL_DIRECT;
     if (want == DMRT_KERNEL_DIRECT && p.storage != DMRT_FP32) {
-        set_err(c, "the direct kernel stores float32 only; 16-bit storage runs the TMA kernel");
+        set_err(c, "the direct kernel stores float32 only; 16-bit and mixed storage run the TMA kernel");
         return DMRT_E_ARG;
     }
     c->kernel = want;
@@ -344,10 +396,11 @@ int setup_kernel(dmrt_ctx* c) {
         set_err(c, "TMA kernel needs ny >= %d", R);
         return DMRT_E_ARG;
     }
-    const int strip = dmrt::tma_strip(elem_bytes(p.storage));
+    const int fb = f_bytes(p.storage), gb = g_bytes(p.storage);
+    const int strip = dmrt::tma_strip(std::min(fb, gb));
     c->geo.n_strips = (p.nx + strip - 1) / strip;
     c->geo.n_rowblocks = (p.ny + R - 1) / R;
-    c->tma_smem = dmrt::tma_smem_bytes(R, S, elem_bytes(p.storage));
+    c->tma_smem = dmrt::tma_smem_bytes_fg(R, S, fb, gb);
     CK(cudaFuncSetAttribute(c->tma_func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->tma_smem),
        "set TMA kernel shared memory");
     int dev = 0, sms = 0, per_sm = 0;
@@ -362,9 +415,19 @@ int setup_kernel(dmrt_ctx* c) {
     const long long items = (long long)c->geo.n_strips * c->geo.n_rowblocks;
     c->tma_grid = (int)std::min<long long>(items, (long long)sms * per_sm);
     for (int b = 0; b < 2; ++b) {
-        int rc = encode_map(c, &c->map6[b], buf(c, b), 6, c->R);
-        if (rc) return rc;
-        rc = encode_map(c, &c->map4[b], buf(c, b), 4, c->R);
+        CUtensorMap* m = c->maps[b];
+        int rc;
+        if (p.storage == DMRT_MIXED) {
+            // 9 float16 flow planes, then 5 float32 thermal planes.
+            char* g = reinterpret_cast<char*>(buf(c, b)) + (size_t)9 * c->L.plane * 2;
+            rc = encode_map(c, &m[0], buf(c, b), DMRT_FP16, 9, 3, c->R);
+            if (!rc) rc = encode_map(c, &m[1], g, DMRT_FP32, 5, 3, c->R);
+            if (!rc) rc = encode_map(c, &m[2], g, DMRT_FP32, 5, 1, c->R);
+        } else {
+            rc = encode_map(c, &m[0], buf(c, b), p.storage, kPlanes, 6, c->R);
+            if (!rc) rc = encode_map(c, &m[1], buf(c, b), p.storage, kPlanes, 4, c->R);
+            m[2] = m[1];
+        }
         if (rc) return rc;
     }
     return DMRT_OK;
@@ -391,8 +454,8 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "wall kinds must be DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC");
         return DMRT_E_ARG;
     }
-    if (p->storage != DMRT_FP32 && p->storage != DMRT_FP16 && p->storage != DMRT_BF16) {
-        set_err(c, "storage must be DMRT_FP32, DMRT_FP16 or DMRT_BF16 (got %d)", p->storage);
+    if (p->storage < DMRT_FP32 || p->storage > DMRT_MIXED) {
+        set_err(c, "storage must be DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (got %d)", p->storage);
         return DMRT_E_ARG;
     }
     if (p->rounding != DMRT_ROUND_NEAREST && p->rounding != DMRT_ROUND_STOCHASTIC) {
@@ -400,7 +463,7 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         return DMRT_E_ARG;
     }
     if (p->rounding == DMRT_ROUND_STOCHASTIC && p->storage == DMRT_FP32) {
-        set_err(c, "stochastic rounding applies to 16-bit storage only");
+        set_err(c, "stochastic rounding applies to 16-bit and mixed storage only");
         return DMRT_E_ARG;
     }
     if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_TMA) {
@@ -539,9 +602,9 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     s.abb = (float)k.abb;
     s.left_fixed = p->left_wall == DMRT_WALL_FIXED;
     s.right_fixed = p->right_wall == DMRT_WALL_FIXED;
-    // 16-bit storage keeps g_i - w_i theta_ref (w_0 = (1-a)/5, w_1..4 = (4+a)/20).
-    const double sh0 = p->storage == DMRT_FP32 ? 0.0 : (1.0 - k.a) / 5.0 * p->theta_ref;
-    const double sh1 = p->storage == DMRT_FP32 ? 0.0 : (4.0 + k.a) / 20.0 * p->theta_ref;
+    // 16-bit thermal storage keeps g_i - w_i theta_ref (w_0 = (1-a)/5, w_1..4 = (4+a)/20).
+    const double sh0 = g_16bit(p->storage) ? (1.0 - k.a) / 5.0 * p->theta_ref : 0.0;
+    const double sh1 = g_16bit(p->storage) ? (4.0 + k.a) / 20.0 * p->theta_ref : 0.0;
     s.gsh0 = (float)sh0;
     s.gsh1 = (float)sh1;
     const double dT = p->theta_hot - p->theta_cold;
@@ -571,21 +634,22 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
         reinterpret_cast<float*>(c->ws + L.off_cold), nullptr, p->theta_cold, p->ny);
     const double* d_theta0 = nullptr;
     if (theta0) {
-        // Stage the host field in buffer B (not yet used: it holds 28 or 56 bytes per node).
+        // Stage the host field in buffer B (not yet used: it holds 28 to 56 bytes per node).
         double* stage = reinterpret_cast<double*>(c->ws + L.off_b);
         cudaError_t e = cudaMemcpyAsync(stage, theta0, (size_t)p->nx * p->ny * sizeof(double),
                                         cudaMemcpyHostToDevice, c->stream);
         if (e != cudaSuccess) return fail(cuda_fail(c, e, "copy theta0"));
         d_theta0 = stage;
     }
-    with_elem(p->storage, [&](auto tag) {
-        using E = decltype(tag);
-        init_kernel<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<E*>(buf(c, 0)), d_theta0,
-                                                    p->theta_init, k.a, sh0, sh1, p->nx, p->ny,
-                                                    L.pitch, L.plane);
+    with_layout(p->storage, [&](auto tag) {
+        using Lt = decltype(tag);
+        init_kernel<Lt><<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 0)), d_theta0,
+                                                     p->theta_init, k.a, sh0, sh1, p->nx, p->ny,
+                                                     L.pitch, L.plane);
         // Buffer B's padding columns must read as zero too.
-        init_kernel<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<E*>(buf(c, 1)), nullptr, p->theta_ref,
-                                                    k.a, sh0, sh1, p->nx, p->ny, L.pitch, L.plane);
+        init_kernel<Lt><<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 1)), nullptr,
+                                                     p->theta_ref, k.a, sh0, sh1, p->nx, p->ny, L.pitch,
+                                                     L.plane);
     });
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init kernels"));
@@ -599,7 +663,7 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
 static int launch_step(dmrt_ctx* c, int from) {
     dmrt::StepArgs A = step_args(c, from);
     if (c->kernel == DMRT_KERNEL_TMA) {
-        void* params[5] = {&c->map6[from], &c->map4[from], &A, &c->sc, &c->geo};
+        void* params[6] = {&c->maps[from][0], &c->maps[from][1], &c->maps[from][2], &A, &c->sc, &c->geo};
         cudaError_t e = cudaLaunchKernel(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), params,
                                          c->tma_smem, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "TMA step launch");
@@ -628,7 +692,8 @@ static int build_graph(dmrt_ctx* c, int from) {
         const int src = (i & 1) ? 1 - from : from;
         cudaKernelNodeParams kp = {};
         void* dparams[2] = {&args[i & 1], &c->sc};
-        void* tparams[5] = {&c->map6[src], &c->map4[src], &args[i & 1], &c->sc, &c->geo};
+        void* tparams[6] = {&c->maps[src][0], &c->maps[src][1], &c->maps[src][2], &args[i & 1], &c->sc,
+                            &c->geo};
         if (c->kernel == DMRT_KERNEL_TMA) {
             kp.func = const_cast<void*>(c->tma_func);
             kp.gridDim = dim3(c->tma_grid);
@@ -708,11 +773,11 @@ int dmrt_fields(dmrt_ctx* c, float* u, float* v, float* theta, int on_device) {
         dt = theta ? stage + 2 * n : nullptr;
     }
     const int blocks = (int)std::min<long long>((n + 255) / 256, 152 * 16);
-    with_elem(p.storage, [&](auto tag) {
-        using E = decltype(tag);
-        fields_kernel<E><<<blocks, 256, 0, c->stream>>>(reinterpret_cast<const E*>(buf(c, c->cur)), du, dv,
-                                                        dt, p.nx, p.ny, c->L.pitch, c->L.plane, c->sc.gbeta,
-                                                        c->sc.theta_ref, c->sc.gsh0, c->sc.gsh1);
+    with_layout(p.storage, [&](auto tag) {
+        using Lt = decltype(tag);
+        fields_kernel<Lt><<<blocks, 256, 0, c->stream>>>(reinterpret_cast<const unsigned char*>(buf(c, c->cur)),
+                                                         du, dv, dt, p.nx, p.ny, c->L.pitch, c->L.plane,
+                                                         c->sc.gbeta, c->sc.theta_ref, c->sc.gsh0, c->sc.gsh1);
     });
     CK(cudaGetLastError(), "fields kernel");
     if (!on_device) {
@@ -785,9 +850,9 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold) {
 }
 
 // Copy between a dense host array [14][ny][nx] of float32 and the padded
-// device planes of the current state. float32 storage: one 2D copy per plane.
-// 16-bit storage: one plane at a time is converted through the idle buffer
-// (which holds 28 bytes per node, a float32 plane needs 4).
+// device planes of the current state. A float32 plane: one 2D copy. A 16-bit
+// plane: converted through the idle buffer (which holds at least 28 bytes per
+// node; a float32 plane needs 4).
 static float plane_shift(const dmrt_ctx* c, int host_k) {
     return host_k < 9 ? 0.f : (host_k == 9 ? c->sc.gsh0 : c->sc.gsh1);
 }
@@ -796,27 +861,25 @@ int dmrt_get_state(dmrt_ctx* c, float* host) {
     if (!c || !host) return DMRT_E_ARG;
     const dmrt_params& p = c->p;
     const size_t n = (size_t)p.nx * p.ny;
-    if (p.storage == DMRT_FP32) {
-        const float* S = buf(c, c->cur);
-        for (int k = 0; k < kPlanes; ++k)
-            CK(cudaMemcpy2DAsync(host + (size_t)k * n, (size_t)p.nx * sizeof(float),
-                                 S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
-                                 (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyDeviceToHost, c->stream),
+    float* stage = buf(c, 1 - c->cur);
+    for (int k = 0; k < kPlanes; ++k) {
+        const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        const int st = plane_storage(p, k);
+        if (st == DMRT_FP32) {
+            CK(cudaMemcpy2DAsync(host + (size_t)k * n, (size_t)p.nx * sizeof(float), P,
+                                 (size_t)c->L.pitch * sizeof(float), (size_t)p.nx * sizeof(float), p.ny,
+                                 cudaMemcpyDeviceToHost, c->stream),
                "copy state to host");
-    } else {
-        float* stage = buf(c, 1 - c->cur);
-        for (int k = 0; k < kPlanes; ++k) {
-            with_elem(p.storage, [&](auto tag) {
-                using E = decltype(tag);
-                const E* P = reinterpret_cast<const E*>(buf(c, c->cur)) + (size_t)host_plane(k) * c->L.plane;
-                plane_to_f32<E><<<1024, 256, 0, c->stream>>>(P, stage, p.nx, p.ny, c->L.pitch,
-                                                             plane_shift(c, k));
-            });
-            CK(cudaGetLastError(), "state conversion");
-            CK(cudaMemcpyAsync(host + (size_t)k * n, stage, n * sizeof(float), cudaMemcpyDeviceToHost,
-                               c->stream),
-               "copy state to host");
+            continue;
         }
+        with_elem(st, [&](auto tag) {
+            using E = decltype(tag);
+            plane_to_f32<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<const E*>(P), stage, p.nx, p.ny,
+                                                         c->L.pitch, plane_shift(c, k));
+        });
+        CK(cudaGetLastError(), "state conversion");
+        CK(cudaMemcpyAsync(host + (size_t)k * n, stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+           "copy state to host");
     }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DMRT_OK;
@@ -826,27 +889,25 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
     if (!c || !host) return DMRT_E_ARG;
     const dmrt_params& p = c->p;
     const size_t n = (size_t)p.nx * p.ny;
-    if (p.storage == DMRT_FP32) {
-        float* S = buf(c, c->cur);
-        for (int k = 0; k < kPlanes; ++k)
-            CK(cudaMemcpy2DAsync(S + (size_t)host_plane(k) * c->L.plane, (size_t)c->L.pitch * sizeof(float),
-                                 host + (size_t)k * n, (size_t)p.nx * sizeof(float),
-                                 (size_t)p.nx * sizeof(float), p.ny, cudaMemcpyHostToDevice, c->stream),
+    float* stage = buf(c, 1 - c->cur);
+    for (int k = 0; k < kPlanes; ++k) {
+        char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        const int st = plane_storage(p, k);
+        if (st == DMRT_FP32) {
+            CK(cudaMemcpy2DAsync(P, (size_t)c->L.pitch * sizeof(float), host + (size_t)k * n,
+                                 (size_t)p.nx * sizeof(float), (size_t)p.nx * sizeof(float), p.ny,
+                                 cudaMemcpyHostToDevice, c->stream),
                "copy state to device");
-    } else {
-        float* stage = buf(c, 1 - c->cur);
-        for (int k = 0; k < kPlanes; ++k) {
-            CK(cudaMemcpyAsync(stage, host + (size_t)k * n, n * sizeof(float), cudaMemcpyHostToDevice,
-                               c->stream),
-               "copy state to device");
-            with_elem(p.storage, [&](auto tag) {
-                using E = decltype(tag);
-                E* P = reinterpret_cast<E*>(buf(c, c->cur)) + (size_t)host_plane(k) * c->L.plane;
-                plane_from_f32<E><<<1024, 256, 0, c->stream>>>(P, stage, p.nx, p.ny, c->L.pitch,
-                                                               plane_shift(c, k));
-            });
-            CK(cudaGetLastError(), "state conversion");
+            continue;
         }
+        CK(cudaMemcpyAsync(stage, host + (size_t)k * n, n * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "copy state to device");
+        with_elem(st, [&](auto tag) {
+            using E = decltype(tag);
+            plane_from_f32<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<E*>(P), stage, p.nx, p.ny,
+                                                           c->L.pitch, plane_shift(c, k));
+        });
+        CK(cudaGetLastError(), "state conversion");
     }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DMRT_OK;
@@ -1119,8 +1180,10 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         cav[i].stage_bytes = (unsigned)(kPlanes * RC * WB * sizeof(float));
         items += (long long)cav[i].n_strips * cav[i].n_rowblocks;
         for (int bf = 0; bf < 2; ++bf) {
-            rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 0], buf(c, bf), 6, RC, WB);
-            if (!rc) rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 1], buf(c, bf), 4, RC, WB);
+            rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 0], buf(c, bf), DMRT_FP32, kPlanes, 6, RC, WB);
+            if (!rc)
+                rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 1], buf(c, bf), DMRT_FP32, kPlanes, 4, RC,
+                                WB);
             if (rc) {
                 std::snprintf(b->err, sizeof b->err, "cavity %d: %.200s", i, c->err);
                 return fail(rc);

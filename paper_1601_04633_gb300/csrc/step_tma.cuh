@@ -1,16 +1,20 @@
 // Fused double-MRT time step, TMA-pipelined persistent variant (sm_103a).
 //
 // Work items are (strip, row block): a strip is 256 - 2 HALO nodes of a row
-// (248 for float32 storage, 240 for 16-bit storage), a row block R consecutive
-// rows. For one item the pull-stream needs, per plane group (see lattice.cuh),
-// R rows of 256 elements starting HALO nodes left of the strip (one halo column
-// each side, rounded out so the copy starts on a 16-byte boundary; HALO = 16
-// bytes / element size):
-//   group Z (6 planes) from rows j0 .. j0+R-1,
-//   group P (4 planes) from rows j0-1 .. j0+R-2,
-//   group N (4 planes) from rows j0+1 .. j0+R.
-// Each is one 3-D tensor copy (cp.async.bulk.tensor, box 256 x R x planes) into
-// a shared-memory stage; S stages form a ring guarded by mbarriers, so while
+// (248 for float32 storage, 240 for 16-bit and mixed storage), a row block R
+// consecutive rows. For one item the pull-stream needs, per plane group (see
+// lattice.cuh), R rows of 256 elements starting HALO nodes left of the strip
+// (one halo column each side, rounded out so the copy starts on a 16-byte
+// boundary; HALO = 16 bytes / size of the narrowest stored element):
+//   group Z (e_y = 0) from rows j0 .. j0+R-1,
+//   group P (e_y = +1) from rows j0-1 .. j0+R-2,
+//   group N (e_y = -1) from rows j0+1 .. j0+R.
+// One-type storage (all planes float32, float16 or bfloat16) takes one 3-D
+// tensor copy per group (cp.async.bulk.tensor, box 256 x R x planes: 6, 4, 4).
+// Mixed storage (flow planes float16, thermal planes float32, in two blocks)
+// takes six: three for the flow groups (3 planes each) and three for the
+// thermal groups (3, 1, 1 planes). The copies land in a shared-memory stage;
+// S stages form a ring guarded by mbarriers, so while
 // the block computes one item the copies of the next S-1 items are in flight.
 // Out-of-range boxes (the left of the first strip, the rows above and below
 // the cavity) are zero-filled by the copy engine and replaced by the wall
@@ -46,6 +50,14 @@ struct TmaGeo {
 __host__ __device__ constexpr int tma_stage_elems(int R) { return kPlanes * R * kTmaBox; }
 __host__ __device__ constexpr size_t tma_smem_bytes(int R, int S, int elem_bytes) {
     return (size_t)S * tma_stage_elems(R) * elem_bytes + (size_t)S * 8;
+}
+// Stage of R rows with the 9 flow planes in f_bytes and the 5 thermal planes in
+// g_bytes per element, plus one mbarrier per stage.
+__host__ __device__ constexpr size_t tma_stage_bytes_fg(int R, int f_bytes, int g_bytes) {
+    return (size_t)R * kTmaBox * (9 * f_bytes + 5 * g_bytes);
+}
+__host__ __device__ constexpr size_t tma_smem_bytes_fg(int R, int S, int f_bytes, int g_bytes) {
+    return (size_t)S * tma_stage_bytes_fg(R, f_bytes, g_bytes) + (size_t)S * 8;
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -212,20 +224,22 @@ __device__ __forceinline__ unsigned lcg(unsigned& r) {
     return r;
 }
 
+// Stochastically rounded store of N nodes; r[e] is node e's random state, so
+// a node draws the same bits whatever the number of nodes per thread.
 template <typename E, int N>
-__device__ __forceinline__ void vec_put_sr(E* p, const float (&o)[N], float shift, unsigned& r) {
+__device__ __forceinline__ void vec_put_sr(E* p, const float (&o)[N], float shift, unsigned (&r)[N]) {
     Pack<E, N> q;
 #pragma unroll
-    for (int e = 0; e < N; ++e) q.v[e] = from_f_sr<E>(o[e] - shift, lcg(r));
+    for (int e = 0; e < N; ++e) q.v[e] = from_f_sr<E>(o[e] - shift, lcg(r[e]));
     *reinterpret_cast<Pack<E, N>*>(p) = q;
 }
 
 // NPT consecutive values of a shared-memory plane row for nodes n0..n0+NPT-1,
 // shifted for a pull with lattice x-velocity EX: node n takes the value at
 // n - EX. The row starts HALO nodes left of the strip, so node n sits at n + HALO.
-template <int EX, int NPT, typename E>
+// (HALO is the layout's: 16 bytes of its narrowest stored type.)
+template <int EX, int NPT, int HALO, typename E>
 __device__ __forceinline__ void lds_pull(const E* rowp, int n0, float (&o)[NPT], float shift) {
-    constexpr int HALO = tma_halo(sizeof(E));
     const E* p = rowp + HALO + n0;
     if constexpr (EX == 0 || NPT == 1) {
         vec_get<E, NPT>(p - EX, o);
@@ -274,21 +288,64 @@ __device__ __forceinline__ void collide_nodes(float (&F)[9][NPT], float (&Gq)[5]
     }
 }
 
+// Population layouts. OneType<E>: 14 planes of E, grouped Z/P/N (lattice.cuh).
+// Split<EF, EG>: the 9 flow planes of EF (Z f1 f2 f4, P f3 f6 f7, N f5 f8 f9)
+// followed by the 5 thermal planes of EG (Z g1 g2 g4, P g3, N g5), paper numbering.
+__host__ __device__ constexpr int split_f(int k) {
+    return k == 0 ? 0 : k == 1 ? 1 : k == 3 ? 2 : k == 2 ? 3 : k == 5 ? 4 : k == 6 ? 5 : k == 4 ? 6 : k == 7 ? 7 : 8;
+}
+__host__ __device__ constexpr int split_g(int k) { return k == 0 ? 0 : k == 1 ? 1 : k == 3 ? 2 : k == 2 ? 3 : 4; }
+
+template <typename E>
+struct OneType {
+    using Ef = E;
+    using Eg = E;
+    static constexpr bool kSplit = false;
+    static constexpr int kHalo = tma_halo(sizeof(E));
+    __host__ __device__ static constexpr int pf(int k) { return plane_f(k); }
+    __host__ __device__ static constexpr int pg(int k) { return plane_g(k); }
+};
+
+template <typename EF, typename EG>
+struct Split {
+    using Ef = EF;
+    using Eg = EG;
+    static constexpr bool kSplit = true;
+    static constexpr int kHalo = tma_halo(sizeof(EF) < sizeof(EG) ? sizeof(EF) : sizeof(EG));
+    __host__ __device__ static constexpr int pf(int k) { return split_f(k); }
+    __host__ __device__ static constexpr int pg(int k) { return split_g(k); }
+};
+
+template <typename E, int NPT, bool SR>
+__device__ __forceinline__ void put_vals(E* p, const float (&o)[NPT], float shift, unsigned (&r)[NPT]) {
+    if constexpr (SR && kShifted<E>) vec_put_sr<E, NPT>(p, o, shift, r);
+    else vec_put<E, NPT>(p, o, shift);
+}
+
 // Pull, collide and store one work item (strip, row block) from its shared-
-// memory stage `st`, and report the Nusselt number of the rows it owns in the
+// memory stage, and report the Nusselt number of the rows it owns in the
 // first strip. Called by every thread of the block (the Nusselt report is a
 // warp collective); `ok` is false when the stage's wait expired.
-// Geometry: strips of W nodes, shared-memory rows of WB elements (HALO left
-// of the strip), RC rows per item, plane groups P and N starting offP / offN
-// elements into the stage (group Z at 0); compile-time constants in the
-// single-cavity kernel, per-cavity values in the batched one.
-template <typename E, int NPT, bool SR>
-__device__ __forceinline__ void process_item(const E* st, const StepArgs& A, const StepConsts& K,
+// Geometry: strips of W nodes, shared-memory rows of WB elements (kHalo left
+// of the strip), RC rows per item. One-type layout: plane groups P and N start
+// offP / offN elements into the stage (group Z at 0). Split layout: the flow
+// planes, then the thermal planes, each [plane][row][WB].
+template <typename L, int NPT, bool SR>
+__device__ __forceinline__ void process_item(const unsigned char* stage, const StepArgs& A, const StepConsts& K,
                                              int strip, int rb, int rg, int t, bool ok,
                                              unsigned salt, int W, int WB, int RC, int offP, int offN) {
-    const E* Sg = reinterpret_cast<const E*>(A.src);
-    const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 for float32)
+    using Ef = typename L::Ef;
+    using Eg = typename L::Eg;
+    constexpr int HALO = L::kHalo;
     const long long PL = A.plane;
+    const Ef* Sf = reinterpret_cast<const Ef*>(A.src);
+    const Eg* Sgg = L::kSplit ? reinterpret_cast<const Eg*>(reinterpret_cast<const unsigned char*>(A.src) +
+                                                            (size_t)9 * PL * sizeof(Ef))
+                              : reinterpret_cast<const Eg*>(A.src);
+    const Ef* stf = reinterpret_cast<const Ef*>(stage);
+    const Eg* stg = L::kSplit ? reinterpret_cast<const Eg*>(stage + (size_t)9 * RC * WB * sizeof(Ef))
+                              : reinterpret_cast<const Eg*>(stage);
+    const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 unless g is 16-bit)
     const float sign_l_g = K.left_fixed ? -1.f : 1.f;
     const float sign_r_g = K.right_fixed ? -1.f : 1.f;
     const int j = rb * RC + rg;
@@ -300,59 +357,62 @@ __device__ __forceinline__ void process_item(const E* st, const StepArgs& A, con
 #pragma unroll
     for (int e = 0; e < NPT; ++e) theta[e] = 0.f;
     if (mine) {
-        auto rowp = [&](int plane) {
+        auto grouped = [&](int plane) {
             const int g0 = plane >= kGroupN ? kGroupN : plane >= kGroupP ? kGroupP : kGroupZ;
             const int off = plane >= kGroupN ? offN : plane >= kGroupP ? offP : 0;
-            return st + off + ((plane - g0) * RC + rg) * WB;
+            return off + ((plane - g0) * RC + rg) * WB;
         };
+        auto rowf = [&](int plane) { return stf + (L::kSplit ? (plane * RC + rg) * WB : grouped(plane)); };
+        auto rowg = [&](int plane) { return stg + (L::kSplit ? (plane * RC + rg) * WB : grouped(plane)); };
         float F[9][NPT], Gq[5][NPT];
-        lds_pull<0>(rowp(plane_f(0)), n0, F[0], 0.f);
-        lds_pull<1>(rowp(plane_f(1)), n0, F[1], 0.f);
-        lds_pull<0>(rowp(plane_f(2)), n0, F[2], 0.f);
-        lds_pull<-1>(rowp(plane_f(3)), n0, F[3], 0.f);
-        lds_pull<0>(rowp(plane_f(4)), n0, F[4], 0.f);
-        lds_pull<1>(rowp(plane_f(5)), n0, F[5], 0.f);
-        lds_pull<-1>(rowp(plane_f(6)), n0, F[6], 0.f);
-        lds_pull<-1>(rowp(plane_f(7)), n0, F[7], 0.f);
-        lds_pull<1>(rowp(plane_f(8)), n0, F[8], 0.f);
-        lds_pull<0>(rowp(plane_g(0)), n0, Gq[0], sh0);
-        lds_pull<1>(rowp(plane_g(1)), n0, Gq[1], sh1);
-        lds_pull<0>(rowp(plane_g(2)), n0, Gq[2], sh1);
-        lds_pull<-1>(rowp(plane_g(3)), n0, Gq[3], sh1);
-        lds_pull<0>(rowp(plane_g(4)), n0, Gq[4], sh1);
+        lds_pull<0, NPT, HALO>(rowf(L::pf(0)), n0, F[0], 0.f);
+        lds_pull<1, NPT, HALO>(rowf(L::pf(1)), n0, F[1], 0.f);
+        lds_pull<0, NPT, HALO>(rowf(L::pf(2)), n0, F[2], 0.f);
+        lds_pull<-1, NPT, HALO>(rowf(L::pf(3)), n0, F[3], 0.f);
+        lds_pull<0, NPT, HALO>(rowf(L::pf(4)), n0, F[4], 0.f);
+        lds_pull<1, NPT, HALO>(rowf(L::pf(5)), n0, F[5], 0.f);
+        lds_pull<-1, NPT, HALO>(rowf(L::pf(6)), n0, F[6], 0.f);
+        lds_pull<-1, NPT, HALO>(rowf(L::pf(7)), n0, F[7], 0.f);
+        lds_pull<1, NPT, HALO>(rowf(L::pf(8)), n0, F[8], 0.f);
+        lds_pull<0, NPT, HALO>(rowg(L::pg(0)), n0, Gq[0], sh0);
+        lds_pull<1, NPT, HALO>(rowg(L::pg(1)), n0, Gq[1], sh1);
+        lds_pull<0, NPT, HALO>(rowg(L::pg(2)), n0, Gq[2], sh1);
+        lds_pull<-1, NPT, HALO>(rowg(L::pg(3)), n0, Gq[3], sh1);
+        lds_pull<0, NPT, HALO>(rowg(L::pg(4)), n0, Gq[4], sh1);
 
         // Walls. Bottom row: links from below (f2, f5, f6, g2) bounce back from
         // the node's own opposites (f4, f7, f8, g4); top row the reverse.
-        const E* rowj = Sg + (size_t)j * A.pitch;
+        const Ef* rowjf = Sf + (size_t)j * A.pitch;
+        const Eg* rowjg = Sgg + (size_t)j * A.pitch;
         if (j == 0) {
-            vec_ldg<E, NPT>(rowj + plane_f(4) * PL + x0, F[2], 0.f);
-            vec_ldg<E, NPT>(rowj + plane_f(7) * PL + x0, F[5], 0.f);
-            vec_ldg<E, NPT>(rowj + plane_f(8) * PL + x0, F[6], 0.f);
-            vec_ldg<E, NPT>(rowj + plane_g(4) * PL + x0, Gq[2], sh1);
+            vec_ldg<Ef, NPT>(rowjf + L::pf(4) * PL + x0, F[2], 0.f);
+            vec_ldg<Ef, NPT>(rowjf + L::pf(7) * PL + x0, F[5], 0.f);
+            vec_ldg<Ef, NPT>(rowjf + L::pf(8) * PL + x0, F[6], 0.f);
+            vec_ldg<Eg, NPT>(rowjg + L::pg(4) * PL + x0, Gq[2], sh1);
         }
         if (j == A.ny - 1) {
-            vec_ldg<E, NPT>(rowj + plane_f(2) * PL + x0, F[4], 0.f);
-            vec_ldg<E, NPT>(rowj + plane_f(5) * PL + x0, F[7], 0.f);
-            vec_ldg<E, NPT>(rowj + plane_f(6) * PL + x0, F[8], 0.f);
-            vec_ldg<E, NPT>(rowj + plane_g(2) * PL + x0, Gq[4], sh1);
+            vec_ldg<Ef, NPT>(rowjf + L::pf(2) * PL + x0, F[4], 0.f);
+            vec_ldg<Ef, NPT>(rowjf + L::pf(5) * PL + x0, F[7], 0.f);
+            vec_ldg<Ef, NPT>(rowjf + L::pf(6) * PL + x0, F[8], 0.f);
+            vec_ldg<Eg, NPT>(rowjg + L::pg(2) * PL + x0, Gq[4], sh1);
         }
         // Left wall (node x = 0): links with e_x = +1 (f1, f5, f8, g1).
         if (x0 == 0) {
-            F[1][0] = ldg_one(rowj + plane_f(3) * PL, 0.f);
-            F[5][0] = ldg_one(rowj + plane_f(7) * PL, 0.f);
-            F[8][0] = ldg_one(rowj + plane_f(6) * PL, 0.f);
+            F[1][0] = ldg_one(rowjf + L::pf(3) * PL, 0.f);
+            F[5][0] = ldg_one(rowjf + L::pf(7) * PL, 0.f);
+            F[8][0] = ldg_one(rowjf + L::pf(6) * PL, 0.f);
             const float add = K.left_fixed ? K.abb * __ldg(A.hot + j) : 0.f;
-            Gq[1][0] = sign_l_g * ldg_one(rowj + plane_g(3) * PL, sh1) + add;
+            Gq[1][0] = sign_l_g * ldg_one(rowjg + L::pg(3) * PL, sh1) + add;
         }
         // Right wall (node x = nx - 1): links with e_x = -1 (f3, f6, f7, g3).
         const int re = A.nx - 1 - x0;
         if (re < NPT) {
             const int xr = A.nx - 1;
-            const float v3 = ldg_one(rowj + plane_f(1) * PL + xr, 0.f);
-            const float v6 = ldg_one(rowj + plane_f(8) * PL + xr, 0.f);
-            const float v7 = ldg_one(rowj + plane_f(5) * PL + xr, 0.f);
+            const float v3 = ldg_one(rowjf + L::pf(1) * PL + xr, 0.f);
+            const float v6 = ldg_one(rowjf + L::pf(8) * PL + xr, 0.f);
+            const float v7 = ldg_one(rowjf + L::pf(5) * PL + xr, 0.f);
             const float add = K.right_fixed ? K.abb * __ldg(A.cold + j) : 0.f;
-            const float vg = sign_r_g * ldg_one(rowj + plane_g(1) * PL + xr, sh1) + add;
+            const float vg = sign_r_g * ldg_one(rowjg + L::pg(1) * PL + xr, sh1) + add;
 #pragma unroll
             for (int e = 0; e < NPT; ++e) {
                 if (e == re) {
@@ -366,19 +426,20 @@ __device__ __forceinline__ void process_item(const E* st, const StepArgs& A, con
 
         bool bad = false;
         collide_nodes<NPT>(F, Gq, K, theta, min(NPT, A.nx - x0), bad);
-        E* D = reinterpret_cast<E*>(A.dst) + (size_t)j * A.pitch + x0;
-        if constexpr (SR) {
-            unsigned r = hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)x0) ^ salt);
+        Ef* Df = reinterpret_cast<Ef*>(A.dst) + (size_t)j * A.pitch + x0;
+        Eg* Dg = (L::kSplit ? reinterpret_cast<Eg*>(reinterpret_cast<unsigned char*>(A.dst) +
+                                                    (size_t)9 * PL * sizeof(Ef))
+                            : reinterpret_cast<Eg*>(A.dst)) +
+                 (size_t)j * A.pitch + x0;
+        // Stochastic rounding: each node's bits come from a hash of its index and the step.
+        unsigned r[NPT];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) vec_put_sr<E, NPT>(D + plane_f(k) * PL, F[k], 0.f, r);
+        for (int e = 0; e < NPT; ++e)
+            r[e] = SR ? hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)(x0 + e)) ^ salt) : 0u;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) vec_put_sr<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1, r);
-        } else {
+        for (int k = 0; k < 9; ++k) put_vals<Ef, NPT, SR>(Df + L::pf(k) * PL, F[k], 0.f, r);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) vec_put<E, NPT>(D + plane_f(k) * PL, F[k], 0.f);
-#pragma unroll
-            for (int k = 0; k < 5; ++k) vec_put<E, NPT>(D + plane_g(k) * PL, Gq[k], k == 0 ? sh0 : sh1);
-        }
+        for (int k = 0; k < 5; ++k) put_vals<Eg, NPT, SR>(Dg + L::pg(k) * PL, Gq[k], k == 0 ? sh0 : sh1, r);
         if (bad) atomicOr(A.err, kErrNonFinite);
     }
     // Nusselt number of row j from the first warp of the row's thread group
@@ -417,21 +478,25 @@ struct ItemCursor {
     }
 };
 
-template <typename E, int NPT, int R, int S, bool SR = false>
-__global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_constant__ CUtensorMap map6,
-                                                          const __grid_constant__ CUtensorMap map4,
+template <typename L, int NPT, int R, int S, bool SR>
+__global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_constant__ CUtensorMap map0,
+                                                          const __grid_constant__ CUtensorMap map1,
+                                                          const __grid_constant__ CUtensorMap map2,
                                                           StepArgs A, StepConsts K, TmaGeo T) {
+    using Ef = typename L::Ef;
+    using Eg = typename L::Eg;
+    constexpr uint32_t kStageBytes = (uint32_t)tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    E* stages = reinterpret_cast<E*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * tma_stage_elems(R) * sizeof(E));
-    constexpr int HALO = tma_halo(sizeof(E));
-    constexpr int STRIP = tma_strip(sizeof(E));
-    constexpr int TPR = 256 / NPT;  // threads per row of a strip
+    unsigned char* stages = smem_raw;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);
+    constexpr int HALO = L::kHalo;
+    constexpr int STRIP = kTmaBox - 2 * HALO;
+    constexpr int TPR = 256 / NPT;   // threads per row of a strip
+    constexpr int PB = R * kTmaBox;  // elements of one plane in a stage
     const int tid = threadIdx.x;
     const int rg = tid / TPR;  // row of the block this thread works on
     const int t = tid % TPR;   // node group within the strip
     const int G = gridDim.x;
-    constexpr uint32_t kStageBytes = (uint32_t)(kPlanes * R * kTmaBox * sizeof(E));
 
     // After an expired wait in an earlier launch the state is already invalid:
     // return at once instead of waiting again.
@@ -443,14 +508,30 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     }
     __syncthreads();
 
+    // One item: every plane's R rows of row block rb, groups P and N taken one
+    // row below / above (their e_y). One-type layout: map0 has 6-plane boxes
+    // (group Z), map1 4-plane boxes (P, N); map2 is unused. Split layout: map0
+    // has 3-plane flow boxes, map1 3-plane thermal boxes, map2 1-plane thermal boxes.
     auto issue = [&](const ItemCursor& c, int s) {
         const int x = c.strip * STRIP - HALO;
         const int j0 = c.rb * R;
-        E* st = stages + (size_t)s * tma_stage_elems(R);
+        unsigned char* st = stages + (size_t)s * kStageBytes;
         mbar_expect_tx(&bars[s], kStageBytes);
-        tma_load_3d(st, &map6, x, j0, kGroupZ, &bars[s]);
-        tma_load_3d(st + kGroupP * R * kTmaBox, &map4, x, j0 - 1, kGroupP, &bars[s]);
-        tma_load_3d(st + kGroupN * R * kTmaBox, &map4, x, j0 + 1, kGroupN, &bars[s]);
+        if constexpr (!L::kSplit) {
+            Ef* e = reinterpret_cast<Ef*>(st);
+            tma_load_3d(e, &map0, x, j0, kGroupZ, &bars[s]);
+            tma_load_3d(e + kGroupP * PB, &map1, x, j0 - 1, kGroupP, &bars[s]);
+            tma_load_3d(e + kGroupN * PB, &map1, x, j0 + 1, kGroupN, &bars[s]);
+        } else {
+            Ef* f = reinterpret_cast<Ef*>(st);
+            Eg* g = reinterpret_cast<Eg*>(st + (size_t)9 * PB * sizeof(Ef));
+            tma_load_3d(f, &map0, x, j0, 0, &bars[s]);
+            tma_load_3d(f + 3 * PB, &map0, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(f + 6 * PB, &map0, x, j0 + 1, 6, &bars[s]);
+            tma_load_3d(g, &map1, x, j0, 0, &bars[s]);
+            tma_load_3d(g + 3 * PB, &map2, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(g + 4 * PB, &map2, x, j0 + 1, 4, &bars[s]);
+        }
     };
 
     // Producer (thread 0): issues items ahead of the consumers, S - 1 in flight.
@@ -485,8 +566,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         }
         const bool ok = mbar_wait_bounded(&bars[s], phase);
 
-        process_item<E, NPT, SR>(stages + (size_t)s * tma_stage_elems(R), A, K, cc.strip, cc.rb, rg,
-                                 t, ok, salt, STRIP, kTmaBox, R, kGroupP * R * kTmaBox, kGroupN * R * kTmaBox);
+        process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, A, K, cc.strip, cc.rb, rg, t, ok, salt,
+                                 STRIP, kTmaBox, R, kGroupP * PB, kGroupN * PB);
         // All threads are done with stage s; a timeout anywhere ends the block.
         if (__syncthreads_or(!ok)) {
             timed_out = true;
@@ -619,8 +700,9 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         const int tpr = bc.tpr;
         const int rg = tid / tpr;
         const int t = tid - rg * tpr;
-        process_item<E, NPT, false>(stages + (size_t)s * tma_stage_elems(R), bc.args[parity], bc.K,
-                                    cc.strip, cc.rb, rg, t, ok, 0u, bc.W, bc.WB, bc.RC, bc.offP, bc.offN);
+        process_item<OneType<E>, NPT, false>(reinterpret_cast<const unsigned char*>(stages + (size_t)s * tma_stage_elems(R)),
+                                             bc.args[parity], bc.K, cc.strip, cc.rb, rg, t, ok, 0u, bc.W, bc.WB,
+                                             bc.RC, bc.offP, bc.offN);
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;

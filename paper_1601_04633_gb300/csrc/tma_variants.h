@@ -6,7 +6,7 @@
 namespace dmrt {
 
 struct TmaVariant {
-    int storage;   // DMRT_FP32, DMRT_FP16 or DMRT_BF16
+    int storage;   // DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED
     int rounding;  // DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC
     int npt, R, S;
     const void* func;
@@ -17,6 +17,7 @@ const TmaVariant* tma_variants_npt2(int* n);
 const TmaVariant* tma_variants_npt1(int* n);
 const TmaVariant* tma_variants_fp16(int* n);
 const TmaVariant* tma_variants_bf16(int* n);
+const TmaVariant* tma_variants_mixed(int* n);  // float16 flow, float32 thermal
 const TmaVariant* tma_variants_batch(int* n);  // batched sweep kernels
 
 }  // namespace dmrt

@@ -24,6 +24,8 @@ SINGLE_TILES_FP32 = ([(1, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (2,
                                               (4, 2), (4, 3)]])
 SINGLE_TILES_16 = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (1, 4, 4), (2, 2, 2), (2, 4, 2), (2, 4, 3), (4, 4, 2)]
 SINGLE_TILES_16_SR = [(1, 1, 2), (1, 4, 2), (2, 2, 2), (4, 4, 2)]
+SINGLE_TILES_MIXED = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (2, 2, 2)]
+SINGLE_TILES_MIXED_SR = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 2, 2), (2, 4, 2)]
 
 
 def _time_steps(step, steps, warmup):
@@ -97,7 +99,10 @@ def tune_single(cav, storage=0, rounding=0, steps=200, warmup=20, tiles=None, ca
     from . import dmrt as D
 
     if tiles is None:
-        tiles = SINGLE_TILES_FP32 if storage == 0 else (SINGLE_TILES_16_SR if rounding else SINGLE_TILES_16)
+        if storage == 3:
+            tiles = SINGLE_TILES_MIXED_SR if rounding else SINGLE_TILES_MIXED
+        else:
+            tiles = SINGLE_TILES_FP32 if storage == 0 else (SINGLE_TILES_16_SR if rounding else SINGLE_TILES_16)
     key = _key("single", [(cav.nx, cav.ny)], f"{storage}-{rounding}-{steps}")
     hit = _cache_get(cache, key)
     if hit:
