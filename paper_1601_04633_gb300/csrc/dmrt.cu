@@ -95,7 +95,7 @@ struct dmrt_ctx {
     int tma_grid;
     size_t tma_smem;
     const void* tma_func;
-    CUtensorMap maps[2][3];  // per source buffer: the step kernel's three tensor maps
+    dmrt::TmaMaps tmaps[2];  // per source buffer: the step kernel's load and store maps
     cudaGraphExec_t graph[2];
     int graph_len;
     char err[256];
@@ -331,16 +331,17 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// 3-D view {pitch, ny, nplanes} of planes of element type `storage` (FP32,
-// FP16 or BF16) starting at base, with boxes {width, rows, planes}.
+// 3-D view {xdim, ny, nplanes} (row stride pitch; xdim = pitch when 0) of
+// planes of element type `storage` (FP32, FP16 or BF16) starting at base,
+// with boxes {width, rows, planes}.
 int encode_map(dmrt_ctx* c, CUtensorMap* m, void* base, int storage, int nplanes, int planes, int rows,
-               int width = dmrt::kTmaBox) {
+               int width = dmrt::kTmaBox, int xdim = 0) {
     auto enc = tensor_map_encoder();
     if (!enc) {
         set_err(c, "cuTensorMapEncodeTiled is not available from the driver");
         return DMRT_E_CUDA;
     }
-    cuuint64_t dims[3] = {(cuuint64_t)c->L.pitch, (cuuint64_t)c->p.ny, (cuuint64_t)nplanes};
+    cuuint64_t dims[3] = {(cuuint64_t)(xdim > 0 ? xdim : c->L.pitch), (cuuint64_t)c->p.ny, (cuuint64_t)nplanes};
     const int eb = f_bytes(storage);
     cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * eb, (cuuint64_t)c->L.plane * eb};
     const CUtensorMapDataType dt = storage == DMRT_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -400,7 +401,12 @@ int setup_kernel(dmrt_ctx* c) {
     const int strip = dmrt::tma_strip(std::min(fb, gb));
     c->geo.n_strips = (p.nx + strip - 1) / strip;
     c->geo.n_rowblocks = (p.ny + R - 1) / R;
-    c->tma_smem = dmrt::tma_smem_bytes_fg(R, S, fb, gb);
+    const bool split = p.storage == DMRT_MIXED;
+    c->tma_smem = dmrt::step_tma_smem_bytes(split, v->ts != 0, R, S, fb, gb);
+    if (c->tma_smem > (size_t)dmrt::kMaxSmem) {
+        set_err(c, "TMA tile %dx%d needs %zu bytes of shared memory", R, S, c->tma_smem);
+        return DMRT_E_ARG;
+    }
     CK(cudaFuncSetAttribute(c->tma_func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->tma_smem),
        "set TMA kernel shared memory");
     int dev = 0, sms = 0, per_sm = 0;
@@ -415,18 +421,25 @@ int setup_kernel(dmrt_ctx* c) {
     const long long items = (long long)c->geo.n_strips * c->geo.n_rowblocks;
     c->tma_grid = (int)std::min<long long>(items, (long long)sms * per_sm);
     for (int b = 0; b < 2; ++b) {
-        CUtensorMap* m = c->maps[b];
+        // Loads from buffer b, stores (nx columns wide) to the other one.
+        dmrt::TmaMaps& m = c->tmaps[b];
+        std::memset(&m, 0, sizeof m);
+        float* dst = buf(c, 1 - b);
         int rc;
-        if (p.storage == DMRT_MIXED) {
+        if (split) {
             // 9 float16 flow planes, then 5 float32 thermal planes.
-            char* g = reinterpret_cast<char*>(buf(c, b)) + (size_t)9 * c->L.plane * 2;
-            rc = encode_map(c, &m[0], buf(c, b), DMRT_FP16, 9, 3, c->R);
-            if (!rc) rc = encode_map(c, &m[1], g, DMRT_FP32, 5, 3, c->R);
-            if (!rc) rc = encode_map(c, &m[2], g, DMRT_FP32, 5, 1, c->R);
+            const size_t goff = (size_t)9 * c->L.plane * 2;
+            char* g = reinterpret_cast<char*>(buf(c, b)) + goff;
+            char* gd = reinterpret_cast<char*>(dst) + goff;
+            rc = encode_map(c, &m.ld[0], buf(c, b), DMRT_FP16, 9, 3, R);
+            if (!rc) rc = encode_map(c, &m.ld[1], g, DMRT_FP32, 5, 3, R);
+            if (!rc) rc = encode_map(c, &m.ld[2], g, DMRT_FP32, 5, 1, R);
+            if (!rc) rc = encode_map(c, &m.st[0], dst, DMRT_FP16, 9, 9, R, strip, p.nx);
+            if (!rc) rc = encode_map(c, &m.st[1], gd, DMRT_FP32, 5, 5, R, strip, p.nx);
         } else {
-            rc = encode_map(c, &m[0], buf(c, b), p.storage, kPlanes, 6, c->R);
-            if (!rc) rc = encode_map(c, &m[1], buf(c, b), p.storage, kPlanes, 4, c->R);
-            m[2] = m[1];
+            rc = encode_map(c, &m.ld[0], buf(c, b), p.storage, kPlanes, 6, R);
+            if (!rc) rc = encode_map(c, &m.ld[1], buf(c, b), p.storage, kPlanes, 4, R);
+            if (!rc) rc = encode_map(c, &m.st[0], dst, p.storage, kPlanes, kPlanes, R, strip, p.nx);
         }
         if (rc) return rc;
     }
@@ -663,7 +676,7 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
 static int launch_step(dmrt_ctx* c, int from) {
     dmrt::StepArgs A = step_args(c, from);
     if (c->kernel == DMRT_KERNEL_TMA) {
-        void* params[6] = {&c->maps[from][0], &c->maps[from][1], &c->maps[from][2], &A, &c->sc, &c->geo};
+        void* params[4] = {&c->tmaps[from], &A, &c->sc, &c->geo};
         cudaError_t e = cudaLaunchKernel(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), params,
                                          c->tma_smem, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "TMA step launch");
@@ -692,8 +705,7 @@ static int build_graph(dmrt_ctx* c, int from) {
         const int src = (i & 1) ? 1 - from : from;
         cudaKernelNodeParams kp = {};
         void* dparams[2] = {&args[i & 1], &c->sc};
-        void* tparams[6] = {&c->maps[src][0], &c->maps[src][1], &c->maps[src][2], &args[i & 1], &c->sc,
-                            &c->geo};
+        void* tparams[4] = {&c->tmaps[src], &args[i & 1], &c->sc, &c->geo};
         if (c->kernel == DMRT_KERNEL_TMA) {
             kp.func = const_cast<void*>(c->tma_func);
             kp.gridDim = dim3(c->tma_grid);

@@ -104,45 +104,43 @@ __device__ __forceinline__ void collide_node(float (&f)[9], float (&g)[5], const
     const float qy = -2.f * a24 + s56 - s78;
     const float eps = 4.f * f[0] - 2.f * s1234 + s5678;
     const float uu = u * u + v * v;
-    // Non-equilibrium parts (Eq. 34, m4_eq = -2 drho + 3 |u|^2), scaled.
-    const float d3 = K.se36 * (e + 2.f * rho - 3.f * uu);
-    const float d4 = K.snu4 * (pxx - (u * u - v * v));
-    const float d5 = K.snu4 * (pxy - u * v);
-    const float d6 = K.sq12 * (qx + u);
-    const float d7 = K.sq12 * (qy + v);
-    const float d8 = K.seps36 * (eps - rho + 3.f * uu);
-
     const float theta = g[0] + g[1] + g[2] + g[3] + g[4];  // Eq. 41
 
-    // Buoyancy force (Eqs. 26-27): F_i = 3 (e_i - u).G f_i_eq(rho0 = 1, u),
-    // G = (0, gbeta (theta - theta_ref)).
-    const float c3 = 3.f * K.gbeta * (theta - K.theta_ref);
-    const float base = 1.f - 1.5f * uu;
-    const float cv_m = c3 * (-v), cv_p = c3 * (1.f - v), cv_n = c3 * (-1.f - v);
-    const float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-    const float u3 = 3.f * u, v3 = 3.f * v, uu45 = 4.5f * u * u, vv45 = 4.5f * v * v;
-    const float upv = u + v, umv = u - v;
-    const float qp = base + 4.5f * upv * upv, qm = base + 4.5f * umv * umv;
-    const float F0 = cv_m * (4.f / 9.f) * base;
-    const float F1 = cv_m * w1 * (base + u3 + uu45);
-    const float F2 = cv_p * w1 * (base + v3 + vv45);
-    const float F3 = cv_m * w1 * (base - u3 + uu45);
-    const float F4 = cv_n * w1 * (base - v3 + vv45);
-    const float F5 = cv_p * w5 * (qp + 3.f * upv);
-    const float F6 = cv_p * w5 * (qm - 3.f * umv);
-    const float F7 = cv_n * w5 * (qp - 3.f * upv);
-    const float F8 = cv_n * w5 * (qm + 3.f * umv);
+    // Buoyancy force (Eqs. 26-27): F_i = 3 (e_i - u).G f_i^eq(rho0 = 1, u) with
+    // G = (0, Gy), Gy = gbeta (theta - theta_ref). It is added in moment space:
+    // the moments M F of that F are, exactly, (rho, e, eps, jx, qx, jy, qy, pxx,
+    // pxy) = (0, 3 Gy v (2 - 3|u|^2), -3 Gy v (2 - 3|u|^2), 0, 6 Gy u v, Gy,
+    // Gy (3u^2 - 1), -Gy v (3(u^2 - v^2) + 2), Gy u (1 - 3v^2)), and
+    // F = M^-1 (M F), so each term joins its moment's relaxation below
+    // (divided by the moment's norm, as M^-1 = M^T diag(1/norm)).
+    const float Gy = K.gbeta * (theta - K.theta_ref);
+    const float uu_d = u * u - v * v;
+    const float g12 = Gy * (1.f / 12.f);
+    const float fe = g12 * v * (2.f - 3.f * uu);                // (M F)_e / 36 = -(M F)_eps / 36
+    const float fqx = 0.5f * Gy * u * v;                        // (M F)_qx / 12
+    const float fqy = g12 * (3.f * u * u - 1.f);                // (M F)_qy / 12
+    const float fpxx = -0.25f * Gy * v * (3.f * uu_d + 2.f);    // (M F)_pxx / 4
+    const float fpxy = 0.25f * Gy * u * (1.f - 3.f * v * v);    // (M F)_pxy / 4
+    const float fjy = Gy * (1.f / 6.f);                         // (M F)_jy / 6
 
-    // f* = f - M^-1 S (m - m_eq) + F, with M^-1 = M^T diag(1/norm) (Eq. 28).
-    f[0] = f[0] + 4.f * d3 - 4.f * d8 + F0;
-    f[1] = f[1] + d3 - d4 + 2.f * d6 + 2.f * d8 + F1;
-    f[2] = f[2] + d3 + d4 + 2.f * d7 + 2.f * d8 + F2;
-    f[3] = f[3] + d3 - d4 - 2.f * d6 + 2.f * d8 + F3;
-    f[4] = f[4] + d3 + d4 - 2.f * d7 + 2.f * d8 + F4;
-    f[5] = f[5] - 2.f * d3 - d5 - d6 - d7 - d8 + F5;
-    f[6] = f[6] - 2.f * d3 + d5 + d6 - d7 - d8 + F6;
-    f[7] = f[7] - 2.f * d3 - d5 + d6 + d7 - d8 + F7;
-    f[8] = f[8] - 2.f * d3 + d5 - d6 + d7 - d8 + F8;
+    // Non-equilibrium parts (Eq. 34, m4_eq = -2 drho + 3 |u|^2), scaled, less the force terms.
+    const float d3 = K.se36 * (e + 2.f * rho - 3.f * uu) - fe;
+    const float d4 = K.snu4 * (pxx - uu_d) - fpxx;
+    const float d5 = K.snu4 * (pxy - u * v) - fpxy;
+    const float d6 = K.sq12 * (qx + u) - fqx;
+    const float d7 = K.sq12 * (qy + v) - fqy;
+    const float d8 = K.seps36 * (eps - rho + 3.f * uu) + fe;
+
+    // f* = f - M^-1 (S (m - m_eq) - M F), with M^-1 = M^T diag(1/norm) (Eq. 28).
+    f[0] = f[0] + 4.f * d3 - 4.f * d8;
+    f[1] = f[1] + d3 - d4 + 2.f * d6 + 2.f * d8;
+    f[2] = f[2] + d3 + d4 + 2.f * d7 + 2.f * d8 + fjy;
+    f[3] = f[3] + d3 - d4 - 2.f * d6 + 2.f * d8;
+    f[4] = f[4] + d3 + d4 - 2.f * d7 + 2.f * d8 - fjy;
+    f[5] = f[5] - 2.f * d3 - d5 - d6 - d7 - d8 + fjy;
+    f[6] = f[6] - 2.f * d3 + d5 + d6 - d7 - d8 + fjy;
+    f[7] = f[7] - 2.f * d3 - d5 + d6 + d7 - d8 - fjy;
+    f[8] = f[8] - 2.f * d3 + d5 - d6 + d7 - d8 - fjy;
 
     // D2Q5: n = N g (Eq. 37, fifth row (0,1,-1,1,-1)), n_eq = (theta, u theta,
     // v theta, a theta, 0) (Eq. 42), g* = g - N^-1 Q (n - n_eq) (Eq. 36).

@@ -37,6 +37,7 @@
 namespace dmrt {
 
 constexpr int kTmaBox = 256;  // elements per box row (strip + halos, aligned)
+constexpr int kMaxSmem = 232448;  // dynamic shared memory a block may opt in to (227 KB)
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 
 __host__ __device__ constexpr int tma_halo(int elem_bytes) { return 16 / elem_bytes; }
@@ -115,6 +116,21 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
+
+// Tensor store of a shared-memory box (bulk-group completion), and the bulk-group
+// bookkeeping: commit, wait until the committed stores have read their shared
+// memory (.read) or have completed.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Make this thread's shared-memory writes visible to the copy engine.
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---- typed storage -----------------------------------------------------------
 // Populations are stored as float32, or rounded to-nearest to float16 / bfloat16
@@ -278,7 +294,7 @@ __device__ __forceinline__ void collide_nodes(float (&F)[9][NPT], float (&Gq)[5]
         for (int k = 0; k < 5; ++k) g[k] = Gq[k][e];
         float rho, th;
         collide_node(f, g, K, rho, th);
-        const bool valid = e < nvalid;
+        const bool valid = NPT == 1 || e < nvalid;  // one node per thread: only valid nodes get here
         if (valid) bad |= !(fabsf(rho) < 1e30f) || !(fabsf(th) < 1e30f);
 #pragma unroll
         for (int k = 0; k < 9; ++k) F[k][e] = valid ? f[k] : 0.f;
@@ -316,6 +332,30 @@ struct Split {
     __host__ __device__ static constexpr int pg(int k) { return split_g(k); }
 };
 
+// Shared-memory output tile of one item for the tensor-store epilogue: the
+// item's R rows x W nodes (W = strip width) of every plane, [plane][row][node];
+// split layouts put the thermal planes at a 128-byte aligned offset (a tensor
+// copy's shared-memory address must be 128-byte aligned).
+__host__ __device__ constexpr size_t round128(size_t x) { return (x + 127) & ~size_t(127); }
+__host__ __device__ constexpr size_t out_g_offset(bool split, int R, int W, int f_bytes) {
+    return split ? round128((size_t)9 * R * W * f_bytes) : 0;
+}
+__host__ __device__ constexpr size_t out_tile_bytes(bool split, int R, int W, int f_bytes, int g_bytes) {
+    return split ? round128(out_g_offset(true, R, W, f_bytes) + (size_t)5 * R * W * g_bytes)
+                 : round128((size_t)kPlanes * R * W * f_bytes);
+}
+
+// Tensor maps of the single-cavity TMA kernel for one source buffer: loads
+// from the source (one-type layout: 6-plane and 4-plane boxes; split layout:
+// 3-plane flow, 3-plane and 1-plane thermal boxes) and the epilogue's stores
+// to the destination (one-type: one 14-plane box; split: a 9-plane flow and a
+// 5-plane thermal box). The store maps span nx columns, so the padding columns
+// of the last strip are never written.
+struct TmaMaps {
+    CUtensorMap ld[3];
+    CUtensorMap st[2];
+};
+
 template <typename E, int NPT, bool SR>
 __device__ __forceinline__ void put_vals(E* p, const float (&o)[NPT], float shift, unsigned (&r)[NPT]) {
     if constexpr (SR && kShifted<E>) vec_put_sr<E, NPT>(p, o, shift, r);
@@ -330,10 +370,13 @@ __device__ __forceinline__ void put_vals(E* p, const float (&o)[NPT], float shif
 // of the strip), RC rows per item. One-type layout: plane groups P and N start
 // offP / offN elements into the stage (group Z at 0). Split layout: the flow
 // planes, then the thermal planes, each [plane][row][WB].
-template <typename L, int NPT, bool SR>
+// TS: store the results into the shared-memory output tile `out` (see
+// out_tile_bytes) for the block's tensor store, instead of to global memory.
+template <typename L, int NPT, bool SR, bool TS = false>
 __device__ __forceinline__ void process_item(const unsigned char* stage, const StepArgs& A, const StepConsts& K,
                                              int strip, int rb, int rg, int t, bool ok,
-                                             unsigned salt, int W, int WB, int RC, int offP, int offN) {
+                                             unsigned salt, int W, int WB, int RC, int offP, int offN,
+                                             unsigned char* out = nullptr) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     constexpr int HALO = L::kHalo;
@@ -426,20 +469,30 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
 
         bool bad = false;
         collide_nodes<NPT>(F, Gq, K, theta, min(NPT, A.nx - x0), bad);
-        Ef* Df = reinterpret_cast<Ef*>(A.dst) + (size_t)j * A.pitch + x0;
-        Eg* Dg = (L::kSplit ? reinterpret_cast<Eg*>(reinterpret_cast<unsigned char*>(A.dst) +
+        Ef* Df;
+        Eg* Dg;
+        long long DP;  // plane stride of the destination, elements
+        if constexpr (TS) {
+            DP = (long long)RC * W;
+            Df = reinterpret_cast<Ef*>(out) + rg * W + n0;
+            Dg = reinterpret_cast<Eg*>(out + out_g_offset(L::kSplit, RC, W, sizeof(Ef))) + rg * W + n0;
+        } else {
+            DP = PL;
+            Df = reinterpret_cast<Ef*>(A.dst) + (size_t)j * A.pitch + x0;
+            Dg = (L::kSplit ? reinterpret_cast<Eg*>(reinterpret_cast<unsigned char*>(A.dst) +
                                                     (size_t)9 * PL * sizeof(Ef))
                             : reinterpret_cast<Eg*>(A.dst)) +
                  (size_t)j * A.pitch + x0;
+        }
         // Stochastic rounding: each node's bits come from a hash of its index and the step.
         unsigned r[NPT];
 #pragma unroll
         for (int e = 0; e < NPT; ++e)
             r[e] = SR ? hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)(x0 + e)) ^ salt) : 0u;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) put_vals<Ef, NPT, SR>(Df + L::pf(k) * PL, F[k], 0.f, r);
+        for (int k = 0; k < 9; ++k) put_vals<Ef, NPT, SR>(Df + L::pf(k) * DP, F[k], 0.f, r);
 #pragma unroll
-        for (int k = 0; k < 5; ++k) put_vals<Eg, NPT, SR>(Dg + L::pg(k) * PL, Gq[k], k == 0 ? sh0 : sh1, r);
+        for (int k = 0; k < 5; ++k) put_vals<Eg, NPT, SR>(Dg + L::pg(k) * DP, Gq[k], k == 0 ? sh0 : sh1, r);
         if (bad) atomicOr(A.err, kErrNonFinite);
     }
     // Nusselt number of row j from the first warp of the row's thread group
@@ -478,19 +531,36 @@ struct ItemCursor {
     }
 };
 
-template <typename L, int NPT, int R, int S, bool SR>
-__global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_constant__ CUtensorMap map0,
-                                                          const __grid_constant__ CUtensorMap map1,
-                                                          const __grid_constant__ CUtensorMap map2,
+// Shared memory of the single-cavity kernel: S input stages, with TS two
+// output tiles, and S mbarriers.
+__host__ __device__ constexpr size_t step_tma_smem_bytes(bool split, bool ts, int R, int S, int f_bytes,
+                                                         int g_bytes) {
+    return (size_t)S * tma_stage_bytes_fg(R, f_bytes, g_bytes) +
+           (ts ? 2 * out_tile_bytes(split, R, kTmaBox - 2 * tma_halo(f_bytes < g_bytes ? f_bytes : g_bytes),
+                                    f_bytes, g_bytes)
+               : 0) +
+           (size_t)S * 8;
+}
+
+// Epilogue. TS false: every thread stores its nodes to global memory. TS true:
+// results go through a shared-memory output tile (two, alternating) and leave
+// by tensor store: one elected thread stores item k after the barrier that
+// ends it; before that barrier it waits until the store of item k - 1 has read
+// its tile, which item k + 1 then overwrites.
+template <typename L, int NPT, int R, int S, bool SR, bool TS>
+__global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_constant__ TmaMaps M,
                                                           StepArgs A, StepConsts K, TmaGeo T) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     constexpr uint32_t kStageBytes = (uint32_t)tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
-    unsigned char* stages = smem_raw;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);
     constexpr int HALO = L::kHalo;
     constexpr int STRIP = kTmaBox - 2 * HALO;
+    constexpr size_t kOutBytes = out_tile_bytes(L::kSplit, R, STRIP, sizeof(Ef), sizeof(Eg));
+    constexpr size_t kOutG = out_g_offset(L::kSplit, R, STRIP, sizeof(Ef));
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* stages = smem_raw;
+    unsigned char* outs = smem_raw + (size_t)S * kStageBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(outs + (TS ? 2 * kOutBytes : 0));
     constexpr int TPR = 256 / NPT;   // threads per row of a strip
     constexpr int PB = R * kTmaBox;  // elements of one plane in a stage
     const int tid = threadIdx.x;
@@ -509,9 +579,9 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     __syncthreads();
 
     // One item: every plane's R rows of row block rb, groups P and N taken one
-    // row below / above (their e_y). One-type layout: map0 has 6-plane boxes
-    // (group Z), map1 4-plane boxes (P, N); map2 is unused. Split layout: map0
-    // has 3-plane flow boxes, map1 3-plane thermal boxes, map2 1-plane thermal boxes.
+    // row below / above (their e_y). One-type layout: ld[0] has 6-plane boxes
+    // (group Z), ld[1] 4-plane boxes (P, N). Split layout: ld[0] has 3-plane
+    // flow boxes, ld[1] 3-plane thermal boxes, ld[2] 1-plane thermal boxes.
     auto issue = [&](const ItemCursor& c, int s) {
         const int x = c.strip * STRIP - HALO;
         const int j0 = c.rb * R;
@@ -519,19 +589,28 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         mbar_expect_tx(&bars[s], kStageBytes);
         if constexpr (!L::kSplit) {
             Ef* e = reinterpret_cast<Ef*>(st);
-            tma_load_3d(e, &map0, x, j0, kGroupZ, &bars[s]);
-            tma_load_3d(e + kGroupP * PB, &map1, x, j0 - 1, kGroupP, &bars[s]);
-            tma_load_3d(e + kGroupN * PB, &map1, x, j0 + 1, kGroupN, &bars[s]);
+            tma_load_3d(e, &M.ld[0], x, j0, kGroupZ, &bars[s]);
+            tma_load_3d(e + kGroupP * PB, &M.ld[1], x, j0 - 1, kGroupP, &bars[s]);
+            tma_load_3d(e + kGroupN * PB, &M.ld[1], x, j0 + 1, kGroupN, &bars[s]);
         } else {
             Ef* f = reinterpret_cast<Ef*>(st);
             Eg* g = reinterpret_cast<Eg*>(st + (size_t)9 * PB * sizeof(Ef));
-            tma_load_3d(f, &map0, x, j0, 0, &bars[s]);
-            tma_load_3d(f + 3 * PB, &map0, x, j0 - 1, 3, &bars[s]);
-            tma_load_3d(f + 6 * PB, &map0, x, j0 + 1, 6, &bars[s]);
-            tma_load_3d(g, &map1, x, j0, 0, &bars[s]);
-            tma_load_3d(g + 3 * PB, &map2, x, j0 - 1, 3, &bars[s]);
-            tma_load_3d(g + 4 * PB, &map2, x, j0 + 1, 4, &bars[s]);
+            tma_load_3d(f, &M.ld[0], x, j0, 0, &bars[s]);
+            tma_load_3d(f + 3 * PB, &M.ld[0], x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(f + 6 * PB, &M.ld[0], x, j0 + 1, 6, &bars[s]);
+            tma_load_3d(g, &M.ld[1], x, j0, 0, &bars[s]);
+            tma_load_3d(g + 3 * PB, &M.ld[2], x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(g + 4 * PB, &M.ld[2], x, j0 + 1, 4, &bars[s]);
         }
+    };
+    // Item (strip, rb) from output tile o: a box of STRIP x R x planes at the
+    // strip's first node (a multiple of 16 bytes).
+    auto store = [&](int strip, int rb, const unsigned char* o) {
+        const int x = strip * STRIP;
+        const int j0 = rb * R;
+        tma_store_3d(&M.st[0], o, x, j0, 0);
+        if constexpr (L::kSplit) tma_store_3d(&M.st[1], o + kOutG, x, j0, 0);
+        bulk_commit();
     };
 
     // Producer (thread 0): issues items ahead of the consumers, S - 1 in flight.
@@ -566,19 +645,27 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         }
         const bool ok = mbar_wait_bounded(&bars[s], phase);
 
-        process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, A, K, cc.strip, cc.rb, rg, t, ok, salt,
-                                 STRIP, kTmaBox, R, kGroupP * PB, kGroupN * PB);
-        // All threads are done with stage s; a timeout anywhere ends the block.
+        unsigned char* out = outs + (size_t)(k & 1) * kOutBytes;
+        process_item<L, NPT, SR, TS>(stages + (size_t)s * kStageBytes, A, K, cc.strip, cc.rb, rg, t, ok, salt,
+                                     STRIP, kTmaBox, R, kGroupP * PB, kGroupN * PB, out);
+        if constexpr (TS) {
+            fence_async_smem();
+            if (tid == 0) bulk_wait_read_all();  // item k - 1's store has read the other tile
+        }
+        // All threads are done with stage s and have filled tile k & 1; a
+        // timeout anywhere ends the block.
         if (__syncthreads_or(!ok)) {
             timed_out = true;
             break;
         }
+        if (TS && tid == 0) store(cc.strip, cc.rb, out);
         cc.advance(T.n_strips);
         if (++s == S) {
             s = 0;
             phase ^= 1u;
         }
     }
+    if (TS && tid == 0) bulk_wait_all();  // the stores have read their tiles and written global memory
     if (timed_out && tid == 0) {
         atomicOr(A.err, kErrTimeout);
         // Let the copies this block issued land before its shared memory is released.

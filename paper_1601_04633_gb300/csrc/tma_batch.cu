@@ -6,14 +6,14 @@
 namespace dmrt {
 
 static const TmaVariant kVariants[] = {
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 2, (const void*)step_tma_batch_kernel<1, 1, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 2, (const void*)step_tma_batch_kernel<1, 2, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 2, (const void*)step_tma_batch_kernel<1, 4, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 3, (const void*)step_tma_batch_kernel<1, 4, 3>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 2, 2, (const void*)step_tma_batch_kernel<2, 2, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 4, 2, (const void*)step_tma_batch_kernel<2, 4, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 1, 4, (const void*)step_tma_batch_kernel<4, 1, 4>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 4, 2, (const void*)step_tma_batch_kernel<4, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<1, 1, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<1, 2, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<1, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 3, 0, (const void*)step_tma_batch_kernel<1, 4, 3>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 2, 2, 0, (const void*)step_tma_batch_kernel<2, 2, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<2, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<4, 1, 4>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<4, 4, 2>},
 };
 
 const TmaVariant* tma_variants_batch(int* n) {

@@ -10,16 +10,16 @@ namespace dmrt {
 using Mixed = Split<__half, float>;
 
 static const TmaVariant kVariants[] = {
-    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 1, 2, (const void*)step_tma_kernel<Mixed, 1, 1, 2, false>},
-    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 2, 2, (const void*)step_tma_kernel<Mixed, 1, 2, 2, false>},
-    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 4, 2, (const void*)step_tma_kernel<Mixed, 1, 4, 2, false>},
-    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 2, (const void*)step_tma_kernel<Mixed, 2, 2, 2, false>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 1, 2, (const void*)step_tma_kernel<Mixed, 1, 1, 2, true>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 2, 2, (const void*)step_tma_kernel<Mixed, 1, 2, 2, true>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 2, (const void*)step_tma_kernel<Mixed, 1, 4, 2, true>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 3, (const void*)step_tma_kernel<Mixed, 1, 4, 3, true>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 2, (const void*)step_tma_kernel<Mixed, 2, 2, 2, true>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 4, 2, (const void*)step_tma_kernel<Mixed, 2, 4, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 1, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 1, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 2, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 4, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 4, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 2, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 1, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 1, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 2, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 4, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 3, 1, (const void*)step_tma_kernel<Mixed, 1, 4, 3, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 2, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 4, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 4, 2, true, true>},
 };
 
 const TmaVariant* tma_variants_mixed(int* n) {

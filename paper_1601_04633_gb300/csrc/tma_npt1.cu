@@ -6,15 +6,15 @@
 namespace dmrt {
 
 static const TmaVariant kVariants[] = {
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 2, (const void*)step_tma_kernel<OneType<float>, 1, 1, 2, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 3, (const void*)step_tma_kernel<OneType<float>, 1, 1, 3, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 4, (const void*)step_tma_kernel<OneType<float>, 1, 1, 4, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 5, (const void*)step_tma_kernel<OneType<float>, 1, 1, 5, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 2, (const void*)step_tma_kernel<OneType<float>, 1, 2, 2, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 3, (const void*)step_tma_kernel<OneType<float>, 1, 2, 3, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 3, 2, (const void*)step_tma_kernel<OneType<float>, 1, 3, 2, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 2, (const void*)step_tma_kernel<OneType<float>, 1, 4, 2, false>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 3, (const void*)step_tma_kernel<OneType<float>, 1, 4, 3, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 2, 0, (const void*)step_tma_kernel<OneType<float>, 1, 1, 2, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 3, 0, (const void*)step_tma_kernel<OneType<float>, 1, 1, 3, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 4, 0, (const void*)step_tma_kernel<OneType<float>, 1, 1, 4, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 5, 0, (const void*)step_tma_kernel<OneType<float>, 1, 1, 5, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 2, 0, (const void*)step_tma_kernel<OneType<float>, 1, 2, 2, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 3, 0, (const void*)step_tma_kernel<OneType<float>, 1, 2, 3, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 3, 2, 0, (const void*)step_tma_kernel<OneType<float>, 1, 3, 2, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 2, 0, (const void*)step_tma_kernel<OneType<float>, 1, 4, 2, false, false>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 3, 0, (const void*)step_tma_kernel<OneType<float>, 1, 4, 3, false, false>},
 };
 
 const TmaVariant* tma_variants_npt1(int* n) {

@@ -9,6 +9,7 @@ struct TmaVariant {
     int storage;   // DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED
     int rounding;  // DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC
     int npt, R, S;
+    int ts;  // 1: tensor-store epilogue through shared-memory output tiles
     const void* func;
 };
 

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_1601_04633_gb300 import inputs
+from paper_1601_04633_gb300 import inputs, tune
 
 pytestmark = pytest.mark.gpu
 
@@ -192,9 +192,7 @@ def test_deterministic_and_graph_equals_single_launches(D, kernel):
     assert np.array_equal(na, nb) and np.array_equal(na, nc)
 
 
-TMA_TILES = ([(4, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (2, 2), (2, 3), (2, 4), (4, 2), (4, 3)]]
-             + [(2, r, s) for r, s in [(1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (4, 2)]]
-             + [(1, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (3, 2), (4, 2), (4, 3)]])
+TMA_TILES = tune.SINGLE_TILES_FP32  # every compiled float32 tile
 
 
 def test_all_kernel_variants_agree_bitwise(D):

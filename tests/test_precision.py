@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_1601_04633_gb300 import inputs
+from paper_1601_04633_gb300 import inputs, tune
 
 pytestmark = pytest.mark.gpu
 
@@ -123,9 +123,7 @@ def test_long_run_error_report(D, storage, rounding):
         assert np.isfinite(nu_err) and nu_err < 1.0 and th_err < 1.0
 
 
-TILES = {(1, 1): [(1, 1, 2), (1, 4, 2), (2, 2, 2), (4, 4, 2)],
-         (3, 0): [(1, 1, 2), (1, 2, 2), (1, 4, 2), (2, 2, 2)],
-         (3, 1): [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 2, 2), (2, 4, 2)]}
+TILES = {(1, 1): tune.SINGLE_TILES_16_SR, (3, 0): tune.SINGLE_TILES_MIXED, (3, 1): tune.SINGLE_TILES_MIXED_SR}
 
 
 @pytest.mark.parametrize("storage,rounding", list(TILES), ids=["fp16_sr", "mixed", "mixed_sr"])
