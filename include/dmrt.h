@@ -194,6 +194,31 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold);
 int dmrt_get_state(dmrt_ctx* c, float* host);
 int dmrt_set_state(dmrt_ctx* c, const float* host);
 
+/* ---- Checkpoint and resume (the paper has no counterpart) ----
+ *
+ * dmrt_save writes a self-describing checkpoint of everything a later step
+ * reads into a caller-owned host buffer: the population state of the current
+ * time level in its stored representation (bit for bit, also for 16-bit and
+ * mixed storage), the step count and the device step counter (which seeds the
+ * stochastic rounding), the wall profiles, the local and latest mean Nusselt
+ * numbers, the recorded part of the Nusselt ring (at most nu_capacity values)
+ * and the error word, followed by a 64-bit FNV-1a checksum. Layout:
+ * little-endian header (magic "DMRTCKP1", version, grid, storage, the
+ * physical parameters it was taken with), then the sections in that order.
+ * With host_buf == NULL only *used is set to the size needed. Errors:
+ * DMRT_E_ARG (c or used NULL), DMRT_E_SPACE (cap < needed; *used is set).
+ * Synchronises the context's stream.
+ *
+ * dmrt_load restores such a checkpoint into a context created with the same
+ * nx, ny and storage (its own Ra, Pr, walls and rounding govern the steps
+ * after it). Stepping after a load continues bit for bit as the saved context
+ * would have. The Nusselt ring keeps the last min(saved, nu_capacity) values.
+ * Errors: DMRT_E_ARG (NULL or too short), DMRT_E_STATE (wrong magic, version,
+ * grid or storage, or a checksum mismatch; the context is unchanged).
+ * Synchronises. */
+int dmrt_save(dmrt_ctx* c, void* host_buf, size_t cap, size_t* used);
+int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size);
+
 /* ---- One step without any device allocation (the paper has no counterpart) ----
  *
  * For callers that cannot allocate device memory where they step a cavity: code

@@ -98,6 +98,7 @@ struct dmrt_ctx {
     dmrt::TmaMaps tmaps[2];  // per source buffer: the step kernel's load and store maps
     cudaGraphExec_t graph[2];
     int graph_len;
+    long long nu_floor;  // ring values of steps before this one are unavailable (after a load)
     char err[256];
 };
 
@@ -599,6 +600,7 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     c->t = 0;
     c->graph[0] = c->graph[1] = nullptr;
     c->graph_len = 64;
+    c->nu_floor = 0;
     c->err[0] = 0;
 
     dmrt::StepConsts& s = c->sc;
@@ -815,7 +817,7 @@ int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
     if (series && cap > 0) {
         const long long R = c->p.nu_capacity;
         const long long recorded = m.step[c->cur];
-        long long avail = std::min<long long>(recorded, R);
+        long long avail = std::min<long long>(recorded - c->nu_floor, R);
         long long want = std::min<long long>(avail, cap);
         long long first = recorded - want;  // step index of the oldest value returned
         const double* ring = reinterpret_cast<const double*>(c->ws + c->L.off_ring);
@@ -922,6 +924,201 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
         CK(cudaGetLastError(), "state conversion");
     }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    return DMRT_OK;
+}
+
+// ---- checkpoint and resume ----------------------------------------------------
+namespace {
+
+constexpr char kCkptMagic[8] = {'D', 'M', 'R', 'T', 'C', 'K', 'P', '1'};
+constexpr uint32_t kCkptVersion = 1;
+
+struct CkptHeader {
+    char magic[8];
+    uint32_t version;
+    uint32_t header_bytes;
+    int32_t nx, ny, storage, rounding;
+    int32_t left_wall, right_wall;
+    double Ra, Pr, alpha, theta_hot, theta_cold, theta_ref;
+    int64_t t;          // steps taken
+    int64_t recorded;   // device step counter of the current buffer
+    int64_t n_series;   // most recent mean-Nu values saved
+    double nu_last;
+    uint32_t err;
+    uint32_t reserved;
+    uint64_t state_bytes;
+};
+
+// 64-bit FNV-1a (Fowler, Noll, Vo).
+uint64_t fnv1a64(const unsigned char* p, size_t n) {
+    uint64_t h = 14695981039346656037ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+size_t plane_elem_bytes(const dmrt_params& p, int k) { return plane_storage(p, k) == DMRT_FP32 ? 4 : 2; }
+
+size_t ckpt_state_bytes(const dmrt_params& p) {
+    size_t s = 0;
+    for (int k = 0; k < kPlanes; ++k) s += plane_elem_bytes(p, k) * (size_t)p.nx * p.ny;
+    return s;
+}
+
+size_t ckpt_bytes(const dmrt_params& p, int64_t n_series) {
+    return sizeof(CkptHeader) + 2 * (size_t)p.ny * sizeof(float) + (size_t)p.ny * sizeof(double) +
+           (size_t)n_series * sizeof(double) + ckpt_state_bytes(p) + sizeof(uint64_t);
+}
+
+}  // namespace
+
+int dmrt_save(dmrt_ctx* c, void* host_buf, size_t cap, size_t* used) {
+    if (!c || !used) return DMRT_E_ARG;
+    const dmrt_params& p = c->p;
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    Misc m;
+    CK(cudaMemcpy(&m, misc(c), sizeof m, cudaMemcpyDeviceToHost), "read scalars");
+    const long long recorded = m.step[c->cur];
+    const long long n_series = std::min<long long>(recorded - c->nu_floor, p.nu_capacity);
+    const size_t need = ckpt_bytes(p, n_series);
+    *used = need;
+    if (!host_buf) return DMRT_OK;
+    if (cap < need) {
+        set_err(c, "checkpoint needs %zu bytes, buffer has %zu", need, cap);
+        return DMRT_E_SPACE;
+    }
+    unsigned char* base = static_cast<unsigned char*>(host_buf);
+    unsigned char* o = base;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = kCkptVersion;
+    h.header_bytes = sizeof h;
+    h.nx = p.nx;
+    h.ny = p.ny;
+    h.storage = p.storage;
+    h.rounding = p.rounding;
+    h.left_wall = p.left_wall;
+    h.right_wall = p.right_wall;
+    h.Ra = p.Ra;
+    h.Pr = p.Pr;
+    h.alpha = c->k.alpha;
+    h.theta_hot = p.theta_hot;
+    h.theta_cold = p.theta_cold;
+    h.theta_ref = p.theta_ref;
+    h.t = c->t;
+    h.recorded = recorded;
+    h.n_series = n_series;
+    h.nu_last = m.nu_last;
+    h.err = m.err;
+    h.state_bytes = ckpt_state_bytes(p);
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    const size_t ny = (size_t)p.ny, nx = (size_t)p.nx;
+    CK(cudaMemcpy(o, c->ws + c->L.off_hot, ny * sizeof(float), cudaMemcpyDeviceToHost), "copy hot wall");
+    o += ny * sizeof(float);
+    CK(cudaMemcpy(o, c->ws + c->L.off_cold, ny * sizeof(float), cudaMemcpyDeviceToHost), "copy cold wall");
+    o += ny * sizeof(float);
+    CK(cudaMemcpy(o, c->ws + c->L.off_rows, ny * sizeof(double), cudaMemcpyDeviceToHost), "copy local Nu");
+    o += ny * sizeof(double);
+    // Mean Nu of steps recorded - n_series .. recorded - 1, oldest first (ring slot = step % capacity).
+    const double* ring = reinterpret_cast<const double*>(c->ws + c->L.off_ring);
+    const long long R = p.nu_capacity;
+    for (long long done = 0; done < n_series;) {
+        const long long slot = (recorded - n_series + done) % R;
+        const long long run = std::min<long long>(n_series - done, R - slot);
+        CK(cudaMemcpy(o + done * sizeof(double), ring + slot, run * sizeof(double), cudaMemcpyDeviceToHost),
+           "copy Nu series");
+        done += run;
+    }
+    o += n_series * sizeof(double);
+    // Population planes in host order (f_1..f_9, g_1..g_5), stored representation, x < nx.
+    for (int k = 0; k < kPlanes; ++k) {
+        const size_t eb = plane_elem_bytes(p, k);
+        const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        CK(cudaMemcpy2D(o, nx * eb, P, (size_t)c->L.pitch * eb, nx * eb, ny, cudaMemcpyDeviceToHost),
+           "copy state plane");
+        o += nx * ny * eb;
+    }
+    const uint64_t sum = fnv1a64(base, (size_t)(o - base));
+    std::memcpy(o, &sum, sizeof sum);
+    return DMRT_OK;
+}
+
+int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size) {
+    if (!c || !host_buf || size < sizeof(CkptHeader) + sizeof(uint64_t)) {
+        if (c) set_err(c, "checkpoint buffer missing or shorter than its header");
+        return DMRT_E_ARG;
+    }
+    const dmrt_params& p = c->p;
+    const unsigned char* base = static_cast<const unsigned char*>(host_buf);
+    CkptHeader h;
+    std::memcpy(&h, base, sizeof h);
+    if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != kCkptVersion || h.header_bytes != sizeof h) {
+        set_err(c, "not a checkpoint of this format (magic / version)");
+        return DMRT_E_STATE;
+    }
+    if (h.nx != p.nx || h.ny != p.ny || h.storage != p.storage) {
+        set_err(c, "checkpoint of a %d x %d grid with storage %d; this context is %d x %d with storage %d", h.nx,
+                h.ny, h.storage, p.nx, p.ny, p.storage);
+        return DMRT_E_STATE;
+    }
+    if (h.recorded < 0 || h.n_series < 0 || h.n_series > h.recorded || h.t < 0 ||
+        h.state_bytes != ckpt_state_bytes(p)) {
+        set_err(c, "inconsistent checkpoint header");
+        return DMRT_E_STATE;
+    }
+    const size_t need = ckpt_bytes(p, h.n_series);
+    if (size < need) {
+        set_err(c, "checkpoint truncated: %zu bytes of %zu", size, need);
+        return DMRT_E_ARG;
+    }
+    uint64_t sum;
+    std::memcpy(&sum, base + need - sizeof sum, sizeof sum);
+    if (sum != fnv1a64(base, need - sizeof sum)) {
+        set_err(c, "checkpoint checksum mismatch");
+        return DMRT_E_STATE;
+    }
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    const unsigned char* o = base + sizeof h;
+    const size_t ny = (size_t)p.ny, nx = (size_t)p.nx;
+    CK(cudaMemcpy(c->ws + c->L.off_hot, o, ny * sizeof(float), cudaMemcpyHostToDevice), "copy hot wall");
+    o += ny * sizeof(float);
+    CK(cudaMemcpy(c->ws + c->L.off_cold, o, ny * sizeof(float), cudaMemcpyHostToDevice), "copy cold wall");
+    o += ny * sizeof(float);
+    CK(cudaMemcpy(c->ws + c->L.off_rows, o, ny * sizeof(double), cudaMemcpyHostToDevice), "copy local Nu");
+    o += ny * sizeof(double);
+    // Keep the last min(n_series, capacity) values, each in its step's ring slot.
+    double* ring = reinterpret_cast<double*>(c->ws + c->L.off_ring);
+    const long long R = p.nu_capacity;
+    const long long keep = std::min<long long>(h.n_series, R);
+    const unsigned char* series = o + (h.n_series - keep) * sizeof(double);
+    for (long long done = 0; done < keep;) {
+        const long long slot = (h.recorded - keep + done) % R;
+        const long long run = std::min<long long>(keep - done, R - slot);
+        CK(cudaMemcpy(ring + slot, series + done * sizeof(double), run * sizeof(double), cudaMemcpyHostToDevice),
+           "copy Nu series");
+        done += run;
+    }
+    o += h.n_series * sizeof(double);
+    for (int k = 0; k < kPlanes; ++k) {
+        const size_t eb = plane_elem_bytes(p, k);
+        char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        CK(cudaMemcpy2D(P, (size_t)c->L.pitch * eb, o, nx * eb, nx * eb, ny, cudaMemcpyHostToDevice),
+           "copy state plane");
+        o += nx * ny * eb;
+    }
+    Misc m;
+    std::memset(&m, 0, sizeof m);
+    m.step[0] = m.step[1] = h.recorded;
+    m.nu_last = h.nu_last;
+    m.counter = 0u;
+    m.err = h.err;
+    CK(cudaMemcpy(misc(c), &m, sizeof m, cudaMemcpyHostToDevice), "write scalars");
+    c->t = h.t;
+    c->nu_floor = h.recorded - keep;
     return DMRT_OK;
 }
 

@@ -114,6 +114,8 @@ SIGNATURES = {
     "dmrt_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
+    "dmrt_save": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_load": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
     "dmrt_adjoint_workspace_size": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "dmrt_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _DP, _DP, _DP]),
@@ -261,6 +263,21 @@ def dmrt_set_state(h, state):
     _check(load().dmrt_set_state(h, a.ctypes.data_as(_FP)), h)
 
 
+def dmrt_save(h) -> bytes:
+    """Checkpoint of the context (state in its stored representation, step
+    counters, wall profiles, Nusselt ring) as bytes."""
+    need = ctypes.c_size_t(0)
+    _check(load().dmrt_save(h, None, 0, ctypes.byref(need)), h)
+    buf = ctypes.create_string_buffer(need.value)
+    _check(load().dmrt_save(h, ctypes.cast(buf, _VP), need.value, ctypes.byref(need)), h)
+    return buf.raw[: need.value]
+
+
+def dmrt_load(h, blob: bytes):
+    b = bytes(blob)
+    _check(load().dmrt_load(h, ctypes.cast(ctypes.c_char_p(b), _VP), len(b)), h)
+
+
 def dmrt_step_noalloc(p: Params, src_ptr: int, dst_ptr: int, nu_mean_ptr: int, stream_ptr: int,
                       hot_ptr: int = 0, cold_ptr: int = 0):
     """One step between caller-owned device buffers, with no device allocation."""
@@ -378,6 +395,25 @@ class Cavity2D:
 
     def set_state(self, state):
         dmrt_set_state(self.h, state)
+
+    def save(self, path=None) -> bytes:
+        """Checkpoint (bytes; also written to ``path`` when given)."""
+        blob = dmrt_save(self.h)
+        if path is not None:
+            tmp = str(path) + ".tmp"
+            with open(tmp, "wb") as fh:
+                fh.write(blob)
+            os.replace(tmp, path)
+        return blob
+
+    def load(self, blob_or_path):
+        """Resume from a checkpoint made by ``save`` (bytes or a file path)."""
+        if isinstance(blob_or_path, (bytes, bytearray, memoryview)):
+            blob = bytes(blob_or_path)
+        else:
+            with open(blob_or_path, "rb") as fh:
+                blob = fh.read()
+        dmrt_load(self.h, blob)
 
     def nusselt(self, series_cap: int = 0):
         return dmrt_nusselt(self.h, self.ny, series_cap)
