@@ -1171,6 +1171,7 @@ struct dmrt_batch {
     CUtensorMap* d_maps;
     unsigned* d_err;
     int total_items;
+    int static_per_block;  // items each block takes before drawing from the shared pool
     int npt, R, S, grid, block;
     size_t smem;
     const void* func;
@@ -1237,7 +1238,7 @@ int batch_cuda_fail(dmrt_batch* b, cudaError_t e, const char* what) {
     } while (0)
 
 int batch_launch(dmrt_batch* b, int parity) {
-    void* params[6] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &parity, &b->d_err};
+    void* params[7] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &b->static_per_block, &parity, &b->d_err};
     BCK(cudaLaunchKernel(b->func, dim3(b->grid), dim3(b->block), params, b->smem, b->stream),
         "batch step launch");
     return DMRT_OK;
@@ -1250,7 +1251,8 @@ int batch_build_graph(dmrt_batch* b, int from) {
     int par[2] = {from, 1 - from};
     for (int i = 0; i < b->graph_len; ++i) {
         cudaKernelNodeParams kp = {};
-        void* params[6] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &par[i & 1], &b->d_err};
+        void* params[7] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &b->static_per_block, &par[i & 1],
+                           &b->d_err};
         kp.func = const_cast<void*>(b->func);
         kp.gridDim = dim3(b->grid);
         kp.blockDim = dim3(b->block);
@@ -1429,6 +1431,8 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         return fail(DMRT_E_ARG);
     }
     b->grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+    // Three quarters of the items are split statically, the rest are drawn at run time.
+    b->static_per_block = (int)(items * 3 / 4 / b->grid);
     *out = b;
     return DMRT_OK;
 }

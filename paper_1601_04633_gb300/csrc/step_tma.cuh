@@ -79,6 +79,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -675,11 +679,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
 
 // ---- batched sweep ------------------------------------------------------------
 // One launch steps every cavity of a batch. The work items of all cavities
-// form one list, cavity after cavity (strip fastest, then row block); each
-// block of the persistent grid takes one contiguous chunk of it, so consecutive
-// items of a block mostly belong to one cavity. The producer and the
-// consumers walk the same cursor through the chunk (the consumers S - 1 items
-// behind), so no item descriptor has to pass through shared memory.
+// form one list, cavity after cavity (strip fastest, then row block), which
+// the blocks of the persistent grid share out as described at the kernel.
 // Float32 storage only.
 // Each cavity has its own strip geometry: strips of W nodes (a multiple of
 // 32 NPT, so that every warp stays within one row), boxes WB = W + 8 elements
@@ -697,49 +698,31 @@ struct BatchCavity {
     int pad2;
 };
 
-struct BatchCursor {
-    int c, strip, rb;
-    __device__ __forceinline__ void init(const BatchCavity* __restrict__ cav, int n_cav, int item) {
-        int lo = 0, hi = n_cav - 1;  // last cavity whose item_base <= item
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (cav[mid].item_base <= item) lo = mid;
-            else hi = mid - 1;
-        }
-        c = lo;
-        const int local = item - cav[c].item_base;
-        const int ns = cav[c].n_strips;
-        strip = local % ns;
-        rb = local / ns;
-    }
-    __device__ __forceinline__ void advance(const BatchCavity* __restrict__ cav) {
-        if (++strip == cav[c].n_strips) {
-            strip = 0;
-            if (++rb == cav[c].n_rowblocks) {
-                rb = 0;
-                ++c;
-            }
-        }
-    }
-};
-
+// Work distribution: block b first takes the static items [b Q, (b + 1) Q)
+// (contiguous, so mostly one cavity), then draws single items from the
+// dynamic pool [G Q, total) through a per-launch counter. Items of narrow
+// cavities cost more per node (every item carries side walls and the Nusselt
+// rows), so a static split by item count leaves a long tail; the pool evens it
+// out. Which block computes an item does not change its result. The producer
+// (thread 0) picks the items and passes each one's (cavity, strip, row block)
+// to the consumers through shared memory with the stage; an item of -1 ends
+// the block. Counters: ctr[parity] serves this launch; this launch zeroes
+// ctr[1 - parity] for the next one.
 template <int NPT, int R, int S>
 __global__ void __launch_bounds__(R * (256 / NPT))
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
-                          int n_cav, int total_items, int parity, unsigned* batch_err) {
+                          int n_cav, int total_items, int static_per_block, int parity, unsigned* batch_err) {
     using E = float;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     E* stages = reinterpret_cast<E*>(smem_raw);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * tma_stage_elems(R) * sizeof(E));
+    __shared__ int4 stage_item[S];  // (cavity, strip, row block, item) of each stage; cavity -1: no more items
     constexpr int HALO = tma_halo(sizeof(E));
     const int tid = threadIdx.x;
+    unsigned* ctr = batch_err + 1;
 
     if (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout) return;
-
-    const int first = (int)((long long)blockIdx.x * total_items / gridDim.x);
-    const int last = (int)((long long)(blockIdx.x + 1) * total_items / gridDim.x);
-    const int count = last - first;
-    if (count <= 0) return;
+    if (blockIdx.x == 0 && tid == 0) ctr[1 - parity] = 0u;
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
@@ -747,12 +730,38 @@ __global__ void __launch_bounds__(R * (256 / NPT))
     }
     __syncthreads();
 
+    // Producer state (thread 0 only).
+    int next_static = blockIdx.x * static_per_block;
+    const int static_end = next_static + static_per_block;
+    const int pool_base = gridDim.x * static_per_block;
+    bool drained = false;
+    int pc = 0;  // cavity of the last item issued (items issued by a block increase)
+    auto next_item = [&]() -> int {
+        if (next_static < static_end) return next_static++;
+        if (drained) return -1;
+        const int it = pool_base + (int)atomicAdd(&ctr[parity], 1u);
+        if (it >= total_items) {
+            drained = true;
+            return -1;
+        }
+        return it;
+    };
     // maps[(c * 2 + buffer) * 2 + 0]: 6-plane boxes, [... + 1]: 4-plane boxes.
-    auto issue = [&](const BatchCursor& q, int s) {
-        const BatchCavity& bc = cav[q.c];
-        const int x = q.strip * bc.W - HALO;
-        const int j0 = q.rb * bc.RC;
-        const CUtensorMap* m = maps + ((size_t)q.c * 2 + parity) * 2;
+    auto issue = [&](int it, int s) {
+        if (it < 0) {
+            stage_item[s] = make_int4(-1, 0, 0, -1);
+            mbar_arrive(&bars[s]);  // completes the phase with nothing to load
+            return;
+        }
+        while (pc + 1 < n_cav && cav[pc + 1].item_base <= it) ++pc;
+        const BatchCavity& bc = cav[pc];
+        const int local = it - bc.item_base;
+        const int rb = local / bc.n_strips;
+        const int strip = local - rb * bc.n_strips;
+        stage_item[s] = make_int4(pc, strip, rb, it);
+        const int x = strip * bc.W - HALO;
+        const int j0 = rb * bc.RC;
+        const CUtensorMap* m = maps + ((size_t)pc * 2 + parity) * 2;
         E* st = stages + (size_t)s * tma_stage_elems(R);
         mbar_expect_tx(&bars[s], bc.stage_bytes);
         tma_load_3d(st, m, x, j0, kGroupZ, &bars[s]);
@@ -760,41 +769,44 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         tma_load_3d(st + bc.offN, m + 1, x, j0 + 1, kGroupN, &bars[s]);
     };
 
-    BatchCursor pc;
-    pc.init(cav, n_cav, first);
     int issued = 0;
     if (tid == 0) {
-        for (int q = 0; q < S - 1 && q < count; ++q) {
-            issue(pc, q);
-            pc.advance(cav);
+        for (int q = 0; q < S - 1; ++q) {
+            issue(next_item(), q);
             issued = q + 1;
         }
     }
-    BatchCursor cc;
-    cc.init(cav, n_cav, first);
     bool timed_out = false;
     int k = 0, s = 0;
     uint32_t phase = 0;
-    for (; k < count; ++k) {
-        if (tid == 0 && k + S - 1 < count) {
+    for (;; ++k) {
+        if (tid == 0) {
+            // Item k + S - 1 goes to the stage of item k - 1, released by the
+            // barrier that ended it.
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            issue(pc, s == 0 ? S - 1 : s - 1);
-            pc.advance(cav);
+            issue(next_item(), s == 0 ? S - 1 : s - 1);
             issued = k + S;
         }
         const bool ok = mbar_wait_bounded(&bars[s], phase);
-        const BatchCavity& bc = cav[cc.c];
+        // Every thread reads the same entry; a thread whose wait expired may
+        // read a stale one, and the barrier below then ends the block anyway.
+        const int4 w = stage_item[s];
+        const bool work = ok && w.x >= 0;
+        const BatchCavity& bc = cav[work ? w.x : 0];
         const int tpr = bc.tpr;
         const int rg = tid / tpr;
         const int t = tid - rg * tpr;
         process_item<OneType<E>, NPT, false>(reinterpret_cast<const unsigned char*>(stages + (size_t)s * tma_stage_elems(R)),
-                                             bc.args[parity], bc.K, cc.strip, cc.rb, rg, t, ok, 0u, bc.W, bc.WB,
+                                             bc.args[parity], bc.K, work ? w.y : 1, w.z, rg, t, work, 0u, bc.W, bc.WB,
                                              bc.RC, bc.offP, bc.offN);
-        if (__syncthreads_or(!ok)) {
+        // One barrier per item: it releases the stage and tells every thread
+        // whether any wait expired; with none expired, w is the same valid
+        // entry in every thread, so the end test is block-uniform.
+        if (__syncthreads_count(!ok)) {
             timed_out = true;
             break;
         }
-        cc.advance(cav);
+        if (w.x < 0) break;
         if (++s == S) {
             s = 0;
             phase ^= 1u;
