@@ -209,7 +209,8 @@ __device__ __forceinline__ void store_quad(const StepArgs& A, int j, int x0, con
 
 // Hot-wall Nusselt number (Eqs. 18-19). Called by all 32 lanes of a warp; the
 // lane with has_nu holds row j's local value. The warp that completes the
-// count of ny rows sums them in a fixed order (lane-strided, then a butterfly),
+// count of ny rows sums them in a fixed order (lane-strided with eight partial
+// sums per lane, then a butterfly),
 // so the mean does not depend on which warps arrive first, and appends it to
 // the ring.
 __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j, double nuj) {
@@ -225,7 +226,20 @@ __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j,
     if (n_here && before + n_here == (unsigned)A.ny) {
         __threadfence();
         double s = 0.0;
-        for (int r = lane; r < A.ny; r += 32) s += __ldcg(A.nu_rows + r);
+        // Eight independent partial sums per lane keep eight loads in flight
+        // (rows lane + 32 (8 i + q) go to partial q); they are added in a fixed order.
+        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        int r = lane;
+        for (; r + 7 * 32 < A.ny; r += 8 * 32) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = __ldcg(A.nu_rows + r + 32 * q);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] += v[q];
+        }
+        for (int q = 0; r < A.ny; r += 32, ++q) acc[q] += __ldcg(A.nu_rows + r);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s += acc[q];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0) {
