@@ -297,6 +297,30 @@ def run_dmrt(args):
             s2.close()
             del s2
 
+    # Small cavities (state resident in L2, launch-bound): MLUPS only; the
+    # roofline fraction is reported for the large cavity and the batched sweep.
+    if not args.no_secondary and args.storage == "fp32":
+        small = {}
+        for name, cav_s, st, n_s in (("cavity_64_fp32", inputs.cavity_64(), 0, 20000),
+                                     ("cavity_128_adjoint_fp32", inputs.cavity_128_adjoint(), 0, 10000),
+                                     ("cavity_256_fp32", inputs.cavity_256_oscillatory(), 0, 20000),
+                                     ("cavity_256_mixed", inputs.cavity_256_oscillatory(), 3, 20000)):
+            s3 = D.Cavity2D.from_inputs(cav_s, nu_capacity=n_s + args.warmup, storage=st)
+            s3.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s3.step(n_s)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            s3.check()
+            ms3 = e0.elapsed_time(e1)
+            small[name] = {"value": cav_s.nx * cav_s.ny * n_s / (ms3 / 1e3) / 1e6, "unit": UNIT,
+                           "steps": n_s, "us_per_step": 1e3 * ms3 / n_s, "launch": dict(s3.launch)}
+            s3.close()
+            del s3
+        secondary["small_cavities"] = small
+
     # Batched sweep (64 cavities of uneven sizes and (Ra, Pr)): one launch per step
     # with the autotuned tile, against the same cavities stepped one after another
     # through their own contexts. Tuning runs before, and outside, the timed region.

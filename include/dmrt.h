@@ -227,8 +227,8 @@ int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size);
  * device, or plug-in hosts that forbid allocation inside their callbacks.
  * dmrt_step_noalloc advances one time step (the same fused step as dmrt_step,
  * run by the direct-load kernel) from src to dst and allocates nothing: the
- * scratch the step needs (per-row Nusselt values, the arrival counter of the
- * fused reduction, the wall temperatures, the error word) lives in one
+ * scratch the step needs (per-row Nusselt values, the step counter and pending
+ * flag of the Nusselt reduction, the wall temperatures, the error word) lives in one
  * file-scope device array of 16 * DMRT_NOALLOC_MAX_NY + 256 bytes (about 128 KB)
  * that every GPU which loads the library holds until the process exits.
  *

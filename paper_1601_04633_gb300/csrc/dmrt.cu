@@ -54,7 +54,7 @@ Layout make_layout(const dmrt_params& p) {
     L.off_b = o; o += L.buf_bytes;
     L.off_hot = o; o += align256((size_t)p.ny * sizeof(float));
     L.off_cold = o; o += align256((size_t)p.ny * sizeof(float));
-    L.off_rows = o; o += align256((size_t)p.ny * sizeof(double));
+    L.off_rows = o; o += align256((size_t)2 * p.ny * sizeof(double));  // by source buffer
     L.off_ring = o; o += align256((size_t)p.nu_capacity * sizeof(double));
     L.off_misc = o; o += 256;
     L.total = o;
@@ -66,7 +66,7 @@ struct Misc {
     long long step[2];   // steps recorded in the Nu ring; slot b is current when the
                          // state is in buffer b (a launch reads one slot, writes the other)
     double nu_last;      // mean Nu of the latest step
-    unsigned counter;    // rows reported in the running step
+    unsigned pending;    // the last step's local Nu rows are not yet summed into the ring
     unsigned err;        // error bits
 };
 
@@ -127,6 +127,10 @@ float* buf(dmrt_ctx* c, int which) {
     return reinterpret_cast<float*>(c->ws + (which == 0 ? c->L.off_a : c->L.off_b));
 }
 Misc* misc(dmrt_ctx* c) { return reinterpret_cast<Misc*>(c->ws + c->L.off_misc); }
+// Local Nu rows of the last step taken (it ran from buffer 1 - cur).
+double* last_rows(dmrt_ctx* c) {
+    return reinterpret_cast<double*>(c->ws + c->L.off_rows) + (size_t)(1 - c->cur) * c->p.ny;
+}
 
 dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
     dmrt::StepArgs A;
@@ -134,11 +138,15 @@ dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
     A.dst = buf(c, 1 - from);
     A.hot = reinterpret_cast<const float*>(c->ws + c->L.off_hot);
     A.cold = reinterpret_cast<const float*>(c->ws + c->L.off_cold);
-    A.nu_rows = reinterpret_cast<double*>(c->ws + c->L.off_rows);
+    // Local Nu rows: a step from buffer b writes rows[b] and sums rows[1 - b],
+    // those of the step before it.
+    double* rows = reinterpret_cast<double*>(c->ws + c->L.off_rows);
+    A.nu_rows = rows + (size_t)from * c->p.ny;
+    A.prev_rows = rows + (size_t)(1 - from) * c->p.ny;
     A.nu_ring = reinterpret_cast<double*>(c->ws + c->L.off_ring);
     Misc* m = misc(c);
     A.nu_last = &m->nu_last;
-    A.counter = &m->counter;
+    A.pending = &m->pending;
     A.err = &m->err;
     A.step_in = &m->step[from];
     A.step_out = &m->step[1 - from];
@@ -735,6 +743,14 @@ static int build_graph(dmrt_ctx* c, int from) {
     return DMRT_OK;
 }
 
+// After a run of steps: sum the last step's local Nusselt numbers into the ring
+// (every step sums its predecessor's; the last one has no successor yet).
+static int finalize_nu(dmrt_ctx* c) {
+    dmrt::nu_finalize_kernel<<<1, 256, 0, c->stream>>>(step_args(c, c->cur));
+    CK(cudaGetLastError(), "step launch");
+    return DMRT_OK;
+}
+
 int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
     while (nsteps > 0) {
@@ -752,7 +768,7 @@ int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
             nsteps -= 1;
         }
     }
-    CK(cudaGetLastError(), "step launch");
+    return finalize_nu(c);
     return DMRT_OK;
 }
 
@@ -811,7 +827,7 @@ int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
     CK(cudaMemcpy(&m, misc(c), sizeof m, cudaMemcpyDeviceToHost), "read scalars");
     if (nu_mean) *nu_mean = m.nu_last;
     if (nu_local)
-        CK(cudaMemcpy(nu_local, c->ws + c->L.off_rows, (size_t)c->p.ny * sizeof(double),
+        CK(cudaMemcpy(nu_local, last_rows(c), (size_t)c->p.ny * sizeof(double),
                       cudaMemcpyDeviceToHost), "copy local Nu");
     long long written = 0;
     if (series && cap > 0) {
@@ -1021,7 +1037,7 @@ int dmrt_save(dmrt_ctx* c, void* host_buf, size_t cap, size_t* used) {
     o += ny * sizeof(float);
     CK(cudaMemcpy(o, c->ws + c->L.off_cold, ny * sizeof(float), cudaMemcpyDeviceToHost), "copy cold wall");
     o += ny * sizeof(float);
-    CK(cudaMemcpy(o, c->ws + c->L.off_rows, ny * sizeof(double), cudaMemcpyDeviceToHost), "copy local Nu");
+    CK(cudaMemcpy(o, last_rows(c), ny * sizeof(double), cudaMemcpyDeviceToHost), "copy local Nu");
     o += ny * sizeof(double);
     // Mean Nu of steps recorded - n_series .. recorded - 1, oldest first (ring slot = step % capacity).
     const double* ring = reinterpret_cast<const double*>(c->ws + c->L.off_ring);
@@ -1088,7 +1104,7 @@ int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size) {
     o += ny * sizeof(float);
     CK(cudaMemcpy(c->ws + c->L.off_cold, o, ny * sizeof(float), cudaMemcpyHostToDevice), "copy cold wall");
     o += ny * sizeof(float);
-    CK(cudaMemcpy(c->ws + c->L.off_rows, o, ny * sizeof(double), cudaMemcpyHostToDevice), "copy local Nu");
+    CK(cudaMemcpy(last_rows(c), o, ny * sizeof(double), cudaMemcpyHostToDevice), "copy local Nu");
     o += ny * sizeof(double);
     // Keep the last min(n_series, capacity) values, each in its step's ring slot.
     double* ring = reinterpret_cast<double*>(c->ws + c->L.off_ring);
@@ -1114,7 +1130,7 @@ int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size) {
     std::memset(&m, 0, sizeof m);
     m.step[0] = m.step[1] = h.recorded;
     m.nu_last = h.nu_last;
-    m.counter = 0u;
+    m.pending = 0u;
     m.err = h.err;
     CK(cudaMemcpy(misc(c), &m, sizeof m, cudaMemcpyHostToDevice), "write scalars");
     c->t = h.t;
@@ -1462,6 +1478,8 @@ int dmrt_batch_step(dmrt_batch* b, int64_t nsteps) {
             done += 1;
         }
     }
+    if (nsteps > 0)  // each cavity's last step: its local Nu rows into its ring
+        dmrt::nu_finalize_batch_kernel<<<b->n, 256, 0, b->stream>>>(b->d_cav, b->parity);
     BCK(cudaGetLastError(), "batch step launch");
     b->t += nsteps;
     for (dmrt_ctx* c : b->sub) {
@@ -1546,7 +1564,7 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_nu1 = o; o += L.state;
     L.off_dthw = o; o += align256((size_t)c->p.ny * sizeof(double));
     L.off_misc = o; o += 256;
-    L.off_rows = o; o += align256((size_t)c->p.ny * sizeof(double) + 8);
+    L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
     L.total = o;
     return L;
 }
@@ -1615,10 +1633,10 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     CK(cudaMemsetAsync(w + AL.off_dthw, 0, AL.off_rows - AL.off_dthw, c->stream), "zero gradients");
     double* dgb = &scratch->nu_last;  // the scratch block's double doubles as dJ/dgbeta
     dmrt::StepArgs RA = step_args(c, 0);  // recompute: Nusselt output into scratch
-    RA.nu_rows = reinterpret_cast<double*>(w + AL.off_rows);
-    RA.nu_ring = reinterpret_cast<double*>(w + AL.off_rows) + c->p.ny;
+    double* ra_rows = reinterpret_cast<double*>(w + AL.off_rows);  // two buffers, alternating by step
+    RA.nu_ring = ra_rows + 2 * (size_t)c->p.ny;
     RA.nu_last = RA.nu_ring;
-    RA.counter = &scratch->counter;
+    RA.pending = &scratch->pending;
     RA.err = &scratch->err;
     RA.step_in = &scratch->step[0];
     RA.step_out = &scratch->step[1];
@@ -1641,6 +1659,8 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         for (long long t = 1; t < len; ++t) {  // s_{start + t} into slot t
             RA.src = t == 1 ? ckpt(q) : slot(t - 1);
             RA.dst = slot(t);
+            RA.nu_rows = ra_rows + (size_t)(t & 1) * c->p.ny;
+            RA.prev_rows = ra_rows + (size_t)((t + 1) & 1) * c->p.ny;
             dmrt::step_direct_kernel<<<c->grid, dmrt::kDirectThreads, 0, c->stream>>>(RA, c->sc);
         }
         for (long long k = end; k > start; --k) {

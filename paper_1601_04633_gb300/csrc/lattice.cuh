@@ -46,13 +46,14 @@ struct StepArgs {
     float* __restrict__ dst;        // post-collision state at time t + 1
     const float* __restrict__ hot;  // [ny] left-wall temperature
     const float* __restrict__ cold; // [ny] right-wall temperature
-    double* nu_rows;                // [ny] local Nu of the latest step
+    double* nu_rows;                // [ny] local Nu of this step
+    const double* prev_rows;        // [ny] local Nu of the previous step (summed by this step)
     double* nu_ring;                // [cap] mean Nu per step
-    double* nu_last;                // mean Nu of the latest step
-    unsigned* counter;              // rows reported in the current step
+    double* nu_last;                // mean Nu of the latest summed step
+    unsigned* pending;              // 1 while prev_rows holds a step not yet summed into the ring
     unsigned* err;                  // bit 0: non-finite value; bit 1: wait timed out
-    const long long* step_in;       // steps recorded before this launch (read by all)
-    long long* step_out;            // written once, = step_in + 1, by the reducer
+    const long long* step_in;       // steps taken before this step (read by all)
+    long long* step_out;            // written once, = step_in + 1
     int rounding;                   // 16-bit storage: 0 nearest, 1 stochastic
     long long cap;
     long long plane;  // elements per plane = ny * pitch
@@ -207,50 +208,72 @@ __device__ __forceinline__ void store_quad(const StepArgs& A, int j, int x0, con
     for (int k = 0; k < 5; ++k) *reinterpret_cast<float4*>(D + plane_g(k) * A.plane) = Gq[k];
 }
 
-// Hot-wall Nusselt number (Eqs. 18-19). Called by all 32 lanes of a warp; the
-// lane with has_nu holds row j's local value. The warp that completes the
-// count of ny rows sums them in a fixed order (lane-strided with eight partial
-// sums per lane, then a butterfly),
-// so the mean does not depend on which warps arrive first, and appends it to
-// the ring.
+// Hot-wall Nusselt number (Eqs. 18-19), in two halves so that no step waits
+// for its own mean. During a step the thread holding row j's local value
+// stores it (nu_report). The mean over the rows is taken by one warp at the
+// start of the next step by one block, or by the finalize launch after a run
+// of steps (nu_finish_prev), when the rows are complete without any counting.
 __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j, double nuj) {
-    const int lane = threadIdx.x & 31;
-    if (has_nu) {
-        A.nu_rows[j] = nuj;
-        __threadfence();
-    }
-    const unsigned n_here = __popc(__ballot_sync(kFull, has_nu));
-    unsigned before = 0;
-    if (lane == 0 && n_here) before = atomicAdd(A.counter, n_here);
-    before = __shfl_sync(kFull, before, 0);
-    if (n_here && before + n_here == (unsigned)A.ny) {
-        __threadfence();
-        double s = 0.0;
-        // Eight independent partial sums per lane keep eight loads in flight
-        // (rows lane + 32 (8 i + q) go to partial q); they are added in a fixed order.
-        double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-        int r = lane;
-        for (; r + 7 * 32 < A.ny; r += 8 * 32) {
-            double v[8];
+    if (has_nu) A.nu_rows[j] = nuj;
+}
+
+// Called by every thread of a block (it synchronises the block), once per
+// step (step = true, at any point of the step's launch) or once after a run of
+// steps (step = false). If prev_rows holds a step not yet summed, its ny rows
+// are summed in a fixed order and appended to the ring as step step_in - 1: 256
+// partial sums, partial p over rows p, p + 256, p + 512, ... in that order,
+// kept by lane p % 32 of the warp that takes stream q = p / 32 (warps take
+// q = w, w + nwarps, ...); lane l then adds its eight partials q = 0..7 in order
+// and the warp adds the 32 lane sums by a butterfly. The order does not depend
+// on the block size or on scheduling. A step then advances the step counter
+// (step_out = step_in + 1) and marks its own rows as pending; the finalize
+// call clears the mark.
+__device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
+    __shared__ double part[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long t = __ldcg(A.step_in);
+    const unsigned pend = __ldcg(A.pending);
+    __syncthreads();  // every thread has read the flag before thread 0 rewrites it
+    if (pend) {
+        for (int q = warp; q < 8; q += nw) {
+            double acc = 0.0;
+            int r = lane + 32 * q;
+            for (; r + 3 * 256 < A.ny; r += 4 * 256) {  // four loads in flight, added in order
+                double v[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = __ldcg(A.nu_rows + r + 32 * q);
+                for (int i = 0; i < 4; ++i) v[i] = __ldcg(A.prev_rows + r + 256 * i);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] += v[q];
+                for (int i = 0; i < 4; ++i) acc += v[i];
+            }
+            for (; r < A.ny; r += 256) acc += __ldcg(A.prev_rows + r);
+            part[q][lane] = acc;
         }
-        for (int q = 0; r < A.ny; r += 32, ++q) acc[q] += __ldcg(A.nu_rows + r);
+        __syncthreads();
+        if (warp == 0) {
+            double s = 0.0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) s += acc[q];
+            for (int q = 0; q < 8; ++q) s += part[q][lane];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (lane == 0) {
-            const double mean = s / (double)A.ny;
-            const long long t = *A.step_in;
-            A.nu_ring[t % A.cap] = mean;
-            *A.nu_last = mean;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+            if (lane == 0) {
+                const double mean = s / (double)A.ny;
+                A.nu_ring[(t - 1) % A.cap] = mean;
+                *A.nu_last = mean;
+            }
+        }
+        __syncthreads();  // part may be reused by the next call
+    }
+    if (threadIdx.x == 0) {
+        if (step) {
             *A.step_out = t + 1;
-            *A.counter = 0u;
+            *A.pending = 1u;
+        } else {
+            *A.pending = 0u;
         }
     }
 }
+
+// Sums the last step of a run (one block of 256 threads).
+static __global__ void nu_finalize_kernel(StepArgs A) { nu_finish_prev(A, false); }
 
 }  // namespace dmrt

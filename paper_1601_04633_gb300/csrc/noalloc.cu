@@ -6,8 +6,8 @@
 // synchronise the device, or plug-in hosts that forbid allocation inside their
 // callbacks. This entry point takes the two population buffers from the
 // caller and keeps everything else the step kernel needs (wall temperatures,
-// per-row Nusselt values, the arrival counter of the fused reduction, the
-// error word) in one file-scope device array of fixed size. Every GPU that
+// per-row Nusselt values, the step counter and pending flag of the Nusselt
+// reduction, the error word) in one file-scope device array of fixed size. Every GPU that
 // loads the library holds that array until the process exits.
 #include <cuda_runtime.h>
 
@@ -27,7 +27,7 @@ namespace {
 //   [0, 8 * MAX)            per-row local Nusselt numbers (double)
 //   [8 * MAX, 12 * MAX)     left-wall temperatures (float)
 //   [12 * MAX, 16 * MAX)    right-wall temperatures (float)
-//   [16 * MAX, + 256)       step counter, latest mean, arrival counter, error word
+//   [16 * MAX, + 256)       step counter, latest mean, pending flag, error word
 constexpr int kMaxNy = DMRT_NOALLOC_MAX_NY;
 constexpr size_t kOffRows = 0;
 constexpr size_t kOffHot = 8 * (size_t)kMaxNy;
@@ -39,7 +39,7 @@ struct Misc {
     long long step[2];
     double nu_last;
     double nu_sink;  // target of the mean when the caller passes no output
-    unsigned counter;
+    unsigned pending;
     unsigned err;
 };
 
@@ -108,7 +108,7 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     // The array keeps the previous call's contents: clear the reduction's
-    // counter, step and error word, and write this call's wall temperatures.
+    // pending flag, step and error word, and write this call's wall temperatures.
     e = cudaMemsetAsync(misc, 0, sizeof(Misc), s);
     if (e != cudaSuccess) return fail(DMRT_E_CUDA, "cudaMemsetAsync: ", cudaGetErrorString(e));
     noalloc_fill<<<(p->ny + 255) / 256, 256, 0, s>>>(hot, cold, theta_hot, theta_cold,
@@ -138,9 +138,10 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     A.hot = hot;
     A.cold = cold;
     A.nu_rows = reinterpret_cast<double*>(b + kOffRows);
+    A.prev_rows = A.nu_rows;  // summed only by the finalize launch below (nothing is pending before)
     A.nu_ring = nu_mean ? nu_mean : &misc->nu_sink;  // a ring of length 1
     A.nu_last = &misc->nu_last;
-    A.counter = &misc->counter;
+    A.pending = &misc->pending;
     A.err = &misc->err;
     A.step_in = &misc->step[0];
     A.step_out = &misc->step[1];
@@ -158,6 +159,10 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     const int rows_per_block = (dmrt::kDirectThreads / 32) * (32 / wx);
     const dim3 grid((nxq + wx - 1) / wx, (p->ny + rows_per_block - 1) / rows_per_block, 1);
     dmrt::step_direct_kernel<<<grid, dmrt::kDirectThreads, 0, s>>>(A, sc);
+    // The step stores its local Nusselt numbers; one block then sums them into *nu_mean.
+    dmrt::StepArgs F = A;
+    F.step_in = &misc->step[1];
+    dmrt::nu_finalize_kernel<<<1, 256, 0, s>>>(F);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(DMRT_E_CUDA, "step launch: ", cudaGetErrorString(e));
     return DMRT_OK;

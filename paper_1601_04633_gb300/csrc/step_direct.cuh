@@ -78,6 +78,8 @@ __device__ __forceinline__ float4 pull_finish(const PlaneLoad& L, int j, int x0,
 // Internal linkage: every translation unit that launches it compiles its own copy.
 static __global__ void __launch_bounds__(kDirectThreads, 4) step_direct_kernel(StepArgs A, StepConsts K) {
     const int lane = threadIdx.x & 31;
+    // The previous step's mean Nusselt number: the first block.
+    if (blockIdx.x == 0 && blockIdx.y == 0) nu_finish_prev(A, true);
     const int warp = threadIdx.x >> 5;
     Geo G;
     G.nx = A.nx;

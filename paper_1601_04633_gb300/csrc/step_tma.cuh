@@ -581,6 +581,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         mbar_fence_init();
     }
     __syncthreads();
+    // The previous step's mean Nusselt number: block 0, before its first item.
+    if (blockIdx.x == 0) nu_finish_prev(A, true);
 
     // One item: every plane's R rows of row block rb, groups P and N taken one
     // row below / above (their e_y). One-type layout: ld[0] has 6-plane boxes
@@ -729,6 +731,9 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         mbar_fence_init();
     }
     __syncthreads();
+    // The previous step's mean Nusselt number of each cavity: blocks 0, 1, ...
+    // before their first item.
+    for (int cc = blockIdx.x; cc < n_cav; cc += gridDim.x) nu_finish_prev(cav[cc].args[parity], true);
 
     // Producer state (thread 0 only).
     int next_static = blockIdx.x * static_per_block;
@@ -816,6 +821,11 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         atomicOr(batch_err, kErrTimeout);
         for (int q = k; q < issued; ++q) mbar_wait_bounded(&bars[q % S], (uint32_t)((q / S) & 1));
     }
+}
+
+// Sums each cavity's last step of a run (one block of 256 threads per cavity).
+static __global__ void nu_finalize_batch_kernel(const BatchCavity* __restrict__ cav, int parity) {
+    nu_finish_prev(cav[blockIdx.x].args[parity], false);
 }
 
 }  // namespace dmrt
