@@ -186,6 +186,16 @@ int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
  * by the Nusselt number. */
 int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold);
 
+/* Secondary hot-wall Nusselt number of the current state, from the heat the
+ * next streaming carries across the hot wall's links (Eq. 45 with Fourier's
+ * law behind Eqs. 18-19): Nu_j = H (2 sqrt(3) alpha theta_w(j) - 2 g*_3(0, j)) /
+ * (alpha (theta_hot - theta_cold)), g* the post-collision thermal populations
+ * of the wall column; 0 for an adiabatic left wall. Exactly 1 in the
+ * conduction limit, like the wall-gradient estimator of dmrt_nusselt, which it
+ * matches to the discretisation level otherwise. Host outputs, both nullable:
+ * nu_mean (mean over rows), nu_local [ny]. Synchronises. */
+int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local);
+
 /* Post-collision population state at the current time level as a dense host
  * float32 array [14][ny][nx]: planes f_1..f_9 (Eq. 23 order; f stored shifted
  * so that sum f_i = delta-rho, Eq. 33) then g_1..g_5 (Eq. 35 order).

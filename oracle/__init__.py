@@ -90,6 +90,8 @@ def lib():
             L.orc_run.argtypes = [mp, ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.orc_run.restype = ctypes.c_int
             L.orc_fields_from_post.argtypes = [mp, dp, dp, dp, dp, dp]
+            L.orc_nu_flux.argtypes = [mp, dp, dp, dp]
+            L.orc_nu_flux.restype = ctypes.c_double
             L.orc_collide_vjp.argtypes = [mp, dp, dp, dp, dp]
             L.orc_adjoint.argtypes = [mp, ctypes.c_int64, ctypes.c_int64, dp, dp, dp, dp, dp, dp]
             L.orc_adjoint.restype = ctypes.c_int
@@ -259,6 +261,19 @@ def fields_from_post(model: Model, fs, gs):
     u, v, t = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
     lib().orc_fields_from_post(ctypes.byref(model), _p(fs), _p(gs), _p(u), _p(v), _p(t))
     return u, v, t
+
+
+def nu_flux(model: Model, gs, theta_hot_profile=None):
+    """Secondary hot-wall Nusselt number of a post-collision thermal state
+    ``gs`` (5, ny, nx): the heat the next streaming carries across the hot wall's
+    links (Eq. 45), Nu_j = H (abb theta_w(j) - 2 g*_3(0, j)) / (alpha dT).
+    Returns (mean over rows, per-row array)."""
+    ny = model.ny
+    local = np.zeros(ny)
+    hp = _profile(theta_hot_profile, ny)
+    mean = lib().orc_nu_flux(ctypes.byref(model), _p(np.ascontiguousarray(gs, dtype=np.float64)), _p(hp),
+                             _p(local))
+    return float(mean), local
 
 
 def collide_vjp(model: Model, x, lam):

@@ -438,6 +438,27 @@ int orc_run(const orc_model *md, int64_t nsteps, double *fs, double *gs,
 /* Post-collision state -> macroscopic fields at the same time level.
  * theta = sum g* (the thermal collision conserves theta, Q_1 = 0) and the
  * pre-collision momentum is sum e f* minus the force's momentum rho0 G. */
+/* Secondary Nusselt estimator. Over one streaming, the left wall's link of row
+ * j brings g_1(0, j) = 2 sqrt(3) alpha theta_w(j) - g*_3(0, j) into the cavity
+ * (anti-bounce-back, Eq. 45) and takes g*_3(0, j) out, so the heat entering per
+ * row and step is abb theta_w - 2 g*_3. Fourier's law (Eqs. 18-19 in flux form)
+ * gives the local Nusselt number Nu_j = H q_j / (alpha dT); an adiabatic left
+ * wall (Eq. 44) returns its link unchanged and carries no heat. */
+double orc_nu_flux(const orc_model *md, const double *gs, const double *theta_hot_prof, double *local) {
+    int ny = md->ny, nx = md->nx;
+    double sum = 0.0;
+    for (int j = 0; j < ny; ++j) {
+        double q = 0.0;
+        if (md->left_bc == ORC_WALL_FIXED)
+            q = md->abb_coef * wall_theta(theta_hot_prof, md->theta_hot, j) - 2.0 * F_AT(gs, 3, j, 0);
+        double nuj = (md->dT != 0.0) ? md->H * q / (md->alpha * md->dT) : 0.0;
+        if (local) local[j] = nuj;
+        sum += nuj;
+    }
+    (void)nx;
+    return sum / ny;
+}
+
 void orc_fields_from_post(const orc_model *md, const double *fs, const double *gs,
                           double *u, double *v, double *theta) {
     int nx = md->nx, ny = md->ny;

@@ -44,6 +44,10 @@ int orc_run(const orc_model *md, int64_t nsteps, double *fs, double *gs,
             const double *theta_hot_prof, const double *theta_cold_prof,
             double *nu_series, double *u_out, double *v_out, double *theta_out,
             double *nu_local);
+/* Secondary hot-wall Nusselt number from a post-collision thermal state: the
+ * heat the next streaming carries into the cavity across the hot wall's links.
+ * local[j] (ny values) and the returned mean over the rows. */
+double orc_nu_flux(const orc_model *md, const double *gs, const double *theta_hot_prof, double *local);
 void orc_fields_from_post(const orc_model *md, const double *fs, const double *gs,
                           double *u, double *v, double *theta);
 /* Discrete adjoint (all forward states kept: small grids). J = mean over the last

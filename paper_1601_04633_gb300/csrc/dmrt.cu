@@ -273,6 +273,22 @@ __global__ void fill_kernel(float* p, const double* src, double value, int n) {
 // Host state arrays are ordered f_1..f_9, g_1..g_5; the device planes are grouped.
 int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
 
+// Secondary hot-wall Nusselt number per row from the post-collision thermal
+// populations of the wall column: the next streaming brings abb theta_w(j) -
+// g*_3(0, j) in across the left wall's link (anti-bounce-back, Eq. 45) and takes
+// g*_3(0, j) out; Nu_j = H (abb theta_w - 2 g*_3) / (alpha dT). abb = 0 and
+// sign = 0 for an adiabatic left wall (no heat crosses it).
+template <typename L>
+__global__ void nu_flux_kernel(const unsigned char* __restrict__ S, const float* __restrict__ hot,
+                               double* __restrict__ out, int ny, int pitch, long long plane, double abb,
+                               double g_sign, double sh1, double scale) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ny) return;
+    const auto* Sg = g_base<L>(S, plane);
+    const double g3 = (double)elem_to_f(Sg[L::pg(3) * plane + (size_t)j * pitch]) + sh1;
+    out[j] = scale * (abb * (double)hot[j] - g_sign * 2.0 * g3);
+}
+
 // Call fn with a value of the element type of a one-type storage (float, __half, __nv_bfloat16).
 template <typename Fn>
 void with_elem(int storage, Fn&& fn) {
@@ -789,6 +805,32 @@ int dmrt_check(dmrt_ctx* c) {
 }
 
 int64_t dmrt_steps_done(const dmrt_ctx* c) { return c ? c->t : -1; }
+
+int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local) {
+    if (!c) return DMRT_E_ARG;
+    const dmrt_params& p = c->p;
+    const bool fixed = p.left_wall == DMRT_WALL_FIXED;
+    const double dT = p.theta_hot - p.theta_cold;
+    const double scale = dT != 0.0 ? (double)p.ny / (c->k.alpha * dT) : 0.0;
+    // Per-row values staged in the idle population buffer (no allocation).
+    double* stage = reinterpret_cast<double*>(buf(c, 1 - c->cur));
+    with_layout(p.storage, [&](auto tag) {
+        using Lt = decltype(tag);
+        nu_flux_kernel<Lt><<<(p.ny + 255) / 256, 256, 0, c->stream>>>(
+            reinterpret_cast<const unsigned char*>(buf(c, c->cur)), reinterpret_cast<const float*>(c->ws + c->L.off_hot),
+            stage, p.ny, c->L.pitch, c->L.plane, fixed ? c->k.abb : 0.0, fixed ? 1.0 : 0.0, (double)c->sc.gsh1, scale);
+    });
+    CK(cudaGetLastError(), "flux Nusselt kernel");
+    std::vector<double> local((size_t)p.ny);
+    CK(cudaMemcpyAsync(local.data(), stage, local.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "copy flux Nusselt");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    double sum = 0.0;
+    for (double x : local) sum += x;  // rows in order
+    if (nu_mean) *nu_mean = sum / (double)p.ny;
+    if (nu_local) std::memcpy(nu_local, local.data(), local.size() * sizeof(double));
+    return DMRT_OK;
+}
 
 int dmrt_fields(dmrt_ctx* c, float* u, float* v, float* theta, int on_device) {
     if (!c) return DMRT_E_ARG;

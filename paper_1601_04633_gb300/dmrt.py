@@ -110,6 +110,7 @@ SIGNATURES = {
     "dmrt_nusselt": (ctypes.c_int, [_VP, _DP, _DP, _DP, ctypes.c_int64,
                                     ctypes.POINTER(ctypes.c_int64)]),
     "dmrt_set_wall_profiles": (ctypes.c_int, [_VP, _DP, _DP]),
+    "dmrt_nusselt_flux": (ctypes.c_int, [_VP, _DP, _DP]),
     "dmrt_get_consts": (ctypes.c_int, [_VP, ctypes.POINTER(Consts)]),
     "dmrt_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
@@ -417,6 +418,13 @@ class Cavity2D:
 
     def nusselt(self, series_cap: int = 0):
         return dmrt_nusselt(self.h, self.ny, series_cap)
+
+    def nusselt_flux(self):
+        """(mean, per-row array) of the link-flux Nusselt estimator of the current state."""
+        local = np.zeros(self.ny)
+        mean = ctypes.c_double(0.0)
+        _check(load().dmrt_nusselt_flux(self.h, ctypes.byref(mean), local.ctypes.data_as(_DP)), self.h)
+        return mean.value, local
 
     def close(self):
         if getattr(self, "h", None):

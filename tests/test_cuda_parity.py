@@ -269,3 +269,40 @@ def test_non_finite_state_is_reported(D):
         sim.check()
     assert ei.value.code == D.DMRT_E_DIVERGED
     sim.close()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 3], ids=["fp32", "fp16", "mixed"])
+def test_flux_nusselt_matches_oracle(D, storage):
+    # The link-flux estimator (dmrt_nusselt_flux) on the GPU's own state equals
+    # the oracle's definition evaluated on that state, and after 500 steps it
+    # stays within the Nusselt tolerance of the oracle's own run.
+    cav = inputs.Cavity(130, 97, 3e4, 0.01, noise_amp=1e-3, seed=29)
+    prof = 0.5 + 0.02 * np.cos(np.arange(97) / 9.0)
+    sim = D.Cavity2D.from_inputs(cav, storage=storage, nu_capacity=600)
+    D.dmrt_set_wall_profiles(sim.h, hot=prof)
+    sim.step(500)
+    sim.check()
+    mean, local = sim.nusselt_flux()
+    state = sim.get_state().astype(np.float64)
+    sim.close()
+    m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+    hot32 = prof.astype(np.float32).astype(np.float64)  # the device keeps the wall profile in float32
+    ref_mean, ref_local = O.nu_flux(m, state[9:], theta_hot_profile=hot32)
+    assert np.abs(local - ref_local).max() <= 1e-9 * np.abs(ref_local).max()
+    assert mean == pytest.approx(ref_mean, rel=1e-9)
+    if storage == 0:
+        f, g = O.init(m, cav.theta0())
+        O.run(m, 500, f, g, theta_hot_profile=prof)
+        assert mean == pytest.approx(O.nu_flux(m, g, theta_hot_profile=prof)[0], rel=NU_TOL)
+
+
+def test_flux_nusselt_conduction_limit(D):
+    cav = inputs.Cavity(32, 32, 0.0, 0.01, noise_amp=0.0)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=16)
+    sim.step(40000)
+    sim.check()
+    mean, local = sim.nusselt_flux()
+    nu = sim.nusselt()[0]
+    sim.close()
+    assert mean == pytest.approx(1.0, abs=1e-4) and np.allclose(local, 1.0, atol=1e-4)
+    assert nu == pytest.approx(1.0, abs=1e-4)

@@ -257,6 +257,30 @@ def test_conduction_limit_square():
     assert np.allclose(r["nu_local"], 1.0, atol=1e-12)
 
 
+def test_flux_nusselt_conduction_limit_and_case1():
+    # The secondary estimator (heat carried across the hot wall's links, Eq. 45)
+    # is exactly 1 in the square conduction limit, H / width in a rectangle, and
+    # agrees with the wall-gradient estimator (Eqs. 18-19) at the steady Case 1
+    # state to the discretisation level.
+    for nx, ny, expect in ((16, 16, 1.0), (24, 16, 16 / 24)):
+        m = O.derive(nx, ny, 0.0, 0.01, 0.1)
+        f, g = O.init(m, np.zeros((ny, nx)))
+        r = O.run(m, 40000, f, g)
+        mean, local = O.nu_flux(m, g)
+        assert mean == pytest.approx(expect, abs=1e-12)
+        assert np.allclose(local, expect, atol=1e-12)
+        assert r["nu_series"][-1] == pytest.approx(expect, abs=1e-12)
+    m = O.derive(16, 16, 0.0, 0.01, 0.1, left_bc=O.WALL_ADIABATIC)
+    f, g = O.init(m, np.zeros((16, 16)))
+    O.run(m, 100, f, g)
+    assert O.nu_flux(m, g)[0] == 0.0  # an adiabatic wall carries no heat
+    c = inputs.cavity_64()
+    m = O.derive(c.nx, c.ny, c.Ra, c.Pr, c.alpha)
+    f, g = O.init(m, c.theta0())
+    r = O.run(m, 20000, f, g)
+    assert O.nu_flux(m, g)[0] == pytest.approx(r["nu_series"][-1], rel=1e-3)
+
+
 def test_conduction_limit_rectangle_and_other_walls():
     # Width 24, height H = 16: -d theta/dX = H dT / width. Wall temperatures 1 and 0.
     m = O.derive(24, 16, 0.0, 0.01, 0.05, theta_hot=1.0, theta_cold=0.0)
