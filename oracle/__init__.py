@@ -90,6 +90,7 @@ def lib():
             L.orc_run.argtypes = [mp, ctypes.c_int64, dp, dp, dp, dp, dp, dp, dp, dp, dp]
             L.orc_run.restype = ctypes.c_int
             L.orc_fields_from_post.argtypes = [mp, dp, dp, dp, dp, dp]
+            L.orc_stream_transpose.argtypes = [mp, dp, dp, dp]
             L.orc_nu_flux.argtypes = [mp, dp, dp, dp]
             L.orc_nu_flux.restype = ctypes.c_double
             L.orc_collide_vjp.argtypes = [mp, dp, dp, dp, dp]
@@ -261,6 +262,17 @@ def fields_from_post(model: Model, fs, gs):
     u, v, t = np.zeros((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx))
     lib().orc_fields_from_post(ctypes.byref(model), _p(fs), _p(gs), _p(u), _p(v), _p(t))
     return u, v, t
+
+
+def stream_transpose(model: Model, lam):
+    """S^T lam for the linear part S of ``stream`` (lam: 14 planes, f then g), and
+    the hot-wall temperature derivative it carries. Returns (lprev, dthw)."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    assert lam.shape == (14, model.ny, model.nx)
+    out = np.zeros_like(lam)
+    dthw = np.zeros(model.ny)
+    lib().orc_stream_transpose(ctypes.byref(model), _p(lam), _p(out), _p(dthw))
+    return out, dthw
 
 
 def nu_flux(model: Model, gs, theta_hot_profile=None):

@@ -577,6 +577,49 @@ void orc_collide_vjp(const orc_model *md, const double x[14], const double lam[1
     }
 }
 
+/* Transposed streaming: lprev = S^T nu for the linear part S of orc_stream
+ * (Eqs. 25 and 36 with the bounce-back rules, Eqs. 44-45): every pulled entry
+ * goes back to where it came from; a bounced link goes back to the node's
+ * opposite direction, with a minus sign on a fixed-temperature wall (Eq. 45).
+ * There the pulled value also depends on theta_w(j) with coefficient abb_coef,
+ * which is added to dthw[j] (left wall only; dthw may be NULL). */
+void orc_stream_transpose(const orc_model *md, const double *nu, double *lprev, double *dthw) {
+    int nx = md->nx, ny = md->ny;
+    size_t n = (size_t)nx * ny, sz = 14 * n;
+    for (size_t c = 0; c < sz; ++c) lprev[c] = 0.0;
+    for (int k9 = 0; k9 < 9; ++k9) {
+        int kb = opposite9(k9);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int si = i - EX9[k9], sj = j - EY9[k9];
+                double val = nu[(size_t)k9 * n + (size_t)j * nx + i];
+                if (si >= 0 && si < nx && sj >= 0 && sj < ny)
+                    lprev[(size_t)k9 * n + (size_t)sj * nx + si] += val;
+                else
+                    lprev[(size_t)kb * n + (size_t)j * nx + i] += val;
+            }
+    }
+    for (int k5 = 0; k5 < 5; ++k5) {
+        int kb = opposite5(k5);
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int si = i - EX5[k5], sj = j - EY5[k5];
+                double val = nu[(size_t)(9 + k5) * n + (size_t)j * nx + i];
+                if (si >= 0 && si < nx && sj >= 0 && sj < ny) {
+                    lprev[(size_t)(9 + k5) * n + (size_t)sj * nx + si] += val;
+                    continue;
+                }
+                int bc = si < 0 ? md->left_bc : si >= nx ? md->right_bc : ORC_WALL_ADIABATIC;
+                if (bc == ORC_WALL_FIXED) {
+                    lprev[(size_t)(9 + kb) * n + (size_t)j * nx + i] -= val; /* Eq. 45 */
+                    if (si < 0 && dthw) dthw[j] += md->abb_coef * val;
+                } else {
+                    lprev[(size_t)(9 + kb) * n + (size_t)j * nx + i] += val; /* Eq. 44 */
+                }
+            }
+    }
+}
+
 int orc_adjoint(const orc_model *md, int64_t nsteps, int64_t avg_last, const double *f0,
                 const double *g0, const double *theta_hot_prof, double *J, double *dJ_dthw,
                 double *dJ_dgbeta) {
@@ -629,39 +672,7 @@ int orc_adjoint(const orc_model *md, int64_t nsteps, int64_t avg_last, const dou
                 }
                 dJ_dthw[j] += w * 8.0 * scale / ny;
             }
-        /* Transposed streaming: every pulled entry goes back to where it came from. */
-        for (size_t c = 0; c < sz; ++c) lprev[c] = 0.0;
-        for (int k9 = 0; k9 < 9; ++k9) {
-            int kb = opposite9(k9);
-            for (int j = 0; j < ny; ++j)
-                for (int i = 0; i < nx; ++i) {
-                    int si = i - EX9[k9], sj = j - EY9[k9];
-                    double val = nu[(size_t)k9 * n + (size_t)j * nx + i];
-                    if (si >= 0 && si < nx && sj >= 0 && sj < ny)
-                        lprev[(size_t)k9 * n + (size_t)sj * nx + si] += val;
-                    else
-                        lprev[(size_t)kb * n + (size_t)j * nx + i] += val;
-                }
-        }
-        for (int k5 = 0; k5 < 5; ++k5) {
-            int kb = opposite5(k5);
-            for (int j = 0; j < ny; ++j)
-                for (int i = 0; i < nx; ++i) {
-                    int si = i - EX5[k5], sj = j - EY5[k5];
-                    double val = nu[(size_t)(9 + k5) * n + (size_t)j * nx + i];
-                    if (si >= 0 && si < nx && sj >= 0 && sj < ny) {
-                        lprev[(size_t)(9 + k5) * n + (size_t)sj * nx + si] += val;
-                        continue;
-                    }
-                    int bc = si < 0 ? md->left_bc : si >= nx ? md->right_bc : ORC_WALL_ADIABATIC;
-                    if (bc == ORC_WALL_FIXED) {
-                        lprev[(size_t)(9 + kb) * n + (size_t)j * nx + i] -= val; /* Eq. 45 */
-                        if (si < 0) dJ_dthw[j] += md->abb_coef * val;
-                    } else {
-                        lprev[(size_t)(9 + kb) * n + (size_t)j * nx + i] += val; /* Eq. 44 */
-                    }
-                }
-        }
+        orc_stream_transpose(md, nu, lprev, dJ_dthw);
         double *tmp = lam;
         lam = lprev;
         lprev = tmp;

@@ -44,6 +44,9 @@ int orc_run(const orc_model *md, int64_t nsteps, double *fs, double *gs,
             const double *theta_hot_prof, const double *theta_cold_prof,
             double *nu_series, double *u_out, double *v_out, double *theta_out,
             double *nu_local);
+/* Transposed streaming (the adjoint of the linear part of orc_stream); arrays
+ * of 14 planes [14][ny][nx]; adds the hot-wall temperature derivative to dthw. */
+void orc_stream_transpose(const orc_model *md, const double *nu, double *lprev, double *dthw);
 /* Secondary hot-wall Nusselt number from a post-collision thermal state: the
  * heat the next streaming carries into the cavity across the hot wall's links.
  * local[j] (ny values) and the returned mean over the rows. */

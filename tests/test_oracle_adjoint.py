@@ -57,3 +57,27 @@ def test_adjoint_matches_finite_differences(nx, ny, Ra):
         / (2e-5 * m.gbeta)
     assert dgb == pytest.approx(fd, rel=1e-6, abs=1e-8)
     assert abs(dgb) > 0 and np.abs(dth).max() > 0
+
+
+def test_transposed_streaming_dot_product():
+    # Dot-product test of the adjoint streaming: <S x, y> = <x, S^T y> for the
+    # linear part S of the pull-stream with all wall rules (wall temperatures 0),
+    # and the hot-wall term: <dS/dtheta_w delta, y> = <delta, dthw(y)>.
+    rng = np.random.default_rng(7)
+    for nx, ny, left in ((5, 4, O.WALL_FIXED), (7, 3, O.WALL_ADIABATIC)):
+        m = O.derive(nx, ny, 1e4, 0.01, 0.1, left_bc=left, right_bc=O.WALL_FIXED)
+        lin = m.copy()
+        lin.theta_hot = lin.theta_cold = 0.0
+        x = rng.standard_normal((14, ny, nx))
+        y = rng.standard_normal((14, ny, nx))
+        f, g = O.stream(lin, np.ascontiguousarray(x[:9]), np.ascontiguousarray(x[9:]))
+        sx = np.concatenate([f, g])
+        sty, dthw = O.stream_transpose(m, y)
+        assert np.dot(sx.ravel(), y.ravel()) == pytest.approx(np.dot(x.ravel(), sty.ravel()), rel=1e-13)
+        delta = rng.standard_normal(ny)
+        f1, g1 = O.stream(lin, np.ascontiguousarray(x[:9]), np.ascontiguousarray(x[9:]), theta_hot_profile=delta)
+        ds = np.concatenate([f1, g1]) - sx
+        lhs = np.dot(ds.ravel(), y.ravel())
+        assert lhs == pytest.approx(np.dot(delta, dthw), rel=1e-12, abs=1e-13)
+        if left == O.WALL_ADIABATIC:
+            assert np.all(dthw == 0.0)
