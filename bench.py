@@ -172,8 +172,21 @@ def time_oracle(cav, budget_s, max_steps=50, rows=None):
     t0 = time.perf_counter()
     O.run(m, steps, f, g)
     dt = time.perf_counter() - t0
-    return {"value": cav.nx * ny * steps / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{steps} fp64 oracle steps of {cav.nx}x{ny} (same Ra, Pr, alpha), {dt:.1f} s"}
+    out = {"value": cav.nx * ny * steps / dt / 1e6, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"{steps} fp64 oracle steps of {cav.nx}x{ny} (same Ra, Pr, alpha), {dt:.1f} s"}
+    # The same oracle on one thread (identical results), on a band of rows sized
+    # for about a quarter of the budget.
+    O.set_threads(1)
+    band = max(4, min(ny, int(0.25 * budget_s / max(t1 * threads, 1e-9) * ny)))
+    m1 = O.derive(cav.nx, band, cav.Ra, cav.Pr, cav.alpha)
+    f1, g1 = O.init(m1, th[:band])
+    t0 = time.perf_counter()
+    O.run(m1, 1, f1, g1)
+    dt1 = time.perf_counter() - t0
+    out["single_thread"] = {"value": cav.nx * band / dt1 / 1e6, "unit": UNIT, "cores": 1,
+                            "sample": f"1 fp64 oracle step of {cav.nx}x{band}, {dt1:.1f} s"}
+    O.set_threads(threads)
+    return out
 
 
 def run_reference(args):
