@@ -311,8 +311,9 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
 
 /* ---- Batched sweep: many independent cavities per launch ----------------------
  *
- * Steps n independent side-heated cavities (any sizes and parameters, float32
- * storage) with one launch per time step of a persistent TMA kernel over the
+ * Steps n independent side-heated cavities (any sizes and parameters; all
+ * float32 or all mixed storage, rounding to nearest) with one launch per time
+ * step of a persistent TMA kernel over the
  * concatenated work items of all cavities, replayed from CUDA graphs. Each
  * member is also an ordinary context (dmrt_batch_context), so dmrt_fields,
  * dmrt_nusselt, dmrt_get_state, ... work on it, and stepping the members one
@@ -322,15 +323,15 @@ typedef struct dmrt_batch dmrt_batch;
 
 /* Tile of the batched kernel: nodes per thread, rows per item, pipeline stages
  * (0 = default 1, 4, 2), and steps per CUDA graph (0 = 64; must be even).
- * Compiled tiles (npt, R, S): (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,2,2) (2,4,2)
- * (4,1,4) (4,4,2). */
+ * Compiled tiles (npt, R, S), for both storages: (1,1,2) (1,2,2) (1,4,2)
+ * (1,4,3) (2,2,2) (2,4,2) (4,1,4) (4,4,2). */
 typedef struct {
     int32_t tma_npt, tma_rows, tma_stages, graph_steps;
 } dmrt_batch_opts;
 
 /* Device workspace for a batch of n cavities (the members' workspaces plus the
- * kernel's tables). Errors as dmrt_derive for any member; DMRT_E_ARG for n < 1
- * or 16-bit storage. */
+ * kernel's tables). Errors as dmrt_derive for any member; DMRT_E_ARG for n < 1,
+ * FP16 / BF16 storage, members stored differently, or stochastic rounding. */
 int dmrt_batch_workspace_size(const dmrt_params* arr, int32_t n, size_t* bytes);
 
 /* Create a batch. arr: n parameter sets; theta0: NULL, or n host pointers (each

@@ -1258,8 +1258,16 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
     for (int i = 0; i < n; ++i) {
         int rc = validate(&arr[i], nullptr);
         if (rc) return rc;
-        if (arr[i].storage != DMRT_FP32) {
-            set_err(nullptr, "batched sweep: cavity %d: float32 storage only", i);
+        if (arr[i].storage != DMRT_FP32 && arr[i].storage != DMRT_MIXED) {
+            set_err(nullptr, "batched sweep: cavity %d: float32 or mixed storage only", i);
+            return DMRT_E_ARG;
+        }
+        if (arr[i].storage != arr[0].storage) {
+            set_err(nullptr, "batched sweep: cavity %d: every cavity needs the same storage", i);
+            return DMRT_E_ARG;
+        }
+        if (arr[i].rounding != DMRT_ROUND_NEAREST) {
+            set_err(nullptr, "batched sweep: cavity %d: rounding to nearest only", i);
             return DMRT_E_ARG;
         }
         L->off[i] = o;
@@ -1269,7 +1277,7 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
     L->off_cav = o;
     o += align256((size_t)n * sizeof(dmrt::BatchCavity));
     L->off_maps = o;
-    o += align256((size_t)n * 4 * sizeof(CUtensorMap));
+    o += align256((size_t)n * 2 * dmrt::kBatchMaps * sizeof(CUtensorMap));
     L->off_err = o;
     o += 256;
     L->total = o;
@@ -1373,10 +1381,12 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     int nv = 0;
     const dmrt::TmaVariant* vars = dmrt::tma_variants_batch(&nv);
     const void* func = nullptr;
+    const int storage = arr[0].storage;
     for (int i = 0; i < nv; ++i)
-        if (vars[i].npt == npt && vars[i].R == R && vars[i].S == S) func = vars[i].func;
+        if (vars[i].storage == storage && vars[i].npt == npt && vars[i].R == R && vars[i].S == S) func = vars[i].func;
     if (!func) {
-        set_err(nullptr, "no batched tile with %d nodes/thread, %d rows, %d stages is compiled in", npt, R, S);
+        set_err(nullptr, "no batched tile with %d nodes/thread, %d rows, %d stages is compiled in for this storage",
+                npt, R, S);
         return DMRT_E_ARG;
     }
     dmrt_batch* b = new (std::nothrow) dmrt_batch();
@@ -1416,11 +1426,16 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     }
     // Device tables: per-cavity arguments and tensor maps (boxes of R rows).
     std::vector<dmrt::BatchCavity> cav(n);
-    std::vector<CUtensorMap> maps((size_t)n * 4);
+    std::vector<CUtensorMap> maps((size_t)n * 2 * dmrt::kBatchMaps);
+    std::memset(maps.data(), 0, maps.size() * sizeof(maps[0]));
     long long items = 0;
+    const bool split = storage == DMRT_MIXED;
+    const int fb = split ? 2 : 4, gb = 4;               // bytes per flow / thermal element
+    const int halo = dmrt::tma_halo(std::min(fb, gb));  // 16 bytes of the narrowest element
     const int block = R * (256 / npt);
-    const int quantum = 32 * npt;                          // strip widths keep warps in one row
-    const int w_max = (dmrt::kTmaBox - 8) / quantum * quantum;
+    const int quantum = 32 * npt;                       // strip widths keep warps in one row
+    const int w_max = (dmrt::kTmaBox - 2 * halo) / quantum * quantum;
+    const int stage_bytes = dmrt::tma_stage_elems(R) * 4;  // the compiled stage (float32 sizing)
     for (int i = 0; i < n; ++i) {
         dmrt_ctx* c = b->sub[i];
         std::memset(&cav[i], 0, sizeof cav[i]);
@@ -1429,16 +1444,32 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         cav[i].K = c->sc;
         const int ns = (c->p.nx + w_max - 1) / w_max;
         const int W = ((c->p.nx + ns - 1) / ns + quantum - 1) / quantum * quantum;
-        const int WB = W + 8;
+        const int WB = W + 2 * halo;
         const int tpr = W / npt;
-        // Rows per item: bounded by the block's threads and by the stage, which
-        // must also hold up to 2 x 124 bytes of 128-byte alignment padding.
-        const int stage_elems = dmrt::tma_stage_elems(R);
-        int RC = std::max(1, std::min(block / tpr, R * dmrt::kTmaBox / WB));
-        auto round128 = [](int elems) { return (elems * 4 + 127) / 128 * 128 / 4; };
-        while (RC > 1 && round128(6 * RC * WB) + round128(4 * RC * WB) + 4 * RC * WB > stage_elems) --RC;
-        cav[i].offP = round128(6 * RC * WB);
-        cav[i].offN = cav[i].offP + round128(4 * RC * WB);
+        // Stage placement for RC rows: each plane group starts on a 128-byte
+        // boundary (a tensor copy's destination must); 0 when it does not fit.
+        auto r128 = [](long long bytes) { return (bytes + 127) / 128 * 128; };
+        auto place = [&](int rc, dmrt::StageOffsets& so) -> long long {
+            const long long row = (long long)rc * WB;
+            if (!split) {
+                const long long zP = r128(6 * row * 4), zN = r128(zP + 4 * row * 4);
+                so = {(int)(zP / 4), (int)(zN / 4), 0, 0, 0};
+                return zN + 4 * row * 4;
+            }
+            const long long zP = r128(3 * row * 2), zN = r128(zP + 3 * row * 2), g0 = r128(zN + 3 * row * 2);
+            const long long gP = r128(3 * row * 4), gN = r128(gP + row * 4);
+            so = {(int)(zP / 2), (int)(zN / 2), (int)g0, (int)(gP / 4), (int)(gN / 4)};
+            return g0 + gN + row * 4;
+        };
+        // Rows per item: as many as the block's threads and the stage allow.
+        int RC = std::max(1, block / tpr);
+        dmrt::StageOffsets so;
+        while (RC > 1 && place(RC, so) > stage_bytes) --RC;
+        if (place(RC, so) > stage_bytes) {
+            std::snprintf(b->err, sizeof b->err, "cavity %d: strip of %d nodes does not fit the stage", i, W);
+            return fail(DMRT_E_ARG);
+        }
+        cav[i].so = so;
         cav[i].n_strips = (c->p.nx + W - 1) / W;
         cav[i].n_rowblocks = (c->p.ny + RC - 1) / RC;
         cav[i].item_base = (int)items;
@@ -1446,13 +1477,19 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         cav[i].WB = WB;
         cav[i].RC = RC;
         cav[i].tpr = tpr;
-        cav[i].stage_bytes = (unsigned)(kPlanes * RC * WB * sizeof(float));
+        cav[i].stage_bytes = (unsigned)((size_t)RC * WB * (9 * fb + 5 * gb));
         items += (long long)cav[i].n_strips * cav[i].n_rowblocks;
         for (int bf = 0; bf < 2; ++bf) {
-            rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 0], buf(c, bf), DMRT_FP32, kPlanes, 6, RC, WB);
-            if (!rc)
-                rc = encode_map(c, &maps[((size_t)i * 2 + bf) * 2 + 1], buf(c, bf), DMRT_FP32, kPlanes, 4, RC,
-                                WB);
+            CUtensorMap* m = &maps[((size_t)i * 2 + bf) * dmrt::kBatchMaps];
+            if (split) {  // 9 float16 flow planes, then 5 float32 thermal planes
+                char* g = reinterpret_cast<char*>(buf(c, bf)) + (size_t)9 * c->L.plane * 2;
+                rc = encode_map(c, &m[0], buf(c, bf), DMRT_FP16, 9, 3, RC, WB);
+                if (!rc) rc = encode_map(c, &m[1], g, DMRT_FP32, 5, 3, RC, WB);
+                if (!rc) rc = encode_map(c, &m[2], g, DMRT_FP32, 5, 1, RC, WB);
+            } else {
+                rc = encode_map(c, &m[0], buf(c, bf), DMRT_FP32, kPlanes, 6, RC, WB);
+                if (!rc) rc = encode_map(c, &m[1], buf(c, bf), DMRT_FP32, kPlanes, 4, RC, WB);
+            }
             if (rc) {
                 std::snprintf(b->err, sizeof b->err, "cavity %d: %.200s", i, c->err);
                 return fail(rc);

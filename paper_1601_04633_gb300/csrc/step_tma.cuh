@@ -366,20 +366,29 @@ __device__ __forceinline__ void put_vals(E* p, const float (&o)[NPT], float shif
     else vec_put<E, NPT>(p, o, shift);
 }
 
+// Where each plane group starts in a shared-memory stage, every start 128-byte
+// aligned (a tensor copy's destination must be). One-type layout: groups Z, P,
+// N of the 14 planes at elements 0, zP, zN. Split layout: the flow groups Z, P,
+// N at flow elements 0, zP, zN; the thermal block at byte g_bytes, its groups
+// Z, P, N at thermal elements 0, gP, gN. Each group is [plane][row][WB].
+struct StageOffsets {
+    int zP, zN;
+    int g_bytes;
+    int gP, gN;
+};
+
 // Pull, collide and store one work item (strip, row block) from its shared-
 // memory stage, and report the Nusselt number of the rows it owns in the
 // first strip. Called by every thread of the block (the Nusselt report is a
 // warp collective); `ok` is false when the stage's wait expired.
 // Geometry: strips of W nodes, shared-memory rows of WB elements (kHalo left
-// of the strip), RC rows per item. One-type layout: plane groups P and N start
-// offP / offN elements into the stage (group Z at 0). Split layout: the flow
-// planes, then the thermal planes, each [plane][row][WB].
+// of the strip), RC rows per item, plane groups placed as `so` says.
 // TS: store the results into the shared-memory output tile `out` (see
 // out_tile_bytes) for the block's tensor store, instead of to global memory.
 template <typename L, int NPT, bool SR, bool TS = false>
 __device__ __forceinline__ void process_item(const unsigned char* stage, const StepArgs& A, const StepConsts& K,
                                              int strip, int rb, int rg, int t, bool ok,
-                                             unsigned salt, int W, int WB, int RC, int offP, int offN,
+                                             unsigned salt, int W, int WB, int RC, const StageOffsets& so,
                                              unsigned char* out = nullptr) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
@@ -390,8 +399,7 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
                                                             (size_t)9 * PL * sizeof(Ef))
                               : reinterpret_cast<const Eg*>(A.src);
     const Ef* stf = reinterpret_cast<const Ef*>(stage);
-    const Eg* stg = L::kSplit ? reinterpret_cast<const Eg*>(stage + (size_t)9 * RC * WB * sizeof(Ef))
-                              : reinterpret_cast<const Eg*>(stage);
+    const Eg* stg = L::kSplit ? reinterpret_cast<const Eg*>(stage + so.g_bytes) : reinterpret_cast<const Eg*>(stage);
     const float sh0 = K.gsh0, sh1 = K.gsh1;  // thermal storage shifts (0 unless g is 16-bit)
     const float sign_l_g = K.left_fixed ? -1.f : 1.f;
     const float sign_r_g = K.right_fixed ? -1.f : 1.f;
@@ -404,13 +412,21 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
 #pragma unroll
     for (int e = 0; e < NPT; ++e) theta[e] = 0.f;
     if (mine) {
-        auto grouped = [&](int plane) {
-            const int g0 = plane >= kGroupN ? kGroupN : plane >= kGroupP ? kGroupP : kGroupZ;
-            const int off = plane >= kGroupN ? offN : plane >= kGroupP ? offP : 0;
+        // Plane p of a layout whose groups start at planes 0, p_P, p_N and at
+        // elements 0, oP, oN of the stage.
+        auto grouped = [&](int plane, int p_P, int p_N, int oP, int oN) {
+            const int g0 = plane >= p_N ? p_N : plane >= p_P ? p_P : 0;
+            const int off = plane >= p_N ? oN : plane >= p_P ? oP : 0;
             return off + ((plane - g0) * RC + rg) * WB;
         };
-        auto rowf = [&](int plane) { return stf + (L::kSplit ? (plane * RC + rg) * WB : grouped(plane)); };
-        auto rowg = [&](int plane) { return stg + (L::kSplit ? (plane * RC + rg) * WB : grouped(plane)); };
+        auto rowf = [&](int plane) {
+            return stf + (L::kSplit ? grouped(plane, 3, 6, so.zP, so.zN)
+                                    : grouped(plane, kGroupP, kGroupN, so.zP, so.zN));
+        };
+        auto rowg = [&](int plane) {
+            return stg + (L::kSplit ? grouped(plane, 3, 4, so.gP, so.gN)
+                                    : grouped(plane, kGroupP, kGroupN, so.zP, so.zN));
+        };
         float F[9][NPT], Gq[5][NPT];
         lds_pull<0, NPT, HALO>(rowf(L::pf(0)), n0, F[0], 0.f);
         lds_pull<1, NPT, HALO>(rowf(L::pf(1)), n0, F[1], 0.f);
@@ -567,6 +583,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     uint64_t* bars = reinterpret_cast<uint64_t*>(outs + (TS ? 2 * kOutBytes : 0));
     constexpr int TPR = 256 / NPT;   // threads per row of a strip
     constexpr int PB = R * kTmaBox;  // elements of one plane in a stage
+    constexpr StageOffsets kSO = L::kSplit ? StageOffsets{3 * PB, 6 * PB, (int)(9 * PB * sizeof(Ef)), 3 * PB, 4 * PB}
+                                           : StageOffsets{kGroupP * PB, kGroupN * PB, 0, 0, 0};
     const int tid = threadIdx.x;
     const int rg = tid / TPR;  // row of the block this thread works on
     const int t = tid % TPR;   // node group within the strip
@@ -653,7 +671,7 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
 
         unsigned char* out = outs + (size_t)(k & 1) * kOutBytes;
         process_item<L, NPT, SR, TS>(stages + (size_t)s * kStageBytes, A, K, cc.strip, cc.rb, rg, t, ok, salt,
-                                     STRIP, kTmaBox, R, kGroupP * PB, kGroupN * PB, out);
+                                     STRIP, kTmaBox, R, kSO, out);
         if constexpr (TS) {
             fence_async_smem();
             if (tid == 0) bulk_wait_read_all();  // item k - 1's store has read the other tile
@@ -683,11 +701,14 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
 // One launch steps every cavity of a batch. The work items of all cavities
 // form one list, cavity after cavity (strip fastest, then row block), which
 // the blocks of the persistent grid share out as described at the kernel.
-// Float32 storage only.
 // Each cavity has its own strip geometry: strips of W nodes (a multiple of
-// 32 NPT, so that every warp stays within one row), boxes WB = W + 8 elements
-// wide and RC rows tall (as many rows as the block's threads and the stage's
-// shared memory allow), so narrow cavities keep the block's lanes busy.
+// 32 NPT, so that every warp stays within one row), boxes WB = W + 2 HALO
+// elements wide and RC rows tall (as many rows as the block's threads and the
+// stage's shared memory allow), so narrow cavities keep the block's lanes busy.
+// Float32 storage (one-type layout, two tensor maps per buffer: 6-plane and
+// 4-plane boxes) or mixed storage (split layout, three: 3-plane flow boxes,
+// 3-plane and 1-plane thermal boxes); maps[(c * 2 + buffer) * 3 + k].
+constexpr int kBatchMaps = 3;
 struct BatchCavity {
     StepArgs args[2];  // by source buffer: args[b] reads buffer b, writes 1 - b
     StepConsts K;
@@ -695,9 +716,8 @@ struct BatchCavity {
     int item_base;     // index of the cavity's first item in the batch list
     int W, WB, RC;     // strip width, box width, rows per item
     int tpr;           // threads per row = W / NPT
-    int offP, offN;    // stage offsets (elements) of plane groups P and N, 128-byte aligned
-    unsigned stage_bytes;
-    int pad2;
+    StageOffsets so;   // plane groups in the stage
+    unsigned stage_bytes;  // bytes the item's tensor copies bring
 };
 
 // Work distribution: block b first takes the static items [b Q, (b + 1) Q)
@@ -710,16 +730,18 @@ struct BatchCavity {
 // to the consumers through shared memory with the stage; an item of -1 ends
 // the block. Counters: ctr[parity] serves this launch; this launch zeroes
 // ctr[1 - parity] for the next one.
-template <int NPT, int R, int S>
+template <typename L, int NPT, int R, int S>
 __global__ void __launch_bounds__(R * (256 / NPT))
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
                           int n_cav, int total_items, int static_per_block, int parity, unsigned* batch_err) {
-    using E = float;
+    using Ef = typename L::Ef;
+    using Eg = typename L::Eg;
+    constexpr size_t kStageBytes = (size_t)tma_stage_elems(R) * sizeof(float);  // same for both layouts
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    E* stages = reinterpret_cast<E*>(smem_raw);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * tma_stage_elems(R) * sizeof(E));
+    unsigned char* stages = smem_raw;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);
     __shared__ int4 stage_item[S];  // (cavity, strip, row block, item) of each stage; cavity -1: no more items
-    constexpr int HALO = tma_halo(sizeof(E));
+    constexpr int HALO = L::kHalo;
     const int tid = threadIdx.x;
     unsigned* ctr = batch_err + 1;
 
@@ -751,7 +773,6 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         }
         return it;
     };
-    // maps[(c * 2 + buffer) * 2 + 0]: 6-plane boxes, [... + 1]: 4-plane boxes.
     auto issue = [&](int it, int s) {
         if (it < 0) {
             stage_item[s] = make_int4(-1, 0, 0, -1);
@@ -766,12 +787,24 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         stage_item[s] = make_int4(pc, strip, rb, it);
         const int x = strip * bc.W - HALO;
         const int j0 = rb * bc.RC;
-        const CUtensorMap* m = maps + ((size_t)pc * 2 + parity) * 2;
-        E* st = stages + (size_t)s * tma_stage_elems(R);
+        const CUtensorMap* m = maps + ((size_t)pc * 2 + parity) * kBatchMaps;
+        unsigned char* st = stages + (size_t)s * kStageBytes;
         mbar_expect_tx(&bars[s], bc.stage_bytes);
-        tma_load_3d(st, m, x, j0, kGroupZ, &bars[s]);
-        tma_load_3d(st + bc.offP, m + 1, x, j0 - 1, kGroupP, &bars[s]);
-        tma_load_3d(st + bc.offN, m + 1, x, j0 + 1, kGroupN, &bars[s]);
+        if constexpr (!L::kSplit) {
+            Ef* e = reinterpret_cast<Ef*>(st);
+            tma_load_3d(e, m, x, j0, kGroupZ, &bars[s]);
+            tma_load_3d(e + bc.so.zP, m + 1, x, j0 - 1, kGroupP, &bars[s]);
+            tma_load_3d(e + bc.so.zN, m + 1, x, j0 + 1, kGroupN, &bars[s]);
+        } else {
+            Ef* f = reinterpret_cast<Ef*>(st);
+            Eg* g = reinterpret_cast<Eg*>(st + bc.so.g_bytes);
+            tma_load_3d(f, m, x, j0, 0, &bars[s]);
+            tma_load_3d(f + bc.so.zP, m, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(f + bc.so.zN, m, x, j0 + 1, 6, &bars[s]);
+            tma_load_3d(g, m + 1, x, j0, 0, &bars[s]);
+            tma_load_3d(g + bc.so.gP, m + 2, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(g + bc.so.gN, m + 2, x, j0 + 1, 4, &bars[s]);
+        }
     };
 
     int issued = 0;
@@ -801,9 +834,8 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         const int tpr = bc.tpr;
         const int rg = tid / tpr;
         const int t = tid - rg * tpr;
-        process_item<OneType<E>, NPT, false>(reinterpret_cast<const unsigned char*>(stages + (size_t)s * tma_stage_elems(R)),
-                                             bc.args[parity], bc.K, work ? w.y : 1, w.z, rg, t, work, 0u, bc.W, bc.WB,
-                                             bc.RC, bc.offP, bc.offN);
+        process_item<L, NPT, false>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
+                                    rg, t, work, 0u, bc.W, bc.WB, bc.RC, bc.so);
         // One barrier per item: it releases the stage and tells every thread
         // whether any wait expired; with none expired, w is the same valid
         // entry in every thread, so the end test is block-uniform.

@@ -1,4 +1,4 @@
-// Batched-sweep TMA step-kernel tiles (float32 storage; see step_tma.cuh).
+// Batched-sweep TMA step-kernel tiles: float32 and mixed storage (see step_tma.cuh).
 #include "dmrt.h"
 #include "step_tma.cuh"
 #include "tma_variants.h"
@@ -6,14 +6,22 @@
 namespace dmrt {
 
 static const TmaVariant kVariants[] = {
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<1, 1, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<1, 2, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<1, 4, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 3, 0, (const void*)step_tma_batch_kernel<1, 4, 3>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 2, 2, 0, (const void*)step_tma_batch_kernel<2, 2, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<2, 4, 2>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<4, 1, 4>},
-    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<4, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 1, 1, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 1, 2, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 1, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 1, 4, 3, 0, (const void*)step_tma_batch_kernel<OneType<float>, 1, 4, 3>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 2, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 2, 2, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 2, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<OneType<float>, 4, 1, 4>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 4, 4, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 1, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 2, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 4, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 4, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 4, 3>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2>},
 };
 
 const TmaVariant* tma_variants_batch(int* n) {

@@ -69,12 +69,12 @@ def _cache_put(path, key, value):
     os.replace(tmp, path)
 
 
-def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None):
-    """Pick the batched kernel's tile for these cavities. Returns
-    {"opts": {...}, "mlups": best, "trials": [...]}."""
+def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0):
+    """Pick the batched kernel's tile for these cavities (storage 0: float32,
+    3: mixed). Returns {"opts": {...}, "mlups": best, "trials": [...]}."""
     from . import dmrt as D
 
-    key = _key("batch", [(c.nx, c.ny) for c in cavities], str(steps))
+    key = _key("batch", [(c.nx, c.ny) for c in cavities], f"{steps}-{storage}")
     hit = _cache_get(cache, key)
     if hit:
         return hit
@@ -83,7 +83,7 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
     for npt, R, S in (tiles or BATCH_TILES):
         for g in graph_steps:
             opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g)
-            b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + 8)
+            b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + 8, storage=storage)
             sec = _time_steps(b.step, steps, warmup)
             b.check()
             b.close()

@@ -111,3 +111,49 @@ def test_autotuner_picks_a_compiled_tile(D):
     r = tune.tune_batch(cavs, steps=20, warmup=4, tiles=[(1, 4, 2), (2, 2, 2)])
     assert r["opts"]["tma_npt"] in (1, 2) and len(r["trials"]) == 2
     assert all(t["mlups"] > 0 for t in r["trials"])
+
+
+@pytest.mark.parametrize("tile", [(1, 4, 2), (2, 2, 2), (4, 4, 2), (1, 1, 2)])
+def test_mixed_batch_members_match_single_contexts_bitwise(D, tile):
+    # Mixed storage (float16 flow, float32 thermal populations): the batched
+    # kernel stores the same rounded values as the single-cavity kernel.
+    cavs = _uneven()
+    npt, R, S = tile
+    b = D.Batch.from_inputs(cavs, opts=dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=16),
+                            nu_capacity=128, storage=D.DMRT_MIXED)
+    b.step(37)
+    b.check()
+    for i, cav in enumerate(cavs):
+        single = D.Cavity2D.from_inputs(cav, nu_capacity=128, storage=D.DMRT_MIXED)
+        single.step(37)
+        single.check()
+        m = b.members[i]
+        assert np.array_equal(m.get_state(), single.get_state()), i
+        assert np.array_equal(m.nusselt(37)[2], single.nusselt(37)[2]), i
+        single.close()
+    b.close()
+
+
+def test_mixed_sweep_sampled_against_oracle(D):
+    # The 64-cavity sweep in mixed storage, 2000 steps: sampled members' Nu
+    # histories within 1e-3 of the oracle's (the mixed-storage target).
+    cavs = inputs.batch_sweep()
+    steps = 2000
+    b = D.Batch.from_inputs(cavs, nu_capacity=steps, storage=D.DMRT_MIXED)
+    b.step(steps)
+    b.check()
+    for i in (0, 17, 63):
+        cav = cavs[i]
+        series = b.members[i].nusselt(steps)[2]
+        mo = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+        f, g = O.init(mo, cav.theta0())
+        ref = O.run(mo, steps, f, g)
+        nu_err = (np.abs(series - ref["nu_series"]) / np.abs(ref["nu_series"])).max()
+        assert nu_err <= 1e-3, (i, nu_err)
+    b.close()
+
+
+def test_batch_rejects_unsupported_storage(D):
+    cavs = _uneven()[:2]
+    with pytest.raises(D.DmrtError):
+        D.Batch.from_inputs(cavs, storage=D.DMRT_FP16)
