@@ -76,10 +76,12 @@ extern "C" {
  * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
  * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)
  * (4,2); NPT 1 with (1,2) (1,3) (1,4) (1,5) (2,2) (2,3) (3,2) (4,2) (4,3).
- * Default (1, 4, 2). FP16 / BF16 storage, rounding to nearest: (1,1,2)
+ * Default (1, 4, 2). FP16 / BF16 storage (default (2, 2, 2)), rounding to nearest: (1,1,2)
  * (1,2,2) (1,4,2) (1,4,3) (1,4,4) (2,2,2) (2,4,2) (2,4,3) (4,4,2); stochastic:
- * (1,1,2) (1,4,2) (2,2,2) (4,4,2). MIXED storage, nearest: (1,1,2) (1,2,2)
- * (1,4,2) (2,2,2); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,2,2) (2,4,2). */
+ * (1,1,2) (1,4,2) (2,2,2) (4,4,2). MIXED storage (default (2, 1, 2)), nearest:
+ * (1,1,2) (1,1,3) (1,1,4) (1,2,2) (1,2,3) (1,4,2) (2,1,2) (2,1,3) (2,1,4)
+ * (2,2,2) (4,1,3) (4,1,4); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2)
+ * (2,1,3) (2,2,2) (2,4,2) (4,1,3). */
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
@@ -106,9 +108,9 @@ typedef struct {
                            storage run the TMA kernel; arithmetic is float32 in every case) */
     int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
-    int32_t tma_rows;   /* TMA kernel: rows per work item (0 = default 4) */
-    int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default 2) */
-    int32_t tma_npt;    /* TMA kernel: nodes per thread, 4, 2 or 1 (0 = default 1) */
+    int32_t tma_rows;   /* TMA kernel: rows per work item (0 = the storage's default tile) */
+    int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default) */
+    int32_t tma_npt;    /* TMA kernel: nodes per thread, 4, 2 or 1 (0 = default) */
     int32_t rounding;   /* 16-bit stores (all populations for FP16 / BF16, the flow
                            populations for MIXED): DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC */
 } dmrt_params;

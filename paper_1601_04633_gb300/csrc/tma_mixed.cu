@@ -14,12 +14,23 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 2, 2, false, true>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 4, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 4, 2, false, true>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 2, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 1, 3, 1, (const void*)step_tma_kernel<Mixed, 1, 1, 3, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 1, 4, 1, (const void*)step_tma_kernel<Mixed, 1, 1, 4, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 2, 3, 1, (const void*)step_tma_kernel<Mixed, 1, 2, 3, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 3, 1, (const void*)step_tma_kernel<Mixed, 2, 1, 3, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 1, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 4, 1, (const void*)step_tma_kernel<Mixed, 2, 1, 4, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 1, 3, 1, (const void*)step_tma_kernel<Mixed, 4, 1, 3, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 1, 4, 1, (const void*)step_tma_kernel<Mixed, 4, 1, 4, false, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 1, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 1, 2, true, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 2, 2, true, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 2, 1, (const void*)step_tma_kernel<Mixed, 1, 4, 2, true, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 3, 1, (const void*)step_tma_kernel<Mixed, 1, 4, 3, true, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 2, 2, true, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 4, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 4, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 2, 1, (const void*)step_tma_kernel<Mixed, 2, 1, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 3, 1, (const void*)step_tma_kernel<Mixed, 2, 1, 3, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 1, 3, 1, (const void*)step_tma_kernel<Mixed, 4, 1, 3, true, true>},
 };
 
 const TmaVariant* tma_variants_mixed(int* n) {

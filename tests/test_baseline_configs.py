@@ -4,9 +4,10 @@
   relative error per field) and the mean-Nu history within 1e-4.
 * 256 x 256 oscillatory (Ra 1e5, Pr 0.005): fields at step 1e4 for every
   storage mode (float32 within 1e-4, the 1e-3-step tolerance grown linearly;
-  the 16-bit and mixed errors are reported with loose bounds); the 1e6-step
-  Nu history's mean, period and amplitude against the oracle's (golden file
-  from tests/golden/make_baseline_goldens.py).
+  the 16-bit and mixed errors are reported with loose bounds); over 1e6 steps
+  the float32 Nu history sample by sample and the mixed-storage histories'
+  mean, period and amplitude against the oracle's record (golden file from
+  tests/golden/make_baseline_goldens.py).
 * The 64-cavity sweep, 50,000 steps in one batch: three sampled members' Nu
   histories within 1e-3 of the oracle's (same golden script).
 * 4096 x 4096, Ra 1e7, Pr 0.001, 20,000 steps: the mixed-storage run's mean-Nu
@@ -97,25 +98,37 @@ def test_cavity_256_fields_at_step_10000(D):
 
 
 def test_cavity_256_one_million_steps_statistics(D):
+    # The oscillatory cavity over 1e6 steps (Fo 1.53) against the oracle's
+    # record. float32 follows the oracle sample by sample for the whole run.
+    # Mixed storage leaves it after Fo ~0.11 (the oscillation's phase drifts),
+    # so its statistics are compared: with stochastic rounding of the flow
+    # populations the mean over the second half stays within 1e-3 (measured
+    # 1.4e-4); with rounding to nearest it is biased low (measured -3.1e-3:
+    # increments below half a float16 unit are lost), which is recorded here
+    # with a bound that only catches a broken path.
     gold = _gold("oracle_config2_256.json")
     cav = inputs.cavity_256_oscillatory()
     steps, every = gold["steps"], gold["every"]
     fo = cav.alpha / cav.ny ** 2 * every
     ref = np.array(gold["nu"])
-    win = 0.5  # Fourier units at the end of the run
-    so = A.nu_statistics(ref, fo, window_fo=win)
-    for storage, rounding in ((0, 0), (3, 0)):
+    half = len(ref) // 2
+    so = A.nu_statistics(ref, fo, window_fo=1.0)
+    for storage, rounding, bound in ((0, 0, 1e-4), (3, 1, 1e-3), (3, 0, 1e-2)):
         sim = D.Cavity2D.from_inputs(cav, storage=storage, rounding=rounding, nu_capacity=steps)
         sim.step(steps)
         sim.check()
         nu = sim.nusselt(steps)[2][every - 1::every]
         sim.close()
-        sg = A.nu_statistics(nu, fo, window_fo=win)
-        print(f"256^2 x 1e6, storage {storage}: mean {sg.mean:.5f} (oracle {so.mean:.5f}), period "
-              f"{sg.period_fo} ({so.period_fo}), amplitude {sg.amplitude:.4f} ({so.amplitude:.4f})")
-        assert sg.mean == pytest.approx(so.mean, rel=2e-3)
-        assert sg.steady == so.steady
-        if not so.steady:
+        sg = A.nu_statistics(nu, fo, window_fo=1.0)
+        dmean = (nu[half:].mean() - ref[half:].mean()) / ref[half:].mean()
+        print(f"256^2 x 1e6, storage {storage} rounding {rounding}: second-half mean {nu[half:].mean():.5f} "
+              f"(oracle {ref[half:].mean():.5f}, {dmean:+.2e}), period {sg.period_fo:.4f} ({so.period_fo:.4f}), "
+              f"amplitude {sg.amplitude:.4f} ({so.amplitude:.4f})")
+        assert abs(dmean) <= bound, (storage, rounding, dmean)
+        assert not sg.steady and not so.steady
+        if storage == 0:
+            assert np.abs(nu - ref).max() <= 1e-3 * np.abs(ref).max()
+        if rounding == 1 or storage == 0:
             assert sg.period_fo == pytest.approx(so.period_fo, rel=0.05)
             assert sg.amplitude == pytest.approx(so.amplitude, rel=0.1)
 
