@@ -314,7 +314,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
 /* ---- Batched sweep: many independent cavities per launch ----------------------
  *
  * Steps n independent side-heated cavities (any sizes and parameters; all
- * float32 or all mixed storage, rounding to nearest) with one launch per time
+ * float32, or all mixed storage with one rounding mode) with one launch per time
  * step of a persistent TMA kernel over the
  * concatenated work items of all cavities, replayed from CUDA graphs. Each
  * member is also an ordinary context (dmrt_batch_context), so dmrt_fields,
@@ -333,7 +333,7 @@ typedef struct {
 
 /* Device workspace for a batch of n cavities (the members' workspaces plus the
  * kernel's tables). Errors as dmrt_derive for any member; DMRT_E_ARG for n < 1,
- * FP16 / BF16 storage, members stored differently, or stochastic rounding. */
+ * FP16 / BF16 storage, or members stored or rounded differently. */
 int dmrt_batch_workspace_size(const dmrt_params* arr, int32_t n, size_t* bytes);
 
 /* Create a batch. arr: n parameter sets; theta0: NULL, or n host pointers (each

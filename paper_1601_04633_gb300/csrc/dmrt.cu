@@ -1279,8 +1279,8 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
             set_err(nullptr, "batched sweep: cavity %d: every cavity needs the same storage", i);
             return DMRT_E_ARG;
         }
-        if (arr[i].rounding != DMRT_ROUND_NEAREST) {
-            set_err(nullptr, "batched sweep: cavity %d: rounding to nearest only", i);
+        if (arr[i].rounding != arr[0].rounding) {
+            set_err(nullptr, "batched sweep: cavity %d: every cavity needs the same rounding", i);
             return DMRT_E_ARG;
         }
         L->off[i] = o;
@@ -1396,7 +1396,9 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     const void* func = nullptr;
     const int storage = arr[0].storage;
     for (int i = 0; i < nv; ++i)
-        if (vars[i].storage == storage && vars[i].npt == npt && vars[i].R == R && vars[i].S == S) func = vars[i].func;
+        if (vars[i].storage == storage && vars[i].rounding == arr[0].rounding && vars[i].npt == npt && vars[i].R == R &&
+            vars[i].S == S)
+            func = vars[i].func;
     if (!func) {
         set_err(nullptr, "no batched tile with %d nodes/thread, %d rows, %d stages is compiled in for this storage",
                 npt, R, S);

@@ -730,7 +730,7 @@ struct BatchCavity {
 // to the consumers through shared memory with the stage; an item of -1 ends
 // the block. Counters: ctr[parity] serves this launch; this launch zeroes
 // ctr[1 - parity] for the next one.
-template <typename L, int NPT, int R, int S>
+template <typename L, int NPT, int R, int S, bool SR = false>
 __global__ void __launch_bounds__(R * (256 / NPT))
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
                           int n_cav, int total_items, int static_per_block, int parity, unsigned* batch_err) {
@@ -834,8 +834,13 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         const int tpr = bc.tpr;
         const int rg = tid / tpr;
         const int t = tid - rg * tpr;
-        process_item<L, NPT, false>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
-                                    rg, t, work, 0u, bc.W, bc.WB, bc.RC, bc.so);
+        // Stochastic rounding: the cavity's per-step salt, as its own context would
+        // use (its step count was written by the previous launch: read-only here).
+        unsigned salt = 0;
+        if constexpr (SR)
+            if (work) salt = hash32((unsigned)__ldg(bc.args[parity].step_in) * 0x9e3779b9u + 0x632be5abu);
+        process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
+                                 rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so);
         // One barrier per item: it releases the stage and tells every thread
         // whether any wait expired; with none expired, w is the same valid
         // entry in every thread, so the end test is block-uniform.

@@ -22,6 +22,14 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 1, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 2, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 4, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 4, 3, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2, true>},
 };
 
 const TmaVariant* tma_variants_batch(int* n) {

@@ -492,10 +492,12 @@ class Batch:
         self.members = [_Member(self, i, params_list[i]) for i in range(n)]
 
     @classmethod
-    def from_inputs(cls, cavities, opts=None, nu_capacity=1 << 16, storage=DMRT_FP32, **kw):
-        """Every cavity stored alike: DMRT_FP32 or DMRT_MIXED."""
+    def from_inputs(cls, cavities, opts=None, nu_capacity=1 << 16, storage=DMRT_FP32,
+                    rounding=DMRT_ROUND_NEAREST, **kw):
+        """Every cavity stored alike: DMRT_FP32, or DMRT_MIXED with either rounding."""
         ps = [make_params(c.nx, c.ny, c.Ra, c.Pr, c.alpha, theta_hot=c.theta_hot, theta_cold=c.theta_cold,
-                          theta_init=c.theta_init, nu_capacity=nu_capacity, storage=storage) for c in cavities]
+                          theta_init=c.theta_init, nu_capacity=nu_capacity, storage=storage, rounding=rounding)
+              for c in cavities]
         return cls(ps, [c.theta0() for c in cavities], opts=opts, **kw)
 
     @property

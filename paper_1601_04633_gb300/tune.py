@@ -71,12 +71,12 @@ def _cache_put(path, key, value):
     os.replace(tmp, path)
 
 
-def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0):
+def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0, rounding=0):
     """Pick the batched kernel's tile for these cavities (storage 0: float32,
     3: mixed). Returns {"opts": {...}, "mlups": best, "trials": [...]}."""
     from . import dmrt as D
 
-    key = _key("batch", [(c.nx, c.ny) for c in cavities], f"{steps}-{storage}")
+    key = _key("batch", [(c.nx, c.ny) for c in cavities], f"{steps}-{storage}-{rounding}")
     hit = _cache_get(cache, key)
     if hit:
         return hit
@@ -86,7 +86,8 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
         for g in graph_steps:
             opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g)
             # The warm-up covers one whole graph, so its instantiation is not timed.
-            b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + g + 8, storage=storage)
+            b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + g + 8, storage=storage,
+                                    rounding=rounding)
             sec = _time_steps(b.step, steps, max(warmup, g))
             b.check()
             b.close()

@@ -113,18 +113,20 @@ def test_autotuner_picks_a_compiled_tile(D):
     assert all(t["mlups"] > 0 for t in r["trials"])
 
 
+@pytest.mark.parametrize("rounding", [0, 1], ids=["nearest", "stochastic"])
 @pytest.mark.parametrize("tile", [(1, 4, 2), (2, 2, 2), (4, 4, 2), (1, 1, 2)])
-def test_mixed_batch_members_match_single_contexts_bitwise(D, tile):
+def test_mixed_batch_members_match_single_contexts_bitwise(D, tile, rounding):
     # Mixed storage (float16 flow, float32 thermal populations): the batched
-    # kernel stores the same rounded values as the single-cavity kernel.
+    # kernel stores the same rounded values as the single-cavity kernel (for
+    # stochastic rounding, the same bits from each cavity's own step count).
     cavs = _uneven()
     npt, R, S = tile
     b = D.Batch.from_inputs(cavs, opts=dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=16),
-                            nu_capacity=128, storage=D.DMRT_MIXED)
+                            nu_capacity=128, storage=D.DMRT_MIXED, rounding=rounding)
     b.step(37)
     b.check()
     for i, cav in enumerate(cavs):
-        single = D.Cavity2D.from_inputs(cav, nu_capacity=128, storage=D.DMRT_MIXED)
+        single = D.Cavity2D.from_inputs(cav, nu_capacity=128, storage=D.DMRT_MIXED, rounding=rounding)
         single.step(37)
         single.check()
         m = b.members[i]
