@@ -218,10 +218,13 @@ template <typename E>
 __device__ __forceinline__ E from_f_sr(float x, unsigned rnd);
 template <>
 __device__ __forceinline__ __half from_f_sr<__half>(float x, unsigned rnd) {
+    // Discarded bits: 13 for normal float16 targets (biased float32 exponent
+    // e >= 113), one more per binade below, at most 24; the random word is
+    // shifted right by 32 minus that count, i.e. by max(min(19, e - 94), 8).
     const unsigned b = __float_as_uint(x);
     const int e = (int)((b >> 23) & 0xffu);
-    const int width = min(13 + max(0, 113 - e), 24);
-    return __float2half_rz(__uint_as_float(b + (rnd >> (32 - width))));
+    const int sh = max(min(19, e - 94), 8);
+    return __float2half_rz(__uint_as_float(b + (rnd >> sh)));
 }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f_sr<__nv_bfloat16>(float x, unsigned rnd) {
