@@ -231,6 +231,19 @@ int dmrt_set_state(dmrt_ctx* c, const float* host);
 int dmrt_save(dmrt_ctx* c, void* host_buf, size_t cap, size_t* used);
 int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size);
 
+/* ---- Failure-path check of the bounded waits (the paper has no counterpart) ----
+ *
+ * The TMA step kernels wait on mbarriers for their tensor copies; every such
+ * wait gives up after 2 s, records the failure (dmrt_check then returns
+ * DMRT_E_TIMEOUT) and lets the kernel end, so a copy that never completes
+ * cannot hang the GPU. dmrt_probe_bounded_wait runs that wait routine on an
+ * mbarrier that nothing ever completes, with limit_ns in [1 ms, 2 s], on the
+ * given stream (cudaStream_t as void*), and returns DMRT_E_TIMEOUT when the
+ * wait gave up as designed (*waited_ns, nullable: the time it waited),
+ * DMRT_OK if it completed (a defect), DMRT_E_ARG or DMRT_E_CUDA otherwise.
+ * Uses a file-scope device word; allocates nothing. Synchronises the stream. */
+int dmrt_probe_bounded_wait(int64_t limit_ns, void* stream, int64_t* waited_ns);
+
 /* ---- One step without any device allocation (the paper has no counterpart) ----
  *
  * For callers that cannot allocate device memory where they step a cavity: code

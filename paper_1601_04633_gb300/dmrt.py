@@ -116,6 +116,7 @@ SIGNATURES = {
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_save": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_probe_bounded_wait": (ctypes.c_int, [ctypes.c_int64, _VP, ctypes.POINTER(ctypes.c_int64)]),
     "dmrt_load": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
     "dmrt_adjoint_workspace_size": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
