@@ -492,7 +492,7 @@ def run_dmrt(args):
         "e2e": {"value": ws * nodes * args.steps / e2e_s / 1e6, "unit": UNIT,
                 "h2d_bytes_per_step": 8 * nodes / steps,
                 "d2h_bytes_per_step": (12 * nodes + 8 * args.steps) / steps},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps + 1,  # one step kernel per step, one Nusselt finalize per run
         "clocks": sampler.summary(),
         "nu_mean_last": nu_mean,
     }
