@@ -317,7 +317,9 @@ def run_dmrt(args):
         for name, cav_s, st, n_s in (("cavity_64_fp32", inputs.cavity_64(), 0, 20000),
                                      ("cavity_128_adjoint_fp32", inputs.cavity_128_adjoint(), 0, 10000),
                                      ("cavity_256_fp32", inputs.cavity_256_oscillatory(), 0, 20000),
-                                     ("cavity_256_mixed", inputs.cavity_256_oscillatory(), 3, 20000)):
+                                     ("cavity_256_mixed", inputs.cavity_256_oscillatory(), 3, 20000),
+                                     ("cavity_256_fp16", inputs.cavity_256_oscillatory(), 1, 20000),
+                                     ("cavity_256_bf16", inputs.cavity_256_oscillatory(), 2, 20000)):
             s3 = D.Cavity2D.from_inputs(cav_s, nu_capacity=n_s + args.warmup, storage=st)
             s3.step(args.warmup)
             torch.cuda.synchronize()
