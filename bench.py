@@ -39,8 +39,8 @@ STORAGES = {"fp32": (0, 0), "fp16": (1, 0), "bf16": (2, 0), "fp16_sr": (1, 1), "
 BYTES_PER_NODE = {"fp32": 112, "fp16": 56, "bf16": 56, "fp16_sr": 56, "bf16_sr": 56, "mixed": 76,
                   "mixed_sr": 76}
 # Tiles (nodes per thread, rows, stages) of the secondary storage runs.
-SECONDARY_TILES = {"fp16": (2, 2, 2), "bf16": (2, 2, 2), "fp16_sr": (2, 2, 2), "mixed": (2, 1, 2),
-                   "mixed_sr": (2, 1, 2)}
+SECONDARY_TILES = {"fp16": (2, 4, 2), "bf16": (2, 4, 2), "fp16_sr": (4, 4, 2), "bf16_sr": (4, 4, 2),
+                   "mixed": (2, 1, 2), "mixed_sr": (2, 1, 2)}
 FALLBACK_HBM_GBS = 6800.0
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_4096x4096.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", f)

@@ -63,7 +63,9 @@ extern "C" {
  * neighbour in units of the spacing, so that the expected stored value equals
  * the float32 value and increments smaller than half a unit in the last place
  * are kept on average; the random bits come from a per-node, per-step hash
- * (deterministic: a run repeats bit for bit). Float32 storage rounds nothing. */
+ * (deterministic: a run repeats bit for bit), 13 per value for float16 and 16
+ * for bfloat16, consumed by the GPU's stochastically rounding conversion
+ * instruction. Float32 storage rounds nothing. */
 #define DMRT_ROUND_NEAREST 0
 #define DMRT_ROUND_STOCHASTIC 1
 
@@ -76,9 +78,10 @@ extern "C" {
  * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
  * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)
  * (4,2); NPT 1 with (1,2) (1,3) (1,4) (1,5) (2,2) (2,3) (3,2) (4,2) (4,3).
- * Default (1, 4, 2). FP16 / BF16 storage (default (2, 2, 2)), rounding to nearest: (1,1,2)
- * (1,2,2) (1,4,2) (1,4,3) (1,4,4) (2,2,2) (2,4,2) (2,4,3) (4,4,2); stochastic:
- * (1,1,2) (1,4,2) (2,2,2) (4,4,2). MIXED storage (default (2, 1, 2)), nearest:
+ * Default (1, 4, 2). FP16 / BF16 storage, rounding to nearest (default (2, 4, 2)):
+ * (1,1,2) (1,2,2) (1,4,2) (1,4,3) (1,4,4) (2,2,2) (2,4,2) (2,4,3) (4,2,2) (4,4,2);
+ * stochastic (default (4, 4, 2)): (1,1,2) (1,4,2) (2,2,2) (2,4,2) (4,2,2) (4,4,2);
+ * with fewer rows than the default tile, (1, 1, 2). MIXED storage (default (2, 1, 2)), nearest:
  * (1,1,2) (1,1,3) (1,1,4) (1,2,2) (1,2,3) (1,4,2) (2,1,2) (2,1,3) (2,1,4)
  * (2,2,2) (4,1,3) (4,1,4); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2)
  * (2,1,3) (2,2,2) (2,4,2) (4,1,3). */

@@ -329,11 +329,11 @@ int plane_storage(const dmrt_params& p, int k) {
 // Default TMA tile (nodes per thread, rows, stages) per storage mode, the
 // fastest measured on the 4096^2 cavity.
 void default_tile(int storage, int rounding, int* npt, int* R, int* S) {
-    (void)rounding;
     if (storage == DMRT_MIXED) {
         *npt = 2, *R = 1, *S = 2;
     } else if (storage == DMRT_FP16 || storage == DMRT_BF16) {
-        *npt = 2, *R = 2, *S = 2;
+        if (rounding == DMRT_ROUND_STOCHASTIC) *npt = 4, *R = 4, *S = 2;
+        else *npt = 2, *R = 4, *S = 2;
     } else {
         *npt = 1, *R = 4, *S = 2;
     }
@@ -405,8 +405,10 @@ int setup_kernel(dmrt_ctx* c) {
     int R = p.tma_rows > 0 ? p.tma_rows : dr;
     int S = p.tma_stages > 0 ? p.tma_stages : ds;
     if (p.tma_rows <= 0 && p.ny < R) {
-        // Fewer rows than the default tile: one row per item.
+        // Fewer rows than the default tile: one row per item (16-bit storage:
+        // one node per thread, the one-row tile compiled for both roundings).
         R = 1;
+        if (p.tma_npt <= 0 && (p.storage == DMRT_FP16 || p.storage == DMRT_BF16)) npt = 1;
         if (p.tma_stages <= 0) S = npt == 1 ? 2 : 3;
     }
     if (want == DMRT_KERNEL_AUTO)

@@ -138,22 +138,14 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---- typed storage -----------------------------------------------------------
-// Populations are stored as float32, or rounded to-nearest to float16 / bfloat16
-// (the collision always runs in float32). 16-bit storage keeps the thermal
+// Populations are stored as float32, or rounded (to nearest, or stochastically)
+// to float16 / bfloat16 (the collision always runs in float32). 16-bit storage keeps the thermal
 // populations shifted by their rest weight times theta_ref: a stored g_i is
 // g_i - w_i theta_ref (w_0 = (1-a)/5, w_1..4 = (4+a)/20); the flow populations
 // are already shifted by w_i rho0 (Eq. 33).
 __device__ __forceinline__ float to_f(float x) { return x; }
 __device__ __forceinline__ float to_f(__half x) { return __half2float(x); }
 __device__ __forceinline__ float to_f(__nv_bfloat16 x) { return __bfloat162float(x); }
-template <typename E>
-__device__ __forceinline__ E from_f(float x);
-template <>
-__device__ __forceinline__ float from_f<float>(float x) { return x; }
-template <>
-__device__ __forceinline__ __half from_f<__half>(float x) { return __float2half_rn(x); }
-template <>
-__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
 // Only 16-bit storage is shifted; float32 values are stored as they are.
 template <typename E>
@@ -199,37 +191,47 @@ __device__ __forceinline__ float ldg_one(const E* p, float shift) {
     return o[0];
 }
 
-template <typename E, int N>
-__device__ __forceinline__ void vec_put(E* p, const float (&o)[N], float shift) {
-    Pack<E, N> q;
-#pragma unroll
-    for (int e = 0; e < N; ++e) q.v[e] = from_f<E>(kShifted<E> ? o[e] - shift : o[e]);
-    *reinterpret_cast<Pack<E, N>*>(p) = q;
+// Two float32 values converted to a packed pair of E, the first in the low half
+// (the lower address). Rounding to nearest even: one paired conversion.
+template <typename E>
+__device__ __forceinline__ unsigned pack2_rn(float lo, float hi);
+template <>
+__device__ __forceinline__ unsigned pack2_rn<__half>(float lo, float hi) {
+    unsigned d;
+    asm("cvt.rn.f16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
+}
+template <>
+__device__ __forceinline__ unsigned pack2_rn<__nv_bfloat16>(float lo, float hi) {
+    unsigned d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 
-// Stochastic rounding of a float32 value to E (used for 16-bit stores when
-// requested): a uniform random integer below the spacing of E at x is added to
-// the magnitude bits of x, then the result is truncated toward zero, so x is
-// rounded up in magnitude with probability equal to its distance from the
-// lower neighbour in units of the spacing (Croci et al., "Stochastic rounding:
-// implementation, error analysis and applications", R. Soc. Open Sci. 2022).
-// For float16 the discarded bit count grows by one per binade below its
-// smallest normal 2^-14, so subnormal targets are rounded the same way.
+// Stochastic rounding (used for 16-bit stores when requested) by the
+// conversion instruction of this GPU family: for each value a uniform random
+// integer is added below the bits that are kept and the result is truncated
+// toward zero, so x is rounded up in magnitude with probability equal to its
+// distance from the lower neighbour in units of the spacing (Croci et al.,
+// "Stochastic rounding: implementation, error analysis and applications",
+// R. Soc. Open Sci. 2022). The random word holds one 16-bit field per value
+// (high value: bits 16-31, low value: bits 0-15); bfloat16 uses all 16 bits of
+// a field, float16 its low 13 (the bits a normal float16 discards). Each field
+// is filled from bits 16-31 of that value's own draw, so a value's rounding
+// depends on its own draw only, whatever it is paired with.
 template <typename E>
-__device__ __forceinline__ E from_f_sr(float x, unsigned rnd);
+__device__ __forceinline__ unsigned pack2_rs(float lo, float hi, unsigned rlo, unsigned rhi);
 template <>
-__device__ __forceinline__ __half from_f_sr<__half>(float x, unsigned rnd) {
-    // Discarded bits: 13 for normal float16 targets (biased float32 exponent
-    // e >= 113), one more per binade below, at most 24; the random word is
-    // shifted right by 32 minus that count, i.e. by max(min(19, e - 94), 8).
-    const unsigned b = __float_as_uint(x);
-    const int e = (int)((b >> 23) & 0xffu);
-    const int sh = max(min(19, e - 94), 8);
-    return __float2half_rz(__uint_as_float(b + (rnd >> sh)));
+__device__ __forceinline__ unsigned pack2_rs<__half>(float lo, float hi, unsigned rlo, unsigned rhi) {
+    unsigned d;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(__byte_perm(rlo, rhi, 0x7632)));
+    return d;
 }
 template <>
-__device__ __forceinline__ __nv_bfloat16 from_f_sr<__nv_bfloat16>(float x, unsigned rnd) {
-    return __float2bfloat16_rz(__uint_as_float(__float_as_uint(x) + (rnd >> 16)));
+__device__ __forceinline__ unsigned pack2_rs<__nv_bfloat16>(float lo, float hi, unsigned rlo, unsigned rhi) {
+    unsigned d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(__byte_perm(rlo, rhi, 0x7632)));
+    return d;
 }
 
 // Integer hash "lowbias32" (C. Wellons, "Prospecting for hash functions", 2018).
@@ -248,14 +250,36 @@ __device__ __forceinline__ unsigned lcg(unsigned& r) {
     return r;
 }
 
-// Stochastically rounded store of N nodes; r[e] is node e's random state, so
-// a node draws the same bits whatever the number of nodes per thread.
-template <typename E, int N>
-__device__ __forceinline__ void vec_put_sr(E* p, const float (&o)[N], float shift, unsigned (&r)[N]) {
-    Pack<E, N> q;
+// Store of N nodes' values (shifted for 16-bit storage), rounded to nearest
+// or, with SR, stochastically; r[e] is node e's random state, so a node draws
+// the same bits whatever the number of nodes per thread.
+template <typename E, int N, bool SR>
+__device__ __forceinline__ void vec_put(E* p, const float (&o)[N], float shift, unsigned (&r)[N]) {
+    if constexpr (!kShifted<E>) {
+        Pack<E, N> q;
 #pragma unroll
-    for (int e = 0; e < N; ++e) q.v[e] = from_f_sr<E>(o[e] - shift, lcg(r[e]));
-    *reinterpret_cast<Pack<E, N>*>(p) = q;
+        for (int e = 0; e < N; ++e) q.v[e] = o[e];
+        *reinterpret_cast<Pack<E, N>*>(p) = q;
+    } else if constexpr (N == 1) {
+        const unsigned d = SR ? pack2_rs<E>(o[0] - shift, 0.f, lcg(r[0]), 0u) : pack2_rn<E>(o[0] - shift, 0.f);
+        *reinterpret_cast<unsigned short*>(p) = (unsigned short)d;
+    } else {
+        static_assert(N == 2 || N == 4 || N == 8, "16-bit stores take pairs of nodes");
+        unsigned w[N / 2];
+#pragma unroll
+        for (int e = 0; e < N; e += 2) {
+            if constexpr (SR) {
+                const unsigned r0 = lcg(r[e]);
+                const unsigned r1 = lcg(r[e + 1]);
+                w[e / 2] = pack2_rs<E>(o[e] - shift, o[e + 1] - shift, r0, r1);
+            } else {
+                w[e / 2] = pack2_rn<E>(o[e] - shift, o[e + 1] - shift);
+            }
+        }
+        if constexpr (N == 2) *reinterpret_cast<unsigned*>(p) = w[0];
+        else if constexpr (N == 4) *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+        else *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // NPT consecutive values of a shared-memory plane row for nodes n0..n0+NPT-1,
@@ -366,8 +390,7 @@ struct TmaMaps {
 
 template <typename E, int NPT, bool SR>
 __device__ __forceinline__ void put_vals(E* p, const float (&o)[NPT], float shift, unsigned (&r)[NPT]) {
-    if constexpr (SR && kShifted<E>) vec_put_sr<E, NPT>(p, o, shift, r);
-    else vec_put<E, NPT>(p, o, shift);
+    vec_put<E, NPT, SR>(p, o, shift, r);
 }
 
 // Where each plane group starts in a shared-memory stage, every start 128-byte

@@ -15,10 +15,13 @@ static const TmaVariant kVariants[] = {
     {DMRT_BF16, DMRT_ROUND_NEAREST, 2, 4, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 2, 4, 2, false, true>},
     {DMRT_BF16, DMRT_ROUND_NEAREST, 2, 4, 3, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 2, 4, 3, false, true>},
     {DMRT_BF16, DMRT_ROUND_NEAREST, 4, 4, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 4, 4, 2, false, true>},
+    {DMRT_BF16, DMRT_ROUND_NEAREST, 4, 2, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 4, 2, 2, false, true>},
     {DMRT_BF16, DMRT_ROUND_STOCHASTIC, 1, 1, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 1, 1, 2, true, true>},
     {DMRT_BF16, DMRT_ROUND_STOCHASTIC, 1, 4, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 1, 4, 2, true, true>},
     {DMRT_BF16, DMRT_ROUND_STOCHASTIC, 2, 2, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 2, 2, 2, true, true>},
     {DMRT_BF16, DMRT_ROUND_STOCHASTIC, 4, 4, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 4, 4, 2, true, true>},
+    {DMRT_BF16, DMRT_ROUND_STOCHASTIC, 2, 4, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 2, 4, 2, true, true>},
+    {DMRT_BF16, DMRT_ROUND_STOCHASTIC, 4, 2, 2, 1, (const void*)step_tma_kernel<OneType<__nv_bfloat16>, 4, 2, 2, true, true>},
 };
 
 const TmaVariant* tma_variants_bf16(int* n) {

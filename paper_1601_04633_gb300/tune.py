@@ -22,8 +22,9 @@ SINGLE_TILES_FP32 = ([(1, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (2,
                      + [(2, r, s) for r, s in [(1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (4, 2)]]
                      + [(4, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (2, 2), (2, 3), (2, 4),
                                               (4, 2), (4, 3)]])
-SINGLE_TILES_16 = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (1, 4, 4), (2, 2, 2), (2, 4, 2), (2, 4, 3), (4, 4, 2)]
-SINGLE_TILES_16_SR = [(1, 1, 2), (1, 4, 2), (2, 2, 2), (4, 4, 2)]
+SINGLE_TILES_16 = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (1, 4, 4), (2, 2, 2), (2, 4, 2), (2, 4, 3), (4, 2, 2),
+                   (4, 4, 2)]
+SINGLE_TILES_16_SR = [(1, 1, 2), (1, 4, 2), (2, 2, 2), (2, 4, 2), (4, 2, 2), (4, 4, 2)]
 SINGLE_TILES_MIXED = [(1, 1, 2), (1, 1, 3), (1, 1, 4), (1, 2, 2), (1, 2, 3), (1, 4, 2), (2, 1, 2), (2, 1, 3),
                       (2, 1, 4), (2, 2, 2), (4, 1, 3), (4, 1, 4)]
 SINGLE_TILES_MIXED_SR = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 1, 2), (2, 1, 3), (2, 2, 2), (2, 4, 2),
