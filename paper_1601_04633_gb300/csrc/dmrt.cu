@@ -404,12 +404,21 @@ int setup_kernel(dmrt_ctx* c) {
     int npt = p.tma_npt > 0 ? p.tma_npt : dn;
     int R = p.tma_rows > 0 ? p.tma_rows : dr;
     int S = p.tma_stages > 0 ? p.tma_stages : ds;
+    const bool st16 = p.storage == DMRT_FP16 || p.storage == DMRT_BF16;
     if (p.tma_rows <= 0 && p.ny < R) {
         // Fewer rows than the default tile: one row per item (16-bit storage:
         // one node per thread, the one-row tile compiled for both roundings).
         R = 1;
-        if (p.tma_npt <= 0 && (p.storage == DMRT_FP16 || p.storage == DMRT_BF16)) npt = 1;
+        if (p.tma_npt <= 0 && st16) npt = 1;
         if (p.tma_stages <= 0) S = npt == 1 ? 2 : 3;
+    } else if (p.tma_rows <= 0 && st16 && R == 4) {
+        // A small 16-bit grid (fewer than two 4-row items per SM, e.g. 256^2)
+        // takes 2-row items: twice the blocks for a launch that is one wave.
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev), "cudaGetDevice");
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+        const long long strips = (p.nx + dmrt::tma_strip(2) - 1) / dmrt::tma_strip(2);
+        if (strips * ((p.ny + 3) / 4) < 2LL * sms) R = 2;
     }
     if (want == DMRT_KERNEL_AUTO)
         want = (p.storage != DMRT_FP32 || (p.nx > 2 * dmrt::tma_strip(4) && p.ny >= 4 * R))
