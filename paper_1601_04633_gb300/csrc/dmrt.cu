@@ -1251,6 +1251,7 @@ struct dmrt_batch {
     cudaStream_t stream;
     dmrt::BatchCavity* d_cav;
     CUtensorMap* d_maps;
+    int* d_ib;  // first item of each cavity, then the total (n + 1 entries)
     unsigned* d_err;
     int total_items;
     int static_per_block;  // items each block takes before drawing from the shared pool
@@ -1268,7 +1269,7 @@ namespace {
 
 struct BatchLayout {
     std::vector<size_t> off, bytes;
-    size_t off_cav, off_maps, off_err, total;
+    size_t off_cav, off_maps, off_ib, off_err, total;
 };
 
 int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
@@ -1302,6 +1303,8 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
     o += align256((size_t)n * sizeof(dmrt::BatchCavity));
     L->off_maps = o;
     o += align256((size_t)n * 2 * dmrt::kBatchMaps * sizeof(CUtensorMap));
+    L->off_ib = o;
+    o += align256((size_t)(n + 1) * sizeof(int));
     L->off_err = o;
     o += 256;
     L->total = o;
@@ -1328,7 +1331,8 @@ int batch_cuda_fail(dmrt_batch* b, cudaError_t e, const char* what) {
     } while (0)
 
 int batch_launch(dmrt_batch* b, int parity) {
-    void* params[7] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &b->static_per_block, &parity, &b->d_err};
+    void* params[8] = {&b->d_cav, &b->d_maps, &b->d_ib, &b->n, &b->total_items, &b->static_per_block, &parity,
+                       &b->d_err};
     BCK(cudaLaunchKernel(b->func, dim3(b->grid), dim3(b->block), params, b->smem, b->stream),
         "batch step launch");
     return DMRT_OK;
@@ -1341,8 +1345,8 @@ int batch_build_graph(dmrt_batch* b, int from) {
     int par[2] = {from, 1 - from};
     for (int i = 0; i < b->graph_len; ++i) {
         cudaKernelNodeParams kp = {};
-        void* params[7] = {&b->d_cav, &b->d_maps, &b->n, &b->total_items, &b->static_per_block, &par[i & 1],
-                           &b->d_err};
+        void* params[8] = {&b->d_cav, &b->d_maps, &b->d_ib, &b->n, &b->total_items, &b->static_per_block,
+                           &par[i & 1], &b->d_err};
         kp.func = const_cast<void*>(b->func);
         kp.gridDim = dim3(b->grid);
         kp.blockDim = dim3(b->block);
@@ -1529,12 +1533,18 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     b->total_items = (int)items;
     b->d_cav = reinterpret_cast<dmrt::BatchCavity*>(b->ws + L.off_cav);
     b->d_maps = reinterpret_cast<CUtensorMap*>(b->ws + L.off_maps);
+    b->d_ib = reinterpret_cast<int*>(b->ws + L.off_ib);
     b->d_err = reinterpret_cast<unsigned*>(b->ws + L.off_err);
+    std::vector<int> ib(n + 1);
+    for (int i = 0; i < n; ++i) ib[i] = cav[i].item_base;
+    ib[n] = (int)items;
     cudaError_t e = cudaMemcpyAsync(b->d_cav, cav.data(), cav.size() * sizeof(cav[0]), cudaMemcpyHostToDevice,
                                     b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(maps[0]), cudaMemcpyHostToDevice,
                             b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_ib, ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 256, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch tables"));

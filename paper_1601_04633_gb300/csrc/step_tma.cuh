@@ -756,11 +756,17 @@ struct BatchCavity {
 // (thread 0) picks the items and passes each one's (cavity, strip, row block)
 // to the consumers through shared memory with the stage; an item of -1 ends
 // the block. Counters: ctr[parity] serves this launch; this launch zeroes
-// ctr[1 - parity] for the next one.
+// ctr[1 - parity] for the next one. The producer's own latency is on the
+// block's critical path (it computes its share of each item after issuing the
+// next copies), so it reserves its next pool item one item ahead (the atomic
+// completes while the item is computed) and finds an item's cavity in the
+// compact item_base array (first item of each cavity; n_cav + 1 entries,
+// cached in L1) rather than in the cavity records.
 template <typename L, int NPT, int R, int S, bool SR = false>
 __global__ void __launch_bounds__(R * (256 / NPT))
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
-                          int n_cav, int total_items, int static_per_block, int parity, unsigned* batch_err) {
+                          const int* __restrict__ item_base, int n_cav, int total_items, int static_per_block,
+                          int parity, unsigned* batch_err) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     constexpr size_t kStageBytes = (size_t)tma_stage_elems(R) * sizeof(float);  // same for both layouts
@@ -789,15 +795,23 @@ __global__ void __launch_bounds__(R * (256 / NPT))
     const int static_end = next_static + static_per_block;
     const int pool_base = gridDim.x * static_per_block;
     bool drained = false;
+    int reserved = -1;  // pool item reserved ahead (-1: none)
     int pc = 0;  // cavity of the last item issued (items issued by a block increase)
     auto next_item = [&]() -> int {
-        if (next_static < static_end) return next_static++;
-        if (drained) return -1;
-        const int it = pool_base + (int)atomicAdd(&ctr[parity], 1u);
-        if (it >= total_items) {
-            drained = true;
-            return -1;
+        int it;
+        if (next_static < static_end) {
+            it = next_static++;
+            if (next_static < static_end) return it;
+        } else {
+            if (drained) return -1;
+            it = reserved >= 0 ? reserved : pool_base + (int)atomicAdd(&ctr[parity], 1u);
+            if (it >= total_items) {
+                drained = true;
+                return -1;
+            }
         }
+        // The block's next item comes from the pool: reserve it now.
+        reserved = pool_base + (int)atomicAdd(&ctr[parity], 1u);
         return it;
     };
     auto issue = [&](int it, int s) {
@@ -806,7 +820,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
             mbar_arrive(&bars[s]);  // completes the phase with nothing to load
             return;
         }
-        while (pc + 1 < n_cav && cav[pc + 1].item_base <= it) ++pc;
+        while (pc + 1 < n_cav && __ldg(item_base + pc + 1) <= it) ++pc;
         const BatchCavity& bc = cav[pc];
         const int local = it - bc.item_base;
         const int rb = local / bc.n_strips;
