@@ -340,9 +340,10 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
 typedef struct dmrt_batch dmrt_batch;
 
 /* Tile of the batched kernel: nodes per thread, rows per item, pipeline stages
- * (0 = default 1, 4, 2), and steps per CUDA graph (0 = 64; must be even).
- * Compiled tiles (npt, R, S), for both storages: (1,1,2) (1,2,2) (1,4,2)
- * (1,4,3) (2,2,2) (2,4,2) (4,1,4) (4,4,2). */
+ * (0 = default: 2, 2, 2 for FLOAT32, 4, 2, 2 for MIXED storage), and steps
+ * per CUDA graph (0 = 64; must be even). Compiled tiles (npt, R, S), for both
+ * storages and roundings: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2) (2,1,3)
+ * (2,2,2) (2,2,3) (2,4,2) (4,1,4) (4,2,2) (4,4,2). */
 typedef struct {
     int32_t tma_npt, tma_rows, tma_stages, graph_steps;
 } dmrt_batch_opts;

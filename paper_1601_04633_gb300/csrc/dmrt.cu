@@ -18,6 +18,7 @@
 #include "adjoint.cuh"
 #include "step_direct.cuh"
 #include "step_tma.cuh"
+#include "step_tma_batch.cuh"
 #include "tma_variants.h"
 
 using dmrt::plane_f;
@@ -1398,8 +1399,9 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         set_err(nullptr, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
         return DMRT_E_SPACE;
     }
-    const int npt = opts && opts->tma_npt > 0 ? opts->tma_npt : 1;
-    const int R = opts && opts->tma_rows > 0 ? opts->tma_rows : 4;
+    const bool mixed_def = arr[0].storage == DMRT_MIXED;
+    const int npt = opts && opts->tma_npt > 0 ? opts->tma_npt : (mixed_def ? 4 : 2);
+    const int R = opts && opts->tma_rows > 0 ? opts->tma_rows : 2;
     const int S = opts && opts->tma_stages > 0 ? opts->tma_stages : 2;
     const int glen = opts && opts->graph_steps > 0 ? opts->graph_steps : 64;
     if (glen % 2) {
@@ -1465,7 +1467,7 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     const int block = R * (256 / npt);
     const int quantum = 32 * npt;                       // strip widths keep warps in one row
     const int w_max = (dmrt::kTmaBox - 2 * halo) / quantum * quantum;
-    const int stage_bytes = dmrt::tma_stage_elems(R) * 4;  // the compiled stage (float32 sizing)
+    const int stage_bytes = (int)dmrt::tma_stage_bytes_fg(R, fb, gb);  // the compiled stage
     for (int i = 0; i < n; ++i) {
         dmrt_ctx* c = b->sub[i];
         std::memset(&cav[i], 0, sizeof cav[i]);
@@ -1550,7 +1552,7 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch tables"));
     // Launch shape: persistent grid of resident blocks.
     b->block = R * (256 / npt);
-    b->smem = dmrt::tma_smem_bytes(R, S, 4);
+    b->smem = dmrt::tma_smem_bytes_fg(R, S, split ? 2 : 4, 4);
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaFuncSetAttribute(b->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);

@@ -1,0 +1,191 @@
+// Batched step: one launch advances every cavity of a sweep (float32 or mixed
+// storage), built on the single-cavity item routine of step_tma.cuh.
+#pragma once
+
+#include "step_tma.cuh"
+
+namespace dmrt {
+
+// ---- batched sweep ------------------------------------------------------------
+// One launch steps every cavity of a batch. The work items of all cavities
+// form one list, cavity after cavity (strip fastest, then row block), which
+// the blocks of the persistent grid share out as described at the kernel.
+// Each cavity has its own strip geometry: strips of W nodes (a multiple of
+// 32 NPT, so that every warp stays within one row), boxes WB = W + 2 HALO
+// elements wide and RC rows tall (as many rows as the block's threads and the
+// stage's shared memory allow), so narrow cavities keep the block's lanes busy.
+// Float32 storage (one-type layout, two tensor maps per buffer: 6-plane and
+// 4-plane boxes) or mixed storage (split layout, three: 3-plane flow boxes,
+// 3-plane and 1-plane thermal boxes); maps[(c * 2 + buffer) * 3 + k].
+constexpr int kBatchMaps = 3;
+struct BatchCavity {
+    StepArgs args[2];  // by source buffer: args[b] reads buffer b, writes 1 - b
+    StepConsts K;
+    int n_strips, n_rowblocks;
+    int item_base;     // index of the cavity's first item in the batch list
+    int W, WB, RC;     // strip width, box width, rows per item
+    int tpr;           // threads per row = W / NPT
+    StageOffsets so;   // plane groups in the stage
+    unsigned stage_bytes;  // bytes the item's tensor copies bring
+};
+
+// Work distribution: block b first takes the static items [b Q, (b + 1) Q)
+// (contiguous, so mostly one cavity), then draws single items from the
+// dynamic pool [G Q, total) through a per-launch counter. Items of narrow
+// cavities cost more per node (every item carries side walls and the Nusselt
+// rows), so a static split by item count leaves a long tail; the pool evens it
+// out. Which block computes an item does not change its result. The producer
+// (thread 0) picks the items and passes each one's (cavity, strip, row block)
+// to the consumers through shared memory with the stage; an item of -1 ends
+// the block. Counters: ctr[parity] serves this launch; this launch zeroes
+// ctr[1 - parity] for the next one. The producer's own latency is on the
+// block's critical path (it computes its share of each item after issuing the
+// next copies), so it reserves its next pool item one item ahead (the atomic
+// completes while the item is computed) and finds an item's cavity in the
+// compact item_base array (first item of each cavity; n_cav + 1 entries,
+// cached in L1) rather than in the cavity records.
+template <typename L, int NPT, int R, int S, bool SR = false>
+__global__ void __launch_bounds__(R * (256 / NPT))
+    step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
+                          const int* __restrict__ item_base, int n_cav, int total_items, int static_per_block,
+                          int parity, unsigned* batch_err) {
+    using Ef = typename L::Ef;
+    using Eg = typename L::Eg;
+    constexpr size_t kStageBytes = tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));  // a multiple of 128
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* stages = smem_raw;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);
+    __shared__ int4 stage_item[S];  // (cavity, strip, row block, item) of each stage; cavity -1: no more items
+    constexpr int HALO = L::kHalo;
+    const int tid = threadIdx.x;
+    unsigned* ctr = batch_err + 1;
+
+    if (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout) return;
+    if (blockIdx.x == 0 && tid == 0) ctr[1 - parity] = 0u;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    // The previous step's mean Nusselt number of each cavity: blocks 0, 1, ...
+    // before their first item.
+    for (int cc = blockIdx.x; cc < n_cav; cc += gridDim.x) nu_finish_prev(cav[cc].args[parity], true);
+
+    // Producer state (thread 0 only).
+    int next_static = blockIdx.x * static_per_block;
+    const int static_end = next_static + static_per_block;
+    const int pool_base = gridDim.x * static_per_block;
+    bool drained = false;
+    int reserved = -1;  // pool item reserved ahead (-1: none)
+    int pc = 0;  // cavity of the last item issued (items issued by a block increase)
+    auto next_item = [&]() -> int {
+        int it;
+        if (next_static < static_end) {
+            it = next_static++;
+            if (next_static < static_end) return it;
+        } else {
+            if (drained) return -1;
+            it = reserved >= 0 ? reserved : pool_base + (int)atomicAdd(&ctr[parity], 1u);
+            if (it >= total_items) {
+                drained = true;
+                return -1;
+            }
+        }
+        // The block's next item comes from the pool: reserve it now.
+        reserved = pool_base + (int)atomicAdd(&ctr[parity], 1u);
+        return it;
+    };
+    auto issue = [&](int it, int s) {
+        if (it < 0) {
+            stage_item[s] = make_int4(-1, 0, 0, -1);
+            mbar_arrive(&bars[s]);  // completes the phase with nothing to load
+            return;
+        }
+        while (pc + 1 < n_cav && __ldg(item_base + pc + 1) <= it) ++pc;
+        const BatchCavity& bc = cav[pc];
+        const int local = it - bc.item_base;
+        const int rb = local / bc.n_strips;
+        const int strip = local - rb * bc.n_strips;
+        stage_item[s] = make_int4(pc, strip, rb, it);
+        const int x = strip * bc.W - HALO;
+        const int j0 = rb * bc.RC;
+        const CUtensorMap* m = maps + ((size_t)pc * 2 + parity) * kBatchMaps;
+        unsigned char* st = stages + (size_t)s * kStageBytes;
+        mbar_expect_tx(&bars[s], bc.stage_bytes);
+        if constexpr (!L::kSplit) {
+            Ef* e = reinterpret_cast<Ef*>(st);
+            tma_load_3d(e, m, x, j0, kGroupZ, &bars[s]);
+            tma_load_3d(e + bc.so.zP, m + 1, x, j0 - 1, kGroupP, &bars[s]);
+            tma_load_3d(e + bc.so.zN, m + 1, x, j0 + 1, kGroupN, &bars[s]);
+        } else {
+            Ef* f = reinterpret_cast<Ef*>(st);
+            Eg* g = reinterpret_cast<Eg*>(st + bc.so.g_bytes);
+            tma_load_3d(f, m, x, j0, 0, &bars[s]);
+            tma_load_3d(f + bc.so.zP, m, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(f + bc.so.zN, m, x, j0 + 1, 6, &bars[s]);
+            tma_load_3d(g, m + 1, x, j0, 0, &bars[s]);
+            tma_load_3d(g + bc.so.gP, m + 2, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(g + bc.so.gN, m + 2, x, j0 + 1, 4, &bars[s]);
+        }
+    };
+
+    int issued = 0;
+    if (tid == 0) {
+        for (int q = 0; q < S - 1; ++q) {
+            issue(next_item(), q);
+            issued = q + 1;
+        }
+    }
+    bool timed_out = false;
+    int k = 0, s = 0;
+    uint32_t phase = 0;
+    for (;; ++k) {
+        if (tid == 0) {
+            // Item k + S - 1 goes to the stage of item k - 1, released by the
+            // barrier that ended it.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue(next_item(), s == 0 ? S - 1 : s - 1);
+            issued = k + S;
+        }
+        const bool ok = mbar_wait_bounded(&bars[s], phase);
+        // Every thread reads the same entry; a thread whose wait expired may
+        // read a stale one, and the barrier below then ends the block anyway.
+        const int4 w = stage_item[s];
+        const bool work = ok && w.x >= 0;
+        const BatchCavity& bc = cav[work ? w.x : 0];
+        const int tpr = bc.tpr;
+        const int rg = tid / tpr;
+        const int t = tid - rg * tpr;
+        // Stochastic rounding: the cavity's per-step salt, as its own context would
+        // use (its step count was written by the previous launch: read-only here).
+        unsigned salt = 0;
+        if constexpr (SR)
+            if (work) salt = hash32((unsigned)__ldg(bc.args[parity].step_in) * 0x9e3779b9u + 0x632be5abu);
+        process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
+                                 rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so);
+        // One barrier per item: it releases the stage and tells every thread
+        // whether any wait expired; with none expired, w is the same valid
+        // entry in every thread, so the end test is block-uniform.
+        if (__syncthreads_count(!ok)) {
+            timed_out = true;
+            break;
+        }
+        if (w.x < 0) break;
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
+        }
+    }
+    if (timed_out && tid == 0) {
+        atomicOr(batch_err, kErrTimeout);
+        for (int q = k; q < issued; ++q) mbar_wait_bounded(&bars[q % S], (uint32_t)((q / S) & 1));
+    }
+}
+
+// Sums each cavity's last step of a run (one block of 256 threads per cavity).
+static __global__ void nu_finalize_batch_kernel(const BatchCavity* __restrict__ cav, int parity) {
+    nu_finish_prev(cav[blockIdx.x].args[parity], false);
+}
+
+}  // namespace dmrt

@@ -1,6 +1,7 @@
 // Batched-sweep TMA step-kernel tiles: float32 and mixed storage (see step_tma.cuh).
 #include "dmrt.h"
 #include "step_tma.cuh"
+#include "step_tma_batch.cuh"
 #include "tma_variants.h"
 
 namespace dmrt {
@@ -14,6 +15,10 @@ static const TmaVariant kVariants[] = {
     {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 2, 4, 2>},
     {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<OneType<float>, 4, 1, 4>},
     {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 4, 4, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 2, 1, 2>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 1, 3, 0, (const void*)step_tma_batch_kernel<OneType<float>, 2, 1, 3>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 2, 3, 0, (const void*)step_tma_batch_kernel<OneType<float>, 2, 2, 3>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 4, 2, 2, 0, (const void*)step_tma_batch_kernel<OneType<float>, 4, 2, 2>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 1, 2>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 2, 2>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 4, 2>},
@@ -22,6 +27,10 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 2>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 3>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 3>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 1, 2, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 2, 2, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 1, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 1, 4, 2, true>},
@@ -30,6 +39,10 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 3, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 3, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2, true>},
 };
 
 const TmaVariant* tma_variants_batch(int* n) {

@@ -8,6 +8,7 @@ every tile computes bit-identical steps.
 
     python -m paper_1601_04633_gb300.tune --batch      # the 64-cavity sweep
     python -m paper_1601_04633_gb300.tune --single 4096
+    python -m paper_1601_04633_gb300.tune --batch --storage 3 --tile 4 4 2 --steps 16 --graph-steps 16
 """
 from __future__ import annotations
 
@@ -17,7 +18,8 @@ import json
 import os
 
 # Compiled tiles (see include/dmrt.h).
-BATCH_TILES = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 2, 2), (2, 4, 2), (4, 1, 4), (4, 4, 2)]
+BATCH_TILES = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 1, 2), (2, 1, 3), (2, 2, 2), (2, 2, 3), (2, 4, 2),
+               (4, 1, 4), (4, 2, 2), (4, 4, 2)]
 SINGLE_TILES_FP32 = ([(1, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (3, 2), (4, 2), (4, 3)]]
                      + [(2, r, s) for r, s in [(1, 3), (1, 4), (1, 5), (2, 2), (2, 3), (4, 2)]]
                      + [(4, r, s) for r, s in [(1, 2), (1, 3), (1, 4), (1, 5), (1, 6), (2, 2), (2, 3), (2, 4),
@@ -134,13 +136,21 @@ def main():
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--single", type=int, default=0, help="side of a square cavity")
     ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--storage", type=int, default=0, help="0 float32, 1 float16, 2 bfloat16, 3 mixed")
+    ap.add_argument("--rounding", type=int, default=0, help="0 nearest, 1 stochastic")
+    ap.add_argument("--tile", type=int, nargs=3, metavar=("NPT", "R", "S"), help="time this tile only")
+    ap.add_argument("--graph-steps", type=int, default=64, help="steps per CUDA graph (batched sweep)")
     ap.add_argument("--cache", default=None)
     args = ap.parse_args()
+    tiles = [tuple(args.tile)] if args.tile else None
     if args.batch:
-        print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, cache=args.cache), indent=1))
+        print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, tiles=tiles,
+                                    graph_steps=(args.graph_steps,), cache=args.cache, storage=args.storage,
+                                    rounding=args.rounding), indent=1))
     if args.single:
         cav = inputs.Cavity(args.single, args.single, 1e7, 0.001, seed=5)
-        print(json.dumps(tune_single(cav, steps=args.steps, cache=args.cache), indent=1))
+        print(json.dumps(tune_single(cav, storage=args.storage, rounding=args.rounding, steps=args.steps,
+                                     tiles=tiles, cache=args.cache), indent=1))
 
 
 if __name__ == "__main__":

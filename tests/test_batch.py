@@ -41,7 +41,7 @@ def _uneven():
     return out
 
 
-@pytest.mark.parametrize("tile", [(1, 4, 2), (1, 1, 2), (2, 2, 2), (4, 4, 2), (4, 1, 4)])
+@pytest.mark.parametrize("tile", [(1, 4, 2), (1, 1, 2), (2, 2, 2), (4, 4, 2), (4, 1, 4), (2, 1, 3), (2, 2, 3)])
 def test_batch_members_match_single_contexts_bitwise(D, tile):
     cavs = _uneven()
     npt, R, S = tile
@@ -114,7 +114,7 @@ def test_autotuner_picks_a_compiled_tile(D):
 
 
 @pytest.mark.parametrize("rounding", [0, 1], ids=["nearest", "stochastic"])
-@pytest.mark.parametrize("tile", [(1, 4, 2), (2, 2, 2), (4, 4, 2), (1, 1, 2)])
+@pytest.mark.parametrize("tile", [(1, 4, 2), (2, 2, 2), (4, 4, 2), (1, 1, 2), (2, 1, 2), (2, 2, 3)])
 def test_mixed_batch_members_match_single_contexts_bitwise(D, tile, rounding):
     # Mixed storage (float16 flow, float32 thermal populations): the batched
     # kernel stores the same rounded values as the single-cavity kernel (for
