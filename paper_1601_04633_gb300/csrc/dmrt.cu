@@ -434,7 +434,15 @@ int setup_kernel(dmrt_ctx* c) {
     c->R = R;
     c->S = S;
     c->tma_func = nullptr;
-    if (want != DMRT_KERNEL_TMA) return DMRT_OK;
+    if (want != DMRT_KERNEL_TMA) {
+        // A direct grid of fewer blocks than two per SM gets one more row of
+        // blocks, whose first block only sums the previous step's Nusselt rows.
+        int dev = 0, sms = 0;
+        CK(cudaGetDevice(&dev), "cudaGetDevice");
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+        if ((long long)c->grid.x * c->grid.y < 2LL * sms) c->grid.y += 1;
+        return DMRT_OK;
+    }
     const dmrt::TmaVariant* v = find_tma_variant(p.storage, p.rounding, npt, R, S);
     if (!v) {
         set_err(c, "no TMA tile with %d nodes/thread, %d rows, %d stages is compiled in for this "
@@ -469,7 +477,9 @@ int setup_kernel(dmrt_ctx* c) {
         return DMRT_E_ARG;
     }
     const long long items = (long long)c->geo.n_strips * c->geo.n_rowblocks;
-    c->tma_grid = (int)std::min<long long>(items, (long long)sms * per_sm);
+    // A grid smaller than the resident capacity gets one more block, which only
+    // sums the previous step's Nusselt rows (off the first item's path).
+    c->tma_grid = items < (long long)sms * per_sm ? (int)items + 1 : sms * per_sm;
     for (int b = 0; b < 2; ++b) {
         // Loads from buffer b, stores (nx columns wide) to the other one.
         dmrt::TmaMaps& m = c->tmaps[b];
@@ -745,6 +755,26 @@ static int launch_one(dmrt_ctx* c) {
     return DMRT_OK;
 }
 
+// Appends kernel node `kp` to graph g after `prev` (none: first node) through a
+// programmatic edge: the node's blocks may launch while prev's last blocks run
+// and wait in the kernel (grid_dep_wait) for prev to complete. If the edge type
+// is refused, an ordinary edge (launch after completion) is used instead.
+static cudaError_t add_step_node(cudaGraph_t g, cudaGraphNode_t prev, const cudaKernelNodeParams* kp,
+                                 cudaGraphNode_t* node) {
+    cudaError_t e = cudaGraphAddKernelNode(node, g, nullptr, 0, kp);
+    if (e != cudaSuccess || !prev) return e;
+    cudaGraphEdgeData ed;
+    std::memset(&ed, 0, sizeof ed);
+    ed.from_port = cudaGraphKernelNodePortProgrammatic;
+    ed.type = cudaGraphDependencyTypeProgrammatic;
+    e = cudaGraphAddDependencies(g, &prev, node, &ed, 1);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        e = cudaGraphAddDependencies(g, &prev, node, nullptr, 1);
+    }
+    return e;
+}
+
 // A graph of graph_len (even) steps starting from buffer `from`, built node by
 // node (no stream capture, so it works on any stream, the legacy default included).
 static int build_graph(dmrt_ctx* c, int from) {
@@ -771,7 +801,7 @@ static int build_graph(dmrt_ctx* c, int from) {
             kp.kernelParams = dparams;
         }
         cudaGraphNode_t node;
-        cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        cudaError_t e = add_step_node(g, prev, &kp, &node);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
             return cuda_fail(c, e, "cudaGraphAddKernelNode");
@@ -1354,7 +1384,7 @@ int batch_build_graph(dmrt_batch* b, int from) {
         kp.sharedMemBytes = (unsigned)b->smem;
         kp.kernelParams = params;
         cudaGraphNode_t node;
-        cudaError_t e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+        cudaError_t e = add_step_node(g, prev, &kp, &node);
         if (e != cudaSuccess) {
             cudaGraphDestroy(g);
             return batch_cuda_fail(b, e, "cudaGraphAddKernelNode");

@@ -64,6 +64,17 @@ struct StepArgs {
 constexpr unsigned kErrNonFinite = 1u;
 constexpr unsigned kErrTimeout = 2u;
 
+// Programmatic dependent launch. In the step graphs each step kernel depends on
+// the previous one through a programmatic edge, so its blocks may be launched
+// while the previous step's last blocks still run. grid_dep_wait() returns once
+// the previous kernel has completed and its memory operations are visible (at
+// once for a kernel launched without such an edge); a step kernel calls it
+// before its first access to global memory, so nothing it reads or writes
+// overlaps the previous step. grid_dep_launch() then allows the next step's
+// launch to begin.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ float4 ldg4(const float* p) {
     return __ldg(reinterpret_cast<const float4*>(p));
 }

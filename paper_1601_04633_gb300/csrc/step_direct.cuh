@@ -77,9 +77,19 @@ __device__ __forceinline__ float4 pull_finish(const PlaneLoad& L, int j, int x0,
 
 // Internal linkage: every translation unit that launches it compiles its own copy.
 static __global__ void __launch_bounds__(kDirectThreads, 4) step_direct_kernel(StepArgs A, StepConsts K) {
+    grid_dep_wait();
+    grid_dep_launch();
     const int lane = threadIdx.x & 31;
-    // The previous step's mean Nusselt number: the first block.
-    if (blockIdx.x == 0 && blockIdx.y == 0) nu_finish_prev(A, true);
+    // The previous step's mean Nusselt number: the first block, or, when the
+    // grid has one row of blocks more than the cavity needs (small grids, where
+    // it would delay the first block's nodes), the first block of that row,
+    // which does nothing else.
+    const int work_y = (A.ny + (kDirectThreads >> A.wx_log2) - 1) / (kDirectThreads >> A.wx_log2);
+    if (blockIdx.y >= work_y) {
+        if (blockIdx.x == 0) nu_finish_prev(A, true);
+        return;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && gridDim.y == work_y) nu_finish_prev(A, true);
     const int warp = threadIdx.x >> 5;
     Geo G;
     G.nx = A.nx;

@@ -611,19 +611,26 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     const int tid = threadIdx.x;
     const int rg = tid / TPR;  // row of the block this thread works on
     const int t = tid % TPR;   // node group within the strip
-    const int G = gridDim.x;
-
-    // After an expired wait in an earlier launch the state is already invalid:
-    // return at once instead of waiting again.
-    if (*reinterpret_cast<volatile unsigned*>(A.err) & kErrTimeout) return;
+    // Blocks beyond the item count (small grids: one) only sum the previous
+    // step's Nusselt rows, which otherwise delay block 0's first item.
+    const int n_items = T.n_strips * T.n_rowblocks;
+    const bool nu_extra = (int)gridDim.x > n_items;
+    const int G = nu_extra ? n_items : (int)gridDim.x;
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
     }
+    grid_dep_wait();
+    grid_dep_launch();
+    // After an expired wait in an earlier launch the state is already invalid:
+    // return at once instead of waiting again.
+    if (*reinterpret_cast<volatile unsigned*>(A.err) & kErrTimeout) return;
     __syncthreads();
-    // The previous step's mean Nusselt number: block 0, before its first item.
-    if (blockIdx.x == 0) nu_finish_prev(A, true);
+    // The previous step's mean Nusselt number: block 0 before its first item, or
+    // the extra block.
+    if (nu_extra ? (int)blockIdx.x == n_items : blockIdx.x == 0) nu_finish_prev(A, true);
+    if ((int)blockIdx.x >= G) return;
 
     // One item: every plane's R rows of row block rb, groups P and N taken one
     // row below / above (their e_y). One-type layout: ld[0] has 6-plane boxes

@@ -60,13 +60,14 @@ __global__ void __launch_bounds__(R * (256 / NPT))
     const int tid = threadIdx.x;
     unsigned* ctr = batch_err + 1;
 
-    if (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout) return;
-    if (blockIdx.x == 0 && tid == 0) ctr[1 - parity] = 0u;
-
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
         mbar_fence_init();
     }
+    grid_dep_wait();
+    grid_dep_launch();
+    if (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout) return;
+    if (blockIdx.x == 0 && tid == 0) ctr[1 - parity] = 0u;
     __syncthreads();
     // The previous step's mean Nusselt number of each cavity: blocks 0, 1, ...
     // before their first item.
