@@ -120,6 +120,8 @@ __device__ __forceinline__ void collide_vjp(const float (&f)[9], const float (&g
 }
 
 __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts K) {
+    grid_dep_wait();  // launched programmatically after the previous kernel of the sweep
+    grid_dep_launch();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const bool in = i < A.nx;

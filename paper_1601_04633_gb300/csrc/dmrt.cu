@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "dmrt.h"
@@ -781,16 +782,52 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     return DMRT_OK;
 }
 
+extern "C++" {
+// A kernel launch on the stream that may begin while the previous kernel on
+// the stream finishes (programmatic stream serialization); the kernel waits
+// for that kernel's completion (grid_dep_wait) before touching global memory.
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_overlapped(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t stream,
+                                    Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+static cudaError_t launch_overlapped(const void* kernel, dim3 grid, dim3 block, size_t smem,
+                                     cudaStream_t stream, void** params) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, kernel, params);
+}
+}  // extern "C++"
+
 // One step from buffer `from` to the other one.
 static int launch_step(dmrt_ctx* c, int from) {
     dmrt::StepArgs A = step_args(c, from);
     if (c->kernel == DMRT_KERNEL_TMA) {
         void* params[4] = {&c->tmaps[from], &A, &c->sc, &c->geo};
-        cudaError_t e = cudaLaunchKernel(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), params,
-                                         c->tma_smem, c->stream);
+        cudaError_t e = launch_overlapped(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), c->tma_smem,
+                                          c->stream, params);
         if (e != cudaSuccess) return cuda_fail(c, e, "TMA step launch");
     } else {
-        dmrt::step_direct_kernel<<<c->grid, dmrt::kDirectThreads, 0, c->stream>>>(A, c->sc);
+        cudaError_t e = launch_overlapped(dmrt::step_direct_kernel, c->grid, dim3(dmrt::kDirectThreads),
+                                          c->stream, A, c->sc);
+        if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     }
     return DMRT_OK;
 }
@@ -1889,14 +1926,17 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
             RA.dst = slot(t);
             RA.nu_rows = ra_rows + (size_t)(t & 1) * c->p.ny;
             RA.prev_rows = ra_rows + (size_t)((t + 1) & 1) * c->p.ny;
-            dmrt::step_direct_kernel<<<c->grid, dmrt::kDirectThreads, 0, c->stream>>>(RA, c->sc);
+            CK(launch_overlapped(dmrt::step_direct_kernel, c->grid, dim3(dmrt::kDirectThreads), c->stream, RA,
+                                 c->sc),
+               "adjoint recompute launch");
         }
         for (long long k = end; k > start; --k) {
             AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(k - 1 - start);
             AA.nu_in = nu_a;
             AA.nu_out = nu_b;
             AA.w = (k > N - avg_last) ? (float)(1.0 / (double)avg_last) : 0.f;
-            dmrt::adjoint_step_kernel<<<agrid, 128, 0, c->stream>>>(AA, c->sc);
+            CK(launch_overlapped(dmrt::adjoint_step_kernel, agrid, dim3(128), c->stream, AA, c->sc),
+               "adjoint step launch");
             std::swap(nu_a, nu_b);
         }
         CK(cudaGetLastError(), "adjoint launch");
