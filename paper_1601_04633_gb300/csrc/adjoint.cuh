@@ -34,7 +34,7 @@ struct AdjArgs {
     const float* __restrict__ hot;
     const float* __restrict__ cold;
     double* dthw;                      // [ny] dJ/dtheta_w, accumulated
-    double* dgbeta;                    // dJ/dgbeta, accumulated
+    double* dgbeta;                    // dJ/dgbeta, accumulated per block: [gridDim.y][gridDim.x]
     long long plane;
     int nx, ny, pitch;
     float w;                           // w_k (0 outside the averaging window)
@@ -203,11 +203,18 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
 #pragma unroll
         for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
     }
-    // dJ/dgbeta: block sum in fp64, one atomic per warp.
+    // dJ/dgbeta: the block's sum in fp64 in a fixed order (butterfly within each
+    // warp, then the four warps in order), added to the block's own slot. The
+    // steps run one after another, so no atomics are needed and the sum over
+    // the slots, taken in index order at the end, is the same in every run.
+    __shared__ double warp_sum[4];
     double d = in ? (double)dgb : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-    if ((threadIdx.x & 31) == 0 && d != 0.0) atomicAdd(A.dgbeta, d);
+    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = d;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        A.dgbeta[(size_t)blockIdx.y * gridDim.x + blockIdx.x] += ((warp_sum[0] + warp_sum[1]) + warp_sum[2]) + warp_sum[3];
 }
 
 }  // namespace dmrt

@@ -1813,7 +1813,8 @@ namespace {
 struct AdjLayout {
     long long K, C;  // checkpoint interval and count
     size_t state;    // bytes of one state
-    size_t off_ckpt, off_seg, off_nu0, off_nu1, off_dthw, off_misc, off_rows, total;
+    size_t off_ckpt, off_seg, off_nu0, off_nu1, off_dthw, off_dgb, off_misc, off_rows, total;
+    long long n_blocks;  // blocks of the reverse-step grid: one dJ/dgbeta slot each
 };
 
 AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
@@ -1828,6 +1829,8 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_nu0 = o; o += L.state;
     L.off_nu1 = o; o += L.state;
     L.off_dthw = o; o += align256((size_t)c->p.ny * sizeof(double));
+    L.n_blocks = (long long)((c->p.nx + 127) / 128) * c->p.ny;
+    L.off_dgb = o; o += align256((size_t)L.n_blocks * sizeof(double));
     L.off_misc = o; o += 256;
     L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
     L.total = o;
@@ -1896,7 +1899,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     Misc* scratch = reinterpret_cast<Misc*>(w + AL.off_misc);
     CK(cudaMemsetAsync(nu_a, 0, copy_bytes, c->stream), "zero adjoint");
     CK(cudaMemsetAsync(w + AL.off_dthw, 0, AL.off_rows - AL.off_dthw, c->stream), "zero gradients");
-    double* dgb = &scratch->nu_last;  // the scratch block's double doubles as dJ/dgbeta
+    double* dgb = reinterpret_cast<double*>(w + AL.off_dgb);  // per-block slots, zeroed with the gradients
     dmrt::StepArgs RA = step_args(c, 0);  // recompute: Nusselt output into scratch
     double* ra_rows = reinterpret_cast<double*>(w + AL.off_rows);  // two buffers, alternating by step
     RA.nu_ring = ra_rows + 2 * (size_t)c->p.ny;
@@ -1946,14 +1949,17 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     dmrt::adjoint_step_kernel<<<agrid, 128, 0, c->stream>>>(AA, c->sc);
     CK(cudaGetLastError(), "adjoint launch");
     std::vector<double> g((size_t)c->p.ny);
-    double dgbeta = 0.0;
+    std::vector<double> slots((size_t)AL.n_blocks);
     CK(cudaMemcpyAsync(g.data(), dthw, g.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read dJ/dtheta_w");
-    CK(cudaMemcpyAsync(&dgbeta, dgb, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "read dJ/dgbeta");
+    CK(cudaMemcpyAsync(slots.data(), dgb, slots.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "read dJ/dgbeta");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     // The Nusselt stencil's own theta_w term, 8 scale / ny per averaged step.
     const double direct = 8.0 * c->sc.nu_scale / (double)c->p.ny;
     if (dJ_dthetaw)
         for (int j = 0; j < c->p.ny; ++j) dJ_dthetaw[j] = g[(size_t)j] + direct;
+    double dgbeta = 0.0;
+    for (double v : slots) dgbeta += v;  // in block order
     // gbeta = Ra nu alpha / (H^3 dT), so dJ/dRa = dJ/dgbeta * nu alpha / (H^3 dT).
     const double H = (double)c->p.ny, dT = c->p.theta_hot - c->p.theta_cold;
     if (dJ_dRa) *dJ_dRa = dT != 0.0 ? dgbeta * c->k.nu * c->k.alpha / (H * H * H * dT) : 0.0;

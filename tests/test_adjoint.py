@@ -61,6 +61,20 @@ def test_adjoint_advances_like_a_forward_run(D):
     b.close()
 
 
+def test_adjoint_is_deterministic(D):
+    # Every gradient is accumulated in a fixed order (dJ/dgbeta in per-block
+    # slots summed in block order, dJ/dtheta_w by one thread per row), so two
+    # runs give the same bits.
+    cav = inputs.Cavity(200, 90, 1e5, 0.01, noise_amp=1e-3, seed=6)
+    out = []
+    for _ in range(2):
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=400)
+        out.append(sim.adjoint(400, 150))
+        sim.close()
+    (J1, d1, r1), (J2, d2, r2) = out
+    assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
+
+
 def test_adjoint_config_128_against_finite_differences(D):
     # 128 x 128, Ra 1e5, Pr 0.01, hot wall 0.5 + 0.01 N(0, 1), 10000 steps, J over the last 2000.
     cav = inputs.cavity_128_adjoint()
