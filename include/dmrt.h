@@ -74,8 +74,10 @@ extern "C" {
  * global memory, x-shifts by warp shuffles. TMA: a persistent kernel that
  * stages (strip x row-block) tiles in shared memory with 3-D tensor copies
  * through a multi-stage mbarrier pipeline. AUTO picks TMA for grids wider
- * than 496 nodes, CLUSTER for float32 grids of at most 24 direct tiles (about
- * 96^2 nodes), DIRECT otherwise. TMA tiles compiled in, as (nodes per
+ * than 496 nodes and for float32 grids whose one-row items (248-node strips x
+ * rows) number at most 4 per SM, with tile (1, 1, 2) up to 2 per SM and (2, 1,
+ * 3) beyond (e.g. 64^2 to 256^2), DIRECT otherwise (e.g. 384^2). TMA tiles
+ * compiled in, as (nodes per
  * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
  * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)
  * (4,2); NPT 1 with (1,2) (1,3) (1,4) (1,5) (2,2) (2,3) (3,2) (4,2) (4,3).
@@ -89,12 +91,6 @@ extern "C" {
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
-/* CLUSTER (float32; small cavities): the direct kernel's tiles run by one
- * thread-block cluster of up to 16 blocks that advances many steps per launch,
- * with a cluster barrier between steps instead of a kernel boundary (up to
- * 65536 steps per launch; one block of the cluster sums the Nusselt rows).
- * Bit-identical to DIRECT. */
-#define DMRT_KERNEL_CLUSTER 3
 
 /* Wall kinds for the left and right (vertical) walls. Top and bottom are
  * always adiabatic (Eqs. 7-8, 44). */
@@ -116,7 +112,7 @@ typedef struct {
     int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t storage;    /* DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (16-bit and mixed
                            storage run the TMA kernel; arithmetic is float32 in every case) */
-    int32_t kernel;     /* DMRT_KERNEL_AUTO, _DIRECT, _TMA or _CLUSTER */
+    int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
     int32_t tma_rows;   /* TMA kernel: rows per work item (0 = the storage's default tile) */
     int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default) */
@@ -294,9 +290,9 @@ int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* dst,
 
 /* Launch configuration a context resolved to (for reports and tuning). */
 typedef struct {
-    int32_t kernel;       /* DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA or DMRT_KERNEL_CLUSTER */
+    int32_t kernel;       /* DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
     int32_t tma_npt, tma_rows, tma_stages;
-    int32_t grid, block;  /* blocks per step launch (CLUSTER: per launch, one cluster), threads per block */
+    int32_t grid, block;  /* blocks per step launch, threads per block */
     int64_t smem_bytes;   /* dynamic shared memory per block */
     int32_t graph_steps;  /* steps per captured CUDA graph */
 } dmrt_launch;

@@ -87,13 +87,10 @@ struct dmrt_ctx {
     int cur;             // 0: state in buffer A, 1: in buffer B
     long long t;         // steps enqueued
     dmrt::StepConsts sc;
-    int kernel;          // DMRT_KERNEL_DIRECT, _TMA or _CLUSTER (resolved)
-    // direct kernel (and the cluster kernel's tiles)
+    int kernel;          // DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA (resolved)
+    // direct kernel
     int wx_log2;
     dim3 grid;
-    int gy_work;         // rows of direct tiles the cavity needs (grid.y may add one)
-    // cluster kernel: blocks in the one cluster, threads per block
-    int cl_blocks, cl_block;
     // TMA kernel
     int npt, R, S, tma_block;
     dmrt::TmaGeo geo;
@@ -429,60 +426,32 @@ int setup_kernel(dmrt_ctx* c) {
         want = (p.storage != DMRT_FP32 || (p.nx > 2 * dmrt::tma_strip(4) && p.ny >= 4 * R))
                    ? DMRT_KERNEL_TMA
                    : DMRT_KERNEL_DIRECT;
-        // At most 24 direct tiles (about 96^2 nodes): the multi-step cluster
-        // kernel is faster than one launch per step (3.3 against 4.8 us per
-        // step at 64^2; slower from 128^2, where 15 SMs hold too many tiles).
-        if (want == DMRT_KERNEL_DIRECT && (long long)c->grid.x * c->grid.y <= 24) want = DMRT_KERNEL_CLUSTER;
+        if (want == DMRT_KERNEL_DIRECT && p.tma_rows <= 0 && p.tma_npt <= 0 && p.tma_stages <= 0) {
+            // Small float32 grids: one-row items, one or two nodes per thread,
+            // while the one-row items number at most four per SM (one step of a
+            // 64^2 cavity 2.7 us against 4.9 us with the direct kernel; 256^2
+            // 4.2 against 4.8 us; the direct kernel from about 384^2).
+            int dev = 0, sms = 0;
+            CK(cudaGetDevice(&dev), "cudaGetDevice");
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+            const long long rows1 = (long long)((p.nx + dmrt::tma_strip(4) - 1) / dmrt::tma_strip(4)) * p.ny;
+            if (rows1 <= 4LL * sms) {
+                want = DMRT_KERNEL_TMA;
+                R = 1;
+                if (rows1 <= 2LL * sms) npt = 1, S = 2;
+                else npt = 2, S = 3;
+            }
+        }
     }
-    if ((want == DMRT_KERNEL_DIRECT || want == DMRT_KERNEL_CLUSTER) && p.storage != DMRT_FP32) {
-        set_err(c, "the direct and cluster kernels store float32 only; 16-bit and mixed storage run the TMA "
-                   "kernel");
+    if (want == DMRT_KERNEL_DIRECT && p.storage != DMRT_FP32) {
+        set_err(c, "the direct kernel stores float32 only; 16-bit and mixed storage run the TMA kernel");
         return DMRT_E_ARG;
-    }
-    c->gy_work = (int)c->grid.y;
-    if (want == DMRT_KERNEL_CLUSTER) {
-        // One cluster of up to 16 blocks (8 where a 16-block cluster cannot be
-        // placed): up to 15 with up to four 128-thread groups of direct tiles
-        // each, and one that sums the Nusselt rows.
-        const int nvb = (int)(c->grid.x * c->grid.y);
-        const void* f = (const void*)dmrt::step_cluster_kernel;
-        CK(cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1), "cluster size attribute");
-        c->cl_blocks = 0;
-        for (int cb : {16, 8}) {
-            const int nb = std::min(cb, nvb + 1);  // the last block sums the Nusselt rows
-            const int groups = std::min(dmrt::kClusterMaxGroups, (nvb + nb - 2) / (nb - 1));
-            cudaLaunchConfig_t cfg = {};
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = (unsigned)nb;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.gridDim = dim3(nb);
-            cfg.blockDim = dim3(groups * dmrt::kDirectThreads);
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int clusters = 0;
-            if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) {
-                (void)cudaGetLastError();
-                clusters = 0;
-            }
-            if (clusters >= 1) {
-                c->cl_blocks = nb;
-                c->cl_block = groups * dmrt::kDirectThreads;
-                break;
-            }
-        }
-        if (!c->cl_blocks) {
-            set_err(c, "no thread-block cluster for the cluster kernel fits on this GPU");
-            return DMRT_E_ARG;
-        }
     }
     c->kernel = want;
     c->npt = npt;
     c->R = R;
     c->S = S;
     c->tma_func = nullptr;
-    if (want == DMRT_KERNEL_CLUSTER) return DMRT_OK;
     if (want != DMRT_KERNEL_TMA) {
         // A direct grid of fewer blocks than two per SM gets one more row of
         // blocks, whose first block only sums the previous step's Nusselt rows.
@@ -588,8 +557,8 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "stochastic rounding applies to 16-bit and mixed storage only");
         return DMRT_E_ARG;
     }
-    if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_CLUSTER) {
-        set_err(c, "kernel must be DMRT_KERNEL_AUTO, _DIRECT, _TMA or _CLUSTER");
+    if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_TMA) {
+        set_err(c, "kernel must be DMRT_KERNEL_AUTO, _DIRECT or _TMA");
         return DMRT_E_ARG;
     }
     if (p->nu_capacity < 1) {
@@ -907,36 +876,8 @@ static int finalize_nu(dmrt_ctx* c) {
     return DMRT_OK;
 }
 
-// n steps (at most kClusterChunk) in one launch of the cluster kernel.
-constexpr int64_t kClusterChunk = 1 << 16;
-static int launch_cluster(dmrt_ctx* c, int n) {
-    dmrt::StepArgs A0 = step_args(c, c->cur), A1 = step_args(c, 1 - c->cur);
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)c->cl_blocks;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(c->cl_blocks);
-    cfg.blockDim = dim3(c->cl_block);
-    cfg.stream = c->stream;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    const int gx = (int)c->grid.x, gy = c->gy_work;
-    CK(cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel, A0, A1, c->sc, n, gx, gy), "cluster step launch");
-    c->cur ^= n & 1;
-    c->t += n;
-    return DMRT_OK;
-}
-
 int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
-    while (c->kernel == DMRT_KERNEL_CLUSTER && nsteps > 0) {
-        const int n = (int)std::min<int64_t>(nsteps, kClusterChunk);
-        int rc = launch_cluster(c, n);
-        if (rc) return rc;
-        nsteps -= n;
-    }
     while (nsteps > 0) {
         if (nsteps >= c->graph_len) {
             if (!c->graph[c->cur]) {
@@ -1358,11 +1299,6 @@ int dmrt_get_launch(const dmrt_ctx* c, dmrt_launch* out) {
         out->grid = c->tma_grid;
         out->block = c->tma_block;
         out->smem_bytes = (int64_t)c->tma_smem;
-    } else if (c->kernel == DMRT_KERNEL_CLUSTER) {
-        out->tma_npt = out->tma_rows = out->tma_stages = 0;
-        out->grid = c->cl_blocks;
-        out->block = c->cl_block;
-        out->smem_bytes = 0;
     } else {
         out->tma_npt = out->tma_rows = out->tma_stages = 0;
         out->grid = (int32_t)(c->grid.x * c->grid.y);

@@ -32,36 +32,22 @@ struct PlaneLoad {
     float edge;
 };
 
-// State loads: through the read-only path for a state written by an earlier
-// launch, or (CG) from L2, bypassing L1, for a state that other blocks of the
-// same launch wrote (the multi-step cluster kernel).
-template <bool CG>
-__device__ __forceinline__ float4 ld_state4(const float* p) {
-    if constexpr (CG) return __ldcg(reinterpret_cast<const float4*>(p));
-    else return ldg4(p);
-}
-template <bool CG>
-__device__ __forceinline__ float ld_state(const float* p) {
-    if constexpr (CG) return __ldcg(p);
-    else return __ldg(p);
-}
-
-template <int EX, int EY, bool CG>
+template <int EX, int EY>
 __device__ __forceinline__ void pull_load(const float* __restrict__ P, const float* __restrict__ Popp,
                                           int j, int x0, int right_e, const Geo& G, PlaneLoad& L) {
     const int r = j - EY;
     const bool yin = (r >= 0) && (r < G.ny);
     const float* orow = Popp + (size_t)j * G.pitch;
     const float* row = yin ? P + (size_t)r * G.pitch : orow;
-    L.v = ld_state4<CG>(row + x0);
+    L.v = ldg4(row + x0);
     L.edge = 0.f;
     if constexpr (EX == 1) {
-        if (yin && x0 == 0) L.edge = ld_state<CG>(orow);                       // wall partner
-        else if (yin && G.seg_lane == 0) L.edge = ld_state<CG>(row + x0 - 1);  // halo
+        if (yin && x0 == 0) L.edge = __ldg(orow);                       // wall partner
+        else if (yin && G.seg_lane == 0) L.edge = __ldg(row + x0 - 1);  // halo
     }
     if constexpr (EX == -1) {
-        if (yin && right_e >= 0 && right_e < 4) L.edge = ld_state<CG>(orow + G.nx - 1);
-        else if (yin && G.seg_lane == G.wx - 1 && x0 + 4 < G.pitch) L.edge = ld_state<CG>(row + x0 + 4);
+        if (yin && right_e >= 0 && right_e < 4) L.edge = __ldg(orow + G.nx - 1);
+        else if (yin && G.seg_lane == G.wx - 1 && x0 + 4 < G.pitch) L.edge = __ldg(row + x0 + 4);
     }
 }
 
@@ -91,7 +77,6 @@ __device__ __forceinline__ float4 pull_finish(const PlaneLoad& L, int j, int x0,
 
 // The nodes of tile (bx, by) of the direct grid: 128 threads (4 warps), each
 // with four consecutive nodes of one row; rows of WX lanes per warp segment.
-template <bool CG>
 __device__ __forceinline__ void direct_tile(const StepArgs& A, const StepConsts& K, int bx, int by) {
     const int lane = threadIdx.x & 31;
     const int warp = (threadIdx.x & (kDirectThreads - 1)) >> 5;
@@ -121,20 +106,20 @@ __device__ __forceinline__ void direct_tile(const StepArgs& A, const StepConsts&
     PlaneLoad L[kPlanes];
 #define DMRT_PF(k) (S + plane_f(k) * PL)
 #define DMRT_PG(k) (S + plane_g(k) * PL)
-    pull_load<0, 0, CG>(DMRT_PF(0), DMRT_PF(0), j, x0, right_e, G, L[0]);
-    pull_load<1, 0, CG>(DMRT_PF(1), DMRT_PF(3), j, x0, right_e, G, L[1]);
-    pull_load<0, 1, CG>(DMRT_PF(2), DMRT_PF(4), j, x0, right_e, G, L[2]);
-    pull_load<-1, 0, CG>(DMRT_PF(3), DMRT_PF(1), j, x0, right_e, G, L[3]);
-    pull_load<0, -1, CG>(DMRT_PF(4), DMRT_PF(2), j, x0, right_e, G, L[4]);
-    pull_load<1, 1, CG>(DMRT_PF(5), DMRT_PF(7), j, x0, right_e, G, L[5]);
-    pull_load<-1, 1, CG>(DMRT_PF(6), DMRT_PF(8), j, x0, right_e, G, L[6]);
-    pull_load<-1, -1, CG>(DMRT_PF(7), DMRT_PF(5), j, x0, right_e, G, L[7]);
-    pull_load<1, -1, CG>(DMRT_PF(8), DMRT_PF(6), j, x0, right_e, G, L[8]);
-    pull_load<0, 0, CG>(DMRT_PG(0), DMRT_PG(0), j, x0, right_e, G, L[9]);
-    pull_load<1, 0, CG>(DMRT_PG(1), DMRT_PG(3), j, x0, right_e, G, L[10]);
-    pull_load<0, 1, CG>(DMRT_PG(2), DMRT_PG(4), j, x0, right_e, G, L[11]);
-    pull_load<-1, 0, CG>(DMRT_PG(3), DMRT_PG(1), j, x0, right_e, G, L[12]);
-    pull_load<0, -1, CG>(DMRT_PG(4), DMRT_PG(2), j, x0, right_e, G, L[13]);
+    pull_load<0, 0>(DMRT_PF(0), DMRT_PF(0), j, x0, right_e, G, L[0]);
+    pull_load<1, 0>(DMRT_PF(1), DMRT_PF(3), j, x0, right_e, G, L[1]);
+    pull_load<0, 1>(DMRT_PF(2), DMRT_PF(4), j, x0, right_e, G, L[2]);
+    pull_load<-1, 0>(DMRT_PF(3), DMRT_PF(1), j, x0, right_e, G, L[3]);
+    pull_load<0, -1>(DMRT_PF(4), DMRT_PF(2), j, x0, right_e, G, L[4]);
+    pull_load<1, 1>(DMRT_PF(5), DMRT_PF(7), j, x0, right_e, G, L[5]);
+    pull_load<-1, 1>(DMRT_PF(6), DMRT_PF(8), j, x0, right_e, G, L[6]);
+    pull_load<-1, -1>(DMRT_PF(7), DMRT_PF(5), j, x0, right_e, G, L[7]);
+    pull_load<1, -1>(DMRT_PF(8), DMRT_PF(6), j, x0, right_e, G, L[8]);
+    pull_load<0, 0>(DMRT_PG(0), DMRT_PG(0), j, x0, right_e, G, L[9]);
+    pull_load<1, 0>(DMRT_PG(1), DMRT_PG(3), j, x0, right_e, G, L[10]);
+    pull_load<0, 1>(DMRT_PG(2), DMRT_PG(4), j, x0, right_e, G, L[11]);
+    pull_load<-1, 0>(DMRT_PG(3), DMRT_PG(1), j, x0, right_e, G, L[12]);
+    pull_load<0, -1>(DMRT_PG(4), DMRT_PG(2), j, x0, right_e, G, L[13]);
 #undef DMRT_PF
 #undef DMRT_PG
 
@@ -187,39 +172,7 @@ static __global__ void __launch_bounds__(kDirectThreads, 4) step_direct_kernel(S
         return;
     }
     if (blockIdx.x == 0 && blockIdx.y == 0 && gridDim.y == work_y) nu_finish_prev(A, true);
-    direct_tile<false>(A, K, blockIdx.x, blockIdx.y);
-}
-
-// Multi-step variant for small cavities, where a step is far shorter than a
-// kernel boundary: one thread-block cluster (its blocks are co-scheduled)
-// advances the cavity nsteps steps in one launch. The direct grid's gx x gy
-// tiles are shared out over the cluster's 128-thread groups, and a cluster
-// barrier (release / acquire at cluster scope) ends each step instead of a
-// kernel boundary; the state is loaded from L2 (.cg), since other blocks of
-// the cluster wrote it within this launch. The cluster's last block sums the
-// previous step's Nusselt rows during each step. Every thread runs every step and
-// every barrier (no early exit). Results are bit-identical to step_direct_kernel.
-constexpr int kClusterMaxGroups = 4;  // 128-thread groups per block (at most 512 threads)
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-static __global__ void __launch_bounds__(kDirectThreads * kClusterMaxGroups, 1)
-    step_cluster_kernel(StepArgs A0, StepArgs A1, StepConsts K, int nsteps, int gx, int gy) {
-    grid_dep_wait();
-    // The last block of the cluster only sums the Nusselt rows; the others
-    // share out the tiles.
-    const int per_block = blockDim.x / kDirectThreads;
-    const int groups = (gridDim.x - 1) * per_block;
-    const int g = blockIdx.x * per_block + threadIdx.x / kDirectThreads;
-    const bool nu_block = blockIdx.x == gridDim.x - 1;
-    const int nvb = gx * gy;
-    for (int s = 0; s < nsteps; ++s) {
-        const StepArgs& A = (s & 1) ? A1 : A0;
-        if (nu_block) nu_finish_prev(A, true);
-        else
-            for (int v = g; v < nvb; v += groups) direct_tile<true>(A, K, v % gx, v / gx);
-        cluster_sync();
-    }
+    direct_tile(A, K, blockIdx.x, blockIdx.y);
 }
 
 }  // namespace dmrt

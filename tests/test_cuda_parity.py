@@ -67,8 +67,8 @@ def assert_parity(gpu, ref, field_tol=FIELD_TOL, nu_tol=NU_TOL):
     assert e <= nu_tol, f"local Nu: {e:.3e}"
 
 
-KERNELS = [1, 2, 3]  # DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA, DMRT_KERNEL_CLUSTER
-KERNEL_IDS = ["direct", "tma", "cluster"]
+KERNELS = [0, 1, 2]  # DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA
+KERNEL_IDS = ["auto", "direct", "tma"]
 
 
 @pytest.mark.parametrize("kernel", KERNELS, ids=KERNEL_IDS)
@@ -195,38 +195,15 @@ def test_deterministic_and_graph_equals_single_launches(D, kernel):
 TMA_TILES = tune.SINGLE_TILES_FP32  # every compiled float32 tile
 
 
-@pytest.mark.parametrize("nx,ny", [(32, 32), (64, 64), (128, 128), (256, 256)])
-def test_cluster_kernel_runs_equal_direct_steps(D, nx, ny):
-    # One launch of the cluster kernel runs up to 65536 steps with a cluster
-    # barrier between them; a run longer than that (two launches, the second of
-    # odd length) and runs split over several calls give the direct kernel's bits.
-    steps = 70001 if nx == 32 else 2001
-    cav = inputs.Cavity(nx, ny, 1e4 if nx == 32 else 1e5, 0.01, noise_amp=1e-3, seed=nx + 7)  # Ma <= 0.07
-    out = []
-    for kernel, chunks in ((1, [steps]), (3, [steps]), (3, [1, steps // 2, steps - 1 - steps // 2])):
-        sim = D.Cavity2D.from_inputs(cav, kernel=kernel, nu_capacity=steps)
-        for n in chunks:
-            sim.step(n)
-        sim.check()
-        launch = sim.launch
-        out.append((sim.get_state(), sim.nusselt(steps)[2]))
-        sim.close()
-        if kernel == 3:
-            assert launch["kernel"] == 3 and 1 <= launch["grid"] <= 16
-    for st, nu in out[1:]:
-        assert np.array_equal(st, out[0][0]) and np.array_equal(nu, out[0][1])
-
-
 def test_all_kernel_variants_agree_bitwise(D):
     # Every variant computes the same per-node arithmetic on the same pulled values:
-    # the direct kernel, the multi-step cluster kernel and every compiled TMA tile
-    # give identical bits, including the Nusselt series, over several steps from a
-    # random state.
+    # the direct kernel and every compiled TMA tile give identical bits, including
+    # the Nusselt series, over several steps from a random state.
     nx, ny, steps = 1000, 301, 5
     cav = inputs.Cavity(nx, ny, 1e6, 0.005, noise_amp=0.0)
     state = _random_state(nx, ny, seed=41)
     outs = []
-    for kernel, (npt, R, S) in [(1, (0, 0, 0)), (3, (0, 0, 0))] + [(2, t) for t in TMA_TILES]:
+    for kernel, (npt, R, S) in [(1, (0, 0, 0))] + [(2, t) for t in TMA_TILES]:
         sim = D.Cavity2D.from_inputs(cav, kernel=kernel, tma_rows=R, tma_stages=S, tma_npt=npt)
         sim.set_state(state)
         sim.step(steps)
