@@ -1858,6 +1858,20 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     AA.nu_next = (float)(c->sc.nu_scale / c->p.ny);
     AA.gather_only = 0;
     const dim3 agrid((c->p.nx + 127) / 128, c->p.ny);
+    // The segment recompute runs the context's own step kernel. For the TMA
+    // kernel every checkpoint and segment slot it reads gets its load maps
+    // (float32 storage stores from registers, so no store maps are needed).
+    const bool tma_re = c->kernel == DMRT_KERNEL_TMA;
+    std::vector<dmrt::TmaMaps> ck_maps(tma_re ? (size_t)AL.C : 0), sl_maps(tma_re ? (size_t)AL.K : 0);
+    for (size_t q = 0; q < ck_maps.size() + sl_maps.size(); ++q) {
+        const bool ck = q < ck_maps.size();
+        dmrt::TmaMaps& m = ck ? ck_maps[q] : sl_maps[q - ck_maps.size()];
+        float* base = ck ? ckpt((long long)q) : slot((long long)(q - ck_maps.size()));
+        std::memset(&m, 0, sizeof m);
+        rc = encode_map(c, &m.ld[0], base, DMRT_FP32, kPlanes, 6, c->R);
+        if (!rc) rc = encode_map(c, &m.ld[1], base, DMRT_FP32, kPlanes, 4, c->R);
+        if (rc) return rc;
+    }
     for (long long q = AL.C - 1; q >= 0; --q) {
         const long long start = q * K, end = std::min(start + K, N), len = end - start;
         for (long long t = 1; t < len; ++t) {  // s_{start + t} into slot t
@@ -1865,9 +1879,17 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
             RA.dst = slot(t);
             RA.nu_rows = ra_rows + (size_t)(t & 1) * c->p.ny;
             RA.prev_rows = ra_rows + (size_t)((t + 1) & 1) * c->p.ny;
-            CK(launch_overlapped(dmrt::step_direct_kernel, c->grid, dim3(dmrt::kDirectThreads), c->stream, RA,
-                                 c->sc),
-               "adjoint recompute launch");
+            if (tma_re) {
+                dmrt::TmaMaps& M = t == 1 ? ck_maps[(size_t)q] : sl_maps[(size_t)(t - 1)];
+                void* params[4] = {&M, &RA, &c->sc, &c->geo};
+                CK(launch_overlapped(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), c->tma_smem, c->stream,
+                                     params),
+                   "adjoint recompute launch");
+            } else {
+                CK(launch_overlapped(dmrt::step_direct_kernel, c->grid, dim3(dmrt::kDirectThreads), c->stream,
+                                     RA, c->sc),
+                   "adjoint recompute launch");
+            }
         }
         for (long long k = end; k > start; --k) {
             AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(k - 1 - start);

@@ -75,6 +75,21 @@ def test_adjoint_is_deterministic(D):
     assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
 
 
+@pytest.mark.parametrize("nx,ny", [(128, 128), (600, 40)])
+def test_adjoint_same_bits_with_either_step_kernel(D, nx, ny):
+    # The segment recompute runs the context's step kernel (direct, or TMA with
+    # load maps for every checkpoint and slot); both give the forward run's bits,
+    # so the gradients agree bit for bit.
+    cav = inputs.Cavity(nx, ny, 1e5, 0.01, noise_amp=1e-3, seed=7)
+    out = []
+    for kernel in (1, 2):
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=300, kernel=kernel)
+        out.append(sim.adjoint(300, 100))
+        sim.close()
+    (J1, d1, r1), (J2, d2, r2) = out
+    assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
+
+
 def test_adjoint_config_128_against_finite_differences(D):
     # 128 x 128, Ra 1e5, Pr 0.01, hot wall 0.5 + 0.01 N(0, 1), 10000 steps, J over the last 2000.
     cav = inputs.cavity_128_adjoint()
