@@ -84,7 +84,8 @@ extern "C" {
  * Default (1, 4, 2). FP16 / BF16 storage, rounding to nearest (default (2, 4, 2)):
  * (1,1,2) (1,2,2) (1,4,2) (1,4,3) (1,4,4) (2,2,2) (2,4,2) (2,4,3) (4,2,2) (4,4,2);
  * stochastic (default (4, 4, 2)): (1,1,2) (1,4,2) (2,2,2) (2,4,2) (4,2,2) (4,4,2);
- * with fewer rows than the default tile, (1, 1, 2). MIXED storage (default (2, 1, 2)), nearest:
+ * with fewer rows than the default tile, or one-row items at most 2 per SM,
+ * (1, 1, 2); 4-row items fewer than 4 per SM, 2-row items. MIXED storage (default (2, 1, 2)), nearest:
  * (1,1,2) (1,1,3) (1,1,4) (1,2,2) (1,2,3) (1,4,2) (2,1,2) (2,1,3) (2,1,4)
  * (2,2,2) (4,1,3) (4,1,4); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2)
  * (2,1,3) (2,2,2) (2,4,2) (4,1,3). */
