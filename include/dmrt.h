@@ -316,9 +316,10 @@ void dmrt_destroy(dmrt_ctx* c);
  * theta_w(j) (which enters Eq. 45 and the Nusselt stencil) and to Ra (which
  * enters through the buoyancy scale of Eq. 27), by a hand-written reverse
  * (transposed collide-stream) kernel: the exact adjoint of the discrete
- * float32 step, with the gradients accumulated in float64. Memory: sqrt(N)
- * checkpoints of the state plus a sqrt(N)-step segment that is recomputed from
- * its checkpoint before being swept backwards.
+ * float32 step, with the gradients accumulated in float64 in a fixed order
+ * (the results repeat bit for bit). Memory: sqrt(N) checkpoints of the state
+ * plus a sqrt(N)-step segment that is recomputed from its checkpoint, by the
+ * context's own step kernel, before being swept backwards.
  *
  * dmrt_adjoint starts from the context's current state and wall profiles,
  * advances the context by nsteps (its state, step count and Nusselt ring are
