@@ -299,6 +299,15 @@ typedef struct {
 } dmrt_launch;
 int dmrt_get_launch(const dmrt_ctx* c, dmrt_launch* out);
 
+/* The kernel and tile (nodes per thread, rows, stages) that dmrt_create would
+ * choose for parameters p on a GPU with sms streaming multiprocessors: host
+ * logic only, no device call (the rules are listed at DMRT_KERNEL_AUTO and the
+ * storage modes' tile lists). The tile is 0, 0, 0 for the direct kernel. Errors
+ * as dmrt_derive; DMRT_E_ARG for a NULL pointer, sms < 1, or the direct kernel
+ * asked for with 16-bit or mixed storage. */
+int dmrt_choose_launch(const dmrt_params* p, int32_t sms, int32_t* kernel, int32_t* npt, int32_t* rows,
+                       int32_t* stages);
+
 /* Derived constants of a context. */
 int dmrt_get_consts(const dmrt_ctx* c, dmrt_consts* out);
 

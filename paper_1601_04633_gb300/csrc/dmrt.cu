@@ -397,9 +397,10 @@ int encode_map(dmrt_ctx* c, CUtensorMap* m, void* base, int storage, int nplanes
     return DMRT_OK;
 }
 
-// Resolve the kernel variant and prepare its launch configuration.
-int setup_kernel(dmrt_ctx* c) {
-    const dmrt_params& p = c->p;
+// The kernel and tile that parameters p run with on a GPU of `sms` SMs (host
+// logic only; AUTO resolves to DIRECT or TMA). Measured choices are noted at
+// each rule.
+void choose_launch(const dmrt_params& p, int sms, int* kernel, int* npt_out, int* R_out, int* S_out) {
     int want = p.kernel;
     int dn, dr, ds;
     default_tile(p.storage, p.rounding, &dn, &dr, &ds);
@@ -418,9 +419,6 @@ int setup_kernel(dmrt_ctx* c) {
         // number at most two per SM (64^2: 2.9 against 3.4 us per step with
         // 2-row items); else 2-row items while 4-row items would number fewer
         // than four per SM (512^2: 7.9 against 9.4 us with 4-row items).
-        int dev = 0, sms = 0;
-        CK(cudaGetDevice(&dev), "cudaGetDevice");
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
         const long long strips = (p.nx + dmrt::tma_strip(2) - 1) / dmrt::tma_strip(2);
         if (p.tma_npt <= 0 && p.tma_stages <= 0 && strips * p.ny <= 2LL * sms) {
             R = 1;
@@ -439,9 +437,6 @@ int setup_kernel(dmrt_ctx* c) {
             // while the one-row items number at most four per SM (one step of a
             // 64^2 cavity 2.7 us against 4.9 us with the direct kernel; 256^2
             // 4.2 against 4.8 us; the direct kernel from about 384^2).
-            int dev = 0, sms = 0;
-            CK(cudaGetDevice(&dev), "cudaGetDevice");
-            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
             const long long rows1 = (long long)((p.nx + dmrt::tma_strip(4) - 1) / dmrt::tma_strip(4)) * p.ny;
             if (rows1 <= 4LL * sms) {
                 want = DMRT_KERNEL_TMA;
@@ -451,6 +446,20 @@ int setup_kernel(dmrt_ctx* c) {
             }
         }
     }
+    *kernel = want;
+    *npt_out = npt;
+    *R_out = R;
+    *S_out = S;
+}
+
+// Resolve the kernel variant and prepare its launch configuration.
+int setup_kernel(dmrt_ctx* c) {
+    const dmrt_params& p = c->p;
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev), "cudaGetDevice");
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    int want, npt, R, S;
+    choose_launch(p, sms, &want, &npt, &R, &S);
     if (want == DMRT_KERNEL_DIRECT && p.storage != DMRT_FP32) {
         set_err(c, "the direct kernel stores float32 only; 16-bit and mixed storage run the TMA kernel");
         return DMRT_E_ARG;
@@ -463,9 +472,6 @@ int setup_kernel(dmrt_ctx* c) {
     if (want != DMRT_KERNEL_TMA) {
         // A direct grid of fewer blocks than two per SM gets one more row of
         // blocks, whose first block only sums the previous step's Nusselt rows.
-        int dev = 0, sms = 0;
-        CK(cudaGetDevice(&dev), "cudaGetDevice");
-        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
         if ((long long)c->grid.x * c->grid.y < 2LL * sms) c->grid.y += 1;
         return DMRT_OK;
     }
@@ -493,9 +499,7 @@ int setup_kernel(dmrt_ctx* c) {
     }
     CK(cudaFuncSetAttribute(c->tma_func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->tma_smem),
        "set TMA kernel shared memory");
-    int dev = 0, sms = 0, per_sm = 0;
-    CK(cudaGetDevice(&dev), "cudaGetDevice");
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
+    int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, c->tma_func, c->tma_block, c->tma_smem),
        "occupancy");
     if (per_sm < 1) {
@@ -881,6 +885,27 @@ static int build_graph(dmrt_ctx* c, int from) {
 static int finalize_nu(dmrt_ctx* c) {
     dmrt::nu_finalize_kernel<<<1, 256, 0, c->stream>>>(step_args(c, c->cur));
     CK(cudaGetLastError(), "step launch");
+    return DMRT_OK;
+}
+
+int dmrt_choose_launch(const dmrt_params* p, int32_t sms, int32_t* kernel, int32_t* npt, int32_t* rows,
+                       int32_t* stages) {
+    if (!p || sms < 1 || !kernel || !npt || !rows || !stages) {
+        set_err(nullptr, "dmrt_choose_launch: NULL argument or sms < 1");
+        return DMRT_E_ARG;
+    }
+    int rc = validate(p, nullptr);
+    if (rc) return rc;
+    int k, n, r, st;
+    choose_launch(*p, sms, &k, &n, &r, &st);
+    if (k == DMRT_KERNEL_DIRECT && p->storage != DMRT_FP32) {
+        set_err(nullptr, "the direct kernel stores float32 only; 16-bit and mixed storage run the TMA kernel");
+        return DMRT_E_ARG;
+    }
+    *kernel = k;
+    *npt = k == DMRT_KERNEL_TMA ? n : 0;
+    *rows = k == DMRT_KERNEL_TMA ? r : 0;
+    *stages = k == DMRT_KERNEL_TMA ? st : 0;
     return DMRT_OK;
 }
 

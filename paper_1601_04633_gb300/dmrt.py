@@ -113,6 +113,7 @@ SIGNATURES = {
     "dmrt_nusselt_flux": (ctypes.c_int, [_VP, _DP, _DP]),
     "dmrt_get_consts": (ctypes.c_int, [_VP, ctypes.POINTER(Consts)]),
     "dmrt_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
+    "dmrt_choose_launch": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
     "dmrt_get_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_set_state": (ctypes.c_int, [_VP, _FP]),
     "dmrt_save": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
@@ -252,6 +253,14 @@ def dmrt_get_launch(h) -> Launch:
     k = Launch()
     _check(load().dmrt_get_launch(h, ctypes.byref(k)), h)
     return k
+
+
+def dmrt_choose_launch(p: Params, sms: int) -> tuple:
+    """(kernel, nodes per thread, rows, stages) that parameters p run with on a
+    GPU with `sms` SMs (host logic; the tile is 0, 0, 0 for the direct kernel)."""
+    out = [ctypes.c_int32() for _ in range(4)]
+    _check(load().dmrt_choose_launch(ctypes.byref(p), sms, *[ctypes.byref(x) for x in out]), None)
+    return tuple(x.value for x in out)
 
 
 def dmrt_get_state(h, nx: int, ny: int) -> np.ndarray:
