@@ -65,9 +65,15 @@ extern "C" {
  * are kept on average; the random bits come from a per-node, per-step hash
  * (deterministic: a run repeats bit for bit), 13 per value for float16 and 16
  * for bfloat16, consumed by the GPU's stochastically rounding conversion
- * instruction. Float32 storage rounds nothing. */
+ * instruction. Float32 storage rounds nothing. AUTO (the default of
+ * dmrt_default_params): STOCHASTIC for FP16, BF16 and MIXED storage, nothing
+ * for FP32. Rounding to nearest loses the increments below half a unit in the
+ * last place on every step; over long runs that biases the hot-wall Nusselt
+ * number by more than 1e-3 (mixed storage: -3.1e-3 over 1e6 steps of the
+ * 256^2, Ra 1e5 cavity), which stochastic rounding avoids. */
 #define DMRT_ROUND_NEAREST 0
 #define DMRT_ROUND_STOCHASTIC 1
+#define DMRT_ROUND_AUTO 2
 
 /* Step kernel variants. All compute the same step; they differ only in how
  * the populations reach the registers. DIRECT: 128-bit loads straight from
@@ -119,7 +125,8 @@ typedef struct {
     int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default) */
     int32_t tma_npt;    /* TMA kernel: nodes per thread, 4, 2 or 1 (0 = default) */
     int32_t rounding;   /* 16-bit stores (all populations for FP16 / BF16, the flow
-                           populations for MIXED): DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC */
+                           populations for MIXED): DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC
+                           or DMRT_ROUND_AUTO (stochastic unless the storage is FP32) */
 } dmrt_params;
 
 /* Constants derived from dmrt_params (Eqs. 9, 31-32, 38-40, 43, 45). */
@@ -138,7 +145,8 @@ typedef struct {
 typedef struct dmrt_ctx dmrt_ctx;
 
 /* Fill *p with defaults: 64x64, Ra 1e4, Pr 0.01, alpha 0.1, walls +-0.5,
- * theta_ref 0, theta_init 0, fixed-temperature side walls, FP32, ring 2^20. */
+ * theta_ref 0, theta_init 0, fixed-temperature side walls, FP32, ring 2^20,
+ * rounding DMRT_ROUND_AUTO. */
 void dmrt_default_params(dmrt_params* p);
 
 /* Validate *p and derive the model constants (host only, no GPU needed).
@@ -164,7 +172,12 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
  * pull-stream f and g with the walls, moments, D2Q9 MRT collision (Eq. 28),
  * buoyancy force (Eq. 26), D2Q5 MRT collision (Eq. 36), store, and the
  * hot-wall Nusselt number of the pre-collision temperature (Eqs. 18-19)
- * appended to the ring. Does not synchronise. */
+ * appended to the ring. Does not synchronise, except to poll for divergence:
+ * each time the context's step count passes a multiple of 65536, it waits for
+ * the steps enqueued so far and reads the device error word; if a step saw a
+ * non-finite value it returns DMRT_E_DIVERGED (DMRT_E_TIMEOUT for an expired
+ * wait) without enqueueing the remaining steps (dmrt_steps_done tells how
+ * many were taken). */
 int dmrt_step(dmrt_ctx* c, int64_t nsteps);
 
 /* Synchronise the stream and report DMRT_E_DIVERGED if any step so far saw a
@@ -204,6 +217,23 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold);
  * matches to the discretisation level otherwise. Host outputs, both nullable:
  * nu_mean (mean over rows), nu_local [ny]. Synchronises. */
 int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local);
+
+/* Heat content and wall heat input of the current state, summed in float64 on
+ * the GPU in a fixed order (the same bits for the same state), host outputs,
+ * both nullable:
+ *   theta_sum: sum over all nodes of theta = sum_i g*_i (Eq. 41; the thermal
+ *              collision conserves theta, so this is the heat content of the
+ *              current time level);
+ *   wall_in:   the heat the next streaming brings in across the side walls:
+ *              sum over rows of (2 sqrt(3) alpha theta_w(j) - 2 g*_4(0, j)) for a
+ *              fixed-temperature left wall (anti-bounce-back, Eq. 45, returns
+ *              2 sqrt(3) alpha theta_w - g*_4 and the wall link removes g*_4) plus
+ *              the same with theta_c(j) and g*_2(nx-1, j) for a fixed right wall
+ *              (paper numbering: g_2 moves in +x, g_4 in -x); bounce-back walls
+ *              (Eq. 44, the top and bottom ones always) carry no heat.
+ * Hence the next step's theta_sum equals theta_sum + wall_in up to float32
+ * rounding. Synchronises. */
+int dmrt_energy(dmrt_ctx* c, double* theta_sum, double* wall_in);
 
 /* Post-collision population state at the current time level as a dense host
  * float32 array [14][ny][nx]: planes f_1..f_9 (Eq. 23 order; f stored shifted
@@ -270,13 +300,15 @@ int dmrt_probe_bounded_wait(int64_t limit_ns, void* stream, int64_t* waited_ns);
  *   src, dst:   distinct 16-byte aligned device buffers, each 14 * ny * pitch
  *               floats, pitch = nx rounded up to a multiple of 128: the
  *               post-collision populations at time t (read) and t + 1 (written),
- *               14 planes [ny][pitch] in the order (paper numbering)
- *               f1 f2 f4 g1 g2 g4 f3 f6 f7 g3 f5 f8 f9 g5. Padding columns are
- *               ignored on input.
+ *               14 planes [ny][pitch]. The planes are those of dmrt_set_state
+ *               (host order f_1..f_9, g_1..g_5, numbered 1..14), arranged on the
+ *               device as host planes 1 2 4 10 11 13 3 6 7 12 5 8 9 14. Padding
+ *               columns are ignored on input.
  *   theta_hot, theta_cold: device float arrays [ny] of wall temperatures, or NULL
  *               for the constant theta_hot / theta_cold of p.
  *   nu_mean:    device pointer to one double that receives the step's mean
- *               hot-wall Nusselt number (Eqs. 18-19), or NULL.
+ *               hot-wall Nusselt number (the value dmrt_nusselt reports as
+ *               nu_mean after the same step), or NULL.
  *   stream:     cudaStream_t as void*; the call only enqueues work on it.
  *
  * The first call on a device looks up the array's device address (host code

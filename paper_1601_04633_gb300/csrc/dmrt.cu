@@ -17,6 +17,7 @@
 
 #include "dmrt.h"
 #include "adjoint.cuh"
+#include "step_consts.h"
 #include "step_direct.cuh"
 #include "step_tma.cuh"
 #include "step_tma_batch.cuh"
@@ -44,7 +45,18 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 // Bytes per stored flow (f) and thermal (g) population.
 int f_bytes(int storage) { return storage == DMRT_FP32 ? 4 : 2; }
 int g_bytes(int storage) { return storage == DMRT_FP32 || storage == DMRT_MIXED ? 4 : 2; }
-bool g_16bit(int storage) { return storage == DMRT_FP16 || storage == DMRT_BF16; }
+
+// DMRT_ROUND_AUTO resolved: stochastic rounding for 16-bit and mixed storage,
+// nearest (nothing is rounded) for float32.
+int resolved_rounding(const dmrt_params& p) {
+    if (p.rounding != DMRT_ROUND_AUTO) return p.rounding;
+    return p.storage == DMRT_FP32 ? DMRT_ROUND_NEAREST : DMRT_ROUND_STOCHASTIC;
+}
+dmrt_params resolved(const dmrt_params& p) {
+    dmrt_params q = p;
+    q.rounding = resolved_rounding(p);
+    return q;
+}
 
 Layout make_layout(const dmrt_params& p) {
     Layout L;
@@ -62,6 +74,9 @@ Layout make_layout(const dmrt_params& p) {
     L.total = o;
     return L;
 }
+
+// dmrt_step reads the device error word once per this many steps.
+constexpr long long kPollSteps = 1LL << 16;
 
 // Scalars kept on the device (one 256-byte block).
 struct Misc {
@@ -101,6 +116,7 @@ struct dmrt_ctx {
     cudaGraphExec_t graph[2];
     int graph_len;
     long long nu_floor;  // ring values of steps before this one are unavailable (after a load)
+    long long next_poll; // dmrt_step reads the error word once the step count reaches this
     char err[256];
 };
 
@@ -291,6 +307,69 @@ __global__ void nu_flux_kernel(const unsigned char* __restrict__ S, const float*
     out[j] = scale * (abb * (double)hot[j] - g_sign * 2.0 * g3);
 }
 
+// Heat content of each row (sum of theta = sum_i g*_i over the row, Eq. 41) and
+// the heat the next streaming brings in across the row's fixed-temperature wall
+// links (Eq. 45: anti-bounce-back returns abb theta_w - g* and the wall link
+// takes g* out, so the row gains abb theta_w - 2 g*; bounce-back, Eq. 44,
+// returns what leaves). One warp per row, float64: lane l adds nodes l, l + 32,
+// ... in order, the warp combines the lanes by a butterfly (a fixed order).
+template <typename L>
+__global__ void energy_rows_kernel(const unsigned char* __restrict__ S, const float* __restrict__ hot,
+                                   const float* __restrict__ cold, double* __restrict__ row_theta,
+                                   double* __restrict__ row_in, int nx, int ny, int pitch, long long plane,
+                                   double abb_l, double sign_l, double abb_r, double sign_r, double sh0,
+                                   double sh1) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= ny) return;  // warp-uniform
+    const auto* Sg = g_base<L>(S, plane);
+    const size_t row = (size_t)j * pitch;
+    double acc = 0.0;
+    for (int i = lane; i < nx; i += 32) {
+        double th = 0.0;
+        for (int k = 0; k < 5; ++k) th += (double)elem_to_f(Sg[L::pg(k) * plane + row + i]) + (k == 0 ? sh0 : sh1);
+        acc += th;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+        // West-moving g (0-based direction 3) leaves through the left wall,
+        // east-moving g (direction 1) through the right wall.
+        const double gw = (double)elem_to_f(Sg[L::pg(3) * plane + row]) + sh1;
+        const double ge = (double)elem_to_f(Sg[L::pg(1) * plane + row + nx - 1]) + sh1;
+        row_theta[j] = acc;
+        row_in[j] = (abb_l * (double)hot[j] - sign_l * 2.0 * gw) + (abb_r * (double)cold[j] - sign_r * 2.0 * ge);
+    }
+}
+
+// Sums of n values of x and of y, each in a fixed order (256 partial sums over
+// the indices congruent mod 256, added in index order, then combined in a fixed
+// tree); one block of 256 threads. out[0] = sum x, out[1] = sum y.
+__global__ void sum2_fixed_kernel(const double* __restrict__ x, const double* __restrict__ y, int n,
+                                  double* __restrict__ out) {
+    __shared__ double px[256], py[256];
+    const int t = threadIdx.x;
+    double ax = 0.0, ay = 0.0;
+    for (int i = t; i < n; i += 256) {
+        ax += x[i];
+        ay += y[i];
+    }
+    px[t] = ax;
+    py[t] = ay;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w) {
+            px[t] += px[t + w];
+            py[t] += py[t + w];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        out[0] = px[0];
+        out[1] = py[0];
+    }
+}
+
 // Call fn with a value of the element type of a one-type storage (float, __half, __nv_bfloat16).
 template <typename Fn>
 void with_elem(int storage, Fn&& fn) {
@@ -400,7 +479,8 @@ int encode_map(dmrt_ctx* c, CUtensorMap* m, void* base, int storage, int nplanes
 // The kernel and tile that parameters p run with on a GPU of `sms` SMs (host
 // logic only; AUTO resolves to DIRECT or TMA). Measured choices are noted at
 // each rule.
-void choose_launch(const dmrt_params& p, int sms, int* kernel, int* npt_out, int* R_out, int* S_out) {
+void choose_launch(const dmrt_params& p_in, int sms, int* kernel, int* npt_out, int* R_out, int* S_out) {
+    const dmrt_params p = resolved(p_in);
     int want = p.kernel;
     int dn, dr, ds;
     default_tile(p.storage, p.rounding, &dn, &dr, &ds);
@@ -561,8 +641,9 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "storage must be DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (got %d)", p->storage);
         return DMRT_E_ARG;
     }
-    if (p->rounding != DMRT_ROUND_NEAREST && p->rounding != DMRT_ROUND_STOCHASTIC) {
-        set_err(c, "rounding must be DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC");
+    if (p->rounding != DMRT_ROUND_NEAREST && p->rounding != DMRT_ROUND_STOCHASTIC &&
+        p->rounding != DMRT_ROUND_AUTO) {
+        set_err(c, "rounding must be DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC or DMRT_ROUND_AUTO");
         return DMRT_E_ARG;
     }
     if (p->rounding == DMRT_ROUND_STOCHASTIC && p->storage == DMRT_FP32) {
@@ -610,7 +691,7 @@ void dmrt_default_params(dmrt_params* p) {
     p->tma_rows = 0;
     p->tma_stages = 0;
     p->tma_npt = 0;
-    p->rounding = DMRT_ROUND_NEAREST;
+    p->rounding = DMRT_ROUND_AUTO;
 }
 
 int dmrt_derive(const dmrt_params* p, dmrt_consts* out) {
@@ -680,7 +761,7 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
         set_err(nullptr, "out of host memory");
         return DMRT_E_SPACE;
     }
-    c->p = *p;
+    c->p = resolved(*p);
     c->k = k;
     c->L = L;
     c->ws = static_cast<char*>(workspace);
@@ -690,29 +771,12 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     c->graph[0] = c->graph[1] = nullptr;
     c->graph_len = 64;
     c->nu_floor = 0;
+    c->next_poll = kPollSteps;
     c->err[0] = 0;
 
-    dmrt::StepConsts& s = c->sc;
-    s.se36 = (float)(k.s_e / 36.0);
-    s.snu4 = (float)(k.s_nu / 4.0);
-    s.sq12 = (float)(k.s_q / 12.0);
-    s.seps36 = (float)(k.s_eps / 36.0);
-    s.sk2 = (float)(k.sig_k / 2.0);
-    s.se20 = (float)(k.sig_e / 20.0);
-    s.snu4t = (float)(k.sig_nu / 4.0);
-    s.a = (float)k.a;
-    s.gbeta = (float)k.gbeta;
-    s.theta_ref = (float)p->theta_ref;
-    s.abb = (float)k.abb;
-    s.left_fixed = p->left_wall == DMRT_WALL_FIXED;
-    s.right_fixed = p->right_wall == DMRT_WALL_FIXED;
-    // 16-bit thermal storage keeps g_i - w_i theta_ref (w_0 = (1-a)/5, w_1..4 = (4+a)/20).
-    const double sh0 = g_16bit(p->storage) ? (1.0 - k.a) / 5.0 * p->theta_ref : 0.0;
-    const double sh1 = g_16bit(p->storage) ? (4.0 + k.a) / 20.0 * p->theta_ref : 0.0;
-    s.gsh0 = (float)sh0;
-    s.gsh1 = (float)sh1;
-    const double dT = p->theta_hot - p->theta_cold;
-    s.nu_scale = dT != 0.0 ? (double)p->ny / (3.0 * dT) : 0.0;
+    c->sc = dmrt::make_step_consts(*p, k);
+    const double sh0 = dmrt::thermal_shift0(*p, k);
+    const double sh1 = dmrt::thermal_shift1(*p, k);
 
     const int nxq = (p->nx + 3) / 4;
     int wx = 1;
@@ -909,9 +973,34 @@ int dmrt_choose_launch(const dmrt_params* p, int32_t sms, int32_t* kernel, int32
     return DMRT_OK;
 }
 
+// Reads the device error word (synchronises the stream): DMRT_E_TIMEOUT or
+// DMRT_E_DIVERGED when a bit is set, else DMRT_OK.
+static int poll_error(dmrt_ctx* c) {
+    unsigned err = 0;
+    CK(cudaMemcpyAsync(&err, &misc(c)->err, sizeof err, cudaMemcpyDeviceToHost, c->stream), "read error flag");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (err & dmrt::kErrTimeout) {
+        set_err(c, "a bounded device-side wait expired after %lld steps", c->t);
+        return DMRT_E_TIMEOUT;
+    }
+    if (err & dmrt::kErrNonFinite) {
+        set_err(c, "non-finite density or temperature after %lld steps", c->t);
+        return DMRT_E_DIVERGED;
+    }
+    return DMRT_OK;
+}
+
 int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
     while (nsteps > 0) {
+        if (c->t >= c->next_poll) {
+            // Every kPollSteps steps: stop a run that has diverged (the steps
+            // enqueued so far complete; the ring holds their Nusselt numbers).
+            c->next_poll = c->t + kPollSteps;
+            int rc = finalize_nu(c);
+            if (!rc) rc = poll_error(c);
+            if (rc) return rc;
+        }
         if (nsteps >= c->graph_len) {
             if (!c->graph[c->cur]) {
                 int rc = build_graph(c, c->cur);
@@ -927,23 +1016,11 @@ int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
         }
     }
     return finalize_nu(c);
-    return DMRT_OK;
 }
 
 int dmrt_check(dmrt_ctx* c) {
     if (!c) return DMRT_E_ARG;
-    CK(cudaStreamSynchronize(c->stream), "synchronize");
-    unsigned err = 0;
-    CK(cudaMemcpy(&err, &misc(c)->err, sizeof err, cudaMemcpyDeviceToHost), "read error flag");
-    if (err & dmrt::kErrTimeout) {
-        set_err(c, "a bounded device-side wait expired after %lld steps", c->t);
-        return DMRT_E_TIMEOUT;
-    }
-    if (err & dmrt::kErrNonFinite) {
-        set_err(c, "non-finite density or temperature after %lld steps", c->t);
-        return DMRT_E_DIVERGED;
-    }
-    return DMRT_OK;
+    return poll_error(c);
 }
 
 int64_t dmrt_steps_done(const dmrt_ctx* c) { return c ? c->t : -1; }
@@ -971,6 +1048,32 @@ int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local) {
     for (double x : local) sum += x;  // rows in order
     if (nu_mean) *nu_mean = sum / (double)p.ny;
     if (nu_local) std::memcpy(nu_local, local.data(), local.size() * sizeof(double));
+    return DMRT_OK;
+}
+
+int dmrt_energy(dmrt_ctx* c, double* theta_sum, double* wall_in) {
+    if (!c) return DMRT_E_ARG;
+    const dmrt_params& p = c->p;
+    const bool lf = p.left_wall == DMRT_WALL_FIXED, rf = p.right_wall == DMRT_WALL_FIXED;
+    // Per-row values and the two sums staged in the idle population buffer (no allocation).
+    double* rows = reinterpret_cast<double*>(buf(c, 1 - c->cur));
+    double* sums = rows + 2 * (size_t)p.ny;
+    const int warps = 8;
+    with_layout(p.storage, [&](auto tag) {
+        using Lt = decltype(tag);
+        energy_rows_kernel<Lt><<<(p.ny + warps - 1) / warps, 32 * warps, 0, c->stream>>>(
+            reinterpret_cast<const unsigned char*>(buf(c, c->cur)), reinterpret_cast<const float*>(c->ws + c->L.off_hot),
+            reinterpret_cast<const float*>(c->ws + c->L.off_cold), rows, rows + p.ny, p.nx, p.ny, c->L.pitch,
+            c->L.plane, lf ? c->k.abb : 0.0, lf ? 1.0 : 0.0, rf ? c->k.abb : 0.0, rf ? 1.0 : 0.0,
+            (double)c->sc.gsh0, (double)c->sc.gsh1);
+    });
+    sum2_fixed_kernel<<<1, 256, 0, c->stream>>>(rows, rows + p.ny, p.ny, sums);
+    CK(cudaGetLastError(), "energy kernels");
+    double h[2];
+    CK(cudaMemcpyAsync(h, sums, sizeof h, cudaMemcpyDeviceToHost, c->stream), "copy energy");
+    CK(cudaStreamSynchronize(c->stream), "synchronize");
+    if (theta_sum) *theta_sum = h[0];
+    if (wall_in) *wall_in = h[1];
     return DMRT_OK;
 }
 
@@ -1318,6 +1421,7 @@ int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size) {
     m.err = h.err;
     CK(cudaMemcpy(misc(c), &m, sizeof m, cudaMemcpyHostToDevice), "write scalars");
     c->t = h.t;
+    c->next_poll = h.t + kPollSteps;
     c->nu_floor = h.recorded - keep;
     return DMRT_OK;
 }
@@ -1409,7 +1513,7 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
             set_err(nullptr, "batched sweep: cavity %d: every cavity needs the same storage", i);
             return DMRT_E_ARG;
         }
-        if (arr[i].rounding != arr[0].rounding) {
+        if (resolved_rounding(arr[i]) != resolved_rounding(arr[0])) {
             set_err(nullptr, "batched sweep: cavity %d: every cavity needs the same rounding", i);
             return DMRT_E_ARG;
         }
@@ -1530,7 +1634,8 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     const void* func = nullptr;
     const int storage = arr[0].storage;
     for (int i = 0; i < nv; ++i)
-        if (vars[i].storage == storage && vars[i].rounding == arr[0].rounding && vars[i].npt == npt && vars[i].R == R &&
+        if (vars[i].storage == storage && vars[i].rounding == resolved_rounding(arr[0]) && vars[i].npt == npt &&
+            vars[i].R == R &&
             vars[i].S == S)
             func = vars[i].func;
     if (!func) {

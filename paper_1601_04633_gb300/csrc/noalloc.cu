@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "dmrt.h"
+#include "step_consts.h"
 #include "step_direct.cuh"
 
 // Defined in dmrt.cu: the message dmrt_last_error(NULL) returns.
@@ -114,22 +115,7 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     noalloc_fill<<<(p->ny + 255) / 256, 256, 0, s>>>(hot, cold, theta_hot, theta_cold,
                                                      (float)p->theta_hot, (float)p->theta_cold, p->ny);
 
-    dmrt::StepConsts sc;
-    sc.se36 = (float)(k.s_e / 36.0);
-    sc.snu4 = (float)(k.s_nu / 4.0);
-    sc.sq12 = (float)(k.s_q / 12.0);
-    sc.seps36 = (float)(k.s_eps / 36.0);
-    sc.sk2 = (float)(k.sig_k / 2.0);
-    sc.se20 = (float)(k.sig_e / 20.0);
-    sc.snu4t = (float)(k.sig_nu / 4.0);
-    sc.a = (float)k.a;
-    sc.gbeta = (float)k.gbeta;
-    sc.theta_ref = (float)p->theta_ref;
-    sc.abb = (float)k.abb;
-    sc.left_fixed = p->left_wall == DMRT_WALL_FIXED;
-    sc.right_fixed = p->right_wall == DMRT_WALL_FIXED;
-    const double dT = p->theta_hot - p->theta_cold;
-    sc.nu_scale = dT != 0.0 ? (double)p->ny / (3.0 * dT) : 0.0;
+    const dmrt::StepConsts sc = dmrt::make_step_consts(*p, k);
 
     const int pitch = ((p->nx + 127) / 128) * 128;
     dmrt::StepArgs A;

@@ -624,9 +624,11 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     grid_dep_wait();
     grid_dep_launch();
     // After an expired wait in an earlier launch the state is already invalid:
-    // return at once instead of waiting again.
-    if (*reinterpret_cast<volatile unsigned*>(A.err) & kErrTimeout) return;
-    __syncthreads();
+    // return at once instead of waiting again. One thread reads the word and
+    // the barrier hands its answer to the whole block, so either every thread
+    // of the block returns here or none does (the barrier also publishes the
+    // mbarrier initialisation).
+    if (__syncthreads_or(tid == 0 && (*reinterpret_cast<volatile unsigned*>(A.err) & kErrTimeout))) return;
     // The previous step's mean Nusselt number: block 0 before its first item, or
     // the extra block.
     if (nu_extra ? (int)blockIdx.x == n_items : blockIdx.x == 0) nu_finish_prev(A, true);

@@ -66,9 +66,10 @@ __global__ void __launch_bounds__(R * (256 / NPT))
     }
     grid_dep_wait();
     grid_dep_launch();
-    if (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout) return;
+    // A block-uniform decision (one reader, handed out by the barrier, which
+    // also publishes the mbarrier initialisation): every thread returns or none.
+    if (__syncthreads_or(tid == 0 && (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout))) return;
     if (blockIdx.x == 0 && tid == 0) ctr[1 - parity] = 0u;
-    __syncthreads();
     // The previous step's mean Nusselt number of each cavity: blocks 0, 1, ...
     // before their first item.
     for (int cc = blockIdx.x; cc < n_cav; cc += gridDim.x) nu_finish_prev(cav[cc].args[parity], true);

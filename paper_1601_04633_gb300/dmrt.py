@@ -30,7 +30,7 @@ DMRT_E_STATE = -7
 DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED = 0, 1, 2, 3
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
 DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA = 0, 1, 2
-DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC = 0, 1
+DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC, DMRT_ROUND_AUTO = 0, 1, 2
 DMRT_NOALLOC_MAX_NY = 8192
 # Device plane order of the population buffers: entry d is the index, in the host
 # order f1..f9, g1..g5 (paper numbering), of device plane d.
@@ -111,6 +111,7 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int64)]),
     "dmrt_set_wall_profiles": (ctypes.c_int, [_VP, _DP, _DP]),
     "dmrt_nusselt_flux": (ctypes.c_int, [_VP, _DP, _DP]),
+    "dmrt_energy": (ctypes.c_int, [_VP, _DP, _DP]),
     "dmrt_get_consts": (ctypes.c_int, [_VP, ctypes.POINTER(Consts)]),
     "dmrt_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
     "dmrt_choose_launch": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32] + [ctypes.POINTER(ctypes.c_int32)] * 4),
@@ -243,6 +244,15 @@ def dmrt_set_wall_profiles(h, hot=None, cold=None):
     _check(load().dmrt_set_wall_profiles(h, _dptr(hp), _dptr(cp)), h)
 
 
+def dmrt_energy(h) -> tuple:
+    """(sum of theta over the cavity, heat the next streaming brings in across
+    the fixed-temperature walls), float64 sums taken on the GPU."""
+    th = ctypes.c_double()
+    win = ctypes.c_double()
+    _check(load().dmrt_energy(h, ctypes.byref(th), ctypes.byref(win)), h)
+    return th.value, win.value
+
+
 def dmrt_get_consts(h) -> Consts:
     k = Consts()
     _check(load().dmrt_get_consts(h, ctypes.byref(k)), h)
@@ -306,7 +316,7 @@ def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.
                 theta_ref=None, theta_init=0.0, left_wall=DMRT_WALL_FIXED,
                 right_wall=DMRT_WALL_FIXED, storage=DMRT_FP32, nu_capacity=1 << 20,
                 kernel=DMRT_KERNEL_AUTO, tma_rows=0, tma_stages=0, tma_npt=0,
-                rounding=DMRT_ROUND_NEAREST) -> Params:
+                rounding=DMRT_ROUND_AUTO) -> Params:
     p = dmrt_default_params()
     p.nx, p.ny, p.Ra, p.Pr, p.alpha, p.Ma = int(nx), int(ny), float(Ra), float(Pr), float(alpha), float(Ma)
     p.theta_hot, p.theta_cold = float(theta_hot), float(theta_cold)
@@ -429,6 +439,10 @@ class Cavity2D:
     def nusselt(self, series_cap: int = 0):
         return dmrt_nusselt(self.h, self.ny, series_cap)
 
+    def energy(self):
+        """(sum of theta, wall heat input of the next step) of the current state."""
+        return dmrt_energy(self.h)
+
     def nusselt_flux(self):
         """(mean, per-row array) of the link-flux Nusselt estimator of the current state."""
         local = np.zeros(self.ny)
@@ -503,8 +517,9 @@ class Batch:
 
     @classmethod
     def from_inputs(cls, cavities, opts=None, nu_capacity=1 << 16, storage=DMRT_FP32,
-                    rounding=DMRT_ROUND_NEAREST, **kw):
-        """Every cavity stored alike: DMRT_FP32, or DMRT_MIXED with either rounding."""
+                    rounding=DMRT_ROUND_AUTO, **kw):
+        """Every cavity stored alike: DMRT_FP32, or DMRT_MIXED with either rounding
+        (AUTO: stochastic for mixed storage)."""
         ps = [make_params(c.nx, c.ny, c.Ra, c.Pr, c.alpha, theta_hot=c.theta_hot, theta_cold=c.theta_cold,
                           theta_init=c.theta_init, nu_capacity=nu_capacity, storage=storage, rounding=rounding)
               for c in cavities]

@@ -44,6 +44,20 @@ def test_default_params(D):
     assert (p.nx, p.ny, p.Ra, p.Pr, p.alpha) == (64, 64, 1e4, 0.01, 0.1)
     assert (p.theta_hot, p.theta_cold, p.theta_ref) == (0.5, -0.5, 0.0)
     assert p.storage == D.DMRT_FP32 and p.nu_capacity == 1 << 20
+    assert p.rounding == D.DMRT_ROUND_AUTO
+
+
+def test_auto_rounding_resolves_per_storage(D):
+    # AUTO means stochastic rounding for 16-bit and mixed storage (the rounding
+    # that keeps the long-run Nusselt number within 1e-3) and nothing for float32:
+    # the launch chosen for AUTO is the one chosen for the resolved mode.
+    for storage, resolved in ((D.DMRT_FP32, D.DMRT_ROUND_NEAREST), (D.DMRT_FP16, D.DMRT_ROUND_STOCHASTIC),
+                              (D.DMRT_BF16, D.DMRT_ROUND_STOCHASTIC), (D.DMRT_MIXED, D.DMRT_ROUND_STOCHASTIC)):
+        for n in (64, 1000, 4096):
+            auto = D.make_params(n, n, 1e5, 0.01, storage=storage, rounding=D.DMRT_ROUND_AUTO)
+            expl = D.make_params(n, n, 1e5, 0.01, storage=storage, rounding=resolved)
+            D.dmrt_derive(auto)
+            assert D.dmrt_choose_launch(auto, 152) == D.dmrt_choose_launch(expl, 152)
 
 
 @pytest.mark.parametrize("nx,ny,Ra,Pr,alpha", [(64, 64, 1e4, 0.01, 0.1), (256, 256, 1e5, 0.005, 0.1),
@@ -72,7 +86,8 @@ def test_alpha_from_mach(D):
     (dict(nx=1), -1), (dict(ny=40000), -1), (dict(Pr=0.0), -1), (dict(Ra=-1.0), -1),
     (dict(alpha=0.0, Ma=0.0), -1), (dict(alpha=0.2), -2), (dict(theta_hot=0.0, theta_cold=0.0), -1),
     (dict(storage=7), -1), (dict(nu_capacity=0), -1), (dict(left_wall=3), -1),
-    (dict(rounding=2), -1), (dict(rounding=1), -1),  # stochastic rounding needs 16-bit storage
+    (dict(rounding=3), -1), (dict(rounding=-1), -1),
+    (dict(rounding=1), -1),  # stochastic rounding needs 16-bit storage
     (dict(kernel=3), -1), (dict(kernel=-1), -1),
 ])
 def test_invalid_params_rejected(D, kw, code):

@@ -113,16 +113,57 @@ def test_parity_adjoint_config_shape(D):
 
 
 def test_energy_conserved_with_adiabatic_walls(D):
+    # All walls adiabatic (bounce-back, Eq. 44) and the collision conserving theta
+    # (Q_1 = 0, Eq. 38): the heat content stays constant up to float32 rounding,
+    # summed in float64 on the GPU by dmrt_energy, and no heat crosses a wall.
     cav = inputs.Cavity(100, 60, 1e5, 0.01, noise_amp=0.2, seed=22)
     p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, left_wall=D.DMRT_WALL_ADIABATIC,
                       right_wall=D.DMRT_WALL_ADIABATIC)
     sim = D.Cavity2D(p, theta0=cav.theta0())
-    th0 = sim.fields()[2].double().sum().item()
+    e0, w0 = sim.energy()
     sim.step(2000)
     sim.check()
-    th1 = sim.fields()[2].double().sum().item()
+    e1, w1 = sim.energy()
     sim.close()
-    assert abs(th1 - th0) <= 1e-6 * np.abs(cav.theta0()).sum()
+    assert w0 == 0.0 and w1 == 0.0
+    assert abs(e0 - cav.theta0().sum()) <= 1e-6 * np.abs(cav.theta0()).sum()  # float32 initial state
+    assert abs(e1 - e0) <= 1e-6 * np.abs(cav.theta0()).sum()
+
+
+@pytest.mark.parametrize("storage", [0, 1, 3], ids=["fp32", "fp16", "mixed"])
+@pytest.mark.parametrize("walls", [(0, 0), (0, 1), (1, 0)], ids=["fixed_fixed", "fixed_adiabatic", "adiabatic_fixed"])
+def test_energy_budget_with_fixed_temperature_walls(D, storage, walls):
+    # Over one step the heat content changes by exactly the wall heat input of
+    # the step before it (Eqs. 44-45), up to float32 rounding of each node's
+    # populations; both sums come from dmrt_energy and are checked against the
+    # same sums taken in numpy from the state that dmrt_get_state returns.
+    cav = inputs.Cavity(300, 70, 1e5, 0.01, noise_amp=1e-3, seed=23)
+    cav.theta_hot_profile = 0.5 + 0.05 * np.sin(np.linspace(0, 3, cav.ny))
+    sim = D.Cavity2D.from_inputs(cav, storage=storage, left_wall=walls[0], right_wall=walls[1])
+    sim.step(300)
+    st = sim.get_state().astype(np.float64)
+    e0, w0 = sim.energy()
+    k = sim.consts
+    sim.step(1)
+    sim.check()
+    e1, _ = sim.energy()
+    sim.close()
+    g = st[9:]
+    hot = cav.theta_hot_profile.astype(np.float32).astype(np.float64)
+    w_ref = 0.0
+    if walls[0] == 0:
+        w_ref += np.sum(k.abb * hot - 2.0 * g[3, :, 0])
+    if walls[1] == 0:
+        w_ref += np.sum(k.abb * cav.theta_cold - 2.0 * g[1, :, -1])
+    n = cav.nx * cav.ny
+    scale = np.abs(g).sum()
+    assert abs(e0 - g.sum()) <= 1e-12 * scale
+    assert abs(w0 - w_ref) <= 1e-6 * (abs(w_ref) + cav.ny)
+    u = {0: 2.0 ** -24, 1: 2.0 ** -11, 3: 2.0 ** -24}[storage]  # rounding unit of the stored g
+    tol = 10 * u * scale + 1e-6 * abs(w0)
+    assert abs((e1 - e0) - w0) <= tol, (e1 - e0, w0)
+    if storage == 0:
+        assert abs(w0) > 1e3 * tol  # the float32 budget is not vacuous
 
 
 def _random_state(nx, ny, seed):

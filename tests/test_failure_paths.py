@@ -3,7 +3,9 @@
 * A bounded device-side wait that nothing completes gives up after its limit
   and is reported (dmrt_probe_bounded_wait runs the step kernels' wait routine
   on an mbarrier nothing arrives on); the GPU and later steps are unaffected.
-* A non-finite state is reported as DMRT_E_DIVERGED (tests/test_cuda_parity.py).
+* A non-finite state is reported as DMRT_E_DIVERGED (tests/test_cuda_parity.py),
+  and a long dmrt_step call stops at its next poll of the error word instead
+  of stepping a diverged state to the end.
 """
 import ctypes
 
@@ -50,3 +52,25 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(D):
     sim.close()
     ref.close()
     assert L.dmrt_probe_bounded_wait(10, ctypes.c_void_p(stream), None) == D.DMRT_E_ARG
+
+
+def test_long_step_call_stops_at_the_divergence_poll(D):
+    # A NaN temperature in one node: dmrt_step polls the error word each time the
+    # step count passes a multiple of 65536 and returns DMRT_E_DIVERGED there.
+    cav = inputs.Cavity(16, 16, 1e4, 0.01, noise_amp=1e-3, seed=6)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=64)
+    st = sim.get_state()
+    st[9, 5, 7] = np.nan
+    sim.set_state(st)
+    want = 3 * 65536 + 100
+    with pytest.raises(D.DmrtError) as ei:
+        sim.step(want)
+    assert ei.value.code == D.DMRT_E_DIVERGED
+    assert sim.steps_done == 65536
+    sim.close()
+    # A healthy run of the same length is not interrupted.
+    ok = D.Cavity2D.from_inputs(cav, nu_capacity=64)
+    ok.step(want)
+    ok.check()
+    assert ok.steps_done == want
+    ok.close()

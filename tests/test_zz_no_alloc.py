@@ -6,8 +6,10 @@ real-time loop in which an allocation would synchronise the device, a plug-in
 host that forbids allocation in its callbacks). The entry point keeps its
 scratch in a static device array inside the library; these tests call it
 through the C ABI and check two calls in a row against the regular entry
-points (dmrt_set_state + dmrt_step) with the tolerances of the parity tests.
-This file is collected last on purpose.
+points (dmrt_set_state + dmrt_step). Every step kernel of the library computes
+the same bits (the parity tests check that across kernels and tiles), so the
+states and the Nusselt numbers must be equal exactly, not only within the
+parity tolerances. This file is collected last on purpose.
 """
 import numpy as np
 import pytest
@@ -15,9 +17,6 @@ import pytest
 from paper_1601_04633_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
-
-FIELD_TOL = 1e-5
-NU_TOL = 1e-4
 
 
 @pytest.fixture(scope="module")
@@ -68,10 +67,18 @@ def _from_device_layout(D, dev, nx):
     return host
 
 
-def _close(a, b, tol):
-    for k in range(14):
-        scale = max(np.abs(b[k]).max(), 1e-30)
-        assert np.abs(a[k].astype(np.float64) - b[k]).max() <= tol * scale, f"plane {k}"
+def _regular_two_steps(D, cav, state0, hot, cold):
+    # The regular entry points: a context with its own workspace.
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=8)
+    D.dmrt_set_wall_profiles(sim.h, hot=None if hot is None else hot.astype(np.float64),
+                             cold=None if cold is None else cold.astype(np.float64))
+    sim.set_state(state0)
+    sim.step(1)
+    ref1, nu1 = sim.get_state(), sim.nusselt()[0]
+    sim.step(1)
+    ref2, nu2 = sim.get_state(), sim.nusselt()[0]
+    sim.close()
+    return ref1, nu1, ref2, nu2
 
 
 @pytest.mark.parametrize("nx,ny", [(300, 200), (67, 45)])
@@ -80,16 +87,7 @@ def test_noalloc_two_calls_match_regular_path(env, nx, ny):
     cav = inputs.Cavity(nx, ny, 1e5, 0.01, noise_amp=0.0)
     state0 = _random_state(nx, ny, seed=51)
     hot = (0.5 + 0.02 * np.sin(np.linspace(0.0, 3.0, ny))).astype(np.float32)
-
-    # Regular entry points: a context with its own workspace.
-    sim = D.Cavity2D.from_inputs(cav, nu_capacity=8)
-    D.dmrt_set_wall_profiles(sim.h, hot=hot.astype(np.float64))
-    sim.set_state(state0)
-    sim.step(1)
-    ref1, nu1 = sim.get_state(), sim.nusselt()[0]
-    sim.step(1)
-    ref2, nu2 = sim.get_state(), sim.nusselt()[0]
-    sim.close()
+    ref1, nu1, ref2, nu2 = _regular_two_steps(D, cav, state0, hot, None)
 
     # No-allocation entry point: caller-owned buffers, two calls in a row (ping-pong).
     p = D.make_params(nx, ny, cav.Ra, cav.Pr, cav.alpha)
@@ -105,10 +103,39 @@ def test_noalloc_two_calls_match_regular_path(env, nx, ny):
     out2 = _from_device_layout(D, a, nx)
     nus = nu.cpu().numpy()
 
-    _close(out1, ref1, FIELD_TOL)
-    _close(out2, ref2, FIELD_TOL)
-    assert abs(nus[0] - nu1) <= NU_TOL * abs(nu1)
-    assert abs(nus[1] - nu2) <= NU_TOL * abs(nu2)
+    assert np.array_equal(out1, ref1)
+    assert np.array_equal(out2, ref2)
+    assert nus[0] == nu1 and nus[1] == nu2
+
+
+def test_noalloc_cold_profile_no_output_and_changing_sizes(env):
+    # A cold-wall profile given as a device pointer and no Nusselt output (the
+    # mean goes to the array's internal sink), then calls on a taller and a
+    # shorter cavity in a row: the array keeps the previous call's contents, so
+    # each call must reset what its step reads.
+    torch, D = env
+    stream = torch.cuda.current_stream().cuda_stream
+    for nx, ny, want_nu in ((130, 90, False), (96, 400, True), (40, 24, True)):
+        cav = inputs.Cavity(nx, ny, 1e5, 0.01, noise_amp=0.0)
+        state0 = _random_state(nx, ny, seed=52 + ny)
+        cold = (-0.5 + 0.03 * np.cos(np.linspace(0.0, 2.0, ny))).astype(np.float32)
+        ref1, nu1, ref2, nu2 = _regular_two_steps(D, cav, state0, None, cold)
+        p = D.make_params(nx, ny, cav.Ra, cav.Pr, cav.alpha)
+        a = _to_device_layout(torch, D, state0)
+        b = torch.zeros_like(a)
+        cold_dev = torch.from_numpy(cold).cuda()
+        nu = torch.zeros(2, dtype=torch.float64, device="cuda")
+        out_ptr = (lambda k: nu.data_ptr() + 8 * k) if want_nu else (lambda k: 0)
+        D.dmrt_step_noalloc(p, a.data_ptr(), b.data_ptr(), out_ptr(0), stream, cold_ptr=cold_dev.data_ptr())
+        D.dmrt_step_noalloc(p, b.data_ptr(), a.data_ptr(), out_ptr(1), stream, cold_ptr=cold_dev.data_ptr())
+        torch.cuda.synchronize()
+        assert np.array_equal(_from_device_layout(D, b, nx), ref1), (nx, ny)
+        assert np.array_equal(_from_device_layout(D, a, nx), ref2), (nx, ny)
+        nus = nu.cpu().numpy()
+        if want_nu:
+            assert nus[0] == nu1 and nus[1] == nu2, (nx, ny)
+        else:
+            assert not nus.any()
 
 
 def test_noalloc_rejects_rows_beyond_its_scratch(env):
