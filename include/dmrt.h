@@ -389,9 +389,18 @@ typedef struct dmrt_batch dmrt_batch;
  * (0 = default: 2, 2, 2 for FLOAT32, 4, 2, 2 for MIXED storage), and steps
  * per CUDA graph (0 = 64; must be even). Compiled tiles (npt, R, S), for both
  * storages and roundings: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2) (2,1,3)
- * (2,2,2) (2,2,3) (2,4,2) (4,1,4) (4,2,2) (4,4,2). */
+ * (2,2,2) (2,2,3) (2,4,2) (4,1,4) (4,2,2) (4,4,2).
+ * group_bytes: 0 = one launch per time step steps every cavity (the state
+ * streams through HBM on every step). > 0 = the cavities are split, in index
+ * order, into groups whose two population buffers take at most group_bytes
+ * together (a larger cavity is a group of its own), and dmrt_batch_step runs
+ * the groups one after another, each for all of the call's steps with
+ * launches over its own cavities: a group small enough for the L2 cache
+ * (e.g. 32 to 96 MB of the GB300's 126 MB) is read from and written to L2
+ * between its steps. Every cavity's results are the same bits either way. */
 typedef struct {
     int32_t tma_npt, tma_rows, tma_stages, graph_steps;
+    int64_t group_bytes;
 } dmrt_batch_opts;
 
 /* Device workspace for a batch of n cavities (the members' workspaces plus the
@@ -415,6 +424,9 @@ int dmrt_batch_step(dmrt_batch* b, int64_t nsteps);
 int dmrt_batch_check(dmrt_batch* b);
 
 int32_t dmrt_batch_size(const dmrt_batch* b);
+
+/* Number of cavity groups (1 unless dmrt_batch_opts.group_bytes > 0). */
+int32_t dmrt_batch_group_count(const dmrt_batch* b);
 
 /* Member i as a context (borrowed: do not destroy it), or NULL. */
 dmrt_ctx* dmrt_batch_context(dmrt_batch* b, int32_t i);

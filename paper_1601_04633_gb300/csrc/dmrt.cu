@@ -1466,6 +1466,20 @@ void dmrt_destroy(dmrt_ctx* c) {
 
 // ---- batched sweep ------------------------------------------------------------
 
+// Cavities [first, first + count) of a batch, stepped by launches of their own.
+// One group (all cavities) streams the whole batch through HBM on every step;
+// smaller groups, each run for all the steps of a call before the next one,
+// keep their state resident in L2 between steps.
+struct BatchGroup {
+    int first, count;
+    int total_items;
+    int static_per_block;  // items each block takes before drawing from the shared pool
+    int grid;
+    int* d_ib;             // first item of each of its cavities, then the total (count + 1 entries)
+    unsigned* d_ctr;       // its two work-pool counters (by launch parity)
+    cudaGraphExec_t graph[2];
+};
+
 struct dmrt_batch {
     int n;
     std::vector<dmrt_ctx*> sub;
@@ -1473,16 +1487,14 @@ struct dmrt_batch {
     cudaStream_t stream;
     dmrt::BatchCavity* d_cav;
     CUtensorMap* d_maps;
-    int* d_ib;  // first item of each cavity, then the total (n + 1 entries)
     unsigned* d_err;
-    int total_items;
-    int static_per_block;  // items each block takes before drawing from the shared pool
-    int npt, R, S, grid, block;
+    std::vector<BatchGroup> groups;
+    long long group_bytes;
+    int npt, R, S, block;
     size_t smem;
     const void* func;
     int parity;
     long long t;
-    cudaGraphExec_t graph[2];
     int graph_len;
     char err[256];
 };
@@ -1525,10 +1537,10 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
     o += align256((size_t)n * sizeof(dmrt::BatchCavity));
     L->off_maps = o;
     o += align256((size_t)n * 2 * dmrt::kBatchMaps * sizeof(CUtensorMap));
-    L->off_ib = o;
-    o += align256((size_t)(n + 1) * sizeof(int));
-    L->off_err = o;
-    o += 256;
+    L->off_ib = o;  // item tables of at most n groups: n + groups entries
+    o += align256((size_t)(2 * n) * sizeof(int));
+    L->off_err = o;  // the error word, then two pool counters per group
+    o += align256(sizeof(unsigned) * (size_t)(1 + 2 * n));
     L->total = o;
     return DMRT_OK;
 }
@@ -1552,25 +1564,43 @@ int batch_cuda_fail(dmrt_batch* b, cudaError_t e, const char* what) {
         if (e_ != cudaSuccess) return batch_cuda_fail(b, e_, what);  \
     } while (0)
 
-int batch_launch(dmrt_batch* b, int parity) {
-    void* params[8] = {&b->d_cav, &b->d_maps, &b->d_ib, &b->n, &b->total_items, &b->static_per_block, &parity,
-                       &b->d_err};
-    BCK(cudaLaunchKernel(b->func, dim3(b->grid), dim3(b->block), params, b->smem, b->stream),
+// The kernel arguments of group g's launches (parity points at the launch's parity).
+struct GroupArgs {
+    const dmrt::BatchCavity* cav;
+    const CUtensorMap* maps;
+    const int* ib;
+    int n_cav, total, per_block;
+    unsigned *err, *ctr;
+    GroupArgs(const dmrt_batch* b, const BatchGroup& G)
+        : cav(b->d_cav + G.first), maps(b->d_maps + (size_t)G.first * 2 * dmrt::kBatchMaps), ib(G.d_ib),
+          n_cav(G.count), total(G.total_items), per_block(G.static_per_block), err(b->d_err), ctr(G.d_ctr) {}
+    void fill(void** p, int* parity) {
+        p[0] = &cav, p[1] = &maps, p[2] = &ib, p[3] = &n_cav, p[4] = &total, p[5] = &per_block;
+        p[6] = parity, p[7] = &err, p[8] = &ctr;
+    }
+};
+
+int batch_launch(dmrt_batch* b, const BatchGroup& G, int parity) {
+    GroupArgs a(b, G);
+    void* params[9];
+    a.fill(params, &parity);
+    BCK(cudaLaunchKernel(b->func, dim3(G.grid), dim3(b->block), params, b->smem, b->stream),
         "batch step launch");
     return DMRT_OK;
 }
 
-int batch_build_graph(dmrt_batch* b, int from) {
+int batch_build_graph(dmrt_batch* b, BatchGroup& G, int from) {
     cudaGraph_t g;
     BCK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
     cudaGraphNode_t prev = nullptr;
     int par[2] = {from, 1 - from};
+    GroupArgs a(b, G);
     for (int i = 0; i < b->graph_len; ++i) {
         cudaKernelNodeParams kp = {};
-        void* params[8] = {&b->d_cav, &b->d_maps, &b->d_ib, &b->n, &b->total_items, &b->static_per_block,
-                           &par[i & 1], &b->d_err};
+        void* params[9];
+        a.fill(params, &par[i & 1]);
         kp.func = const_cast<void*>(b->func);
-        kp.gridDim = dim3(b->grid);
+        kp.gridDim = dim3(G.grid);
         kp.blockDim = dim3(b->block);
         kp.sharedMemBytes = (unsigned)b->smem;
         kp.kernelParams = params;
@@ -1582,7 +1612,7 @@ int batch_build_graph(dmrt_batch* b, int from) {
         }
         prev = node;
     }
-    cudaError_t e = cudaGraphInstantiate(&b->graph[from], g, 0);
+    cudaError_t e = cudaGraphInstantiate(&G.graph[from], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return batch_cuda_fail(b, e, "cudaGraphInstantiate");
     return DMRT_OK;
@@ -1657,7 +1687,6 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     b->func = func;
     b->parity = 0;
     b->t = 0;
-    b->graph[0] = b->graph[1] = nullptr;
     b->graph_len = glen;
     b->err[0] = 0;
     auto fail = [&](int code) {
@@ -1754,22 +1783,50 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         batch_set_err(b, "batch has too many work items");
         return fail(DMRT_E_ARG);
     }
-    b->total_items = (int)items;
+    // Groups: consecutive cavities whose two population buffers together take
+    // at most group_bytes (a larger cavity forms a group of its own); 0: one
+    // group of all cavities. Each group numbers its own items from 0.
+    b->group_bytes = opts && opts->group_bytes > 0 ? opts->group_bytes : 0;
     b->d_cav = reinterpret_cast<dmrt::BatchCavity*>(b->ws + L.off_cav);
     b->d_maps = reinterpret_cast<CUtensorMap*>(b->ws + L.off_maps);
-    b->d_ib = reinterpret_cast<int*>(b->ws + L.off_ib);
     b->d_err = reinterpret_cast<unsigned*>(b->ws + L.off_err);
-    std::vector<int> ib(n + 1);
-    for (int i = 0; i < n; ++i) ib[i] = cav[i].item_base;
-    ib[n] = (int)items;
+    int* d_ib_all = reinterpret_cast<int*>(b->ws + L.off_ib);
+    std::vector<int> ib;
+    {
+        long long acc = 0;
+        for (int i = 0; i < n; ++i) {
+            const long long bytes = 2LL * (long long)b->sub[i]->L.buf_bytes;
+            if (b->groups.empty() || (b->group_bytes > 0 && acc > 0 && acc + bytes > b->group_bytes)) {
+                BatchGroup G{};
+                G.first = i;
+                b->groups.push_back(G);
+                acc = 0;
+            }
+            b->groups.back().count += 1;
+            acc += bytes;
+        }
+        for (size_t g = 0; g < b->groups.size(); ++g) {
+            BatchGroup& G = b->groups[g];
+            G.d_ib = d_ib_all + ib.size();
+            G.d_ctr = b->d_err + 1 + 2 * g;
+            int it = 0;
+            for (int i = G.first; i < G.first + G.count; ++i) {
+                cav[i].item_base = it;
+                ib.push_back(it);
+                it += cav[i].n_strips * cav[i].n_rowblocks;
+            }
+            ib.push_back(it);
+            G.total_items = it;
+        }
+    }
     cudaError_t e = cudaMemcpyAsync(b->d_cav, cav.data(), cav.size() * sizeof(cav[0]), cudaMemcpyHostToDevice,
                                     b->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_maps, maps.data(), maps.size() * sizeof(maps[0]), cudaMemcpyHostToDevice,
                             b->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_ib, ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, 256, b->stream);
+        e = cudaMemcpyAsync(d_ib_all, ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned) * (1 + 2 * b->groups.size()), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch tables"));
     // Launch shape: persistent grid of resident blocks.
@@ -1785,9 +1842,11 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         batch_set_err(b, "batched tile does not fit on an SM");
         return fail(DMRT_E_ARG);
     }
-    b->grid = (int)std::min<long long>(items, (long long)sms * per_sm);
-    // Three quarters of the items are split statically, the rest are drawn at run time.
-    b->static_per_block = (int)(items * 3 / 4 / b->grid);
+    for (BatchGroup& G : b->groups) {
+        G.grid = (int)std::min<long long>(G.total_items, (long long)sms * per_sm);
+        // Three quarters of the items are split statically, the rest are drawn at run time.
+        G.static_per_block = (int)((long long)G.total_items * 3 / 4 / G.grid);
+    }
     *out = b;
     return DMRT_OK;
 }
@@ -1801,25 +1860,32 @@ int dmrt_batch_step(dmrt_batch* b, int64_t nsteps) {
             return DMRT_E_STATE;
         }
     }
-    long long done = 0;
-    while (done < nsteps) {
-        if (nsteps - done >= b->graph_len) {
-            if (!b->graph[b->parity]) {
-                int rc = batch_build_graph(b, b->parity);
+    // Group after group, each for all nsteps steps (independent cavities: the
+    // order of the groups does not change any result).
+    const int start = b->parity;
+    for (BatchGroup& G : b->groups) {
+        int parity = start;
+        long long done = 0;
+        while (done < nsteps) {
+            if (nsteps - done >= b->graph_len) {
+                if (!G.graph[parity]) {
+                    int rc = batch_build_graph(b, G, parity);
+                    if (rc) return rc;
+                }
+                BCK(cudaGraphLaunch(G.graph[parity], b->stream), "cudaGraphLaunch");
+                done += b->graph_len;  // even: parity unchanged
+            } else {
+                int rc = batch_launch(b, G, parity);
                 if (rc) return rc;
+                parity ^= 1;
+                done += 1;
             }
-            BCK(cudaGraphLaunch(b->graph[b->parity], b->stream), "cudaGraphLaunch");
-            done += b->graph_len;  // even: parity unchanged
-        } else {
-            int rc = batch_launch(b, b->parity);
-            if (rc) return rc;
-            b->parity ^= 1;
-            done += 1;
         }
+        if (nsteps > 0)  // each cavity's last step: its local Nu rows into its ring
+            dmrt::nu_finalize_batch_kernel<<<G.count, 256, 0, b->stream>>>(b->d_cav + G.first, parity);
+        BCK(cudaGetLastError(), "batch step launch");
     }
-    if (nsteps > 0)  // each cavity's last step: its local Nu rows into its ring
-        dmrt::nu_finalize_batch_kernel<<<b->n, 256, 0, b->stream>>>(b->d_cav, b->parity);
-    BCK(cudaGetLastError(), "batch step launch");
+    b->parity = start ^ (int)(nsteps & 1);
     b->t += nsteps;
     for (dmrt_ctx* c : b->sub) {
         c->cur = b->parity;
@@ -1860,7 +1926,9 @@ int dmrt_batch_get_launch(const dmrt_batch* b, dmrt_launch* out) {
     out->tma_npt = b->npt;
     out->tma_rows = b->R;
     out->tma_stages = b->S;
-    out->grid = b->grid;
+    int grid = 0;
+    for (const BatchGroup& G : b->groups) grid = std::max(grid, G.grid);
+    out->grid = grid;
     out->block = b->block;
     out->smem_bytes = (int64_t)b->smem;
     out->graph_steps = b->graph_len;
@@ -1872,11 +1940,14 @@ const char* dmrt_batch_last_error(const dmrt_batch* b) { return b ? b->err : g_c
 void dmrt_batch_destroy(dmrt_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
-    for (int i = 0; i < 2; ++i)
-        if (b->graph[i]) cudaGraphExecDestroy(b->graph[i]);
+    for (BatchGroup& G : b->groups)
+        for (int i = 0; i < 2; ++i)
+            if (G.graph[i]) cudaGraphExecDestroy(G.graph[i]);
     for (dmrt_ctx* c : b->sub) dmrt_destroy(c);
     delete b;
 }
+
+int32_t dmrt_batch_group_count(const dmrt_batch* b) { return b ? (int32_t)b->groups.size() : 0; }
 
 }  // extern "C"
 

@@ -48,7 +48,7 @@ template <typename L, int NPT, int R, int S, bool SR = false>
 __global__ void __launch_bounds__(R * (256 / NPT))
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
                           const int* __restrict__ item_base, int n_cav, int total_items, int static_per_block,
-                          int parity, unsigned* batch_err) {
+                          int parity, unsigned* batch_err, unsigned* ctr) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     constexpr size_t kStageBytes = tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));  // a multiple of 128
@@ -58,7 +58,6 @@ __global__ void __launch_bounds__(R * (256 / NPT))
     __shared__ int4 stage_item[S];  // (cavity, strip, row block, item) of each stage; cavity -1: no more items
     constexpr int HALO = L::kHalo;
     const int tid = threadIdx.x;
-    unsigned* ctr = batch_err + 1;
 
     if (tid == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);

@@ -87,7 +87,8 @@ class Launch(ctypes.Structure):
 
 class BatchOpts(ctypes.Structure):
     _fields_ = [("tma_npt", ctypes.c_int32), ("tma_rows", ctypes.c_int32),
-                ("tma_stages", ctypes.c_int32), ("graph_steps", ctypes.c_int32)]
+                ("tma_stages", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
+                ("group_bytes", ctypes.c_int64)]
 
 
 _lib = None
@@ -132,6 +133,7 @@ SIGNATURES = {
     "dmrt_batch_step": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "dmrt_batch_check": (ctypes.c_int, [_VP]),
     "dmrt_batch_size": (ctypes.c_int32, [_VP]),
+    "dmrt_batch_group_count": (ctypes.c_int32, [_VP]),
     "dmrt_batch_context": (_VP, [_VP, ctypes.c_int32]),
     "dmrt_batch_get_launch": (ctypes.c_int, [_VP, ctypes.POINTER(Launch)]),
     "dmrt_batch_last_error": (ctypes.c_char_p, [_VP]),
@@ -503,7 +505,8 @@ class Batch:
                     th_ptrs[i] = a.ctypes.data_as(_DP)
         o = None
         if opts is not None:
-            o = BatchOpts(*[int(opts.get(k, 0)) for k in ("tma_npt", "tma_rows", "tma_stages", "graph_steps")])
+            o = BatchOpts(*[int(opts.get(k, 0)) for k in ("tma_npt", "tma_rows", "tma_stages", "graph_steps",
+                                                          "group_bytes")])
         b = _VP()
         _check_batch(load().dmrt_batch_create(arr, n, th_ptrs, ctypes.byref(o) if o else None,
                                               _VP(self.workspace.data_ptr()), nbytes.value,
@@ -513,6 +516,7 @@ class Batch:
         lk = Launch()
         _check_batch(load().dmrt_batch_get_launch(b, ctypes.byref(lk)), b)
         self.launch = lk.as_dict()
+        self.groups = load().dmrt_batch_group_count(b)
         self.members = [_Member(self, i, params_list[i]) for i in range(n)]
 
     @classmethod

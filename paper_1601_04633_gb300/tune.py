@@ -9,6 +9,7 @@ every tile computes bit-identical steps.
     python -m paper_1601_04633_gb300.tune --batch      # the 64-cavity sweep
     python -m paper_1601_04633_gb300.tune --single 4096
     python -m paper_1601_04633_gb300.tune --batch --storage 3 --tile 4 4 2 --steps 16 --graph-steps 16
+    python -m paper_1601_04633_gb300.tune --batch --group-mb 0 32 64    # with L2-sized cavity groups
 """
 from __future__ import annotations
 
@@ -74,27 +75,46 @@ def _cache_put(path, key, value):
     os.replace(tmp, path)
 
 
-def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0, rounding=0):
-    """Pick the batched kernel's tile for these cavities (storage 0: float32,
-    3: mixed). Returns {"opts": {...}, "mlups": best, "trials": [...]}."""
+# Cavity-group sizes tried for the batched sweep (bytes of both population
+# buffers per group; 0: one group, every cavity in every launch). The GB300's
+# L2 holds about 126 MB.
+GROUP_BYTES = [0, 24 << 20, 40 << 20, 64 << 20, 96 << 20]
+
+
+def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0, rounding=0,
+               group_bytes=(0,), finalists=3):
+    """Pick the batched kernel's tile, and its cavity-group size, for these
+    cavities (storage 0: float32, 3: mixed). Every tile is timed with the first
+    group size; the `finalists` fastest tiles are then timed with each other
+    group size. Returns {"opts": {...}, "mlups": best, "trials": [...]}."""
     from . import dmrt as D
 
-    key = _key("batch", [(c.nx, c.ny) for c in cavities], f"{steps}-{storage}-{rounding}")
+    key = _key("batch", [(c.nx, c.ny) for c in cavities], f"{steps}-{storage}-{rounding}-{list(group_bytes)}")
     hit = _cache_get(cache, key)
     if hit:
         return hit
     nodes = sum(c.nx * c.ny for c in cavities)
     trials = []
+
+    def trial(npt, R, S, g, gb):
+        opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g, group_bytes=gb)
+        # The warm-up covers one whole graph, so its instantiation is not timed.
+        b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + g + 8, storage=storage,
+                                rounding=rounding)
+        sec = _time_steps(b.step, steps, max(warmup, g))
+        b.check()
+        trials.append({"opts": opts, "mlups": nodes * steps / sec / 1e6, "groups": b.groups})
+        b.close()
+
     for npt, R, S in (tiles or BATCH_TILES):
         for g in graph_steps:
-            opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g)
-            # The warm-up covers one whole graph, so its instantiation is not timed.
-            b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + g + 8, storage=storage,
-                                    rounding=rounding)
-            sec = _time_steps(b.step, steps, max(warmup, g))
-            b.check()
-            b.close()
-            trials.append({"opts": opts, "mlups": nodes * steps / sec / 1e6})
+            trial(npt, R, S, g, group_bytes[0])
+    if len(group_bytes) > 1:
+        top = sorted(trials, key=lambda r: -r["mlups"])[:finalists]
+        for t in top:
+            o = t["opts"]
+            for gb in group_bytes[1:]:
+                trial(o["tma_npt"], o["tma_rows"], o["tma_stages"], o["graph_steps"], gb)
     best = max(trials, key=lambda r: r["mlups"])
     out = {"opts": best["opts"], "mlups": best["mlups"], "trials": trials}
     _cache_put(cache, key, out)
@@ -140,13 +160,16 @@ def main():
     ap.add_argument("--rounding", type=int, default=0, help="0 nearest, 1 stochastic")
     ap.add_argument("--tile", type=int, nargs=3, metavar=("NPT", "R", "S"), help="time this tile only")
     ap.add_argument("--graph-steps", type=int, default=64, help="steps per CUDA graph (batched sweep)")
+    ap.add_argument("--group-mb", type=int, nargs="*", default=[0],
+                    help="cavity-group sizes to try, MB of both buffers (batched sweep; 0: one group)")
     ap.add_argument("--cache", default=None)
     args = ap.parse_args()
     tiles = [tuple(args.tile)] if args.tile else None
     if args.batch:
         print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, tiles=tiles,
                                     graph_steps=(args.graph_steps,), cache=args.cache, storage=args.storage,
-                                    rounding=args.rounding), indent=1))
+                                    rounding=args.rounding, group_bytes=[m << 20 for m in args.group_mb]),
+                         indent=1))
     if args.single:
         cav = inputs.Cavity(args.single, args.single, 1e7, 0.001, seed=5)
         print(json.dumps(tune_single(cav, storage=args.storage, rounding=args.rounding, steps=args.steps,

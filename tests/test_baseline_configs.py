@@ -4,14 +4,17 @@
   relative error per field) and the mean-Nu history within 1e-4.
 * 256 x 256 oscillatory (Ra 1e5, Pr 0.005): fields at step 1e4 for every
   storage mode (float32 within 1e-4, the 1e-3-step tolerance grown linearly;
-  the 16-bit and mixed errors are reported with loose bounds); over 1e6 steps
+  the 16-bit and mixed errors held to about twice their measured values) and
+  the Nusselt gate (1e-3, step by step; strict expected failures for the
+  storage modes that miss it); over 1e6 steps
   the float32 Nu history sample by sample and the mixed-storage histories'
   mean, period and amplitude against the oracle's record (golden file from
   tests/golden/make_baseline_goldens.py).
 * The 64-cavity sweep, 50,000 steps in one batch: three sampled members' Nu
   histories within 1e-3 of the oracle's (same golden script).
-* 4096 x 4096, Ra 1e7, Pr 0.001, 20,000 steps: the mixed-storage run's mean-Nu
-  history within 1e-3 of the float32 run's.
+* 4096 x 4096, Ra 1e7, Pr 0.001, 20,000 steps: each storage mode's mean-Nu
+  history within 1e-3 of the float32 run's, step by step (strict expected
+  failures for the modes that miss it).
 """
 import json
 import os
@@ -75,62 +78,126 @@ def test_cavity_64_20000_steps(D):
     print(f"64^2 x 20000: steady mean Nu {nu[-1]:.6f} (oracle {ref['nu_series'][-1]:.6f})")
 
 
-def test_cavity_256_fields_at_step_10000(D):
-    cav = inputs.cavity_256_oscillatory()
-    steps = 10_000
-    m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
-    f, g = O.init(m, cav.theta0())
-    ref = O.run(m, steps, f, g)
-    # float32: the 1e-5 tolerance holds at 1e3 steps; rounding errors grow at
-    # most linearly with the step count, so 1e-4 at 1e4 steps. The other modes
-    # are reported, with bounds that only catch a broken path.
-    # Mixed storage keeps theta within ~3e-5 and Nu within ~5e-7 but the
-    # velocities only to ~1.5 % (the float16 resolution of the flow populations
-    # while the flow is still weak).
-    bounds = {(0, 0): 1e-4, (3, 0): 0.05, (3, 1): 0.05, (1, 1): 0.5, (1, 0): 10.0, (2, 0): 10.0, (2, 1): 10.0}
-    for (storage, rounding), bound in bounds.items():
+# 256^2 at step 1e4, every storage mode. float32: the 1e-5 tolerance holds at
+# 1e3 steps; rounding errors grow at most linearly with the step count, so 1e-4
+# at 1e4 steps. The other modes are held to about twice their measured field
+# errors (GB300, max over u, v, theta of max |a - b| / max |b|: mixed 1.5e-2,
+# mixed SR 1.3e-2, float16 0.12, bfloat16 0.58, float16 SR 1.1e-2, bfloat16 SR
+# 7.1e-2); mixed storage keeps theta within ~3e-5 and the velocities only to
+# ~1.5 % (the float16 resolution of the flow populations while the flow is
+# still weak). The Nusselt gate is checked step by step over the 1e4 steps.
+FIELDS_256_BOUND = {(0, 0): 1e-4, (3, 0): 0.03, (3, 1): 0.03, (1, 0): 0.25, (2, 0): 1.2, (1, 1): 0.025,
+                    (2, 1): 0.15}
+_runs_256 = {}
+
+
+def _run_256(D, storage, rounding):
+    key = (storage, rounding)
+    if key not in _runs_256:
+        cav = inputs.cavity_256_oscillatory()
+        steps = 10_000
+        if "ref" not in _runs_256:
+            m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+            f, g = O.init(m, cav.theta0())
+            _runs_256["ref"] = O.run(m, steps, f, g)
+        ref = _runs_256["ref"]
         u, v, th, nu = _gpu_run(D, cav, steps, storage=storage, rounding=rounding)
         errs = {name: _field_err(a, ref[name]) for name, a in (("u", u), ("v", v), ("theta", th))}
-        nu_err = float(np.abs(nu - ref["nu_series"]).max() / np.abs(ref["nu_series"]).max())
+        nu_pw = float(np.max(np.abs(nu - ref["nu_series"]) / np.abs(ref["nu_series"])))
         print(f"256^2 step 1e4, storage {storage} rounding {rounding}: field errors "
-              + ", ".join(f"{k} {e:.2e}" for k, e in errs.items()) + f", Nu {nu_err:.2e}")
-        assert max(errs.values()) <= bound, (storage, rounding, errs)
+              + ", ".join(f"{k} {e:.2e}" for k, e in errs.items()) + f", Nu step-by-step {nu_pw:.2e}")
+        _runs_256[key] = (errs, nu_pw)
+    return _runs_256[key]
 
 
-def test_cavity_256_one_million_steps_statistics(D):
-    # The oscillatory cavity over 1e6 steps (Fo 1.53) against the oracle's
-    # record. float32 follows the oracle sample by sample for the whole run.
-    # Mixed storage leaves it after Fo ~0.11 (the oscillation's phase drifts),
-    # so its statistics are compared: with stochastic rounding of the flow
-    # populations the mean over the second half stays within 1e-3 (measured
-    # 1.4e-4); with rounding to nearest it is biased low (measured -3.1e-3:
-    # increments below half a float16 unit are lost), which is recorded here
-    # with a bound that only catches a broken path.
-    gold = _gold("oracle_config2_256.json")
-    cav = inputs.cavity_256_oscillatory()
-    steps, every = gold["steps"], gold["every"]
-    fo = cav.alpha / cav.ny ** 2 * every
-    ref = np.array(gold["nu"])
-    half = len(ref) // 2
-    so = A.nu_statistics(ref, fo, window_fo=1.0)
-    for storage, rounding, bound in ((0, 0, 1e-4), (3, 1, 1e-3), (3, 0, 1e-2)):
+@pytest.mark.parametrize("storage,rounding", list(FIELDS_256_BOUND),
+                         ids=["fp32", "mixed", "mixed_sr", "fp16", "bf16", "fp16_sr", "bf16_sr"])
+def test_cavity_256_fields_at_step_10000(D, storage, rounding):
+    errs, nu_pw = _run_256(D, storage, rounding)
+    assert max(errs.values()) <= FIELDS_256_BOUND[(storage, rounding)], errs
+    if storage == 0:
+        assert nu_pw <= 1e-4
+
+
+def _gate_fails(reason):
+    return pytest.mark.xfail(strict=True, reason=reason)
+
+
+GATE_CASES = [
+    pytest.param(3, 0, id="mixed"),
+    pytest.param(3, 1, id="mixed_sr"),
+    pytest.param(1, 0, id="fp16", marks=_gate_fails("float16 nearest storage misses the Nu target")),
+    pytest.param(2, 0, id="bf16", marks=_gate_fails("bfloat16 nearest storage misses the Nu target")),
+    pytest.param(1, 1, id="fp16_sr", marks=_gate_fails("float16 SR storage misses the Nu target")),
+    pytest.param(2, 1, id="bf16_sr", marks=_gate_fails("bfloat16 SR storage misses the Nu target")),
+]
+
+
+@pytest.mark.parametrize("storage,rounding", GATE_CASES)
+def test_cavity_256_nu_gate_at_step_10000(D, storage, rounding):
+    _, nu_pw = _run_256(D, storage, rounding)
+    assert nu_pw <= 1e-3
+
+
+_runs_1e6 = {}
+
+
+def _run_1e6(D, storage, rounding):
+    key = (storage, rounding)
+    if key not in _runs_1e6:
+        gold = _gold("oracle_config2_256.json")
+        cav = inputs.cavity_256_oscillatory()
+        steps, every = gold["steps"], gold["every"]
+        fo = cav.alpha / cav.ny ** 2 * every
+        ref = np.array(gold["nu"])
+        half = len(ref) // 2
         sim = D.Cavity2D.from_inputs(cav, storage=storage, rounding=rounding, nu_capacity=steps)
         sim.step(steps)
         sim.check()
         nu = sim.nusselt(steps)[2][every - 1::every]
         sim.close()
         sg = A.nu_statistics(nu, fo, window_fo=1.0)
+        so = A.nu_statistics(ref, fo, window_fo=1.0)
         dmean = (nu[half:].mean() - ref[half:].mean()) / ref[half:].mean()
         print(f"256^2 x 1e6, storage {storage} rounding {rounding}: second-half mean {nu[half:].mean():.5f} "
               f"(oracle {ref[half:].mean():.5f}, {dmean:+.2e}), period {sg.period_fo:.4f} ({so.period_fo:.4f}), "
               f"amplitude {sg.amplitude:.4f} ({so.amplitude:.4f})")
-        assert abs(dmean) <= bound, (storage, rounding, dmean)
-        assert not sg.steady and not so.steady
-        if storage == 0:
-            assert np.abs(nu - ref).max() <= 1e-3 * np.abs(ref).max()
-        if rounding == 1 or storage == 0:
-            assert sg.period_fo == pytest.approx(so.period_fo, rel=0.05)
-            assert sg.amplitude == pytest.approx(so.amplitude, rel=0.1)
+        _runs_1e6[key] = (nu, ref, sg, so, dmean)
+    return _runs_1e6[key]
+
+
+# Bias of the second-half mean against the oracle's record, held to about twice
+# its measured value (GB300: float32 +7.0e-6, mixed SR -7.1e-4, mixed nearest
+# -3.1e-3).
+MEAN_1E6_BOUND = {(0, 0): 1e-4, (3, 1): 1e-3, (3, 0): 7e-3}
+
+
+@pytest.mark.parametrize("storage,rounding", list(MEAN_1E6_BOUND), ids=["fp32", "mixed_sr", "mixed"])
+def test_cavity_256_one_million_steps_statistics(D, storage, rounding):
+    # The oscillatory cavity over 1e6 steps (Fo 1.53) against the oracle's
+    # record. float32 follows the oracle sample by sample for the whole run.
+    # Mixed storage leaves it after Fo ~0.11 (the oscillation's phase drifts),
+    # so its statistics are compared: mean over the second half, period and
+    # amplitude (stochastic rounding), or the mean's bias alone (nearest, whose
+    # increments below half a float16 unit are lost; its gate is below).
+    nu, ref, sg, so, dmean = _run_1e6(D, storage, rounding)
+    assert abs(dmean) <= MEAN_1E6_BOUND[(storage, rounding)], dmean
+    assert not sg.steady and not so.steady
+    if storage == 0:
+        assert np.abs(nu - ref).max() <= 1e-3 * np.abs(ref).max()
+    if rounding == 1 or storage == 0:
+        assert sg.period_fo == pytest.approx(so.period_fo, rel=0.05)
+        assert sg.amplitude == pytest.approx(so.amplitude, rel=0.1)
+
+
+@pytest.mark.parametrize("storage,rounding", [
+    pytest.param(3, 1, id="mixed_sr"),
+    pytest.param(3, 0, id="mixed", marks=_gate_fails("mixed nearest: long-run mean biased by -3.1e-3")),
+])
+def test_cavity_256_one_million_steps_mean_gate(D, storage, rounding):
+    # The Nusselt target over the long run: the second-half mean within 1e-3.
+    dmean = _run_1e6(D, storage, rounding)[4]
+    assert abs(dmean) <= 1e-3
 
 
 def test_sweep_50000_steps_sampled_members(D):
@@ -150,17 +217,28 @@ def test_sweep_50000_steps_sampled_members(D):
     b.close()
 
 
-def test_cavity_4096_20000_steps_mixed_against_float32(D):
-    cav = inputs.cavity_4096()
-    steps = 20_000
-    runs = {}
-    for name, kw in (("fp32", {}), ("mixed", dict(storage=3)), ("fp16_sr", dict(storage=1, rounding=1))):
-        sim = D.Cavity2D.from_inputs(cav, nu_capacity=steps, **kw)
+_runs_4096 = {}
+
+
+def _run_4096(D, storage, rounding):
+    key = (storage, rounding)
+    if key not in _runs_4096:
+        cav = inputs.cavity_4096()
+        steps = 20_000
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=steps, storage=storage, rounding=rounding)
         sim.step(steps)
         sim.check()
-        runs[name] = sim.nusselt(steps)[2]
+        _runs_4096[key] = sim.nusselt(steps)[2]
         sim.close()
-    ref = runs["fp32"]
-    errs = {k: float(np.abs(v - ref).max() / np.abs(ref).max()) for k, v in runs.items() if k != "fp32"}
-    print("4096^2 x 20000: max Nu deviation from float32:", {k: f"{e:.2e}" for k, e in errs.items()})
-    assert errs["mixed"] <= 1e-3
+    return _runs_4096[key]
+
+
+@pytest.mark.parametrize("storage,rounding", GATE_CASES)
+def test_cavity_4096_20000_steps_nu_gate_against_float32(D, storage, rounding):
+    # The metric's gate on the large cavity: the mean-Nu history within 1e-3 of
+    # the float32 run's, step by step, over the stated 20,000 steps.
+    ref = _run_4096(D, 0, 0)
+    nu = _run_4096(D, storage, rounding)
+    dev = float(np.max(np.abs(nu - ref) / np.abs(ref)))
+    print(f"4096^2 x 20000, storage {storage} rounding {rounding}: Nu step-by-step deviation from float32 {dev:.2e}")
+    assert dev <= 1e-3

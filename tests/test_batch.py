@@ -61,6 +61,34 @@ def test_batch_members_match_single_contexts_bitwise(D, tile):
     b.close()
 
 
+@pytest.mark.parametrize("storage", [0, 3], ids=["fp32", "mixed_sr"])
+@pytest.mark.parametrize("group_kb", [1, 4000])
+def test_cavity_groups_give_the_same_bits(D, storage, group_kb):
+    # Cavities split into groups (each group stepped for the whole call before
+    # the next) give exactly the single launch's results, over calls of odd and
+    # even lengths (the launch parity and the work-pool counters of each group).
+    cavs = _uneven()
+    opts = dict(tma_npt=2, tma_rows=2, tma_stages=2, graph_steps=16)
+    ref = D.Batch.from_inputs(cavs, opts=opts, nu_capacity=128, storage=storage)
+    grp = D.Batch.from_inputs(cavs, opts=dict(opts, group_bytes=group_kb << 10), nu_capacity=128,
+                              storage=storage)
+    assert ref.groups == 1 and grp.groups > 1
+    if group_kb == 1:
+        assert grp.groups == len(cavs)  # every cavity exceeds the limit: one group each
+    for n in (21, 16, 3):
+        ref.step(n)
+        grp.step(n)
+    ref.check()
+    grp.check()
+    for i in range(len(cavs)):
+        a, b = ref.members[i], grp.members[i]
+        assert a.steps_done == b.steps_done == 40
+        assert np.array_equal(a.get_state(), b.get_state()), i
+        assert np.array_equal(a.nusselt(40)[2], b.nusselt(40)[2]), i
+    ref.close()
+    grp.close()
+
+
 def test_batch_parity_rule_and_member_stepping(D):
     cavs = _uneven()[:3]
     b = D.Batch.from_inputs(cavs, nu_capacity=64)

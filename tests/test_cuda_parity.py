@@ -162,8 +162,11 @@ def test_energy_budget_with_fixed_temperature_walls(D, storage, walls):
     u = {0: 2.0 ** -24, 1: 2.0 ** -11, 3: 2.0 ** -24}[storage]  # rounding unit of the stored g
     tol = 10 * u * scale + 1e-6 * abs(w0)
     assert abs((e1 - e0) - w0) <= tol, (e1 - e0, w0)
-    if storage == 0:
-        assert abs(w0) > 1e3 * tol  # the float32 budget is not vacuous
+    if storage == 0 and walls != (0, 0):
+        # One heated wall: the heat input is far above the rounding allowance, so
+        # a dropped or mis-signed wall term would fail. (With both walls fixed at
+        # +-0.5 the two inputs nearly cancel by the cavity's symmetry.)
+        assert abs(w0) > 1e3 * tol
 
 
 def _random_state(nx, ny, seed):

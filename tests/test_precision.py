@@ -7,10 +7,10 @@ oracle run from the same (already rounded) state: the only extra error of a
 in the last place (nearest) or one unit (stochastic), u = 2^-11 (float16) or
 2^-8 (bfloat16) of the stored (shifted) value, plus the float32 arithmetic
 (~1e-6 of the plane); a float32 plane of the mixed layout has only the latter.
-Long runs are compared with the oracle. Plain 16-bit storage misses the 1e-3
-Nusselt target (increments below half an ulp are lost, and the temperature
-noise of 16-bit thermal populations remains with stochastic rounding); the
-mixed layout with stochastic rounding of the flow populations meets it.
+Long runs are compared with the oracle step by step. Plain 16-bit storage
+misses the 1e-3 Nusselt target (increments below half an ulp are lost, and the
+temperature noise of 16-bit thermal populations remains with stochastic
+rounding): those cases are strict expected failures. The mixed layout meets it.
 """
 import numpy as np
 import pytest
@@ -96,36 +96,67 @@ def test_one_step_matches_oracle_within_rounding(D, storage, walls, nx, ny, roun
     assert abs(nu_mean - r["nu"]) <= 1e-5 * abs(r["nu"]) + 1e-9
 
 
-@pytest.mark.parametrize("storage,rounding", [(0, 0), (1, 0), (2, 0), (1, 1), (2, 1), (3, 0), (3, 1)],
+# Long runs: 64 x 64, Ra 1e4, Pr 0.01 (Case 1), 5000 steps, against the oracle.
+# The Nusselt gate is the step-by-step relative deviation of the mean-Nu
+# history, max_t |Nu(t) - Nu_oracle(t)| / |Nu_oracle(t)| <= 1e-3. The field
+# errors are held to about twice their measured values (GB300; max |a - b| /
+# max |b| of theta: float32 1.9e-7, float16 4.4e-2, bfloat16 0.31, float16 SR
+# 8.7e-4, bfloat16 SR 8.8e-3, mixed 1.6e-5, mixed SR 2.7e-5).
+LONG_RUN_THETA_BOUND = {(0, 0): 1e-5, (1, 0): 0.09, (2, 0): 0.6, (1, 1): 2e-3, (2, 1): 2e-2, (3, 0): 5e-5,
+                        (3, 1): 6e-5}
+_long_runs = {}
+
+
+def _long_run(D, storage, rounding):
+    key = (storage, rounding)
+    if key not in _long_runs:
+        cav = inputs.cavity_64()
+        steps = 5000
+        sim = D.Cavity2D.from_inputs(cav, storage=storage, rounding=rounding, nu_capacity=steps)
+        sim.step(steps)
+        sim.check()
+        u, v, th = (x.cpu().numpy().astype(np.float64) for x in sim.fields())
+        series = sim.nusselt(steps)[2]
+        sim.close()
+        if "ref" not in _long_runs:
+            m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
+            f, g = O.init(m, cav.theta0())
+            _long_runs["ref"] = O.run(m, steps, f, g)
+        ref = _long_runs["ref"]
+        nu_pw = float(np.max(np.abs(series - ref["nu_series"]) / np.abs(ref["nu_series"])))
+        th_err = np.abs(th - ref["theta"]).max() / np.abs(ref["theta"]).max()
+        print(f"storage {storage} rounding {rounding}: Nu step-by-step error {nu_pw:.3e}, theta error {th_err:.3e}")
+        _long_runs[key] = (nu_pw, th_err)
+    return _long_runs[key]
+
+
+@pytest.mark.parametrize("storage,rounding", list(LONG_RUN_THETA_BOUND),
                          ids=["fp32", "fp16", "bf16", "fp16_sr", "bf16_sr", "mixed", "mixed_sr"])
-def test_long_run_error_report(D, storage, rounding):
-    # 64 x 64, Ra 1e4, Pr 0.01 (Case 1), 5000 steps: float32 meets the parity
-    # tolerances; the 16-bit errors are recorded and only required to be finite
-    # and smaller than the quantities themselves, except for mixed storage with
-    # stochastic rounding, which must meet the Nusselt target.
-    cav = inputs.cavity_64()
-    steps = 5000
-    sim = D.Cavity2D.from_inputs(cav, storage=storage, rounding=rounding, nu_capacity=steps)
-    sim.step(steps)
-    sim.check()
-    u, v, th = (x.cpu().numpy().astype(np.float64) for x in sim.fields())
-    series = sim.nusselt(steps)[2]
-    sim.close()
-    m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
-    f, g = O.init(m, cav.theta0())
-    ref = O.run(m, steps, f, g)
-    nu_err = np.abs(series - ref["nu_series"]).max() / np.abs(ref["nu_series"]).max()
-    th_err = np.abs(th - ref["theta"]).max() / np.abs(ref["theta"]).max()
-    print(f"storage {storage} rounding {rounding}: max Nu error {nu_err:.3e}, theta error {th_err:.3e}")
+def test_long_run_field_error_bounds(D, storage, rounding):
+    nu_pw, th_err = _long_run(D, storage, rounding)
+    assert np.isfinite(nu_pw) and th_err <= LONG_RUN_THETA_BOUND[(storage, rounding)]
     if storage == 0:
-        assert nu_err <= 1e-4 and th_err <= 1e-5
-    elif storage == 3 and rounding == 1:
-        assert nu_err <= NU_TARGET
-    elif storage == 1 and rounding == 1:
-        # stochastic rounding keeps sub-ulp increments: ~1% instead of ~20% (nearest)
-        assert nu_err < 0.03 and th_err < 0.01
-    else:
-        assert np.isfinite(nu_err) and nu_err < 1.0 and th_err < 1.0
+        assert nu_pw <= 1e-4
+
+
+def _gate_fails(reason):
+    return pytest.mark.xfail(strict=True, reason=reason)
+
+
+@pytest.mark.parametrize("storage,rounding", [
+    pytest.param(0, 0, id="fp32"),
+    pytest.param(3, 0, id="mixed"),
+    pytest.param(3, 1, id="mixed_sr"),
+    pytest.param(1, 0, id="fp16", marks=_gate_fails("float16 nearest loses sub-half-ulp thermal increments")),
+    pytest.param(2, 0, id="bf16", marks=_gate_fails("bfloat16 nearest: 8-bit mantissa, far off")),
+    pytest.param(1, 1, id="fp16_sr", marks=_gate_fails("float16 SR: temperature noise, ~0.7 % on Nu")),
+    pytest.param(2, 1, id="bf16_sr", marks=_gate_fails("bfloat16 SR: temperature noise, several % on Nu")),
+])
+def test_long_run_nu_gate(D, storage, rounding):
+    # The metric's target: Nu within 1e-3 of the oracle at every step. Storage
+    # modes that miss it are expected failures (strict: passing would be news).
+    nu_pw, _ = _long_run(D, storage, rounding)
+    assert nu_pw <= NU_TARGET
 
 
 TILES = {(1, 0): tune.SINGLE_TILES_16, (1, 1): tune.SINGLE_TILES_16_SR, (2, 0): tune.SINGLE_TILES_16,
@@ -163,6 +194,6 @@ def test_mixed_long_run_meets_nu_target_at_256(D):
     m = O.derive(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha)
     f, g = O.init(m, cav.theta0())
     ref = O.run(m, steps, f, g)
-    nu_err = np.abs(series - ref["nu_series"]).max() / np.abs(ref["nu_series"]).max()
-    print(f"mixed stochastic 256^2: max Nu error {nu_err:.3e}")
+    nu_err = float(np.max(np.abs(series - ref["nu_series"]) / np.abs(ref["nu_series"])))
+    print(f"mixed stochastic 256^2: Nu step-by-step error {nu_err:.3e}")
     assert nu_err <= NU_TARGET
