@@ -321,6 +321,59 @@ int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* dst,
                       const float* theta_hot, const float* theta_cold, double* nu_mean,
                       void* stream);
 
+/* ---- One cavity split into y-slabs (for several GPUs) ------------------------
+ *
+ * A cavity can be cut into slabs of whole rows, one context per slab (one per
+ * GPU, or several on one GPU), that step together. The streaming of Eqs. 25
+ * and 36 moves populations by at most one row, so a slab's step needs only its
+ * own rows plus one row on each side: from the row below, the populations that
+ * move up (e_y = +1: f_3, f_6, f_7 of Eq. 23 and g_3 of Eq. 35); from the row
+ * above, those that move down (f_5, f_8, f_9, g_5). A slab context holds these
+ * two halo rows next to its own and fills them from its neighbours' messages
+ * between steps; the walls of Eqs. 14-17 and 44-45 apply only at the slab sides
+ * that are cavity walls. The constants (Ra, gbeta, the Nusselt scale) are those
+ * of the whole cavity (H = p->ny), and every slab's state is bit for bit the
+ * state of the same rows of the whole cavity stepped as one context, for every
+ * storage mode (stochastic rounding draws on the cavity row index).
+ *
+ * dmrt_slab_workspace_size / dmrt_create_slab: as dmrt_workspace_size /
+ *   dmrt_create, for rows y0 .. y0 + rows - 1 of the cavity p (1 <= rows,
+ *   y0 + rows <= p->ny); theta0 is NULL or the slab's own [rows][nx] initial
+ *   temperatures. All other entry points work on a slab as on a cavity of
+ *   `rows` rows (fields, state, checkpoints, wall profiles: the slab's rows),
+ *   except that: the Nusselt means (dmrt_nusselt, its ring, dmrt_nusselt_flux)
+ *   are the slab's share of the cavity's mean (its rows' sum divided by the
+ *   cavity's p->ny), so the cavity's mean is the sum over slabs; dmrt_energy
+ *   sums the slab's rows; dmrt_step takes at most one step on a slab that has
+ *   a neighbour (DMRT_E_STATE otherwise); dmrt_adjoint refuses a slab.
+ *
+ * Messages: dmrt_slab_halo_bytes() bytes each, device memory owned by the
+ *   caller (the library allocates nothing), the face planes of one row in the
+ *   slab's storage type.
+ * dmrt_slab_pack(c, to_below, to_above): enqueue copies of the current state's
+ *   first row's downward populations into to_below and of its last row's
+ *   upward populations into to_above (either NULL to skip).
+ * dmrt_slab_unpack(c, from_below, from_above): enqueue copies of the messages
+ *   of the neighbour below (its to_above) and above (its to_below) into the
+ *   current state's halo rows (either NULL to skip; a side that is a cavity
+ *   wall needs none).
+ * dmrt_slab_step(c, to_below, to_above): one time step (the fused step kernel,
+ *   reading the halo rows), then dmrt_slab_pack of the new state.
+ * A run: create the slabs; pack and unpack once (the halo rows of the initial
+ *   state); then per time step: dmrt_slab_step on every slab, deliver each
+ *   message to its neighbour (a copy on one GPU, a send/receive between GPUs),
+ *   dmrt_slab_unpack on every slab. dmrt_slab_step leaves the step's Nusselt
+ *   rows to be summed by the next step; dmrt_step(c, 0) sums the last one. All
+ *   copies are enqueued on the slab's stream; ordering them against the
+ *   transfer between slabs is the caller's. */
+int dmrt_slab_workspace_size(const dmrt_params* p, int32_t rows, size_t* bytes);
+int dmrt_create_slab(const dmrt_params* p, int32_t y0, int32_t rows, const double* theta0, void* workspace,
+                     size_t workspace_bytes, void* stream, dmrt_ctx** out);
+int dmrt_slab_halo_bytes(const dmrt_ctx* c, size_t* bytes);
+int dmrt_slab_pack(dmrt_ctx* c, void* to_below, void* to_above);
+int dmrt_slab_unpack(dmrt_ctx* c, const void* from_below, const void* from_above);
+int dmrt_slab_step(dmrt_ctx* c, void* to_below, void* to_above);
+
 /* Launch configuration a context resolved to (for reports and tuning). */
 typedef struct {
     int32_t kernel;       /* DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */

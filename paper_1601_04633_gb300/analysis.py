@@ -128,3 +128,53 @@ def nu_statistics(series, fo_per_step: float, window_fo: float | None = None,
     return NuStats(steady=bool(steady), mean=mean, amplitude=amplitude if not steady else 0.0,
                    peak_to_peak=p2p, period_fo=spectral, crossing_period_fo=period if not steady else None,
                    cycles=cycles if not steady else 0, window_fo=(float(f[0]), float(f[-1])), drift=drift)
+
+
+# The four cases of the paper's Table 1 (Sec. 4): (Ra, Pr).
+PAPER_CASES = {1: (1e4, 0.01), 2: (5e4, 0.01), 3: (5e4, 0.005), 4: (1e5, 0.01)}
+
+
+def run_case(case: int, n: int, alpha: float, fo_end: float = 4.0, window_fo: float = 2.0, seed=None,
+             device="cuda"):
+    """One of the paper's cases on the GPU: an n x n cavity at lattice thermal
+    diffusivity alpha (which sets the Mach number, Ma = sqrt(3) alpha
+    sqrt(Ra Pr) / n, through Eqs. 9 and 21), run to Fourier number fo_end; the
+    statistics of its mean-Nu history over the last window_fo."""
+    from . import dmrt as D
+    from . import inputs
+
+    Ra, Pr = PAPER_CASES[case]
+    steps = int(round(fo_end * n * n / alpha))
+    cav = inputs.Cavity(n, n, Ra, Pr, alpha=alpha, seed=10 + case if seed is None else seed)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=steps, device=device)
+    sim.step(steps)
+    sim.check()
+    series = sim.nusselt(steps)[2]
+    ma = sim.consts.Ma
+    sim.close()
+    s = nu_statistics(series, alpha / (n * n), window_fo=window_fo)
+    out = {"case": case, "Ra": Ra, "Pr": Pr, "n": n, "alpha": alpha, "Ma": ma, "steps": steps}
+    out.update(s.as_dict())
+    return out
+
+
+def main():
+    import argparse
+    import json
+
+    ap = argparse.ArgumentParser(description="Statistics of the paper's cases (Table 1) on the GPU, "
+                                             "over grids and lattice diffusivities (Mach numbers).")
+    ap.add_argument("--cases", type=int, nargs="+", default=[2, 3, 4])
+    ap.add_argument("--n", type=int, nargs="+", default=[128])
+    ap.add_argument("--alpha", type=float, nargs="+", default=[0.05, 0.1, 0.14])
+    ap.add_argument("--fo", type=float, default=4.0, help="Fourier number to run to")
+    ap.add_argument("--window", type=float, default=2.0, help="analysis window (Fo) at the end of the run")
+    args = ap.parse_args()
+    for n in args.n:
+        for alpha in args.alpha:
+            for case in args.cases:
+                print(json.dumps(run_case(case, n, alpha, args.fo, args.window)), flush=True)
+
+
+if __name__ == "__main__":
+    main()

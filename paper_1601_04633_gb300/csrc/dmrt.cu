@@ -58,10 +58,11 @@ dmrt_params resolved(const dmrt_params& p) {
     return q;
 }
 
-Layout make_layout(const dmrt_params& p) {
+// halo_rows: extra population rows held by a y-slab (one below, one above its ny rows).
+Layout make_layout(const dmrt_params& p, int halo_rows = 0) {
     Layout L;
     L.pitch = ((p.nx + 127) / 128) * 128;
-    L.plane = (long long)p.ny * L.pitch;
+    L.plane = (long long)(p.ny + halo_rows) * L.pitch;
     L.buf_bytes = align256((size_t)L.plane * (9 * f_bytes(p.storage) + 5 * g_bytes(p.storage)));
     size_t o = 0;
     L.off_a = o; o += L.buf_bytes;
@@ -117,6 +118,11 @@ struct dmrt_ctx {
     int graph_len;
     long long nu_floor;  // ring values of steps before this one are unavailable (after a load)
     long long next_poll; // dmrt_step reads the error word once the step count reaches this
+    // A y-slab of a larger cavity (rows y0 .. y0 + p.ny - 1 of H rows) holds one
+    // halo row on each side (row0 = 1) that its neighbours fill; a whole cavity
+    // has row0 = 0, y0 = 0, H = p.ny and both walls.
+    bool slab;
+    int row0, y0, H, wall_lo, wall_hi;
     char err[256];
 };
 
@@ -175,6 +181,11 @@ dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
     A.ny = c->p.ny;
     A.pitch = c->L.pitch;
     A.wx_log2 = c->wx_log2;
+    A.row0 = c->row0;
+    A.wall_lo = c->wall_lo;
+    A.wall_hi = c->wall_hi;
+    A.jglob0 = c->y0;
+    A.nu_div = (double)c->H;
     return A;
 }
 
@@ -213,17 +224,17 @@ __device__ __forceinline__ auto* g_base(B* S, long long plane) {
 template <typename L>
 __global__ void init_kernel(unsigned char* __restrict__ S, const double* __restrict__ theta0, double theta_const,
                             double a, double sh0, double sh1, int nx, int ny, int pitch,
-                            long long plane) {
+                            long long plane, int row0) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     Ef* Sf = f_base<L>(S);
     Eg* Sg = g_base<L>(S, plane);
-    const long long n = (long long)ny * pitch;
+    const long long n = plane;  // every row held, halo rows (zero) included
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(q / pitch), i = (int)(q % pitch);
+        const int j = (int)(q / pitch) - row0, i = (int)(q % pitch);
         double th = 0.0;
-        const bool in = i < nx;
+        const bool in = i < nx && j >= 0 && j < ny;
         if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
         for (int k = 0; k < 9; ++k) Sf[L::pf(k) * plane + q] = elem_from_f<Ef>(0.f);
         Sg[L::pg(0) * plane + q] = elem_from_f<Eg>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
@@ -239,14 +250,14 @@ template <typename L>
 __global__ void fields_kernel(const unsigned char* __restrict__ S, float* __restrict__ u,
                               float* __restrict__ v, float* __restrict__ th, int nx, int ny,
                               int pitch, long long plane, float gbeta, float theta_ref,
-                              float sh0, float sh1) {
+                              float sh0, float sh1, int row0) {
     const auto* Sf = f_base<L>(S);
     const auto* Sg = g_base<L>(S, plane);
     const long long n = (long long)nx * ny;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
          q += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(q / nx), i = (int)(q % nx);
-        const long long s = (long long)j * pitch + i;
+        const long long s = (long long)(j + row0) * pitch + i;
         float f[9], g[5];
         for (int k = 0; k < 9; ++k) f[k] = elem_to_f(Sf[L::pf(k) * plane + s]);
         for (int k = 0; k < 5; ++k) g[k] = elem_to_f(Sg[L::pg(k) * plane + s]) + (k == 0 ? sh0 : sh1);
@@ -299,11 +310,11 @@ int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
 template <typename L>
 __global__ void nu_flux_kernel(const unsigned char* __restrict__ S, const float* __restrict__ hot,
                                double* __restrict__ out, int ny, int pitch, long long plane, double abb,
-                               double g_sign, double sh1, double scale) {
+                               double g_sign, double sh1, double scale, int row0) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ny) return;
     const auto* Sg = g_base<L>(S, plane);
-    const double g3 = (double)elem_to_f(Sg[L::pg(3) * plane + (size_t)j * pitch]) + sh1;
+    const double g3 = (double)elem_to_f(Sg[L::pg(3) * plane + (size_t)(j + row0) * pitch]) + sh1;
     out[j] = scale * (abb * (double)hot[j] - g_sign * 2.0 * g3);
 }
 
@@ -318,12 +329,12 @@ __global__ void energy_rows_kernel(const unsigned char* __restrict__ S, const fl
                                    const float* __restrict__ cold, double* __restrict__ row_theta,
                                    double* __restrict__ row_in, int nx, int ny, int pitch, long long plane,
                                    double abb_l, double sign_l, double abb_r, double sign_r, double sh0,
-                                   double sh1) {
+                                   double sh1, int row0) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= ny) return;  // warp-uniform
     const auto* Sg = g_base<L>(S, plane);
-    const size_t row = (size_t)j * pitch;
+    const size_t row = (size_t)(j + row0) * pitch;
     double acc = 0.0;
     for (int i = lane; i < nx; i += 32) {
         double th = 0.0;
@@ -406,6 +417,7 @@ int plane_storage(const dmrt_params& p, int k) {
     if (p.storage == DMRT_MIXED) return k < 9 ? DMRT_FP16 : DMRT_FP32;
     return p.storage;
 }
+size_t plane_elem_bytes(const dmrt_params& p, int k) { return plane_storage(p, k) == DMRT_FP32 ? 4 : 2; }
 
 // Default TMA tile (nodes per thread, rows, stages) per storage mode, the
 // fastest measured on the 4096^2 cavity.
@@ -452,13 +464,16 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // planes of element type `storage` (FP32, FP16 or BF16) starting at base,
 // with boxes {width, rows, planes}.
 int encode_map(dmrt_ctx* c, CUtensorMap* m, void* base, int storage, int nplanes, int planes, int rows,
-               int width = dmrt::kTmaBox, int xdim = 0) {
+               int width = dmrt::kTmaBox, int xdim = 0, int ydim = 0) {
     auto enc = tensor_map_encoder();
     if (!enc) {
         set_err(c, "cuTensorMapEncodeTiled is not available from the driver");
         return DMRT_E_CUDA;
     }
-    cuuint64_t dims[3] = {(cuuint64_t)(xdim > 0 ? xdim : c->L.pitch), (cuuint64_t)c->p.ny, (cuuint64_t)nplanes};
+    // Rows: every row the buffers hold (a slab's halo rows included), or ydim.
+    const int rows_held = (int)(c->L.plane / c->L.pitch);
+    cuuint64_t dims[3] = {(cuuint64_t)(xdim > 0 ? xdim : c->L.pitch), (cuuint64_t)(ydim > 0 ? ydim : rows_held),
+                          (cuuint64_t)nplanes};
     const int eb = f_bytes(storage);
     cuuint64_t strides[2] = {(cuuint64_t)c->L.pitch * eb, (cuuint64_t)c->L.plane * eb};
     const CUtensorMapDataType dt = storage == DMRT_FP32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
@@ -604,12 +619,12 @@ int setup_kernel(dmrt_ctx* c) {
             rc = encode_map(c, &m.ld[0], buf(c, b), DMRT_FP16, 9, 3, R);
             if (!rc) rc = encode_map(c, &m.ld[1], g, DMRT_FP32, 5, 3, R);
             if (!rc) rc = encode_map(c, &m.ld[2], g, DMRT_FP32, 5, 1, R);
-            if (!rc) rc = encode_map(c, &m.st[0], dst, DMRT_FP16, 9, 9, R, strip, p.nx);
-            if (!rc) rc = encode_map(c, &m.st[1], gd, DMRT_FP32, 5, 5, R, strip, p.nx);
+            if (!rc) rc = encode_map(c, &m.st[0], dst, DMRT_FP16, 9, 9, R, strip, p.nx, c->row0 + p.ny);
+            if (!rc) rc = encode_map(c, &m.st[1], gd, DMRT_FP32, 5, 5, R, strip, p.nx, c->row0 + p.ny);
         } else {
             rc = encode_map(c, &m.ld[0], buf(c, b), p.storage, kPlanes, 6, R);
             if (!rc) rc = encode_map(c, &m.ld[1], buf(c, b), p.storage, kPlanes, 4, R);
-            if (!rc) rc = encode_map(c, &m.st[0], dst, p.storage, kPlanes, kPlanes, R, strip, p.nx);
+            if (!rc) rc = encode_map(c, &m.st[0], dst, p.storage, kPlanes, kPlanes, R, strip, p.nx, c->row0 + p.ny);
         }
         if (rc) return rc;
     }
@@ -737,17 +752,30 @@ int dmrt_workspace_size(const dmrt_params* p, size_t* bytes) {
     return DMRT_OK;
 }
 
-int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
-                size_t workspace_bytes, void* stream, dmrt_ctx** out) {
+}  // extern "C"
+
+// A context for rows y0 .. y0 + rows - 1 of the cavity pg (the whole cavity:
+// y0 = 0, rows = pg->ny, slab = false). The model constants come from the
+// whole cavity (H = pg->ny in Eqs. 9 and 18); the context's own parameters are
+// those of its rows.
+static int create_ctx(const dmrt_params* pg, int y0, int rows, bool slab, const double* theta0, void* workspace,
+                      size_t workspace_bytes, void* stream, dmrt_ctx** out) {
     if (!out) {
         set_err(nullptr, "out is NULL");
         return DMRT_E_ARG;
     }
     *out = nullptr;
     dmrt_consts k;
-    int rc = dmrt_derive(p, &k);
+    int rc = dmrt_derive(pg, &k);
     if (rc) return rc;
-    Layout L = make_layout(*p);
+    if (slab && (y0 < 0 || rows < 1 || y0 + rows > pg->ny)) {
+        set_err(nullptr, "slab rows %d .. %d outside the cavity's %d rows", y0, y0 + rows - 1, pg->ny);
+        return DMRT_E_ARG;
+    }
+    dmrt_params pl = resolved(*pg);
+    pl.ny = rows;
+    const int row0 = slab ? 1 : 0;
+    Layout L = make_layout(pl, 2 * row0);
     if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255)) {
         set_err(nullptr, "workspace must be a 256-byte aligned device pointer");
         return DMRT_E_ARG;
@@ -761,7 +789,8 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
         set_err(nullptr, "out of host memory");
         return DMRT_E_SPACE;
     }
-    c->p = resolved(*p);
+    const dmrt_params* p = &c->p;
+    c->p = pl;
     c->k = k;
     c->L = L;
     c->ws = static_cast<char*>(workspace);
@@ -773,10 +802,16 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     c->nu_floor = 0;
     c->next_poll = kPollSteps;
     c->err[0] = 0;
+    c->slab = slab;
+    c->row0 = row0;
+    c->y0 = y0;
+    c->H = pg->ny;
+    c->wall_lo = y0 == 0;
+    c->wall_hi = y0 + rows == pg->ny;
 
-    c->sc = dmrt::make_step_consts(*p, k);
-    const double sh0 = dmrt::thermal_shift0(*p, k);
-    const double sh1 = dmrt::thermal_shift1(*p, k);
+    c->sc = dmrt::make_step_consts(*pg, k);  // H of the whole cavity
+    const double sh0 = dmrt::thermal_shift0(*pg, k);
+    const double sh1 = dmrt::thermal_shift1(*pg, k);
 
     const int nxq = (p->nx + 3) / 4;
     int wx = 1;
@@ -813,11 +848,11 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
         using Lt = decltype(tag);
         init_kernel<Lt><<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 0)), d_theta0,
                                                      p->theta_init, k.a, sh0, sh1, p->nx, p->ny,
-                                                     L.pitch, L.plane);
+                                                     L.pitch, L.plane, row0);
         // Buffer B's padding columns must read as zero too.
         init_kernel<Lt><<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 1)), nullptr,
                                                      p->theta_ref, k.a, sh0, sh1, p->nx, p->ny, L.pitch,
-                                                     L.plane);
+                                                     L.plane, row0);
     });
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init kernels"));
@@ -825,6 +860,39 @@ int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init synchronize"));
     *out = c;
     return DMRT_OK;
+}
+
+extern "C" {
+
+int dmrt_create(const dmrt_params* p, const double* theta0, void* workspace,
+                size_t workspace_bytes, void* stream, dmrt_ctx** out) {
+    if (!p) {
+        set_err(nullptr, "params is NULL");
+        return DMRT_E_ARG;
+    }
+    return create_ctx(p, 0, p->ny, false, theta0, workspace, workspace_bytes, stream, out);
+}
+
+int dmrt_slab_workspace_size(const dmrt_params* p, int32_t rows, size_t* bytes) {
+    int rc = validate(p, nullptr);
+    if (rc) return rc;
+    if (!bytes || rows < 1 || rows > p->ny) {
+        set_err(nullptr, "need 1 <= rows <= ny and a non-NULL bytes");
+        return DMRT_E_ARG;
+    }
+    dmrt_params pl = *p;
+    pl.ny = rows;
+    *bytes = make_layout(pl, 2).total;
+    return DMRT_OK;
+}
+
+int dmrt_create_slab(const dmrt_params* p, int32_t y0, int32_t rows, const double* theta0, void* workspace,
+                     size_t workspace_bytes, void* stream, dmrt_ctx** out) {
+    if (!p) {
+        set_err(nullptr, "params is NULL");
+        return DMRT_E_ARG;
+    }
+    return create_ctx(p, y0, rows, true, theta0, workspace, workspace_bytes, stream, out);
 }
 
 extern "C++" {
@@ -992,6 +1060,11 @@ static int poll_error(dmrt_ctx* c) {
 
 int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
+    if (c->slab && !(c->wall_lo && c->wall_hi) && nsteps > 1) {
+        set_err(c, "a slab with neighbours takes one step at a time (dmrt_slab_step), its halo rows "
+                   "exchanged in between");
+        return DMRT_E_STATE;
+    }
     while (nsteps > 0) {
         if (c->t >= c->next_poll) {
             // Every kPollSteps steps: stop a run that has diverged (the steps
@@ -1018,6 +1091,113 @@ int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
     return finalize_nu(c);
 }
 
+// ---- y-slabs: halo rows --------------------------------------------------------
+namespace {
+
+// The plane groups a face message carries: P (the populations moving up,
+// e_y = +1: f3 f6 f7 g3) or N (moving down: f5 f8 f9 g5), of one buffer row.
+// One-type layout: 4 consecutive planes; split layout: 3 flow planes, then 1
+// thermal plane. The message holds each plane's nx values, in plane order.
+struct FacePart {
+    size_t plane_byte;  // byte offset of the part's first plane in the buffer
+    size_t eb;          // bytes per element
+    int planes;
+};
+int face_parts(const dmrt_ctx* c, bool up, FacePart* parts) {
+    const long long PL = c->L.plane;
+    if (c->p.storage == DMRT_MIXED) {
+        parts[0] = {(size_t)(up ? 3 : 6) * PL * 2, 2, 3};
+        parts[1] = {(size_t)9 * PL * 2 + (size_t)(up ? 3 : 4) * PL * 4, 4, 1};
+        return 2;
+    }
+    const size_t eb = (size_t)f_bytes(c->p.storage);
+    parts[0] = {(size_t)(up ? dmrt::kGroupP : dmrt::kGroupN) * PL * eb, eb, 4};
+    return 1;
+}
+size_t face_bytes(const dmrt_ctx* c) {
+    FacePart parts[2];
+    const int n = face_parts(c, true, parts);
+    size_t b = 0;
+    for (int i = 0; i < n; ++i) b += parts[i].eb * parts[i].planes * (size_t)c->p.nx;
+    return b;
+}
+// Copy the face planes of buffer row `brow` of the current state to msg
+// (to_msg) or from msg into it; stream-ordered on the context's stream.
+int face_copy(dmrt_ctx* c, bool up, int brow, void* msg, bool to_msg) {
+    FacePart parts[2];
+    const int n = face_parts(c, up, parts);
+    char* base = reinterpret_cast<char*>(buf(c, c->cur));
+    char* m = static_cast<char*>(msg);
+    for (int i = 0; i < n; ++i) {
+        const FacePart& f = parts[i];
+        char* plane0 = base + f.plane_byte + (size_t)brow * c->L.pitch * f.eb;
+        const size_t width = (size_t)c->p.nx * f.eb;
+        const size_t spitch = (size_t)c->L.plane * f.eb;
+        cudaError_t e = to_msg ? cudaMemcpy2DAsync(m, width, plane0, spitch, width, f.planes,
+                                                   cudaMemcpyDeviceToDevice, c->stream)
+                               : cudaMemcpy2DAsync(plane0, spitch, m, width, width, f.planes,
+                                                   cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "halo row copy");
+        m += width * f.planes;
+    }
+    return DMRT_OK;
+}
+
+}  // namespace
+
+int dmrt_slab_halo_bytes(const dmrt_ctx* c, size_t* bytes) {
+    if (!c || !bytes) return DMRT_E_ARG;
+    *bytes = face_bytes(c);
+    return DMRT_OK;
+}
+
+int dmrt_slab_pack(dmrt_ctx* c, void* to_below, void* to_above) {
+    if (!c) return DMRT_E_ARG;
+    if (!c->slab) {
+        set_err(c, "not a slab context");
+        return DMRT_E_ARG;
+    }
+    // The neighbour below pulls our first row's downward populations into its
+    // top row; the neighbour above pulls our last row's upward populations.
+    if (to_below) {
+        int rc = face_copy(c, false, c->row0, to_below, true);
+        if (rc) return rc;
+    }
+    if (to_above) {
+        int rc = face_copy(c, true, c->row0 + c->p.ny - 1, to_above, true);
+        if (rc) return rc;
+    }
+    return DMRT_OK;
+}
+
+int dmrt_slab_unpack(dmrt_ctx* c, const void* from_below, const void* from_above) {
+    if (!c) return DMRT_E_ARG;
+    if (!c->slab) {
+        set_err(c, "not a slab context");
+        return DMRT_E_ARG;
+    }
+    if (from_below) {
+        int rc = face_copy(c, true, c->row0 - 1, const_cast<void*>(from_below), false);
+        if (rc) return rc;
+    }
+    if (from_above) {
+        int rc = face_copy(c, false, c->row0 + c->p.ny, const_cast<void*>(from_above), false);
+        if (rc) return rc;
+    }
+    return DMRT_OK;
+}
+
+int dmrt_slab_step(dmrt_ctx* c, void* to_below, void* to_above) {
+    if (!c) return DMRT_E_ARG;
+    if (!c->slab) {
+        set_err(c, "not a slab context");
+        return DMRT_E_ARG;
+    }
+    int rc = launch_one(c);
+    if (rc) return rc;
+    return dmrt_slab_pack(c, to_below, to_above);
+}
+
 int dmrt_check(dmrt_ctx* c) {
     if (!c) return DMRT_E_ARG;
     return poll_error(c);
@@ -1030,14 +1210,15 @@ int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local) {
     const dmrt_params& p = c->p;
     const bool fixed = p.left_wall == DMRT_WALL_FIXED;
     const double dT = p.theta_hot - p.theta_cold;
-    const double scale = dT != 0.0 ? (double)p.ny / (c->k.alpha * dT) : 0.0;
+    const double scale = dT != 0.0 ? (double)c->H / (c->k.alpha * dT) : 0.0;
     // Per-row values staged in the idle population buffer (no allocation).
     double* stage = reinterpret_cast<double*>(buf(c, 1 - c->cur));
     with_layout(p.storage, [&](auto tag) {
         using Lt = decltype(tag);
         nu_flux_kernel<Lt><<<(p.ny + 255) / 256, 256, 0, c->stream>>>(
             reinterpret_cast<const unsigned char*>(buf(c, c->cur)), reinterpret_cast<const float*>(c->ws + c->L.off_hot),
-            stage, p.ny, c->L.pitch, c->L.plane, fixed ? c->k.abb : 0.0, fixed ? 1.0 : 0.0, (double)c->sc.gsh1, scale);
+            stage, p.ny, c->L.pitch, c->L.plane, fixed ? c->k.abb : 0.0, fixed ? 1.0 : 0.0, (double)c->sc.gsh1, scale,
+            c->row0);
     });
     CK(cudaGetLastError(), "flux Nusselt kernel");
     std::vector<double> local((size_t)p.ny);
@@ -1046,7 +1227,7 @@ int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local) {
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     double sum = 0.0;
     for (double x : local) sum += x;  // rows in order
-    if (nu_mean) *nu_mean = sum / (double)p.ny;
+    if (nu_mean) *nu_mean = sum / (double)c->H;  // a slab: its share of the cavity's mean
     if (nu_local) std::memcpy(nu_local, local.data(), local.size() * sizeof(double));
     return DMRT_OK;
 }
@@ -1065,7 +1246,7 @@ int dmrt_energy(dmrt_ctx* c, double* theta_sum, double* wall_in) {
             reinterpret_cast<const unsigned char*>(buf(c, c->cur)), reinterpret_cast<const float*>(c->ws + c->L.off_hot),
             reinterpret_cast<const float*>(c->ws + c->L.off_cold), rows, rows + p.ny, p.nx, p.ny, c->L.pitch,
             c->L.plane, lf ? c->k.abb : 0.0, lf ? 1.0 : 0.0, rf ? c->k.abb : 0.0, rf ? 1.0 : 0.0,
-            (double)c->sc.gsh0, (double)c->sc.gsh1);
+            (double)c->sc.gsh0, (double)c->sc.gsh1, c->row0);
     });
     sum2_fixed_kernel<<<1, 256, 0, c->stream>>>(rows, rows + p.ny, p.ny, sums);
     CK(cudaGetLastError(), "energy kernels");
@@ -1094,7 +1275,8 @@ int dmrt_fields(dmrt_ctx* c, float* u, float* v, float* theta, int on_device) {
         using Lt = decltype(tag);
         fields_kernel<Lt><<<blocks, 256, 0, c->stream>>>(reinterpret_cast<const unsigned char*>(buf(c, c->cur)),
                                                          du, dv, dt, p.nx, p.ny, c->L.pitch, c->L.plane,
-                                                         c->sc.gbeta, c->sc.theta_ref, c->sc.gsh0, c->sc.gsh1);
+                                                         c->sc.gbeta, c->sc.theta_ref, c->sc.gsh0, c->sc.gsh1,
+                                                         c->row0);
     });
     CK(cudaGetLastError(), "fields kernel");
     if (!on_device) {
@@ -1180,7 +1362,8 @@ int dmrt_get_state(dmrt_ctx* c, float* host) {
     const size_t n = (size_t)p.nx * p.ny;
     float* stage = buf(c, 1 - c->cur);
     for (int k = 0; k < kPlanes; ++k) {
-        const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k) +
+                        (size_t)c->row0 * c->L.pitch * plane_elem_bytes(p, k);
         const int st = plane_storage(p, k);
         if (st == DMRT_FP32) {
             CK(cudaMemcpy2DAsync(host + (size_t)k * n, (size_t)p.nx * sizeof(float), P,
@@ -1208,7 +1391,8 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
     const size_t n = (size_t)p.nx * p.ny;
     float* stage = buf(c, 1 - c->cur);
     for (int k = 0; k < kPlanes; ++k) {
-        char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k) +
+                  (size_t)c->row0 * c->L.pitch * plane_elem_bytes(p, k);
         const int st = plane_storage(p, k);
         if (st == DMRT_FP32) {
             CK(cudaMemcpy2DAsync(P, (size_t)c->L.pitch * sizeof(float), host + (size_t)k * n,
@@ -1262,7 +1446,6 @@ uint64_t fnv1a64(const unsigned char* p, size_t n) {
     return h;
 }
 
-size_t plane_elem_bytes(const dmrt_params& p, int k) { return plane_storage(p, k) == DMRT_FP32 ? 4 : 2; }
 
 size_t ckpt_state_bytes(const dmrt_params& p) {
     size_t s = 0;
@@ -1340,7 +1523,8 @@ int dmrt_save(dmrt_ctx* c, void* host_buf, size_t cap, size_t* used) {
     // Population planes in host order (f_1..f_9, g_1..g_5), stored representation, x < nx.
     for (int k = 0; k < kPlanes; ++k) {
         const size_t eb = plane_elem_bytes(p, k);
-        const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k) +
+                        (size_t)c->row0 * c->L.pitch * eb;
         CK(cudaMemcpy2D(o, nx * eb, P, (size_t)c->L.pitch * eb, nx * eb, ny, cudaMemcpyDeviceToHost),
            "copy state plane");
         o += nx * ny * eb;
@@ -1408,7 +1592,8 @@ int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size) {
     o += h.n_series * sizeof(double);
     for (int k = 0; k < kPlanes; ++k) {
         const size_t eb = plane_elem_bytes(p, k);
-        char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k);
+        char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k) +
+                  (size_t)c->row0 * c->L.pitch * eb;
         CK(cudaMemcpy2D(P, (size_t)c->L.pitch * eb, o, nx * eb, nx * eb, ny, cudaMemcpyHostToDevice),
            "copy state plane");
         o += nx * ny * eb;
@@ -2001,6 +2186,10 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     }
     if (c->p.storage != DMRT_FP32) {
         set_err(c, "the adjoint needs float32 storage");
+        return DMRT_E_ARG;
+    }
+    if (c->slab) {
+        set_err(c, "the adjoint runs on a whole cavity, not on a slab");
         return DMRT_E_ARG;
     }
     if (avg_last > c->p.nu_capacity) {

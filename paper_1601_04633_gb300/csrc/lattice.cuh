@@ -56,9 +56,19 @@ struct StepArgs {
     long long* step_out;            // written once, = step_in + 1
     int rounding;                   // 16-bit storage: 0 nearest, 1 stochastic
     long long cap;
-    long long plane;  // elements per plane = ny * pitch
+    long long plane;  // elements per plane = (rows held) * pitch
     int nx, ny, pitch;
     int wx_log2;      // direct kernel: lanes per row segment = 1 << wx_log2
+    // A y-slab of a larger cavity holds one halo row below and one above its
+    // ny rows: node row j sits in buffer row j + row0 (row0 = 1; 0 for a whole
+    // cavity), and only the slab sides that are cavity walls (wall_lo: row 0,
+    // wall_hi: row ny - 1) apply the wall rules; across the others the pull
+    // reads the halo rows, which the neighbouring slabs fill. jglob0 is the
+    // cavity row of node row 0 (it seeds the stochastic rounding, so a slab
+    // rounds as the whole cavity would), nu_div the row count of the whole
+    // cavity (the Nusselt mean of a slab is its share of the cavity's mean).
+    int row0, wall_lo, wall_hi, jglob0;
+    double nu_div;
 };
 
 constexpr unsigned kErrNonFinite = 1u;
@@ -212,7 +222,7 @@ __device__ __forceinline__ void collide_quad(float4 (&F)[9], float4 (&Gq)[5], co
 // Store a collided quad (4 nodes from x0 of row j) to the destination planes.
 __device__ __forceinline__ void store_quad(const StepArgs& A, int j, int x0, const float4 (&F)[9],
                                            const float4 (&Gq)[5]) {
-    float* D = A.dst + (size_t)j * A.pitch + x0;
+    float* D = A.dst + (size_t)(j + A.row0) * A.pitch + x0;
 #pragma unroll
     for (int k = 0; k < 9; ++k) *reinterpret_cast<float4*>(D + plane_f(k) * A.plane) = F[k];
 #pragma unroll
@@ -267,7 +277,7 @@ __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             if (lane == 0) {
-                const double mean = s / (double)A.ny;
+                const double mean = s / A.nu_div;
                 A.nu_ring[(t - 1) % A.cap] = mean;
                 *A.nu_last = mean;
             }

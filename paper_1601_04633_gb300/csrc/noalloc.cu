@@ -137,6 +137,11 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     A.nx = p->nx;
     A.ny = p->ny;
     A.pitch = pitch;
+    A.row0 = 0;  // a whole cavity: no halo rows, walls on both sides
+    A.wall_lo = 1;
+    A.wall_hi = 1;
+    A.jglob0 = 0;
+    A.nu_div = (double)p->ny;
     const int nxq = (p->nx + 3) / 4;
     int wx = 1;
     while (wx < nxq && wx < 32) wx <<= 1;

@@ -18,6 +18,7 @@ constexpr int kDirectThreads = 128;  // 4 warps per block
 
 struct Geo {
     int nx, ny, pitch, wx, seg_lane;
+    int row0, wall_lo, wall_hi;  // see StepArgs
 };
 
 // Pull-stream of one plane for the four nodes (x0..x0+3, j): the value at node
@@ -36,9 +37,9 @@ template <int EX, int EY>
 __device__ __forceinline__ void pull_load(const float* __restrict__ P, const float* __restrict__ Popp,
                                           int j, int x0, int right_e, const Geo& G, PlaneLoad& L) {
     const int r = j - EY;
-    const bool yin = (r >= 0) && (r < G.ny);
-    const float* orow = Popp + (size_t)j * G.pitch;
-    const float* row = yin ? P + (size_t)r * G.pitch : orow;
+    const bool yin = (r >= 0 || !G.wall_lo) && (r < G.ny || !G.wall_hi);
+    const float* orow = Popp + (size_t)(j + G.row0) * G.pitch;
+    const float* row = yin ? P + (size_t)(r + G.row0) * G.pitch : orow;
     L.v = ldg4(row + x0);
     L.edge = 0.f;
     if constexpr (EX == 1) {
@@ -56,7 +57,7 @@ __device__ __forceinline__ float4 pull_finish(const PlaneLoad& L, int j, int x0,
                                               const Geo& G, float sign_l, float add_l,
                                               float sign_r, float add_r) {
     const int r = j - EY;
-    const bool yin = (r >= 0) && (r < G.ny);
+    const bool yin = (r >= 0 || !G.wall_lo) && (r < G.ny || !G.wall_hi);
     const float4 v = L.v;
     float4 out;
     if constexpr (EX == 0) {
@@ -84,6 +85,9 @@ __device__ __forceinline__ void direct_tile(const StepArgs& A, const StepConsts&
     G.nx = A.nx;
     G.ny = A.ny;
     G.pitch = A.pitch;
+    G.row0 = A.row0;
+    G.wall_lo = A.wall_lo;
+    G.wall_hi = A.wall_hi;
     G.wx = 1 << A.wx_log2;
     G.seg_lane = lane & (G.wx - 1);
     const int rows_per_warp = 32 >> A.wx_log2;

@@ -468,15 +468,15 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
 
         // Walls. Bottom row: links from below (f2, f5, f6, g2) bounce back from
         // the node's own opposites (f4, f7, f8, g4); top row the reverse.
-        const Ef* rowjf = Sf + (size_t)j * A.pitch;
-        const Eg* rowjg = Sgg + (size_t)j * A.pitch;
-        if (j == 0) {
+        const Ef* rowjf = Sf + (size_t)(j + A.row0) * A.pitch;
+        const Eg* rowjg = Sgg + (size_t)(j + A.row0) * A.pitch;
+        if (j == 0 && A.wall_lo) {
             vec_ldg<Ef, NPT>(rowjf + L::pf(4) * PL + x0, F[2], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(7) * PL + x0, F[5], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(8) * PL + x0, F[6], 0.f);
             vec_ldg<Eg, NPT>(rowjg + L::pg(4) * PL + x0, Gq[2], sh1);
         }
-        if (j == A.ny - 1) {
+        if (j == A.ny - 1 && A.wall_hi) {
             vec_ldg<Ef, NPT>(rowjf + L::pf(2) * PL + x0, F[4], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(5) * PL + x0, F[7], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(6) * PL + x0, F[8], 0.f);
@@ -521,17 +521,17 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             Dg = reinterpret_cast<Eg*>(out + out_g_offset(L::kSplit, RC, W, sizeof(Ef))) + rg * W + n0;
         } else {
             DP = PL;
-            Df = reinterpret_cast<Ef*>(A.dst) + (size_t)j * A.pitch + x0;
+            Df = reinterpret_cast<Ef*>(A.dst) + (size_t)(j + A.row0) * A.pitch + x0;
             Dg = (L::kSplit ? reinterpret_cast<Eg*>(reinterpret_cast<unsigned char*>(A.dst) +
                                                     (size_t)9 * PL * sizeof(Ef))
                             : reinterpret_cast<Eg*>(A.dst)) +
-                 (size_t)j * A.pitch + x0;
+                 (size_t)(j + A.row0) * A.pitch + x0;
         }
         // Stochastic rounding: each node's bits come from a hash of its index and the step.
         unsigned r[NPT];
 #pragma unroll
         for (int e = 0; e < NPT; ++e)
-            r[e] = SR ? hash32(((unsigned)j * (unsigned)A.pitch + (unsigned)(x0 + e)) ^ salt) : 0u;
+            r[e] = SR ? hash32(((unsigned)(j + A.jglob0) * (unsigned)A.pitch + (unsigned)(x0 + e)) ^ salt) : 0u;
 #pragma unroll
         for (int k = 0; k < 9; ++k) put_vals<Ef, NPT, SR>(Df + L::pf(k) * DP, F[k], 0.f, r);
 #pragma unroll
@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     // flow boxes, ld[1] 3-plane thermal boxes, ld[2] 1-plane thermal boxes.
     auto issue = [&](const ItemCursor& c, int s) {
         const int x = c.strip * STRIP - HALO;
-        const int j0 = c.rb * R;
+        const int j0 = c.rb * R + A.row0;  // buffer row of the item's first row
         unsigned char* st = stages + (size_t)s * kStageBytes;
         mbar_expect_tx(&bars[s], kStageBytes);
         if constexpr (!L::kSplit) {
@@ -663,7 +663,7 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     // strip's first node (a multiple of 16 bytes).
     auto store = [&](int strip, int rb, const unsigned char* o) {
         const int x = strip * STRIP;
-        const int j0 = rb * R;
+        const int j0 = rb * R + A.row0;
         tma_store_3d(&M.st[0], o, x, j0, 0);
         if constexpr (L::kSplit) tma_store_3d(&M.st[1], o + kOutG, x, j0, 0);
         bulk_commit();

@@ -125,6 +125,14 @@ SIGNATURES = {
     "dmrt_adjoint_workspace_size": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "dmrt_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _DP, _DP, _DP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
+    "dmrt_slab_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
+                                                ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_create_slab": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.c_int32, _DP, _VP,
+                                        ctypes.c_size_t, _VP, ctypes.POINTER(_VP)]),
+    "dmrt_slab_halo_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_slab_pack": (ctypes.c_int, [_VP, _VP, _VP]),
+    "dmrt_slab_unpack": (ctypes.c_int, [_VP, _VP, _VP]),
+    "dmrt_slab_step": (ctypes.c_int, [_VP, _VP, _VP]),
     "dmrt_batch_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
                                                  ctypes.POINTER(ctypes.c_size_t)]),
     "dmrt_batch_create": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32, ctypes.POINTER(_DP),
@@ -312,6 +320,44 @@ def dmrt_destroy(h):
     load().dmrt_destroy(h)
 
 
+def dmrt_slab_workspace_size(p: Params, rows: int) -> int:
+    n = ctypes.c_size_t()
+    _check(load().dmrt_slab_workspace_size(ctypes.byref(p), int(rows), ctypes.byref(n)))
+    return n.value
+
+
+def dmrt_create_slab(p: Params, y0: int, rows: int, theta0, workspace_ptr: int, workspace_bytes: int,
+                     stream_ptr: int):
+    """Context of rows y0 .. y0 + rows - 1 of cavity p; theta0: None or [rows][nx] float64."""
+    h = _VP()
+    th = None
+    if theta0 is not None:
+        th = np.ascontiguousarray(theta0, dtype=np.float64)
+        if th.size != p.nx * rows:
+            raise ValueError("theta0 must hold nx * rows values")
+    _check(load().dmrt_create_slab(ctypes.byref(p), int(y0), int(rows), _dptr(th), _VP(workspace_ptr),
+                                   workspace_bytes, _VP(stream_ptr), ctypes.byref(h)))
+    return h
+
+
+def dmrt_slab_halo_bytes(h) -> int:
+    n = ctypes.c_size_t()
+    _check(load().dmrt_slab_halo_bytes(h, ctypes.byref(n)), h)
+    return n.value
+
+
+def dmrt_slab_pack(h, to_below_ptr: int, to_above_ptr: int):
+    _check(load().dmrt_slab_pack(h, _VP(to_below_ptr or None), _VP(to_above_ptr or None)), h)
+
+
+def dmrt_slab_unpack(h, from_below_ptr: int, from_above_ptr: int):
+    _check(load().dmrt_slab_unpack(h, _VP(from_below_ptr or None), _VP(from_above_ptr or None)), h)
+
+
+def dmrt_slab_step(h, to_below_ptr: int, to_above_ptr: int):
+    _check(load().dmrt_slab_step(h, _VP(to_below_ptr or None), _VP(to_above_ptr or None)), h)
+
+
 # ---- convenience object --------------------------------------------------------
 
 def make_params(nx, ny, Ra, Pr, alpha=0.1, Ma=0.0, theta_hot=0.5, theta_cold=-0.5,
@@ -462,6 +508,54 @@ class Cavity2D:
             self.close()
         except Exception:
             pass
+
+
+class Slab(Cavity2D):
+    """Rows y0 .. y0 + rows - 1 of the cavity ``params`` as a context with two
+    halo rows, plus its four face messages (torch uint8 device tensors of
+    ``halo_bytes`` each): ``to_below`` / ``to_above`` (what this slab sends) and
+    ``from_below`` / ``from_above`` (what it receives)."""
+
+    def __init__(self, params: Params, y0: int, rows: int, theta0=None, device="cuda", stream=None,
+                 theta_hot_profile=None):
+        import torch
+
+        self.p = params
+        self.nx, self.ny = params.nx, int(rows)
+        self.y0, self.H = int(y0), params.ny
+        self.device = torch.device(device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = dmrt_slab_workspace_size(params, rows)
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.h = dmrt_create_slab(params, y0, rows, theta0, self.workspace.data_ptr(), nbytes,
+                                  self.stream.cuda_stream)
+        self.consts = dmrt_get_consts(self.h)
+        self.launch = dmrt_get_launch(self.h).as_dict()
+        self.halo_bytes = dmrt_slab_halo_bytes(self.h)
+        self.has_below = self.y0 > 0
+        self.has_above = self.y0 + self.ny < self.H
+        mk = lambda: torch.zeros(self.halo_bytes, dtype=torch.uint8, device=self.device)  # noqa: E731
+        self.to_below, self.to_above, self.from_below, self.from_above = mk(), mk(), mk(), mk()
+        if theta_hot_profile is not None:
+            dmrt_set_wall_profiles(self.h, hot=theta_hot_profile)
+
+    def _ptr(self, t, use):
+        return t.data_ptr() if use else 0
+
+    def pack(self):
+        dmrt_slab_pack(self.h, self._ptr(self.to_below, self.has_below), self._ptr(self.to_above, self.has_above))
+
+    def unpack(self):
+        dmrt_slab_unpack(self.h, self._ptr(self.from_below, self.has_below),
+                         self._ptr(self.from_above, self.has_above))
+
+    def step_one(self):
+        """One time step, then the new boundary rows packed into to_below / to_above."""
+        dmrt_slab_step(self.h, self._ptr(self.to_below, self.has_below), self._ptr(self.to_above, self.has_above))
+
+    def finish(self):
+        """Sum the last step's Nusselt rows into the ring (dmrt_step(c, 0))."""
+        dmrt_step(self.h, 0)
 
 
 class _Member(Cavity2D):
