@@ -450,10 +450,20 @@ typedef struct dmrt_batch dmrt_batch;
  * the groups one after another, each for all of the call's steps with
  * launches over its own cavities: a group small enough for the L2 cache
  * (e.g. 32 to 96 MB of the GB300's 126 MB) is read from and written to L2
- * between its steps. Every cavity's results are the same bits either way. */
+ * between its steps. Every cavity's results are the same bits either way.
+ * steps_per_launch: 0 or 1 = one launch per time step (graphs of graph_steps
+ * launches). K > 1 (even) = a persistent kernel advances every cavity of a
+ * group by K steps in one launch, with no grid-wide barrier between the steps:
+ * a cavity's next step starts as soon as that cavity's previous step is
+ * complete (a per-cavity counter, acquired before the tensor copies of the
+ * next step; bounded waits, DMRT_E_TIMEOUT on expiry); graphs hold two such
+ * launches. Compiled multi-step tiles: FP32 (1,2,2) (2,1,2) (2,2,2) (2,2,3)
+ * (4,2,2) (4,4,2); MIXED, both roundings, (2,2,2) (4,2,2) (4,4,2). The same
+ * bits as one launch per step. */
 typedef struct {
     int32_t tma_npt, tma_rows, tma_stages, graph_steps;
     int64_t group_bytes;
+    int32_t steps_per_launch;
 } dmrt_batch_opts;
 
 /* Device workspace for a batch of n cavities (the members' workspaces plus the

@@ -1662,6 +1662,8 @@ struct BatchGroup {
     int grid;
     int* d_ib;             // first item of each of its cavities, then the total (count + 1 entries)
     unsigned* d_ctr;       // its two work-pool counters (by launch parity)
+    unsigned* d_sync;      // multi-step launches: two sets of (queue counter, done[], ready[])
+    int mgrid;             // blocks of a multi-step launch
     cudaGraphExec_t graph[2];
 };
 
@@ -1678,6 +1680,8 @@ struct dmrt_batch {
     int npt, R, S, block;
     size_t smem;
     const void* func;
+    int K;                 // steps per launch (1: one launch per step; else the multi-step kernel)
+    const void* mfunc;     // the multi-step kernel (K > 1)
     int parity;
     long long t;
     int graph_len;
@@ -1688,7 +1692,7 @@ namespace {
 
 struct BatchLayout {
     std::vector<size_t> off, bytes;
-    size_t off_cav, off_maps, off_ib, off_err, total;
+    size_t off_cav, off_maps, off_ib, off_err, off_sync, total;
 };
 
 int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
@@ -1726,6 +1730,8 @@ int batch_layout(const dmrt_params* arr, int32_t n, BatchLayout* L) {
     o += align256((size_t)(2 * n) * sizeof(int));
     L->off_err = o;  // the error word, then two pool counters per group
     o += align256(sizeof(unsigned) * (size_t)(1 + 2 * n));
+    L->off_sync = o;  // multi-step launches: two synchronisation sets per group (at most n groups)
+    o += align256(sizeof(unsigned) * (size_t)(2 * (dmrt::mstep_set_words(0) + 2) * n));
     L->total = o;
     return DMRT_OK;
 }
@@ -1774,7 +1780,57 @@ int batch_launch(dmrt_batch* b, const BatchGroup& G, int parity) {
     return DMRT_OK;
 }
 
+// Arguments of a multi-step launch of group G (K steps from buffer `parity`,
+// synchronisation set lp).
+struct MstepArgs {
+    const dmrt::BatchCavity* cav;
+    const CUtensorMap* maps;
+    const int* ib;
+    int n_cav, per_step, K, parity;
+    unsigned *err, *sync;
+    int lp;
+    MstepArgs(const dmrt_batch* b, const BatchGroup& G, int parity_, int lp_)
+        : cav(b->d_cav + G.first), maps(b->d_maps + (size_t)G.first * 2 * dmrt::kBatchMaps), ib(G.d_ib),
+          n_cav(G.count), per_step(G.total_items), K(b->K), parity(parity_), err(b->d_err), sync(G.d_sync),
+          lp(lp_) {}
+    void fill(void** p) {
+        p[0] = &cav, p[1] = &maps, p[2] = &ib, p[3] = &n_cav, p[4] = &per_step, p[5] = &K, p[6] = &parity;
+        p[7] = &err, p[8] = &sync, p[9] = &lp;
+    }
+};
+
+// Graph of two multi-step launches (synchronisation sets 0 then 1), 2 K steps
+// from buffer `from` (K even: each launch ends in the buffer it started from).
+int batch_build_mstep_graph(dmrt_batch* b, BatchGroup& G, int from) {
+    cudaGraph_t g;
+    BCK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+    cudaGraphNode_t prev = nullptr;
+    MstepArgs a[2] = {MstepArgs(b, G, from, 0), MstepArgs(b, G, from, 1)};
+    for (int i = 0; i < 2; ++i) {
+        cudaKernelNodeParams kp = {};
+        void* params[10];
+        a[i].fill(params);
+        kp.func = const_cast<void*>(b->mfunc);
+        kp.gridDim = dim3(G.mgrid);
+        kp.blockDim = dim3(b->block);
+        kp.sharedMemBytes = (unsigned)b->smem;
+        kp.kernelParams = params;
+        cudaGraphNode_t node;
+        cudaError_t e = add_step_node(g, prev, &kp, &node);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return batch_cuda_fail(b, e, "cudaGraphAddKernelNode");
+        }
+        prev = node;
+    }
+    cudaError_t e = cudaGraphInstantiate(&G.graph[from], g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return batch_cuda_fail(b, e, "cudaGraphInstantiate");
+    return DMRT_OK;
+}
+
 int batch_build_graph(dmrt_batch* b, BatchGroup& G, int from) {
+    if (b->K > 1) return batch_build_mstep_graph(b, G, from);
     cudaGraph_t g;
     BCK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
     cudaGraphNode_t prev = nullptr;
@@ -1839,7 +1895,12 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     const int npt = opts && opts->tma_npt > 0 ? opts->tma_npt : (mixed_def ? 4 : 2);
     const int R = opts && opts->tma_rows > 0 ? opts->tma_rows : 2;
     const int S = opts && opts->tma_stages > 0 ? opts->tma_stages : 2;
-    const int glen = opts && opts->graph_steps > 0 ? opts->graph_steps : 64;
+    const int K = opts && opts->steps_per_launch > 1 ? opts->steps_per_launch : 1;
+    if (K > 1 && K % 2) {
+        set_err(nullptr, "steps_per_launch must be even");
+        return DMRT_E_ARG;
+    }
+    const int glen = K > 1 ? 2 * K : (opts && opts->graph_steps > 0 ? opts->graph_steps : 64);
     if (glen % 2) {
         set_err(nullptr, "graph_steps must be even");
         return DMRT_E_ARG;
@@ -1858,6 +1919,20 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
                 npt, R, S);
         return DMRT_E_ARG;
     }
+    const void* mfunc = nullptr;
+    if (K > 1) {
+        int nm = 0;
+        const dmrt::TmaVariant* mv = dmrt::tma_variants_batch_mstep(&nm);
+        for (int i = 0; i < nm; ++i)
+            if (mv[i].storage == storage && mv[i].rounding == resolved_rounding(arr[0]) && mv[i].npt == npt &&
+                mv[i].R == R && mv[i].S == S)
+                mfunc = mv[i].func;
+        if (!mfunc) {
+            set_err(nullptr, "no multi-step batched tile with %d nodes/thread, %d rows, %d stages is compiled in "
+                             "for this storage", npt, R, S);
+            return DMRT_E_ARG;
+        }
+    }
     dmrt_batch* b = new (std::nothrow) dmrt_batch();
     if (!b) {
         set_err(nullptr, "out of host memory");
@@ -1873,6 +1948,8 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     b->parity = 0;
     b->t = 0;
     b->graph_len = glen;
+    b->K = K;
+    b->mfunc = mfunc;
     b->err[0] = 0;
     auto fail = [&](int code) {
         std::snprintf(g_create_error, sizeof g_create_error, "%s", b->err[0] ? b->err : g_create_error);
@@ -1976,6 +2053,8 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     b->d_maps = reinterpret_cast<CUtensorMap*>(b->ws + L.off_maps);
     b->d_err = reinterpret_cast<unsigned*>(b->ws + L.off_err);
     int* d_ib_all = reinterpret_cast<int*>(b->ws + L.off_ib);
+    unsigned* d_sync_all = reinterpret_cast<unsigned*>(b->ws + L.off_sync);
+    size_t sync_words = 0;
     std::vector<int> ib;
     {
         long long acc = 0;
@@ -1994,6 +2073,8 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
             BatchGroup& G = b->groups[g];
             G.d_ib = d_ib_all + ib.size();
             G.d_ctr = b->d_err + 1 + 2 * g;
+            G.d_sync = d_sync_all + sync_words;
+            sync_words += 2 * (size_t)dmrt::mstep_set_words(G.count);
             int it = 0;
             for (int i = G.first; i < G.first + G.count; ++i) {
                 cav[i].item_base = it;
@@ -2012,6 +2093,7 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ib_all, ib.data(), ib.size() * sizeof(int), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_err, 0, sizeof(unsigned) * (1 + 2 * b->groups.size()), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_sync_all, 0, sizeof(unsigned) * sync_words, b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
     if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch tables"));
     // Launch shape: persistent grid of resident blocks.
@@ -2027,7 +2109,20 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         batch_set_err(b, "batched tile does not fit on an SM");
         return fail(DMRT_E_ARG);
     }
+    int mper_sm = 0;
+    if (K > 1) {
+        e = cudaFuncSetAttribute(b->mfunc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&mper_sm, b->mfunc, b->block, b->smem);
+        if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "multi-step launch shape"));
+        if (mper_sm < 1) {
+            batch_set_err(b, "multi-step batched tile does not fit on an SM");
+            return fail(DMRT_E_ARG);
+        }
+    }
     for (BatchGroup& G : b->groups) {
+        // Multi-step launches: every block resident; each takes items from the queue.
+        G.mgrid = (int)std::min<long long>((long long)G.total_items * K, (long long)sms * std::max(mper_sm, 1));
         G.grid = (int)std::min<long long>(G.total_items, (long long)sms * per_sm);
         // Three quarters of the items are split statically, the rest are drawn at run time.
         G.static_per_block = (int)((long long)G.total_items * 3 / 4 / G.grid);

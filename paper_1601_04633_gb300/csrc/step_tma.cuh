@@ -160,20 +160,22 @@ __device__ __forceinline__ void vec_get(const E* p, float (&o)[N]) {
     for (int e = 0; e < N; ++e) o[e] = to_f(q.v[e]);
 }
 
+// Global loads through L2 (ld.global.cg), not the non-coherent cache: the
+// multi-step batched kernel reads state written earlier in the same launch.
 template <typename E, int N>
 __device__ __forceinline__ void vec_ldg(const E* p, float (&o)[N], float shift) {
     Pack<E, N> q;
     if constexpr (sizeof(Pack<E, N>) == 16) {
-        const uint4 r = __ldg(reinterpret_cast<const uint4*>(p));
+        const uint4 r = __ldcg(reinterpret_cast<const uint4*>(p));
         q = *reinterpret_cast<const Pack<E, N>*>(&r);
     } else if constexpr (sizeof(Pack<E, N>) == 8) {
-        const uint2 r = __ldg(reinterpret_cast<const uint2*>(p));
+        const uint2 r = __ldcg(reinterpret_cast<const uint2*>(p));
         q = *reinterpret_cast<const Pack<E, N>*>(&r);
     } else if constexpr (sizeof(Pack<E, N>) == 4) {
-        const unsigned r = __ldg(reinterpret_cast<const unsigned*>(p));
+        const unsigned r = __ldcg(reinterpret_cast<const unsigned*>(p));
         q = *reinterpret_cast<const Pack<E, N>*>(&r);
     } else {
-        const unsigned short r = __ldg(reinterpret_cast<const unsigned short*>(p));
+        const unsigned short r = __ldcg(reinterpret_cast<const unsigned short*>(p));
         q = *reinterpret_cast<const Pack<E, N>*>(&r);
     }
 #pragma unroll

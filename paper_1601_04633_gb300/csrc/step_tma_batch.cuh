@@ -190,3 +190,267 @@ static __global__ void nu_finalize_batch_kernel(const BatchCavity* __restrict__ 
 }
 
 }  // namespace dmrt
+
+namespace dmrt {
+
+// ---- batched sweep, several time steps per launch ------------------------------
+// The cavities of a batch are independent: step s + 1 of cavity c needs only
+// cavity c's step s to be complete (its pull reads neighbouring rows of that
+// state, and it overwrites the buffer step s read). So one launch can advance
+// every cavity by K steps without a grid-wide barrier between them: the work
+// list is every (step, cavity, item) in step-major order, handed out one item
+// at a time from a queue counter, and an item of step s + 1 of cavity c is
+// loaded only once cavity c's step s is complete. Blocks keep their copy
+// pipeline full across step boundaries, and no launch boundary (ramp, tail,
+// launch gap) sits between steps.
+//
+// Progress: a block waits for a dependency only when it has computed every
+// item it has loaded (the producer first tries without waiting; if the next
+// item's cavity is not ready it lets the block compute the current item and
+// waits after that). A waited-for step is always earlier than the step of the
+// waiting block's earliest held item, and every item of an earlier step was
+// taken from the queue by a running block, so no wait can be circular. Every
+// wait is bounded (%globaltimer); on expiry the launch records kErrTimeout.
+//
+// Completion of a cavity's step: every thread fences its stores, the block
+// barrier follows, thread 0 counts the item (done[c]); the block completing
+// the cavity's step sums the step's per-row Nusselt numbers in warp 0 (the
+// same fixed order as nu_finish_prev: partial p over rows p, p + 256, ...;
+// lane l adds its partials q = 0..7, then a butterfly), appends the mean to
+// the cavity's ring, and publishes ready[c] = s + 1 (a fence, then the store).
+// The consumer of ready[c] acquires it and orders the following tensor copies
+// after it with a proxy fence. Loads of the wall columns (ld.global.cg in
+// process_item) bypass the non-coherent cache, since the state they read was
+// written by this launch.
+//
+// Synchronisation words: two sets of (queue counter, done[n], ready[n]), by
+// launch parity lp; a launch zeroes the other set for the next one.
+__host__ __device__ constexpr int mstep_set_words(int n_cav) { return 32 + 2 * n_cav; }
+
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Waits (bounded) until *p >= want; acquire: later reads see what the publisher wrote before.
+__device__ __forceinline__ bool wait_at_least(const unsigned* p, unsigned want,
+                                              unsigned long long limit_ns = kWaitLimitNs) {
+    if (*reinterpret_cast<const volatile unsigned*>(p) >= want) {
+        __threadfence();
+        return true;
+    }
+    const unsigned long long t0 = global_ns();
+    while (*reinterpret_cast<const volatile unsigned*>(p) < want) {
+        if (global_ns() - t0 > limit_ns) return false;
+        __nanosleep(64);
+    }
+    __threadfence();
+    return true;
+}
+
+template <typename L, int NPT, int R, int S, bool SR = false>
+__global__ void __launch_bounds__(R * (256 / NPT))
+    step_tma_batch_mstep_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
+                                const int* __restrict__ item_base, int n_cav, int items_per_step, int K,
+                                int parity, unsigned* batch_err, unsigned* sync, int lp) {
+    using Ef = typename L::Ef;
+    using Eg = typename L::Eg;
+    constexpr size_t kStageBytes = tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* stages = smem_raw;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);
+    // (cavity, strip, row block, step) of each stage; cavity -1: no more items, -2: abort.
+    __shared__ int4 stage_item[S];
+    constexpr int HALO = L::kHalo;
+    const int tid = threadIdx.x;
+    const int words = mstep_set_words(n_cav);
+    unsigned* set = sync + (size_t)lp * words;
+    unsigned* ctr = set;
+    unsigned* done = set + 32;
+    unsigned* ready = set + 32 + n_cav;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s], 1);
+        mbar_fence_init();
+    }
+    grid_dep_wait();
+    grid_dep_launch();
+    if (__syncthreads_or(tid == 0 && (*reinterpret_cast<volatile unsigned*>(batch_err) & kErrTimeout))) return;
+    {
+        // The previous launch used the other set and has completed: zero it for the next one.
+        unsigned* other = sync + (size_t)(1 - lp) * words;
+        for (int i = blockIdx.x * blockDim.x + tid; i < words; i += gridDim.x * blockDim.x) other[i] = 0u;
+    }
+    const int total = K * items_per_step;
+
+    // Producer state (thread 0): the next item to issue (a queue index, or
+    // >= total for the end), one reserved after it, and the count issued.
+    int next_g = 0, resv_g = 0, issued = 0;
+    if (tid == 0) {
+        next_g = (int)atomicAdd(ctr, 1u);
+        resv_g = next_g < total ? (int)atomicAdd(ctr, 1u) : total;
+    }
+    auto decode = [&](int g, int& c, int& st, int& local) {
+        st = g / items_per_step;
+        const int r = g - st * items_per_step;
+        int lo = 0, hi = n_cav - 1;  // last cavity whose first item <= r
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(item_base + mid) <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        c = lo;
+        local = r - __ldg(item_base + c);
+    };
+    // Issue the next item into stage `s` if its cavity's previous step is
+    // complete (wait: spin up to the limit; else one look). Returns false if
+    // not issued (not ready, or the wait expired: *expired then true).
+    auto try_issue = [&](int s, bool wait, bool* expired) -> bool {
+        if (next_g >= total) {
+            stage_item[s] = make_int4(-1, 0, 0, 0);
+            mbar_arrive(&bars[s]);  // completes the phase with nothing to load
+            return true;
+        }
+        int c, st, local;
+        decode(next_g, c, st, local);
+        if (st > 0) {
+            const unsigned* rp = ready + c;
+            if (wait) {
+                if (!wait_at_least(rp, (unsigned)st)) {
+                    *expired = true;
+                    stage_item[s] = make_int4(-2, 0, 0, 0);
+                    mbar_arrive(&bars[s]);
+                    return false;
+                }
+            } else {
+                if (*reinterpret_cast<const volatile unsigned*>(rp) < (unsigned)st) return false;
+                __threadfence();
+            }
+            fence_proxy_async_global();  // the tensor copies below read what the publisher's blocks wrote
+        }
+        const BatchCavity& bc = cav[c];
+        const int rb = local / bc.n_strips;
+        const int strip = local - rb * bc.n_strips;
+        stage_item[s] = make_int4(c, strip, rb, st);
+        const int src = parity ^ (st & 1);
+        const int x = strip * bc.W - HALO;
+        const int j0 = rb * bc.RC;
+        const CUtensorMap* m = maps + ((size_t)c * 2 + src) * kBatchMaps;
+        unsigned char* sp = stages + (size_t)s * kStageBytes;
+        mbar_expect_tx(&bars[s], bc.stage_bytes);
+        if constexpr (!L::kSplit) {
+            Ef* e = reinterpret_cast<Ef*>(sp);
+            tma_load_3d(e, m, x, j0, kGroupZ, &bars[s]);
+            tma_load_3d(e + bc.so.zP, m + 1, x, j0 - 1, kGroupP, &bars[s]);
+            tma_load_3d(e + bc.so.zN, m + 1, x, j0 + 1, kGroupN, &bars[s]);
+        } else {
+            Ef* f = reinterpret_cast<Ef*>(sp);
+            Eg* g = reinterpret_cast<Eg*>(sp + bc.so.g_bytes);
+            tma_load_3d(f, m, x, j0, 0, &bars[s]);
+            tma_load_3d(f + bc.so.zP, m, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(f + bc.so.zN, m, x, j0 + 1, 6, &bars[s]);
+            tma_load_3d(g, m + 1, x, j0, 0, &bars[s]);
+            tma_load_3d(g + bc.so.gP, m + 2, x, j0 - 1, 3, &bars[s]);
+            tma_load_3d(g + bc.so.gN, m + 2, x, j0 + 1, 4, &bars[s]);
+        }
+        next_g = resv_g;
+        resv_g = next_g < total ? (int)atomicAdd(ctr, 1u) : total;
+        return true;
+    };
+
+    bool timed_out = false;
+    uint32_t phase = 0;
+    int k = 0;
+    for (int s = 0;; ++k) {
+        bool expired = false;
+        if (tid == 0) {
+            // Items k .. k + S - 1 may be in flight; their stages were released
+            // by the barriers that ended items k - S .. k - 1. Item k itself is
+            // waited for only when it is not loaded yet: then every item this
+            // block took is computed, and it holds nothing another block needs.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            while (issued < k + S) {
+                if (!try_issue(issued % S, issued == k, &expired)) break;
+                ++issued;
+            }
+        }
+        const bool ok = mbar_wait_bounded(&bars[s], phase);
+        const int4 w = stage_item[s];
+        const bool work = ok && w.x >= 0;
+        const BatchCavity& bc = cav[work ? w.x : 0];
+        const int tpr = bc.tpr;
+        const int rg = tid / tpr;
+        const int t = tid - rg * tpr;
+        const int src = parity ^ (w.w & 1);
+        unsigned salt = 0;
+        if constexpr (SR)
+            if (work)
+                salt = hash32((unsigned)(__ldcg(bc.args[parity].step_in) + w.w) * 0x9e3779b9u + 0x632be5abu);
+        process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, bc.args[src], bc.K, work ? w.y : 1, w.z, rg, t,
+                                 work, salt, bc.W, bc.WB, bc.RC, bc.so);
+        __threadfence();  // this thread's stores (state, Nusselt rows) before the item is counted
+        if (__syncthreads_count(!ok || w.x == -2)) {
+            timed_out = true;
+            break;
+        }
+        if (w.x < 0) break;
+        // Count the item; the block completing the cavity's step sums its Nusselt rows.
+        if (tid < 32) {
+            unsigned last = 0;
+            if (tid == 0) {
+                const unsigned want = (unsigned)((w.w + 1) * (bc.n_strips * bc.n_rowblocks));
+                last = atomicAdd(done + w.x, 1u) + 1u == want;
+            }
+            last = __shfl_sync(kFull, last, 0);
+            if (last) {
+                __threadfence();
+                const StepArgs& A = bc.args[src];
+                double acc8[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    double acc = 0.0;
+                    int r = tid + 32 * q;
+                    for (; r + 3 * 256 < A.ny; r += 4 * 256) {
+                        double v[4];
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) v[i] = __ldcg(A.nu_rows + r + 256 * i);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) acc += v[i];
+                    }
+                    for (; r < A.ny; r += 256) acc += __ldcg(A.nu_rows + r);
+                    acc8[q] = acc;
+                }
+                double sum = 0.0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sum += acc8[q];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
+                if (tid == 0) {
+                    const long long t0 = __ldcg(bc.args[parity].step_in);
+                    const double mean = sum / A.nu_div;
+                    A.nu_ring[(t0 + w.w) % A.cap] = mean;
+                    *A.nu_last = mean;
+                    if (w.w == K - 1) {
+                        // After the launch's K steps (K even) the state is back in
+                        // buffer `parity`, whose step counter slot now holds t0 + K;
+                        // every step's rows are summed, so nothing is pending.
+                        *const_cast<long long*>(bc.args[parity].step_in) = t0 + K;
+                        *A.pending = 0u;
+                    }
+                    __threadfence();
+                    *reinterpret_cast<volatile unsigned*>(ready + w.x) = (unsigned)(w.w + 1);
+                }
+            }
+        }
+        if (++s == S) {
+            s = 0;
+            phase ^= 1u;
+        }
+    }
+    if (timed_out && tid == 0) {
+        atomicOr(batch_err, kErrTimeout);
+        // Wait (bounded) for the copies this block issued before releasing its shared memory.
+        for (int q = k; q < issued; ++q) mbar_wait_bounded(&bars[q % S], (uint32_t)((q / S) & 1));
+    }
+}
+
+}  // namespace dmrt

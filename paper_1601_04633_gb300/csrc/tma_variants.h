@@ -20,5 +20,6 @@ const TmaVariant* tma_variants_fp16(int* n);
 const TmaVariant* tma_variants_bf16(int* n);
 const TmaVariant* tma_variants_mixed(int* n);  // float16 flow, float32 thermal
 const TmaVariant* tma_variants_batch(int* n);  // batched sweep kernels
+const TmaVariant* tma_variants_batch_mstep(int* n);  // batched sweep, several steps per launch
 
 }  // namespace dmrt

@@ -79,42 +79,56 @@ def _cache_put(path, key, value):
 # buffers per group; 0: one group, every cavity in every launch). The GB300's
 # L2 holds about 126 MB.
 GROUP_BYTES = [0, 24 << 20, 40 << 20, 64 << 20, 96 << 20]
+# Tiles compiled for the multi-step batched kernel (several steps per launch).
+BATCH_MSTEP_TILES = {0: [(1, 2, 2), (2, 1, 2), (2, 2, 2), (2, 2, 3), (4, 2, 2), (4, 4, 2)],
+                     3: [(2, 2, 2), (4, 2, 2), (4, 4, 2)]}
+STEPS_PER_LAUNCH = [1, 8, 32]
 
 
 def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0, rounding=0,
-               group_bytes=(0,), finalists=3):
-    """Pick the batched kernel's tile, and its cavity-group size, for these
-    cavities (storage 0: float32, 3: mixed). Every tile is timed with the first
-    group size; the `finalists` fastest tiles are then timed with each other
-    group size. Returns {"opts": {...}, "mlups": best, "trials": [...]}."""
+               group_bytes=(0,), steps_per_launch=(1,), finalists=3):
+    """Pick the batched kernel's tile, cavity-group size and steps per launch
+    for these cavities (storage 0: float32, 3: mixed). Every tile is timed with
+    the first group size and one step per launch; the `finalists` fastest tiles
+    are then timed with each other combination (steps per launch > 1 only for
+    the tiles the multi-step kernel is compiled for). Returns {"opts": {...},
+    "mlups": best, "trials": [...]}."""
     from . import dmrt as D
 
-    key = _key("batch", [(c.nx, c.ny) for c in cavities], f"{steps}-{storage}-{rounding}-{list(group_bytes)}")
+    key = _key("batch", [(c.nx, c.ny) for c in cavities],
+               f"{steps}-{storage}-{rounding}-{list(group_bytes)}-{list(steps_per_launch)}")
     hit = _cache_get(cache, key)
     if hit:
         return hit
     nodes = sum(c.nx * c.ny for c in cavities)
     trials = []
 
-    def trial(npt, R, S, g, gb):
-        opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g, group_bytes=gb)
+    def trial(npt, R, S, g, gb, K):
+        opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g, group_bytes=gb, steps_per_launch=K)
+        glen = 2 * K if K > 1 else g
         # The warm-up covers one whole graph, so its instantiation is not timed.
-        b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + g + 8, storage=storage,
+        b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + glen + 8, storage=storage,
                                 rounding=rounding)
-        sec = _time_steps(b.step, steps, max(warmup, g))
+        sec = _time_steps(b.step, steps, max(warmup, glen))
         b.check()
         trials.append({"opts": opts, "mlups": nodes * steps / sec / 1e6, "groups": b.groups})
         b.close()
 
     for npt, R, S in (tiles or BATCH_TILES):
         for g in graph_steps:
-            trial(npt, R, S, g, group_bytes[0])
-    if len(group_bytes) > 1:
+            trial(npt, R, S, g, group_bytes[0], 1)
+    if len(group_bytes) > 1 or len(steps_per_launch) > 1:
         top = sorted(trials, key=lambda r: -r["mlups"])[:finalists]
         for t in top:
             o = t["opts"]
-            for gb in group_bytes[1:]:
-                trial(o["tma_npt"], o["tma_rows"], o["tma_stages"], o["graph_steps"], gb)
+            tile = (o["tma_npt"], o["tma_rows"], o["tma_stages"])
+            for K in steps_per_launch:
+                if K > 1 and tile not in BATCH_MSTEP_TILES.get(storage, []):
+                    continue
+                for gb in group_bytes:
+                    if (gb, K) == (group_bytes[0], 1):
+                        continue
+                    trial(*tile, o["graph_steps"], gb, K)
     best = max(trials, key=lambda r: r["mlups"])
     out = {"opts": best["opts"], "mlups": best["mlups"], "trials": trials}
     _cache_put(cache, key, out)
@@ -162,13 +176,16 @@ def main():
     ap.add_argument("--graph-steps", type=int, default=64, help="steps per CUDA graph (batched sweep)")
     ap.add_argument("--group-mb", type=int, nargs="*", default=[0],
                     help="cavity-group sizes to try, MB of both buffers (batched sweep; 0: one group)")
+    ap.add_argument("--steps-per-launch", type=int, nargs="*", default=[1],
+                    help="steps per launch to try (batched sweep; 1: one launch per step)")
     ap.add_argument("--cache", default=None)
     args = ap.parse_args()
     tiles = [tuple(args.tile)] if args.tile else None
     if args.batch:
         print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, tiles=tiles,
                                     graph_steps=(args.graph_steps,), cache=args.cache, storage=args.storage,
-                                    rounding=args.rounding, group_bytes=[m << 20 for m in args.group_mb]),
+                                    rounding=args.rounding, group_bytes=[m << 20 for m in args.group_mb],
+                                    steps_per_launch=args.steps_per_launch),
                          indent=1))
     if args.single:
         cav = inputs.Cavity(args.single, args.single, 1e7, 0.001, seed=5)

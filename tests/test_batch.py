@@ -89,6 +89,57 @@ def test_cavity_groups_give_the_same_bits(D, storage, group_kb):
     grp.close()
 
 
+MSTEP_TILES = {0: [(1, 2, 2), (2, 1, 2), (2, 2, 2), (2, 2, 3), (4, 2, 2), (4, 4, 2)],
+               3: [(2, 2, 2), (4, 2, 2), (4, 4, 2)]}
+
+
+@pytest.mark.parametrize("storage,rounding", [(0, 0), (3, 0), (3, 1)], ids=["fp32", "mixed", "mixed_sr"])
+@pytest.mark.parametrize("K", [2, 8])
+def test_multistep_launches_give_the_same_bits(D, storage, rounding, K):
+    # K steps per launch, each cavity's next step gated by its own previous step
+    # only: exactly the results of one launch per step, for every compiled tile,
+    # over calls of odd and even lengths (graphs of 2K steps, single launches
+    # for the rest), with and without cavity groups.
+    cavs = _uneven()
+    for npt, R, S in MSTEP_TILES[storage]:
+        base = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=16)
+        ref = D.Batch.from_inputs(cavs, opts=base, nu_capacity=128, storage=storage, rounding=rounding)
+        runs = [D.Batch.from_inputs(cavs, opts=dict(base, steps_per_launch=K), nu_capacity=128, storage=storage,
+                                    rounding=rounding),
+                D.Batch.from_inputs(cavs, opts=dict(base, steps_per_launch=K, group_bytes=4000 << 10),
+                                    nu_capacity=128, storage=storage, rounding=rounding)]
+        for n in (37, 16, 3):
+            for b in [ref] + runs:
+                b.step(n)
+        for b in [ref] + runs:
+            b.check()
+        for b in runs:
+            for i in range(len(cavs)):
+                a, m = ref.members[i], b.members[i]
+                assert m.steps_done == a.steps_done == 56
+                assert np.array_equal(m.get_state(), a.get_state()), (npt, R, S, i)
+                assert np.array_equal(m.nusselt(56)[2], a.nusselt(56)[2]), (npt, R, S, i)
+            b.close()
+        ref.close()
+
+
+def test_multistep_sweep_member_matches_single_context(D):
+    # The 64-cavity sweep, 8 steps per launch: sampled members against their own
+    # contexts stepped alone.
+    cavs = inputs.batch_sweep()
+    b = D.Batch.from_inputs(cavs, opts=dict(tma_npt=2, tma_rows=2, tma_stages=2, steps_per_launch=8),
+                            nu_capacity=64)
+    b.step(50)
+    b.check()
+    for i in (0, 17, 63):
+        single = D.Cavity2D.from_inputs(cavs[i], nu_capacity=64)
+        single.step(50)
+        assert np.array_equal(b.members[i].get_state(), single.get_state()), i
+        assert np.array_equal(b.members[i].nusselt(50)[2], single.nusselt(50)[2]), i
+        single.close()
+    b.close()
+
+
 def test_batch_parity_rule_and_member_stepping(D):
     cavs = _uneven()[:3]
     b = D.Batch.from_inputs(cavs, nu_capacity=64)

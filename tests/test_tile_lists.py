@@ -19,8 +19,8 @@ ROUNDING = {"DMRT_ROUND_NEAREST": 0, "DMRT_ROUND_STOCHASTIC": 1}
 ENTRY = re.compile(r"\{(DMRT_\w+), (DMRT_ROUND_\w+), (\d+), (\d+), (\d+), ([01]), \(const void\*\)(\w+)<(.*)>\}")
 
 
-def _tables():
-    single, batch = set(), set()
+def _tables(with_mstep=False):
+    single, batch, mstep = set(), set(), set()
     for path in sorted(glob.glob(os.path.join(CSRC, "tma_*.cu"))):
         with open(path) as fh:
             for line in fh:
@@ -32,8 +32,13 @@ def _tables():
                 # The template arguments after the layout repeat (npt, R, S).
                 rest = re.sub(r"^\w+(<[^>]*>)?,\s*", "", targs).split(",")
                 assert [int(x) for x in rest[:3]] == [int(npt), int(R), int(S)], line
-                (batch if kernel == "step_tma_batch_kernel" else single).add(key)
-    return single, batch
+                if kernel == "step_tma_batch_kernel":
+                    batch.add(key)
+                elif kernel == "step_tma_batch_mstep_kernel":
+                    mstep.add(key)
+                else:
+                    single.add(key)
+    return (single, batch, mstep) if with_mstep else (single, batch)
 
 
 def test_tables_parse():
@@ -58,6 +63,17 @@ def test_batch_tuner_tiles_are_compiled_for_every_batch_storage():
         compiled = {k[2:] for k in batch if k[:2] == (st, rd)}
         assert compiled == set(map(tuple, tune.BATCH_TILES)), (st, rd)
     assert {k[:2] for k in batch} == {(0, 0), (3, 0), (3, 1)}
+
+
+def test_multistep_batch_tiles_match_the_tuner_and_have_single_step_twins():
+    # Every multi-step tile the tuner may pick is compiled, and also compiled as
+    # a one-step-per-launch tile (a batch call runs its remainder steps that way).
+    _, batch, mstep = _tables(with_mstep=True)
+    for st, rd in ((0, 0), (3, 0), (3, 1)):
+        compiled = {k[2:] for k in mstep if k[:2] == (st, rd)}
+        assert compiled == set(map(tuple, tune.BATCH_MSTEP_TILES[st])), (st, rd)
+        assert {(st, rd) + t for t in compiled} <= batch
+    assert {k[:2] for k in mstep} == {(0, 0), (3, 0), (3, 1)}
 
 
 def test_default_tiles_are_compiled():
