@@ -11,7 +11,9 @@ so no flush is needed between steps.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl dmrt|reference]
 
 With N > 1 (torchrun) every rank steps its own independent cavity (weak scaling,
-no collective on the data path); timing is the max over ranks.
+no collective on the data path); timing is the max over ranks. The line also
+carries the same cavity split into N y-slabs, one per rank, with one halo-row
+exchange per step (strong scaling).
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -45,6 +47,7 @@ FALLBACK_HBM_GBS = 6800.0
 GATE_STEPS = 20000  # the stated length of the 4096^2 workload; the Nu gate is taken over it
 NU_GATE = 1e-3
 BATCH_MIN_STEPS = 2000  # batched sweeps are timed over at least this many steps
+SLAB_STEPS = 200  # timed steps of the single cavity split over the ranks (N > 1)
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "step_kernel_4096x4096.json")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1601_04633_gb300", "csrc", f)
                   for f in ("lattice.cuh", "step_tma.cuh", "step_direct.cuh")]
@@ -238,6 +241,38 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def slab_split_run(D, dist, cav, rank, ws, args, stream):
+    """One cavity split into ws y-slabs (one per rank), SLAB_STEPS timed steps."""
+    import torch
+
+    from paper_1601_04633_gb300 import slabs
+
+    try:
+        p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, cav.alpha, nu_capacity=SLAB_STEPS + args.warmup)
+        run = slabs.DistributedSlab(dist, p, rank, ws, theta0=cav.theta0())
+        run.step(args.warmup)
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.step(SLAB_STEPS)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        run.slab.check()
+        series = run.nusselt_series(SLAB_STEPS)
+        run.close()
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        return {"value": cav.nx * cav.ny * SLAB_STEPS / (ms / 1e3) / 1e6, "unit": UNIT, "scaling": "strong",
+                "ranks": ws, "steps": SLAB_STEPS, "ms_per_step": ms / SLAB_STEPS,
+                "nu_mean_last": float(series[-1]),
+                "workload": f"one {cav.nx}x{cav.ny} cavity in {ws} y-slabs, one halo-row exchange per step"}
+    except Exception as exc:  # reported on the line; the headline stands on its own
+        return {"error": f"{type(exc).__name__}: {exc}"}
 
 
 def run_dmrt(args):
@@ -482,6 +517,12 @@ def run_dmrt(args):
         secondary["adjoint"] = {"workload": "cavity 128x128 Ra 1e5 Pr 0.01, 10000 steps, J over last 2000",
                                 "forward_s": t_fwd, "adjoint_s": t_adj, "ratio": t_adj / t_fwd,
                                 "J": Jv, "dJ_dRa": dRa, "dJ_dthetaw_norm": float(np.linalg.norm(dth))}
+
+    # With N > 1 ranks: one cavity of the same workload split into N y-slabs, one
+    # per rank, with one halo-row exchange per step over NCCL (strong scaling),
+    # beside the independent replicas of the headline.
+    if dist and not args.no_secondary:
+        secondary["slab_split"] = slab_split_run(D, dist, cav, rank, ws, args, stream)
 
     # End to end through the public C ABI with host buffers: create from a pinned
     # host temperature field (H2D), K steps, then the Nu series and the u, v, theta
