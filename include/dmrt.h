@@ -98,6 +98,13 @@ extern "C" {
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
+/* CLUSTER: for small float32 cavities (both buffers in the shared memory of one
+ * thread-block cluster of up to 16 blocks, e.g. up to 128^2): each dmrt_step
+ * call runs as one launch that keeps the state on chip between steps (one
+ * cluster barrier per step); single steps and the adjoint use the kernel AUTO
+ * picks among the others. The same bits as the other kernels. DMRT_E_ARG at
+ * creation if the cavity does not fit. */
+#define DMRT_KERNEL_CLUSTER 3
 
 /* Wall kinds for the left and right (vertical) walls. Top and bottom are
  * always adiabatic (Eqs. 7-8, 44). */
@@ -119,7 +126,7 @@ typedef struct {
     int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t storage;    /* DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (16-bit and mixed
                            storage run the TMA kernel; arithmetic is float32 in every case) */
-    int32_t kernel;     /* DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT or DMRT_KERNEL_TMA */
+    int32_t kernel;     /* DMRT_KERNEL_AUTO, _DIRECT, _TMA or _CLUSTER */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
     int32_t tma_rows;   /* TMA kernel: rows per work item (0 = the storage's default tile) */
     int32_t tma_stages; /* TMA kernel: pipeline stages (0 = default) */

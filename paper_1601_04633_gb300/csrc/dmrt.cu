@@ -17,6 +17,7 @@
 
 #include "dmrt.h"
 #include "adjoint.cuh"
+#include "step_cluster.cuh"
 #include "step_consts.h"
 #include "step_direct.cuh"
 #include "step_tma.cuh"
@@ -114,6 +115,11 @@ struct dmrt_ctx {
     size_t tma_smem;
     const void* tma_func;
     dmrt::TmaMaps tmaps[2];  // per source buffer: the step kernel's load and store maps
+    // Cluster kernel (runs of steps of a small float32 cavity; single steps and
+    // the adjoint use `kernel`): blocks, rows per block, threads, shared memory.
+    bool cluster;
+    int csize, crows, cthreads;
+    size_t csmem;
     cudaGraphExec_t graph[2];
     int graph_len;
     long long nu_floor;  // ring values of steps before this one are unavailable (after a load)
@@ -548,8 +554,67 @@ void choose_launch(const dmrt_params& p_in, int sms, int* kernel, int* npt_out, 
 }
 
 // Resolve the kernel variant and prepare its launch configuration.
-int setup_kernel(dmrt_ctx* c) {
+// Cluster kernel for runs of steps: float32, a whole cavity, the state of
+// both buffers in the shared memory of one cluster of up to 16 blocks.
+int setup_cluster(dmrt_ctx* c) {
     const dmrt_params& p = c->p;
+    c->cluster = false;
+    if (p.storage != DMRT_FP32 || c->slab) {
+        set_err(c, "the cluster kernel runs float32 storage of a whole cavity only");
+        return DMRT_E_ARG;
+    }
+    const void* fn = (const void*)dmrt::step_cluster_kernel;
+    for (int csize : {16, 8}) {
+        const int cs = std::min(csize, p.ny);
+        const int rows = (p.ny + cs - 1) / cs;
+        const int blocks = (p.ny + rows - 1) / rows;
+        const size_t smem = dmrt::cluster_smem_bytes(rows, p.nx, p.ny);
+        const int threads = std::min(1024, (rows * p.nx + 31) / 32 * 32);
+        if (smem > (size_t)dmrt::kMaxSmem) continue;
+        if (blocks > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = blocks;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(blocks);
+        cfg.blockDim = dim3(threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, fn, &cfg) != cudaSuccess || nclusters < 1) {
+            (void)cudaGetLastError();
+            continue;
+        }
+        c->cluster = true;
+        c->csize = blocks;
+        c->crows = rows;
+        c->cthreads = threads;
+        c->csmem = smem;
+        return DMRT_OK;
+    }
+    set_err(c, "a %d x %d float32 cavity does not fit the shared memory of one thread-block cluster", p.nx, p.ny);
+    return DMRT_E_ARG;
+}
+
+int setup_kernel(dmrt_ctx* c) {
+    const dmrt_params& p0 = c->p;
+    c->cluster = false;
+    if (p0.kernel == DMRT_KERNEL_CLUSTER) {
+        int rc = setup_cluster(c);
+        if (rc) return rc;
+    }
+    dmrt_params p = p0;  // single steps and the adjoint: the kernel AUTO picks among the others
+    if (p.kernel == DMRT_KERNEL_CLUSTER) p.kernel = DMRT_KERNEL_AUTO;
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev), "cudaGetDevice");
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "SM count");
@@ -665,8 +730,8 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "stochastic rounding applies to 16-bit and mixed storage only");
         return DMRT_E_ARG;
     }
-    if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_TMA) {
-        set_err(c, "kernel must be DMRT_KERNEL_AUTO, _DIRECT or _TMA");
+    if (p->kernel < DMRT_KERNEL_AUTO || p->kernel > DMRT_KERNEL_CLUSTER) {
+        set_err(c, "kernel must be DMRT_KERNEL_AUTO, _DIRECT, _TMA or _CLUSTER");
         return DMRT_E_ARG;
     }
     if (p->nu_capacity < 1) {
@@ -1028,6 +1093,17 @@ int dmrt_choose_launch(const dmrt_params* p, int32_t sms, int32_t* kernel, int32
     }
     int rc = validate(p, nullptr);
     if (rc) return rc;
+    if (p->kernel == DMRT_KERNEL_CLUSTER) {
+        // Fits when both buffers' rows fit the shared memory of 16 blocks.
+        const int crows = (p->ny + 15) / 16;
+        if (p->storage != DMRT_FP32 || dmrt::cluster_smem_bytes(crows, p->nx, p->ny) > (size_t)dmrt::kMaxSmem) {
+            set_err(nullptr, "the cluster kernel needs float32 storage and a cavity whose state fits one cluster");
+            return DMRT_E_ARG;
+        }
+        *kernel = DMRT_KERNEL_CLUSTER;
+        *npt = *rows = *stages = 0;
+        return DMRT_OK;
+    }
     int k, n, r, st;
     choose_launch(*p, sms, &k, &n, &r, &st);
     if (k == DMRT_KERNEL_DIRECT && p->storage != DMRT_FP32) {
@@ -1058,8 +1134,50 @@ static int poll_error(dmrt_ctx* c) {
     return DMRT_OK;
 }
 
+// Runs of n >= 2 steps on the cluster kernel: one launch.
+static int launch_cluster(dmrt_ctx* c, int n) {
+    dmrt::ClusterArgs C;
+    C.A[0] = step_args(c, 0);
+    C.A[1] = step_args(c, 1);
+    C.K = c->sc;
+    C.steps = n;
+    C.parity = c->cur;
+    C.rows_per = c->crows;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = c->csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(c->csize);
+    cfg.blockDim = dim3(c->cthreads);
+    cfg.dynamicSmemBytes = c->csmem;
+    cfg.stream = c->stream;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel, C), "cluster step launch");
+    c->cur ^= n & 1;
+    c->t += n;
+    return DMRT_OK;
+}
+
 int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
+    if (c->cluster) {
+        while (nsteps > 0) {
+            if (c->t >= c->next_poll) {
+                c->next_poll = c->t + kPollSteps;
+                int rc = poll_error(c);
+                if (rc) return rc;
+            }
+            // Up to the next divergence poll, in one launch.
+            const long long n = std::min<long long>(nsteps, std::max<long long>(1, c->next_poll - c->t));
+            int rc = n >= 2 ? launch_cluster(c, (int)n) : launch_one(c);
+            if (rc) return rc;
+            nsteps -= n;
+        }
+        return finalize_nu(c);
+    }
     if (c->slab && !(c->wall_lo && c->wall_hi) && nsteps > 1) {
         set_err(c, "a slab with neighbours takes one step at a time (dmrt_slab_step), its halo rows "
                    "exchanged in between");
@@ -1613,6 +1731,15 @@ int dmrt_load(dmrt_ctx* c, const void* host_buf, size_t size) {
 
 int dmrt_get_launch(const dmrt_ctx* c, dmrt_launch* out) {
     if (!c || !out) return DMRT_E_ARG;
+    if (c->cluster) {
+        out->kernel = DMRT_KERNEL_CLUSTER;
+        out->tma_npt = out->tma_rows = out->tma_stages = 0;
+        out->grid = c->csize;
+        out->block = c->cthreads;
+        out->smem_bytes = (int64_t)c->csmem;
+        out->graph_steps = 0;
+        return DMRT_OK;
+    }
     out->kernel = c->kernel;
     if (c->kernel == DMRT_KERNEL_TMA) {
         out->tma_npt = c->npt;

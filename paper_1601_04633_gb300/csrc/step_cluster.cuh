@@ -1,0 +1,228 @@
+// Fused double-MRT steps for small float32 cavities, the whole state held on
+// chip: one thread-block cluster (up to 16 blocks on 16 SMs) keeps both
+// population buffers of the cavity in its blocks' shared memory and runs many
+// time steps per launch.
+//
+// Block r of the cluster owns rows [r rows_per, (r + 1) rows_per) of the
+// cavity; its shared memory holds those rows of both buffers, 14 planes
+// [row][x] each, in the device plane order of lattice.cuh. One thread per node
+// (looping when a block has more nodes than threads). The pull of a block's
+// first row reads the upward-moving planes of the previous block's last row,
+// and the pull of its last row the downward-moving planes of the next block's
+// first row, from those blocks' shared memory (distributed shared memory); the
+// walls are the same rules, in the same arithmetic, as the other step kernels,
+// and the collision is the same routine, so every step gives the other
+// kernels' bits. Between steps one cluster barrier (release / acquire at
+// cluster scope) publishes the new buffer; no step touches global memory
+// except the wall temperatures, the Nusselt ring and the error word.
+//
+// Nusselt number (Eqs. 18-19): the pre-collision temperatures at x = 0 and 1 of
+// each row are staged in shared memory; after a block barrier one thread per
+// row computes the row's value and writes it into block 0's shared row array
+// (distributed shared memory, double-buffered by step parity); after the step's cluster
+// barrier, warp 0 of block 0 sums the rows in the fixed order of
+// nu_finish_prev (partial p over rows p, p + 256, ...; lane l adds partials
+// q = 0..7 in order; butterfly over the lanes) and appends the mean to the
+// ring, while the other warps start the next step.
+//
+// The launch starts from the state in global buffer `parity` (copied in), and
+// ends by copying the final state to global buffer parity ^ (K & 1), the last
+// step's per-row Nusselt values to its rows array, the step counter slot and
+// a cleared pending flag: afterwards the context is exactly as after K steps
+// of the other kernels. The cluster barrier is the hardware's (every block
+// executes the same K iterations, so every block arrives); there is no
+// spin-wait in this kernel.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "lattice.cuh"
+
+namespace dmrt {
+
+struct ClusterArgs {
+    StepArgs A[2];   // global buffers and Nusselt arrays, by source buffer
+    StepConsts K;
+    int steps;       // time steps of the launch
+    int parity;      // global buffer holding the state at launch
+    int rows_per;    // rows per block
+};
+
+__host__ __device__ constexpr size_t cluster_smem_bytes(int rows_per, int nx, int ny) {
+    return (size_t)2 * kPlanes * rows_per * nx * sizeof(float)      // both buffers
+           + (((size_t)2 * rows_per * sizeof(float) + 15) & ~size_t(15))  // theta at x = 0 and 1, per row
+           + (size_t)2 * ny * sizeof(double);                         // Nusselt rows (block 0), by step parity
+}
+
+// Sum of rows[0..ny) by warp 0 in the fixed order of nu_finish_prev (the result in every lane).
+__device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int lane) {
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double acc = 0.0;
+        for (int r = lane + 32 * q; r < ny; r += 256) acc += rows[r];
+        s += acc;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+    return s;
+}
+
+static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int csize = (int)cl.num_blocks();
+    const StepArgs& A0 = C.A[C.parity];
+    const StepConsts& K = C.K;
+    const int nx = A0.nx, ny = A0.ny, pitch = A0.pitch;
+    const long long PL = A0.plane;
+    const int RP = C.rows_per;
+    const int r0 = rank * RP;
+    const int nr = max(0, min(RP, ny - r0));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int plane_sm = RP * nx;  // floats per plane in shared memory
+
+    extern __shared__ __align__(16) unsigned char smem_c[];
+    float* sb[2] = {reinterpret_cast<float*>(smem_c), reinterpret_cast<float*>(smem_c) + kPlanes * plane_sm};
+    float* th01 = reinterpret_cast<float*>(smem_c) + 2 * kPlanes * plane_sm;
+    double* nur = reinterpret_cast<double*>(smem_c + cluster_smem_bytes(RP, nx, ny) - (size_t)2 * ny * sizeof(double));
+
+    grid_dep_wait();
+    grid_dep_launch();
+    // The state of this block's rows, from global buffer `parity`.
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+        const int r = i / nx, x = i - r * nx;
+        const float* src = A0.src + (size_t)(r0 + r) * pitch + x;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) sb[0][p * plane_sm + i] = src[p * PL];
+    }
+    const long long t0 = *A0.step_in;
+    if (rank == 0 && warp == 0 && *A0.pending) {
+        // Rows of an earlier step not yet summed (a single step launched before).
+        const double sum = warp_fixed_sum(A0.prev_rows, ny, lane);
+        if (lane == 0) {
+            A0.nu_ring[(t0 - 1) % A0.cap] = sum / A0.nu_div;
+            *A0.nu_last = sum / A0.nu_div;
+        }
+    }
+    cl.sync();
+
+    const float sign_l_g = K.left_fixed ? -1.f : 1.f;
+    const float sign_r_g = K.right_fixed ? -1.f : 1.f;
+    bool bad = false;
+    for (int s = 0; s < C.steps; ++s) {
+        const float* S = sb[s & 1];
+        float* Dst = sb[(s & 1) ^ 1];
+        const float* Sprev = rank > 0 ? cl.map_shared_rank(S, rank - 1) : nullptr;
+        const float* Snext = rank + 1 < csize ? cl.map_shared_rank(S, rank + 1) : nullptr;
+        double* nu_dst = cl.map_shared_rank(nur, 0) + (size_t)(s & 1) * ny;
+        for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+            const int r = i / nx, x = i - r * nx;
+            const int j = r0 + r;
+            // Post-collision value of plane p at (x, local row rr) of this step's state.
+            // (Across the cavity's bottom and top walls there is no such node: 0,
+            // replaced by the wall rules below.)
+            auto at = [&](int p, int rr, int xx) -> float {
+                if (rr < 0) return Sprev ? Sprev[p * plane_sm + (RP - 1) * nx + xx] : 0.f;  // previous block's last row
+                if (rr >= nr) return Snext ? Snext[p * plane_sm + xx] : 0.f;                // next block's first row
+                return S[p * plane_sm + rr * nx + xx];
+            };
+            auto own = [&](int p) { return S[p * plane_sm + r * nx + x]; };
+            // Pull (Eqs. 25, 36): value of direction k at x comes from x - e_k, where
+            // that node exists; links across a wall are replaced below.
+            float f[9], g[5];
+            const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
+            f[0] = own(plane_f(0));
+            f[1] = at(plane_f(1), r, xl);
+            f[2] = at(plane_f(2), r - 1, x);
+            f[3] = at(plane_f(3), r, xr);
+            f[4] = at(plane_f(4), r + 1, x);
+            f[5] = at(plane_f(5), r - 1, xl);
+            f[6] = at(plane_f(6), r - 1, xr);
+            f[7] = at(plane_f(7), r + 1, xr);
+            f[8] = at(plane_f(8), r + 1, xl);
+            g[0] = own(plane_g(0));
+            g[1] = at(plane_g(1), r, xl);
+            g[2] = at(plane_g(2), r - 1, x);
+            g[3] = at(plane_g(3), r, xr);
+            g[4] = at(plane_g(4), r + 1, x);
+            // Bottom wall (j = 0): f2, f5, f6, g2 from the node's own opposites; top the reverse.
+            if (j == 0) {
+                f[2] = own(plane_f(4));
+                f[5] = own(plane_f(7));
+                f[6] = own(plane_f(8));
+                g[2] = own(plane_g(4));
+            }
+            if (j == ny - 1) {
+                f[4] = own(plane_f(2));
+                f[7] = own(plane_f(5));
+                f[8] = own(plane_f(6));
+                g[4] = own(plane_g(2));
+            }
+            // Left wall (x = 0): links with e_x = +1.
+            if (x == 0) {
+                f[1] = own(plane_f(3));
+                f[5] = own(plane_f(7));
+                f[8] = own(plane_f(6));
+                const float add = K.left_fixed ? K.abb * __ldg(A0.hot + j) : 0.f;
+                g[1] = sign_l_g * own(plane_g(3)) + add;
+            }
+            // Right wall (x = nx - 1): links with e_x = -1.
+            if (x == nx - 1) {
+                f[3] = own(plane_f(1));
+                f[6] = own(plane_f(8));
+                f[7] = own(plane_f(5));
+                const float add = K.right_fixed ? K.abb * __ldg(A0.cold + j) : 0.f;
+                g[3] = sign_r_g * own(plane_g(1)) + add;
+            }
+            float rho, theta;
+            collide_node(f, g, K, rho, theta);
+            bad |= !(fabsf(rho) < 1e30f) || !(fabsf(theta) < 1e30f);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) Dst[plane_f(k) * plane_sm + i] = f[k];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) Dst[plane_g(k) * plane_sm + i] = g[k];
+            if (x == 0) th01[2 * r] = theta;
+            if (x == 1) th01[2 * r + 1] = theta;
+        }
+        __syncthreads();  // theta at x = 0 and 1 of every row of this block
+        for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+            const int j = r0 + r;
+            const double tw = (double)__ldg(A0.hot + j);
+            nu_dst[j] = K.nu_scale * (8.0 * tw - 9.0 * (double)th01[2 * r] + (double)th01[2 * r + 1]);
+        }
+        cl.sync();  // the new state and the step's Nusselt rows are visible to the whole cluster
+        if (rank == 0 && warp == 0) {
+            // Mean of this step's rows while the other warps start the next step.
+            const double sum = warp_fixed_sum(nur + (size_t)(s & 1) * ny, ny, lane);
+            if (lane == 0) {
+                A0.nu_ring[(t0 + s) % A0.cap] = sum / A0.nu_div;
+                *A0.nu_last = sum / A0.nu_div;
+            }
+        }
+    }
+    // The final state to global buffer parity ^ (K & 1); the last step's rows to
+    // the rows array of its source buffer; the step counter slot of the final
+    // buffer; nothing pending.
+    const int pend = C.parity ^ (C.steps & 1);
+    const float* fin = sb[C.steps & 1];
+    float* dstg = const_cast<float*>(C.A[pend].src);
+    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+        const int r = i / nx, x = i - r * nx;
+        float* d = dstg + (size_t)(r0 + r) * pitch + x;
+#pragma unroll
+        for (int p = 0; p < kPlanes; ++p) d[p * PL] = fin[p * plane_sm + i];
+    }
+    if (rank == 0 && C.steps > 0) {
+        const double* last = nur + (size_t)((C.steps - 1) & 1) * ny;
+        double* rows = C.A[C.parity ^ ((C.steps - 1) & 1)].nu_rows;
+        for (int r = threadIdx.x; r < ny; r += blockDim.x) rows[r] = last[r];
+        if (threadIdx.x == 0) {
+            *const_cast<long long*>(C.A[pend].step_in) = t0 + C.steps;
+            *A0.pending = 0u;
+        }
+    }
+    if (bad) atomicOr(A0.err, kErrNonFinite);
+}
+
+}  // namespace dmrt

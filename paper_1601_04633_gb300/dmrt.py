@@ -29,7 +29,7 @@ DMRT_E_SPACE = -6
 DMRT_E_STATE = -7
 DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED = 0, 1, 2, 3
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
-DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA = 0, 1, 2
+DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA, DMRT_KERNEL_CLUSTER = 0, 1, 2, 3
 DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC, DMRT_ROUND_AUTO = 0, 1, 2
 DMRT_NOALLOC_MAX_NY = 8192
 # Device plane order of the population buffers: entry d is the index, in the host

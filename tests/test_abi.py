@@ -88,7 +88,7 @@ def test_alpha_from_mach(D):
     (dict(storage=7), -1), (dict(nu_capacity=0), -1), (dict(left_wall=3), -1),
     (dict(rounding=3), -1), (dict(rounding=-1), -1),
     (dict(rounding=1), -1),  # stochastic rounding needs 16-bit storage
-    (dict(kernel=3), -1), (dict(kernel=-1), -1),
+    (dict(kernel=4), -1), (dict(kernel=-1), -1),
 ])
 def test_invalid_params_rejected(D, kw, code):
     base = dict(nx=64, ny=64, Ra=1e4, Pr=0.01, alpha=0.1)

@@ -98,3 +98,18 @@ def test_every_chosen_tile_is_compiled(D, storage, rounding):
             assert (storage, rounding, npt, R, S) in single, (nx, ny, storage, rounding, (npt, R, S))
         else:
             assert storage == 0 and (npt, R, S) == (0, 0, 0)
+
+
+def test_cluster_kernel_choice_by_size():
+    # Asked for explicitly, the cluster kernel is taken when both float32 buffers
+    # fit the shared memory of 16 blocks (64^2, 128^2) and refused otherwise.
+    from paper_1601_04633_gb300 import dmrt as D
+
+    for n in (2, 64, 128):
+        p = D.make_params(n, n, 1e4, 0.01, kernel=D.DMRT_KERNEL_CLUSTER)
+        assert D.dmrt_choose_launch(p, 152) == (D.DMRT_KERNEL_CLUSTER, 0, 0, 0)
+    for kw in (dict(nx=512, ny=512), dict(nx=64, ny=64, storage=D.DMRT_MIXED)):
+        nx, ny = kw.pop("nx"), kw.pop("ny")
+        p = D.make_params(nx, ny, 1e4, 0.01, kernel=D.DMRT_KERNEL_CLUSTER, **kw)
+        with pytest.raises(D.DmrtError):
+            D.dmrt_choose_launch(p, 152)
