@@ -48,6 +48,9 @@ extern "C" {
 #define DMRT_E_TIMEOUT (-5)  /* a bounded device-side wait ran out (2 s per wait) */
 #define DMRT_E_SPACE (-6)    /* workspace or host buffer too small */
 #define DMRT_E_STATE (-7)    /* checkpoint does not match this context */
+#define DMRT_E_BOUNDS (-8)   /* bounds-checked build (libdmrt_bc.so, compiled with
+                                DMRT_BOUNDS_CHECK): a kernel computed an index outside
+                                its array and skipped that access */
 
 /* Population storage precision. MIXED: the flow populations f in float16 and
  * the thermal populations g in float32 (38 bytes per node and buffer instead of

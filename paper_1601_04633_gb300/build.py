@@ -2,7 +2,8 @@
 
 ``python -m paper_1601_04633_gb300.build`` or ``build_library()``. Each .cu file
 under ``csrc/`` is compiled to an object in parallel, then linked into
-``paper_1601_04633_gb300/_lib/libdmrt.so``.
+``paper_1601_04633_gb300/_lib/libdmrt.so``; the same sources compiled with
+``-DDMRT_BOUNDS_CHECK`` give ``libdmrt_bc.so``.
 """
 from __future__ import annotations
 
@@ -20,6 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libdmrt.so")
+LIB_BC = os.path.join(OUT_DIR, "libdmrt_bc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
               "-I" + INCLUDE, "-I" + CSRC]
@@ -50,19 +52,22 @@ def _fingerprint() -> str:
 
 
 def build_library(force: bool = False, verbose: bool = False) -> str:
+    """Build libdmrt.so and its bounds-checked twin libdmrt_bc.so (every index
+    the kernels compute checked; compiled with -DDMRT_BOUNDS_CHECK); both from
+    the same sources, all translation units in parallel. Returns libdmrt.so."""
     os.makedirs(OUT_DIR, exist_ok=True)
     stamp = os.path.join(OUT_DIR, "libdmrt.stamp")
     fp = _fingerprint()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    if not force and os.path.exists(LIB) and os.path.exists(LIB_BC) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == fp:
                 return LIB
     nvcc = _nvcc()
-    objs = []
 
-    def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+    def compile_one(job):
+        src, bc = job
+        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ("_bc.o" if bc else ".o"))
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *(["-DDMRT_BOUNDS_CHECK"] if bc else []), "-c", src, "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -73,14 +78,16 @@ def build_library(force: bool = False, verbose: bool = False) -> str:
         return obj
 
     srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    jobs = [(s, False) for s in srcs] + [(s, True) for s in srcs]
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, jobs))
+    for lib, part in ((LIB, objs[:len(srcs)]), (LIB_BC, objs[len(srcs):])):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *part]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     with open(stamp, "w") as fh:
         fh.write(fp)
     return LIB

@@ -1127,6 +1127,10 @@ static int poll_error(dmrt_ctx* c) {
         set_err(c, "a bounded device-side wait expired after %lld steps", c->t);
         return DMRT_E_TIMEOUT;
     }
+    if (err & dmrt::kErrBounds) {
+        set_err(c, "an index out of range was seen (bounds-checked build) after %lld steps", c->t);
+        return DMRT_E_BOUNDS;
+    }
     if (err & dmrt::kErrNonFinite) {
         set_err(c, "non-finite density or temperature after %lld steps", c->t);
         return DMRT_E_DIVERGED;
@@ -1438,6 +1442,10 @@ int dmrt_nusselt(dmrt_ctx* c, double* nu_mean, double* nu_local, double* series,
     if (m.err & dmrt::kErrTimeout) {
         set_err(c, "a bounded device-side wait expired after %lld steps", c->t);
         return DMRT_E_TIMEOUT;
+    }
+    if (m.err & dmrt::kErrBounds) {
+        set_err(c, "an index out of range was seen (bounds-checked build) after %lld steps", c->t);
+        return DMRT_E_BOUNDS;
     }
     if (m.err & dmrt::kErrNonFinite) {
         set_err(c, "non-finite density or temperature after %lld steps", c->t);
@@ -2309,6 +2317,10 @@ int dmrt_batch_check(dmrt_batch* b) {
     if (err & dmrt::kErrTimeout) {
         batch_set_err(b, "a bounded device-side wait expired");
         return DMRT_E_TIMEOUT;
+    }
+    if (err & dmrt::kErrBounds) {
+        batch_set_err(b, "an index out of range was seen (bounds-checked build)");
+        return DMRT_E_BOUNDS;
     }
     for (int i = 0; i < b->n; ++i) {
         int rc = dmrt_check(b->sub[i]);

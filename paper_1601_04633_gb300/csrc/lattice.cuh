@@ -73,6 +73,23 @@ struct StepArgs {
 
 constexpr unsigned kErrNonFinite = 1u;
 constexpr unsigned kErrTimeout = 2u;
+constexpr unsigned kErrBounds = 4u;  // an index out of its range (bounds-checked builds)
+
+// Bounds-checked builds (-DDMRT_BOUNDS_CHECK): DMRT_IN(i, lo, hi, err) is true
+// when lo <= i < hi, and otherwise records kErrBounds in *err and is false; the
+// kernels test it before each global and shared-memory access whose index they
+// compute, and skip the access when it is false. Other builds: always true, no
+// code.
+#ifdef DMRT_BOUNDS_CHECK
+__device__ __forceinline__ bool bounds_ok(long long i, long long lo, long long hi, unsigned* err) {
+    if (i >= lo && i < hi) return true;
+    atomicOr(err, kErrBounds);
+    return false;
+}
+#define DMRT_IN(i, lo, hi, err) ::dmrt::bounds_ok((long long)(i), (long long)(lo), (long long)(hi), (err))
+#else
+#define DMRT_IN(i, lo, hi, err) true
+#endif
 
 // Programmatic dependent launch. In the step graphs each step kernel depends on
 // the previous one through a programmatic edge, so its blocks may be launched
@@ -222,7 +239,9 @@ __device__ __forceinline__ void collide_quad(float4 (&F)[9], float4 (&Gq)[5], co
 // Store a collided quad (4 nodes from x0 of row j) to the destination planes.
 __device__ __forceinline__ void store_quad(const StepArgs& A, int j, int x0, const float4 (&F)[9],
                                            const float4 (&Gq)[5]) {
-    float* D = A.dst + (size_t)(j + A.row0) * A.pitch + x0;
+    const long long o = (long long)(j + A.row0) * A.pitch + x0;
+    if (!DMRT_IN(o, 0, A.plane - 3, A.err)) return;
+    float* D = A.dst + o;
 #pragma unroll
     for (int k = 0; k < 9; ++k) *reinterpret_cast<float4*>(D + plane_f(k) * A.plane) = F[k];
 #pragma unroll
@@ -235,7 +254,7 @@ __device__ __forceinline__ void store_quad(const StepArgs& A, int j, int x0, con
 // start of the next step by one block, or by the finalize launch after a run
 // of steps (nu_finish_prev), when the rows are complete without any counting.
 __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j, double nuj) {
-    if (has_nu) A.nu_rows[j] = nuj;
+    if (has_nu && DMRT_IN(j, 0, A.ny, A.err)) A.nu_rows[j] = nuj;
 }
 
 // Called by every thread of a block (it synchronises the block), once per
@@ -278,7 +297,7 @@ __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             if (lane == 0) {
                 const double mean = s / A.nu_div;
-                A.nu_ring[(t - 1) % A.cap] = mean;
+                if (DMRT_IN((t - 1) % A.cap, 0, A.cap, A.err)) A.nu_ring[(t - 1) % A.cap] = mean;
                 *A.nu_last = mean;
             }
         }

@@ -92,6 +92,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     // The state of this block's rows, from global buffer `parity`.
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
         const int r = i / nx, x = i - r * nx;
+        if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err)) continue;
         const float* src = A0.src + (size_t)(r0 + r) * pitch + x;
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) sb[0][p * plane_sm + i] = src[p * PL];
@@ -119,6 +120,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
         for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
             const int r = i / nx, x = i - r * nx;
             const int j = r0 + r;
+            if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN(j, 0, ny, A0.err) || !DMRT_IN(r, 0, RP, A0.err)) continue;
             // Post-collision value of plane p at (x, local row rr) of this step's state.
             // (Across the cavity's bottom and top walls there is no such node: 0,
             // replaced by the wall rules below.)
@@ -188,6 +190,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
         __syncthreads();  // theta at x = 0 and 1 of every row of this block
         for (int r = threadIdx.x; r < nr; r += blockDim.x) {
             const int j = r0 + r;
+            if (!DMRT_IN(j, 0, ny, A0.err)) continue;
             const double tw = (double)__ldg(A0.hot + j);
             nu_dst[j] = K.nu_scale * (8.0 * tw - 9.0 * (double)th01[2 * r] + (double)th01[2 * r + 1]);
         }
@@ -209,6 +212,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     float* dstg = const_cast<float*>(C.A[pend].src);
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
         const int r = i / nx, x = i - r * nx;
+        if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err)) continue;
         float* d = dstg + (size_t)(r0 + r) * pitch + x;
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) d[p * PL] = fin[p * plane_sm + i];

@@ -19,6 +19,8 @@ constexpr int kDirectThreads = 128;  // 4 warps per block
 struct Geo {
     int nx, ny, pitch, wx, seg_lane;
     int row0, wall_lo, wall_hi;  // see StepArgs
+    long long plane;             // elements per plane (bounds-checked builds)
+    unsigned* err;
 };
 
 // Pull-stream of one plane for the four nodes (x0..x0+3, j): the value at node
@@ -38,17 +40,27 @@ __device__ __forceinline__ void pull_load(const float* __restrict__ P, const flo
                                           int j, int x0, int right_e, const Geo& G, PlaneLoad& L) {
     const int r = j - EY;
     const bool yin = (r >= 0 || !G.wall_lo) && (r < G.ny || !G.wall_hi);
-    const float* orow = Popp + (size_t)(j + G.row0) * G.pitch;
-    const float* row = yin ? P + (size_t)(r + G.row0) * G.pitch : orow;
-    L.v = ldg4(row + x0);
+    // Source row: row r of plane P, or across a top/bottom wall the node's own
+    // row of the opposite plane (bounce-back). Offsets are within one plane.
+    const long long oo = (long long)(j + G.row0) * G.pitch;
+    const long long ro = yin ? (long long)(r + G.row0) * G.pitch : oo;
+    const float* orow = Popp + oo;
+    const float* row = (yin ? P : Popp) + ro;
+    L.v = DMRT_IN(ro + x0, 0, G.plane - 3, G.err) ? ldg4(row + x0) : make_float4(0.f, 0.f, 0.f, 0.f);
     L.edge = 0.f;
     if constexpr (EX == 1) {
-        if (yin && x0 == 0) L.edge = __ldg(orow);                       // wall partner
-        else if (yin && G.seg_lane == 0) L.edge = __ldg(row + x0 - 1);  // halo
+        if (yin && x0 == 0) {
+            if (DMRT_IN(oo, 0, G.plane, G.err)) L.edge = __ldg(orow);    // wall partner
+        } else if (yin && G.seg_lane == 0) {
+            if (DMRT_IN(ro + x0 - 1, 0, G.plane, G.err)) L.edge = __ldg(row + x0 - 1);  // halo
+        }
     }
     if constexpr (EX == -1) {
-        if (yin && right_e >= 0 && right_e < 4) L.edge = __ldg(orow + G.nx - 1);
-        else if (yin && G.seg_lane == G.wx - 1 && x0 + 4 < G.pitch) L.edge = __ldg(row + x0 + 4);
+        if (yin && right_e >= 0 && right_e < 4) {
+            if (DMRT_IN(oo + G.nx - 1, 0, G.plane, G.err)) L.edge = __ldg(orow + G.nx - 1);
+        } else if (yin && G.seg_lane == G.wx - 1 && x0 + 4 < G.pitch) {
+            if (DMRT_IN(ro + x0 + 4, 0, G.plane, G.err)) L.edge = __ldg(row + x0 + 4);
+        }
     }
 }
 
@@ -88,6 +100,8 @@ __device__ __forceinline__ void direct_tile(const StepArgs& A, const StepConsts&
     G.row0 = A.row0;
     G.wall_lo = A.wall_lo;
     G.wall_hi = A.wall_hi;
+    G.plane = A.plane;
+    G.err = A.err;
     G.wx = 1 << A.wx_log2;
     G.seg_lane = lane & (G.wx - 1);
     const int rows_per_warp = 32 >> A.wx_log2;
@@ -100,8 +114,9 @@ __device__ __forceinline__ void direct_tile(const StepArgs& A, const StepConsts&
     const float* S = A.src;
     const long long PL = A.plane;
     float add_l_g = 0.f, add_r_g = 0.f;
-    if (x0 == 0 && K.left_fixed) add_l_g = K.abb * __ldg(A.hot + j);
-    if (x0 <= A.nx - 1 && A.nx - 1 < x0 + 4 && K.right_fixed) add_r_g = K.abb * __ldg(A.cold + j);
+    const bool j_in = DMRT_IN(j, 0, A.ny, A.err);
+    if (x0 == 0 && K.left_fixed && j_in) add_l_g = K.abb * __ldg(A.hot + j);
+    if (x0 <= A.nx - 1 && A.nx - 1 < x0 + 4 && K.right_fixed && j_in) add_r_g = K.abb * __ldg(A.cold + j);
     const float sign_l_g = K.left_fixed ? -1.f : 1.f;
     const float sign_r_g = K.right_fixed ? -1.f : 1.f;
 
@@ -154,7 +169,7 @@ __device__ __forceinline__ void direct_tile(const StepArgs& A, const StepConsts&
     if (bx == 0) {
         const bool has_nu = row_ok && G.seg_lane == 0;
         double nuj = 0.0;
-        if (has_nu) {
+        if (has_nu && j_in) {
             const double tw = (double)__ldg(A.hot + j);
             nuj = K.nu_scale * (8.0 * tw - 9.0 * (double)theta4[0] + (double)theta4[1]);
         }

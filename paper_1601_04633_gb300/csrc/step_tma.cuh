@@ -414,7 +414,8 @@ template <typename L, int NPT, bool SR, bool TS = false>
 __device__ __forceinline__ void process_item(const unsigned char* stage, const StepArgs& A, const StepConsts& K,
                                              int strip, int rb, int rg, int t, bool ok,
                                              unsigned salt, int W, int WB, int RC, const StageOffsets& so,
-                                             unsigned char* out = nullptr) {
+                                             unsigned char* out = nullptr, unsigned stage_cap = 0,
+                                             unsigned out_cap = 0) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     constexpr int HALO = L::kHalo;
@@ -436,22 +437,48 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
     float theta[NPT];
 #pragma unroll
     for (int e = 0; e < NPT; ++e) theta[e] = 0.f;
+    // Plane p of a layout whose groups start at planes 0, p_P, p_N and at
+    // elements 0, oP, oN of the stage.
+    auto grouped = [&](int plane, int p_P, int p_N, int oP, int oN) {
+        const int g0 = plane >= p_N ? p_N : plane >= p_P ? p_P : 0;
+        const int off = plane >= p_N ? oN : plane >= p_P ? oP : 0;
+        return off + ((plane - g0) * RC + rg) * WB;
+    };
+    auto rowf = [&](int plane) {
+        return stf + (L::kSplit ? grouped(plane, 3, 6, so.zP, so.zN)
+                                : grouped(plane, kGroupP, kGroupN, so.zP, so.zN));
+    };
+    auto rowg = [&](int plane) {
+        return stg + (L::kSplit ? grouped(plane, 3, 4, so.gP, so.gN)
+                                : grouped(plane, kGroupP, kGroupN, so.zP, so.zN));
+    };
+    bool bc = true;  // every index of this item in range (checked in bounds-checked builds)
+#ifdef DMRT_BOUNDS_CHECK
     if (mine) {
-        // Plane p of a layout whose groups start at planes 0, p_P, p_N and at
-        // elements 0, oP, oN of the stage.
-        auto grouped = [&](int plane, int p_P, int p_N, int oP, int oN) {
-            const int g0 = plane >= p_N ? p_N : plane >= p_P ? p_P : 0;
-            const int off = plane >= p_N ? oN : plane >= p_P ? oP : 0;
-            return off + ((plane - g0) * RC + rg) * WB;
-        };
-        auto rowf = [&](int plane) {
-            return stf + (L::kSplit ? grouped(plane, 3, 6, so.zP, so.zN)
-                                    : grouped(plane, kGroupP, kGroupN, so.zP, so.zN));
-        };
-        auto rowg = [&](int plane) {
-            return stg + (L::kSplit ? grouped(plane, 3, 4, so.gP, so.gN)
-                                    : grouped(plane, kGroupP, kGroupN, so.zP, so.zN));
-        };
+        // The stage rows read (one shifted vector each way), the wall columns
+        // and destination rows of every plane, the output tile, and the rows of
+        // the wall-temperature and Nusselt arrays.
+        bc = DMRT_IN(j, 0, A.ny, A.err) && DMRT_IN(HALO + n0 - NPT, 0, WB, A.err) &&
+             DMRT_IN(HALO + n0 + 2 * NPT - 1, 0, WB, A.err);
+        for (int k = 0; k < 9 && bc; ++k) {
+            const long long b = (long long)(rowf(L::pf(k)) - stf) * (long long)sizeof(Ef);
+            bc = DMRT_IN(b, 0, stage_cap, A.err) && DMRT_IN(b + (long long)WB * sizeof(Ef) - 1, 0, stage_cap, A.err);
+        }
+        for (int k = 0; k < 5 && bc; ++k) {
+            const long long b = (long long)(rowg(L::pg(k)) - stg) * (long long)sizeof(Eg) + (L::kSplit ? so.g_bytes : 0);
+            bc = DMRT_IN(b, 0, stage_cap, A.err) && DMRT_IN(b + (long long)WB * sizeof(Eg) - 1, 0, stage_cap, A.err);
+        }
+        const long long nfp = L::kSplit ? 9 : kPlanes, ngp = L::kSplit ? 5 : kPlanes;
+        const long long ro = (long long)(j + A.row0) * A.pitch;
+        bc = bc && DMRT_IN(ro + x0 + NPT - 1, 0, PL, A.err) && DMRT_IN(ro + A.nx - 1, 0, PL, A.err) &&
+             DMRT_IN((nfp - 1) * PL + ro + x0, 0, nfp * PL, A.err) &&
+             DMRT_IN((ngp - 1) * PL + ro + x0, 0, ngp * PL, A.err);
+        if (TS)
+            bc = bc && DMRT_IN(rg, 0, RC, A.err) && DMRT_IN(n0 + NPT - 1, 0, W, A.err) &&
+                 DMRT_IN((long long)out_tile_bytes(L::kSplit, RC, W, sizeof(Ef), sizeof(Eg)) - 1, 0, out_cap, A.err);
+    }
+#endif
+    if (mine && bc) {
         float F[9][NPT], Gq[5][NPT];
         lds_pull<0, NPT, HALO>(rowf(L::pf(0)), n0, F[0], 0.f);
         lds_pull<1, NPT, HALO>(rowf(L::pf(1)), n0, F[1], 0.f);
@@ -545,7 +572,7 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
     if (strip == 0 && t < 32) {
         float th1 = NPT > 1 ? theta[NPT > 1 ? 1 : 0] : 0.f;
         if constexpr (NPT == 1) th1 = __shfl_down_sync(kFull, theta[0], 1);
-        const bool has_nu = mine && t == 0;
+        const bool has_nu = mine && bc && t == 0;
         double nuj = 0.0;
         if (has_nu) {
             const double tw = (double)__ldg(A.hot + j);
@@ -705,7 +732,7 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
 
         unsigned char* out = outs + (size_t)(k & 1) * kOutBytes;
         process_item<L, NPT, SR, TS>(stages + (size_t)s * kStageBytes, A, K, cc.strip, cc.rb, rg, t, ok, salt,
-                                     STRIP, kTmaBox, R, kSO, out);
+                                     STRIP, kTmaBox, R, kSO, out, kStageBytes, (unsigned)kOutBytes);
         if constexpr (TS) {
             fence_async_smem();
             if (tid == 0) bulk_wait_read_all();  // item k - 1's store has read the other tile

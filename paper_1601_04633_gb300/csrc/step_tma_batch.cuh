@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         // Every thread reads the same entry; a thread whose wait expired may
         // read a stale one, and the barrier below then ends the block anyway.
         const int4 w = stage_item[s];
-        const bool work = ok && w.x >= 0;
+        const bool work = ok && w.x >= 0 && DMRT_IN(w.x, 0, n_cav, batch_err);
         const BatchCavity& bc = cav[work ? w.x : 0];
         const int tpr = bc.tpr;
         const int rg = tid / tpr;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         if constexpr (SR)
             if (work) salt = hash32((unsigned)__ldg(bc.args[parity].step_in) * 0x9e3779b9u + 0x632be5abu);
         process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
-                                 rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so);
+                                 rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so, nullptr, (unsigned)kStageBytes);
         // One barrier per item: it releases the stage and tells every thread
         // whether any wait expired; with none expired, w is the same valid
         // entry in every thread, so the end test is block-uniform.
@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         }
         const bool ok = mbar_wait_bounded(&bars[s], phase);
         const int4 w = stage_item[s];
-        const bool work = ok && w.x >= 0;
+        const bool work = ok && w.x >= 0 && DMRT_IN(w.x, 0, n_cav, batch_err);
         const BatchCavity& bc = cav[work ? w.x : 0];
         const int tpr = bc.tpr;
         const int rg = tid / tpr;
@@ -386,7 +386,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
             if (work)
                 salt = hash32((unsigned)(__ldcg(bc.args[parity].step_in) + w.w) * 0x9e3779b9u + 0x632be5abu);
         process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, bc.args[src], bc.K, work ? w.y : 1, w.z, rg, t,
-                                 work, salt, bc.W, bc.WB, bc.RC, bc.so);
+                                 work, salt, bc.W, bc.WB, bc.RC, bc.so, nullptr, (unsigned)kStageBytes);
         __threadfence();  // this thread's stores (state, Nusselt rows) before the item is counted
         if (__syncthreads_count(!ok || w.x == -2)) {
             timed_out = true;

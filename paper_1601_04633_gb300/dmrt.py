@@ -17,7 +17,10 @@ import threading
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libdmrt.so")
+# DMRT_LIBRARY=bounds_check selects the bounds-checked build (every computed
+# index checked in the kernels; a violation is reported as DMRT_E_BOUNDS).
+LIB_PATH = os.path.join(_PKG, "_lib", "libdmrt_bc.so" if os.environ.get("DMRT_LIBRARY") == "bounds_check"
+                        else "libdmrt.so")
 
 DMRT_OK = 0
 DMRT_E_ARG = -1
@@ -27,6 +30,7 @@ DMRT_E_DIVERGED = -4
 DMRT_E_TIMEOUT = -5
 DMRT_E_SPACE = -6
 DMRT_E_STATE = -7
+DMRT_E_BOUNDS = -8
 DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED = 0, 1, 2, 3
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
 DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA, DMRT_KERNEL_CLUSTER = 0, 1, 2, 3
@@ -42,7 +46,7 @@ def device_pitch(nx: int) -> int:
     return (int(nx) + 127) // 128 * 128
 
 _ERRNAMES = {-1: "DMRT_E_ARG", -2: "DMRT_E_UNSTABLE", -3: "DMRT_E_CUDA", -4: "DMRT_E_DIVERGED",
-             -5: "DMRT_E_TIMEOUT", -6: "DMRT_E_SPACE", -7: "DMRT_E_STATE"}
+             -5: "DMRT_E_TIMEOUT", -6: "DMRT_E_SPACE", -7: "DMRT_E_STATE", -8: "DMRT_E_BOUNDS"}
 
 
 class DmrtError(RuntimeError):
