@@ -474,6 +474,11 @@ typedef struct {
     int32_t tma_npt, tma_rows, tma_stages, graph_steps;
     int64_t group_bytes;
     int32_t steps_per_launch;
+    int32_t tensor_store;  /* 0: stores from registers; 1: the results of an item go
+                              through a shared-memory tile and leave by tensor stores
+                              (per-cavity store maps; one launch per step only).
+                              Compiled: FP32 (2,1,2) (2,2,2); MIXED, both roundings,
+                              (2,2,2) (4,2,2) (4,4,2). The same bits either way. */
 } dmrt_batch_opts;
 
 /* Device workspace for a batch of n cavities (the members' workspaces plus the

@@ -2044,14 +2044,19 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     const dmrt::TmaVariant* vars = dmrt::tma_variants_batch(&nv);
     const void* func = nullptr;
     const int storage = arr[0].storage;
+    // Epilogue: register stores, or tensor stores through shared memory.
+    const bool ts = opts && opts->tensor_store > 0;
     for (int i = 0; i < nv; ++i)
         if (vars[i].storage == storage && vars[i].rounding == resolved_rounding(arr[0]) && vars[i].npt == npt &&
-            vars[i].R == R &&
-            vars[i].S == S)
+            vars[i].R == R && vars[i].S == S && (vars[i].ts != 0) == ts)
             func = vars[i].func;
     if (!func) {
-        set_err(nullptr, "no batched tile with %d nodes/thread, %d rows, %d stages is compiled in for this storage",
-                npt, R, S);
+        set_err(nullptr, "no batched tile with %d nodes/thread, %d rows, %d stages%s is compiled in for this storage",
+                npt, R, S, ts ? " and tensor stores" : "");
+        return DMRT_E_ARG;
+    }
+    if (ts && K > 1) {
+        set_err(nullptr, "the multi-step batched kernel stores from registers (tensor_store must be 0)");
         return DMRT_E_ARG;
     }
     const void* mfunc = nullptr;
@@ -2161,14 +2166,21 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         items += (long long)cav[i].n_strips * cav[i].n_rowblocks;
         for (int bf = 0; bf < 2; ++bf) {
             CUtensorMap* m = &maps[((size_t)i * 2 + bf) * dmrt::kBatchMaps];
+            // Loads from buffer bf; the epilogue's stores (W x RC boxes, nx columns) to the other one.
+            float* dst = buf(c, 1 - bf);
+            const int sm = dmrt::kBatchStoreMap;
             if (split) {  // 9 float16 flow planes, then 5 float32 thermal planes
                 char* g = reinterpret_cast<char*>(buf(c, bf)) + (size_t)9 * c->L.plane * 2;
+                char* gd = reinterpret_cast<char*>(dst) + (size_t)9 * c->L.plane * 2;
                 rc = encode_map(c, &m[0], buf(c, bf), DMRT_FP16, 9, 3, RC, WB);
                 if (!rc) rc = encode_map(c, &m[1], g, DMRT_FP32, 5, 3, RC, WB);
                 if (!rc) rc = encode_map(c, &m[2], g, DMRT_FP32, 5, 1, RC, WB);
+                if (!rc) rc = encode_map(c, &m[sm], dst, DMRT_FP16, 9, 9, RC, W, c->p.nx);
+                if (!rc) rc = encode_map(c, &m[sm + 1], gd, DMRT_FP32, 5, 5, RC, W, c->p.nx);
             } else {
                 rc = encode_map(c, &m[0], buf(c, bf), DMRT_FP32, kPlanes, 6, RC, WB);
                 if (!rc) rc = encode_map(c, &m[1], buf(c, bf), DMRT_FP32, kPlanes, 4, RC, WB);
+                if (!rc) rc = encode_map(c, &m[sm], dst, DMRT_FP32, kPlanes, kPlanes, RC, W, c->p.nx);
             }
             if (rc) {
                 std::snprintf(b->err, sizeof b->err, "cavity %d: %.200s", i, c->err);
@@ -2233,7 +2245,7 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     if (e != cudaSuccess) return fail(batch_cuda_fail(b, e, "batch tables"));
     // Launch shape: persistent grid of resident blocks.
     b->block = R * (256 / npt);
-    b->smem = dmrt::tma_smem_bytes_fg(R, S, split ? 2 : 4, 4);
+    b->smem = dmrt::batch_smem_bytes(ts, R, S, split ? 2 : 4, 4);
     int dev = 0, sms = 0, per_sm = 0;
     e = cudaFuncSetAttribute(b->func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);

@@ -47,9 +47,13 @@ struct ClusterArgs {
     int rows_per;    // rows per block
 };
 
+// Means kept in block 0's shared memory between their flushes to the ring.
+constexpr int kClusterNuChunk = 1024;
+
 __host__ __device__ constexpr size_t cluster_smem_bytes(int rows_per, int nx, int ny) {
     return (size_t)2 * kPlanes * rows_per * nx * sizeof(float)      // both buffers
-           + (((size_t)2 * rows_per * sizeof(float) + 15) & ~size_t(15))  // theta at x = 0 and 1, per row
+           + (((size_t)4 * rows_per * sizeof(float) + 15) & ~size_t(15))  // theta at x = 0 and 1; hot, cold walls
+           + (size_t)kClusterNuChunk * sizeof(double)                  // means not yet in the ring (block 0)
            + (size_t)2 * ny * sizeof(double);                         // Nusselt rows (block 0), by step parity
 }
 
@@ -85,7 +89,9 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     extern __shared__ __align__(16) unsigned char smem_c[];
     float* sb[2] = {reinterpret_cast<float*>(smem_c), reinterpret_cast<float*>(smem_c) + kPlanes * plane_sm};
     float* th01 = reinterpret_cast<float*>(smem_c) + 2 * kPlanes * plane_sm;
+    float* walls = th01 + 2 * RP;  // hot and cold wall temperatures of this block's rows
     double* nur = reinterpret_cast<double*>(smem_c + cluster_smem_bytes(RP, nx, ny) - (size_t)2 * ny * sizeof(double));
+    double* means = nur - kClusterNuChunk;
 
     grid_dep_wait();
     grid_dep_launch();
@@ -96,6 +102,10 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
         const float* src = A0.src + (size_t)(r0 + r) * pitch + x;
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) sb[0][p * plane_sm + i] = src[p * PL];
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        walls[r] = __ldg(A0.hot + r0 + r);
+        walls[RP + r] = __ldg(A0.cold + r0 + r);
     }
     const long long t0 = *A0.step_in;
     if (rank == 0 && warp == 0 && *A0.pending) {
@@ -166,7 +176,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
                 f[1] = own(plane_f(3));
                 f[5] = own(plane_f(7));
                 f[8] = own(plane_f(6));
-                const float add = K.left_fixed ? K.abb * __ldg(A0.hot + j) : 0.f;
+                const float add = K.left_fixed ? K.abb * walls[r] : 0.f;
                 g[1] = sign_l_g * own(plane_g(3)) + add;
             }
             // Right wall (x = nx - 1): links with e_x = -1.
@@ -174,7 +184,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
                 f[3] = own(plane_f(1));
                 f[6] = own(plane_f(8));
                 f[7] = own(plane_f(5));
-                const float add = K.right_fixed ? K.abb * __ldg(A0.cold + j) : 0.f;
+                const float add = K.right_fixed ? K.abb * walls[RP + r] : 0.f;
                 g[3] = sign_r_g * own(plane_g(1)) + add;
             }
             float rho, theta;
@@ -191,16 +201,22 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
         for (int r = threadIdx.x; r < nr; r += blockDim.x) {
             const int j = r0 + r;
             if (!DMRT_IN(j, 0, ny, A0.err)) continue;
-            const double tw = (double)__ldg(A0.hot + j);
+            const double tw = (double)walls[r];
             nu_dst[j] = K.nu_scale * (8.0 * tw - 9.0 * (double)th01[2 * r] + (double)th01[2 * r + 1]);
         }
         cl.sync();  // the new state and the step's Nusselt rows are visible to the whole cluster
         if (rank == 0 && warp == 0) {
-            // Mean of this step's rows while the other warps start the next step.
+            // Mean of this step's rows while the other warps start the next step,
+            // kept in shared memory; a full chunk goes to the ring (global stores
+            // only once per kClusterNuChunk steps, so that the barriers between
+            // steps do not wait for them).
             const double sum = warp_fixed_sum(nur + (size_t)(s & 1) * ny, ny, lane);
-            if (lane == 0) {
-                A0.nu_ring[(t0 + s) % A0.cap] = sum / A0.nu_div;
-                *A0.nu_last = sum / A0.nu_div;
+            if (lane == 0) means[s % kClusterNuChunk] = sum / A0.nu_div;
+            __syncwarp();
+            if (s % kClusterNuChunk == kClusterNuChunk - 1 || s == C.steps - 1) {
+                const int first = s - s % kClusterNuChunk;
+                for (int q = lane; q <= s - first; q += 32) A0.nu_ring[(t0 + first + q) % A0.cap] = means[q];
+                if (lane == 0) *A0.nu_last = means[s - first];
             }
         }
     }

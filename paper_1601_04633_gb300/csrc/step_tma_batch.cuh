@@ -16,8 +16,21 @@ namespace dmrt {
 // stage's shared memory allow), so narrow cavities keep the block's lanes busy.
 // Float32 storage (one-type layout, two tensor maps per buffer: 6-plane and
 // 4-plane boxes) or mixed storage (split layout, three: 3-plane flow boxes,
-// 3-plane and 1-plane thermal boxes); maps[(c * 2 + buffer) * 3 + k].
-constexpr int kBatchMaps = 3;
+// 3-plane and 1-plane thermal boxes); then the epilogue's store maps into the
+// other buffer (one-type: one 14-plane box W x RC; split: a 9-plane flow and a
+// 5-plane thermal box), spanning nx columns; maps[(c * 2 + buffer) * 5 + k].
+constexpr int kBatchMaps = 5;
+constexpr int kBatchStoreMap = 3;
+
+// Shared memory of a batched block: S stages, with TS two output tiles (each
+// the size of a stage, which bounds every cavity's tile), and S mbarriers.
+__host__ __device__ constexpr size_t batch_out_bytes(int R, int f_bytes, int g_bytes) {
+    return round128(tma_stage_bytes_fg(R, f_bytes, g_bytes) + 128);
+}
+__host__ __device__ constexpr size_t batch_smem_bytes(bool ts, int R, int S, int f_bytes, int g_bytes) {
+    return (size_t)S * tma_stage_bytes_fg(R, f_bytes, g_bytes) + (ts ? 2 * batch_out_bytes(R, f_bytes, g_bytes) : 0) +
+           (size_t)S * 8;
+}
 struct BatchCavity {
     StepArgs args[2];  // by source buffer: args[b] reads buffer b, writes 1 - b
     StepConsts K;
@@ -44,7 +57,10 @@ struct BatchCavity {
 // completes while the item is computed) and finds an item's cavity in the
 // compact item_base array (first item of each cavity; n_cav + 1 entries,
 // cached in L1) rather than in the cavity records.
-template <typename L, int NPT, int R, int S, bool SR = false>
+// TS: results go through a shared-memory output tile (two, alternating) and
+// leave by tensor stores issued by one thread after the item's barrier, as in
+// the single-cavity kernel, with the cavity's own store maps.
+template <typename L, int NPT, int R, int S, bool SR = false, bool TS = false>
 __global__ void __launch_bounds__(R * (256 / NPT))
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
                           const int* __restrict__ item_base, int n_cav, int total_items, int static_per_block,
@@ -52,9 +68,11 @@ __global__ void __launch_bounds__(R * (256 / NPT))
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
     constexpr size_t kStageBytes = tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));  // a multiple of 128
+    constexpr size_t kOutBytes = batch_out_bytes(R, sizeof(Ef), sizeof(Eg));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* stages = smem_raw;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);
+    unsigned char* outs = smem_raw + (size_t)S * kStageBytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(outs + (TS ? 2 * kOutBytes : 0));
     __shared__ int4 stage_item[S];  // (cavity, strip, row block, item) of each stage; cavity -1: no more items
     constexpr int HALO = L::kHalo;
     const int tid = threadIdx.x;
@@ -163,8 +181,14 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         unsigned salt = 0;
         if constexpr (SR)
             if (work) salt = hash32((unsigned)__ldg(bc.args[parity].step_in) * 0x9e3779b9u + 0x632be5abu);
-        process_item<L, NPT, SR>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
-                                 rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so, nullptr, (unsigned)kStageBytes);
+        unsigned char* out = outs + (size_t)(k & 1) * kOutBytes;
+        process_item<L, NPT, SR, TS>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
+                                     rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so, out, (unsigned)kStageBytes,
+                                     (unsigned)kOutBytes);
+        if constexpr (TS) {
+            fence_async_smem();
+            if (tid == 0) bulk_wait_read_all();  // item k - 1's store has read the other tile
+        }
         // One barrier per item: it releases the stage and tells every thread
         // whether any wait expired; with none expired, w is the same valid
         // entry in every thread, so the end test is block-uniform.
@@ -173,11 +197,20 @@ __global__ void __launch_bounds__(R * (256 / NPT))
             break;
         }
         if (w.x < 0) break;
+        if (TS && tid == 0 && work) {
+            // The item's tile (W x RC nodes of every plane) to the other buffer.
+            const CUtensorMap* m = maps + ((size_t)w.x * 2 + parity) * kBatchMaps + kBatchStoreMap;
+            const int x = w.y * bc.W, j0 = w.z * bc.RC;
+            tma_store_3d(m, out, x, j0, 0);
+            if constexpr (L::kSplit) tma_store_3d(m + 1, out + out_g_offset(true, bc.RC, bc.W, sizeof(Ef)), x, j0, 0);
+            bulk_commit();
+        }
         if (++s == S) {
             s = 0;
             phase ^= 1u;
         }
     }
+    if (TS && tid == 0) bulk_wait_all();  // the stores have read their tiles and written global memory
     if (timed_out && tid == 0) {
         atomicOr(batch_err, kErrTimeout);
         for (int q = k; q < issued; ++q) mbar_wait_bounded(&bars[q % S], (uint32_t)((q / S) & 1));

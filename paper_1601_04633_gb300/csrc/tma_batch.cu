@@ -43,6 +43,15 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 3, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 3, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2, true>},
+    // Tensor-store epilogue.
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 2, 2, 1, (const void*)step_tma_batch_kernel<OneType<float>, 2, 2, 2, false, true>},
+    {DMRT_FP32, DMRT_ROUND_NEAREST, 2, 1, 2, 1, (const void*)step_tma_batch_kernel<OneType<float>, 2, 1, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 2, 1, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 2, 2, 1, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 4, 2, 1, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2, false, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 2, 1, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 2, 2, 1, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2, true, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 4, 2, 1, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2, true, true>},
 };
 
 const TmaVariant* tma_variants_batch(int* n) {

@@ -83,10 +83,12 @@ GROUP_BYTES = [0, 24 << 20, 40 << 20, 64 << 20, 96 << 20]
 BATCH_MSTEP_TILES = {0: [(1, 2, 2), (2, 1, 2), (2, 2, 2), (2, 2, 3), (4, 2, 2), (4, 4, 2)],
                      3: [(2, 2, 2), (4, 2, 2), (4, 4, 2)]}
 STEPS_PER_LAUNCH = [1, 8, 32]
+# Tiles compiled with the tensor-store epilogue (one launch per step).
+BATCH_TS_TILES = {0: [(2, 1, 2), (2, 2, 2)], 3: [(2, 2, 2), (4, 2, 2), (4, 4, 2)]}
 
 
 def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0, rounding=0,
-               group_bytes=(0,), steps_per_launch=(1,), finalists=3):
+               group_bytes=(0,), steps_per_launch=(1,), tensor_store=False, finalists=3):
     """Pick the batched kernel's tile, cavity-group size and steps per launch
     for these cavities (storage 0: float32, 3: mixed). Every tile is timed with
     the first group size and one step per launch; the `finalists` fastest tiles
@@ -96,15 +98,16 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
     from . import dmrt as D
 
     key = _key("batch", [(c.nx, c.ny) for c in cavities],
-               f"{steps}-{storage}-{rounding}-{list(group_bytes)}-{list(steps_per_launch)}")
+               f"{steps}-{storage}-{rounding}-{list(group_bytes)}-{list(steps_per_launch)}-{tensor_store}")
     hit = _cache_get(cache, key)
     if hit:
         return hit
     nodes = sum(c.nx * c.ny for c in cavities)
     trials = []
 
-    def trial(npt, R, S, g, gb, K):
-        opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g, group_bytes=gb, steps_per_launch=K)
+    def trial(npt, R, S, g, gb, K, ts=0):
+        opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g, group_bytes=gb, steps_per_launch=K,
+                    tensor_store=ts)
         glen = 2 * K if K > 1 else g
         # The warm-up covers one whole graph, so its instantiation is not timed.
         b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + glen + 8, storage=storage,
@@ -117,7 +120,7 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
     for npt, R, S in (tiles or BATCH_TILES):
         for g in graph_steps:
             trial(npt, R, S, g, group_bytes[0], 1)
-    if len(group_bytes) > 1 or len(steps_per_launch) > 1:
+    if len(group_bytes) > 1 or len(steps_per_launch) > 1 or tensor_store:
         top = sorted(trials, key=lambda r: -r["mlups"])[:finalists]
         for t in top:
             o = t["opts"]
@@ -129,6 +132,9 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
                     if (gb, K) == (group_bytes[0], 1):
                         continue
                     trial(*tile, o["graph_steps"], gb, K)
+            if tensor_store and tile in BATCH_TS_TILES.get(storage, []):
+                for gb in group_bytes:
+                    trial(*tile, o["graph_steps"], gb, 1, 1)
     best = max(trials, key=lambda r: r["mlups"])
     out = {"opts": best["opts"], "mlups": best["mlups"], "trials": trials}
     _cache_put(cache, key, out)
@@ -178,6 +184,7 @@ def main():
                     help="cavity-group sizes to try, MB of both buffers (batched sweep; 0: one group)")
     ap.add_argument("--steps-per-launch", type=int, nargs="*", default=[1],
                     help="steps per launch to try (batched sweep; 1: one launch per step)")
+    ap.add_argument("--tensor-store", action="store_true", help="also try the tensor-store epilogue (batched sweep)")
     ap.add_argument("--cache", default=None)
     args = ap.parse_args()
     tiles = [tuple(args.tile)] if args.tile else None
@@ -185,7 +192,7 @@ def main():
         print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, tiles=tiles,
                                     graph_steps=(args.graph_steps,), cache=args.cache, storage=args.storage,
                                     rounding=args.rounding, group_bytes=[m << 20 for m in args.group_mb],
-                                    steps_per_launch=args.steps_per_launch),
+                                    steps_per_launch=args.steps_per_launch, tensor_store=args.tensor_store),
                          indent=1))
     if args.single:
         cav = inputs.Cavity(args.single, args.single, 1e7, 0.001, seed=5)

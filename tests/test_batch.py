@@ -123,6 +123,32 @@ def test_multistep_launches_give_the_same_bits(D, storage, rounding, K):
         ref.close()
 
 
+TS_TILES = {0: [(2, 1, 2), (2, 2, 2)], 3: [(2, 2, 2), (4, 2, 2), (4, 4, 2)]}
+
+
+@pytest.mark.parametrize("storage,rounding", [(0, 0), (3, 0), (3, 1)], ids=["fp32", "mixed", "mixed_sr"])
+def test_tensor_store_epilogue_gives_the_same_bits(D, storage, rounding):
+    # Results through a shared-memory tile and the cavity's own store maps:
+    # exactly the register-store results, for every compiled tile, with groups.
+    cavs = _uneven()
+    for npt, R, S in TS_TILES[storage]:
+        base = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=16)
+        ref = D.Batch.from_inputs(cavs, opts=base, nu_capacity=64, storage=storage, rounding=rounding)
+        runs = [D.Batch.from_inputs(cavs, opts=dict(base, tensor_store=1), nu_capacity=64, storage=storage,
+                                    rounding=rounding),
+                D.Batch.from_inputs(cavs, opts=dict(base, tensor_store=1, group_bytes=4000 << 10), nu_capacity=64,
+                                    storage=storage, rounding=rounding)]
+        for b in [ref] + runs:
+            b.step(37)
+            b.check()
+        for b in runs:
+            for i in range(len(cavs)):
+                assert np.array_equal(b.members[i].get_state(), ref.members[i].get_state()), (npt, R, S, i)
+                assert np.array_equal(b.members[i].nusselt(37)[2], ref.members[i].nusselt(37)[2]), (npt, R, S, i)
+            b.close()
+        ref.close()
+
+
 def test_multistep_sweep_member_matches_single_context(D):
     # The 64-cavity sweep, 8 steps per launch: sampled members against their own
     # contexts stepped alone.

@@ -76,6 +76,20 @@ def test_multistep_batch_tiles_match_the_tuner_and_have_single_step_twins():
     assert {k[:2] for k in mstep} == {(0, 0), (3, 0), (3, 1)}
 
 
+def test_tensor_store_batch_tiles_match_the_tuner():
+    import re as _re
+
+    ts = set()
+    with open(os.path.join(CSRC, "tma_batch.cu")) as fh:
+        for line in fh:
+            m = ENTRY.search(line)
+            if m and m.group(6) == "1":
+                ts.add((STORAGE[m.group(1)], ROUNDING[m.group(2)], int(m.group(3)), int(m.group(4)), int(m.group(5))))
+                assert _re.search(r", true>\}", line), line  # the TS template argument
+    for st, rd in ((0, 0), (3, 0), (3, 1)):
+        assert {k[2:] for k in ts if k[:2] == (st, rd)} == set(tune.BATCH_TS_TILES[st]), (st, rd)
+
+
 def test_default_tiles_are_compiled():
     # The library's defaults (storage, rounding -> tile) and the small-grid
     # tiles it switches to: float32 (1,4,2), one-row (1,1,2) and (2,1,3);
