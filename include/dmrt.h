@@ -431,8 +431,14 @@ void dmrt_destroy(dmrt_ctx* c);
  * array [ny]) and dJ/dRa (each output nullable). Float32 storage only;
  * nu_capacity >= avg_last. workspace: device memory of
  * dmrt_adjoint_workspace_size() bytes, 256-byte aligned, used only during the
- * call. Synchronises; DMRT_E_DIVERGED if the forward run diverged. */
+ * call: then each segment's recompute runs on a second stream (created on the
+ * first such call, released by dmrt_destroy) while the reverse sweep of the
+ * segment after it runs on the context's stream. A workspace of at least
+ * dmrt_adjoint_workspace_min() bytes (one set of segment states fewer) also
+ * works: recompute and sweep then alternate on the context's stream. Both give
+ * the same bits. Synchronises; DMRT_E_DIVERGED if the forward run diverged. */
 int dmrt_adjoint_workspace_size(const dmrt_ctx* c, int64_t nsteps, size_t* bytes);
+int dmrt_adjoint_workspace_min(const dmrt_ctx* c, int64_t nsteps, size_t* bytes);
 int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace, size_t workspace_bytes,
                  double* J, double* dJ_dthetaw, double* dJ_dRa);
 

@@ -33,8 +33,9 @@ struct AdjArgs {
     float* __restrict__ nu_out;        // nu_k
     const float* __restrict__ hot;
     const float* __restrict__ cold;
-    double* dthw;                      // [ny] dJ/dtheta_w, accumulated
-    double* dgbeta;                    // dJ/dgbeta, accumulated per block: [gridDim.y][gridDim.x]
+    double* dthw;                      // [ny] dJ/dtheta_w, accumulated (the final gather only)
+    double* dthw_step;                 // [ny] this step's dJ/dtheta_w terms (written, not accumulated)
+    double* dgbeta_step;               // this step's dJ/dgbeta per block: [gridDim.y][gridDim.x]
     long long plane;
     int nx, ny, pitch;
     float w;                           // w_k (0 outside the averaging window)
@@ -163,7 +164,11 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
             lg[m] = fixed ? -val : val;  // anti-bounce-back (Eq. 45) / bounce-back (Eq. 44)
         }
     }
-    if (in && i == 0 && K.left_fixed) A.dthw[j] += (double)abb * (double)at(A.nu_in, plane_g(1), 0, j);
+    // This step's anti-bounce-back term of dJ/dtheta_w(j) (0 for an adiabatic
+    // hot wall): written into the step's own row, summed after the segment in
+    // step order, so no read-modify-write sits at the end of every step.
+    if (in && i == 0)
+        A.dthw_step[j] = K.left_fixed ? (double)abb * (double)at(A.nu_in, plane_g(1), 0, j) : 0.0;
 
     // q_k at this node: the forward pull of s_{k-1}.
     float f[9], g[5];
@@ -204,9 +209,9 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
         for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
     }
     // dJ/dgbeta: the block's sum in fp64 in a fixed order (butterfly within each
-    // warp, then the four warps in order), added to the block's own slot. The
-    // steps run one after another, so no atomics are needed and the sum over
-    // the slots, taken in index order at the end, is the same in every run.
+    // warp, then the four warps in order), written to the block's slot of this
+    // step; after the segment, the slots are added to the block's total in step
+    // order (adjoint_fold_kernel), so every run gives the same bits.
     __shared__ double warp_sum[4];
     double d = in ? (double)dgb : 0.0;
 #pragma unroll
@@ -214,7 +219,26 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
     if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = d;
     __syncthreads();
     if (threadIdx.x == 0)
-        A.dgbeta[(size_t)blockIdx.y * gridDim.x + blockIdx.x] += ((warp_sum[0] + warp_sum[1]) + warp_sum[2]) + warp_sum[3];
+        A.dgbeta_step[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = ((warp_sum[0] + warp_sum[1]) + warp_sum[2]) + warp_sum[3];
+}
+
+// After a segment's reverse steps: add each step's per-block dJ/dgbeta and per-row
+// dJ/dtheta_w terms to the totals, the segment's last step first (the order in
+// which the steps ran), one thread per slot.
+__global__ void adjoint_fold_kernel(double* __restrict__ dgbeta, const double* __restrict__ dgbeta_steps,
+                                    long long n_blocks, double* __restrict__ dthw,
+                                    const double* __restrict__ dthw_steps, int ny, int len) {
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n_blocks) {
+        double acc = dgbeta[q];
+        for (int t = len - 1; t >= 0; --t) acc += dgbeta_steps[(size_t)t * n_blocks + q];
+        dgbeta[q] = acc;
+    }
+    if (q < ny) {
+        double acc = dthw[q];
+        for (int t = len - 1; t >= 0; --t) acc += dthw_steps[(size_t)t * ny + q];
+        dthw[q] = acc;
+    }
 }
 
 }  // namespace dmrt

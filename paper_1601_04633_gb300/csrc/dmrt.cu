@@ -120,6 +120,9 @@ struct dmrt_ctx {
     bool cluster;
     int csize, crows, cthreads;
     size_t csmem;
+    // Adjoint: a second stream and events for the overlapped recompute (created at first use).
+    cudaStream_t aux;
+    cudaEvent_t ev[5];
     cudaGraphExec_t graph[2];
     int graph_len;
     long long nu_floor;  // ring values of steps before this one are unavailable (after a load)
@@ -1779,6 +1782,12 @@ void dmrt_destroy(dmrt_ctx* c) {
     cudaStreamSynchronize(c->stream);
     for (int i = 0; i < 2; ++i)
         if (c->graph[i]) cudaGraphExecDestroy(c->graph[i]);
+    if (c->aux) {
+        cudaStreamSynchronize(c->aux);
+        for (cudaEvent_t e : c->ev)
+            if (e) cudaEventDestroy(e);
+        cudaStreamDestroy(c->aux);
+    }
     delete c;
 }
 
@@ -2389,7 +2398,10 @@ namespace {
 struct AdjLayout {
     long long K, C;  // checkpoint interval and count
     size_t state;    // bytes of one state
-    size_t off_ckpt, off_seg, off_nu0, off_nu1, off_dthw, off_dgb, off_misc, off_rows, total;
+    size_t off_ckpt, off_nu0, off_nu1, off_dthw, off_dgb, off_misc, off_rows, off_sdgb, off_sdthw;
+    size_t off_seg[2];  // segment slots: one set, or two when the recompute overlaps the reverse sweep
+    size_t total_seq;   // bytes with one set of segment slots
+    size_t total;       // bytes with two
     long long n_blocks;  // blocks of the reverse-step grid: one dJ/dgbeta slot each
 };
 
@@ -2400,8 +2412,6 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.C = (N + L.K - 1) / L.K;
     L.state = align256((size_t)kPlanes * (size_t)c->L.plane * sizeof(float));
     size_t o = 0;
-    L.off_ckpt = o; o += (size_t)L.C * L.state;
-    L.off_seg = o; o += (size_t)L.K * L.state;
     L.off_nu0 = o; o += L.state;
     L.off_nu1 = o; o += L.state;
     L.off_dthw = o; o += align256((size_t)c->p.ny * sizeof(double));
@@ -2409,6 +2419,12 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_dgb = o; o += align256((size_t)L.n_blocks * sizeof(double));
     L.off_misc = o; o += 256;
     L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
+    L.off_sdgb = o; o += align256((size_t)L.K * L.n_blocks * sizeof(double));  // per step of a segment
+    L.off_sdthw = o; o += align256((size_t)L.K * c->p.ny * sizeof(double));
+    L.off_ckpt = o; o += (size_t)L.C * L.state;
+    L.off_seg[0] = o; o += (size_t)L.K * L.state;
+    L.total_seq = o;
+    L.off_seg[1] = o; o += (size_t)L.K * L.state;
     L.total = o;
     return L;
 }
@@ -2420,6 +2436,12 @@ extern "C" {
 int dmrt_adjoint_workspace_size(const dmrt_ctx* c, int64_t nsteps, size_t* bytes) {
     if (!c || !bytes || nsteps < 1) return DMRT_E_ARG;
     *bytes = adjoint_layout(c, nsteps).total;
+    return DMRT_OK;
+}
+
+int dmrt_adjoint_workspace_min(const dmrt_ctx* c, int64_t nsteps, size_t* bytes) {
+    if (!c || !bytes || nsteps < 1) return DMRT_E_ARG;
+    *bytes = adjoint_layout(c, nsteps).total_seq;
     return DMRT_OK;
 }
 
@@ -2444,13 +2466,26 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         return DMRT_E_ARG;
     }
     const AdjLayout AL = adjoint_layout(c, nsteps);
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < AL.total) {
-        set_err(c, "adjoint workspace: need %zu bytes, 256-byte aligned", AL.total);
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < AL.total_seq) {
+        set_err(c, "adjoint workspace: need %zu bytes (%zu to overlap the recompute with the reverse sweep), "
+                   "256-byte aligned", AL.total_seq, AL.total);
         return DMRT_E_SPACE;
     }
+    // With room for two sets of segment slots, the recompute of the next segment
+    // runs on a second stream while the reverse sweep of the current one runs on
+    // the context's stream (the two are latency-bound launches of a few hundred
+    // blocks, so they share the GPU); with one set they alternate.
+    const bool overlap = workspace_bytes >= AL.total;
+    if (overlap && !c->aux) {
+        CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "adjoint stream");
+        for (int i = 0; i < 5; ++i) CK(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming), "adjoint event");
+    }
+    cudaStream_t rs = overlap ? c->aux : c->stream;  // the recompute's stream
     char* w = static_cast<char*>(workspace);
     auto ckpt = [&](long long q) { return reinterpret_cast<float*>(w + AL.off_ckpt + (size_t)q * AL.state); };
-    auto slot = [&](long long q) { return reinterpret_cast<float*>(w + AL.off_seg + (size_t)q * AL.state); };
+    auto slot = [&](int set, long long q) {
+        return reinterpret_cast<float*>(w + AL.off_seg[set] + (size_t)q * AL.state);
+    };
     const size_t copy_bytes = (size_t)kPlanes * (size_t)c->L.plane * sizeof(float);
     const long long N = nsteps, K = AL.K;
 
@@ -2476,10 +2511,12 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     float* nu_a = reinterpret_cast<float*>(w + AL.off_nu0);
     float* nu_b = reinterpret_cast<float*>(w + AL.off_nu1);
     double* dthw = reinterpret_cast<double*>(w + AL.off_dthw);
+    double* sdgb = reinterpret_cast<double*>(w + AL.off_sdgb);
+    double* sdthw = reinterpret_cast<double*>(w + AL.off_sdthw);
     Misc* scratch = reinterpret_cast<Misc*>(w + AL.off_misc);
     CK(cudaMemsetAsync(nu_a, 0, copy_bytes, c->stream), "zero adjoint");
     CK(cudaMemsetAsync(w + AL.off_dthw, 0, AL.off_rows - AL.off_dthw, c->stream), "zero gradients");
-    double* dgb = reinterpret_cast<double*>(w + AL.off_dgb);  // per-block slots, zeroed with the gradients
+    double* dgb = reinterpret_cast<double*>(w + AL.off_dgb);  // per-block totals, zeroed with the gradients
     dmrt::StepArgs RA = step_args(c, 0);  // recompute: Nusselt output into scratch
     double* ra_rows = reinterpret_cast<double*>(w + AL.off_rows);  // two buffers, alternating by step
     RA.nu_ring = ra_rows + 2 * (size_t)c->p.ny;
@@ -2493,7 +2530,6 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     AA.hot = reinterpret_cast<const float*>(c->ws + c->L.off_hot);
     AA.cold = reinterpret_cast<const float*>(c->ws + c->L.off_cold);
     AA.dthw = dthw;
-    AA.dgbeta = dgb;
     AA.plane = c->L.plane;
     AA.nx = c->p.nx;
     AA.ny = c->p.ny;
@@ -2506,45 +2542,79 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     // kernel every checkpoint and segment slot it reads gets its load maps
     // (float32 storage stores from registers, so no store maps are needed).
     const bool tma_re = c->kernel == DMRT_KERNEL_TMA;
-    std::vector<dmrt::TmaMaps> ck_maps(tma_re ? (size_t)AL.C : 0), sl_maps(tma_re ? (size_t)AL.K : 0);
+    const int nsets = overlap ? 2 : 1;
+    std::vector<dmrt::TmaMaps> ck_maps(tma_re ? (size_t)AL.C : 0), sl_maps(tma_re ? (size_t)(nsets * AL.K) : 0);
     for (size_t q = 0; q < ck_maps.size() + sl_maps.size(); ++q) {
         const bool ck = q < ck_maps.size();
-        dmrt::TmaMaps& m = ck ? ck_maps[q] : sl_maps[q - ck_maps.size()];
-        float* base = ck ? ckpt((long long)q) : slot((long long)(q - ck_maps.size()));
+        const size_t qs = q - ck_maps.size();
+        dmrt::TmaMaps& m = ck ? ck_maps[q] : sl_maps[qs];
+        float* base = ck ? ckpt((long long)q) : slot((int)(qs / AL.K), (long long)(qs % AL.K));
         std::memset(&m, 0, sizeof m);
         rc = encode_map(c, &m.ld[0], base, DMRT_FP32, kPlanes, 6, c->R);
         if (!rc) rc = encode_map(c, &m.ld[1], base, DMRT_FP32, kPlanes, 4, c->R);
         if (rc) return rc;
     }
-    for (long long q = AL.C - 1; q >= 0; --q) {
-        const long long start = q * K, end = std::min(start + K, N), len = end - start;
-        for (long long t = 1; t < len; ++t) {  // s_{start + t} into slot t
-            RA.src = t == 1 ? ckpt(q) : slot(t - 1);
-            RA.dst = slot(t);
+    // Recompute of segment q into slot set `set` on stream rs: s_{start + t} into slot t.
+    auto recompute = [&](long long q, int set) -> int {
+        const long long start = q * K, len = std::min(start + K, N) - start;
+        for (long long t = 1; t < len; ++t) {
+            RA.src = t == 1 ? ckpt(q) : slot(set, t - 1);
+            RA.dst = slot(set, t);
             RA.nu_rows = ra_rows + (size_t)(t & 1) * c->p.ny;
             RA.prev_rows = ra_rows + (size_t)((t + 1) & 1) * c->p.ny;
             if (tma_re) {
-                dmrt::TmaMaps& M = t == 1 ? ck_maps[(size_t)q] : sl_maps[(size_t)(t - 1)];
+                dmrt::TmaMaps& M = t == 1 ? ck_maps[(size_t)q] : sl_maps[(size_t)(set * K + t - 1)];
                 void* params[4] = {&M, &RA, &c->sc, &c->geo};
-                CK(launch_overlapped(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), c->tma_smem, c->stream,
-                                     params),
+                CK(launch_overlapped(c->tma_func, dim3(c->tma_grid), dim3(c->tma_block), c->tma_smem, rs, params),
                    "adjoint recompute launch");
             } else {
-                CK(launch_overlapped(dmrt::step_direct_kernel, c->grid, dim3(dmrt::kDirectThreads), c->stream,
-                                     RA, c->sc),
+                CK(launch_overlapped(dmrt::step_direct_kernel, c->grid, dim3(dmrt::kDirectThreads), rs, RA, c->sc),
                    "adjoint recompute launch");
             }
         }
+        return DMRT_OK;
+    };
+    // Events (overlap): ev[0] the forward pass done; ev[1 + set] recompute into
+    // `set` done; ev[3 + set] reverse sweep from `set` done.
+    if (overlap) {
+        CK(cudaEventRecord(c->ev[0], c->stream), "event");
+        CK(cudaStreamWaitEvent(rs, c->ev[0], 0), "wait");
+    }
+    rc = recompute(AL.C - 1, 0);
+    if (rc) return rc;
+    if (overlap) CK(cudaEventRecord(c->ev[1], rs), "event");
+    for (long long q = AL.C - 1; q >= 0; --q) {
+        const int set = (int)((AL.C - 1 - q) & 1) % nsets;
+        const long long start = q * K, end = std::min(start + K, N), len = end - start;
+        if (overlap && q >= 1) {
+            // Segment q - 1 into the other set, once the sweep that last read it is done.
+            if (q + 1 <= AL.C - 1) CK(cudaStreamWaitEvent(rs, c->ev[3 + (set ^ 1)], 0), "wait");
+            rc = recompute(q - 1, set ^ 1);
+            if (rc) return rc;
+            CK(cudaEventRecord(c->ev[1 + (set ^ 1)], rs), "event");
+        }
+        if (overlap) CK(cudaStreamWaitEvent(c->stream, c->ev[1 + set], 0), "wait");
         for (long long k = end; k > start; --k) {
-            AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(k - 1 - start);
+            const long long t = k - start - 1;  // the step's row of partials
+            AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(set, k - 1 - start);
             AA.nu_in = nu_a;
             AA.nu_out = nu_b;
+            AA.dgbeta_step = sdgb + (size_t)t * AL.n_blocks;
+            AA.dthw_step = sdthw + (size_t)t * c->p.ny;
             AA.w = (k > N - avg_last) ? (float)(1.0 / (double)avg_last) : 0.f;
             CK(launch_overlapped(dmrt::adjoint_step_kernel, agrid, dim3(128), c->stream, AA, c->sc),
                "adjoint step launch");
             std::swap(nu_a, nu_b);
         }
+        const long long nf = std::max<long long>(AL.n_blocks, c->p.ny);
+        dmrt::adjoint_fold_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(
+            dgb, sdgb, AL.n_blocks, dthw, sdthw, c->p.ny, (int)len);
         CK(cudaGetLastError(), "adjoint launch");
+        if (overlap) CK(cudaEventRecord(c->ev[3 + set], c->stream), "event");
+        if (!overlap && q >= 1) {
+            rc = recompute(q - 1, 0);
+            if (rc) return rc;
+        }
     }
     AA.nu_in = nu_a;  // nu_1: the anti-bounce-back term of step 1
     AA.gather_only = 1;

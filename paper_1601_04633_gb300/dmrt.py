@@ -128,6 +128,7 @@ SIGNATURES = {
     "dmrt_load": (ctypes.c_int, [_VP, _VP, ctypes.c_size_t]),
     "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
     "dmrt_adjoint_workspace_size": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_adjoint_workspace_min": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "dmrt_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _DP, _DP, _DP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
     "dmrt_slab_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
@@ -447,13 +448,16 @@ class Cavity2D:
         dmrt_fields(self.h, ptrs[0], ptrs[1], ptrs[2], False)
         return tuple(out) if pinned is None else tuple(t.numpy() for t in pinned)
 
-    def adjoint(self, nsteps: int, avg_last: int):
+    def adjoint(self, nsteps: int, avg_last: int, overlap: bool = True):
         """Advance nsteps and return (J, dJ/dtheta_w [ny], dJ/dRa): J = mean hot-wall Nu
-        over the last avg_last steps. The adjoint workspace is allocated with torch."""
+        over the last avg_last steps. The adjoint workspace is allocated with torch:
+        the full size (segment recompute overlapped with the reverse sweep) or,
+        with overlap=False, the smallest (the two alternate)."""
         import torch
 
         nbytes = ctypes.c_size_t()
-        _check(load().dmrt_adjoint_workspace_size(self.h, int(nsteps), ctypes.byref(nbytes)), self.h)
+        size_fn = load().dmrt_adjoint_workspace_size if overlap else load().dmrt_adjoint_workspace_min
+        _check(size_fn(self.h, int(nsteps), ctypes.byref(nbytes)), self.h)
         ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
         J = ctypes.c_double()
         dth = np.zeros(self.ny)

@@ -75,6 +75,23 @@ def test_adjoint_is_deterministic(D):
     assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
 
 
+@pytest.mark.parametrize("kernel", [1, 2], ids=["direct", "tma"])
+def test_adjoint_same_bits_overlapped_or_alternating(D, kernel):
+    # Segment recompute on a second stream beside the reverse sweep (the full
+    # workspace) or alternating with it (the smallest workspace): the same
+    # launches on the same data, so the same bits; 1000 steps = 32 segments,
+    # the last one short.
+    cav = inputs.Cavity(128, 96, 1e5, 0.01, noise_amp=1e-3, seed=8)
+    cav.theta_hot_profile = 0.5 + 0.02 * np.cos(np.arange(96))
+    out = []
+    for overlap in (True, False):
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=1000, kernel=kernel)
+        out.append(sim.adjoint(1000, 300, overlap=overlap))
+        sim.close()
+    (J1, d1, r1), (J2, d2, r2) = out
+    assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
+
+
 @pytest.mark.parametrize("nx,ny", [(128, 128), (600, 40)])
 def test_adjoint_same_bits_with_either_step_kernel(D, nx, ny):
     # The segment recompute runs the context's step kernel (direct, or TMA with
