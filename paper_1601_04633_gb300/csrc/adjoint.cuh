@@ -35,7 +35,7 @@ struct AdjArgs {
     const float* __restrict__ cold;
     double* dthw;                      // [ny] dJ/dtheta_w, accumulated (the final gather only)
     double* dthw_step;                 // [ny] this step's dJ/dtheta_w terms (written, not accumulated)
-    double* dgbeta_step;               // this step's dJ/dgbeta per block: [gridDim.y][gridDim.x]
+    double* dgbeta_step;               // this step's dJ/dgbeta per warp: [gridDim.y][gridDim.x][4]
     long long plane;
     int nx, ny, pitch;
     float w;                           // w_k (0 outside the averaging window)
@@ -132,65 +132,64 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
     const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const int OP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     const int OP5[5] = {0, 3, 4, 1, 2};
-    auto at = [&](const float* base, int plane, int x, int y) {
-        return __ldg(base + plane * PL + (long long)y * A.pitch + x);
-    };
     const float abb = K.abb;
 
     if (A.gather_only) {
         // Anti-bounce-back on the hot wall: q_east(0, j) = abb theta_w(j) - s_west(0, j).
-        if (in && i == 0 && K.left_fixed) A.dthw[j] += (double)abb * (double)at(A.nu_in, plane_g(1), 0, j);
+        if (in && i == 0 && K.left_fixed)
+            A.dthw[j] += (double)abb * (double)__ldg(A.nu_in + plane_g(1) * PL + (long long)j * A.pitch);
         return;
     }
 
-    // lambda_k: transpose of the pull, gathered from nu_{k+1}.
+    // Offsets within a plane of this node and of its neighbours, and which of
+    // the four sides have a neighbour (the walls lie beyond the others).
+    const long long c0 = (long long)j * A.pitch + ic;
+    const long long P = A.pitch;
+    const bool xm = ic > 0, xp = ic + 1 < A.nx, ym = j > 0, yp = j + 1 < A.ny;
+    auto inside = [&](int ex, int ey) {
+        return (ex > 0 ? xp : ex < 0 ? xm : true) && (ey > 0 ? yp : ey < 0 ? ym : true);
+    };
+    const float* __restrict__ NI = A.nu_in;
+    const float* __restrict__ SP = A.s_prev;
+
+    // lambda_k: transpose of the pull, gathered from nu_{k+1}: the neighbour at
+    // x + e_m, or across a wall the node's own opposite (bounce-back; sign -1
+    // for anti-bounce-back of g).
     float lf[9], lg[5];
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
-        const int xn = ic + EX9[m], yn = j + EY9[m];
-        if (xn >= 0 && xn < A.nx && yn >= 0 && yn < A.ny)
-            lf[m] = at(A.nu_in, plane_f(m), xn, yn);
-        else
-            lf[m] = at(A.nu_in, plane_f(OP9[m]), ic, j);  // bounce-back
+        const bool ok = inside(EX9[m], EY9[m]);
+        lf[m] = __ldg(NI + (ok ? plane_f(m) * PL + c0 + EX9[m] + EY9[m] * P : plane_f(OP9[m]) * PL + c0));
     }
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        const int xn = ic + EX9[m], yn = j + EY9[m];
-        if (xn >= 0 && xn < A.nx && yn >= 0 && yn < A.ny) {
-            lg[m] = at(A.nu_in, plane_g(m), xn, yn);
-        } else {
-            const bool fixed = (xn < 0 && K.left_fixed) || (xn >= A.nx && K.right_fixed);
-            const float val = at(A.nu_in, plane_g(OP5[m]), ic, j);
-            lg[m] = fixed ? -val : val;  // anti-bounce-back (Eq. 45) / bounce-back (Eq. 44)
-        }
+        const bool ok = inside(EX9[m], EY9[m]);
+        const float val = __ldg(NI + (ok ? plane_g(m) * PL + c0 + EX9[m] + EY9[m] * P : plane_g(OP5[m]) * PL + c0));
+        const bool fixed = !ok && ((EX9[m] < 0 && K.left_fixed) || (EX9[m] > 0 && K.right_fixed));
+        lg[m] = fixed ? -val : val;  // anti-bounce-back (Eq. 45) / bounce-back (Eq. 44)
     }
     // This step's anti-bounce-back term of dJ/dtheta_w(j) (0 for an adiabatic
     // hot wall): written into the step's own row, summed after the segment in
     // step order, so no read-modify-write sits at the end of every step.
     if (in && i == 0)
-        A.dthw_step[j] = K.left_fixed ? (double)abb * (double)at(A.nu_in, plane_g(1), 0, j) : 0.0;
+        A.dthw_step[j] = K.left_fixed ? (double)abb * (double)__ldg(NI + plane_g(1) * PL + (long long)j * A.pitch) : 0.0;
 
-    // q_k at this node: the forward pull of s_{k-1}.
+    // q_k at this node: the forward pull of s_{k-1} (the neighbour at x - e_m,
+    // or across a wall the wall rule on the node's own opposite).
     float f[9], g[5];
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
-        const int xs = ic - EX9[m], ys = j - EY9[m];
-        if (xs >= 0 && xs < A.nx && ys >= 0 && ys < A.ny)
-            f[m] = at(A.s_prev, plane_f(m), xs, ys);
-        else
-            f[m] = at(A.s_prev, plane_f(OP9[m]), ic, j);
+        const bool ok = inside(-EX9[m], -EY9[m]);
+        f[m] = __ldg(SP + (ok ? plane_f(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_f(OP9[m]) * PL + c0));
     }
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        const int xs = ic - EX9[m], ys = j - EY9[m];
-        if (xs >= 0 && xs < A.nx && ys >= 0 && ys < A.ny) {
-            g[m] = at(A.s_prev, plane_g(m), xs, ys);
-        } else {
-            const float back = at(A.s_prev, plane_g(OP5[m]), ic, j);
-            if (xs < 0 && K.left_fixed) g[m] = abb * __ldg(A.hot + j) - back;
-            else if (xs >= A.nx && K.right_fixed) g[m] = abb * __ldg(A.cold + j) - back;
-            else g[m] = back;
-        }
+        const bool ok = inside(-EX9[m], -EY9[m]);
+        const float v = __ldg(SP + (ok ? plane_g(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_g(OP5[m]) * PL + c0));
+        if (ok) g[m] = v;
+        else if (EX9[m] > 0 && K.left_fixed) g[m] = abb * __ldg(A.hot + j) - v;     // x - e_m < 0
+        else if (EX9[m] < 0 && K.right_fixed) g[m] = abb * __ldg(A.cold + j) - v;   // x - e_m >= nx
+        else g[m] = v;
     }
 
     float nf[9], ng[5], dgb;
@@ -208,18 +207,16 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
 #pragma unroll
         for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
     }
-    // dJ/dgbeta: the block's sum in fp64 in a fixed order (butterfly within each
-    // warp, then the four warps in order), written to the block's slot of this
-    // step; after the segment, the slots are added to the block's total in step
-    // order (adjoint_fold_kernel), so every run gives the same bits.
-    __shared__ double warp_sum[4];
+    // dJ/dgbeta: each warp's sum in fp64 by a butterfly, written to the warp's
+    // slot of this step; after the segment, each block's four warp sums are
+    // added in order and the result to the block's total in step order
+    // (adjoint_fold_kernel), so every run gives the same bits.
+    // (Each warp writes its own slot; the fold adds a block's four warps in order.)
     double d = in ? (double)dgb : 0.0;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
-    if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = d;
-    __syncthreads();
-    if (threadIdx.x == 0)
-        A.dgbeta_step[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = ((warp_sum[0] + warp_sum[1]) + warp_sum[2]) + warp_sum[3];
+    if ((threadIdx.x & 31) == 0)
+        A.dgbeta_step[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + (threadIdx.x >> 5)] = d;
 }
 
 // After a segment's reverse steps: add each step's per-block dJ/dgbeta and per-row
@@ -231,7 +228,10 @@ __global__ void adjoint_fold_kernel(double* __restrict__ dgbeta, const double* _
     const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q < n_blocks) {
         double acc = dgbeta[q];
-        for (int t = len - 1; t >= 0; --t) acc += dgbeta_steps[(size_t)t * n_blocks + q];
+        for (int t = len - 1; t >= 0; --t) {
+            const double* w = dgbeta_steps + ((size_t)t * n_blocks + q) * 4;  // the block's four warps
+            acc += ((w[0] + w[1]) + w[2]) + w[3];
+        }
         dgbeta[q] = acc;
     }
     if (q < ny) {

@@ -1168,7 +1168,9 @@ static int launch_cluster(dmrt_ctx* c, int n) {
     return DMRT_OK;
 }
 
-int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
+// nsteps steps; with `finalize`, the last step's Nusselt rows are summed into
+// the ring at the end (without, the next launch sums them).
+static int step_run(dmrt_ctx* c, int64_t nsteps, bool finalize) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
     if (c->cluster) {
         while (nsteps > 0) {
@@ -1183,7 +1185,7 @@ int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
             if (rc) return rc;
             nsteps -= n;
         }
-        return finalize_nu(c);
+        return finalize ? finalize_nu(c) : DMRT_OK;
     }
     if (c->slab && !(c->wall_lo && c->wall_hi) && nsteps > 1) {
         set_err(c, "a slab with neighbours takes one step at a time (dmrt_slab_step), its halo rows "
@@ -1213,8 +1215,10 @@ int dmrt_step(dmrt_ctx* c, int64_t nsteps) {
             nsteps -= 1;
         }
     }
-    return finalize_nu(c);
+    return finalize ? finalize_nu(c) : DMRT_OK;
 }
+
+int dmrt_step(dmrt_ctx* c, int64_t nsteps) { return step_run(c, nsteps, true); }
 
 // ---- y-slabs: halo rows --------------------------------------------------------
 namespace {
@@ -2409,6 +2413,8 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     AdjLayout L;
     L.K = (long long)std::ceil(std::sqrt((double)N));
     if (L.K < 1) L.K = 1;
+    // Segments of whole step graphs, so that the forward pass replays graphs only.
+    if (L.K > c->graph_len) L.K = (L.K + c->graph_len - 1) / c->graph_len * c->graph_len;
     L.C = (N + L.K - 1) / L.K;
     L.state = align256((size_t)kPlanes * (size_t)c->L.plane * sizeof(float));
     size_t o = 0;
@@ -2419,7 +2425,7 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_dgb = o; o += align256((size_t)L.n_blocks * sizeof(double));
     L.off_misc = o; o += 256;
     L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
-    L.off_sdgb = o; o += align256((size_t)L.K * L.n_blocks * sizeof(double));  // per step of a segment
+    L.off_sdgb = o; o += align256((size_t)L.K * L.n_blocks * 4 * sizeof(double));  // per step and warp
     L.off_sdthw = o; o += align256((size_t)L.K * c->p.ny * sizeof(double));
     L.off_ckpt = o; o += (size_t)L.C * L.state;
     L.off_seg[0] = o; o += (size_t)L.K * L.state;
@@ -2493,7 +2499,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     CK(cudaMemcpyAsync(ckpt(0), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
     for (long long q = 0; q < AL.C; ++q) {
         const long long n = std::min(K, N - q * K);
-        int rc = dmrt_step(c, n);
+        int rc = step_run(c, n, q + 1 == AL.C);  // the last segment sums its last step's rows
         if (rc) return rc;
         if (q + 1 < AL.C)
             CK(cudaMemcpyAsync(ckpt(q + 1), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream),
@@ -2599,7 +2605,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
             AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(set, k - 1 - start);
             AA.nu_in = nu_a;
             AA.nu_out = nu_b;
-            AA.dgbeta_step = sdgb + (size_t)t * AL.n_blocks;
+            AA.dgbeta_step = sdgb + (size_t)t * AL.n_blocks * 4;
             AA.dthw_step = sdthw + (size_t)t * c->p.ny;
             AA.w = (k > N - avg_last) ? (float)(1.0 / (double)avg_last) : 0.f;
             CK(launch_overlapped(dmrt::adjoint_step_kernel, agrid, dim3(128), c->stream, AA, c->sc),
