@@ -559,13 +559,11 @@ void choose_launch(const dmrt_params& p_in, int sms, int* kernel, int* npt_out, 
 // Resolve the kernel variant and prepare its launch configuration.
 // Cluster kernel for runs of steps: float32, a whole cavity, the state of
 // both buffers in the shared memory of one cluster of up to 16 blocks.
-int setup_cluster(dmrt_ctx* c) {
+// The cluster kernel's launch shape for c (blocks, rows per block, threads,
+// shared memory); false if the cavity does not fit one cluster on this GPU.
+bool cluster_fit(dmrt_ctx* c, int* csize_out, int* crows_out, int* threads_out, size_t* smem_out) {
     const dmrt_params& p = c->p;
-    c->cluster = false;
-    if (p.storage != DMRT_FP32 || c->slab) {
-        set_err(c, "the cluster kernel runs float32 storage of a whole cavity only");
-        return DMRT_E_ARG;
-    }
+    if (p.storage != DMRT_FP32 || c->slab) return false;
     const void* fn = (const void*)dmrt::step_cluster_kernel;
     for (int csize : {16, 8}) {
         const int cs = std::min(csize, p.ny);
@@ -598,16 +596,30 @@ int setup_cluster(dmrt_ctx* c) {
             (void)cudaGetLastError();
             continue;
         }
+        *csize_out = blocks;
+        *crows_out = rows;
+        *threads_out = threads;
+        *smem_out = smem;
+        return true;
+    }
+    return false;
+}
+
+int setup_cluster(dmrt_ctx* c) {
+    const dmrt_params& p = c->p;
+    c->cluster = false;
+    if (p.storage != DMRT_FP32 || c->slab) {
+        set_err(c, "the cluster kernel runs float32 storage of a whole cavity only");
+        return DMRT_E_ARG;
+    }
+    if (cluster_fit(c, &c->csize, &c->crows, &c->cthreads, &c->csmem)) {
         c->cluster = true;
-        c->csize = blocks;
-        c->crows = rows;
-        c->cthreads = threads;
-        c->csmem = smem;
         return DMRT_OK;
     }
     set_err(c, "a %d x %d float32 cavity does not fit the shared memory of one thread-block cluster", p.nx, p.ny);
     return DMRT_E_ARG;
 }
+
 
 int setup_kernel(dmrt_ctx* c) {
     const dmrt_params& p0 = c->p;
@@ -1150,6 +1162,9 @@ static int launch_cluster(dmrt_ctx* c, int n) {
     C.steps = n;
     C.parity = c->cur;
     C.rows_per = c->crows;
+    C.start = nullptr;
+    C.record = nullptr;
+    C.record_stride = 0;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -2560,9 +2575,40 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         if (!rc) rc = encode_map(c, &m.ld[1], base, DMRT_FP32, kPlanes, 4, c->R);
         if (rc) return rc;
     }
+    // With the recompute on its own stream, a cavity that fits one thread-block
+    // cluster recomputes each segment in one cluster launch (on 16 SMs or fewer,
+    // so it takes little from the reverse sweep's blocks), writing every state.
+    int ccs = 0, ccr = 0, cct = 0;
+    size_t ccm = 0;
+    const bool cluster_re = overlap && cluster_fit(c, &ccs, &ccr, &cct, &ccm);
     // Recompute of segment q into slot set `set` on stream rs: s_{start + t} into slot t.
     auto recompute = [&](long long q, int set) -> int {
         const long long start = q * K, len = std::min(start + K, N) - start;
+        if (cluster_re && len > 1) {
+            dmrt::ClusterArgs CA;
+            CA.A[0] = CA.A[1] = step_args(c, 0);
+            CA.K = c->sc;
+            CA.steps = (int)(len - 1);
+            CA.parity = 0;
+            CA.rows_per = ccr;
+            CA.start = ckpt(q);
+            CA.record = slot(set, 1);
+            CA.record_stride = (long long)(AL.state / sizeof(float));
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = ccs;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3(ccs);
+            cfg.blockDim = dim3(cct);
+            cfg.dynamicSmemBytes = ccm;
+            cfg.stream = rs;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            CK(cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel, CA), "adjoint recompute launch");
+            return DMRT_OK;
+        }
         for (long long t = 1; t < len; ++t) {
             RA.src = t == 1 ? ckpt(q) : slot(set, t - 1);
             RA.dst = slot(set, t);

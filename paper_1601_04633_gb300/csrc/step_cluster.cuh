@@ -45,6 +45,13 @@ struct ClusterArgs {
     int steps;       // time steps of the launch
     int parity;      // global buffer holding the state at launch
     int rows_per;    // rows per block
+    // Record mode (record != nullptr; the adjoint's segment recompute): start
+    // from the state at `start` (same layout as a population buffer), write the
+    // state after step s to record + s * record_stride, and touch nothing else
+    // (no Nusselt numbers, no context buffers or counters).
+    const float* start;
+    float* record;
+    long long record_stride;  // floats between recorded states
 };
 
 // Means kept in block 0's shared memory between their flushes to the ring.
@@ -95,11 +102,12 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
 
     grid_dep_wait();
     grid_dep_launch();
-    // The state of this block's rows, from global buffer `parity`.
+    const bool rec = C.record != nullptr;
+    // The state of this block's rows, from global buffer `parity` (record mode: from `start`).
     for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
         const int r = i / nx, x = i - r * nx;
         if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err)) continue;
-        const float* src = A0.src + (size_t)(r0 + r) * pitch + x;
+        const float* src = (rec ? C.start : A0.src) + (size_t)(r0 + r) * pitch + x;
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) sb[0][p * plane_sm + i] = src[p * PL];
     }
@@ -108,7 +116,7 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
         walls[RP + r] = __ldg(A0.cold + r0 + r);
     }
     const long long t0 = *A0.step_in;
-    if (rank == 0 && warp == 0 && *A0.pending) {
+    if (!rec && rank == 0 && warp == 0 && *A0.pending) {
         // Rows of an earlier step not yet summed (a single step launched before).
         const double sum = warp_fixed_sum(A0.prev_rows, ny, lane);
         if (lane == 0) {
@@ -194,18 +202,25 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
             for (int k = 0; k < 9; ++k) Dst[plane_f(k) * plane_sm + i] = f[k];
 #pragma unroll
             for (int k = 0; k < 5; ++k) Dst[plane_g(k) * plane_sm + i] = g[k];
+            if (rec) {
+                float* d = C.record + (size_t)s * C.record_stride + (size_t)j * pitch + x;
+#pragma unroll
+                for (int k = 0; k < 9; ++k) d[plane_f(k) * PL] = f[k];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) d[plane_g(k) * PL] = g[k];
+            }
             if (x == 0) th01[2 * r] = theta;
             if (x == 1) th01[2 * r + 1] = theta;
         }
         __syncthreads();  // theta at x = 0 and 1 of every row of this block
-        for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        for (int r = threadIdx.x; r < (rec ? 0 : nr); r += blockDim.x) {
             const int j = r0 + r;
             if (!DMRT_IN(j, 0, ny, A0.err)) continue;
             const double tw = (double)walls[r];
             nu_dst[j] = K.nu_scale * (8.0 * tw - 9.0 * (double)th01[2 * r] + (double)th01[2 * r + 1]);
         }
         cl.sync();  // the new state and the step's Nusselt rows are visible to the whole cluster
-        if (rank == 0 && warp == 0) {
+        if (!rec && rank == 0 && warp == 0) {
             // Mean of this step's rows while the other warps start the next step,
             // kept in shared memory; a full chunk goes to the ring (global stores
             // only once per kClusterNuChunk steps, so that the barriers between
@@ -226,14 +241,14 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     const int pend = C.parity ^ (C.steps & 1);
     const float* fin = sb[C.steps & 1];
     float* dstg = const_cast<float*>(C.A[pend].src);
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+    for (int i = threadIdx.x; i < (rec ? 0 : nr * nx); i += blockDim.x) {
         const int r = i / nx, x = i - r * nx;
         if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err)) continue;
         float* d = dstg + (size_t)(r0 + r) * pitch + x;
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) d[p * PL] = fin[p * plane_sm + i];
     }
-    if (rank == 0 && C.steps > 0) {
+    if (!rec && rank == 0 && C.steps > 0) {
         const double* last = nur + (size_t)((C.steps - 1) & 1) * ny;
         double* rows = C.A[C.parity ^ ((C.steps - 1) & 1)].nu_rows;
         for (int r = threadIdx.x; r < ny; r += blockDim.x) rows[r] = last[r];
