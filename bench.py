@@ -37,12 +37,12 @@ UNIT = "MLUPS"
 BYTES_PER_NODE_FP32 = 112  # 14 populations read + 14 written, 4 bytes each
 # storage mode -> (storage, rounding); bytes moved per node and step (read + write)
 STORAGES = {"fp32": (0, 0), "fp16": (1, 0), "bf16": (2, 0), "fp16_sr": (1, 1), "bf16_sr": (2, 1),
-            "mixed": (3, 0), "mixed_sr": (3, 1)}
+            "mixed": (3, 0), "mixed_sr": (3, 1), "theta32": (4, 0), "theta32_sr": (4, 1)}
 BYTES_PER_NODE = {"fp32": 112, "fp16": 56, "bf16": 56, "fp16_sr": 56, "bf16_sr": 56, "mixed": 76,
-                  "mixed_sr": 76}
+                  "mixed_sr": 76, "theta32": 60, "theta32_sr": 60}
 # Tiles (nodes per thread, rows, stages) of the secondary storage runs.
 SECONDARY_TILES = {"fp16": (2, 4, 2), "bf16": (2, 4, 2), "fp16_sr": (4, 4, 2), "bf16_sr": (4, 4, 2),
-                   "mixed": (2, 1, 2), "mixed_sr": (2, 1, 2)}
+                   "mixed": (2, 1, 2), "mixed_sr": (2, 1, 2), "theta32": (2, 1, 2), "theta32_sr": (2, 1, 2)}
 FALLBACK_HBM_GBS = 6800.0
 GATE_STEPS = 20000  # the stated length of the 4096^2 workload; the Nu gate is taken over it
 NU_GATE = 1e-3

@@ -54,12 +54,26 @@ extern "C" {
 
 /* Population storage precision. MIXED: the flow populations f in float16 and
  * the thermal populations g in float32 (38 bytes per node and buffer instead of
- * 56); the rounding mode applies to the float16 flow stores. 16-bit and mixed
- * storage have no counterpart in the paper (which stores double). */
+ * 56); the rounding mode applies to the float16 flow stores. THETA32: the flow
+ * populations in float16, the temperature theta = sum_i g_i (Eq. 41) in
+ * float32 and the four moving thermal populations as float16 deviations
+ * d_i = g_i - w theta (i = 1..4 in 0-based directions; w = (4 + a)/20, the
+ * weight of a moving direction in the D2Q5 equilibrium at rest, Eq. 42), the
+ * rest population being g_0 = w_0 theta - (d_1 + d_2 + d_3 + d_4) with
+ * w_0 = (1 - a)/5 (30 bytes per node and buffer); the rounding mode applies to
+ * every float16 store. A node's stored thermal populations sum to its theta
+ * (up to float32 arithmetic) whatever the deviations' rounding, so the
+ * rounding moves heat between neighbours but creates none. dmrt_get_state
+ * returns the populations these values stand for; dmrt_set_state stores theta
+ * = sum_i g_i and each deviation rounded to nearest. THETA32 runs the
+ * single-cavity TMA kernel only (no batch, slab, cluster, direct kernel or
+ * adjoint). 16-bit, mixed and THETA32 storage have no counterpart in the paper
+ * (which stores double). */
 #define DMRT_FP32 0
 #define DMRT_FP16 1
 #define DMRT_BF16 2
 #define DMRT_MIXED 3
+#define DMRT_THETA32 4
 
 /* Rounding of 16-bit population stores. NEAREST: round to nearest even.
  * STOCHASTIC: round up with probability equal to the distance to the lower
@@ -97,7 +111,9 @@ extern "C" {
  * (1, 1, 2); 4-row items fewer than 4 per SM, 2-row items. MIXED storage (default (2, 1, 2)), nearest:
  * (1,1,2) (1,1,3) (1,1,4) (1,2,2) (1,2,3) (1,4,2) (2,1,2) (2,1,3) (2,1,4)
  * (2,2,2) (4,1,3) (4,1,4); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2)
- * (2,1,3) (2,2,2) (2,4,2) (4,1,3). */
+ * (2,1,3) (2,2,2) (2,4,2) (4,1,3). THETA32 storage (default (2, 1, 2)),
+ * nearest: (1,1,2) (2,1,2) (2,1,3) (2,2,2) (4,1,3); stochastic: (1,1,2) (1,2,2)
+ * (2,1,2) (2,1,3) (2,2,2) (2,4,2) (4,1,3) (4,2,2). */
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
@@ -127,8 +143,9 @@ typedef struct {
     double theta_init;  /* uniform initial temperature when no field is given */
     int32_t left_wall;  /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
     int32_t right_wall; /* DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC */
-    int32_t storage;    /* DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (16-bit and mixed
-                           storage run the TMA kernel; arithmetic is float32 in every case) */
+    int32_t storage;    /* DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED or DMRT_THETA32 (16-bit,
+                           mixed and THETA32 storage run the TMA kernel; arithmetic is
+                           float32 in every case) */
     int32_t kernel;     /* DMRT_KERNEL_AUTO, _DIRECT, _TMA or _CLUSTER */
     int64_t nu_capacity; /* length of the device ring of mean-Nu values, >= 1 */
     int32_t tma_rows;   /* TMA kernel: rows per work item (0 = the storage's default tile) */

@@ -36,16 +36,20 @@ struct Layout {
     int pitch;            // elements per row (multiple of 128)
     long long plane;      // elements per plane
     size_t buf_bytes;     // one population buffer (14 planes; mixed storage: 9 float16
-                          // flow planes, then 5 float32 thermal planes)
+                          // flow planes, then 5 float32 thermal planes; THETA32: 9
+                          // float16 flow planes, a float32 theta plane, 4 float16
+                          // deviation planes)
     size_t off_a, off_b, off_hot, off_cold, off_rows, off_ring, off_misc;
     size_t total;
 };
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// Bytes per stored flow (f) and thermal (g) population.
+// Bytes per stored flow (f) and thermal (g) population (THETA32: per deviation),
+// and of a node's whole thermal block.
 int f_bytes(int storage) { return storage == DMRT_FP32 ? 4 : 2; }
 int g_bytes(int storage) { return storage == DMRT_FP32 || storage == DMRT_MIXED ? 4 : 2; }
+int thermal_bytes(int storage) { return storage == DMRT_THETA32 ? 4 + 4 * 2 : 5 * g_bytes(storage); }
 
 // DMRT_ROUND_AUTO resolved: stochastic rounding for 16-bit and mixed storage,
 // nearest (nothing is rounded) for float32.
@@ -64,7 +68,7 @@ Layout make_layout(const dmrt_params& p, int halo_rows = 0) {
     Layout L;
     L.pitch = ((p.nx + 127) / 128) * 128;
     L.plane = (long long)(p.ny + halo_rows) * L.pitch;
-    L.buf_bytes = align256((size_t)L.plane * (9 * f_bytes(p.storage) + 5 * g_bytes(p.storage)));
+    L.buf_bytes = align256((size_t)L.plane * (9 * f_bytes(p.storage) + thermal_bytes(p.storage)));
     size_t o = 0;
     L.off_a = o; o += L.buf_bytes;
     L.off_b = o; o += L.buf_bytes;
@@ -225,6 +229,38 @@ __device__ __forceinline__ auto* g_base(B* S, long long plane) {
     using T = typename std::conditional<std::is_const<B>::value, const Eg, Eg>::type;
     return reinterpret_cast<T*>(S + (L::kSplit ? (size_t)9 * plane * sizeof(typename L::Ef) : 0));
 }
+// ThetaSplit: the theta plane and deviation plane k (k = 1..4).
+template <typename L, typename B>
+__device__ __forceinline__ auto* theta_plane(B* S, long long plane) {
+    using T = typename std::conditional<std::is_const<B>::value, const float, float>::type;
+    return reinterpret_cast<T*>(S + (size_t)9 * plane * 2);
+}
+template <typename L, typename B>
+__device__ __forceinline__ auto* dev_plane(B* S, long long plane, int k) {
+    using Eg = typename L::Eg;
+    using T = typename std::conditional<std::is_const<B>::value, const Eg, Eg>::type;
+    return reinterpret_cast<T*>(S + (size_t)9 * plane * 2 + (size_t)plane * 4) + (size_t)(k - 1) * plane;
+}
+// Post-collision thermal population k >= 1 of buffer element s, and theta =
+// sum_i g_i, in float64 (stored value + shift; ThetaSplit: w theta + d_k, and
+// theta as stored).
+template <typename L>
+__device__ __forceinline__ double g_moving(const unsigned char* S, long long plane, long long s, int k, double sh1,
+                                           double w1) {
+    if constexpr (L::kTheta)
+        return w1 * (double)theta_plane<L>(S, plane)[s] + (double)elem_to_f(dev_plane<L>(S, plane, k)[s]);
+    else
+        return (double)elem_to_f(g_base<L>(S, plane)[L::pg(k) * plane + s]) + sh1;
+}
+template <typename L>
+__device__ __forceinline__ double theta_sum(const unsigned char* S, long long plane, long long s, double sh0,
+                                            double sh1) {
+    if constexpr (L::kTheta) return (double)theta_plane<L>(S, plane)[s];
+    const auto* Sg = g_base<L>(S, plane);
+    double th = 0.0;
+    for (int k = 0; k < 5; ++k) th += (double)elem_to_f(Sg[L::pg(k) * plane + s]) + (k == 0 ? sh0 : sh1);
+    return th;
+}
 
 // Initial post-collision state: f = 0 (rest, delta-rho = 0) and g at the D2Q5
 // equilibrium of theta0 at rest, g_0 = (1 - a) theta / 5, g_1..4 = (4 + a) theta / 20
@@ -246,6 +282,12 @@ __global__ void init_kernel(unsigned char* __restrict__ S, const double* __restr
         const bool in = i < nx && j >= 0 && j < ny;
         if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
         for (int k = 0; k < 9; ++k) Sf[L::pf(k) * plane + q] = elem_from_f<Ef>(0.f);
+        if constexpr (L::kTheta) {
+            // At rest g_k = w theta exactly: theta and zero deviations.
+            theta_plane<L>(S, plane)[q] = in ? (float)th : 0.f;
+            for (int k = 1; k < 5; ++k) dev_plane<L>(S, plane, k)[q] = elem_from_f<Eg>(0.f);
+            continue;
+        }
         Sg[L::pg(0) * plane + q] = elem_from_f<Eg>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
         const float side = in ? (float)((4.0 + a) * th / 20.0 - sh1) : 0.f;
         for (int k = 1; k < 5; ++k) Sg[L::pg(k) * plane + q] = elem_from_f<Eg>(side);
@@ -267,12 +309,18 @@ __global__ void fields_kernel(const unsigned char* __restrict__ S, float* __rest
          q += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(q / nx), i = (int)(q % nx);
         const long long s = (long long)(j + row0) * pitch + i;
-        float f[9], g[5];
+        float f[9];
         for (int k = 0; k < 9; ++k) f[k] = elem_to_f(Sf[L::pf(k) * plane + s]);
-        for (int k = 0; k < 5; ++k) g[k] = elem_to_f(Sg[L::pg(k) * plane + s]) + (k == 0 ? sh0 : sh1);
+        float t;
+        if constexpr (L::kTheta) {
+            t = theta_plane<L>(S, plane)[s];
+        } else {
+            float g[5];
+            for (int k = 0; k < 5; ++k) g[k] = elem_to_f(Sg[L::pg(k) * plane + s]) + (k == 0 ? sh0 : sh1);
+            t = g[0] + g[1] + g[2] + g[3] + g[4];
+        }
         const float jx = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
         const float jy = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-        const float t = g[0] + g[1] + g[2] + g[3] + g[4];
         if (u) u[q] = jx;
         if (v) v[q] = jy - gbeta * (t - theta_ref);
         if (th) th[q] = t;
@@ -303,6 +351,45 @@ __global__ void plane_from_f32(E* __restrict__ P, const float* __restrict__ in, 
     }
 }
 
+// THETA32 thermal block <-> dense float32 populations [5][ny][nx] (0-based
+// directions 0..4, host planes g_1..g_5): g_k = w theta + d_k (k >= 1) and
+// g_0 = w_0 theta - (d_1 + d_3 + d_2 + d_4), formed as the step kernel forms
+// them; back: theta = sum_k g_k and d_k = g_k - w theta rounded to the nearest
+// float16 (padding columns zero).
+__global__ void theta_to_g32(const unsigned char* __restrict__ S, long long plane, int pitch, int nx, int ny,
+                             int row0, float w0, float w1, float* __restrict__ out) {
+    const long long n = (long long)nx * ny;
+    const float* T = reinterpret_cast<const float*>(S + (size_t)9 * plane * 2);
+    const __half* D = reinterpret_cast<const __half*>(S + (size_t)9 * plane * 2 + (size_t)plane * 4);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / nx), i = (int)(q % nx);
+        const long long s = (long long)(j + row0) * pitch + i;
+        const float th = T[s];
+        float d[5];
+        for (int k = 1; k < 5; ++k) d[k] = __half2float(D[(k - 1) * plane + s]);
+        out[q] = fmaf(w0, th, -((d[1] + d[3]) + (d[2] + d[4])));
+        for (int k = 1; k < 5; ++k) out[k * n + q] = fmaf(w1, th, d[k]);
+    }
+}
+__global__ void theta_from_g32(unsigned char* __restrict__ S, long long plane, int pitch, int nx, int ny, int row0,
+                               float w1, const float* __restrict__ in) {
+    const long long n = (long long)nx * ny;
+    float* T = reinterpret_cast<float*>(S + (size_t)9 * plane * 2);
+    __half* D = reinterpret_cast<__half*>(S + (size_t)9 * plane * 2 + (size_t)plane * 4);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)ny * pitch;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(q / pitch), i = (int)(q % pitch);
+        const long long s = (long long)(j + row0) * pitch + i;
+        float g[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (i < nx)
+            for (int k = 0; k < 5; ++k) g[k] = in[k * n + (long long)j * nx + i];
+        const float th = g[0] + g[1] + g[2] + g[3] + g[4];
+        T[s] = th;
+        for (int k = 1; k < 5; ++k) D[(k - 1) * plane + s] = __float2half_rn(fmaf(-w1, th, g[k]));
+    }
+}
+
 __global__ void fill_kernel(float* p, const double* src, double value, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) p[i] = (float)(src ? src[i] : value);
@@ -319,11 +406,10 @@ int host_plane(int k) { return k < 9 ? plane_f(k) : plane_g(k - 9); }
 template <typename L>
 __global__ void nu_flux_kernel(const unsigned char* __restrict__ S, const float* __restrict__ hot,
                                double* __restrict__ out, int ny, int pitch, long long plane, double abb,
-                               double g_sign, double sh1, double scale, int row0) {
+                               double g_sign, double sh1, double w1, double scale, int row0) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ny) return;
-    const auto* Sg = g_base<L>(S, plane);
-    const double g3 = (double)elem_to_f(Sg[L::pg(3) * plane + (size_t)(j + row0) * pitch]) + sh1;
+    const double g3 = g_moving<L>(S, plane, (long long)(j + row0) * pitch, 3, sh1, w1);
     out[j] = scale * (abb * (double)hot[j] - g_sign * 2.0 * g3);
 }
 
@@ -338,25 +424,20 @@ __global__ void energy_rows_kernel(const unsigned char* __restrict__ S, const fl
                                    const float* __restrict__ cold, double* __restrict__ row_theta,
                                    double* __restrict__ row_in, int nx, int ny, int pitch, long long plane,
                                    double abb_l, double sign_l, double abb_r, double sign_r, double sh0,
-                                   double sh1, int row0) {
+                                   double sh1, double w1, int row0) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (j >= ny) return;  // warp-uniform
-    const auto* Sg = g_base<L>(S, plane);
     const size_t row = (size_t)(j + row0) * pitch;
     double acc = 0.0;
-    for (int i = lane; i < nx; i += 32) {
-        double th = 0.0;
-        for (int k = 0; k < 5; ++k) th += (double)elem_to_f(Sg[L::pg(k) * plane + row + i]) + (k == 0 ? sh0 : sh1);
-        acc += th;
-    }
+    for (int i = lane; i < nx; i += 32) acc += theta_sum<L>(S, plane, (long long)(row + i), sh0, sh1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
         // West-moving g (0-based direction 3) leaves through the left wall,
         // east-moving g (direction 1) through the right wall.
-        const double gw = (double)elem_to_f(Sg[L::pg(3) * plane + row]) + sh1;
-        const double ge = (double)elem_to_f(Sg[L::pg(1) * plane + row + nx - 1]) + sh1;
+        const double gw = g_moving<L>(S, plane, (long long)row, 3, sh1, w1);
+        const double ge = g_moving<L>(S, plane, (long long)(row + nx - 1), 1, sh1, w1);
         row_theta[j] = acc;
         row_in[j] = (abb_l * (double)hot[j] - sign_l * 2.0 * gw) + (abb_r * (double)cold[j] - sign_r * 2.0 * ge);
     }
@@ -410,20 +491,29 @@ void with_layout(int storage, Fn&& fn) {
         fn(dmrt::OneType<__nv_bfloat16>{});
     else if (storage == DMRT_MIXED)
         fn(dmrt::Split<__half, float>{});
+    else if (storage == DMRT_THETA32)
+        fn(dmrt::ThetaSplit{});
     else
         fn(dmrt::OneType<float>{});
 }
 
 // Byte offset of host-order plane k (f_1..f_9, g_1..g_5) in a population
 // buffer, and the one-type storage its elements have.
+// THETA32: host planes 9..13 (g_1..g_5) are the stored theta (float32) and
+// the deviations d_1..d_4 (float16), not populations; dmrt_get_state and
+// dmrt_set_state convert them.
 size_t plane_offset(const dmrt_params& p, long long plane, int k) {
     if (p.storage == DMRT_MIXED)
         return k < 9 ? (size_t)dmrt::split_f(k) * plane * 2
                      : (size_t)9 * plane * 2 + (size_t)dmrt::split_g(k - 9) * plane * 4;
+    if (p.storage == DMRT_THETA32)
+        return k < 9 ? (size_t)dmrt::split_f(k) * plane * 2
+                     : (size_t)9 * plane * 2 + (k == 9 ? 0 : (size_t)plane * 4 + (size_t)(k - 10) * plane * 2);
     return (size_t)host_plane(k) * plane * f_bytes(p.storage);
 }
 int plane_storage(const dmrt_params& p, int k) {
     if (p.storage == DMRT_MIXED) return k < 9 ? DMRT_FP16 : DMRT_FP32;
+    if (p.storage == DMRT_THETA32) return k == 9 ? DMRT_FP32 : DMRT_FP16;
     return p.storage;
 }
 size_t plane_elem_bytes(const dmrt_params& p, int k) { return plane_storage(p, k) == DMRT_FP32 ? 4 : 2; }
@@ -431,7 +521,7 @@ size_t plane_elem_bytes(const dmrt_params& p, int k) { return plane_storage(p, k
 // Default TMA tile (nodes per thread, rows, stages) per storage mode, the
 // fastest measured on the 4096^2 cavity.
 void default_tile(int storage, int rounding, int* npt, int* R, int* S) {
-    if (storage == DMRT_MIXED) {
+    if (storage == DMRT_MIXED || storage == DMRT_THETA32) {
         *npt = 2, *R = 1, *S = 2;
     } else if (storage == DMRT_FP16 || storage == DMRT_BF16) {
         if (rounding == DMRT_ROUND_STOCHASTIC) *npt = 4, *R = 4, *S = 2;
@@ -442,9 +532,10 @@ void default_tile(int storage, int rounding, int* npt, int* R, int* S) {
 }
 
 const dmrt::TmaVariant* find_tma_variant(int storage, int rounding, int npt, int R, int S) {
-    const dmrt::TmaVariant* (*lists[6])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
+    const dmrt::TmaVariant* (*lists[7])(int*) = {dmrt::tma_variants_npt4, dmrt::tma_variants_npt2,
                                                 dmrt::tma_variants_npt1, dmrt::tma_variants_fp16,
-                                                dmrt::tma_variants_bf16, dmrt::tma_variants_mixed};
+                                                dmrt::tma_variants_bf16, dmrt::tma_variants_mixed,
+                                                dmrt::tma_variants_theta};
     for (auto list : lists) {
         int n = 0;
         const dmrt::TmaVariant* v = list(&n);
@@ -570,7 +661,7 @@ bool cluster_fit(dmrt_ctx* c, int* csize_out, int* crows_out, int* threads_out, 
         const int rows = (p.ny + cs - 1) / cs;
         const int blocks = (p.ny + rows - 1) / rows;
         const size_t smem = dmrt::cluster_smem_bytes(rows, p.nx, p.ny);
-        const int threads = std::min(1024, (rows * p.nx + 31) / 32 * 32);
+        const int threads = dmrt::cluster_threads(rows, p.nx);
         if (smem > (size_t)dmrt::kMaxSmem) continue;
         if (blocks > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -667,7 +758,9 @@ int setup_kernel(dmrt_ctx* c) {
     c->geo.n_strips = (p.nx + strip - 1) / strip;
     c->geo.n_rowblocks = (p.ny + R - 1) / R;
     const bool split = p.storage == DMRT_MIXED;
-    c->tma_smem = dmrt::step_tma_smem_bytes(split, v->ts != 0, R, S, fb, gb);
+    const bool theta = p.storage == DMRT_THETA32;
+    c->tma_smem = theta ? dmrt::step_tma_smem_bytes_theta(v->ts != 0, R, S)
+                        : dmrt::step_tma_smem_bytes(split, v->ts != 0, R, S, fb, gb);
     if (c->tma_smem > (size_t)dmrt::kMaxSmem) {
         set_err(c, "TMA tile %dx%d needs %zu bytes of shared memory", R, S, c->tma_smem);
         return DMRT_E_ARG;
@@ -691,7 +784,19 @@ int setup_kernel(dmrt_ctx* c) {
         std::memset(&m, 0, sizeof m);
         float* dst = buf(c, 1 - b);
         int rc;
-        if (split) {
+        if (theta) {
+            // 9 float16 flow planes, the float32 theta plane, 4 float16 deviation
+            // planes; theta and the deviations are loaded R + 2 rows high.
+            const size_t toff = (size_t)9 * c->L.plane * 2, doff = toff + (size_t)c->L.plane * 4;
+            char* src = reinterpret_cast<char*>(buf(c, b));
+            char* dd = reinterpret_cast<char*>(dst);
+            rc = encode_map(c, &m.ld[0], buf(c, b), DMRT_FP16, 9, 3, R);
+            if (!rc) rc = encode_map(c, &m.ld[1], src + toff, DMRT_FP32, 1, 1, R + 2);
+            if (!rc) rc = encode_map(c, &m.ld[2], src + doff, DMRT_FP16, 4, 4, R + 2);
+            if (!rc) rc = encode_map(c, &m.st[0], dst, DMRT_FP16, 9, 9, R, strip, p.nx, c->row0 + p.ny);
+            if (!rc) rc = encode_map(c, &m.st[1], dd + toff, DMRT_FP32, 1, 1, R, strip, p.nx, c->row0 + p.ny);
+            if (!rc) rc = encode_map(c, &m.st[2], dd + doff, DMRT_FP16, 4, 4, R, strip, p.nx, c->row0 + p.ny);
+        } else if (split) {
             // 9 float16 flow planes, then 5 float32 thermal planes.
             const size_t goff = (size_t)9 * c->L.plane * 2;
             char* g = reinterpret_cast<char*>(buf(c, b)) + goff;
@@ -732,8 +837,9 @@ int validate(const dmrt_params* p, dmrt_ctx* c) {
         set_err(c, "wall kinds must be DMRT_WALL_FIXED or DMRT_WALL_ADIABATIC");
         return DMRT_E_ARG;
     }
-    if (p->storage < DMRT_FP32 || p->storage > DMRT_MIXED) {
-        set_err(c, "storage must be DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED (got %d)", p->storage);
+    if (p->storage < DMRT_FP32 || p->storage > DMRT_THETA32) {
+        set_err(c, "storage must be DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED or DMRT_THETA32 (got %d)",
+                p->storage);
         return DMRT_E_ARG;
     }
     if (p->rounding != DMRT_ROUND_NEAREST && p->rounding != DMRT_ROUND_STOCHASTIC &&
@@ -852,6 +958,12 @@ static int create_ctx(const dmrt_params* pg, int y0, int rows, bool slab, const 
         set_err(nullptr, "slab rows %d .. %d outside the cavity's %d rows", y0, y0 + rows - 1, pg->ny);
         return DMRT_E_ARG;
     }
+    if (slab && pg->storage == DMRT_THETA32) {
+        // A THETA32 pull reads the source row's theta as well as the crossing
+        // populations, which the face messages do not carry.
+        set_err(nullptr, "slabs take float32, 16-bit or mixed storage, not THETA32");
+        return DMRT_E_ARG;
+    }
     dmrt_params pl = resolved(*pg);
     pl.ny = rows;
     const int row0 = slab ? 1 : 0;
@@ -958,6 +1070,10 @@ int dmrt_slab_workspace_size(const dmrt_params* p, int32_t rows, size_t* bytes) 
     if (rc) return rc;
     if (!bytes || rows < 1 || rows > p->ny) {
         set_err(nullptr, "need 1 <= rows <= ny and a non-NULL bytes");
+        return DMRT_E_ARG;
+    }
+    if (p->storage == DMRT_THETA32) {
+        set_err(nullptr, "slabs take float32, 16-bit or mixed storage, not THETA32");
         return DMRT_E_ARG;
     }
     dmrt_params pl = *p;
@@ -1361,8 +1477,8 @@ int dmrt_nusselt_flux(dmrt_ctx* c, double* nu_mean, double* nu_local) {
         using Lt = decltype(tag);
         nu_flux_kernel<Lt><<<(p.ny + 255) / 256, 256, 0, c->stream>>>(
             reinterpret_cast<const unsigned char*>(buf(c, c->cur)), reinterpret_cast<const float*>(c->ws + c->L.off_hot),
-            stage, p.ny, c->L.pitch, c->L.plane, fixed ? c->k.abb : 0.0, fixed ? 1.0 : 0.0, (double)c->sc.gsh1, scale,
-            c->row0);
+            stage, p.ny, c->L.pitch, c->L.plane, fixed ? c->k.abb : 0.0, fixed ? 1.0 : 0.0, (double)c->sc.gsh1,
+            (4.0 + c->k.a) / 20.0, scale, c->row0);
     });
     CK(cudaGetLastError(), "flux Nusselt kernel");
     std::vector<double> local((size_t)p.ny);
@@ -1390,7 +1506,7 @@ int dmrt_energy(dmrt_ctx* c, double* theta_sum, double* wall_in) {
             reinterpret_cast<const unsigned char*>(buf(c, c->cur)), reinterpret_cast<const float*>(c->ws + c->L.off_hot),
             reinterpret_cast<const float*>(c->ws + c->L.off_cold), rows, rows + p.ny, p.nx, p.ny, c->L.pitch,
             c->L.plane, lf ? c->k.abb : 0.0, lf ? 1.0 : 0.0, rf ? c->k.abb : 0.0, rf ? 1.0 : 0.0,
-            (double)c->sc.gsh0, (double)c->sc.gsh1, c->row0);
+            (double)c->sc.gsh0, (double)c->sc.gsh1, (4.0 + c->k.a) / 20.0, c->row0);
     });
     sum2_fixed_kernel<<<1, 256, 0, c->stream>>>(rows, rows + p.ny, p.ny, sums);
     CK(cudaGetLastError(), "energy kernels");
@@ -1499,7 +1615,8 @@ int dmrt_set_wall_profiles(dmrt_ctx* c, const double* hot, const double* cold) {
 // Copy between a dense host array [14][ny][nx] of float32 and the padded
 // device planes of the current state. A float32 plane: one 2D copy. A 16-bit
 // plane: converted through the idle buffer (which holds at least 28 bytes per
-// node; a float32 plane needs 4).
+// node; a float32 plane needs 4). THETA32: the thermal block converted to and
+// from the five population planes as a whole (20 bytes per node).
 static float plane_shift(const dmrt_ctx* c, int host_k) {
     return host_k < 9 ? 0.f : (host_k == 9 ? c->sc.gsh0 : c->sc.gsh1);
 }
@@ -1509,7 +1626,8 @@ int dmrt_get_state(dmrt_ctx* c, float* host) {
     const dmrt_params& p = c->p;
     const size_t n = (size_t)p.nx * p.ny;
     float* stage = buf(c, 1 - c->cur);
-    for (int k = 0; k < kPlanes; ++k) {
+    const bool theta = p.storage == DMRT_THETA32;
+    for (int k = 0; k < (theta ? 9 : kPlanes); ++k) {
         const char* P = reinterpret_cast<const char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k) +
                         (size_t)c->row0 * c->L.pitch * plane_elem_bytes(p, k);
         const int st = plane_storage(p, k);
@@ -1529,6 +1647,15 @@ int dmrt_get_state(dmrt_ctx* c, float* host) {
         CK(cudaMemcpyAsync(host + (size_t)k * n, stage, n * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
            "copy state to host");
     }
+    if (theta) {
+        // The idle buffer holds 30 bytes per node: room for 5 float32 planes.
+        theta_to_g32<<<1024, 256, 0, c->stream>>>(reinterpret_cast<const unsigned char*>(buf(c, c->cur)),
+                                                  c->L.plane, c->L.pitch, p.nx, p.ny, c->row0, c->sc.w0,
+                                                  c->sc.w1, stage);
+        CK(cudaGetLastError(), "state conversion");
+        CK(cudaMemcpyAsync(host + (size_t)9 * n, stage, 5 * n * sizeof(float), cudaMemcpyDeviceToHost, c->stream),
+           "copy state to host");
+    }
     CK(cudaStreamSynchronize(c->stream), "synchronize");
     return DMRT_OK;
 }
@@ -1538,7 +1665,8 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
     const dmrt_params& p = c->p;
     const size_t n = (size_t)p.nx * p.ny;
     float* stage = buf(c, 1 - c->cur);
-    for (int k = 0; k < kPlanes; ++k) {
+    const bool theta = p.storage == DMRT_THETA32;
+    for (int k = 0; k < (theta ? 9 : kPlanes); ++k) {
         char* P = reinterpret_cast<char*>(buf(c, c->cur)) + plane_offset(p, c->L.plane, k) +
                   (size_t)c->row0 * c->L.pitch * plane_elem_bytes(p, k);
         const int st = plane_storage(p, k);
@@ -1556,6 +1684,13 @@ int dmrt_set_state(dmrt_ctx* c, const float* host) {
             plane_from_f32<E><<<1024, 256, 0, c->stream>>>(reinterpret_cast<E*>(P), stage, p.nx, p.ny,
                                                            c->L.pitch, plane_shift(c, k));
         });
+        CK(cudaGetLastError(), "state conversion");
+    }
+    if (theta) {
+        CK(cudaMemcpyAsync(stage, host + (size_t)9 * n, 5 * n * sizeof(float), cudaMemcpyHostToDevice, c->stream),
+           "copy state to device");
+        theta_from_g32<<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, c->cur)), c->L.plane,
+                                                    c->L.pitch, p.nx, p.ny, c->row0, c->sc.w1, stage);
         CK(cudaGetLastError(), "state conversion");
     }
     CK(cudaStreamSynchronize(c->stream), "synchronize");

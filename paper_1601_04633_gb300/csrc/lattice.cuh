@@ -38,6 +38,7 @@ struct StepConsts {
     float abb;                       // 2 sqrt(3) alpha (Eq. 45)
     int left_fixed, right_fixed;     // 1 = anti-bounce-back wall, 0 = adiabatic
     float gsh0, gsh1;                // 16-bit storage: g_0, g_1..4 stored minus these
+    float w0, w1;                    // D2Q5 rest weights (1 - a)/5 and (4 + a)/20 (Eq. 42)
     double nu_scale;                 // H / (3 (theta_hot - theta_cold))
 };
 

@@ -4,26 +4,30 @@
 // time steps per launch.
 //
 // Block r of the cluster owns rows [r rows_per, (r + 1) rows_per) of the
-// cavity; its shared memory holds those rows of both buffers, 14 planes
-// [row][x] each, in the device plane order of lattice.cuh. One thread per node
-// (looping when a block has more nodes than threads). The pull of a block's
-// first row reads the upward-moving planes of the previous block's last row,
-// and the pull of its last row the downward-moving planes of the next block's
-// first row, from those blocks' shared memory (distributed shared memory); the
-// walls are the same rules, in the same arithmetic, as the other step kernels,
-// and the collision is the same routine, so every step gives the other
-// kernels' bits. Between steps one cluster barrier (release / acquire at
-// cluster scope) publishes the new buffer; no step touches global memory
-// except the wall temperatures, the Nusselt ring and the error word.
+// cavity; its shared memory holds those rows of both buffers plus one halo row
+// below and one above, 14 planes [row][x] each, in the device plane order of
+// lattice.cuh. One thread per node (looping when a block has more nodes than
+// threads). Every pull reads this block's shared memory: when a thread stores
+// its node of the block's first row it also stores the downward-moving
+// populations (e_y = -1) into the halo row above of the previous block's
+// destination buffer, and for the last row the upward-moving ones (e_y = +1)
+// into the halo row below of the next block's (distributed shared memory
+// stores, which do not wait for a reply). Between steps one cluster barrier
+// (release / acquire at cluster scope) publishes the new buffers, halo rows
+// included. The walls are the same rules, in the same arithmetic, as the other
+// step kernels, and the collision is the same routine, so every step gives
+// the other kernels' bits. No step touches global memory except the wall
+// temperatures, the Nusselt ring and the error word.
 //
 // Nusselt number (Eqs. 18-19): the pre-collision temperatures at x = 0 and 1 of
 // each row are staged in shared memory; after a block barrier one thread per
 // row computes the row's value and writes it into block 0's shared row array
-// (distributed shared memory, double-buffered by step parity); after the step's cluster
-// barrier, warp 0 of block 0 sums the rows in the fixed order of
-// nu_finish_prev (partial p over rows p, p + 256, ...; lane l adds partials
-// q = 0..7 in order; butterfly over the lanes) and appends the mean to the
-// ring, while the other warps start the next step.
+// (distributed shared memory, double-buffered by step parity); after the
+// step's cluster barrier, one extra warp of block 0 (the last; it owns no
+// nodes) sums the rows in the fixed order of nu_finish_prev (partial p over
+// rows p, p + 256, ...; lane l adds partials q = 0..7 in order; butterfly over
+// the lanes) and appends the mean to the ring while the other warps compute
+// the next step.
 //
 // The launch starts from the state in global buffer `parity` (copied in), and
 // ends by copying the final state to global buffer parity ^ (K & 1), the last
@@ -57,8 +61,14 @@ struct ClusterArgs {
 // Means kept in block 0's shared memory between their flushes to the ring.
 constexpr int kClusterNuChunk = 1024;
 
+// Threads of a cluster block: one per node of its rows (at most 992), rounded up
+// to whole warps, and the Nusselt warp.
+__host__ __device__ constexpr int cluster_threads(int rows_per, int nx) {
+    return ((rows_per * nx + 31) / 32 * 32 < 992 ? (rows_per * nx + 31) / 32 * 32 : 992) + 32;
+}
+
 __host__ __device__ constexpr size_t cluster_smem_bytes(int rows_per, int nx, int ny) {
-    return (size_t)2 * kPlanes * rows_per * nx * sizeof(float)      // both buffers
+    return (size_t)2 * kPlanes * (rows_per + 2) * nx * sizeof(float)  // both buffers, with halo rows
            + (((size_t)4 * rows_per * sizeof(float) + 15) & ~size_t(15))  // theta at x = 0 and 1; hot, cold walls
            + (size_t)kClusterNuChunk * sizeof(double)                  // means not yet in the ring (block 0)
            + (size_t)2 * ny * sizeof(double);                         // Nusselt rows (block 0), by step parity
@@ -78,7 +88,7 @@ __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int
     return s;
 }
 
-static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
+static __global__ void __launch_bounds__(1024) step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
@@ -91,7 +101,9 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     const int r0 = rank * RP;
     const int nr = max(0, min(RP, ny - r0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int plane_sm = RP * nx;  // floats per plane in shared memory
+    const int plane_sm = (RP + 2) * nx;  // floats per plane in shared memory: rows -1 .. RP
+    const int nwork = (int)blockDim.x - 32;  // node threads; the last warp sums Nusselt rows
+    const bool nu_warp = (int)threadIdx.x >= nwork;
 
     extern __shared__ __align__(16) unsigned char smem_c[];
     float* sb[2] = {reinterpret_cast<float*>(smem_c), reinterpret_cast<float*>(smem_c) + kPlanes * plane_sm};
@@ -103,11 +115,21 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     grid_dep_wait();
     grid_dep_launch();
     const bool rec = C.record != nullptr;
-    // The state of this block's rows, from global buffer `parity` (record mode: from `start`).
-    for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
-        const int r = i / nx, x = i - r * nx;
-        if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err)) continue;
-        const float* src = (rec ? C.start : A0.src) + (size_t)(r0 + r) * pitch + x;
+    // The state of this block's rows and of the rows next to them, from global
+    // buffer `parity` (record mode: from `start`); halo rows beyond the
+    // cavity's walls read as zero in both buffers (the wall rules replace
+    // what a pull would take from them).
+    for (int i = threadIdx.x; i < (nr + 2) * nx; i += blockDim.x) {
+        const int rr = i / nx - 1, x = i - (rr + 1) * nx;
+        const int j = r0 + rr;
+        if (!DMRT_IN(i, 0, plane_sm, A0.err)) continue;
+        if (j < 0 || j >= ny) {
+#pragma unroll
+            for (int p = 0; p < kPlanes; ++p) sb[0][p * plane_sm + i] = sb[1][p * plane_sm + i] = 0.f;
+            continue;
+        }
+        if (!DMRT_IN((long long)j * pitch + x, 0, PL, A0.err)) continue;
+        const float* src = (rec ? C.start : A0.src) + (size_t)j * pitch + x;
 #pragma unroll
         for (int p = 0; p < kPlanes; ++p) sb[0][p * plane_sm + i] = src[p * PL];
     }
@@ -129,25 +151,30 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     const float sign_l_g = K.left_fixed ? -1.f : 1.f;
     const float sign_r_g = K.right_fixed ? -1.f : 1.f;
     bool bad = false;
+    // The halo rows this block fills in its neighbours' buffers: the row above
+    // the previous block's RP rows, the row below the next block's rows.
+    float* const below0 = rank > 0 ? cl.map_shared_rank(sb[0], rank - 1) + (size_t)(RP + 1) * nx : nullptr;
+    float* const below1 = rank > 0 ? cl.map_shared_rank(sb[1], rank - 1) + (size_t)(RP + 1) * nx : nullptr;
+    float* const above0 = rank + 1 < csize ? cl.map_shared_rank(sb[0], rank + 1) : nullptr;
+    float* const above1 = rank + 1 < csize ? cl.map_shared_rank(sb[1], rank + 1) : nullptr;
+    double* nu_rows0 = cl.map_shared_rank(nur, 0);
     for (int s = 0; s < C.steps; ++s) {
-        const float* S = sb[s & 1];
-        float* Dst = sb[(s & 1) ^ 1];
-        const float* Sprev = rank > 0 ? cl.map_shared_rank(S, rank - 1) : nullptr;
-        const float* Snext = rank + 1 < csize ? cl.map_shared_rank(S, rank + 1) : nullptr;
-        double* nu_dst = cl.map_shared_rank(nur, 0) + (size_t)(s & 1) * ny;
-        for (int i = threadIdx.x; i < nr * nx; i += blockDim.x) {
+        const bool odd = (s & 1) != 0;
+        const float* S = odd ? sb[1] : sb[0];
+        float* Dst = odd ? sb[0] : sb[1];
+        float* Dbelow = odd ? below0 : below1;
+        float* Dabove = odd ? above0 : above1;
+        double* nu_dst = nu_rows0 + (size_t)(s & 1) * ny;
+        for (int i = threadIdx.x; i < (nu_warp ? 0 : nr * nx); i += nwork) {
             const int r = i / nx, x = i - r * nx;
             const int j = r0 + r;
-            if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN(j, 0, ny, A0.err) || !DMRT_IN(r, 0, RP, A0.err)) continue;
-            // Post-collision value of plane p at (x, local row rr) of this step's state.
-            // (Across the cavity's bottom and top walls there is no such node: 0,
-            // replaced by the wall rules below.)
-            auto at = [&](int p, int rr, int xx) -> float {
-                if (rr < 0) return Sprev ? Sprev[p * plane_sm + (RP - 1) * nx + xx] : 0.f;  // previous block's last row
-                if (rr >= nr) return Snext ? Snext[p * plane_sm + xx] : 0.f;                // next block's first row
-                return S[p * plane_sm + rr * nx + xx];
-            };
-            auto own = [&](int p) { return S[p * plane_sm + r * nx + x]; };
+            if (!DMRT_IN(i + nx, 0, plane_sm, A0.err) || !DMRT_IN(j, 0, ny, A0.err) || !DMRT_IN(r, 0, RP, A0.err))
+                continue;
+            // Post-collision value of plane p at (x, local row rr = -1 .. nr) of
+            // this step's state. (Across the cavity's bottom and top walls the
+            // halo rows hold zeros, replaced by the wall rules below.)
+            auto at = [&](int p, int rr, int xx) -> float { return S[p * plane_sm + (rr + 1) * nx + xx]; };
+            auto own = [&](int p) { return S[p * plane_sm + (r + 1) * nx + x]; };
             // Pull (Eqs. 25, 36): value of direction k at x comes from x - e_k, where
             // that node exists; links across a wall are replaced below.
             float f[9], g[5];
@@ -199,9 +226,25 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
             collide_node(f, g, K, rho, theta);
             bad |= !(fabsf(rho) < 1e30f) || !(fabsf(theta) < 1e30f);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) Dst[plane_f(k) * plane_sm + i] = f[k];
+            for (int k = 0; k < 9; ++k) Dst[plane_f(k) * plane_sm + nx + i] = f[k];
 #pragma unroll
-            for (int k = 0; k < 5; ++k) Dst[plane_g(k) * plane_sm + i] = g[k];
+            for (int k = 0; k < 5; ++k) Dst[plane_g(k) * plane_sm + nx + i] = g[k];
+            // The neighbours' halo rows: downward-moving populations (0-based
+            // directions f 4, 7, 8 and g 4) of the first row to the previous
+            // block, upward-moving ones (f 2, 5, 6 and g 2) of the last row to
+            // the next block.
+            if (r == 0 && Dbelow) {
+                Dbelow[plane_f(4) * plane_sm + x] = f[4];
+                Dbelow[plane_f(7) * plane_sm + x] = f[7];
+                Dbelow[plane_f(8) * plane_sm + x] = f[8];
+                Dbelow[plane_g(4) * plane_sm + x] = g[4];
+            }
+            if (r == nr - 1 && Dabove) {
+                Dabove[plane_f(2) * plane_sm + x] = f[2];
+                Dabove[plane_f(5) * plane_sm + x] = f[5];
+                Dabove[plane_f(6) * plane_sm + x] = f[6];
+                Dabove[plane_g(2) * plane_sm + x] = g[2];
+            }
             if (rec) {
                 float* d = C.record + (size_t)s * C.record_stride + (size_t)j * pitch + x;
 #pragma unroll
@@ -213,14 +256,14 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
             if (x == 1) th01[2 * r + 1] = theta;
         }
         __syncthreads();  // theta at x = 0 and 1 of every row of this block
-        for (int r = threadIdx.x; r < (rec ? 0 : nr); r += blockDim.x) {
+        for (int r = threadIdx.x; r < (rec || nu_warp ? 0 : nr); r += nwork) {
             const int j = r0 + r;
             if (!DMRT_IN(j, 0, ny, A0.err)) continue;
             const double tw = (double)walls[r];
             nu_dst[j] = K.nu_scale * (8.0 * tw - 9.0 * (double)th01[2 * r] + (double)th01[2 * r + 1]);
         }
         cl.sync();  // the new state and the step's Nusselt rows are visible to the whole cluster
-        if (!rec && rank == 0 && warp == 0) {
+        if (!rec && rank == 0 && nu_warp) {
             // Mean of this step's rows while the other warps start the next step,
             // kept in shared memory; a full chunk goes to the ring (global stores
             // only once per kClusterNuChunk steps, so that the barriers between
@@ -243,10 +286,11 @@ static __global__ void step_cluster_kernel(const __grid_constant__ ClusterArgs C
     float* dstg = const_cast<float*>(C.A[pend].src);
     for (int i = threadIdx.x; i < (rec ? 0 : nr * nx); i += blockDim.x) {
         const int r = i / nx, x = i - r * nx;
-        if (!DMRT_IN(i, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err)) continue;
+        if (!DMRT_IN(i + nx, 0, plane_sm, A0.err) || !DMRT_IN((long long)(r0 + r) * pitch + x, 0, PL, A0.err))
+            continue;
         float* d = dstg + (size_t)(r0 + r) * pitch + x;
 #pragma unroll
-        for (int p = 0; p < kPlanes; ++p) d[p * PL] = fin[p * plane_sm + i];
+        for (int p = 0; p < kPlanes; ++p) d[p * PL] = fin[p * plane_sm + nx + i];
     }
     if (!rec && rank == 0 && C.steps > 0) {
         const double* last = nur + (size_t)((C.steps - 1) & 1) * ny;

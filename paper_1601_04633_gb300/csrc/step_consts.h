@@ -38,6 +38,8 @@ inline StepConsts make_step_consts(const dmrt_params& p, const dmrt_consts& k) {
     s.right_fixed = p.right_wall == DMRT_WALL_FIXED;
     s.gsh0 = (float)thermal_shift0(p, k);
     s.gsh1 = (float)thermal_shift1(p, k);
+    s.w0 = (float)((1.0 - k.a) / 5.0);
+    s.w1 = (float)((4.0 + k.a) / 20.0);
     const double dT = p.theta_hot - p.theta_cold;
     s.nu_scale = dT != 0.0 ? (double)p.ny / (3.0 * dT) : 0.0;
     return s;

@@ -310,6 +310,45 @@ __device__ __forceinline__ void lds_pull(const E* rowp, int n0, float (&o)[NPT],
     }
 }
 
+// NPT consecutive nodes n0.. of a shared-memory row together with their left
+// neighbours (l[e] = node n0 + e - 1) and, for lds_three, right neighbours
+// (r[e] = node n0 + e + 1): the unshifted vector and one shifted read per side.
+template <int NPT, int HALO, typename E>
+__device__ __forceinline__ void lds_left_own(const E* rowp, int n0, float (&l)[NPT], float (&c)[NPT]) {
+    const E* p = rowp + HALO + n0;
+    float a[NPT];
+    vec_get<E, NPT>(p - NPT, a);
+    vec_get<E, NPT>(p, c);
+    l[0] = a[NPT - 1];
+#pragma unroll
+    for (int e = 1; e < NPT; ++e) l[e] = c[e - 1];
+}
+template <int NPT, int HALO, typename E>
+__device__ __forceinline__ void lds_right_own(const E* rowp, int n0, float (&r)[NPT], float (&c)[NPT]) {
+    const E* p = rowp + HALO + n0;
+    float b[NPT];
+    vec_get<E, NPT>(p, c);
+    vec_get<E, NPT>(p + NPT, b);
+#pragma unroll
+    for (int e = 0; e < NPT - 1; ++e) r[e] = c[e + 1];
+    r[NPT - 1] = b[0];
+}
+template <int NPT, int HALO, typename E>
+__device__ __forceinline__ void lds_three(const E* rowp, int n0, float (&l)[NPT], float (&c)[NPT],
+                                          float (&r)[NPT]) {
+    const E* p = rowp + HALO + n0;
+    float a[NPT], b[NPT];
+    vec_get<E, NPT>(p - NPT, a);
+    vec_get<E, NPT>(p, c);
+    vec_get<E, NPT>(p + NPT, b);
+    l[0] = a[NPT - 1];
+#pragma unroll
+    for (int e = 1; e < NPT; ++e) l[e] = c[e - 1];
+#pragma unroll
+    for (int e = 0; e < NPT - 1; ++e) r[e] = c[e + 1];
+    r[NPT - 1] = b[0];
+}
+
 // Collide NPT nodes in place; nodes at or beyond nvalid (padding) are zeroed.
 template <int NPT>
 __device__ __forceinline__ void collide_nodes(float (&F)[9][NPT], float (&Gq)[5][NPT],
@@ -330,7 +369,7 @@ __device__ __forceinline__ void collide_nodes(float (&F)[9][NPT], float (&Gq)[5]
         for (int k = 0; k < 9; ++k) F[k][e] = valid ? f[k] : 0.f;
 #pragma unroll
         for (int k = 0; k < 5; ++k) Gq[k][e] = valid ? g[k] : (k == 0 ? K.gsh0 : K.gsh1);
-        theta[e] = th;
+        theta[e] = valid ? th : 0.f;
     }
 }
 
@@ -347,6 +386,7 @@ struct OneType {
     using Ef = E;
     using Eg = E;
     static constexpr bool kSplit = false;
+    static constexpr bool kTheta = false;
     static constexpr int kHalo = tma_halo(sizeof(E));
     __host__ __device__ static constexpr int pf(int k) { return plane_f(k); }
     __host__ __device__ static constexpr int pg(int k) { return plane_g(k); }
@@ -357,11 +397,38 @@ struct Split {
     using Ef = EF;
     using Eg = EG;
     static constexpr bool kSplit = true;
+    static constexpr bool kTheta = false;
     static constexpr int kHalo = tma_halo(sizeof(EF) < sizeof(EG) ? sizeof(EF) : sizeof(EG));
     __host__ __device__ static constexpr int pf(int k) { return split_f(k); }
     __host__ __device__ static constexpr int pg(int k) { return split_g(k); }
 };
 
+// ThetaSplit: the 9 flow planes in float16 as in Split, then the thermal
+// block: one float32 plane holding theta = sum_i g_i (Eq. 41), then four
+// float16 planes holding d_k = g_k - w theta for the moving directions k = 1..4
+// (0-based: +x, +y, -x, -y; w = (4 + a)/20, the D2Q5 rest weight of Eq. 42),
+// deviation plane k - 1. The rest population is g_0 = w_0 theta - (d_1 + d_2 +
+// d_3 + d_4) (w_0 = (1 - a)/5), so a node's stored populations sum to its
+// theta whatever the rounding of the deviations. Pulling g_k into a node needs
+// the source node's theta and d_k, and g_0 the node's own four deviations: the
+// thermal block is staged with one halo row on each side (R + 2 rows) instead
+// of by plane group. Eg is the deviations' type; pg is not used.
+struct ThetaSplit {
+    using Ef = __half;
+    using Eg = __half;
+    static constexpr bool kSplit = true;
+    static constexpr bool kTheta = true;
+    static constexpr int kHalo = tma_halo(2);
+    __host__ __device__ static constexpr int pf(int k) { return split_f(k); }
+    __host__ __device__ static constexpr int pg(int k) { return k; }
+};
+
+// ThetaSplit stage of R rows: the flow groups (9 planes x R rows of float16),
+// then theta (R + 2 rows of float32), then the deviations (4 planes x (R + 2)
+// rows of float16); every part starts 128-byte aligned.
+__host__ __device__ constexpr size_t theta_stage_th(int R) { return (size_t)9 * R * kTmaBox * 2; }
+__host__ __device__ constexpr size_t theta_stage_d(int R) { return theta_stage_th(R) + (size_t)(R + 2) * kTmaBox * 4; }
+__host__ __device__ constexpr size_t theta_stage_bytes(int R) { return theta_stage_d(R) + (size_t)4 * (R + 2) * kTmaBox * 2; }
 // Shared-memory output tile of one item for the tensor-store epilogue: the
 // item's R rows x W nodes (W = strip width) of every plane, [plane][row][node];
 // split layouts put the thermal planes at a 128-byte aligned offset (a tensor
@@ -374,16 +441,27 @@ __host__ __device__ constexpr size_t out_tile_bytes(bool split, int R, int W, in
     return split ? round128(out_g_offset(true, R, W, f_bytes) + (size_t)5 * R * W * g_bytes)
                  : round128((size_t)kPlanes * R * W * f_bytes);
 }
+// ThetaSplit output tile of R rows x W nodes: flow [9][R][W] float16, theta
+// [R][W] float32, deviations [4][R][W] float16, each part 128-byte aligned.
+__host__ __device__ constexpr size_t theta_out_th(int R, int W) { return round128((size_t)9 * R * W * 2); }
+__host__ __device__ constexpr size_t theta_out_d(int R, int W) {
+    return theta_out_th(R, W) + round128((size_t)R * W * 4);
+}
+__host__ __device__ constexpr size_t theta_out_bytes(int R, int W) {
+    return theta_out_d(R, W) + round128((size_t)4 * R * W * 2);
+}
 
 // Tensor maps of the single-cavity TMA kernel for one source buffer: loads
 // from the source (one-type layout: 6-plane and 4-plane boxes; split layout:
-// 3-plane flow, 3-plane and 1-plane thermal boxes) and the epilogue's stores
-// to the destination (one-type: one 14-plane box; split: a 9-plane flow and a
-// 5-plane thermal box). The store maps span nx columns, so the padding columns
+// 3-plane flow, 3-plane and 1-plane thermal boxes; ThetaSplit: 3-plane flow
+// boxes, a theta box and a 4-plane deviation box of R + 2 rows) and the
+// epilogue's stores to the destination (one-type: one 14-plane box; split: a
+// 9-plane flow and a 5-plane thermal box; ThetaSplit: flow, theta and
+// deviation boxes). The store maps span nx columns, so the padding columns
 // of the last strip are never written.
 struct TmaMaps {
     CUtensorMap ld[3];
-    CUtensorMap st[2];
+    CUtensorMap st[3];
 };
 
 template <typename E, int NPT, bool SR>
@@ -400,6 +478,7 @@ struct StageOffsets {
     int zP, zN;
     int g_bytes;
     int gP, gN;
+    int d_bytes;  // ThetaSplit: theta at byte g_bytes, the deviation planes at byte d_bytes
 };
 
 // Pull, collide and store one work item (strip, row block) from its shared-
@@ -464,18 +543,31 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             const long long b = (long long)(rowf(L::pf(k)) - stf) * (long long)sizeof(Ef);
             bc = DMRT_IN(b, 0, stage_cap, A.err) && DMRT_IN(b + (long long)WB * sizeof(Ef) - 1, 0, stage_cap, A.err);
         }
-        for (int k = 0; k < 5 && bc; ++k) {
-            const long long b = (long long)(rowg(L::pg(k)) - stg) * (long long)sizeof(Eg) + (L::kSplit ? so.g_bytes : 0);
-            bc = DMRT_IN(b, 0, stage_cap, A.err) && DMRT_IN(b + (long long)WB * sizeof(Eg) - 1, 0, stage_cap, A.err);
+        if constexpr (L::kTheta) {
+            // Theta rows rg .. rg + 2 and the same rows of the 4 deviation planes.
+            const long long bt = so.g_bytes + (long long)(rg + 2) * WB * 4;
+            const long long bd = so.d_bytes + ((long long)3 * (RC + 2) + rg + 2) * WB * 2;
+            bc = bc && DMRT_IN(bt + (long long)WB * 4 - 1, 0, stage_cap, A.err) &&
+                 DMRT_IN(bd + (long long)WB * 2 - 1, 0, stage_cap, A.err);
+        } else {
+            for (int k = 0; k < 5 && bc; ++k) {
+                const long long b =
+                    (long long)(rowg(L::pg(k)) - stg) * (long long)sizeof(Eg) + (L::kSplit ? so.g_bytes : 0);
+                bc = DMRT_IN(b, 0, stage_cap, A.err) && DMRT_IN(b + (long long)WB * sizeof(Eg) - 1, 0, stage_cap, A.err);
+            }
         }
-        const long long nfp = L::kSplit ? 9 : kPlanes, ngp = L::kSplit ? 5 : kPlanes;
+        // Destination offsets within the flow and thermal blocks (ThetaSplit: a
+        // thermal block of 6 float16-sized planes, theta taking two).
+        const long long nfp = L::kSplit ? 9 : kPlanes, ngp = L::kTheta ? 6 : L::kSplit ? 5 : kPlanes;
         const long long ro = (long long)(j + A.row0) * A.pitch;
         bc = bc && DMRT_IN(ro + x0 + NPT - 1, 0, PL, A.err) && DMRT_IN(ro + A.nx - 1, 0, PL, A.err) &&
              DMRT_IN((nfp - 1) * PL + ro + x0, 0, nfp * PL, A.err) &&
              DMRT_IN((ngp - 1) * PL + ro + x0, 0, ngp * PL, A.err);
         if (TS)
             bc = bc && DMRT_IN(rg, 0, RC, A.err) && DMRT_IN(n0 + NPT - 1, 0, W, A.err) &&
-                 DMRT_IN((long long)out_tile_bytes(L::kSplit, RC, W, sizeof(Ef), sizeof(Eg)) - 1, 0, out_cap, A.err);
+                 DMRT_IN((long long)(L::kTheta ? theta_out_bytes(RC, W)
+                                               : out_tile_bytes(L::kSplit, RC, W, sizeof(Ef), sizeof(Eg))) - 1,
+                         0, out_cap, A.err);
     }
 #endif
     if (mine && bc) {
@@ -489,11 +581,42 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
         lds_pull<-1, NPT, HALO>(rowf(L::pf(6)), n0, F[6], 0.f);
         lds_pull<-1, NPT, HALO>(rowf(L::pf(7)), n0, F[7], 0.f);
         lds_pull<1, NPT, HALO>(rowf(L::pf(8)), n0, F[8], 0.f);
-        lds_pull<0, NPT, HALO>(rowg(L::pg(0)), n0, Gq[0], sh0);
-        lds_pull<1, NPT, HALO>(rowg(L::pg(1)), n0, Gq[1], sh1);
-        lds_pull<0, NPT, HALO>(rowg(L::pg(2)), n0, Gq[2], sh1);
-        lds_pull<-1, NPT, HALO>(rowg(L::pg(3)), n0, Gq[3], sh1);
-        lds_pull<0, NPT, HALO>(rowg(L::pg(4)), n0, Gq[4], sh1);
+        // ThetaSplit: the node's own theta and deviations (g*_k = w theta + d_k of
+        // the previous step's collision at this node, for g_0 and the walls).
+        float thc[NPT], d1o[NPT], d2o[NPT], d3o[NPT], d4o[NPT];
+        if constexpr (L::kTheta) {
+            const float* sth = reinterpret_cast<const float*>(stage + so.g_bytes) + rg * WB;  // row j - 1
+            const Eg* sd = reinterpret_cast<const Eg*>(stage + so.d_bytes) + rg * WB;
+            const int DPB = (RC + 2) * WB;  // elements of one deviation plane in the stage
+            float thl[NPT], thr[NPT], thd[NPT], thu[NPT], dv[NPT];
+            lds_three<NPT, HALO>(sth + WB, n0, thl, thc, thr);
+            lds_pull<0, NPT, HALO>(sth, n0, thd, 0.f);
+            lds_pull<0, NPT, HALO>(sth + 2 * WB, n0, thu, 0.f);
+            // g_k pulled from the source node x - e_k: w theta(source) + d_k(source).
+            lds_left_own<NPT, HALO>(sd + WB, n0, dv, d1o);  // k = 1 (+x) from x - 1
+#pragma unroll
+            for (int e = 0; e < NPT; ++e) Gq[1][e] = fmaf(K.w1, thl[e], dv[e]);
+            lds_right_own<NPT, HALO>(sd + 2 * DPB + WB, n0, dv, d3o);  // k = 3 (-x) from x + 1
+#pragma unroll
+            for (int e = 0; e < NPT; ++e) Gq[3][e] = fmaf(K.w1, thr[e], dv[e]);
+            lds_pull<0, NPT, HALO>(sd + DPB, n0, dv, 0.f);  // k = 2 (+y) from row j - 1
+            lds_pull<0, NPT, HALO>(sd + DPB + WB, n0, d2o, 0.f);
+#pragma unroll
+            for (int e = 0; e < NPT; ++e) Gq[2][e] = fmaf(K.w1, thd[e], dv[e]);
+            lds_pull<0, NPT, HALO>(sd + 3 * DPB + 2 * WB, n0, dv, 0.f);  // k = 4 (-y) from row j + 1
+            lds_pull<0, NPT, HALO>(sd + 3 * DPB + WB, n0, d4o, 0.f);
+#pragma unroll
+            for (int e = 0; e < NPT; ++e) {
+                Gq[4][e] = fmaf(K.w1, thu[e], dv[e]);
+                Gq[0][e] = fmaf(K.w0, thc[e], -((d1o[e] + d3o[e]) + (d2o[e] + d4o[e])));
+            }
+        } else {
+            lds_pull<0, NPT, HALO>(rowg(L::pg(0)), n0, Gq[0], sh0);
+            lds_pull<1, NPT, HALO>(rowg(L::pg(1)), n0, Gq[1], sh1);
+            lds_pull<0, NPT, HALO>(rowg(L::pg(2)), n0, Gq[2], sh1);
+            lds_pull<-1, NPT, HALO>(rowg(L::pg(3)), n0, Gq[3], sh1);
+            lds_pull<0, NPT, HALO>(rowg(L::pg(4)), n0, Gq[4], sh1);
+        }
 
         // Walls. Bottom row: links from below (f2, f5, f6, g2) bounce back from
         // the node's own opposites (f4, f7, f8, g4); top row the reverse.
@@ -503,13 +626,23 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             vec_ldg<Ef, NPT>(rowjf + L::pf(4) * PL + x0, F[2], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(7) * PL + x0, F[5], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(8) * PL + x0, F[6], 0.f);
-            vec_ldg<Eg, NPT>(rowjg + L::pg(4) * PL + x0, Gq[2], sh1);
+            if constexpr (L::kTheta) {
+#pragma unroll
+                for (int e = 0; e < NPT; ++e) Gq[2][e] = fmaf(K.w1, thc[e], d4o[e]);
+            } else {
+                vec_ldg<Eg, NPT>(rowjg + L::pg(4) * PL + x0, Gq[2], sh1);
+            }
         }
         if (j == A.ny - 1 && A.wall_hi) {
             vec_ldg<Ef, NPT>(rowjf + L::pf(2) * PL + x0, F[4], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(5) * PL + x0, F[7], 0.f);
             vec_ldg<Ef, NPT>(rowjf + L::pf(6) * PL + x0, F[8], 0.f);
-            vec_ldg<Eg, NPT>(rowjg + L::pg(2) * PL + x0, Gq[4], sh1);
+            if constexpr (L::kTheta) {
+#pragma unroll
+                for (int e = 0; e < NPT; ++e) Gq[4][e] = fmaf(K.w1, thc[e], d2o[e]);
+            } else {
+                vec_ldg<Eg, NPT>(rowjg + L::pg(2) * PL + x0, Gq[4], sh1);
+            }
         }
         // Left wall (node x = 0): links with e_x = +1 (f1, f5, f8, g1).
         if (x0 == 0) {
@@ -517,7 +650,8 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             F[5][0] = ldg_one(rowjf + L::pf(7) * PL, 0.f);
             F[8][0] = ldg_one(rowjf + L::pf(6) * PL, 0.f);
             const float add = K.left_fixed ? K.abb * __ldg(A.hot + j) : 0.f;
-            Gq[1][0] = sign_l_g * ldg_one(rowjg + L::pg(3) * PL, sh1) + add;
+            const float g3 = L::kTheta ? fmaf(K.w1, thc[0], d3o[0]) : ldg_one(rowjg + L::pg(3) * PL, sh1);
+            Gq[1][0] = sign_l_g * g3 + add;
         }
         // Right wall (node x = nx - 1): links with e_x = -1 (f3, f6, f7, g3).
         const int re = A.nx - 1 - x0;
@@ -527,14 +661,14 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             const float v6 = ldg_one(rowjf + L::pf(8) * PL + xr, 0.f);
             const float v7 = ldg_one(rowjf + L::pf(5) * PL + xr, 0.f);
             const float add = K.right_fixed ? K.abb * __ldg(A.cold + j) : 0.f;
-            const float vg = sign_r_g * ldg_one(rowjg + L::pg(1) * PL + xr, sh1) + add;
+            const float vg = L::kTheta ? 0.f : sign_r_g * ldg_one(rowjg + L::pg(1) * PL + xr, sh1) + add;
 #pragma unroll
             for (int e = 0; e < NPT; ++e) {
                 if (e == re) {
                     F[3][e] = v3;
                     F[6][e] = v6;
                     F[7][e] = v7;
-                    Gq[3][e] = vg;
+                    Gq[3][e] = L::kTheta ? sign_r_g * fmaf(K.w1, thc[e], d1o[e]) + add : vg;
                 }
             }
         }
@@ -563,8 +697,34 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             r[e] = SR ? hash32(((unsigned)(j + A.jglob0) * (unsigned)A.pitch + (unsigned)(x0 + e)) ^ salt) : 0u;
 #pragma unroll
         for (int k = 0; k < 9; ++k) put_vals<Ef, NPT, SR>(Df + L::pf(k) * DP, F[k], 0.f, r);
+        if constexpr (L::kTheta) {
+            // theta (the collision keeps it) and d_k = g*_k - w theta, k = 1..4.
+            float* Dth;
+            Eg* Dd;
+            if constexpr (TS) {
+                Dth = reinterpret_cast<float*>(out + theta_out_th(RC, W)) + rg * W + n0;
+                Dd = reinterpret_cast<Eg*>(out + theta_out_d(RC, W)) + rg * W + n0;
+            } else {
+                unsigned char* tb = reinterpret_cast<unsigned char*>(A.dst) + (size_t)9 * PL * sizeof(Ef);
+                const size_t o = (size_t)(j + A.row0) * A.pitch + x0;
+                Dth = reinterpret_cast<float*>(tb) + o;
+                Dd = reinterpret_cast<Eg*>(tb + (size_t)PL * 4) + o;
+            }
+            Pack<float, NPT> tq;
 #pragma unroll
-        for (int k = 0; k < 5; ++k) put_vals<Eg, NPT, SR>(Dg + L::pg(k) * DP, Gq[k], k == 0 ? sh0 : sh1, r);
+            for (int e = 0; e < NPT; ++e) tq.v[e] = theta[e];
+            *reinterpret_cast<Pack<float, NPT>*>(Dth) = tq;
+#pragma unroll
+            for (int k = 1; k < 5; ++k) {
+                float dv[NPT];
+#pragma unroll
+                for (int e = 0; e < NPT; ++e) dv[e] = fmaf(-K.w1, theta[e], Gq[k][e]);
+                put_vals<Eg, NPT, SR>(Dd + (k - 1) * DP, dv, 0.f, r);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 5; ++k) put_vals<Eg, NPT, SR>(Dg + L::pg(k) * DP, Gq[k], k == 0 ? sh0 : sh1, r);
+        }
         if (bad) atomicOr(A.err, kErrNonFinite);
     }
     // Nusselt number of row j from the first warp of the row's thread group
@@ -605,6 +765,10 @@ struct ItemCursor {
 
 // Shared memory of the single-cavity kernel: S input stages, with TS two
 // output tiles, and S mbarriers.
+__host__ __device__ constexpr size_t step_tma_smem_bytes_theta(bool ts, int R, int S) {
+    return (size_t)S * theta_stage_bytes(R) + (ts ? 2 * theta_out_bytes(R, kTmaBox - 2 * tma_halo(2)) : 0) +
+           (size_t)S * 8;
+}
 __host__ __device__ constexpr size_t step_tma_smem_bytes(bool split, bool ts, int R, int S, int f_bytes,
                                                          int g_bytes) {
     return (size_t)S * tma_stage_bytes_fg(R, f_bytes, g_bytes) +
@@ -624,19 +788,23 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
                                                           StepArgs A, StepConsts K, TmaGeo T) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
-    constexpr uint32_t kStageBytes = (uint32_t)tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));
+    constexpr uint32_t kStageBytes =
+        (uint32_t)(L::kTheta ? theta_stage_bytes(R) : tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg)));
     constexpr int HALO = L::kHalo;
     constexpr int STRIP = kTmaBox - 2 * HALO;
-    constexpr size_t kOutBytes = out_tile_bytes(L::kSplit, R, STRIP, sizeof(Ef), sizeof(Eg));
-    constexpr size_t kOutG = out_g_offset(L::kSplit, R, STRIP, sizeof(Ef));
+    constexpr size_t kOutBytes =
+        L::kTheta ? theta_out_bytes(R, STRIP) : out_tile_bytes(L::kSplit, R, STRIP, sizeof(Ef), sizeof(Eg));
+    constexpr size_t kOutG = L::kTheta ? theta_out_th(R, STRIP) : out_g_offset(L::kSplit, R, STRIP, sizeof(Ef));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* stages = smem_raw;
     unsigned char* outs = smem_raw + (size_t)S * kStageBytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(outs + (TS ? 2 * kOutBytes : 0));
     constexpr int TPR = 256 / NPT;   // threads per row of a strip
     constexpr int PB = R * kTmaBox;  // elements of one plane in a stage
-    constexpr StageOffsets kSO = L::kSplit ? StageOffsets{3 * PB, 6 * PB, (int)(9 * PB * sizeof(Ef)), 3 * PB, 4 * PB}
-                                           : StageOffsets{kGroupP * PB, kGroupN * PB, 0, 0, 0};
+    constexpr StageOffsets kSO =
+        L::kTheta   ? StageOffsets{3 * PB, 6 * PB, (int)theta_stage_th(R), 0, 0, (int)theta_stage_d(R)}
+        : L::kSplit ? StageOffsets{3 * PB, 6 * PB, (int)(9 * PB * sizeof(Ef)), 3 * PB, 4 * PB, 0}
+                    : StageOffsets{kGroupP * PB, kGroupN * PB, 0, 0, 0, 0};
     const int tid = threadIdx.x;
     const int rg = tid / TPR;  // row of the block this thread works on
     const int t = tid % TPR;   // node group within the strip
@@ -667,6 +835,8 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
     // row below / above (their e_y). One-type layout: ld[0] has 6-plane boxes
     // (group Z), ld[1] 4-plane boxes (P, N). Split layout: ld[0] has 3-plane
     // flow boxes, ld[1] 3-plane thermal boxes, ld[2] 1-plane thermal boxes.
+    // ThetaSplit: ld[0] as Split, ld[1] theta boxes and ld[2] 4-plane
+    // deviation boxes of R + 2 rows from the row below the item's first.
     auto issue = [&](const ItemCursor& c, int s) {
         const int x = c.strip * STRIP - HALO;
         const int j0 = c.rb * R + A.row0;  // buffer row of the item's first row
@@ -679,13 +849,18 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
             tma_load_3d(e + kGroupN * PB, &M.ld[1], x, j0 + 1, kGroupN, &bars[s]);
         } else {
             Ef* f = reinterpret_cast<Ef*>(st);
-            Eg* g = reinterpret_cast<Eg*>(st + (size_t)9 * PB * sizeof(Ef));
             tma_load_3d(f, &M.ld[0], x, j0, 0, &bars[s]);
             tma_load_3d(f + 3 * PB, &M.ld[0], x, j0 - 1, 3, &bars[s]);
             tma_load_3d(f + 6 * PB, &M.ld[0], x, j0 + 1, 6, &bars[s]);
-            tma_load_3d(g, &M.ld[1], x, j0, 0, &bars[s]);
-            tma_load_3d(g + 3 * PB, &M.ld[2], x, j0 - 1, 3, &bars[s]);
-            tma_load_3d(g + 4 * PB, &M.ld[2], x, j0 + 1, 4, &bars[s]);
+            if constexpr (L::kTheta) {
+                tma_load_3d(st + kSO.g_bytes, &M.ld[1], x, j0 - 1, 0, &bars[s]);
+                tma_load_3d(st + kSO.d_bytes, &M.ld[2], x, j0 - 1, 0, &bars[s]);
+            } else {
+                Eg* g = reinterpret_cast<Eg*>(st + (size_t)9 * PB * sizeof(Ef));
+                tma_load_3d(g, &M.ld[1], x, j0, 0, &bars[s]);
+                tma_load_3d(g + 3 * PB, &M.ld[2], x, j0 - 1, 3, &bars[s]);
+                tma_load_3d(g + 4 * PB, &M.ld[2], x, j0 + 1, 4, &bars[s]);
+            }
         }
     };
     // Item (strip, rb) from output tile o: a box of STRIP x R x planes at the
@@ -695,6 +870,7 @@ __global__ void __launch_bounds__(R * (256 / NPT)) step_tma_kernel(const __grid_
         const int j0 = rb * R + A.row0;
         tma_store_3d(&M.st[0], o, x, j0, 0);
         if constexpr (L::kSplit) tma_store_3d(&M.st[1], o + kOutG, x, j0, 0);
+        if constexpr (L::kTheta) tma_store_3d(&M.st[2], o + theta_out_d(R, STRIP), x, j0, 0);
         bulk_commit();
     };
 

@@ -6,7 +6,7 @@
 namespace dmrt {
 
 struct TmaVariant {
-    int storage;   // DMRT_FP32, DMRT_FP16, DMRT_BF16 or DMRT_MIXED
+    int storage;   // DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED or DMRT_THETA32
     int rounding;  // DMRT_ROUND_NEAREST or DMRT_ROUND_STOCHASTIC
     int npt, R, S;
     int ts;  // 1: tensor-store epilogue through shared-memory output tiles
@@ -19,6 +19,7 @@ const TmaVariant* tma_variants_npt1(int* n);
 const TmaVariant* tma_variants_fp16(int* n);
 const TmaVariant* tma_variants_bf16(int* n);
 const TmaVariant* tma_variants_mixed(int* n);  // float16 flow, float32 thermal
+const TmaVariant* tma_variants_theta(int* n);  // float16 flow and deviations, float32 theta
 const TmaVariant* tma_variants_batch(int* n);  // batched sweep kernels
 const TmaVariant* tma_variants_batch_mstep(int* n);  // batched sweep, several steps per launch
 

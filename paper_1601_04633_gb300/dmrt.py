@@ -31,7 +31,7 @@ DMRT_E_TIMEOUT = -5
 DMRT_E_SPACE = -6
 DMRT_E_STATE = -7
 DMRT_E_BOUNDS = -8
-DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED = 0, 1, 2, 3
+DMRT_FP32, DMRT_FP16, DMRT_BF16, DMRT_MIXED, DMRT_THETA32 = 0, 1, 2, 3, 4
 DMRT_WALL_FIXED, DMRT_WALL_ADIABATIC = 0, 1
 DMRT_KERNEL_AUTO, DMRT_KERNEL_DIRECT, DMRT_KERNEL_TMA, DMRT_KERNEL_CLUSTER = 0, 1, 2, 3
 DMRT_ROUND_NEAREST, DMRT_ROUND_STOCHASTIC, DMRT_ROUND_AUTO = 0, 1, 2

@@ -32,6 +32,8 @@ SINGLE_TILES_MIXED = [(1, 1, 2), (1, 1, 3), (1, 1, 4), (1, 2, 2), (1, 2, 3), (1,
                       (2, 1, 4), (2, 2, 2), (4, 1, 3), (4, 1, 4)]
 SINGLE_TILES_MIXED_SR = [(1, 1, 2), (1, 2, 2), (1, 4, 2), (1, 4, 3), (2, 1, 2), (2, 1, 3), (2, 2, 2), (2, 4, 2),
                          (4, 1, 3)]
+SINGLE_TILES_THETA = [(1, 1, 2), (2, 1, 2), (2, 1, 3), (2, 2, 2), (4, 1, 3)]
+SINGLE_TILES_THETA_SR = [(1, 1, 2), (1, 2, 2), (2, 1, 2), (2, 1, 3), (2, 2, 2), (2, 4, 2), (4, 1, 3), (4, 2, 2)]
 
 
 def _time_steps(step, steps, warmup):
@@ -148,6 +150,8 @@ def tune_single(cav, storage=0, rounding=0, steps=200, warmup=20, tiles=None, ca
     if tiles is None:
         if storage == 3:
             tiles = SINGLE_TILES_MIXED_SR if rounding else SINGLE_TILES_MIXED
+        elif storage == 4:
+            tiles = SINGLE_TILES_THETA_SR if rounding else SINGLE_TILES_THETA
         else:
             tiles = SINGLE_TILES_FP32 if storage == 0 else (SINGLE_TILES_16_SR if rounding else SINGLE_TILES_16)
     key = _key("single", [(cav.nx, cav.ny)], f"{storage}-{rounding}-{steps}")

@@ -52,7 +52,8 @@ def test_auto_rounding_resolves_per_storage(D):
     # that keeps the long-run Nusselt number within 1e-3) and nothing for float32:
     # the launch chosen for AUTO is the one chosen for the resolved mode.
     for storage, resolved in ((D.DMRT_FP32, D.DMRT_ROUND_NEAREST), (D.DMRT_FP16, D.DMRT_ROUND_STOCHASTIC),
-                              (D.DMRT_BF16, D.DMRT_ROUND_STOCHASTIC), (D.DMRT_MIXED, D.DMRT_ROUND_STOCHASTIC)):
+                              (D.DMRT_BF16, D.DMRT_ROUND_STOCHASTIC), (D.DMRT_MIXED, D.DMRT_ROUND_STOCHASTIC),
+                              (D.DMRT_THETA32, D.DMRT_ROUND_STOCHASTIC)):
         for n in (64, 1000, 4096):
             auto = D.make_params(n, n, 1e5, 0.01, storage=storage, rounding=D.DMRT_ROUND_AUTO)
             expl = D.make_params(n, n, 1e5, 0.01, storage=storage, rounding=resolved)
@@ -110,6 +111,30 @@ def test_workspace_size(D):
     assert 2 * 14 * 4 * 4096 * 4096 <= n < 2 * 14 * 4 * 4096 * 4096 + (16 << 20)
     p2 = D.make_params(130, 7, 1e4, 0.01, 0.1)
     assert D.dmrt_workspace_size(p2) >= 2 * 14 * 4 * 256 * 7  # rows padded to 128 elements
+
+
+def test_workspace_size_per_storage(D):
+    # Bytes per node and buffer: float32 56, float16 / bfloat16 28, mixed 38
+    # (float16 flow, float32 thermal), THETA32 30 (float16 flow and deviations,
+    # float32 theta).
+    for storage, per_node in ((D.DMRT_FP32, 56), (D.DMRT_FP16, 28), (D.DMRT_BF16, 28), (D.DMRT_MIXED, 38),
+                              (D.DMRT_THETA32, 30)):
+        p = D.make_params(1024, 512, 1e5, 0.01, 0.1, storage=storage, nu_capacity=1024)
+        n = D.dmrt_workspace_size(p)
+        assert 2 * per_node * 1024 * 512 <= n < 2 * per_node * 1024 * 512 + (1 << 20), storage
+
+
+def test_theta32_refused_where_it_has_no_kernel(D):
+    # THETA32 runs the single-cavity TMA kernel only: no slabs, no direct kernel.
+    p = D.make_params(256, 256, 1e5, 0.01, 0.1, storage=D.DMRT_THETA32)
+    with pytest.raises(D.DmrtError) as ei:
+        D.dmrt_slab_workspace_size(p, 128)
+    assert ei.value.code == D.DMRT_E_ARG
+    p.kernel = D.DMRT_KERNEL_DIRECT
+    with pytest.raises(D.DmrtError):
+        D.dmrt_choose_launch(p, 152)
+    p.kernel = D.DMRT_KERNEL_AUTO
+    assert D.dmrt_choose_launch(p, 152)[0] == D.DMRT_KERNEL_TMA
 
 
 def test_create_without_workspace_fails_cleanly(D):

@@ -28,6 +28,8 @@ SINGLE = [
     ("481x8_fp16", 481, 8, {"storage": 1}), ("300x70_bf16", 300, 70, {"storage": 2, "rounding": 1}),
     ("1000x301_mixed", 1000, 301, {"storage": 3}), ("67x45_mixed", 67, 45, {"storage": 3, "rounding": 0}),
     ("64x64_cluster", 64, 64, {"kernel": 3}), ("37x23_cluster", 37, 23, {"kernel": 3}),
+    ("1000x301_theta32", 1000, 301, {"storage": 4}), ("5x3_theta32", 5, 3, {"storage": 4, "rounding": 0}),
+    ("481x8_theta32_r4", 481, 8, {"storage": 4, "tma_npt": 2, "tma_rows": 4, "tma_stages": 2}),
 ]
 STEPS = 21
 

@@ -130,7 +130,7 @@ def test_energy_conserved_with_adiabatic_walls(D):
     assert abs(e1 - e0) <= 1e-6 * np.abs(cav.theta0()).sum()
 
 
-@pytest.mark.parametrize("storage", [0, 1, 3], ids=["fp32", "fp16", "mixed"])
+@pytest.mark.parametrize("storage", [0, 1, 3, 4], ids=["fp32", "fp16", "mixed", "theta32"])
 @pytest.mark.parametrize("walls", [(0, 0), (0, 1), (1, 0)], ids=["fixed_fixed", "fixed_adiabatic", "adiabatic_fixed"])
 def test_energy_budget_with_fixed_temperature_walls(D, storage, walls):
     # Over one step the heat content changes by exactly the wall heat input of
@@ -157,9 +157,12 @@ def test_energy_budget_with_fixed_temperature_walls(D, storage, walls):
         w_ref += np.sum(k.abb * cav.theta_cold - 2.0 * g[1, :, -1])
     n = cav.nx * cav.ny
     scale = np.abs(g).sum()
-    assert abs(e0 - g.sum()) <= 1e-12 * scale
+    # THETA32 sums its stored theta; dmrt_get_state rebuilds the populations
+    # from theta and the deviations in float32, which sum to theta to rounding.
+    assert abs(e0 - g.sum()) <= (1e-6 if storage == 4 else 1e-12) * scale
     assert abs(w0 - w_ref) <= 1e-6 * (abs(w_ref) + cav.ny)
-    u = {0: 2.0 ** -24, 1: 2.0 ** -11, 3: 2.0 ** -24}[storage]  # rounding unit of the stored g
+    # Rounding unit of the stored heat: THETA32 keeps theta in float32.
+    u = {0: 2.0 ** -24, 1: 2.0 ** -11, 3: 2.0 ** -24, 4: 2.0 ** -24}[storage]
     tol = 10 * u * scale + 1e-6 * abs(w0)
     assert abs((e1 - e0) - w0) <= tol, (e1 - e0, w0)
     if storage == 0 and walls != (0, 0):

@@ -160,10 +160,12 @@ def test_long_run_nu_gate(D, storage, rounding):
 
 
 TILES = {(1, 0): tune.SINGLE_TILES_16, (1, 1): tune.SINGLE_TILES_16_SR, (2, 0): tune.SINGLE_TILES_16,
-         (2, 1): tune.SINGLE_TILES_16_SR, (3, 0): tune.SINGLE_TILES_MIXED, (3, 1): tune.SINGLE_TILES_MIXED_SR}
+         (2, 1): tune.SINGLE_TILES_16_SR, (3, 0): tune.SINGLE_TILES_MIXED, (3, 1): tune.SINGLE_TILES_MIXED_SR,
+         (4, 0): tune.SINGLE_TILES_THETA, (4, 1): tune.SINGLE_TILES_THETA_SR}
 
 
-@pytest.mark.parametrize("storage,rounding", list(TILES), ids=["fp16", "fp16_sr", "bf16", "bf16_sr", "mixed", "mixed_sr"])
+@pytest.mark.parametrize("storage,rounding", list(TILES),
+                         ids=["fp16", "fp16_sr", "bf16", "bf16_sr", "mixed", "mixed_sr", "theta32", "theta32_sr"])
 @pytest.mark.parametrize("nx,ny", [(1000, 301), (67, 45), (481, 8)])
 def test_16bit_tiles_agree_bitwise(D, nx, ny, storage, rounding):
     # Every compiled tile of a storage mode computes the same step (a node's

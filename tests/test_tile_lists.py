@@ -14,7 +14,7 @@ import re
 from paper_1601_04633_gb300 import tune
 
 CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1601_04633_gb300", "csrc")
-STORAGE = {"DMRT_FP32": 0, "DMRT_FP16": 1, "DMRT_BF16": 2, "DMRT_MIXED": 3}
+STORAGE = {"DMRT_FP32": 0, "DMRT_FP16": 1, "DMRT_BF16": 2, "DMRT_MIXED": 3, "DMRT_THETA32": 4}
 ROUNDING = {"DMRT_ROUND_NEAREST": 0, "DMRT_ROUND_STOCHASTIC": 1}
 ENTRY = re.compile(r"\{(DMRT_\w+), (DMRT_ROUND_\w+), (\d+), (\d+), (\d+), ([01]), \(const void\*\)(\w+)<(.*)>\}")
 
@@ -50,7 +50,7 @@ def test_single_tuner_tiles_are_compiled_and_complete():
     single, _ = _tables()
     lists = {(0, 0): tune.SINGLE_TILES_FP32, (1, 0): tune.SINGLE_TILES_16, (1, 1): tune.SINGLE_TILES_16_SR,
              (2, 0): tune.SINGLE_TILES_16, (2, 1): tune.SINGLE_TILES_16_SR, (3, 0): tune.SINGLE_TILES_MIXED,
-             (3, 1): tune.SINGLE_TILES_MIXED_SR}
+             (3, 1): tune.SINGLE_TILES_MIXED_SR, (4, 0): tune.SINGLE_TILES_THETA, (4, 1): tune.SINGLE_TILES_THETA_SR}
     for (st, rd), tiles in lists.items():
         listed = {(st, rd) + tuple(t) for t in tiles}
         compiled = {k for k in single if k[:2] == (st, rd)}
@@ -94,13 +94,14 @@ def test_default_tiles_are_compiled():
     # The library's defaults (storage, rounding -> tile) and the small-grid
     # tiles it switches to: float32 (1,4,2), one-row (1,1,2) and (2,1,3);
     # 16-bit nearest (2,4,2) and stochastic (4,4,2), 2-row (2,2,2) / (4,2,2),
-    # one-row (1,1,2); mixed (2,1,2).
+    # one-row (1,1,2); mixed and THETA32 (2,1,2), one-row (1,1,2).
     single, batch = _tables()
     want = [(0, 0, 1, 4, 2), (0, 0, 1, 1, 2), (0, 0, 2, 1, 3)]
     for st in (1, 2):
         want += [(st, 0, 2, 4, 2), (st, 0, 2, 2, 2), (st, 0, 1, 1, 2),
                  (st, 1, 4, 4, 2), (st, 1, 4, 2, 2), (st, 1, 1, 1, 2)]
     want += [(3, 0, 2, 1, 2), (3, 1, 2, 1, 2)]
+    want += [(4, 0, 2, 1, 2), (4, 1, 2, 1, 2), (4, 0, 1, 1, 2), (4, 1, 1, 1, 2)]
     for k in want:
         assert k in single, k
     for k in [(0, 0, 2, 2, 2), (3, 0, 4, 2, 2), (3, 1, 4, 2, 2)]:
