@@ -42,7 +42,7 @@ BYTES_PER_NODE = {"fp32": 112, "fp16": 56, "bf16": 56, "fp16_sr": 56, "bf16_sr":
                   "mixed_sr": 76, "theta32": 60, "theta32_sr": 60}
 # Tiles (nodes per thread, rows, stages) of the secondary storage runs.
 SECONDARY_TILES = {"fp16": (2, 4, 2), "bf16": (2, 4, 2), "fp16_sr": (4, 4, 2), "bf16_sr": (4, 4, 2),
-                   "mixed": (2, 1, 2), "mixed_sr": (2, 1, 2), "theta32": (2, 1, 2), "theta32_sr": (2, 1, 2)}
+                   "mixed": (2, 1, 2), "mixed_sr": (2, 1, 2), "theta32": (2, 1, 2), "theta32_sr": (4, 2, 2)}
 FALLBACK_HBM_GBS = 6800.0
 GATE_STEPS = 20000  # the stated length of the 4096^2 workload; the Nu gate is taken over it
 NU_GATE = 1e-3

@@ -111,9 +111,9 @@ extern "C" {
  * (1, 1, 2); 4-row items fewer than 4 per SM, 2-row items. MIXED storage (default (2, 1, 2)), nearest:
  * (1,1,2) (1,1,3) (1,1,4) (1,2,2) (1,2,3) (1,4,2) (2,1,2) (2,1,3) (2,1,4)
  * (2,2,2) (4,1,3) (4,1,4); stochastic: (1,1,2) (1,2,2) (1,4,2) (1,4,3) (2,1,2)
- * (2,1,3) (2,2,2) (2,4,2) (4,1,3). THETA32 storage (default (2, 1, 2)),
- * nearest: (1,1,2) (2,1,2) (2,1,3) (2,2,2) (4,1,3); stochastic: (1,1,2) (1,2,2)
- * (2,1,2) (2,1,3) (2,2,2) (2,4,2) (4,1,3) (4,2,2). */
+ * (2,1,3) (2,2,2) (2,4,2) (4,1,3). THETA32 storage, nearest (default
+ * (2, 1, 2)): (1,1,2) (2,1,2) (2,1,3) (2,2,2) (4,1,3); stochastic (default
+ * (4, 2, 2)): (1,1,2) (1,2,2) (2,1,2) (2,1,3) (2,2,2) (2,4,2) (4,1,3) (4,2,2). */
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2

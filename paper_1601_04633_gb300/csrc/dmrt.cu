@@ -521,7 +521,9 @@ size_t plane_elem_bytes(const dmrt_params& p, int k) { return plane_storage(p, k
 // Default TMA tile (nodes per thread, rows, stages) per storage mode, the
 // fastest measured on the 4096^2 cavity.
 void default_tile(int storage, int rounding, int* npt, int* R, int* S) {
-    if (storage == DMRT_MIXED || storage == DMRT_THETA32) {
+    if (storage == DMRT_THETA32 && rounding == DMRT_ROUND_STOCHASTIC) {
+        *npt = 4, *R = 2, *S = 2;  // 80.0k against 78.1k MLUPS for (2, 1, 2) on 4096^2
+    } else if (storage == DMRT_MIXED || storage == DMRT_THETA32) {
         *npt = 2, *R = 1, *S = 2;
     } else if (storage == DMRT_FP16 || storage == DMRT_BF16) {
         if (rounding == DMRT_ROUND_STOCHASTIC) *npt = 4, *R = 4, *S = 2;

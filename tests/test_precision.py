@@ -10,7 +10,9 @@ in the last place (nearest) or one unit (stochastic), u = 2^-11 (float16) or
 Long runs are compared with the oracle step by step. Plain 16-bit storage
 misses the 1e-3 Nusselt target (increments below half an ulp are lost, and the
 temperature noise of 16-bit thermal populations remains with stochastic
-rounding): those cases are strict expected failures. The mixed layout meets it.
+rounding): those cases are strict expected failures. The mixed layout meets it,
+and so does THETA32 (float32 theta, float16 deviations of the moving thermal
+populations; tests/test_theta32.py checks its single step).
 """
 import numpy as np
 import pytest
@@ -101,9 +103,10 @@ def test_one_step_matches_oracle_within_rounding(D, storage, walls, nx, ny, roun
 # history, max_t |Nu(t) - Nu_oracle(t)| / |Nu_oracle(t)| <= 1e-3. The field
 # errors are held to about twice their measured values (GB300; max |a - b| /
 # max |b| of theta: float32 1.9e-7, float16 4.4e-2, bfloat16 0.31, float16 SR
-# 8.7e-4, bfloat16 SR 8.8e-3, mixed 1.6e-5, mixed SR 2.7e-5).
+# 8.7e-4, bfloat16 SR 8.8e-3, mixed 1.6e-5, mixed SR 2.7e-5, THETA32 2.3e-5,
+# THETA32 SR 2.8e-5).
 LONG_RUN_THETA_BOUND = {(0, 0): 1e-5, (1, 0): 0.09, (2, 0): 0.6, (1, 1): 2e-3, (2, 1): 2e-2, (3, 0): 5e-5,
-                        (3, 1): 6e-5}
+                        (3, 1): 6e-5, (4, 0): 5e-5, (4, 1): 6e-5}
 _long_runs = {}
 
 
@@ -131,7 +134,8 @@ def _long_run(D, storage, rounding):
 
 
 @pytest.mark.parametrize("storage,rounding", list(LONG_RUN_THETA_BOUND),
-                         ids=["fp32", "fp16", "bf16", "fp16_sr", "bf16_sr", "mixed", "mixed_sr"])
+                         ids=["fp32", "fp16", "bf16", "fp16_sr", "bf16_sr", "mixed", "mixed_sr", "theta32",
+                              "theta32_sr"])
 def test_long_run_field_error_bounds(D, storage, rounding):
     nu_pw, th_err = _long_run(D, storage, rounding)
     assert np.isfinite(nu_pw) and th_err <= LONG_RUN_THETA_BOUND[(storage, rounding)]
@@ -147,6 +151,8 @@ def _gate_fails(reason):
     pytest.param(0, 0, id="fp32"),
     pytest.param(3, 0, id="mixed"),
     pytest.param(3, 1, id="mixed_sr"),
+    pytest.param(4, 0, id="theta32"),
+    pytest.param(4, 1, id="theta32_sr"),
     pytest.param(1, 0, id="fp16", marks=_gate_fails("float16 nearest loses sub-half-ulp thermal increments")),
     pytest.param(2, 0, id="bf16", marks=_gate_fails("bfloat16 nearest: 8-bit mantissa, far off")),
     pytest.param(1, 1, id="fp16_sr", marks=_gate_fails("float16 SR: temperature noise, ~0.7 % on Nu")),

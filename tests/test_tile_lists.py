@@ -94,14 +94,14 @@ def test_default_tiles_are_compiled():
     # The library's defaults (storage, rounding -> tile) and the small-grid
     # tiles it switches to: float32 (1,4,2), one-row (1,1,2) and (2,1,3);
     # 16-bit nearest (2,4,2) and stochastic (4,4,2), 2-row (2,2,2) / (4,2,2),
-    # one-row (1,1,2); mixed and THETA32 (2,1,2), one-row (1,1,2).
+    # one-row (1,1,2); mixed (2,1,2); THETA32 nearest (2,1,2), stochastic (4,2,2).
     single, batch = _tables()
     want = [(0, 0, 1, 4, 2), (0, 0, 1, 1, 2), (0, 0, 2, 1, 3)]
     for st in (1, 2):
         want += [(st, 0, 2, 4, 2), (st, 0, 2, 2, 2), (st, 0, 1, 1, 2),
                  (st, 1, 4, 4, 2), (st, 1, 4, 2, 2), (st, 1, 1, 1, 2)]
     want += [(3, 0, 2, 1, 2), (3, 1, 2, 1, 2)]
-    want += [(4, 0, 2, 1, 2), (4, 1, 2, 1, 2), (4, 0, 1, 1, 2), (4, 1, 1, 1, 2)]
+    want += [(4, 0, 2, 1, 2), (4, 1, 4, 2, 2), (4, 0, 1, 1, 2), (4, 1, 1, 1, 2)]
     for k in want:
         assert k in single, k
     for k in [(0, 0, 2, 2, 2), (3, 0, 4, 2, 2), (3, 1, 4, 2, 2)]:
