@@ -502,6 +502,12 @@ typedef struct {
                               (per-cavity store maps; one launch per step only).
                               Compiled: FP32 (2,1,2) (2,2,2); MIXED, both roundings,
                               (2,2,2) (4,2,2) (4,4,2). The same bits either way. */
+    int32_t strip_fill;    /* 0: each cavity in the widest strips the stage allows
+                              (fewest halo columns); 1: in the strip width that keeps
+                              the most of the block's threads busy (an item's rows
+                              times threads per row against the block, times the
+                              valid share of the strips' nodes). The same bits
+                              either way. */
 } dmrt_batch_opts;
 
 /* Device workspace for a batch of n cavities (the members' workspaces plus the

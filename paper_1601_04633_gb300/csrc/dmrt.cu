@@ -2285,20 +2285,18 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
     const int block = R * (256 / npt);
     const int quantum = 32 * npt;                       // strip widths keep warps in one row
     const int w_max = (dmrt::kTmaBox - 2 * halo) / quantum * quantum;
-    const int stage_bytes = (int)dmrt::tma_stage_bytes_fg(R, fb, gb);  // the compiled stage
+    const int stage_bytes = (int)dmrt::batch_stage_bytes(R, fb, gb);  // the compiled stage
+    const bool fill = opts && opts->strip_fill > 0;
     for (int i = 0; i < n; ++i) {
         dmrt_ctx* c = b->sub[i];
         std::memset(&cav[i], 0, sizeof cav[i]);
         cav[i].args[0] = step_args(c, 0);
         cav[i].args[1] = step_args(c, 1);
         cav[i].K = c->sc;
-        const int ns = (c->p.nx + w_max - 1) / w_max;
-        const int W = ((c->p.nx + ns - 1) / ns + quantum - 1) / quantum * quantum;
-        const int WB = W + 2 * halo;
-        const int tpr = W / npt;
-        // Stage placement for RC rows: each plane group starts on a 128-byte
-        // boundary (a tensor copy's destination must); 0 when it does not fit.
+        // Stage placement for RC rows of WB elements: each plane group starts on
+        // a 128-byte boundary (a tensor copy's destination must).
         auto r128 = [](long long bytes) { return (bytes + 127) / 128 * 128; };
+        int WB = 0;
         auto place = [&](int rc, dmrt::StageOffsets& so) -> long long {
             const long long row = (long long)rc * WB;
             if (!split) {
@@ -2311,10 +2309,39 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
             so = {(int)(zP / 2), (int)(zN / 2), (int)g0, (int)(gP / 4), (int)(gN / 4)};
             return g0 + gN + row * 4;
         };
-        // Rows per item: as many as the block's threads and the stage allow.
-        int RC = std::max(1, block / tpr);
+        // Rows per item of a strip W nodes wide: as many as the block's threads
+        // and the stage allow.
         dmrt::StageOffsets so;
-        while (RC > 1 && place(RC, so) > stage_bytes) --RC;
+        auto rows_for = [&](int w) {
+            WB = w + 2 * halo;
+            int rc = std::max(1, block / (w / npt));
+            while (rc > 1 && place(rc, so) > stage_bytes) --rc;
+            return rc;
+        };
+        // Strip width. Default: the widest strips (fewest halo columns), the
+        // cavity's width split evenly. strip_fill: the width, among multiples of
+        // the quantum, whose items keep the most of the block's threads busy
+        // (rows x threads per row against the block, times the valid share of
+        // the strips' nodes); ties go to the wider strip.
+        int W;
+        if (fill) {
+            W = quantum;
+            double best = -1.0;
+            for (int w = quantum; w <= w_max; w += quantum) {
+                const int rc = rows_for(w);
+                const long long ns_w = (c->p.nx + w - 1) / w;
+                const double use = (double)rc * (w / npt) / block * c->p.nx / ((double)ns_w * w);
+                if (use > best + 1e-12 || (use > best - 1e-12 && w > W)) {
+                    best = use;
+                    W = w;
+                }
+            }
+        } else {
+            const int ns = (c->p.nx + w_max - 1) / w_max;
+            W = ((c->p.nx + ns - 1) / ns + quantum - 1) / quantum * quantum;
+        }
+        const int tpr = W / npt;
+        int RC = rows_for(W);
         if (place(RC, so) > stage_bytes) {
             std::snprintf(b->err, sizeof b->err, "cavity %d: strip of %d nodes does not fit the stage", i, W);
             return fail(DMRT_E_ARG);
@@ -2327,6 +2354,7 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         cav[i].WB = WB;
         cav[i].RC = RC;
         cav[i].tpr = tpr;
+        cav[i].tpr_magic = (unsigned)((0x100000000ull + (unsigned)tpr - 1) / (unsigned)tpr);
         cav[i].stage_bytes = (unsigned)((size_t)RC * WB * (9 * fb + 5 * gb));
         items += (long long)cav[i].n_strips * cav[i].n_rowblocks;
         for (int bf = 0; bf < 2; ++bf) {

@@ -22,25 +22,49 @@ namespace dmrt {
 constexpr int kBatchMaps = 5;
 constexpr int kBatchStoreMap = 3;
 
-// Shared memory of a batched block: S stages, with TS two output tiles (each
-// the size of a stage, which bounds every cavity's tile), and S mbarriers.
+// Shared memory of a batched block: S stages, with TS two output tiles, and S
+// mbarriers. A stage holds 5/4 of R rows of 256 elements per plane, so that
+// strips whose threads per row divide the block keep every thread busy: a
+// block of R 256 / NPT threads computes R 256 / W rows of a W-node strip, and
+// those rows with their halo columns (W + 2 HALO elements each) take
+// R 256 (1 + 2 HALO / W) elements, at most 5/4 of R 256 for W >= 8 HALO. An
+// output tile holds an item's results without halos (at most R 256 nodes of
+// every plane, the split layout's thermal block 128-byte aligned).
+__host__ __device__ constexpr size_t batch_stage_bytes(int R, int f_bytes, int g_bytes) {
+    return round128(tma_stage_bytes_fg(R, f_bytes, g_bytes) * 5 / 4);
+}
 __host__ __device__ constexpr size_t batch_out_bytes(int R, int f_bytes, int g_bytes) {
     return round128(tma_stage_bytes_fg(R, f_bytes, g_bytes) + 128);
 }
 __host__ __device__ constexpr size_t batch_smem_bytes(bool ts, int R, int S, int f_bytes, int g_bytes) {
-    return (size_t)S * tma_stage_bytes_fg(R, f_bytes, g_bytes) + (ts ? 2 * batch_out_bytes(R, f_bytes, g_bytes) : 0) +
+    return (size_t)S * batch_stage_bytes(R, f_bytes, g_bytes) + (ts ? 2 * batch_out_bytes(R, f_bytes, g_bytes) : 0) +
            (size_t)S * 8;
 }
-struct BatchCavity {
+// A cavity's record, 16-byte aligned and sized so that the single-step kernel
+// copies it into shared memory with the item's stage (one bulk copy), and the
+// consumers read its arguments and constants there.
+struct alignas(16) BatchCavity {
     StepArgs args[2];  // by source buffer: args[b] reads buffer b, writes 1 - b
     StepConsts K;
     int n_strips, n_rowblocks;
     int item_base;     // index of the cavity's first item in the batch list
     int W, WB, RC;     // strip width, box width, rows per item
     int tpr;           // threads per row = W / NPT
+    unsigned tpr_magic;  // ceil(2^32 / tpr): tid / tpr = umulhi(tid, tpr_magic), exact for tid < 2^32 / tpr
     StageOffsets so;   // plane groups in the stage
     unsigned stage_bytes;  // bytes the item's tensor copies bring
 };
+static_assert(sizeof(BatchCavity) % 16 == 0, "bulk copies move multiples of 16 bytes");
+
+// Bulk copy (not tensor-shaped) of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) from global to shared memory, completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 
 // Work distribution: block b first takes the static items [b Q, (b + 1) Q)
 // (contiguous, so mostly one cavity), then draws single items from the
@@ -67,13 +91,14 @@ __global__ void __launch_bounds__(R * (256 / NPT))
                           int parity, unsigned* batch_err, unsigned* ctr) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
-    constexpr size_t kStageBytes = tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));  // a multiple of 128
+    constexpr size_t kStageBytes = batch_stage_bytes(R, sizeof(Ef), sizeof(Eg));  // a multiple of 128
     constexpr size_t kOutBytes = batch_out_bytes(R, sizeof(Ef), sizeof(Eg));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* stages = smem_raw;
     unsigned char* outs = smem_raw + (size_t)S * kStageBytes;
     uint64_t* bars = reinterpret_cast<uint64_t*>(outs + (TS ? 2 * kOutBytes : 0));
     __shared__ int4 stage_item[S];  // (cavity, strip, row block, item) of each stage; cavity -1: no more items
+    __shared__ BatchCavity stage_cav[S];  // the record of each stage's cavity (copied with the stage)
     constexpr int HALO = L::kHalo;
     const int tid = threadIdx.x;
 
@@ -131,7 +156,8 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         const int j0 = rb * bc.RC;
         const CUtensorMap* m = maps + ((size_t)pc * 2 + parity) * kBatchMaps;
         unsigned char* st = stages + (size_t)s * kStageBytes;
-        mbar_expect_tx(&bars[s], bc.stage_bytes);
+        mbar_expect_tx(&bars[s], bc.stage_bytes + (uint32_t)sizeof(BatchCavity));
+        bulk_load(&stage_cav[s], &bc, (uint32_t)sizeof(BatchCavity), &bars[s]);
         if constexpr (!L::kSplit) {
             Ef* e = reinterpret_cast<Ef*>(st);
             tma_load_3d(e, m, x, j0, kGroupZ, &bars[s]);
@@ -172,10 +198,12 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         // read a stale one, and the barrier below then ends the block anyway.
         const int4 w = stage_item[s];
         const bool work = ok && w.x >= 0 && DMRT_IN(w.x, 0, n_cav, batch_err);
-        const BatchCavity& bc = cav[work ? w.x : 0];
-        const int tpr = bc.tpr;
-        const int rg = tid / tpr;
-        const int t = tid - rg * tpr;
+        // The cavity's record, copied into shared memory with the stage (a stage
+        // without an item holds a stale record: only its geometry is read, and
+        // the item routine then touches no memory).
+        const BatchCavity& bc = stage_cav[s];
+        const int rg = work ? (int)__umulhi((unsigned)tid, bc.tpr_magic) : 0;
+        const int t = work ? tid - rg * bc.tpr : tid;
         // Stochastic rounding: the cavity's per-step salt, as its own context would
         // use (its step count was written by the previous launch: read-only here).
         unsigned salt = 0;
@@ -287,7 +315,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
                                 int parity, unsigned* batch_err, unsigned* sync, int lp) {
     using Ef = typename L::Ef;
     using Eg = typename L::Eg;
-    constexpr size_t kStageBytes = tma_stage_bytes_fg(R, sizeof(Ef), sizeof(Eg));
+    constexpr size_t kStageBytes = batch_stage_bytes(R, sizeof(Ef), sizeof(Eg));
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* stages = smem_raw;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * kStageBytes);

@@ -93,7 +93,7 @@ class BatchOpts(ctypes.Structure):
     _fields_ = [("tma_npt", ctypes.c_int32), ("tma_rows", ctypes.c_int32),
                 ("tma_stages", ctypes.c_int32), ("graph_steps", ctypes.c_int32),
                 ("group_bytes", ctypes.c_int64), ("steps_per_launch", ctypes.c_int32),
-                ("tensor_store", ctypes.c_int32)]
+                ("tensor_store", ctypes.c_int32), ("strip_fill", ctypes.c_int32)]
 
 
 _lib = None
@@ -609,7 +609,8 @@ class Batch:
         o = None
         if opts is not None:
             o = BatchOpts(*[int(opts.get(k, 0)) for k in ("tma_npt", "tma_rows", "tma_stages", "graph_steps",
-                                                          "group_bytes", "steps_per_launch", "tensor_store")])
+                                                          "group_bytes", "steps_per_launch", "tensor_store",
+                                                          "strip_fill")])
         b = _VP()
         _check_batch(load().dmrt_batch_create(arr, n, th_ptrs, ctypes.byref(o) if o else None,
                                               _VP(self.workspace.data_ptr()), nbytes.value,

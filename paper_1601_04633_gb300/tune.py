@@ -90,26 +90,27 @@ BATCH_TS_TILES = {0: [(2, 1, 2), (2, 2, 2)], 3: [(2, 2, 2), (4, 2, 2), (4, 4, 2)
 
 
 def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), cache=None, storage=0, rounding=0,
-               group_bytes=(0,), steps_per_launch=(1,), tensor_store=False, finalists=3):
-    """Pick the batched kernel's tile, cavity-group size and steps per launch
-    for these cavities (storage 0: float32, 3: mixed). Every tile is timed with
-    the first group size and one step per launch; the `finalists` fastest tiles
-    are then timed with each other combination (steps per launch > 1 only for
-    the tiles the multi-step kernel is compiled for). Returns {"opts": {...},
-    "mlups": best, "trials": [...]}."""
+               group_bytes=(0,), steps_per_launch=(1,), tensor_store=False, finalists=3, strip_fill=(0, 1)):
+    """Pick the batched kernel's tile, strip policy, cavity-group size and steps
+    per launch for these cavities (storage 0: float32, 3: mixed). Every tile is
+    timed with each strip policy, the first group size and one step per launch;
+    the `finalists` fastest are then timed with each other combination (steps
+    per launch > 1 only for the tiles the multi-step kernel is compiled for).
+    Returns {"opts": {...}, "mlups": best, "trials": [...]}."""
     from . import dmrt as D
 
     key = _key("batch", [(c.nx, c.ny) for c in cavities],
-               f"{steps}-{storage}-{rounding}-{list(group_bytes)}-{list(steps_per_launch)}-{tensor_store}")
+               f"{steps}-{storage}-{rounding}-{list(group_bytes)}-{list(steps_per_launch)}-{tensor_store}-"
+               f"{list(strip_fill)}")
     hit = _cache_get(cache, key)
     if hit:
         return hit
     nodes = sum(c.nx * c.ny for c in cavities)
     trials = []
 
-    def trial(npt, R, S, g, gb, K, ts=0):
+    def trial(npt, R, S, g, gb, K, ts=0, fill=0):
         opts = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=g, group_bytes=gb, steps_per_launch=K,
-                    tensor_store=ts)
+                    tensor_store=ts, strip_fill=fill)
         glen = 2 * K if K > 1 else g
         # The warm-up covers one whole graph, so its instantiation is not timed.
         b = D.Batch.from_inputs(cavities, opts=opts, nu_capacity=steps + warmup + glen + 8, storage=storage,
@@ -121,7 +122,8 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
 
     for npt, R, S in (tiles or BATCH_TILES):
         for g in graph_steps:
-            trial(npt, R, S, g, group_bytes[0], 1)
+            for fill in strip_fill:
+                trial(npt, R, S, g, group_bytes[0], 1, fill=fill)
     if len(group_bytes) > 1 or len(steps_per_launch) > 1 or tensor_store:
         top = sorted(trials, key=lambda r: -r["mlups"])[:finalists]
         for t in top:
@@ -133,10 +135,10 @@ def tune_batch(cavities, steps=200, warmup=20, tiles=None, graph_steps=(64,), ca
                 for gb in group_bytes:
                     if (gb, K) == (group_bytes[0], 1):
                         continue
-                    trial(*tile, o["graph_steps"], gb, K)
+                    trial(*tile, o["graph_steps"], gb, K, fill=o["strip_fill"])
             if tensor_store and tile in BATCH_TS_TILES.get(storage, []):
                 for gb in group_bytes:
-                    trial(*tile, o["graph_steps"], gb, 1, 1)
+                    trial(*tile, o["graph_steps"], gb, 1, 1, fill=o["strip_fill"])
     best = max(trials, key=lambda r: r["mlups"])
     out = {"opts": best["opts"], "mlups": best["mlups"], "trials": trials}
     _cache_put(cache, key, out)
@@ -189,6 +191,8 @@ def main():
     ap.add_argument("--steps-per-launch", type=int, nargs="*", default=[1],
                     help="steps per launch to try (batched sweep; 1: one launch per step)")
     ap.add_argument("--tensor-store", action="store_true", help="also try the tensor-store epilogue (batched sweep)")
+    ap.add_argument("--strip-fill", type=int, nargs="*", default=[0, 1],
+                    help="strip policies to try (batched sweep; 0 widest strips, 1 fullest blocks)")
     ap.add_argument("--cache", default=None)
     args = ap.parse_args()
     tiles = [tuple(args.tile)] if args.tile else None
@@ -196,7 +200,8 @@ def main():
         print(json.dumps(tune_batch(inputs.batch_sweep(), steps=args.steps, tiles=tiles,
                                     graph_steps=(args.graph_steps,), cache=args.cache, storage=args.storage,
                                     rounding=args.rounding, group_bytes=[m << 20 for m in args.group_mb],
-                                    steps_per_launch=args.steps_per_launch, tensor_store=args.tensor_store),
+                                    steps_per_launch=args.steps_per_launch, tensor_store=args.tensor_store,
+                                    strip_fill=args.strip_fill),
                          indent=1))
     if args.single:
         cav = inputs.Cavity(args.single, args.single, 1e7, 0.001, seed=5)

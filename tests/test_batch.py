@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from paper_1601_04633_gb300 import inputs
+from paper_1601_04633_gb300 import inputs, tune
 
 pytestmark = pytest.mark.gpu
 
@@ -149,6 +149,35 @@ def test_tensor_store_epilogue_gives_the_same_bits(D, storage, rounding):
         ref.close()
 
 
+@pytest.mark.parametrize("storage,rounding", [(0, 0), (3, 1)], ids=["fp32", "mixed_sr"])
+def test_strip_policy_gives_the_same_bits(D, storage, rounding):
+    # Strips chosen to fill the blocks (narrower strips, more rows per item)
+    # give exactly the widest strips' results, with register and tensor stores
+    # and several steps per launch.
+    cavs = _uneven() + [inputs.Cavity(192, 96, 1e5, 0.01, noise_amp=1e-3, seed=140),
+                        inputs.Cavity(384, 40, 1e5, 0.005, noise_amp=1e-3, seed=141)]
+    tiles = [(2, 2, 2), (4, 2, 2)] if storage else [(2, 2, 2), (1, 4, 2)]
+    for npt, R, S in tiles:
+        base = dict(tma_npt=npt, tma_rows=R, tma_stages=S, graph_steps=16)
+        ref = D.Batch.from_inputs(cavs, opts=base, nu_capacity=64, storage=storage, rounding=rounding)
+        variants = [dict(base, strip_fill=1)]
+        if (npt, R, S) in tune.BATCH_MSTEP_TILES[storage]:
+            variants.append(dict(base, strip_fill=1, steps_per_launch=4))
+        if (npt, R, S) in TS_TILES[storage]:
+            variants.append(dict(base, strip_fill=1, tensor_store=1))
+        runs = [D.Batch.from_inputs(cavs, opts=o, nu_capacity=64, storage=storage, rounding=rounding)
+                for o in variants]
+        for b in [ref] + runs:
+            b.step(36)
+            b.check()
+        for b in runs:
+            for i in range(len(cavs)):
+                assert np.array_equal(b.members[i].get_state(), ref.members[i].get_state()), (npt, R, S, i)
+                assert np.array_equal(b.members[i].nusselt(36)[2], ref.members[i].nusselt(36)[2]), (npt, R, S, i)
+            b.close()
+        ref.close()
+
+
 def test_multistep_sweep_member_matches_single_context(D):
     # The 64-cavity sweep, 8 steps per launch: sampled members against their own
     # contexts stepped alone.
@@ -214,7 +243,9 @@ def test_autotuner_picks_a_compiled_tile(D):
 
     cavs = _uneven()[:4]
     r = tune.tune_batch(cavs, steps=20, warmup=4, tiles=[(1, 4, 2), (2, 2, 2)])
-    assert r["opts"]["tma_npt"] in (1, 2) and len(r["trials"]) == 2
+    # Each tile with each strip policy.
+    assert r["opts"]["tma_npt"] in (1, 2) and len(r["trials"]) == 4
+    assert {t["opts"]["strip_fill"] for t in r["trials"]} == {0, 1}
     assert all(t["mlups"] > 0 for t in r["trials"])
 
 
