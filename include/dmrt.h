@@ -99,7 +99,10 @@ extern "C" {
  * through a multi-stage mbarrier pipeline. AUTO picks TMA for grids wider
  * than 496 nodes and for float32 grids whose one-row items (248-node strips x
  * rows) number at most 4 per SM, with tile (1, 1, 2) up to 2 per SM and (2, 1,
- * 3) beyond (e.g. 64^2 to 256^2), DIRECT otherwise (e.g. 384^2). TMA tiles
+ * 3) beyond (e.g. 112^2 to 256^2), DIRECT otherwise (e.g. 384^2); for runs of
+ * steps of a float32 cavity whose rows split over 16 blocks give at most 640
+ * nodes per block (e.g. up to 96^2), and no tile asked for, the CLUSTER kernel
+ * below where the GPU fits it (64^2: 2.07 against 2.66 us per step). TMA tiles
  * compiled in, as (nodes per
  * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
  * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)
@@ -117,12 +120,12 @@ extern "C" {
 #define DMRT_KERNEL_AUTO 0
 #define DMRT_KERNEL_DIRECT 1
 #define DMRT_KERNEL_TMA 2
-/* CLUSTER: for small float32 cavities (both buffers in the shared memory of one
- * thread-block cluster of up to 16 blocks, e.g. up to 128^2): each dmrt_step
- * call runs as one launch that keeps the state on chip between steps (one
- * cluster barrier per step); single steps and the adjoint use the kernel AUTO
- * picks among the others. The same bits as the other kernels. DMRT_E_ARG at
- * creation if the cavity does not fit. */
+/* CLUSTER: for small float32 cavities (both buffers, with one halo row per
+ * block, in the shared memory of one thread-block cluster of up to 16 blocks,
+ * e.g. up to 160^2): each dmrt_step call runs as one launch that keeps the
+ * state on chip between steps (one cluster barrier per step); single steps and
+ * the adjoint use the kernel AUTO picks among the others. The same bits as the
+ * other kernels. DMRT_E_ARG at creation if the cavity does not fit. */
 #define DMRT_KERNEL_CLUSTER 3
 
 /* Wall kinds for the left and right (vertical) walls. Top and bottom are

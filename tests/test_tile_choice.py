@@ -2,9 +2,11 @@
 dmrt_choose_launch, the function dmrt_create itself calls).
 
 The rules are measured choices on a 152-SM GB300: float32 cavities wider than
-496 nodes take the TMA kernel with (1, 4, 2); smaller float32 grids take
-one-row TMA items while those number at most four per SM ((1, 1, 2) up to two
-per SM, (2, 1, 3) beyond), else the direct kernel; 16-bit storage takes
+496 nodes take the TMA kernel with (1, 4, 2); float32 cavities whose rows split
+over 16 blocks give at most 640 nodes per block (up to 96^2) take the cluster
+kernel for runs of steps; other small float32 grids take one-row TMA items
+while those number at most four per SM ((1, 1, 2) up to two per SM, (2, 1, 3)
+beyond), else the direct kernel; 16-bit storage takes
 (2, 4, 2) / (4, 4, 2) by rounding, 2-row items while 4-row items would number
 fewer than four per SM, one-row items while those number at most two per SM;
 mixed storage takes (2, 1, 2). Every chosen tile must be compiled in.
@@ -16,7 +18,7 @@ from paper_1601_04633_gb300 import inputs
 from test_tile_lists import _tables
 
 SMS = 152
-DIRECT, TMA = 1, 2
+DIRECT, TMA, CLUSTER = 1, 2, 3
 
 
 @pytest.fixture(scope="module")
@@ -41,7 +43,8 @@ def choose(D, nx, ny, storage=0, rounding=0, sms=SMS, **kw):
 
 @pytest.mark.parametrize("n,expect", [
     (4096, (TMA, 1, 4, 2)), (2048, (TMA, 1, 4, 2)), (1000, (TMA, 1, 4, 2)),
-    (16, (TMA, 1, 1, 2)), (64, (TMA, 1, 1, 2)), (128, (TMA, 1, 1, 2)), (192, (TMA, 1, 1, 2)),
+    (16, (CLUSTER, 0, 0, 0)), (64, (CLUSTER, 0, 0, 0)), (96, (CLUSTER, 0, 0, 0)),
+    (112, (TMA, 1, 1, 2)), (128, (TMA, 1, 1, 2)), (192, (TMA, 1, 1, 2)),
     (256, (TMA, 2, 1, 3)), (304, (TMA, 2, 1, 3)), (384, (DIRECT, 0, 0, 0)), (496, (DIRECT, 0, 0, 0)),
 ])
 def test_float32_square_cavities(D, n, expect):
@@ -98,6 +101,15 @@ def test_every_chosen_tile_is_compiled(D, storage, rounding):
             assert (storage, rounding, npt, R, S) in single, (nx, ny, storage, rounding, (npt, R, S))
         else:
             assert storage == 0 and (npt, R, S) == (0, 0, 0)
+
+
+def test_auto_takes_the_cluster_kernel_for_small_float32_cavities(D):
+    # At most 640 nodes per block of a 16-block cluster, float32, no tile asked for.
+    assert choose(D, 200, 16) == (CLUSTER, 0, 0, 0)      # 1 row of 200 per block
+    assert choose(D, 100, 70) == (CLUSTER, 0, 0, 0)      # 5 rows of 100
+    assert choose(D, 130, 80) != (CLUSTER, 0, 0, 0)      # 5 rows of 130 = 650
+    assert choose(D, 64, 64, 3, 1) == (TMA, 2, 1, 2)     # mixed storage keeps the TMA kernel
+    assert choose(D, 64, 64, tma_npt=1, tma_rows=1, tma_stages=2)[0] != CLUSTER  # a tile asked for
 
 
 def test_cluster_kernel_choice_by_size():
