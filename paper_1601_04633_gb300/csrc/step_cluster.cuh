@@ -272,8 +272,12 @@ static __global__ void __launch_bounds__(1024) step_cluster_kernel(const __grid_
             if (lane == 0) means[s % kClusterNuChunk] = sum / A0.nu_div;
             __syncwarp();
             if (s % kClusterNuChunk == kClusterNuChunk - 1 || s == C.steps - 1) {
+                // Only the chunk's last `cap` means reach the ring, so that no
+                // two lanes write one slot (a smaller ring wraps within a chunk).
                 const int first = s - s % kClusterNuChunk;
-                for (int q = lane; q <= s - first; q += 32) A0.nu_ring[(t0 + first + q) % A0.cap] = means[q];
+                const long long n = s - first + 1;
+                const int q0 = (int)(n > A0.cap ? n - A0.cap : 0);
+                for (int q = q0 + lane; q <= s - first; q += 32) A0.nu_ring[(t0 + first + q) % A0.cap] = means[q];
                 if (lane == 0) *A0.nu_last = means[s - first];
             }
         }

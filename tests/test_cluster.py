@@ -55,6 +55,23 @@ def test_cluster_kernel_bitwise_equal_to_the_others(D, nx, ny):
         assert np.array_equal(loc_c, loc) and m_c == m, kernel
 
 
+@pytest.mark.parametrize("cap", [1, 50, 1000, 3000])
+def test_cluster_kernel_ring_wraps_like_the_others(D, cap):
+    # A run longer than the ring (and than the kernel's on-chip chunk of 1024
+    # means): the ring keeps the last `cap` means, as with the TMA kernel.
+    cav = inputs.Cavity(48, 40, 1e4, 0.01, noise_amp=1e-3, seed=64)
+    out = []
+    for kernel in (D.DMRT_KERNEL_CLUSTER, D.DMRT_KERNEL_TMA):
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=cap, kernel=kernel)
+        sim.step(2500)
+        sim.step(3)
+        sim.check()
+        out.append(sim.nusselt(5000)[2])
+        sim.close()
+    assert len(out[0]) == min(cap, 2503)
+    assert np.array_equal(out[0], out[1])
+
+
 def test_cluster_kernel_adiabatic_walls_conserve_energy(D):
     cav = inputs.Cavity(96, 64, 1e5, 0.01, noise_amp=0.2, seed=62)
     p = D.make_params(cav.nx, cav.ny, cav.Ra, cav.Pr, left_wall=D.DMRT_WALL_ADIABATIC,
