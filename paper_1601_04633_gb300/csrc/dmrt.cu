@@ -2313,31 +2313,9 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
         cav[i].args[0] = step_args(c, 0);
         cav[i].args[1] = step_args(c, 1);
         cav[i].K = c->sc;
-        // Stage placement for RC rows of WB elements: each plane group starts on
-        // a 128-byte boundary (a tensor copy's destination must).
-        auto r128 = [](long long bytes) { return (bytes + 127) / 128 * 128; };
-        int WB = 0;
-        auto place = [&](int rc, dmrt::StageOffsets& so) -> long long {
-            const long long row = (long long)rc * WB;
-            if (!split) {
-                const long long zP = r128(6 * row * 4), zN = r128(zP + 4 * row * 4);
-                so = {(int)(zP / 4), (int)(zN / 4), 0, 0, 0};
-                return zN + 4 * row * 4;
-            }
-            const long long zP = r128(3 * row * 2), zN = r128(zP + 3 * row * 2), g0 = r128(zN + 3 * row * 2);
-            const long long gP = r128(3 * row * 4), gN = r128(gP + row * 4);
-            so = {(int)(zP / 2), (int)(zN / 2), (int)g0, (int)(gP / 4), (int)(gN / 4)};
-            return g0 + gN + row * 4;
-        };
-        // Rows per item of a strip W nodes wide: as many as the block's threads
-        // and the stage allow.
-        dmrt::StageOffsets so;
-        auto rows_for = [&](int w) {
-            WB = w + 2 * halo;
-            int rc = std::max(1, block / (w / npt));
-            while (rc > 1 && place(rc, so) > stage_bytes) --rc;
-            return rc;
-        };
+        // Rows per item and stage placement of a strip W nodes wide (the same
+        // function the kernel specialises its items on).
+        auto geo = [&](int w) { return dmrt::batch_geometry(split, npt, R, w, stage_bytes); };
         // Strip width. Default: the widest strips (fewest halo columns), the
         // cavity's width split evenly. strip_fill: the width, among multiples of
         // the quantum, whose items keep the most of the block's threads busy
@@ -2348,7 +2326,7 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
             W = quantum;
             double best = -1.0;
             for (int w = quantum; w <= w_max; w += quantum) {
-                const int rc = rows_for(w);
+                const int rc = geo(w).RC;
                 const long long ns_w = (c->p.nx + w - 1) / w;
                 const double use = (double)rc * (w / npt) / block * c->p.nx / ((double)ns_w * w);
                 if (use > best + 1e-12 || (use > best - 1e-12 && w > W)) {
@@ -2361,8 +2339,12 @@ int dmrt_batch_create(const dmrt_params* arr, int32_t n, const double* const* th
             W = ((c->p.nx + ns - 1) / ns + quantum - 1) / quantum * quantum;
         }
         const int tpr = W / npt;
-        int RC = rows_for(W);
-        if (place(RC, so) > stage_bytes) {
+        const dmrt::BatchGeo G = geo(W);
+        const int RC = G.RC;
+        const int WB = W + 2 * halo;
+        dmrt::StageOffsets so = G.so;
+        dmrt::StageOffsets so_check{};
+        if (dmrt::batch_place(split, RC, WB, so_check) > stage_bytes) {
             std::snprintf(b->err, sizeof b->err, "cavity %d: strip of %d nodes does not fit the stage", i, W);
             return fail(DMRT_E_ARG);
         }

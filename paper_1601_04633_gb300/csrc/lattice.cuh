@@ -30,7 +30,9 @@ constexpr int kGroupZ = 0, kGroupP = 6, kGroupN = 10;
 // Relaxation constants pre-divided by the squared norms of the rows of the
 // transforms (D2Q9: 9,6,6,36,4,4,12,12,36; D2Q5: 5,2,2,20,4), so that
 // f* = f - sum_k M[k][i] d_k with d_k = rate_k (m_k - m_k_eq) / norm_k.
-struct StepConsts {
+// (16-byte aligned, as StepArgs: where a kernel reads them from shared memory,
+// neighbouring fields come in 16-byte loads.)
+struct alignas(16) StepConsts {
     float se36, snu4, sq12, seps36;  // D2Q9: s_e/36, s_nu/4, s_q/12, s_eps/36
     float sk2, se20, snu4t;          // D2Q5: sigma_k/2, sigma_e/20, sigma_nu/4
     float a;                         // D2Q5 equilibrium parameter (Eq. 43)
@@ -42,7 +44,7 @@ struct StepConsts {
     double nu_scale;                 // H / (3 (theta_hot - theta_cold))
 };
 
-struct StepArgs {
+struct alignas(16) StepArgs {
     const float* __restrict__ src;  // post-collision state at time t
     float* __restrict__ dst;        // post-collision state at time t + 1
     const float* __restrict__ hot;  // [ny] left-wall temperature

@@ -650,7 +650,9 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             F[5][0] = ldg_one(rowjf + L::pf(7) * PL, 0.f);
             F[8][0] = ldg_one(rowjf + L::pf(6) * PL, 0.f);
             const float add = K.left_fixed ? K.abb * __ldg(A.hot + j) : 0.f;
-            const float g3 = L::kTheta ? fmaf(K.w1, thc[0], d3o[0]) : ldg_one(rowjg + L::pg(3) * PL, sh1);
+            float g3;
+            if constexpr (L::kTheta) g3 = fmaf(K.w1, thc[0], d3o[0]);
+            else g3 = ldg_one(rowjg + L::pg(3) * PL, sh1);
             Gq[1][0] = sign_l_g * g3 + add;
         }
         // Right wall (node x = nx - 1): links with e_x = -1 (f3, f6, f7, g3).
@@ -661,14 +663,16 @@ __device__ __forceinline__ void process_item(const unsigned char* stage, const S
             const float v6 = ldg_one(rowjf + L::pf(8) * PL + xr, 0.f);
             const float v7 = ldg_one(rowjf + L::pf(5) * PL + xr, 0.f);
             const float add = K.right_fixed ? K.abb * __ldg(A.cold + j) : 0.f;
-            const float vg = L::kTheta ? 0.f : sign_r_g * ldg_one(rowjg + L::pg(1) * PL + xr, sh1) + add;
+            float vg = 0.f;
+            if constexpr (!L::kTheta) vg = sign_r_g * ldg_one(rowjg + L::pg(1) * PL + xr, sh1) + add;
 #pragma unroll
             for (int e = 0; e < NPT; ++e) {
                 if (e == re) {
                     F[3][e] = v3;
                     F[6][e] = v6;
                     F[7][e] = v7;
-                    Gq[3][e] = L::kTheta ? sign_r_g * fmaf(K.w1, thc[e], d1o[e]) + add : vg;
+                    if constexpr (L::kTheta) Gq[3][e] = sign_r_g * fmaf(K.w1, thc[e], d1o[e]) + add;
+                    else Gq[3][e] = vg;
                 }
             }
         }

@@ -40,6 +40,41 @@ __host__ __device__ constexpr size_t batch_smem_bytes(bool ts, int R, int S, int
     return (size_t)S * batch_stage_bytes(R, f_bytes, g_bytes) + (ts ? 2 * batch_out_bytes(R, f_bytes, g_bytes) : 0) +
            (size_t)S * 8;
 }
+// Geometry of a W-node strip in a batched tile (NPT nodes per thread, R rows,
+// float32 one-type or mixed split layout, stage of stage_bytes): rows per item
+// RC, as many as the block's threads and the stage allow, and the places of the
+// plane groups in the stage, each 128-byte aligned (a tensor copy's
+// destination must be). A pure function of the tile and W: the host builds
+// the cavity records with it, and the kernel specialises its items on it.
+struct BatchGeo {
+    int RC;
+    StageOffsets so;
+};
+__host__ __device__ constexpr long long batch_r128(long long bytes) { return (bytes + 127) / 128 * 128; }
+__host__ __device__ constexpr long long batch_place(bool split, int rc, int WB, StageOffsets& so) {
+    const long long row = (long long)rc * WB;
+    if (!split) {
+        const long long zP = batch_r128(6 * row * 4), zN = batch_r128(zP + 4 * row * 4);
+        so = StageOffsets{(int)(zP / 4), (int)(zN / 4), 0, 0, 0, 0};
+        return zN + 4 * row * 4;
+    }
+    const long long zP = batch_r128(3 * row * 2), zN = batch_r128(zP + 3 * row * 2), g0 = batch_r128(zN + 3 * row * 2);
+    const long long gP = batch_r128(3 * row * 4), gN = batch_r128(gP + row * 4);
+    so = StageOffsets{(int)(zP / 2), (int)(zN / 2), (int)g0, (int)(gP / 4), (int)(gN / 4), 0};
+    return g0 + gN + row * 4;
+}
+__host__ __device__ constexpr BatchGeo batch_geometry(bool split, int npt, int R, int W, long long stage_bytes) {
+    const int halo = tma_halo(split ? 2 : 4);
+    const int WB = W + 2 * halo;
+    const int block = R * (256 / npt);
+    int rc = block / (W / npt);
+    if (rc < 1) rc = 1;
+    StageOffsets so{};
+    while (rc > 1 && batch_place(split, rc, WB, so) > stage_bytes) --rc;
+    batch_place(split, rc, WB, so);
+    return BatchGeo{rc, so};
+}
+
 // A cavity's record, 16-byte aligned and sized so that the single-step kernel
 // copies it into shared memory with the item's stage (one bulk copy), and the
 // consumers read its arguments and constants there.
@@ -202,17 +237,44 @@ __global__ void __launch_bounds__(R * (256 / NPT))
         // without an item holds a stale record: only its geometry is read, and
         // the item routine then touches no memory).
         const BatchCavity& bc = stage_cav[s];
-        const int rg = work ? (int)__umulhi((unsigned)tid, bc.tpr_magic) : 0;
-        const int t = work ? tid - rg * bc.tpr : tid;
         // Stochastic rounding: the cavity's per-step salt, as its own context would
         // use (its step count was written by the previous launch: read-only here).
         unsigned salt = 0;
         if constexpr (SR)
             if (work) salt = hash32((unsigned)__ldg(bc.args[parity].step_in) * 0x9e3779b9u + 0x632be5abu);
         unsigned char* out = outs + (size_t)(k & 1) * kOutBytes;
-        process_item<L, NPT, SR, TS>(stages + (size_t)s * kStageBytes, bc.args[parity], bc.K, work ? w.y : 1, w.z,
-                                     rg, t, work, salt, bc.W, bc.WB, bc.RC, bc.so, out, (unsigned)kStageBytes,
-                                     (unsigned)kOutBytes);
+        unsigned char* st = stages + (size_t)s * kStageBytes;
+        // The item with the strip geometry known at compile time: strip widths are
+        // multiples of 32 NPT that fit a box, so 64, 128 or 192 with 2 nodes per
+        // thread and 128 with 4 (one-node tiles take the geometry at run time).
+        auto item_w = [&](auto wc) {
+            constexpr int W = decltype(wc)::value;
+            constexpr BatchGeo G = batch_geometry(L::kSplit, NPT, R, W, (long long)kStageBytes);
+            constexpr int TPR = W / NPT;
+            if (work && !DMRT_IN(bc.RC, G.RC, G.RC + 1, batch_err)) return;  // the record's RC is G.RC
+            const int rg = work ? tid / TPR : 0;
+            const int t = work ? tid - rg * TPR : tid;
+            process_item<L, NPT, SR, TS>(st, bc.args[parity], bc.K, work ? w.y : 1, w.z, rg, t, work, salt, W, W + 2 * HALO,
+                                         G.RC, G.so, out, (unsigned)kStageBytes, (unsigned)kOutBytes);
+        };
+        auto item_any = [&]() {
+            const int rg = work ? (int)__umulhi((unsigned)tid, bc.tpr_magic) : 0;
+            const int t = work ? tid - rg * bc.tpr : tid;
+            process_item<L, NPT, SR, TS>(st, bc.args[parity], bc.K, work ? w.y : 1, w.z, rg, t, work, salt, bc.W, bc.WB,
+                                         bc.RC, bc.so, out, (unsigned)kStageBytes, (unsigned)kOutBytes);
+        };
+        const int Wrec = work ? bc.W : 0;
+        if constexpr (NPT == 2) {
+            if (Wrec == 128) item_w(std::integral_constant<int, 128>{});
+            else if (Wrec == 192) item_w(std::integral_constant<int, 192>{});
+            else if (Wrec == 64) item_w(std::integral_constant<int, 64>{});
+            else item_any();
+        } else if constexpr (NPT == 4) {
+            if (Wrec == 128) item_w(std::integral_constant<int, 128>{});
+            else item_any();
+        } else {
+            item_any();
+        }
         if constexpr (TS) {
             fence_async_smem();
             if (tid == 0) bulk_wait_read_all();  // item k - 1's store has read the other tile
