@@ -274,23 +274,26 @@ __global__ void init_kernel(unsigned char* __restrict__ S, const double* __restr
     using Eg = typename L::Eg;
     Ef* Sf = f_base<L>(S);
     Eg* Sg = g_base<L>(S, plane);
-    const long long n = plane;  // every row held, halo rows (zero) included
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int j = (int)(q / pitch) - row0, i = (int)(q % pitch);
-        double th = 0.0;
-        const bool in = i < nx && j >= 0 && j < ny;
-        if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
-        for (int k = 0; k < 9; ++k) Sf[L::pf(k) * plane + q] = elem_from_f<Ef>(0.f);
-        if constexpr (L::kTheta) {
-            // At rest g_k = w theta exactly: theta and zero deviations.
-            theta_plane<L>(S, plane)[q] = in ? (float)th : 0.f;
-            for (int k = 1; k < 5; ++k) dev_plane<L>(S, plane, k)[q] = elem_from_f<Eg>(0.f);
-            continue;
+    const int rows = (int)(plane / pitch);  // every row held, halo rows (zero) included
+    // A block per buffer row (striding over rows), its threads along the row.
+    for (int rr = blockIdx.x; rr < rows; rr += gridDim.x) {
+        const int j = rr - row0;
+        for (int i = threadIdx.x; i < pitch; i += blockDim.x) {
+            const long long q = (long long)rr * pitch + i;
+            double th = 0.0;
+            const bool in = i < nx && j >= 0 && j < ny;
+            if (in) th = theta0 ? theta0[(size_t)j * nx + i] : theta_const;
+            for (int k = 0; k < 9; ++k) Sf[L::pf(k) * plane + q] = elem_from_f<Ef>(0.f);
+            if constexpr (L::kTheta) {
+                // At rest g_k = w theta exactly: theta and zero deviations.
+                theta_plane<L>(S, plane)[q] = in ? (float)th : 0.f;
+                for (int k = 1; k < 5; ++k) dev_plane<L>(S, plane, k)[q] = elem_from_f<Eg>(0.f);
+                continue;
+            }
+            Sg[L::pg(0) * plane + q] = elem_from_f<Eg>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
+            const float side = in ? (float)((4.0 + a) * th / 20.0 - sh1) : 0.f;
+            for (int k = 1; k < 5; ++k) Sg[L::pg(k) * plane + q] = elem_from_f<Eg>(side);
         }
-        Sg[L::pg(0) * plane + q] = elem_from_f<Eg>(in ? (float)((1.0 - a) * th / 5.0 - sh0) : 0.f);
-        const float side = in ? (float)((4.0 + a) * th / 20.0 - sh1) : 0.f;
-        for (int k = 1; k < 5; ++k) Sg[L::pg(k) * plane + q] = elem_from_f<Eg>(side);
     }
 }
 
@@ -1053,18 +1056,19 @@ static int create_ctx(const dmrt_params* pg, int y0, int rows, bool slab, const 
         if (e != cudaSuccess) return fail(cuda_fail(c, e, "copy theta0"));
         d_theta0 = stage;
     }
+    const int init_grid = (int)std::min<long long>(L.plane / L.pitch, 4096);
     with_layout(p->storage, [&](auto tag) {
         using Lt = decltype(tag);
-        init_kernel<Lt><<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 0)), d_theta0,
-                                                     p->theta_init, k.a, sh0, sh1, p->nx, p->ny,
-                                                     L.pitch, L.plane, row0);
-        // Buffer B's padding columns must read as zero too.
-        init_kernel<Lt><<<1024, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 1)), nullptr,
-                                                     p->theta_ref, k.a, sh0, sh1, p->nx, p->ny, L.pitch,
-                                                     L.plane, row0);
+        init_kernel<Lt><<<init_grid, 256, 0, c->stream>>>(reinterpret_cast<unsigned char*>(buf(c, 0)), d_theta0,
+                                                          p->theta_init, k.a, sh0, sh1, p->nx, p->ny,
+                                                          L.pitch, L.plane, row0);
     });
     cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(cuda_fail(c, e, "init kernels"));
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "init kernel"));
+    // Buffer B: zero (its padding columns must read as zero; the first step
+    // writes every node, and a slab's halo rows are filled before they are read).
+    e = cudaMemsetAsync(c->ws + L.off_b, 0, L.buf_bytes, c->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(c, e, "clear buffer B"));
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return fail(cuda_fail(c, e, "init synchronize"));
     *out = c;
