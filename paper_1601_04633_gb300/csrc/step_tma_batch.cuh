@@ -119,8 +119,10 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 // TS: results go through a shared-memory output tile (two, alternating) and
 // leave by tensor stores issued by one thread after the item's barrier, as in
 // the single-cavity kernel, with the cavity's own store maps.
-template <typename L, int NPT, int R, int S, bool SR = false, bool TS = false>
-__global__ void __launch_bounds__(R * (256 / NPT))
+// MINB: blocks per SM that the registers must leave room for (1: no bound
+// beyond the block size).
+template <typename L, int NPT, int R, int S, bool SR = false, bool TS = false, int MINB = 1>
+__global__ void __launch_bounds__(R * (256 / NPT), MINB)
     step_tma_batch_kernel(const BatchCavity* __restrict__ cav, const CUtensorMap* __restrict__ maps,
                           const int* __restrict__ item_base, int n_cav, int total_items, int static_per_block,
                           int parity, unsigned* batch_err, unsigned* ctr) {

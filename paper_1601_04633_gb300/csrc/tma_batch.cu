@@ -27,7 +27,8 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2>},
-    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 2>},
+    // (2, 1, 2): registers bounded for 7 blocks per SM (72; shared memory allows 8).
+    {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 2, false, false, 7>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 1, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 3>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 2, 2, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 3>},
     {DMRT_MIXED, DMRT_ROUND_NEAREST, 4, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2>},
@@ -39,7 +40,7 @@ static const TmaVariant kVariants[] = {
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 4, 2, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 1, 4, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 1, 4, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 4, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 4, 2, true>},
-    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 2, true>},
+    {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 2, true, false, 7>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 1, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 1, 3, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 2, 2, 3, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 2, 2, 3, true>},
     {DMRT_MIXED, DMRT_ROUND_STOCHASTIC, 4, 2, 2, 0, (const void*)step_tma_batch_kernel<Split<__half, float>, 4, 2, 2, true>},
