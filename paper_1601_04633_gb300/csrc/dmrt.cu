@@ -657,16 +657,29 @@ void choose_launch(const dmrt_params& p_in, int sms, int* kernel, int* npt_out, 
 // both buffers in the shared memory of one cluster of up to 16 blocks.
 // The cluster kernel's launch shape for c (blocks, rows per block, threads,
 // shared memory); false if the cavity does not fit one cluster on this GPU.
+// The cluster kernel compiled for blocks of at most `threads` threads, and its launch.
+const void* cluster_func(int threads) {
+    return threads <= 320 ? (const void*)dmrt::step_cluster_kernel<320>
+           : threads <= 640 ? (const void*)dmrt::step_cluster_kernel<640>
+                            : (const void*)dmrt::step_cluster_kernel<1024>;
+}
+cudaError_t launch_cluster_kernel(const cudaLaunchConfig_t& cfg, const dmrt::ClusterArgs& C) {
+    const int threads = (int)cfg.blockDim.x;
+    if (threads <= 320) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<320>, C);
+    if (threads <= 640) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<640>, C);
+    return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<1024>, C);
+}
+
 bool cluster_fit(dmrt_ctx* c, int* csize_out, int* crows_out, int* threads_out, size_t* smem_out) {
     const dmrt_params& p = c->p;
     if (p.storage != DMRT_FP32 || c->slab) return false;
-    const void* fn = (const void*)dmrt::step_cluster_kernel;
     for (int csize : {16, 8}) {
         const int cs = std::min(csize, p.ny);
         const int rows = (p.ny + cs - 1) / cs;
         const int blocks = (p.ny + rows - 1) / rows;
         const size_t smem = dmrt::cluster_smem_bytes(rows, p.nx, p.ny);
         const int threads = dmrt::cluster_threads(rows, p.nx);
+        const void* fn = cluster_func(threads);
         if (smem > (size_t)dmrt::kMaxSmem) continue;
         if (blocks > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -1319,7 +1332,7 @@ static int launch_cluster(dmrt_ctx* c, int n) {
     cfg.stream = c->stream;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    CK(cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel, C), "cluster step launch");
+    CK(launch_cluster_kernel(cfg, C), "cluster step launch");
     c->cur ^= n & 1;
     c->t += n;
     return DMRT_OK;
@@ -2777,7 +2790,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
             cfg.stream = rs;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            CK(cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel, CA), "adjoint recompute launch");
+            CK(launch_cluster_kernel(cfg, CA), "adjoint recompute launch");
             return DMRT_OK;
         }
         for (long long t = 1; t < len; ++t) {

@@ -88,7 +88,11 @@ __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int
     return s;
 }
 
-static __global__ void __launch_bounds__(1024) step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
+// MAXT: the largest block it is launched with (the compiler may give a block of
+// at most 320 or 640 threads more registers per thread, hence more
+// independent instructions in flight along a node's chain).
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
     const int rank = (int)cl.block_rank();
