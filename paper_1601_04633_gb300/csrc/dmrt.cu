@@ -198,7 +198,7 @@ dmrt::StepArgs step_args(dmrt_ctx* c, int from) {
     A.wall_lo = c->wall_lo;
     A.wall_hi = c->wall_hi;
     A.jglob0 = c->y0;
-    A.nu_div = (double)c->H;
+    A.nu_inv = 1.0 / (double)c->H;
     return A;
 }
 

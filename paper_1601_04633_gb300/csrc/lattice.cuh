@@ -68,10 +68,11 @@ struct alignas(16) StepArgs {
     // wall_hi: row ny - 1) apply the wall rules; across the others the pull
     // reads the halo rows, which the neighbouring slabs fill. jglob0 is the
     // cavity row of node row 0 (it seeds the stochastic rounding, so a slab
-    // rounds as the whole cavity would), nu_div the row count of the whole
-    // cavity (the Nusselt mean of a slab is its share of the cavity's mean).
+    // rounds as the whole cavity would), nu_inv the reciprocal of the row
+    // count of the whole cavity (the Nusselt mean of a slab is its share of
+    // the cavity's mean; a product, since a float64 division is slow here).
     int row0, wall_lo, wall_hi, jglob0;
-    double nu_div;
+    double nu_inv;
 };
 
 constexpr unsigned kErrNonFinite = 1u;
@@ -266,11 +267,19 @@ __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j,
 // are summed in a fixed order and appended to the ring as step step_in - 1: 256
 // partial sums, partial p over rows p, p + 256, p + 512, ... in that order,
 // kept by lane p % 32 of the warp that takes stream q = p / 32 (warps take
-// q = w, w + nwarps, ...); lane l then adds its eight partials q = 0..7 in order
+// q = w, w + nwarps, ...); lane l then adds its eight partials q = 0..7 pairwise
+// (nu_combine8)
 // and the warp adds the 32 lane sums by a butterfly. The order does not depend
 // on the block size or on scheduling. A step then advances the step counter
 // (step_out = step_in + 1) and marks its own rows as pending; the finalize
 // call clears the mark.
+// A lane's eight partial sums of Nusselt rows, added pairwise: ((p0 + p1) +
+// (p2 + p3)) + ((p4 + p5) + (p6 + p7)). Every kernel that sums a step's rows
+// uses this order.
+__device__ __forceinline__ double nu_combine8(const double (&p)[8]) {
+    return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+}
+
 __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
     __shared__ double part[8][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -293,13 +302,14 @@ __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
         }
         __syncthreads();
         if (warp == 0) {
-            double s = 0.0;
+            double p8[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) s += part[q][lane];
+            for (int q = 0; q < 8; ++q) p8[q] = part[q][lane];
+            double s = nu_combine8(p8);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             if (lane == 0) {
-                const double mean = s / A.nu_div;
+                const double mean = s * A.nu_inv;
                 if (DMRT_IN((t - 1) % A.cap, 0, A.cap, A.err)) A.nu_ring[(t - 1) % A.cap] = mean;
                 *A.nu_last = mean;
             }

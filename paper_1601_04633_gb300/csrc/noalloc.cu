@@ -141,7 +141,7 @@ extern "C" int dmrt_step_noalloc(const dmrt_params* p, const float* src, float* 
     A.wall_lo = 1;
     A.wall_hi = 1;
     A.jglob0 = 0;
-    A.nu_div = (double)p->ny;
+    A.nu_inv = 1.0 / (double)p->ny;
     const int nxq = (p->nx + 3) / 4;
     int wx = 1;
     while (wx < nxq && wx < 32) wx <<= 1;

@@ -25,7 +25,7 @@
 // (distributed shared memory, double-buffered by step parity); after the
 // step's cluster barrier, one extra warp of block 0 (the last; it owns no
 // nodes) sums the rows in the fixed order of nu_finish_prev (partial p over
-// rows p, p + 256, ...; lane l adds partials q = 0..7 in order; butterfly over
+// rows p, p + 256, ...; lane l adds partials q = 0..7 pairwise; butterfly over
 // the lanes) and appends the mean to the ring while the other warps compute
 // the next step.
 //
@@ -76,13 +76,14 @@ __host__ __device__ constexpr size_t cluster_smem_bytes(int rows_per, int nx, in
 
 // Sum of rows[0..ny) by warp 0 in the fixed order of nu_finish_prev (the result in every lane).
 __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int lane) {
-    double s = 0.0;
+    double p8[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         double acc = 0.0;
         for (int r = lane + 32 * q; r < ny; r += 256) acc += rows[r];
-        s += acc;
+        p8[q] = acc;
     }
+    double s = nu_combine8(p8);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     return s;
@@ -146,8 +147,8 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
         // Rows of an earlier step not yet summed (a single step launched before).
         const double sum = warp_fixed_sum(A0.prev_rows, ny, lane);
         if (lane == 0) {
-            A0.nu_ring[(t0 - 1) % A0.cap] = sum / A0.nu_div;
-            *A0.nu_last = sum / A0.nu_div;
+            A0.nu_ring[(t0 - 1) % A0.cap] = sum * A0.nu_inv;
+            *A0.nu_last = sum * A0.nu_inv;
         }
     }
     cl.sync();
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
             // only once per kClusterNuChunk steps, so that the barriers between
             // steps do not wait for them).
             const double sum = warp_fixed_sum(nur + (size_t)(s & 1) * ny, ny, lane);
-            if (lane == 0) means[s % kClusterNuChunk] = sum / A0.nu_div;
+            if (lane == 0) means[s % kClusterNuChunk] = sum * A0.nu_inv;
             __syncwarp();
             if (s % kClusterNuChunk == kClusterNuChunk - 1 || s == C.steps - 1) {
                 // Only the chunk's last `cap` means reach the ring, so that no
