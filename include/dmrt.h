@@ -100,9 +100,9 @@ extern "C" {
  * than 496 nodes and for float32 grids whose one-row items (248-node strips x
  * rows) number at most 4 per SM, with tile (1, 1, 2) up to 2 per SM and (2, 1,
  * 3) beyond (e.g. 112^2 to 256^2), DIRECT otherwise (e.g. 384^2); for runs of
- * steps of a float32 cavity whose rows split over 16 blocks give at most 640
- * nodes per block (e.g. up to 96^2), and no tile asked for, the CLUSTER kernel
- * below where the GPU fits it (64^2: 2.07 against 2.66 us per step). TMA tiles
+ * steps of a float32 cavity whose rows split over 16 blocks give at most 1024
+ * nodes per block (e.g. up to 128^2), and no tile asked for, the CLUSTER kernel
+ * below where the GPU fits it (64^2: 1.43 against 2.66 us per step). TMA tiles
  * compiled in, as (nodes per
  * thread, rows R, stages S): NPT 4 with (R,S) in (1,2) (1,3) (1,4) (1,5) (1,6)
  * (2,2) (2,3) (2,4) (4,2) (4,3); NPT 2 with (1,3) (1,4) (1,5) (2,2) (2,3)

@@ -731,15 +731,15 @@ int setup_cluster(dmrt_ctx* c) {
 
 
 // AUTO takes the cluster kernel for runs of steps of a small float32 cavity:
-// rows split over 16 blocks with at most 640 nodes per block (e.g. up to 96^2),
-// whose state fits the cluster's shared memory, and no tile asked for. Measured
-// per step, cluster / one-row TMA items: 16^2 2.16 / 3.11, 32^2 1.78 / 2.98, 64^2
-// 2.07 / 2.66, 96^2 2.44 / 2.95, 128^2 3.06 / 2.79 us.
+// rows split over 16 blocks with at most 1024 nodes per block (e.g. up to
+// 128^2), whose state fits the cluster's shared memory, and no tile asked for.
+// Measured per step, cluster / one-row TMA items: 16^2 1.23 / 3.11, 32^2 1.23 /
+// 2.98, 64^2 1.43 / 2.66, 96^2 1.65 / 2.95, 128^2 2.60 / 2.78 us.
 bool auto_cluster(const dmrt_params& p) {
     if (p.kernel != DMRT_KERNEL_AUTO || p.storage != DMRT_FP32) return false;
     if (p.tma_npt > 0 || p.tma_rows > 0 || p.tma_stages > 0) return false;
     const int crows = (p.ny + 15) / 16;
-    return (long long)crows * p.nx <= 640 && dmrt::cluster_smem_bytes(crows, p.nx, p.ny) <= (size_t)dmrt::kMaxSmem;
+    return (long long)crows * p.nx <= 1024 && dmrt::cluster_smem_bytes(crows, p.nx, p.ny) <= (size_t)dmrt::kMaxSmem;
 }
 
 int setup_kernel(dmrt_ctx* c) {

@@ -267,17 +267,37 @@ __device__ __forceinline__ void nu_report(const StepArgs& A, bool has_nu, int j,
 // are summed in a fixed order and appended to the ring as step step_in - 1: 256
 // partial sums, partial p over rows p, p + 256, p + 512, ... in that order,
 // kept by lane p % 32 of the warp that takes stream q = p / 32 (warps take
-// q = w, w + nwarps, ...); lane l then adds its eight partials q = 0..7 pairwise
-// (nu_combine8)
-// and the warp adds the 32 lane sums by a butterfly. The order does not depend
+// q = w, w + nwarps, ...), each partial starting from its first row; lane l
+// then adds its partials pairwise (nu_combine), and the warp adds the 32 lane
+// sums by a butterfly. The order does not depend
 // on the block size or on scheduling. A step then advances the step counter
 // (step_out = step_in + 1) and marks its own rows as pending; the finalize
 // call clears the mark.
-// A lane's eight partial sums of Nusselt rows, added pairwise: ((p0 + p1) +
-// (p2 + p3)) + ((p4 + p5) + (p6 + p7)). Every kernel that sums a step's rows
-// uses this order.
-__device__ __forceinline__ double nu_combine8(const double (&p)[8]) {
-    return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+// A lane's partial sums of Nusselt rows p[q], q < nq = min(8, ceil(ny / 32))
+// (partials q >= nq hold no row), added pairwise: ((p0 + p1) + (p2 + p3)) +
+// ((p4 + p5) + (p6 + p7)), a leaf past nq left out (float64 is a slow pipe on
+// this GPU, so no zeros are added). Every kernel that sums a step's rows uses
+// this order; nq is the same in every lane, so the branches are uniform.
+__device__ __forceinline__ int nu_partials(int ny) { return ny >= 256 ? 8 : (ny + 31) / 32; }
+__device__ __forceinline__ double nu_combine(const double (&p)[8], int nq) {
+    double a = p[0];
+    if (nq > 1) a += p[1];
+    if (nq > 2) {
+        double b = p[2];
+        if (nq > 3) b += p[3];
+        a += b;
+    }
+    if (nq > 4) {
+        double c = p[4];
+        if (nq > 5) c += p[5];
+        if (nq > 6) {
+            double d = p[6];
+            if (nq > 7) d += p[7];
+            c += d;
+        }
+        a += c;
+    }
+    return a;
 }
 
 __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
@@ -290,6 +310,10 @@ __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
         for (int q = warp; q < 8; q += nw) {
             double acc = 0.0;
             int r = lane + 32 * q;
+            if (r < A.ny) {  // the partial starts from its first row
+                acc = __ldcg(A.prev_rows + r);
+                r += 256;
+            }
             for (; r + 3 * 256 < A.ny; r += 4 * 256) {  // four loads in flight, added in order
                 double v[4];
 #pragma unroll
@@ -305,7 +329,7 @@ __device__ __forceinline__ void nu_finish_prev(const StepArgs& A, bool step) {
             double p8[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) p8[q] = part[q][lane];
-            double s = nu_combine8(p8);
+            double s = nu_combine(p8, nu_partials(A.ny));
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
             if (lane == 0) {

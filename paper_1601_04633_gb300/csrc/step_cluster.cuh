@@ -20,14 +20,15 @@
 // temperatures, the Nusselt ring and the error word.
 //
 // Nusselt number (Eqs. 18-19): the pre-collision temperatures at x = 0 and 1 of
-// each row are staged in shared memory; after a block barrier one thread per
-// row computes the row's value and writes it into block 0's shared row array
-// (distributed shared memory, double-buffered by step parity); after the
-// step's cluster barrier, one extra warp of block 0 (the last; it owns no
-// nodes) sums the rows in the fixed order of nu_finish_prev (partial p over
-// rows p, p + 256, ...; lane l adds partials q = 0..7 pairwise; butterfly over
-// the lanes) and appends the mean to the ring while the other warps compute
-// the next step.
+// each row are staged in shared memory (double-buffered by step parity). After
+// the step's cluster barrier, one extra warp of each block (the last; it owns
+// no nodes) computes its rows' values and writes them into block 0's shared
+// row array (distributed shared memory, by step parity), and block 0's extra
+// warp sums the previous step's rows in the fixed order of nu_finish_prev
+// (partial p over rows p, p + 256, ...; lane l adds its partials pairwise;
+// butterfly over the lanes) and appends the mean to the ring, while the other
+// warps compute the next step; one more barrier after the last step lets it
+// sum that step too.
 //
 // The launch starts from the state in global buffer `parity` (copied in), and
 // ends by copying the final state to global buffer parity ^ (K & 1), the last
@@ -69,7 +70,7 @@ __host__ __device__ constexpr int cluster_threads(int rows_per, int nx) {
 
 __host__ __device__ constexpr size_t cluster_smem_bytes(int rows_per, int nx, int ny) {
     return (size_t)2 * kPlanes * (rows_per + 2) * nx * sizeof(float)  // both buffers, with halo rows
-           + (((size_t)4 * rows_per * sizeof(float) + 15) & ~size_t(15))  // theta at x = 0 and 1; hot, cold walls
+           + (((size_t)6 * rows_per * sizeof(float) + 15) & ~size_t(15))  // theta at x = 0, 1 (by step parity); walls
            + (size_t)kClusterNuChunk * sizeof(double)                  // means not yet in the ring (block 0)
            + (size_t)2 * ny * sizeof(double);                         // Nusselt rows (block 0), by step parity
 }
@@ -79,11 +80,12 @@ __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int
     double p8[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        double acc = 0.0;
-        for (int r = lane + 32 * q; r < ny; r += 256) acc += rows[r];
+        const int r0q = lane + 32 * q;
+        double acc = r0q < ny ? rows[r0q] : 0.0;
+        for (int r = r0q + 256; r < ny; r += 256) acc += rows[r];
         p8[q] = acc;
     }
-    double s = nu_combine8(p8);
+    double s = nu_combine(p8, nu_partials(ny));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
     return s;
@@ -112,8 +114,8 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
 
     extern __shared__ __align__(16) unsigned char smem_c[];
     float* sb[2] = {reinterpret_cast<float*>(smem_c), reinterpret_cast<float*>(smem_c) + kPlanes * plane_sm};
-    float* th01 = reinterpret_cast<float*>(smem_c) + 2 * kPlanes * plane_sm;
-    float* walls = th01 + 2 * RP;  // hot and cold wall temperatures of this block's rows
+    float* th01 = reinterpret_cast<float*>(smem_c) + 2 * kPlanes * plane_sm;  // [step parity][row][x = 0, 1]
+    float* walls = th01 + 4 * RP;  // hot and cold wall temperatures of this block's rows
     double* nur = reinterpret_cast<double*>(smem_c + cluster_smem_bytes(RP, nx, ny) - (size_t)2 * ny * sizeof(double));
     double* means = nur - kClusterNuChunk;
 
@@ -163,13 +165,39 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
     float* const above0 = rank + 1 < csize ? cl.map_shared_rank(sb[0], rank + 1) : nullptr;
     float* const above1 = rank + 1 < csize ? cl.map_shared_rank(sb[1], rank + 1) : nullptr;
     double* nu_rows0 = cl.map_shared_rank(nur, 0);
+    // The spare warp's Nusselt work (Eqs. 18-19). Rows of step q: from the
+    // temperatures at x = 0 and 1 into block 0's row array (by step parity).
+    auto nu_rows_of = [&](int q) {
+        const float* th = th01 + (q & 1) * 2 * RP;
+        double* dst = nu_rows0 + (size_t)(q & 1) * ny;
+        for (int r = lane; r < nr; r += 32) {
+            const int j = r0 + r;
+            if (!DMRT_IN(j, 0, ny, A0.err)) continue;
+            dst[j] = K.nu_scale * (8.0 * (double)walls[r] - 9.0 * (double)th[2 * r] + (double)th[2 * r + 1]);
+        }
+    };
+    // Block 0: the mean of step q's rows, kept in shared memory; a full chunk
+    // goes to the ring (global stores only once per kClusterNuChunk steps), and
+    // only the chunk's last `cap` means, so that no two lanes write one slot (a
+    // smaller ring wraps within a chunk).
+    auto nu_mean_of = [&](int q) {
+        const double sum = warp_fixed_sum(nur + (size_t)(q & 1) * ny, ny, lane);
+        if (lane == 0) means[q % kClusterNuChunk] = sum * A0.nu_inv;
+        __syncwarp();
+        if (q % kClusterNuChunk == kClusterNuChunk - 1 || q == C.steps - 1) {
+            const int first = q - q % kClusterNuChunk;
+            const long long n = q - first + 1;
+            const int q0 = (int)(n > A0.cap ? n - A0.cap : 0);
+            for (int k = q0 + lane; k <= q - first; k += 32) A0.nu_ring[(t0 + first + k) % A0.cap] = means[k];
+            if (lane == 0) *A0.nu_last = means[q - first];
+        }
+    };
     for (int s = 0; s < C.steps; ++s) {
         const bool odd = (s & 1) != 0;
         const float* S = odd ? sb[1] : sb[0];
         float* Dst = odd ? sb[0] : sb[1];
         float* Dbelow = odd ? below0 : below1;
         float* Dabove = odd ? above0 : above1;
-        double* nu_dst = nu_rows0 + (size_t)(s & 1) * ny;
         for (int i = threadIdx.x; i < (nu_warp ? 0 : nr * nx); i += nwork) {
             const int r = i / nx, x = i - r * nx;
             const int j = r0 + r;
@@ -257,35 +285,21 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
 #pragma unroll
                 for (int k = 0; k < 5; ++k) d[plane_g(k) * PL] = g[k];
             }
-            if (x == 0) th01[2 * r] = theta;
-            if (x == 1) th01[2 * r + 1] = theta;
+            if (x == 0) th01[(s & 1) * 2 * RP + 2 * r] = theta;
+            if (x == 1) th01[(s & 1) * 2 * RP + 2 * r + 1] = theta;
         }
-        __syncthreads();  // theta at x = 0 and 1 of every row of this block
-        for (int r = threadIdx.x; r < (rec || nu_warp ? 0 : nr); r += nwork) {
-            const int j = r0 + r;
-            if (!DMRT_IN(j, 0, ny, A0.err)) continue;
-            const double tw = (double)walls[r];
-            nu_dst[j] = K.nu_scale * (8.0 * tw - 9.0 * (double)th01[2 * r] + (double)th01[2 * r + 1]);
+        cl.sync();  // step s's state, halo rows and wall-side temperatures are visible
+        if (!rec && nu_warp) {
+            // Off the node warps' path: this block's rows of step s into block
+            // 0's row array, and block 0 sums step s - 1, whose rows every block
+            // wrote before this barrier.
+            nu_rows_of(s);
+            if (rank == 0 && s > 0) nu_mean_of(s - 1);
         }
-        cl.sync();  // the new state and the step's Nusselt rows are visible to the whole cluster
-        if (!rec && rank == 0 && nu_warp) {
-            // Mean of this step's rows while the other warps start the next step,
-            // kept in shared memory; a full chunk goes to the ring (global stores
-            // only once per kClusterNuChunk steps, so that the barriers between
-            // steps do not wait for them).
-            const double sum = warp_fixed_sum(nur + (size_t)(s & 1) * ny, ny, lane);
-            if (lane == 0) means[s % kClusterNuChunk] = sum * A0.nu_inv;
-            __syncwarp();
-            if (s % kClusterNuChunk == kClusterNuChunk - 1 || s == C.steps - 1) {
-                // Only the chunk's last `cap` means reach the ring, so that no
-                // two lanes write one slot (a smaller ring wraps within a chunk).
-                const int first = s - s % kClusterNuChunk;
-                const long long n = s - first + 1;
-                const int q0 = (int)(n > A0.cap ? n - A0.cap : 0);
-                for (int q = q0 + lane; q <= s - first; q += 32) A0.nu_ring[(t0 + first + q) % A0.cap] = means[q];
-                if (lane == 0) *A0.nu_last = means[s - first];
-            }
-        }
+    }
+    if (!rec && C.steps > 0) {
+        cl.sync();  // the last step's rows
+        if (rank == 0 && nu_warp) nu_mean_of(C.steps - 1);
     }
     // The final state to global buffer parity ^ (K & 1); the last step's rows to
     // the rows array of its source buffer; the step counter slot of the final

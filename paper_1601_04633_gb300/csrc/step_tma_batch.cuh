@@ -341,7 +341,7 @@ namespace dmrt {
 // barrier follows, thread 0 counts the item (done[c]); the block completing
 // the cavity's step sums the step's per-row Nusselt numbers in warp 0 (the
 // same fixed order as nu_finish_prev: partial p over rows p, p + 256, ...;
-// lane l adds its partials q = 0..7 pairwise, then a butterfly), appends the mean to
+// lane l adds its partials pairwise, then a butterfly), appends the mean to
 // the cavity's ring, and publishes ready[c] = s + 1 (a fence, then the store).
 // The consumer of ready[c] acquires it and orders the following tensor copies
 // after it with a proxy fence. Loads of the wall columns (ld.global.cg in
@@ -534,6 +534,10 @@ __global__ void __launch_bounds__(R * (256 / NPT))
                 for (int q = 0; q < 8; ++q) {
                     double acc = 0.0;
                     int r = tid + 32 * q;
+                    if (r < A.ny) {  // the partial starts from its first row
+                        acc = __ldcg(A.nu_rows + r);
+                        r += 256;
+                    }
                     for (; r + 3 * 256 < A.ny; r += 4 * 256) {
                         double v[4];
 #pragma unroll
@@ -544,7 +548,7 @@ __global__ void __launch_bounds__(R * (256 / NPT))
                     for (; r < A.ny; r += 256) acc += __ldcg(A.nu_rows + r);
                     acc8[q] = acc;
                 }
-                double sum = nu_combine8(acc8);
+                double sum = nu_combine(acc8, nu_partials(A.ny));
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(kFull, sum, o);
                 if (tid == 0) {

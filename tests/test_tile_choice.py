@@ -3,7 +3,7 @@ dmrt_choose_launch, the function dmrt_create itself calls).
 
 The rules are measured choices on a 152-SM GB300: float32 cavities wider than
 496 nodes take the TMA kernel with (1, 4, 2); float32 cavities whose rows split
-over 16 blocks give at most 640 nodes per block (up to 96^2) take the cluster
+over 16 blocks give at most 1024 nodes per block (up to 128^2) take the cluster
 kernel for runs of steps; other small float32 grids take one-row TMA items
 while those number at most four per SM ((1, 1, 2) up to two per SM, (2, 1, 3)
 beyond), else the direct kernel; 16-bit storage takes
@@ -44,7 +44,7 @@ def choose(D, nx, ny, storage=0, rounding=0, sms=SMS, **kw):
 @pytest.mark.parametrize("n,expect", [
     (4096, (TMA, 1, 4, 2)), (2048, (TMA, 1, 4, 2)), (1000, (TMA, 1, 4, 2)),
     (16, (CLUSTER, 0, 0, 0)), (64, (CLUSTER, 0, 0, 0)), (96, (CLUSTER, 0, 0, 0)),
-    (112, (TMA, 1, 1, 2)), (128, (TMA, 1, 1, 2)), (192, (TMA, 1, 1, 2)),
+    (112, (CLUSTER, 0, 0, 0)), (128, (CLUSTER, 0, 0, 0)), (144, (TMA, 1, 1, 2)), (192, (TMA, 1, 1, 2)),
     (256, (TMA, 2, 1, 3)), (304, (TMA, 2, 1, 3)), (384, (DIRECT, 0, 0, 0)), (496, (DIRECT, 0, 0, 0)),
 ])
 def test_float32_square_cavities(D, n, expect):
@@ -104,10 +104,11 @@ def test_every_chosen_tile_is_compiled(D, storage, rounding):
 
 
 def test_auto_takes_the_cluster_kernel_for_small_float32_cavities(D):
-    # At most 640 nodes per block of a 16-block cluster, float32, no tile asked for.
+    # At most 1024 nodes per block of a 16-block cluster, float32, no tile asked for.
     assert choose(D, 200, 16) == (CLUSTER, 0, 0, 0)      # 1 row of 200 per block
     assert choose(D, 100, 70) == (CLUSTER, 0, 0, 0)      # 5 rows of 100
-    assert choose(D, 130, 80) != (CLUSTER, 0, 0, 0)      # 5 rows of 130 = 650
+    assert choose(D, 130, 80) == (CLUSTER, 0, 0, 0)      # 5 rows of 130 = 650
+    assert choose(D, 200, 100) != (CLUSTER, 0, 0, 0)     # 7 rows of 200 = 1400
     assert choose(D, 64, 64, 3, 1) == (TMA, 2, 1, 2)     # mixed storage keeps the TMA kernel
     assert choose(D, 64, 64, tma_npt=1, tma_rows=1, tma_stages=2)[0] != CLUSTER  # a tile asked for
 
