@@ -21,10 +21,10 @@
 //
 // Nusselt number (Eqs. 18-19): the pre-collision temperatures at x = 0 and 1 of
 // each row are staged in shared memory (double-buffered by step parity). After
-// the step's cluster barrier, one extra warp of each block (the last; it owns
-// no nodes) computes its rows' values and writes them into block 0's shared
-// row array (distributed shared memory, by step parity), and block 0's extra
-// warp sums the previous step's rows in the fixed order of nu_finish_prev
+// the step's cluster barrier, an extra warp of each block (it owns no nodes)
+// computes its rows' values and writes them into block 0's shared row array
+// (distributed shared memory, by step parity), and a second extra warp of
+// block 0 sums the previous step's rows in the fixed order of nu_finish_prev
 // (partial p over rows p, p + 256, ...; lane l adds its partials pairwise;
 // butterfly over the lanes) and appends the mean to the ring, while the other
 // warps compute the next step; one more barrier after the last step lets it
@@ -62,10 +62,10 @@ struct ClusterArgs {
 // Means kept in block 0's shared memory between their flushes to the ring.
 constexpr int kClusterNuChunk = 1024;
 
-// Threads of a cluster block: one per node of its rows (at most 992), rounded up
-// to whole warps, and the Nusselt warp.
+// Threads of a cluster block: one per node of its rows (at most 960), rounded up
+// to whole warps, and two Nusselt warps (rows; block 0: the sums).
 __host__ __device__ constexpr int cluster_threads(int rows_per, int nx) {
-    return ((rows_per * nx + 31) / 32 * 32 < 992 ? (rows_per * nx + 31) / 32 * 32 : 992) + 32;
+    return ((rows_per * nx + 31) / 32 * 32 < 960 ? (rows_per * nx + 31) / 32 * 32 : 960) + 64;
 }
 
 __host__ __device__ constexpr size_t cluster_smem_bytes(int rows_per, int nx, int ny) {
@@ -109,8 +109,9 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
     const int nr = max(0, min(RP, ny - r0));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int plane_sm = (RP + 2) * nx;  // floats per plane in shared memory: rows -1 .. RP
-    const int nwork = (int)blockDim.x - 32;  // node threads; the last warp sums Nusselt rows
+    const int nwork = (int)blockDim.x - 64;  // node threads; then the two Nusselt warps
     const bool nu_warp = (int)threadIdx.x >= nwork;
+    const bool sum_warp = (int)threadIdx.x >= nwork + 32;
 
     extern __shared__ __align__(16) unsigned char smem_c[];
     float* sb[2] = {reinterpret_cast<float*>(smem_c), reinterpret_cast<float*>(smem_c) + kPlanes * plane_sm};
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
     float* const above0 = rank + 1 < csize ? cl.map_shared_rank(sb[0], rank + 1) : nullptr;
     float* const above1 = rank + 1 < csize ? cl.map_shared_rank(sb[1], rank + 1) : nullptr;
     double* nu_rows0 = cl.map_shared_rank(nur, 0);
-    // The spare warp's Nusselt work (Eqs. 18-19). Rows of step q: from the
+    // The spare warps' Nusselt work (Eqs. 18-19). Rows of step q: from the
     // temperatures at x = 0 and 1 into block 0's row array (by step parity).
     auto nu_rows_of = [&](int q) {
         const float* th = th01 + (q & 1) * 2 * RP;
@@ -290,16 +291,16 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
         }
         cl.sync();  // step s's state, halo rows and wall-side temperatures are visible
         if (!rec && nu_warp) {
-            // Off the node warps' path: this block's rows of step s into block
-            // 0's row array, and block 0 sums step s - 1, whose rows every block
-            // wrote before this barrier.
-            nu_rows_of(s);
-            if (rank == 0 && s > 0) nu_mean_of(s - 1);
+            // Off the node warps' path, on two warps: this block's rows of step s
+            // into block 0's row array; in block 0, the sum of step s - 1, whose
+            // rows every block wrote before this barrier.
+            if (!sum_warp) nu_rows_of(s);
+            else if (rank == 0 && s > 0) nu_mean_of(s - 1);
         }
     }
     if (!rec && C.steps > 0) {
         cl.sync();  // the last step's rows
-        if (rank == 0 && nu_warp) nu_mean_of(C.steps - 1);
+        if (rank == 0 && sum_warp) nu_mean_of(C.steps - 1);
     }
     // The final state to global buffer parity ^ (K & 1); the last step's rows to
     // the rows array of its source buffer; the step counter slot of the final
