@@ -27,31 +27,73 @@
 
 namespace dmrt {
 
+// The reverse sweep of a segment of K steps (K even) replays one of two
+// graphs, each of K step nodes and a fold node; graph s serves the segments
+// whose recomputed states sit in slot set s, so a node's addresses depend on s
+// and on t, the step within the segment, only. The segment q itself comes from
+// a device counter (graph s reads counter s; its fold leaves q - 1 in the
+// other), needed only for the averaging weight and to skip the missing steps
+// of a short last segment.
 struct AdjArgs {
-    const float* __restrict__ s_prev;  // s_{k-1}
-    const float* __restrict__ nu_in;   // nu_{k+1}
-    float* __restrict__ nu_out;        // nu_k
+    const long long* seg;              // the segment q swept by this replay
+    long long* seg_next;               // the fold writes q - 1 here (the other graph's counter)
+    const float* slot[2];              // set s: s_{qK+t} at slot[s] + t * state (t = 0: the checkpoint's copy)
+    float* nu[2];                      // adjoint states: step k reads nu[(N - k) & 1], writes the other
     const float* __restrict__ hot;
     const float* __restrict__ cold;
-    double* dthw;                      // [ny] dJ/dtheta_w, accumulated (the final gather only)
-    double* dthw_step;                 // [ny] this step's dJ/dtheta_w terms (written, not accumulated)
-    double* dgbeta_step;               // this step's dJ/dgbeta per warp: [gridDim.y][gridDim.x][4]
+    double* dthw;                      // [ny] dJ/dtheta_w totals
+    double* dgbeta;                    // [n_blocks] dJ/dgbeta totals, one per block of the step grid
+    float* dthw_step;                  // [K][ny] nu_{k+1}[g east](0, j) by step (0: adiabatic hot wall)
+    float2* dgbeta_step;               // [K][n_blocks][4] the segment's dJ/dgbeta by step and warp, as (hi, lo)
+    long long state;                   // floats in one state
+    long long K, N, C;                 // segment length, steps, segments
+    long long w_from;                  // steps k > w_from carry the weight w (the averaging window)
+    long long n_blocks;
     long long plane;
+    int nsets;                         // slot sets: with 2, segment q uses set (C - 1 - q) & 1
     int nx, ny, pitch;
-    float w;                           // w_k (0 outside the averaging window)
+    float w;                           // w_k inside the averaging window
     float nu_wall, nu_next;            // dNu/dtheta at columns 0 and 1, divided by ny
-    int gather_only;                   // only the anti-bounce-back term of nu_in
 };
 
-__device__ __forceinline__ void collide_vjp(const float (&f)[9], const float (&g)[5], const float (&lf)[9],
-                                            const float (&lg)[5], const StepConsts& K, float (&nf)[9],
-                                            float (&ng)[5], float& dgb) {
-    // Forward quantities of the pulled state.
-    const float u = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
-    const float v = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
-    const float th = g[0] + g[1] + g[2] + g[3] + g[4];
-    const float uu = u * u + v * v;
-    const float base = 1.f - 1.5f * uu;
+// The half of the local Jacobian that depends on the pulled state only:
+// velocity, temperature and, per direction i, the three factors of the force
+// derivatives (F_i = 3 gbeta (theta - theta_ref)(e_iy - v) w_i P_i,
+// P_i = 1 - 1.5 |u|^2 + 3 e_i.u + 4.5 (e_i.u)^2, Eqs. 26-27):
+//   fu_i = (e_iy - v)(3 e_ix + 9 (e_i.u) e_ix - 3 u)       (d/du without w_i)
+//   fv_i = (e_iy - v)(3 e_iy + 9 (e_i.u) e_iy - 3 v) - P_i  (d/dv)
+//   fp_i = (e_iy - v) P_i                                  (d/dtheta, d/dgbeta)
+struct VjpFwd {
+    float u, v, th;
+    float fu[9], fv[9], fp[9];
+};
+
+__device__ __forceinline__ VjpFwd vjp_forward(const float (&f)[9], const float (&g)[5]) {
+    VjpFwd F;
+    F.u = (f[1] - f[3]) + (f[5] - f[6]) - (f[7] - f[8]);
+    F.v = (f[2] - f[4]) + (f[5] + f[6]) - (f[7] + f[8]);
+    F.th = g[0] + g[1] + g[2] + g[3] + g[4];
+    const float u = F.u, v = F.v;
+    const float base = 1.f - 1.5f * (u * u + v * v);
+    const int EXs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int EYs[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float ex = (float)EXs[i], ey = (float)EYs[i];
+        const float eu = ex * u + ey * v;
+        const float P = base + 3.f * eu + 4.5f * eu * eu;
+        const float dy = ey - v;
+        F.fu[i] = dy * (3.f * ex + 9.f * eu * ex - 3.f * u);
+        F.fv[i] = dy * (3.f * ey + 9.f * eu * ey - 3.f * v) - P;
+        F.fp[i] = dy * P;
+    }
+    return F;
+}
+
+// The other half: nu = C'(q)^T lambda for the pulled state summarised by F.
+__device__ __forceinline__ void collide_vjp(const VjpFwd& F, const float (&lf)[9], const float (&lg)[5],
+                                            const StepConsts& K, float (&nf)[9], float (&ng)[5], float& dgb) {
+    const float u = F.u, v = F.v, th = F.th;
 
     // kappa = S' M lam_f (the conserved rows do not contribute).
     const float a13 = lf[1] - lf[3], a24 = lf[2] - lf[4];
@@ -70,24 +112,17 @@ __device__ __forceinline__ void collide_vjp(const float (&f)[9], const float (&g
     const float ku = 6.f * u * k3 + 2.f * u * k4 + v * k5 - k6 - 6.f * u * k8;
     const float kv = 6.f * v * k3 - 2.f * v * k4 + u * k5 - k7 - 6.f * v * k8;
 
-    // Force F_i = 3 gbeta (theta - theta_ref)(e_iy - v) w_i P_i,
-    // P_i = 1 - 1.5 |u|^2 + 3 e_i.u + 4.5 (e_i.u)^2 (Eqs. 26-27).
+    // Force derivatives contracted with lam_f.
     const float c3 = 3.f * K.gbeta * (th - K.theta_ref);
-    const int EXs[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-    const int EYs[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const float Ws[9] = {4.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f, 1.f / 9.f,
                          1.f / 36.f, 1.f / 36.f, 1.f / 36.f, 1.f / 36.f};
     float Fu = 0.f, Fv = 0.f, Fp = 0.f;  // Fp = sum lam_i (e_iy - v) w_i P_i
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
-        const float ex = (float)EXs[i], ey = (float)EYs[i];
-        const float eu = ex * u + ey * v;
-        const float P = base + 3.f * eu + 4.5f * eu * eu;
         const float lw = lf[i] * Ws[i];
-        const float dy = ey - v;
-        Fu += lw * dy * (3.f * ex + 9.f * eu * ex - 3.f * u);
-        Fv += lw * (dy * (3.f * ey + 9.f * eu * ey - 3.f * v) - P);
-        Fp += lw * dy * P;
+        Fu += lw * F.fu[i];
+        Fv += lw * F.fv[i];
+        Fp += lw * F.fp[i];
     }
     Fu *= c3;
     Fv *= c3;
@@ -120,37 +155,64 @@ __device__ __forceinline__ void collide_vjp(const float (&f)[9], const float (&g
     ng[4] = lg[4] + e2 - e3 + e4 + cg;
 }
 
-__global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts K) {
-    grid_dep_wait();  // launched programmatically after the previous kernel of the sweep
+__global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, int set, int t, StepConsts K) {
+    // Launched programmatically after the previous reverse step, which writes
+    // neither s_{k-1} (slot t of this graph's set, filled before the replay
+    // began) nor the segment counter (set by the previous replay's fold): both
+    // are read, and the forward half of the local Jacobian computed, before
+    // waiting for that step (grid_dep_wait), so their latency overlaps it.
+    // The addresses of s_{k-1} and of the two adjoint states depend on the set
+    // and t only (K is even), not on the segment. nu_{k+1} is read, and
+    // anything written, after the wait.
     grid_dep_launch();
+    const float* __restrict__ SP = A.slot[set] + t * A.state;  // s_{k-1}, k = qK + t + 1
+    const float* __restrict__ NI = A.nu[(A.N - t - 1) & 1];    // nu_{k+1}
+    float* __restrict__ NO = A.nu[(A.N - t) & 1];              // nu_k
+    const long long q = *A.seg;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     const bool in = i < A.nx;
     const int ic = in ? i : A.nx - 1;
-    const long long PL = A.plane;
+    const int PL = (int)A.plane;  // a whole state has fewer than 2^31 values (checked on the host)
     const int EX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const int OP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     const int OP5[5] = {0, 3, 4, 1, 2};
     const float abb = K.abb;
 
-    if (A.gather_only) {
-        // Anti-bounce-back on the hot wall: q_east(0, j) = abb theta_w(j) - s_west(0, j).
-        if (in && i == 0 && K.left_fixed)
-            A.dthw[j] += (double)abb * (double)__ldg(A.nu_in + plane_g(1) * PL + (long long)j * A.pitch);
-        return;
-    }
-
-    // Offsets within a plane of this node and of its neighbours, and which of
+    // Offsets within a state of this node and of its neighbours, and which of
     // the four sides have a neighbour (the walls lie beyond the others).
-    const long long c0 = (long long)j * A.pitch + ic;
-    const long long P = A.pitch;
+    const int c0 = j * A.pitch + ic;
+    const int P = A.pitch;
     const bool xm = ic > 0, xp = ic + 1 < A.nx, ym = j > 0, yp = j + 1 < A.ny;
     auto inside = [&](int ex, int ey) {
         return (ex > 0 ? xp : ex < 0 ? xm : true) && (ey > 0 ? yp : ey < 0 ? ym : true);
     };
-    const float* __restrict__ NI = A.nu_in;
-    const float* __restrict__ SP = A.s_prev;
+
+    // q_k at this node: the forward pull of s_{k-1} (the neighbour at x - e_m,
+    // or across a wall the wall rule on the node's own opposite).
+    float f[9], g[5];
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+        const bool ok = inside(-EX9[m], -EY9[m]);
+        f[m] = __ldg(SP + (ok ? plane_f(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_f(OP9[m]) * PL + c0));
+    }
+    const float hw = __ldg(A.hot + j), cw = __ldg(A.cold + j);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const bool ok = inside(-EX9[m], -EY9[m]);
+        const float v = __ldg(SP + (ok ? plane_g(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_g(OP5[m]) * PL + c0));
+        if (ok) g[m] = v;
+        else if (EX9[m] > 0 && K.left_fixed) g[m] = abb * hw - v;     // x - e_m < 0
+        else if (EX9[m] < 0 && K.right_fixed) g[m] = abb * cw - v;    // x - e_m >= nx
+        else g[m] = v;
+    }
+
+    const VjpFwd F = vjp_forward(f, g);
+    grid_dep_wait();
+    const long long k = q * A.K + t + 1;  // the forward step reversed here
+    if (k > A.N) return;                  // the last segment may be short
+    const float wk = k > A.w_from ? A.w : 0.f;
 
     // lambda_k: transpose of the pull, gathered from nu_{k+1}: the neighbour at
     // x + e_m, or across a wall the node's own opposite (bounce-back; sign -1
@@ -168,77 +230,93 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, StepConsts
         const bool fixed = !ok && ((EX9[m] < 0 && K.left_fixed) || (EX9[m] > 0 && K.right_fixed));
         lg[m] = fixed ? -val : val;  // anti-bounce-back (Eq. 45) / bounce-back (Eq. 44)
     }
-    // This step's anti-bounce-back term of dJ/dtheta_w(j) (0 for an adiabatic
-    // hot wall): written into the step's own row, summed after the segment in
-    // step order, so no read-modify-write sits at the end of every step.
+    // This step's anti-bounce-back term of dJ/dtheta_w(j) is abb times this
+    // value (0 for an adiabatic hot wall): written into the step's own row and
+    // summed, in float64, after the segment, so neither a read-modify-write nor
+    // a float64 operation sits in every step.
     if (in && i == 0)
-        A.dthw_step[j] = K.left_fixed ? (double)abb * (double)__ldg(NI + plane_g(1) * PL + (long long)j * A.pitch) : 0.0;
-
-    // q_k at this node: the forward pull of s_{k-1} (the neighbour at x - e_m,
-    // or across a wall the wall rule on the node's own opposite).
-    float f[9], g[5];
-#pragma unroll
-    for (int m = 0; m < 9; ++m) {
-        const bool ok = inside(-EX9[m], -EY9[m]);
-        f[m] = __ldg(SP + (ok ? plane_f(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_f(OP9[m]) * PL + c0));
-    }
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-        const bool ok = inside(-EX9[m], -EY9[m]);
-        const float v = __ldg(SP + (ok ? plane_g(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_g(OP5[m]) * PL + c0));
-        if (ok) g[m] = v;
-        else if (EX9[m] > 0 && K.left_fixed) g[m] = abb * __ldg(A.hot + j) - v;     // x - e_m < 0
-        else if (EX9[m] < 0 && K.right_fixed) g[m] = abb * __ldg(A.cold + j) - v;   // x - e_m >= nx
-        else g[m] = v;
-    }
+        A.dthw_step[(size_t)t * A.ny + j] = K.left_fixed ? __ldg(NI + plane_g(1) * PL + j * P) : 0.f;
 
     float nf[9], ng[5], dgb;
-    collide_vjp(f, g, lf, lg, K, nf, ng, dgb);
-    if (A.w != 0.f) {
+    collide_vjp(F, lf, lg, K, nf, ng, dgb);
+    if (wk != 0.f) {
         // Nu(k) = (1/ny) sum_j scale (8 theta_w - 9 theta(0, j) + theta(1, j)), theta = sum g.
-        const float add = i == 0 ? A.w * A.nu_wall : (i == 1 ? A.w * A.nu_next : 0.f);
+        const float add = i == 0 ? wk * A.nu_wall : (i == 1 ? wk * A.nu_next : 0.f);
 #pragma unroll
         for (int m = 0; m < 5; ++m) ng[m] += add;
     }
     if (in) {
-        float* D = A.nu_out + (long long)j * A.pitch + i;
+        float* D = NO + c0;
 #pragma unroll
         for (int m = 0; m < 9; ++m) D[plane_f(m) * PL] = nf[m];
 #pragma unroll
         for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
     }
-    // dJ/dgbeta: each warp's sum in fp64 by a butterfly, written to the warp's
-    // slot of this step; after the segment, each block's four warp sums are
-    // added in order and the result to the block's total in step order
-    // (adjoint_fold_kernel), so every run gives the same bits.
-    // (Each warp writes its own slot; the fold adds a block's four warps in order.)
-    double d = in ? (double)dgb : 0.0;
+    // dJ/dgbeta: each warp's sum by a butterfly in float32 pairs (hi, lo)
+    // carrying the rounding error of every addition (Knuth's two-sum), so the
+    // pair holds the sum to about float64 accuracy without the float64 pipe,
+    // which is slow on this GPU; the pair goes to the warp's slot of this step
+    // and adjoint_fold_kernel adds the slots in a fixed order, so every run
+    // gives the same bits. (Lanes combine commutatively, so every lane ends
+    // with the same pair.)
+    float hi = in ? dgb : 0.f, lo = 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(kFull, d, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(kFull, hi, o), l2 = __shfl_xor_sync(kFull, lo, o);
+        const float sum = hi + h2, bp = sum - hi;
+        const float err = (hi - (sum - bp)) + (h2 - bp);
+        hi = sum;
+        lo = (lo + l2) + err;
+    }
     if ((threadIdx.x & 31) == 0)
-        A.dgbeta_step[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + (threadIdx.x >> 5)] = d;
+        A.dgbeta_step[((size_t)t * A.n_blocks + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + (threadIdx.x >> 5)] =
+            make_float2(hi, lo);
 }
 
-// After a segment's reverse steps: add each step's per-block dJ/dgbeta and per-row
-// dJ/dtheta_w terms to the totals, the segment's last step first (the order in
-// which the steps ran), one thread per slot.
-__global__ void adjoint_fold_kernel(double* __restrict__ dgbeta, const double* __restrict__ dgbeta_steps,
-                                    long long n_blocks, double* __restrict__ dthw,
-                                    const double* __restrict__ dthw_steps, int ny, int len) {
-    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (q < n_blocks) {
-        double acc = dgbeta[q];
-        for (int t = len - 1; t >= 0; --t) {
-            const double* w = dgbeta_steps + ((size_t)t * n_blocks + q) * 4;  // the block's four warps
-            acc += ((w[0] + w[1]) + w[2]) + w[3];
+// After a segment's reverse steps: add the segment's dJ/dgbeta terms (per block
+// of the step grid) and dJ/dtheta_w terms (per row) to the totals, in float64,
+// one warp per slot: lane l sums the steps t = l, l + 32, ... in turn, a
+// butterfly adds the lanes, and lane 0 adds the result to the total; then the
+// next segment goes to the other graph's counter. Fixed order, same bits on
+// every run.
+constexpr int kFoldThreads = 256;
+
+__global__ void __launch_bounds__(kFoldThreads) adjoint_fold_kernel(AdjArgs A, StepConsts K) {
+    const long long q = *A.seg;
+    const int len = (int)min(A.K, A.N - q * A.K);
+    const long long s = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s < A.n_blocks + A.ny) {
+        double acc = 0.0;
+        if (s < A.n_blocks) {
+#pragma unroll 4
+            for (int t = lane; t < len; t += 32) {
+                const float2* w = A.dgbeta_step + ((size_t)t * A.n_blocks + s) * 4;  // the block's four warps
+                const float2 w0 = w[0], w1 = w[1], w2 = w[2], w3 = w[3];
+                acc += (((double)w0.x + (double)w0.y) + ((double)w1.x + (double)w1.y)) +
+                       (((double)w2.x + (double)w2.y) + ((double)w3.x + (double)w3.y));
+            }
+        } else {
+            const long long r = s - A.n_blocks;
+#pragma unroll 4
+            for (int t = lane; t < len; t += 32) acc += (double)K.abb * (double)A.dthw_step[(size_t)t * A.ny + r];
         }
-        dgbeta[q] = acc;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+        if (lane == 0) {
+            if (s < A.n_blocks) A.dgbeta[s] += acc;
+            else A.dthw[s - A.n_blocks] += acc;
+        }
     }
-    if (q < ny) {
-        double acc = dthw[q];
-        for (int t = len - 1; t >= 0; --t) acc += dthw_steps[(size_t)t * ny + q];
-        dthw[q] = acc;
-    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *A.seg_next = q - 1;
+}
+
+// The anti-bounce-back term of step 1 (after the sweep): q_east(0, j) =
+// abb theta_w(j) - s_west(0, j) feeds dJ/dtheta_w(j) with abb nu_1[g east](0, j).
+__global__ void adjoint_gather_kernel(AdjArgs A, StepConsts K) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < A.ny && K.left_fixed)
+        A.dthw[j] += (double)K.abb * (double)A.nu[A.N & 1][plane_g(1) * A.plane + (long long)j * A.pitch];
 }
 
 }  // namespace dmrt

@@ -2614,6 +2614,7 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     if (L.K < 1) L.K = 1;
     // Segments of whole step graphs, so that the forward pass replays graphs only.
     if (L.K > c->graph_len) L.K = (L.K + c->graph_len - 1) / c->graph_len * c->graph_len;
+    L.K += L.K & 1;  // even, so that a step's adjoint buffers do not depend on its segment
     L.C = (N + L.K - 1) / L.K;
     L.state = align256((size_t)kPlanes * (size_t)c->L.plane * sizeof(float));
     size_t o = 0;
@@ -2624,8 +2625,8 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_dgb = o; o += align256((size_t)L.n_blocks * sizeof(double));
     L.off_misc = o; o += 256;
     L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
-    L.off_sdgb = o; o += align256((size_t)L.K * L.n_blocks * 4 * sizeof(double));  // per step and warp
-    L.off_sdthw = o; o += align256((size_t)L.K * c->p.ny * sizeof(double));
+    L.off_sdgb = o; o += align256((size_t)L.K * L.n_blocks * 4 * sizeof(float2));  // per step and warp
+    L.off_sdthw = o; o += align256((size_t)L.K * c->p.ny * sizeof(float));
     L.off_ckpt = o; o += (size_t)L.C * L.state;
     L.off_seg[0] = o; o += (size_t)L.K * L.state;
     L.total_seq = o;
@@ -2668,6 +2669,11 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     if (avg_last > c->p.nu_capacity) {
         set_err(c, "nu_capacity (%lld) must hold the %lld averaged steps", (long long)c->p.nu_capacity,
                 (long long)avg_last);
+        return DMRT_E_ARG;
+    }
+    if ((size_t)kPlanes * (size_t)c->L.plane >= ((size_t)1 << 31)) {
+        set_err(c, "the adjoint indexes a state with 32-bit offsets: %lld values per state is too many",
+                (long long)kPlanes * (long long)c->L.plane);
         return DMRT_E_ARG;
     }
     const AdjLayout AL = adjoint_layout(c, nsteps);
@@ -2716,8 +2722,8 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     float* nu_a = reinterpret_cast<float*>(w + AL.off_nu0);
     float* nu_b = reinterpret_cast<float*>(w + AL.off_nu1);
     double* dthw = reinterpret_cast<double*>(w + AL.off_dthw);
-    double* sdgb = reinterpret_cast<double*>(w + AL.off_sdgb);
-    double* sdthw = reinterpret_cast<double*>(w + AL.off_sdthw);
+    float2* sdgb = reinterpret_cast<float2*>(w + AL.off_sdgb);
+    float* sdthw = reinterpret_cast<float*>(w + AL.off_sdthw);
     Misc* scratch = reinterpret_cast<Misc*>(w + AL.off_misc);
     CK(cudaMemsetAsync(nu_a, 0, copy_bytes, c->stream), "zero adjoint");
     CK(cudaMemsetAsync(w + AL.off_dthw, 0, AL.off_rows - AL.off_dthw, c->stream), "zero gradients");
@@ -2731,18 +2737,81 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     RA.step_in = &scratch->step[0];
     RA.step_out = &scratch->step[1];
     RA.cap = 1;
+    long long* seg_ctr = reinterpret_cast<long long*>(w + AL.off_misc + 128);  // the graphs' segment counters
     dmrt::AdjArgs AA;
+    std::memset(&AA, 0, sizeof AA);
+    AA.slot[0] = slot(0, 0);
+    AA.slot[1] = overlap ? slot(1, 0) : slot(0, 0);
+    AA.nu[0] = nu_a;  // nu_{N+1} = 0
+    AA.nu[1] = nu_b;
     AA.hot = reinterpret_cast<const float*>(c->ws + c->L.off_hot);
     AA.cold = reinterpret_cast<const float*>(c->ws + c->L.off_cold);
     AA.dthw = dthw;
+    AA.dgbeta = dgb;
+    AA.dthw_step = sdthw;
+    AA.dgbeta_step = sdgb;
+    AA.state = (long long)(AL.state / sizeof(float));
+    AA.K = K;
+    AA.N = N;
+    AA.C = AL.C;
+    AA.w_from = N - avg_last;
+    AA.n_blocks = AL.n_blocks;
     AA.plane = c->L.plane;
+    AA.nsets = overlap ? 2 : 1;
     AA.nx = c->p.nx;
     AA.ny = c->p.ny;
     AA.pitch = c->L.pitch;
+    AA.w = (float)(1.0 / (double)avg_last);
     AA.nu_wall = (float)(-9.0 * c->sc.nu_scale / c->p.ny);
     AA.nu_next = (float)(c->sc.nu_scale / c->p.ny);
-    AA.gather_only = 0;
     const dim3 agrid((c->p.nx + 127) / 128, c->p.ny);
+    // The reverse sweep of a segment: one graph of K step nodes (programmatic
+    // edges) and the fold; graph p reads counter p and leaves the next segment
+    // in counter 1 - p, so replays alternate between the two.
+    struct Execs {
+        cudaGraphExec_t e[2] = {nullptr, nullptr};
+        ~Execs() {
+            for (cudaGraphExec_t x : e)
+                if (x) cudaGraphExecDestroy(x);
+        }
+    } rg;
+    for (int gp = 0; gp < 2; ++gp) {
+        dmrt::AdjArgs Ap = AA;
+        Ap.seg = seg_ctr + gp;
+        Ap.seg_next = seg_ctr + (gp ^ 1);
+        cudaGraph_t g;
+        CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
+        cudaGraphNode_t prev = nullptr;
+        cudaError_t e = cudaSuccess;
+        for (long long i = 0; i < K && e == cudaSuccess; ++i) {
+            int set = gp, t = (int)(K - 1 - i);  // the segment's last step first
+            void* params[4] = {&Ap, &set, &t, &c->sc};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void*)dmrt::adjoint_step_kernel;
+            kp.gridDim = agrid;
+            kp.blockDim = dim3(128);
+            kp.kernelParams = params;
+            cudaGraphNode_t node;
+            e = add_step_node(g, prev, &kp, &node);
+            prev = node;
+        }
+        if (e == cudaSuccess) {
+            const long long warps = AL.n_blocks + c->p.ny, per = dmrt::kFoldThreads / 32;
+            void* params[2] = {&Ap, &c->sc};
+            cudaKernelNodeParams kp = {};
+            kp.func = (void*)dmrt::adjoint_fold_kernel;
+            kp.gridDim = dim3((unsigned)((warps + per - 1) / per));
+            kp.blockDim = dim3(dmrt::kFoldThreads);
+            kp.kernelParams = params;
+            cudaGraphNode_t node;
+            e = cudaGraphAddKernelNode(&node, g, &prev, 1, &kp);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&rg.e[gp], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(c, e, "adjoint graph");
+    }
+    const long long q_last = AL.C - 1;
+    CK(cudaMemcpyAsync(seg_ctr, &q_last, sizeof q_last, cudaMemcpyHostToDevice, c->stream), "segment counter");
     // The segment recompute runs the context's own step kernel. For the TMA
     // kernel every checkpoint and segment slot it reads gets its load maps
     // (float32 storage stores from registers, so no store maps are needed).
@@ -2765,9 +2834,11 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     int ccs = 0, ccr = 0, cct = 0;
     size_t ccm = 0;
     const bool cluster_re = overlap && cluster_fit(c, &ccs, &ccr, &cct, &ccm);
-    // Recompute of segment q into slot set `set` on stream rs: s_{start + t} into slot t.
+    // Recompute of segment q into slot set `set` on stream rs: s_{start + t} into slot t
+    // (slot 0: a copy of the checkpoint).
     auto recompute = [&](long long q, int set) -> int {
         const long long start = q * K, len = std::min(start + K, N) - start;
+        CK(cudaMemcpyAsync(slot(set, 0), ckpt(q), copy_bytes, cudaMemcpyDeviceToDevice, rs), "segment start");
         if (cluster_re && len > 1) {
             dmrt::ClusterArgs CA;
             CA.A[0] = CA.A[1] = step_args(c, 0);
@@ -2821,7 +2892,6 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     if (overlap) CK(cudaEventRecord(c->ev[1], rs), "event");
     for (long long q = AL.C - 1; q >= 0; --q) {
         const int set = (int)((AL.C - 1 - q) & 1) % nsets;
-        const long long start = q * K, end = std::min(start + K, N), len = end - start;
         if (overlap && q >= 1) {
             // Segment q - 1 into the other set, once the sweep that last read it is done.
             if (q + 1 <= AL.C - 1) CK(cudaStreamWaitEvent(rs, c->ev[3 + (set ^ 1)], 0), "wait");
@@ -2830,31 +2900,14 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
             CK(cudaEventRecord(c->ev[1 + (set ^ 1)], rs), "event");
         }
         if (overlap) CK(cudaStreamWaitEvent(c->stream, c->ev[1 + set], 0), "wait");
-        for (long long k = end; k > start; --k) {
-            const long long t = k - start - 1;  // the step's row of partials
-            AA.s_prev = (k - 1 == start) ? ckpt(q) : slot(set, k - 1 - start);
-            AA.nu_in = nu_a;
-            AA.nu_out = nu_b;
-            AA.dgbeta_step = sdgb + (size_t)t * AL.n_blocks * 4;
-            AA.dthw_step = sdthw + (size_t)t * c->p.ny;
-            AA.w = (k > N - avg_last) ? (float)(1.0 / (double)avg_last) : 0.f;
-            CK(launch_overlapped(dmrt::adjoint_step_kernel, agrid, dim3(128), c->stream, AA, c->sc),
-               "adjoint step launch");
-            std::swap(nu_a, nu_b);
-        }
-        const long long nf = std::max<long long>(AL.n_blocks, c->p.ny);
-        dmrt::adjoint_fold_kernel<<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(
-            dgb, sdgb, AL.n_blocks, dthw, sdthw, c->p.ny, (int)len);
-        CK(cudaGetLastError(), "adjoint launch");
+        CK(cudaGraphLaunch(rg.e[(AL.C - 1 - q) & 1], c->stream), "adjoint sweep launch");
         if (overlap) CK(cudaEventRecord(c->ev[3 + set], c->stream), "event");
         if (!overlap && q >= 1) {
             rc = recompute(q - 1, 0);
             if (rc) return rc;
         }
     }
-    AA.nu_in = nu_a;  // nu_1: the anti-bounce-back term of step 1
-    AA.gather_only = 1;
-    dmrt::adjoint_step_kernel<<<agrid, 128, 0, c->stream>>>(AA, c->sc);
+    dmrt::adjoint_gather_kernel<<<(c->p.ny + 127) / 128, 128, 0, c->stream>>>(AA, c->sc);
     CK(cudaGetLastError(), "adjoint launch");
     std::vector<double> g((size_t)c->p.ny);
     std::vector<double> slots((size_t)AL.n_blocks);
