@@ -28,21 +28,22 @@
 namespace dmrt {
 
 // The reverse sweep of a segment of K steps (K even) replays one of two
-// graphs, each of K step nodes and a fold node; graph s serves the segments
-// whose recomputed states sit in slot set s, so a node's addresses depend on s
-// and on t, the step within the segment, only. The segment q itself comes from
-// a device counter (graph s reads counter s; its fold leaves q - 1 in the
-// other), needed only for the averaging weight and to skip the missing steps
-// of a short last segment.
+// graphs, each of K / 2 pair nodes (reverse steps k and k - 1 in one launch)
+// and a fold node; graph s serves the segments whose recomputed states sit in
+// slot set s, so a node's pre-wait addresses depend on s and on t, the step
+// within the segment, only. The segment q itself comes from a device counter
+// (graph s reads counter s; its fold leaves q - 1 in the other), needed after
+// the wait: for the adjoint buffers, the averaging weight and to skip the
+// missing steps of a short last segment.
 struct AdjArgs {
     const long long* seg;              // the segment q swept by this replay
     long long* seg_next;               // the fold writes q - 1 here (the other graph's counter)
     const float* slot[2];              // set s: s_{qK+t} at slot[s] + t * state (t = 0: the checkpoint's copy)
-    float* nu[2];                      // adjoint states: step k reads nu[(N - k) & 1], writes the other
+    float* nu[2];                      // adjoint states: pair P reads nu[P & 1], writes the other
     const float* __restrict__ hot;
     const float* __restrict__ cold;
     double* dthw;                      // [ny] dJ/dtheta_w totals
-    double* dgbeta;                    // [n_blocks] dJ/dgbeta totals, one per block of the step grid
+    double* dgbeta;                    // [n_blocks] dJ/dgbeta totals, one per tile (block of the step grid)
     float* dthw_step;                  // [K][ny] nu_{k+1}[g east](0, j) by step (0: adiabatic hot wall)
     float2* dgbeta_step;               // [K][n_blocks][4] the segment's dJ/dgbeta by step and warp, as (hi, lo)
     long long state;                   // floats in one state
@@ -52,6 +53,7 @@ struct AdjArgs {
     long long plane;
     int nsets;                         // slot sets: with 2, segment q uses set (C - 1 - q) & 1
     int nx, ny, pitch;
+    int tw, hx;                        // output columns per tile and halo columns (1 when nx > 128, else 0)
     float w;                           // w_k inside the averaging window
     float nu_wall, nu_next;            // dNu/dtheta at columns 0 and 1, divided by ny
 };
@@ -155,111 +157,91 @@ __device__ __forceinline__ void collide_vjp(const VjpFwd& F, const float (&lf)[9
     ng[4] = lg[4] + e2 - e3 + e4 + cg;
 }
 
-__global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, int set, int t, StepConsts K) {
-    // Launched programmatically after the previous reverse step, which writes
-    // neither s_{k-1} (slot t of this graph's set, filled before the replay
-    // began) nor the segment counter (set by the previous replay's fold): both
-    // are read, and the forward half of the local Jacobian computed, before
-    // waiting for that step (grid_dep_wait), so their latency overlaps it.
-    // The addresses of s_{k-1} and of the two adjoint states depend on the set
-    // and t only (K is even), not on the segment. nu_{k+1} is read, and
-    // anything written, after the wait.
-    grid_dep_launch();
-    const float* __restrict__ SP = A.slot[set] + t * A.state;  // s_{k-1}, k = qK + t + 1
-    const float* __restrict__ NI = A.nu[(A.N - t - 1) & 1];    // nu_{k+1}
-    float* __restrict__ NO = A.nu[(A.N - t) & 1];              // nu_k
-    const long long q = *A.seg;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    const bool in = i < A.nx;
-    const int ic = in ? i : A.nx - 1;
-    const int PL = (int)A.plane;  // a whole state has fewer than 2^31 values (checked on the host)
+// A node of the reverse step: its column i, row j, offset within a plane,
+// whether it lies inside the cavity, and which of its four sides have a
+// neighbour (the walls lie beyond the others).
+struct AdjNode {
+    int i, j, c0;
+    bool in, xm, xp, ym, yp;
+    __device__ __forceinline__ bool inside(int ex, int ey) const {
+        return (ex > 0 ? xp : ex < 0 ? xm : true) && (ey > 0 ? yp : ey < 0 ? ym : true);
+    }
+};
+
+// Column i (clamped to the last column when outside), row j (inside).
+__device__ __forceinline__ AdjNode adj_node(const AdjArgs& A, int i, int j) {
+    AdjNode n;
+    n.i = i;
+    n.j = j;
+    n.in = i < A.nx;
+    const int ic = n.in ? i : A.nx - 1;
+    n.c0 = j * A.pitch + ic;  // a whole state has fewer than 2^31 values (checked on the host)
+    n.xm = ic > 0;
+    n.xp = ic + 1 < A.nx;
+    n.ym = j > 0;
+    n.yp = j + 1 < A.ny;
+    return n;
+}
+
+// q_k at the node: the forward pull of s_{k-1} (the neighbour at x - e_m, or
+// across a wall the wall rule on the node's own opposite).
+__device__ __forceinline__ void adj_pull(const float* __restrict__ SP, const AdjNode& n, const AdjArgs& A,
+                                         const StepConsts& K, float (&f)[9], float (&g)[5]) {
     const int EX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     const int OP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
     const int OP5[5] = {0, 3, 4, 1, 2};
-    const float abb = K.abb;
-
-    // Offsets within a state of this node and of its neighbours, and which of
-    // the four sides have a neighbour (the walls lie beyond the others).
-    const int c0 = j * A.pitch + ic;
-    const int P = A.pitch;
-    const bool xm = ic > 0, xp = ic + 1 < A.nx, ym = j > 0, yp = j + 1 < A.ny;
-    auto inside = [&](int ex, int ey) {
-        return (ex > 0 ? xp : ex < 0 ? xm : true) && (ey > 0 ? yp : ey < 0 ? ym : true);
-    };
-
-    // q_k at this node: the forward pull of s_{k-1} (the neighbour at x - e_m,
-    // or across a wall the wall rule on the node's own opposite).
-    float f[9], g[5];
+    const int PL = (int)A.plane, P = A.pitch, c0 = n.c0;
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
-        const bool ok = inside(-EX9[m], -EY9[m]);
+        const bool ok = n.inside(-EX9[m], -EY9[m]);
         f[m] = __ldg(SP + (ok ? plane_f(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_f(OP9[m]) * PL + c0));
     }
-    const float hw = __ldg(A.hot + j), cw = __ldg(A.cold + j);
+    const float hw = __ldg(A.hot + n.j), cw = __ldg(A.cold + n.j);
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        const bool ok = inside(-EX9[m], -EY9[m]);
+        const bool ok = n.inside(-EX9[m], -EY9[m]);
         const float v = __ldg(SP + (ok ? plane_g(m) * PL + c0 - EX9[m] - EY9[m] * P : plane_g(OP5[m]) * PL + c0));
         if (ok) g[m] = v;
-        else if (EX9[m] > 0 && K.left_fixed) g[m] = abb * hw - v;     // x - e_m < 0
-        else if (EX9[m] < 0 && K.right_fixed) g[m] = abb * cw - v;    // x - e_m >= nx
+        else if (EX9[m] > 0 && K.left_fixed) g[m] = K.abb * hw - v;   // x - e_m < 0
+        else if (EX9[m] < 0 && K.right_fixed) g[m] = K.abb * cw - v;  // x - e_m >= nx
         else g[m] = v;
     }
+}
 
-    const VjpFwd F = vjp_forward(f, g);
-    grid_dep_wait();
-    const long long k = q * A.K + t + 1;  // the forward step reversed here
-    if (k > A.N) return;                  // the last segment may be short
-    const float wk = k > A.w_from ? A.w : 0.f;
-
-    // lambda_k: transpose of the pull, gathered from nu_{k+1}: the neighbour at
-    // x + e_m, or across a wall the node's own opposite (bounce-back; sign -1
-    // for anti-bounce-back of g).
-    float lf[9], lg[5];
+// lambda_k: the transpose of the pull, gathered from nu_{k+1} in global
+// memory: the neighbour at x + e_m, or across a wall the node's own opposite
+// (bounce-back; sign -1 for anti-bounce-back of g).
+__device__ __forceinline__ void adj_gather(const float* __restrict__ NI, const AdjNode& n, const AdjArgs& A,
+                                           const StepConsts& K, float (&lf)[9], float (&lg)[5]) {
+    const int EX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int OP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const int OP5[5] = {0, 3, 4, 1, 2};
+    const int PL = (int)A.plane, P = A.pitch, c0 = n.c0;
 #pragma unroll
     for (int m = 0; m < 9; ++m) {
-        const bool ok = inside(EX9[m], EY9[m]);
+        const bool ok = n.inside(EX9[m], EY9[m]);
         lf[m] = __ldg(NI + (ok ? plane_f(m) * PL + c0 + EX9[m] + EY9[m] * P : plane_f(OP9[m]) * PL + c0));
     }
 #pragma unroll
     for (int m = 0; m < 5; ++m) {
-        const bool ok = inside(EX9[m], EY9[m]);
+        const bool ok = n.inside(EX9[m], EY9[m]);
         const float val = __ldg(NI + (ok ? plane_g(m) * PL + c0 + EX9[m] + EY9[m] * P : plane_g(OP5[m]) * PL + c0));
         const bool fixed = !ok && ((EX9[m] < 0 && K.left_fixed) || (EX9[m] > 0 && K.right_fixed));
         lg[m] = fixed ? -val : val;  // anti-bounce-back (Eq. 45) / bounce-back (Eq. 44)
     }
-    // This step's anti-bounce-back term of dJ/dtheta_w(j) is abb times this
-    // value (0 for an adiabatic hot wall): written into the step's own row and
-    // summed, in float64, after the segment, so neither a read-modify-write nor
-    // a float64 operation sits in every step.
-    if (in && i == 0)
-        A.dthw_step[(size_t)t * A.ny + j] = K.left_fixed ? __ldg(NI + plane_g(1) * PL + j * P) : 0.f;
+}
 
-    float nf[9], ng[5], dgb;
-    collide_vjp(F, lf, lg, K, nf, ng, dgb);
-    if (wk != 0.f) {
-        // Nu(k) = (1/ny) sum_j scale (8 theta_w - 9 theta(0, j) + theta(1, j)), theta = sum g.
-        const float add = i == 0 ? wk * A.nu_wall : (i == 1 ? wk * A.nu_next : 0.f);
-#pragma unroll
-        for (int m = 0; m < 5; ++m) ng[m] += add;
-    }
-    if (in) {
-        float* D = NO + c0;
-#pragma unroll
-        for (int m = 0; m < 9; ++m) D[plane_f(m) * PL] = nf[m];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
-    }
-    // dJ/dgbeta: each warp's sum by a butterfly in float32 pairs (hi, lo)
-    // carrying the rounding error of every addition (Knuth's two-sum), so the
-    // pair holds the sum to about float64 accuracy without the float64 pipe,
-    // which is slow on this GPU; the pair goes to the warp's slot of this step
-    // and adjoint_fold_kernel adds the slots in a fixed order, so every run
-    // gives the same bits. (Lanes combine commutatively, so every lane ends
-    // with the same pair.)
-    float hi = in ? dgb : 0.f, lo = 0.f;
+// dJ/dgbeta: each warp's sum by a butterfly in float32 pairs (hi, lo) carrying
+// the rounding error of every addition (Knuth's two-sum), so the pair holds the
+// sum to about float64 accuracy without the float64 pipe, which is slow on this
+// GPU; the pair goes to the slot of step t, tile `tile` and the warp's place in
+// its 128-lane row, and adjoint_fold_kernel adds the slots in a fixed order, so
+// every run gives the same bits. (Lanes combine commutatively, so every lane
+// ends with the same pair.)
+__device__ __forceinline__ void adj_dgb_store(float dgb, int t, long long tile, const AdjArgs& A) {
+    float hi = dgb, lo = 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const float h2 = __shfl_xor_sync(kFull, hi, o), l2 = __shfl_xor_sync(kFull, lo, o);
@@ -269,8 +251,140 @@ __global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, int set, i
         lo = (lo + l2) + err;
     }
     if ((threadIdx.x & 31) == 0)
-        A.dgbeta_step[((size_t)t * A.n_blocks + (size_t)blockIdx.y * gridDim.x + blockIdx.x) * 4 + (threadIdx.x >> 5)] =
-            make_float2(hi, lo);
+        A.dgbeta_step[((size_t)t * A.n_blocks + tile) * 4 + ((threadIdx.x >> 5) & 3)] = make_float2(hi, lo);
+}
+
+// ---- two reverse steps per launch ---------------------------------------------
+// Pair node: reverse steps k_hi = qK + th + 1 and k_lo = k_hi - 1 (th odd) of a
+// tile of tw columns of row j. Step k_hi runs at rows j - 1, j, j + 1 and at
+// the tile's columns plus hx halo columns on each side (384 threads: 128
+// lanes by 3 rows), with nu_{k_hi + 1} gathered from global memory; its
+// output nu_{k_hi} stays in shared memory, where step k_lo (the middle row's
+// output lanes) gathers it; only nu_{k_lo} goes to global memory. So the
+// launch boundary, and its dependency wait, comes once every two steps, at
+// the price of computing step k_hi on the halo as well. Pair P (P-th of the
+// sweep, counted from the end) reads nu[P & 1] and writes nu[(P + 1) & 1].
+// When the last segment has an odd length its first pair begins with the
+// step after the last (k_hi = N + 1): that step is skipped and its output is
+// nu_{N+1} = 0.
+constexpr int kPairThreads = 384;
+
+__device__ __forceinline__ int pair_smem_index(int row, int plane, int lane) { return (row * kPlanes + plane) * 128 + lane; }
+
+// lambda at the middle-row node (lane l) gathered from nu_{k_hi} in shared memory.
+__device__ __forceinline__ void adj_gather_smem(const float* __restrict__ S, int l, const AdjNode& n,
+                                                const StepConsts& K, float (&lf)[9], float (&lg)[5]) {
+    const int EX9[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int EY9[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const int OP9[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const int OP5[5] = {0, 3, 4, 1, 2};
+#pragma unroll
+    for (int m = 0; m < 9; ++m) {
+        const bool ok = n.inside(EX9[m], EY9[m]);
+        lf[m] = S[ok ? pair_smem_index(1 + EY9[m], plane_f(m), l + EX9[m]) : pair_smem_index(1, plane_f(OP9[m]), l)];
+    }
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+        const bool ok = n.inside(EX9[m], EY9[m]);
+        const float val =
+            S[ok ? pair_smem_index(1 + EY9[m], plane_g(m), l + EX9[m]) : pair_smem_index(1, plane_g(OP5[m]), l)];
+        const bool fixed = !ok && ((EX9[m] < 0 && K.left_fixed) || (EX9[m] > 0 && K.right_fixed));
+        lg[m] = fixed ? -val : val;  // anti-bounce-back (Eq. 45) / bounce-back (Eq. 44)
+    }
+}
+
+// nu_k at a node from lambda_k and the forward half, with the Nusselt source
+// of step k (weight wk) on columns 0 and 1; returns the node's dJ/dgbeta term.
+__device__ __forceinline__ float adj_node_step(const VjpFwd& F, const float (&lf)[9], const float (&lg)[5],
+                                               const AdjNode& n, float wk, const AdjArgs& A, const StepConsts& K,
+                                               float (&nf)[9], float (&ng)[5]) {
+    float dgb;
+    collide_vjp(F, lf, lg, K, nf, ng, dgb);
+    if (wk != 0.f) {
+        // Nu(k) = (1/ny) sum_j scale (8 theta_w - 9 theta(0, j) + theta(1, j)), theta = sum g.
+        const float add = n.i == 0 ? wk * A.nu_wall : (n.i == 1 ? wk * A.nu_next : 0.f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) ng[m] += add;
+    }
+    return dgb;
+}
+
+__global__ void __launch_bounds__(kPairThreads) adjoint_pair_kernel(AdjArgs A, int set, int th, StepConsts K) {
+    // Launched programmatically after the previous pair, which writes neither
+    // s_{k_hi - 1}, s_{k_lo - 1} (slots th, th - 1 of this graph's set, filled
+    // before the replay began) nor the segment counter (set by the previous
+    // replay's fold): these are read, and the forward halves computed, before
+    // waiting for that pair (grid_dep_wait), so their latency overlaps it.
+    // nu is read, and anything written, after the wait.
+    __shared__ float S[3 * kPlanes * 128];
+    grid_dep_launch();
+    const int tid = threadIdx.x, l = tid & 127, rr = tid >> 7;  // lane; row j - 1, j, j + 1
+    const int j = blockIdx.y, jr = j + rr - 1;
+    const int x = blockIdx.x * A.tw - A.hx + l;
+    const bool col_ok = x >= 0 && x < A.nx;
+    const bool act = col_ok && jr >= 0 && jr < A.ny;                 // step k_hi here
+    const bool out = rr == 1 && col_ok && l >= A.hx && l < A.hx + A.tw;  // step k_lo here
+    const AdjNode n = adj_node(A, col_ok ? x : A.nx, act ? jr : j);      // (x, jr); clamped when inactive
+    VjpFwd F1, F2;
+    {
+        float f[9], g[5];
+        adj_pull(A.slot[set] + th * A.state, n, A, K, f, g);  // s_{k_hi - 1}
+        F1 = vjp_forward(f, g);
+        if (out) {
+            adj_pull(A.slot[set] + (th - 1) * A.state, n, A, K, f, g);  // s_{k_lo - 1}
+            F2 = vjp_forward(f, g);
+        }
+    }
+    const long long q = *A.seg;
+    grid_dep_wait();
+    const long long k_hi = q * A.K + th + 1, k_lo = k_hi - 1;
+    if (k_lo > A.N) return;  // the last segment may be short
+    const long long P = (A.N + 1 - k_hi) / 2;
+    const float* __restrict__ NI = A.nu[P & 1];  // nu_{k_hi + 1}
+    float* __restrict__ NO = A.nu[(P + 1) & 1];  // nu_{k_lo}
+    const int PL = (int)A.plane;
+    const long long tile = (long long)blockIdx.y * gridDim.x + blockIdx.x;
+    const bool hi_real = k_hi <= A.N;
+
+    // Step k_hi on the 3-row window: nu_{k_hi} into shared memory.
+    float dgb1 = 0.f;
+    if (act) {
+        float nf[9], ng[5];
+        if (hi_real) {
+            float lf[9], lg[5];
+            adj_gather(NI, n, A, K, lf, lg);
+            dgb1 = adj_node_step(F1, lf, lg, n, k_hi > A.w_from ? A.w : 0.f, A, K, nf, ng);
+            if (out && x == 0)
+                A.dthw_step[(size_t)th * A.ny + j] = K.left_fixed ? __ldg(NI + plane_g(1) * PL + j * A.pitch) : 0.f;
+        } else {
+#pragma unroll
+            for (int m = 0; m < 9; ++m) nf[m] = 0.f;  // nu_{N+1} = 0
+#pragma unroll
+            for (int m = 0; m < 5; ++m) ng[m] = 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < 9; ++m) S[pair_smem_index(rr, plane_f(m), l)] = nf[m];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) S[pair_smem_index(rr, plane_g(m), l)] = ng[m];
+    }
+    __syncthreads();
+    if (rr != 1) return;  // the halo rows are done
+
+    // Step k_lo at the middle row's output lanes: nu_{k_lo} to global memory.
+    float dgb2 = 0.f;
+    if (out) {
+        float lf[9], lg[5], nf[9], ng[5];
+        adj_gather_smem(S, l, n, K, lf, lg);
+        dgb2 = adj_node_step(F2, lf, lg, n, k_lo > A.w_from ? A.w : 0.f, A, K, nf, ng);
+        if (x == 0) A.dthw_step[(size_t)(th - 1) * A.ny + j] = K.left_fixed ? S[pair_smem_index(1, plane_g(1), l)] : 0.f;
+        float* D = NO + n.c0;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) D[plane_f(m) * PL] = nf[m];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
+    }
+    if (hi_real) adj_dgb_store(out ? dgb1 : 0.f, th, tile, A);
+    adj_dgb_store(dgb2, th - 1, tile, A);
 }
 
 // After a segment's reverse steps: add the segment's dJ/dgbeta terms (per block
@@ -313,10 +427,11 @@ __global__ void __launch_bounds__(kFoldThreads) adjoint_fold_kernel(AdjArgs A, S
 
 // The anti-bounce-back term of step 1 (after the sweep): q_east(0, j) =
 // abb theta_w(j) - s_west(0, j) feeds dJ/dtheta_w(j) with abb nu_1[g east](0, j).
+// nu_1 is the output of the sweep's last pair, P = (N - 1) / 2.
 __global__ void adjoint_gather_kernel(AdjArgs A, StepConsts K) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < A.ny && K.left_fixed)
-        A.dthw[j] += (double)K.abb * (double)A.nu[A.N & 1][plane_g(1) * A.plane + (long long)j * A.pitch];
+    const float* nu1 = A.nu[((A.N - 1) / 2 + 1) & 1];
+    if (j < A.ny && K.left_fixed) A.dthw[j] += (double)K.abb * (double)nu1[plane_g(1) * A.plane + (long long)j * A.pitch];
 }
 
 }  // namespace dmrt

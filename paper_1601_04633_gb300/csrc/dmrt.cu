@@ -2608,6 +2608,11 @@ struct AdjLayout {
     long long n_blocks;  // blocks of the reverse-step grid: one dJ/dgbeta slot each
 };
 
+// The reverse sweep's tiles: one per row when nx <= 128 (no halo columns),
+// else tiles of 126 columns computed with one halo column on each side.
+int adj_tile_width(int nx) { return nx <= 128 ? nx : 126; }
+int adj_tiles_x(int nx) { return (nx + adj_tile_width(nx) - 1) / adj_tile_width(nx); }
+
 AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     AdjLayout L;
     L.K = (long long)std::ceil(std::sqrt((double)N));
@@ -2621,7 +2626,7 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_nu0 = o; o += L.state;
     L.off_nu1 = o; o += L.state;
     L.off_dthw = o; o += align256((size_t)c->p.ny * sizeof(double));
-    L.n_blocks = (long long)((c->p.nx + 127) / 128) * c->p.ny;
+    L.n_blocks = (long long)adj_tiles_x(c->p.nx) * c->p.ny;
     L.off_dgb = o; o += align256((size_t)L.n_blocks * sizeof(double));
     L.off_misc = o; o += 256;
     L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
@@ -2699,24 +2704,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     };
     const size_t copy_bytes = (size_t)kPlanes * (size_t)c->L.plane * sizeof(float);
     const long long N = nsteps, K = AL.K;
-
-    // Forward pass with checkpoints every K steps; J from the Nusselt ring.
-    CK(cudaMemcpyAsync(ckpt(0), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
-    for (long long q = 0; q < AL.C; ++q) {
-        const long long n = std::min(K, N - q * K);
-        int rc = step_run(c, n, q + 1 == AL.C);  // the last segment sums its last step's rows
-        if (rc) return rc;
-        if (q + 1 < AL.C)
-            CK(cudaMemcpyAsync(ckpt(q + 1), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream),
-               "checkpoint");
-    }
-    std::vector<double> series((size_t)avg_last);
-    int64_t got = 0;
-    int rc = dmrt_nusselt(c, nullptr, nullptr, series.data(), avg_last, &got);
-    if (rc) return rc;
-    double jsum = 0.0;
-    for (int64_t q = 0; q < got; ++q) jsum += series[(size_t)q];
-    if (J) *J = jsum / (double)avg_last;
+    int rc = DMRT_OK;
 
     // Reverse sweep, segment by segment from the last.
     float* nu_a = reinterpret_cast<float*>(w + AL.off_nu0);
@@ -2764,10 +2752,12 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     AA.w = (float)(1.0 / (double)avg_last);
     AA.nu_wall = (float)(-9.0 * c->sc.nu_scale / c->p.ny);
     AA.nu_next = (float)(c->sc.nu_scale / c->p.ny);
-    const dim3 agrid((c->p.nx + 127) / 128, c->p.ny);
-    // The reverse sweep of a segment: one graph of K step nodes (programmatic
-    // edges) and the fold; graph p reads counter p and leaves the next segment
-    // in counter 1 - p, so replays alternate between the two.
+    AA.tw = adj_tile_width(c->p.nx);
+    AA.hx = c->p.nx <= 128 ? 0 : 1;
+    const dim3 agrid(adj_tiles_x(c->p.nx), c->p.ny);
+    // The reverse sweep of a segment: one graph of K / 2 pair nodes
+    // (programmatic edges) and the fold; graph p reads counter p and leaves the
+    // next segment in counter 1 - p, so replays alternate between the two.
     struct Execs {
         cudaGraphExec_t e[2] = {nullptr, nullptr};
         ~Execs() {
@@ -2783,13 +2773,13 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
         cudaGraphNode_t prev = nullptr;
         cudaError_t e = cudaSuccess;
-        for (long long i = 0; i < K && e == cudaSuccess; ++i) {
-            int set = gp, t = (int)(K - 1 - i);  // the segment's last step first
-            void* params[4] = {&Ap, &set, &t, &c->sc};
+        for (long long i = 0; i < K / 2 && e == cudaSuccess; ++i) {
+            int set = gp, th = (int)(K - 1 - 2 * i);  // the segment's last pair first
+            void* params[4] = {&Ap, &set, &th, &c->sc};
             cudaKernelNodeParams kp = {};
-            kp.func = (void*)dmrt::adjoint_step_kernel;
+            kp.func = (void*)dmrt::adjoint_pair_kernel;
             kp.gridDim = agrid;
-            kp.blockDim = dim3(128);
+            kp.blockDim = dim3(dmrt::kPairThreads);
             kp.kernelParams = params;
             cudaGraphNode_t node;
             e = add_step_node(g, prev, &kp, &node);
@@ -2881,6 +2871,18 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         }
         return DMRT_OK;
     };
+    // Forward pass with checkpoints every K steps (issued once the sweep's
+    // graphs and arguments are ready, so that the GPU does not wait for the
+    // host between the passes; J is read from the Nusselt ring at the end).
+    CK(cudaMemcpyAsync(ckpt(0), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
+    for (long long q = 0; q < AL.C; ++q) {
+        const long long n = std::min(K, N - q * K);
+        rc = step_run(c, n, q + 1 == AL.C);  // the last segment sums its last step's rows
+        if (rc) return rc;
+        if (q + 1 < AL.C)
+            CK(cudaMemcpyAsync(ckpt(q + 1), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream),
+               "checkpoint");
+    }
     // Events (overlap): ev[0] the forward pass done; ev[1 + set] recompute into
     // `set` done; ev[3 + set] reverse sweep from `set` done.
     if (overlap) {
@@ -2915,6 +2917,13 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     CK(cudaMemcpyAsync(slots.data(), dgb, slots.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
        "read dJ/dgbeta");
     CK(cudaStreamSynchronize(c->stream), "synchronize");
+    std::vector<double> series((size_t)avg_last);
+    int64_t got = 0;
+    rc = dmrt_nusselt(c, nullptr, nullptr, series.data(), avg_last, &got);
+    if (rc) return rc;
+    double jsum = 0.0;
+    for (int64_t q = 0; q < got; ++q) jsum += series[(size_t)q];
+    if (J) *J = jsum / (double)avg_last;
     // The Nusselt stencil's own theta_w term, 8 scale / ny per averaged step.
     const double direct = 8.0 * c->sc.nu_scale / (double)c->p.ny;
     if (dJ_dthetaw)
