@@ -458,10 +458,15 @@ void dmrt_destroy(dmrt_ctx* c);
  * first such call, released by dmrt_destroy) while the reverse sweep of the
  * segment after it runs on the context's stream. A workspace of at least
  * dmrt_adjoint_workspace_min() bytes (one set of segment states fewer) also
- * works: recompute and sweep then alternate on the context's stream. Both give
- * the same bits. Synchronises; DMRT_E_DIVERGED if the forward run diverged. */
+ * works: recompute and sweep then alternate on the context's stream. When the
+ * context steps with the cluster kernel (DMRT_KERNEL_CLUSTER, or AUTO on a
+ * small float32 cavity), a workspace of dmrt_adjoint_workspace_all() bytes
+ * (nonzero only then: about N + 1 states) stores every state of the forward
+ * pass as the kernel steps, and no segment is recomputed. All three give the
+ * same bits. Synchronises; DMRT_E_DIVERGED if the forward run diverged. */
 int dmrt_adjoint_workspace_size(const dmrt_ctx* c, int64_t nsteps, size_t* bytes);
 int dmrt_adjoint_workspace_min(const dmrt_ctx* c, int64_t nsteps, size_t* bytes);
+int dmrt_adjoint_workspace_all(const dmrt_ctx* c, int64_t nsteps, size_t* bytes);
 int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace, size_t workspace_bytes,
                  double* J, double* dJ_dthetaw, double* dJ_dRa);
 

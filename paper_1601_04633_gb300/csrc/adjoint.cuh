@@ -39,6 +39,7 @@ struct AdjArgs {
     const long long* seg;              // the segment q swept by this replay
     long long* seg_next;               // the fold writes q - 1 here (the other graph's counter)
     const float* slot[2];              // set s: s_{qK+t} at slot[s] + t * state (t = 0: the checkpoint's copy)
+    const float* all;                  // every state stored (s_k at all + k * state), else null
     float* nu[2];                      // adjoint states: pair P reads nu[P & 1], writes the other
     const float* __restrict__ hot;
     const float* __restrict__ cold;
@@ -309,13 +310,16 @@ __device__ __forceinline__ float adj_node_step(const VjpFwd& F, const float (&lf
     return dgb;
 }
 
+// ALL: every forward state is stored (s_{qK+t} at all + (qK + t) * state);
+// else the segment's states are in slot set `set`.
+template <bool ALL>
 __global__ void __launch_bounds__(kPairThreads) adjoint_pair_kernel(AdjArgs A, int set, int th, StepConsts K) {
     // Launched programmatically after the previous pair, which writes neither
     // s_{k_hi - 1}, s_{k_lo - 1} (slots th, th - 1 of this graph's set, filled
-    // before the replay began) nor the segment counter (set by the previous
-    // replay's fold): these are read, and the forward halves computed, before
-    // waiting for that pair (grid_dep_wait), so their latency overlaps it.
-    // nu is read, and anything written, after the wait.
+    // before the replay began, or stored states) nor the segment counter (set
+    // by the previous replay's fold): these are read, and the forward halves
+    // computed, before waiting for that pair (grid_dep_wait), so their latency
+    // overlaps it. nu is read, and anything written, after the wait.
     __shared__ float S[3 * kPlanes * 128];
     grid_dep_launch();
     const int tid = threadIdx.x, l = tid & 127, rr = tid >> 7;  // lane; row j - 1, j, j + 1
@@ -325,17 +329,18 @@ __global__ void __launch_bounds__(kPairThreads) adjoint_pair_kernel(AdjArgs A, i
     const bool act = col_ok && jr >= 0 && jr < A.ny;                 // step k_hi here
     const bool out = rr == 1 && col_ok && l >= A.hx && l < A.hx + A.tw;  // step k_lo here
     const AdjNode n = adj_node(A, col_ok ? x : A.nx, act ? jr : j);      // (x, jr); clamped when inactive
+    const long long q = *A.seg;
+    const float* base = ALL ? A.all + q * A.K * A.state : A.slot[set];  // s_{qK}
     VjpFwd F1, F2;
     {
         float f[9], g[5];
-        adj_pull(A.slot[set] + th * A.state, n, A, K, f, g);  // s_{k_hi - 1}
+        adj_pull(base + th * A.state, n, A, K, f, g);  // s_{k_hi - 1}
         F1 = vjp_forward(f, g);
         if (out) {
-            adj_pull(A.slot[set] + (th - 1) * A.state, n, A, K, f, g);  // s_{k_lo - 1}
+            adj_pull(base + (th - 1) * A.state, n, A, K, f, g);  // s_{k_lo - 1}
             F2 = vjp_forward(f, g);
         }
     }
-    const long long q = *A.seg;
     grid_dep_wait();
     const long long k_hi = q * A.K + th + 1, k_lo = k_hi - 1;
     if (k_lo > A.N) return;  // the last segment may be short

@@ -1309,7 +1309,9 @@ static int poll_error(dmrt_ctx* c) {
 }
 
 // Runs of n >= 2 steps on the cluster kernel: one launch.
-static int launch_cluster(dmrt_ctx* c, int n) {
+// n steps in one cluster launch; with `record`, the state after each step s of
+// the launch is also written to record + s * stride.
+static int launch_cluster(dmrt_ctx* c, int n, float* record = nullptr, long long stride = 0) {
     dmrt::ClusterArgs C;
     C.A[0] = step_args(c, 0);
     C.A[1] = step_args(c, 1);
@@ -1318,8 +1320,8 @@ static int launch_cluster(dmrt_ctx* c, int n) {
     C.parity = c->cur;
     C.rows_per = c->crows;
     C.start = nullptr;
-    C.record = nullptr;
-    C.record_stride = 0;
+    C.record = record;
+    C.record_stride = stride;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -1339,9 +1341,12 @@ static int launch_cluster(dmrt_ctx* c, int n) {
 }
 
 // nsteps steps; with `finalize`, the last step's Nusselt rows are summed into
-// the ring at the end (without, the next launch sums them).
-static int step_run(dmrt_ctx* c, int64_t nsteps, bool finalize) {
+// the ring at the end (without, the next launch sums them). With `record`
+// (cluster kernel only), the state after the run's step s is also written to
+// record + s * stride.
+static int step_run(dmrt_ctx* c, int64_t nsteps, bool finalize, float* record = nullptr, long long stride = 0) {
     if (!c || nsteps < 0) return DMRT_E_ARG;
+    if (record && !c->cluster) return DMRT_E_ARG;
     if (c->cluster) {
         while (nsteps > 0) {
             if (c->t >= c->next_poll) {
@@ -1351,8 +1356,13 @@ static int step_run(dmrt_ctx* c, int64_t nsteps, bool finalize) {
             }
             // Up to the next divergence poll, in one launch.
             const long long n = std::min<long long>(nsteps, std::max<long long>(1, c->next_poll - c->t));
-            int rc = n >= 2 ? launch_cluster(c, (int)n) : launch_one(c);
+            int rc = n >= 2 ? launch_cluster(c, (int)n, record, stride) : launch_one(c);
             if (rc) return rc;
+            if (record && n < 2)
+                CK(cudaMemcpyAsync(record, buf(c, c->cur), (size_t)kPlanes * (size_t)c->L.plane * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, c->stream),
+                   "record");
+            if (record) record += n * stride;
             nsteps -= n;
         }
         return finalize ? finalize_nu(c) : DMRT_OK;
@@ -2605,6 +2615,7 @@ struct AdjLayout {
     size_t off_seg[2];  // segment slots: one set, or two when the recompute overlaps the reverse sweep
     size_t total_seq;   // bytes with one set of segment slots
     size_t total;       // bytes with two
+    size_t total_all;   // bytes with every state stored (from off_ckpt on: C K + 1 states)
     long long n_blocks;  // blocks of the reverse-step grid: one dJ/dgbeta slot each
 };
 
@@ -2637,6 +2648,7 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.total_seq = o;
     L.off_seg[1] = o; o += (size_t)L.K * L.state;
     L.total = o;
+    L.total_all = L.off_ckpt + (size_t)(L.C * L.K + 1) * L.state;  // s_0 .. s_N, padded to whole segments
     return L;
 }
 
@@ -2653,6 +2665,12 @@ int dmrt_adjoint_workspace_size(const dmrt_ctx* c, int64_t nsteps, size_t* bytes
 int dmrt_adjoint_workspace_min(const dmrt_ctx* c, int64_t nsteps, size_t* bytes) {
     if (!c || !bytes || nsteps < 1) return DMRT_E_ARG;
     *bytes = adjoint_layout(c, nsteps).total_seq;
+    return DMRT_OK;
+}
+
+int dmrt_adjoint_workspace_all(const dmrt_ctx* c, int64_t nsteps, size_t* bytes) {
+    if (!c || !bytes || nsteps < 1) return DMRT_E_ARG;
+    *bytes = c->cluster && !c->slab ? adjoint_layout(c, nsteps).total_all : 0;
     return DMRT_OK;
 }
 
@@ -2682,7 +2700,10 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         return DMRT_E_ARG;
     }
     const AdjLayout AL = adjoint_layout(c, nsteps);
-    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < AL.total_seq) {
+    // Every forward state stored (no recompute) when the context runs the
+    // cluster kernel and the workspace holds them all.
+    const bool all = c->cluster && workspace_bytes >= AL.total_all;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || (workspace_bytes < AL.total_seq && !all)) {
         set_err(c, "adjoint workspace: need %zu bytes (%zu to overlap the recompute with the reverse sweep), "
                    "256-byte aligned", AL.total_seq, AL.total);
         return DMRT_E_SPACE;
@@ -2691,7 +2712,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     // runs on a second stream while the reverse sweep of the current one runs on
     // the context's stream (the two are latency-bound launches of a few hundred
     // blocks, so they share the GPU); with one set they alternate.
-    const bool overlap = workspace_bytes >= AL.total;
+    const bool overlap = !all && workspace_bytes >= AL.total;
     if (overlap && !c->aux) {
         CK(cudaStreamCreateWithFlags(&c->aux, cudaStreamNonBlocking), "adjoint stream");
         for (int i = 0; i < 5; ++i) CK(cudaEventCreateWithFlags(&c->ev[i], cudaEventDisableTiming), "adjoint event");
@@ -2730,6 +2751,8 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     std::memset(&AA, 0, sizeof AA);
     AA.slot[0] = slot(0, 0);
     AA.slot[1] = overlap ? slot(1, 0) : slot(0, 0);
+    float* states = reinterpret_cast<float*>(w + AL.off_ckpt);  // with `all`: s_k at states + k * state
+    AA.all = all ? states : nullptr;
     AA.nu[0] = nu_a;  // nu_{N+1} = 0
     AA.nu[1] = nu_b;
     AA.hot = reinterpret_cast<const float*>(c->ws + c->L.off_hot);
@@ -2777,7 +2800,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
             int set = gp, th = (int)(K - 1 - 2 * i);  // the segment's last pair first
             void* params[4] = {&Ap, &set, &th, &c->sc};
             cudaKernelNodeParams kp = {};
-            kp.func = (void*)dmrt::adjoint_pair_kernel;
+            kp.func = all ? (void*)dmrt::adjoint_pair_kernel<true> : (void*)dmrt::adjoint_pair_kernel<false>;
             kp.gridDim = agrid;
             kp.blockDim = dim3(dmrt::kPairThreads);
             kp.kernelParams = params;
@@ -2805,7 +2828,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     // The segment recompute runs the context's own step kernel. For the TMA
     // kernel every checkpoint and segment slot it reads gets its load maps
     // (float32 storage stores from registers, so no store maps are needed).
-    const bool tma_re = c->kernel == DMRT_KERNEL_TMA;
+    const bool tma_re = !all && c->kernel == DMRT_KERNEL_TMA;
     const int nsets = overlap ? 2 : 1;
     std::vector<dmrt::TmaMaps> ck_maps(tma_re ? (size_t)AL.C : 0), sl_maps(tma_re ? (size_t)(nsets * AL.K) : 0);
     for (size_t q = 0; q < ck_maps.size() + sl_maps.size(); ++q) {
@@ -2874,8 +2897,15 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     // Forward pass with checkpoints every K steps (issued once the sweep's
     // graphs and arguments are ready, so that the GPU does not wait for the
     // host between the passes; J is read from the Nusselt ring at the end).
+    // With `all`, every state instead: s_0 copied, s_1 .. s_N written by the
+    // cluster kernel as it steps.
     CK(cudaMemcpyAsync(ckpt(0), buf(c, c->cur), copy_bytes, cudaMemcpyDeviceToDevice, c->stream), "checkpoint");
-    for (long long q = 0; q < AL.C; ++q) {
+    if (all) {
+        const long long sf = (long long)(AL.state / sizeof(float));
+        rc = step_run(c, N, true, states + sf, sf);
+        if (rc) return rc;
+    }
+    for (long long q = 0; q < AL.C && !all; ++q) {
         const long long n = std::min(K, N - q * K);
         rc = step_run(c, n, q + 1 == AL.C);  // the last segment sums its last step's rows
         if (rc) return rc;
@@ -2889,8 +2919,10 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         CK(cudaEventRecord(c->ev[0], c->stream), "event");
         CK(cudaStreamWaitEvent(rs, c->ev[0], 0), "wait");
     }
-    rc = recompute(AL.C - 1, 0);
-    if (rc) return rc;
+    if (!all) {
+        rc = recompute(AL.C - 1, 0);
+        if (rc) return rc;
+    }
     if (overlap) CK(cudaEventRecord(c->ev[1], rs), "event");
     for (long long q = AL.C - 1; q >= 0; --q) {
         const int set = (int)((AL.C - 1 - q) & 1) % nsets;
@@ -2904,7 +2936,7 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         if (overlap) CK(cudaStreamWaitEvent(c->stream, c->ev[1 + set], 0), "wait");
         CK(cudaGraphLaunch(rg.e[(AL.C - 1 - q) & 1], c->stream), "adjoint sweep launch");
         if (overlap) CK(cudaEventRecord(c->ev[3 + set], c->stream), "event");
-        if (!overlap && q >= 1) {
+        if (!overlap && !all && q >= 1) {
             rc = recompute(q - 1, 0);
             if (rc) return rc;
         }

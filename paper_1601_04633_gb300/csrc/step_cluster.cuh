@@ -50,10 +50,11 @@ struct ClusterArgs {
     int steps;       // time steps of the launch
     int parity;      // global buffer holding the state at launch
     int rows_per;    // rows per block
-    // Record mode (record != nullptr; the adjoint's segment recompute): start
-    // from the state at `start` (same layout as a population buffer), write the
-    // state after step s to record + s * record_stride, and touch nothing else
-    // (no Nusselt numbers, no context buffers or counters).
+    // Recompute mode (start != nullptr; the adjoint's segment recompute):
+    // start from the state at `start` (same layout as a population buffer) and
+    // touch nothing but the record (no Nusselt numbers, no context buffers or
+    // counters). In either mode, with record != nullptr, the state after step
+    // s is also written to record + s * record_stride.
     const float* start;
     float* record;
     long long record_stride;  // floats between recorded states
@@ -122,9 +123,9 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
 
     grid_dep_wait();
     grid_dep_launch();
-    const bool rec = C.record != nullptr;
+    const bool rec = C.start != nullptr;
     // The state of this block's rows and of the rows next to them, from global
-    // buffer `parity` (record mode: from `start`); halo rows beyond the
+    // buffer `parity` (recompute mode: from `start`); halo rows beyond the
     // cavity's walls read as zero in both buffers (the wall rules replace
     // what a pull would take from them).
     for (int i = threadIdx.x; i < (nr + 2) * nx; i += blockDim.x) {
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
                 Dabove[plane_f(6) * plane_sm + x] = f[6];
                 Dabove[plane_g(2) * plane_sm + x] = g[2];
             }
-            if (rec) {
+            if (C.record) {
                 float* d = C.record + (size_t)s * C.record_stride + (size_t)j * pitch + x;
 #pragma unroll
                 for (int k = 0; k < 9; ++k) d[plane_f(k) * PL] = f[k];

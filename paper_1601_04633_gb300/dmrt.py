@@ -129,6 +129,7 @@ SIGNATURES = {
     "dmrt_step_noalloc": (ctypes.c_int, [ctypes.POINTER(Params), _VP, _VP, _VP, _VP, _VP, _VP]),
     "dmrt_adjoint_workspace_size": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "dmrt_adjoint_workspace_min": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "dmrt_adjoint_workspace_all": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "dmrt_adjoint": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_size_t, _DP, _DP, _DP]),
     "dmrt_last_error": (ctypes.c_char_p, [_VP]),
     "dmrt_slab_workspace_size": (ctypes.c_int, [ctypes.POINTER(Params), ctypes.c_int32,
@@ -448,22 +449,36 @@ class Cavity2D:
         dmrt_fields(self.h, ptrs[0], ptrs[1], ptrs[2], False)
         return tuple(out) if pinned is None else tuple(t.numpy() for t in pinned)
 
-    def adjoint(self, nsteps: int, avg_last: int, overlap: bool = True):
+    def adjoint(self, nsteps: int, avg_last: int, overlap: bool = True, store: str = "auto"):
         """Advance nsteps and return (J, dJ/dtheta_w [ny], dJ/dRa): J = mean hot-wall Nu
-        over the last avg_last steps. The adjoint workspace is allocated with torch:
-        the full size (segment recompute overlapped with the reverse sweep) or,
-        with overlap=False, the smallest (the two alternate)."""
+        over the last avg_last steps. The adjoint workspace is allocated with torch.
+        store="all": every forward state kept (cluster-kernel contexts only; no
+        segment recompute); "checkpoints": sqrt(N) checkpoints, the segment
+        recompute overlapped with the reverse sweep or, with overlap=False,
+        alternating with it (the smallest workspace); "auto": "all" when the
+        context allows it and the states take at most half of the free device
+        memory, else "checkpoints"."""
         import torch
 
+        if store not in ("auto", "all", "checkpoints"):
+            raise ValueError("store must be 'auto', 'all' or 'checkpoints'")
+        lib = load()
         nbytes = ctypes.c_size_t()
-        size_fn = load().dmrt_adjoint_workspace_size if overlap else load().dmrt_adjoint_workspace_min
-        _check(size_fn(self.h, int(nsteps), ctypes.byref(nbytes)), self.h)
+        if store != "checkpoints":
+            _check(lib.dmrt_adjoint_workspace_all(self.h, int(nsteps), ctypes.byref(nbytes)), self.h)
+            if store == "all" and nbytes.value == 0:
+                raise ValueError("this context does not step with the cluster kernel: store='all' is unavailable")
+            if store == "auto" and (nbytes.value == 0 or nbytes.value > torch.cuda.mem_get_info(self.device)[0] // 2):
+                nbytes.value = 0
+        if nbytes.value == 0:
+            size_fn = lib.dmrt_adjoint_workspace_size if overlap else lib.dmrt_adjoint_workspace_min
+            _check(size_fn(self.h, int(nsteps), ctypes.byref(nbytes)), self.h)
         ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
         J = ctypes.c_double()
         dth = np.zeros(self.ny)
         dRa = ctypes.c_double()
-        _check(load().dmrt_adjoint(self.h, int(nsteps), int(avg_last), _VP(ws.data_ptr()), nbytes.value,
-                                   ctypes.byref(J), _dptr(dth), ctypes.byref(dRa)), self.h)
+        _check(lib.dmrt_adjoint(self.h, int(nsteps), int(avg_last), _VP(ws.data_ptr()), nbytes.value,
+                                ctypes.byref(J), _dptr(dth), ctypes.byref(dRa)), self.h)
         del ws
         return J.value, dth, dRa.value
 

@@ -92,6 +92,25 @@ def test_adjoint_same_bits_overlapped_or_alternating(D, kernel):
     assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
 
 
+def test_adjoint_same_bits_with_every_state_stored(D):
+    # A cluster-kernel context may keep every forward state (recorded by the
+    # kernel as it steps) instead of checkpoints and segment recomputes: the
+    # reverse sweep reads the same states, so every storage mode, and the
+    # direct kernel's checkpoints, give the same bits. 1001 steps: the last
+    # segment is short and of odd length.
+    cav = inputs.Cavity(128, 96, 1e5, 0.01, noise_amp=1e-3, seed=9)
+    cav.theta_hot_profile = 0.5 + 0.02 * np.sin(np.arange(96))
+    out = []
+    for kernel, store, overlap in ((0, "all", True), (0, "checkpoints", True), (0, "checkpoints", False),
+                                   (1, "checkpoints", True)):
+        sim = D.Cavity2D.from_inputs(cav, nu_capacity=1001, kernel=kernel)
+        out.append(sim.adjoint(1001, 250, overlap=overlap, store=store))
+        sim.close()
+    J0, d0, r0 = out[0]
+    for J, d, r in out[1:]:
+        assert J == J0 and r == r0 and np.array_equal(d, d0)
+
+
 @pytest.mark.parametrize("nx,ny", [(128, 128), (600, 40)])
 def test_adjoint_same_bits_with_either_step_kernel(D, nx, ny):
     # The segment recompute runs the context's step kernel (direct, or TMA with
