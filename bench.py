@@ -511,10 +511,11 @@ def run_dmrt(args):
         adj = D.Cavity2D.from_inputs(acav, nu_capacity=2000)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        Jv, dth, dRa = adj.adjoint(10000, 2000)
+        Jv, dth, dRa = adj.adjoint(10000, 2000, store="all")
         t_adj = time.perf_counter() - t0
         adj.close()
         secondary["adjoint"] = {"workload": "cavity 128x128 Ra 1e5 Pr 0.01, 10000 steps, J over last 2000",
+                                "store": "every forward state",
                                 "forward_s": t_fwd, "adjoint_s": t_adj, "ratio": t_adj / t_fwd,
                                 "J": Jv, "dJ_dRa": dRa, "dJ_dthetaw_norm": float(np.linalg.norm(dth))}
 
