@@ -658,16 +658,21 @@ void choose_launch(const dmrt_params& p_in, int sms, int* kernel, int* npt_out, 
 // The cluster kernel's launch shape for c (blocks, rows per block, threads,
 // shared memory); false if the cavity does not fit one cluster on this GPU.
 // The cluster kernel compiled for blocks of at most `threads` threads, and its launch.
-const void* cluster_func(int threads) {
-    return threads <= 320 ? (const void*)dmrt::step_cluster_kernel<320>
-           : threads <= 640 ? (const void*)dmrt::step_cluster_kernel<640>
-                            : (const void*)dmrt::step_cluster_kernel<1024>;
+// The compiled form for a block of `threads` threads whose rows hold
+// `nodes` nodes: one node per node thread (blocks up to 640 threads always) or
+// a loop over the block's nodes.
+const void* cluster_func(int threads, int nodes) {
+    if (threads <= 320) return (const void*)dmrt::step_cluster_kernel<320, true>;
+    if (threads <= 640) return (const void*)dmrt::step_cluster_kernel<640, true>;
+    return nodes <= threads - 64 ? (const void*)dmrt::step_cluster_kernel<1024, true>
+                                 : (const void*)dmrt::step_cluster_kernel<1024, false>;
 }
 cudaError_t launch_cluster_kernel(const cudaLaunchConfig_t& cfg, const dmrt::ClusterArgs& C) {
-    const int threads = (int)cfg.blockDim.x;
-    if (threads <= 320) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<320>, C);
-    if (threads <= 640) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<640>, C);
-    return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<1024>, C);
+    const int threads = (int)cfg.blockDim.x, nodes = C.rows_per * C.A[0].nx;
+    if (threads <= 320) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<320, true>, C);
+    if (threads <= 640) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<640, true>, C);
+    if (nodes <= threads - 64) return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<1024, true>, C);
+    return cudaLaunchKernelEx(&cfg, dmrt::step_cluster_kernel<1024, false>, C);
 }
 
 bool cluster_fit(dmrt_ctx* c, int* csize_out, int* crows_out, int* threads_out, size_t* smem_out) {
@@ -679,7 +684,7 @@ bool cluster_fit(dmrt_ctx* c, int* csize_out, int* crows_out, int* threads_out, 
         const int blocks = (p.ny + rows - 1) / rows;
         const size_t smem = dmrt::cluster_smem_bytes(rows, p.nx, p.ny);
         const int threads = dmrt::cluster_threads(rows, p.nx);
-        const void* fn = cluster_func(threads);
+        const void* fn = cluster_func(threads, rows * p.nx);
         if (smem > (size_t)dmrt::kMaxSmem) continue;
         if (blocks > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
             (void)cudaGetLastError();

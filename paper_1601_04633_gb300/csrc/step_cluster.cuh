@@ -94,8 +94,11 @@ __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int
 
 // MAXT: the largest block it is launched with (the compiler may give a block of
 // at most 320 or 640 threads more registers per thread, hence more
-// independent instructions in flight along a node's chain).
-template <int MAXT>
+// independent instructions in flight along a node's chain). ONE: every block
+// has at most one node per node thread (rows_per * nx <= blockDim.x - 64), so
+// each thread's node, and with it every shared-memory offset, is fixed across
+// steps; otherwise the node threads loop over the block's nodes.
+template <int MAXT, bool ONE>
 __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
     namespace cg = cooperative_groups;
     cg::cluster_group cl = cg::this_cluster();
@@ -194,101 +197,113 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
             if (lane == 0) *A0.nu_last = means[q - first];
         }
     };
+    // One node's step s: node i of the block (row r, column x, cavity row j)
+    // from buffer S into Dst, the halo rows into the neighbours' Dbelow/Dabove.
+    auto node_step = [&](int s, int i, int r, int x, int j, const float* S, float* Dst, float* Dbelow,
+                         float* Dabove) {
+        if (!DMRT_IN(i + nx, 0, plane_sm, A0.err) || !DMRT_IN(j, 0, ny, A0.err) || !DMRT_IN(r, 0, RP, A0.err))
+            return;
+        // Post-collision value of plane p at (x, local row rr = -1 .. nr) of
+        // this step's state. (Across the cavity's bottom and top walls the
+        // halo rows hold zeros, replaced by the wall rules below.)
+        auto at = [&](int p, int rr, int xx) -> float { return S[p * plane_sm + (rr + 1) * nx + xx]; };
+        auto own = [&](int p) { return S[p * plane_sm + (r + 1) * nx + x]; };
+        // Pull (Eqs. 25, 36): value of direction k at x comes from x - e_k, where
+        // that node exists; links across a wall are replaced below.
+        float f[9], g[5];
+        const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
+        f[0] = own(plane_f(0));
+        f[1] = at(plane_f(1), r, xl);
+        f[2] = at(plane_f(2), r - 1, x);
+        f[3] = at(plane_f(3), r, xr);
+        f[4] = at(plane_f(4), r + 1, x);
+        f[5] = at(plane_f(5), r - 1, xl);
+        f[6] = at(plane_f(6), r - 1, xr);
+        f[7] = at(plane_f(7), r + 1, xr);
+        f[8] = at(plane_f(8), r + 1, xl);
+        g[0] = own(plane_g(0));
+        g[1] = at(plane_g(1), r, xl);
+        g[2] = at(plane_g(2), r - 1, x);
+        g[3] = at(plane_g(3), r, xr);
+        g[4] = at(plane_g(4), r + 1, x);
+        // Bottom wall (j = 0): f2, f5, f6, g2 from the node's own opposites; top the reverse.
+        if (j == 0) {
+            f[2] = own(plane_f(4));
+            f[5] = own(plane_f(7));
+            f[6] = own(plane_f(8));
+            g[2] = own(plane_g(4));
+        }
+        if (j == ny - 1) {
+            f[4] = own(plane_f(2));
+            f[7] = own(plane_f(5));
+            f[8] = own(plane_f(6));
+            g[4] = own(plane_g(2));
+        }
+        // Left wall (x = 0): links with e_x = +1.
+        if (x == 0) {
+            f[1] = own(plane_f(3));
+            f[5] = own(plane_f(7));
+            f[8] = own(plane_f(6));
+            const float add = K.left_fixed ? K.abb * walls[r] : 0.f;
+            g[1] = sign_l_g * own(plane_g(3)) + add;
+        }
+        // Right wall (x = nx - 1): links with e_x = -1.
+        if (x == nx - 1) {
+            f[3] = own(plane_f(1));
+            f[6] = own(plane_f(8));
+            f[7] = own(plane_f(5));
+            const float add = K.right_fixed ? K.abb * walls[RP + r] : 0.f;
+            g[3] = sign_r_g * own(plane_g(1)) + add;
+        }
+        float rho, theta;
+        collide_node(f, g, K, rho, theta);
+        bad |= !(fabsf(rho) < 1e30f) || !(fabsf(theta) < 1e30f);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Dst[plane_f(k) * plane_sm + nx + i] = f[k];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) Dst[plane_g(k) * plane_sm + nx + i] = g[k];
+        // The neighbours' halo rows: downward-moving populations (0-based
+        // directions f 4, 7, 8 and g 4) of the first row to the previous
+        // block, upward-moving ones (f 2, 5, 6 and g 2) of the last row to
+        // the next block.
+        if (r == 0 && Dbelow) {
+            Dbelow[plane_f(4) * plane_sm + x] = f[4];
+            Dbelow[plane_f(7) * plane_sm + x] = f[7];
+            Dbelow[plane_f(8) * plane_sm + x] = f[8];
+            Dbelow[plane_g(4) * plane_sm + x] = g[4];
+        }
+        if (r == nr - 1 && Dabove) {
+            Dabove[plane_f(2) * plane_sm + x] = f[2];
+            Dabove[plane_f(5) * plane_sm + x] = f[5];
+            Dabove[plane_f(6) * plane_sm + x] = f[6];
+            Dabove[plane_g(2) * plane_sm + x] = g[2];
+        }
+        if (C.record) {
+            float* d = C.record + (size_t)s * C.record_stride + (size_t)j * pitch + x;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) d[plane_f(k) * PL] = f[k];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) d[plane_g(k) * PL] = g[k];
+        }
+        if (x == 0) th01[(s & 1) * 2 * RP + 2 * r] = theta;
+        if (x == 1) th01[(s & 1) * 2 * RP + 2 * r + 1] = theta;
+    };
+    const int r1 = (int)threadIdx.x / nx, x1 = (int)threadIdx.x - r1 * nx;  // ONE: this thread's node
+    const bool has1 = !nu_warp && (int)threadIdx.x < nr * nx;
     for (int s = 0; s < C.steps; ++s) {
         const bool odd = (s & 1) != 0;
         const float* S = odd ? sb[1] : sb[0];
         float* Dst = odd ? sb[0] : sb[1];
         float* Dbelow = odd ? below0 : below1;
         float* Dabove = odd ? above0 : above1;
-        for (int i = threadIdx.x; i < (nu_warp ? 0 : nr * nx); i += nwork) {
-            const int r = i / nx, x = i - r * nx;
-            const int j = r0 + r;
-            if (!DMRT_IN(i + nx, 0, plane_sm, A0.err) || !DMRT_IN(j, 0, ny, A0.err) || !DMRT_IN(r, 0, RP, A0.err))
-                continue;
-            // Post-collision value of plane p at (x, local row rr = -1 .. nr) of
-            // this step's state. (Across the cavity's bottom and top walls the
-            // halo rows hold zeros, replaced by the wall rules below.)
-            auto at = [&](int p, int rr, int xx) -> float { return S[p * plane_sm + (rr + 1) * nx + xx]; };
-            auto own = [&](int p) { return S[p * plane_sm + (r + 1) * nx + x]; };
-            // Pull (Eqs. 25, 36): value of direction k at x comes from x - e_k, where
-            // that node exists; links across a wall are replaced below.
-            float f[9], g[5];
-            const int xl = x > 0 ? x - 1 : x, xr = x + 1 < nx ? x + 1 : x;
-            f[0] = own(plane_f(0));
-            f[1] = at(plane_f(1), r, xl);
-            f[2] = at(plane_f(2), r - 1, x);
-            f[3] = at(plane_f(3), r, xr);
-            f[4] = at(plane_f(4), r + 1, x);
-            f[5] = at(plane_f(5), r - 1, xl);
-            f[6] = at(plane_f(6), r - 1, xr);
-            f[7] = at(plane_f(7), r + 1, xr);
-            f[8] = at(plane_f(8), r + 1, xl);
-            g[0] = own(plane_g(0));
-            g[1] = at(plane_g(1), r, xl);
-            g[2] = at(plane_g(2), r - 1, x);
-            g[3] = at(plane_g(3), r, xr);
-            g[4] = at(plane_g(4), r + 1, x);
-            // Bottom wall (j = 0): f2, f5, f6, g2 from the node's own opposites; top the reverse.
-            if (j == 0) {
-                f[2] = own(plane_f(4));
-                f[5] = own(plane_f(7));
-                f[6] = own(plane_f(8));
-                g[2] = own(plane_g(4));
+        if constexpr (ONE) {
+            if (has1) node_step(s, (int)threadIdx.x, r1, x1, r0 + r1, S, Dst, Dbelow, Dabove);
+        } else {
+#pragma unroll 1
+            for (int i = threadIdx.x; i < (nu_warp ? 0 : nr * nx); i += nwork) {
+                const int r = i / nx, x = i - r * nx;
+                node_step(s, i, r, x, r0 + r, S, Dst, Dbelow, Dabove);
             }
-            if (j == ny - 1) {
-                f[4] = own(plane_f(2));
-                f[7] = own(plane_f(5));
-                f[8] = own(plane_f(6));
-                g[4] = own(plane_g(2));
-            }
-            // Left wall (x = 0): links with e_x = +1.
-            if (x == 0) {
-                f[1] = own(plane_f(3));
-                f[5] = own(plane_f(7));
-                f[8] = own(plane_f(6));
-                const float add = K.left_fixed ? K.abb * walls[r] : 0.f;
-                g[1] = sign_l_g * own(plane_g(3)) + add;
-            }
-            // Right wall (x = nx - 1): links with e_x = -1.
-            if (x == nx - 1) {
-                f[3] = own(plane_f(1));
-                f[6] = own(plane_f(8));
-                f[7] = own(plane_f(5));
-                const float add = K.right_fixed ? K.abb * walls[RP + r] : 0.f;
-                g[3] = sign_r_g * own(plane_g(1)) + add;
-            }
-            float rho, theta;
-            collide_node(f, g, K, rho, theta);
-            bad |= !(fabsf(rho) < 1e30f) || !(fabsf(theta) < 1e30f);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) Dst[plane_f(k) * plane_sm + nx + i] = f[k];
-#pragma unroll
-            for (int k = 0; k < 5; ++k) Dst[plane_g(k) * plane_sm + nx + i] = g[k];
-            // The neighbours' halo rows: downward-moving populations (0-based
-            // directions f 4, 7, 8 and g 4) of the first row to the previous
-            // block, upward-moving ones (f 2, 5, 6 and g 2) of the last row to
-            // the next block.
-            if (r == 0 && Dbelow) {
-                Dbelow[plane_f(4) * plane_sm + x] = f[4];
-                Dbelow[plane_f(7) * plane_sm + x] = f[7];
-                Dbelow[plane_f(8) * plane_sm + x] = f[8];
-                Dbelow[plane_g(4) * plane_sm + x] = g[4];
-            }
-            if (r == nr - 1 && Dabove) {
-                Dabove[plane_f(2) * plane_sm + x] = f[2];
-                Dabove[plane_f(5) * plane_sm + x] = f[5];
-                Dabove[plane_f(6) * plane_sm + x] = f[6];
-                Dabove[plane_g(2) * plane_sm + x] = g[2];
-            }
-            if (C.record) {
-                float* d = C.record + (size_t)s * C.record_stride + (size_t)j * pitch + x;
-#pragma unroll
-                for (int k = 0; k < 9; ++k) d[plane_f(k) * PL] = f[k];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) d[plane_g(k) * PL] = g[k];
-            }
-            if (x == 0) th01[(s & 1) * 2 * RP + 2 * r] = theta;
-            if (x == 1) th01[(s & 1) * 2 * RP + 2 * r + 1] = theta;
         }
         cl.sync();  // step s's state, halo rows and wall-side temperatures are visible
         if (!rec && nu_warp) {

@@ -35,7 +35,7 @@ def main():
     if args.run == "adjoint_128":
         cav = inputs.cavity_128_adjoint()
         sim = D.Cavity2D.from_inputs(cav, nu_capacity=2000)
-        J, dth, dRa = sim.adjoint(args.steps, 2000)
+        J, dth, dRa = sim.adjoint(args.steps, min(2000, args.steps))
         sim.close()
         out = {"J": J, "dJ_dRa": dRa}
     elif args.run == "cavity":
