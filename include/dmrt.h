@@ -444,9 +444,11 @@ void dmrt_destroy(dmrt_ctx* c);
  * (the results repeat bit for bit). Memory: sqrt(N) checkpoints of the state
  * plus a sqrt(N)-step segment that is recomputed from its checkpoint, by the
  * context's own step kernel, before being swept backwards. The sweep of a
- * segment is one CUDA-graph replay (a reverse-step node per step, chained by
- * programmatic edges, and a fold of the segment's gradient terms); the graphs
- * are built on each call and released before it returns.
+ * segment is one CUDA-graph replay: nodes chained by programmatic edges, each
+ * two reverse steps (small cavities: the first step on a 3-row window, its
+ * result kept in shared memory for the second) or one (cavities that fill the
+ * GPU), and a fold of the segment's gradient terms; the graphs are built on
+ * each call and released before it returns.
  *
  * dmrt_adjoint starts from the context's current state and wall profiles,
  * advances the context by nsteps (its state, step count and Nusselt ring are

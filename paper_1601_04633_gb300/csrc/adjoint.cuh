@@ -40,7 +40,8 @@ struct AdjArgs {
     long long* seg_next;               // the fold writes q - 1 here (the other graph's counter)
     const float* slot[2];              // set s: s_{qK+t} at slot[s] + t * state (t = 0: the checkpoint's copy)
     const float* all;                  // every state stored (s_k at all + k * state), else null
-    float* nu[2];                      // adjoint states: pair P reads nu[P & 1], writes the other
+    float* nu[2];                      // adjoint states: pair P reads nu[P & 1] (single steps: step k reads
+                                       // nu[(N - k) & 1]) and writes the other
     const float* __restrict__ hot;
     const float* __restrict__ cold;
     double* dthw;                      // [ny] dJ/dtheta_w totals
@@ -54,7 +55,8 @@ struct AdjArgs {
     long long plane;
     int nsets;                         // slot sets: with 2, segment q uses set (C - 1 - q) & 1
     int nx, ny, pitch;
-    int tw, hx;                        // output columns per tile and halo columns (1 when nx > 128, else 0)
+    int tw, hx;                        // output columns per tile and halo columns on each side
+    int pairs;                         // 1: pair nodes (two steps per launch), 0: one step per launch
     float w;                           // w_k inside the averaging window
     float nu_wall, nu_next;            // dNu/dtheta at columns 0 and 1, divided by ny
 };
@@ -392,6 +394,46 @@ __global__ void __launch_bounds__(kPairThreads) adjoint_pair_kernel(AdjArgs A, i
     adj_dgb_store(dgb2, th - 1, tile, A);
 }
 
+// ---- one reverse step per launch ------------------------------------------------
+// For cavities large enough to fill the GPU, where the pair's halo rows would
+// be extra work rather than idle SMs put to use: step k = qK + t + 1 at a
+// tile of 128 columns of row j, nu_{k+1} from global memory, nu_k to it.
+template <bool ALL>
+__global__ void __launch_bounds__(128) adjoint_step_kernel(AdjArgs A, int set, int t, StepConsts K) {
+    // As in the pair kernel: s_{k-1} and the segment counter before the wait,
+    // nu and every write after it.
+    grid_dep_launch();
+    const long long q = *A.seg;
+    const float* base = ALL ? A.all + q * A.K * A.state : A.slot[set];
+    const AdjNode n = adj_node(A, blockIdx.x * 128 + threadIdx.x, blockIdx.y);
+    VjpFwd F;
+    {
+        float f[9], g[5];
+        adj_pull(base + t * A.state, n, A, K, f, g);
+        F = vjp_forward(f, g);
+    }
+    grid_dep_wait();
+    const long long k = q * A.K + t + 1;
+    if (k > A.N) return;  // the last segment may be short
+    const float* __restrict__ NI = A.nu[(A.N - k) & 1];  // nu_{k+1}
+    float* __restrict__ NO = A.nu[(A.N - k + 1) & 1];    // nu_k
+    const int PL = (int)A.plane;
+    float dgb = 0.f;
+    if (n.in) {
+        float lf[9], lg[5], nf[9], ng[5];
+        adj_gather(NI, n, A, K, lf, lg);
+        dgb = adj_node_step(F, lf, lg, n, k > A.w_from ? A.w : 0.f, A, K, nf, ng);
+        if (n.i == 0)
+            A.dthw_step[(size_t)t * A.ny + n.j] = K.left_fixed ? __ldg(NI + plane_g(1) * PL + n.j * A.pitch) : 0.f;
+        float* D = NO + n.c0;
+#pragma unroll
+        for (int m = 0; m < 9; ++m) D[plane_f(m) * PL] = nf[m];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) D[plane_g(m) * PL] = ng[m];
+    }
+    adj_dgb_store(dgb, t, (long long)blockIdx.y * gridDim.x + blockIdx.x, A);
+}
+
 // After a segment's reverse steps: add the segment's dJ/dgbeta terms (per block
 // of the step grid) and dJ/dtheta_w terms (per row) to the totals, in float64,
 // one warp per slot: lane l sums the steps t = l, l + 32, ... in turn, a
@@ -432,10 +474,10 @@ __global__ void __launch_bounds__(kFoldThreads) adjoint_fold_kernel(AdjArgs A, S
 
 // The anti-bounce-back term of step 1 (after the sweep): q_east(0, j) =
 // abb theta_w(j) - s_west(0, j) feeds dJ/dtheta_w(j) with abb nu_1[g east](0, j).
-// nu_1 is the output of the sweep's last pair, P = (N - 1) / 2.
+// nu_1 is the output of the sweep's last pair, P = (N - 1) / 2, or of step 1.
 __global__ void adjoint_gather_kernel(AdjArgs A, StepConsts K) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    const float* nu1 = A.nu[((A.N - 1) / 2 + 1) & 1];
+    const float* nu1 = A.pairs ? A.nu[((A.N - 1) / 2 + 1) & 1] : A.nu[A.N & 1];
     if (j < A.ny && K.left_fixed) A.dthw[j] += (double)K.abb * (double)nu1[plane_g(1) * A.plane + (long long)j * A.pitch];
 }
 

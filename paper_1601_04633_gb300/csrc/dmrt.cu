@@ -2622,12 +2622,29 @@ struct AdjLayout {
     size_t total;       // bytes with two
     size_t total_all;   // bytes with every state stored (from off_ckpt on: C K + 1 states)
     long long n_blocks;  // blocks of the reverse-step grid: one dJ/dgbeta slot each
+    bool pairs;          // the sweep's form: pair nodes, or one step per node
 };
 
-// The reverse sweep's tiles: one per row when nx <= 128 (no halo columns),
-// else tiles of 126 columns computed with one halo column on each side.
-int adj_tile_width(int nx) { return nx <= 128 ? nx : 126; }
-int adj_tiles_x(int nx) { return (nx + adj_tile_width(nx) - 1) / adj_tile_width(nx); }
+// The reverse sweep's form: pair nodes (two steps per launch, the first on
+// a 3-row window) while their grid takes at most a third of the GPU's
+// threads, so that the window's extra rows run on otherwise idle SMs; one
+// step per launch above. Tiles of 128 columns; pair tiles of 126 columns with
+// one halo column on each side when nx > 128.
+bool adj_pairs(const dmrt_ctx* c) {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        sms = 152;
+    }
+    const long long tiles = (long long)((c->p.nx + (c->p.nx <= 128 ? c->p.nx : 126) - 1) /
+                                        (c->p.nx <= 128 ? c->p.nx : 126)) * c->p.ny;
+    return tiles * dmrt::kPairThreads <= (long long)sms * 2048 / 3;
+}
+int adj_tile_width(const dmrt_ctx* c, bool pairs) { return pairs && c->p.nx > 128 ? 126 : std::min(c->p.nx, 128); }
+int adj_tiles_x(const dmrt_ctx* c, bool pairs) {
+    const int tw = adj_tile_width(c, pairs);
+    return (c->p.nx + tw - 1) / tw;
+}
 
 AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     AdjLayout L;
@@ -2642,7 +2659,8 @@ AdjLayout adjoint_layout(const dmrt_ctx* c, long long N) {
     L.off_nu0 = o; o += L.state;
     L.off_nu1 = o; o += L.state;
     L.off_dthw = o; o += align256((size_t)c->p.ny * sizeof(double));
-    L.n_blocks = (long long)adj_tiles_x(c->p.nx) * c->p.ny;
+    L.pairs = adj_pairs(c);
+    L.n_blocks = (long long)adj_tiles_x(c, L.pairs) * c->p.ny;
     L.off_dgb = o; o += align256((size_t)L.n_blocks * sizeof(double));
     L.off_misc = o; o += 256;
     L.off_rows = o; o += align256((size_t)2 * c->p.ny * sizeof(double) + 8);
@@ -2780,12 +2798,14 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
     AA.w = (float)(1.0 / (double)avg_last);
     AA.nu_wall = (float)(-9.0 * c->sc.nu_scale / c->p.ny);
     AA.nu_next = (float)(c->sc.nu_scale / c->p.ny);
-    AA.tw = adj_tile_width(c->p.nx);
-    AA.hx = c->p.nx <= 128 ? 0 : 1;
-    const dim3 agrid(adj_tiles_x(c->p.nx), c->p.ny);
-    // The reverse sweep of a segment: one graph of K / 2 pair nodes
-    // (programmatic edges) and the fold; graph p reads counter p and leaves the
-    // next segment in counter 1 - p, so replays alternate between the two.
+    AA.tw = adj_tile_width(c, AL.pairs);
+    AA.hx = AL.pairs && c->p.nx > 128 ? 1 : 0;
+    AA.pairs = AL.pairs ? 1 : 0;
+    const dim3 agrid(adj_tiles_x(c, AL.pairs), c->p.ny);
+    // The reverse sweep of a segment: one graph of K / 2 pair nodes, or K
+    // single-step nodes (programmatic edges), and the fold; graph p reads
+    // counter p and leaves the next segment in counter 1 - p, so replays
+    // alternate between the two.
     struct Execs {
         cudaGraphExec_t e[2] = {nullptr, nullptr};
         ~Execs() {
@@ -2801,13 +2821,19 @@ int dmrt_adjoint(dmrt_ctx* c, int64_t nsteps, int64_t avg_last, void* workspace,
         CK(cudaGraphCreate(&g, 0), "cudaGraphCreate");
         cudaGraphNode_t prev = nullptr;
         cudaError_t e = cudaSuccess;
-        for (long long i = 0; i < K / 2 && e == cudaSuccess; ++i) {
-            int set = gp, th = (int)(K - 1 - 2 * i);  // the segment's last pair first
+        const long long per = AL.pairs ? 2 : 1;  // steps per node
+        for (long long i = 0; i < K / per && e == cudaSuccess; ++i) {
+            int set = gp, th = (int)(K - 1 - per * i);  // the segment's last step (pair) first
             void* params[4] = {&Ap, &set, &th, &c->sc};
             cudaKernelNodeParams kp = {};
-            kp.func = all ? (void*)dmrt::adjoint_pair_kernel<true> : (void*)dmrt::adjoint_pair_kernel<false>;
+            if (AL.pairs) {
+                kp.func = all ? (void*)dmrt::adjoint_pair_kernel<true> : (void*)dmrt::adjoint_pair_kernel<false>;
+                kp.blockDim = dim3(dmrt::kPairThreads);
+            } else {
+                kp.func = all ? (void*)dmrt::adjoint_step_kernel<true> : (void*)dmrt::adjoint_step_kernel<false>;
+                kp.blockDim = dim3(128);
+            }
             kp.gridDim = agrid;
-            kp.blockDim = dim3(dmrt::kPairThreads);
             kp.kernelParams = params;
             cudaGraphNode_t node;
             e = add_step_node(g, prev, &kp, &node);
