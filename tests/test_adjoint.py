@@ -51,6 +51,41 @@ def test_adjoint_matches_oracle_adjoint(D, nx, ny, Ra, steps, avg):
     assert dRa == pytest.approx(dRao, rel=REL)
 
 
+@pytest.mark.parametrize("steps,avg", [(1, 1), (2, 1), (3, 2), (5, 5)])
+def test_adjoint_few_steps_against_oracle(D, steps, avg):
+    # Fewer steps than one segment: a pair node whose first step lies beyond the
+    # run (odd lengths), and the anti-bounce-back term of step 1 after it.
+    nx, ny, Ra = 20, 18, 1e5
+    cav = inputs.Cavity(nx, ny, Ra, 0.01, noise_amp=1e-2, seed=5)
+    cav.theta_hot_profile = 0.5 + 0.03 * np.cos(np.arange(ny))
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=8)
+    J, dth, dRa = sim.adjoint(steps, avg)
+    sim.close()
+    m = O.derive(nx, ny, Ra, 0.01, 0.1)
+    f0, g0 = O.init(m, cav.theta0())
+    Jo, dtho, dgbo = O.adjoint(m, steps, avg, f0, g0, theta_hot_profile=cav.theta_hot_profile)
+    assert J == pytest.approx(Jo, rel=1e-5)
+    assert np.abs(dth - dtho).max() <= REL * np.abs(dtho).max()
+    # dJ/dRa is exactly 0 for one and two steps (the force reaches the wall
+    # temperatures only from the third) and small after.
+    assert dRa == pytest.approx(dgbo * m.gbeta / Ra, rel=1e-3, abs=1e-15)
+
+
+def test_adjoint_store_all_needs_the_cluster_kernel(D):
+    # Every state is recorded by the cluster kernel only: a context on the TMA
+    # kernel reports no such workspace, and asking for it is refused.
+    cav = inputs.Cavity(64, 48, 1e5, 0.01, noise_amp=1e-3, seed=4)
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=50, kernel=2)
+    with pytest.raises(ValueError):
+        sim.adjoint(50, 10, store="all")
+    J1, d1, r1 = sim.adjoint(50, 10)  # auto: checkpoints
+    sim.close()
+    sim = D.Cavity2D.from_inputs(cav, nu_capacity=50, kernel=3)
+    J2, d2, r2 = sim.adjoint(50, 10, store="all")
+    sim.close()
+    assert J1 == J2 and r1 == r2 and np.array_equal(d1, d2)
+
+
 def test_adjoint_advances_like_a_forward_run(D):
     cav = inputs.Cavity(130, 40, 1e5, 0.005, noise_amp=1e-3, seed=5)
     a = D.Cavity2D.from_inputs(cav, nu_capacity=500)
