@@ -685,7 +685,8 @@ bool cluster_fit(dmrt_ctx* c, int* csize_out, int* crows_out, int* threads_out, 
         const size_t smem = dmrt::cluster_smem_bytes(rows, p.nx, p.ny);
         const int threads = dmrt::cluster_threads(rows, p.nx);
         const void* fn = cluster_func(threads, rows * p.nx);
-        if (smem > (size_t)dmrt::kMaxSmem) continue;
+        // At most two nodes per node thread (the kernel takes no more).
+        if (smem > (size_t)dmrt::kMaxSmem || rows * p.nx > 2 * (threads - 64)) continue;
         if (blocks > 8 && cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) {
             (void)cudaGetLastError();
             continue;

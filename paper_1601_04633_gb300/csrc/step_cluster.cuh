@@ -95,9 +95,10 @@ __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int
 // MAXT: the largest block it is launched with (the compiler may give a block of
 // at most 320 or 640 threads more registers per thread, hence more
 // independent instructions in flight along a node's chain). ONE: every block
-// has at most one node per node thread (rows_per * nx <= blockDim.x - 64), so
-// each thread's node, and with it every shared-memory offset, is fixed across
-// steps; otherwise the node threads loop over the block's nodes.
+// has at most one node per node thread (rows_per * nx <= blockDim.x - 64);
+// otherwise a thread has a second node, nwork further on (the host keeps
+// blocks within two nodes per node thread). A thread's nodes, and with them
+// every shared-memory offset, are fixed across steps.
 template <int MAXT, bool ONE>
 __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constant__ ClusterArgs C) {
     namespace cg = cooperative_groups;
@@ -290,20 +291,18 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
     };
     const int r1 = (int)threadIdx.x / nx, x1 = (int)threadIdx.x - r1 * nx;  // ONE: this thread's node
     const bool has1 = !nu_warp && (int)threadIdx.x < nr * nx;
+    const int i2 = (int)threadIdx.x + nwork, r2 = i2 / nx, x2 = i2 - r2 * nx;  // !ONE: the second node
+    const bool has2 = !nu_warp && i2 < nr * nx;
     for (int s = 0; s < C.steps; ++s) {
         const bool odd = (s & 1) != 0;
         const float* S = odd ? sb[1] : sb[0];
         float* Dst = odd ? sb[0] : sb[1];
         float* Dbelow = odd ? below0 : below1;
         float* Dabove = odd ? above0 : above1;
-        if constexpr (ONE) {
-            if (has1) node_step(s, (int)threadIdx.x, r1, x1, r0 + r1, S, Dst, Dbelow, Dabove);
-        } else {
-#pragma unroll 1
-            for (int i = threadIdx.x; i < (nu_warp ? 0 : nr * nx); i += nwork) {
-                const int r = i / nx, x = i - r * nx;
-                node_step(s, i, r, x, r0 + r, S, Dst, Dbelow, Dabove);
-            }
+        if (has1) node_step(s, (int)threadIdx.x, r1, x1, r0 + r1, S, Dst, Dbelow, Dabove);
+        if constexpr (!ONE) {
+            // A block holds at most two nodes per node thread (checked on the host).
+            if (has2) node_step(s, i2, r2, x2, r0 + r2, S, Dst, Dbelow, Dabove);
         }
         cl.sync();  // step s's state, halo rows and wall-side temperatures are visible
         if (!rec && nu_warp) {
