@@ -92,6 +92,14 @@ __device__ __forceinline__ double warp_fixed_sum(const double* rows, int ny, int
     return s;
 }
 
+// Bulk copy (asynchronous proxy) of `bytes` bytes, a multiple of 16, from this
+// block's shared memory to global memory; both addresses 16-byte aligned.
+__device__ __forceinline__ void cluster_bulk_s2g(float* g, const float* s, unsigned bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g),
+                 "r"((unsigned)__cvta_generic_to_shared(s)), "r"(bytes)
+                 : "memory");
+}
+
 // MAXT: the largest block it is launched with (the compiler may give a block of
 // at most 320 or 640 threads more registers per thread, hence more
 // independent instructions in flight along a node's chain). ONE: every block
@@ -128,6 +136,14 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
     grid_dep_wait();
     grid_dep_launch();
     const bool rec = C.start != nullptr;
+    // Recorded states: in the form for the largest blocks, with rows of a
+    // multiple of 4 floats (16-byte aligned in shared memory; the global pitch
+    // and state stride always are), one lane of the Nusselt-rows warp copies
+    // the block's rows out in bulk after each step's barrier, off the node
+    // warps' path; else every node thread stores its node. (The forms for
+    // smaller blocks keep the stores: the copy code there cost their unrecorded
+    // steps 6-10 % through register allocation.)
+    const bool bulk_rec = MAXT == 1024 && C.record != nullptr && (nx & 3) == 0;
     // The state of this block's rows and of the rows next to them, from global
     // buffer `parity` (recompute mode: from `start`); halo rows beyond the
     // cavity's walls read as zero in both buffers (the wall rules replace
@@ -279,7 +295,7 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
             Dabove[plane_f(6) * plane_sm + x] = f[6];
             Dabove[plane_g(2) * plane_sm + x] = g[2];
         }
-        if (C.record) {
+        if (C.record && !bulk_rec) {
             float* d = C.record + (size_t)s * C.record_stride + (size_t)j * pitch + x;
 #pragma unroll
             for (int k = 0; k < 9; ++k) d[plane_f(k) * PL] = f[k];
@@ -305,6 +321,26 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
             if (has2) node_step(s, i2, r2, x2, r0 + r2, S, Dst, Dbelow, Dabove);
         }
         cl.sync();  // step s's state, halo rows and wall-side temperatures are visible
+        const bool copier = bulk_rec && nu_warp && !sum_warp && lane == 0 && nr > 0;
+        if (copier) {
+            // The state after step s (this block's rows of Dst) to its record;
+            // the copies have read Dst before this thread reaches the next
+            // barrier, after which step s + 2 overwrites it.
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            float* g = C.record + (size_t)s * C.record_stride + (size_t)r0 * pitch;
+            const float* src = Dst + nx;  // local row 0
+#pragma unroll 1
+            for (int p = 0; p < kPlanes; ++p) {
+                if (pitch == nx) {
+                    cluster_bulk_s2g(g + p * PL, src + p * plane_sm, (unsigned)(nr * nx * 4));
+                } else {
+                    for (int r = 0; r < nr; ++r)
+                        cluster_bulk_s2g(g + p * PL + (size_t)r * pitch, src + p * plane_sm + r * nx,
+                                         (unsigned)(nx * 4));
+                }
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
         if (!rec && nu_warp) {
             // Off the node warps' path, on two warps: this block's rows of step s
             // into block 0's row array; in block 0, the sum of step s - 1, whose
@@ -312,7 +348,10 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
             if (!sum_warp) nu_rows_of(s);
             else if (rank == 0 && s > 0) nu_mean_of(s - 1);
         }
+        if (copier) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
+    if (bulk_rec && nu_warp && !sum_warp && lane == 0 && nr > 0)
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the records written
     if (!rec && C.steps > 0) {
         cl.sync();  // the last step's rows
         if (rank == 0 && sum_warp) nu_mean_of(C.steps - 1);
