@@ -8,9 +8,9 @@
 //   lambda_k = P^T-gather of nu_{k+1}       (adjoint of s_k; nu_{N+1} = 0)
 //   nu_k     = C'(q_k)^T lambda_k + w_k dNu(k)/dq_k
 //   dJ/dgbeta += lambda_k . dC/dgbeta;  dJ/dtheta_w(j) += abb * nu_{k+1}[g east](0, j)
-// One thread per node. The transpose of the pull is itself a pull in the
-// opposite direction: s_m(x) fed q_m(x + e_m), or, where x + e_m lies outside,
-// the wall value of q_opp(m)(x) (sign -1 for anti-bounce-back).
+// One thread per node and reverse step. The transpose of the pull is itself a
+// pull in the opposite direction: s_m(x) fed q_m(x + e_m), or, where x + e_m
+// lies outside, the wall value of q_opp(m)(x) (sign -1 for anti-bounce-back).
 //
 // The transposed local Jacobian is written out in closed form. With
 // S' = diag(rates / row norms) and A = I - M^T S' M (symmetric),
@@ -29,12 +29,13 @@ namespace dmrt {
 
 // The reverse sweep of a segment of K steps (K even) replays one of two
 // graphs, each of K / 2 pair nodes (reverse steps k and k - 1 in one launch)
-// and a fold node; graph s serves the segments whose recomputed states sit in
-// slot set s, so a node's pre-wait addresses depend on s and on t, the step
-// within the segment, only. The segment q itself comes from a device counter
-// (graph s reads counter s; its fold leaves q - 1 in the other), needed after
-// the wait: for the adjoint buffers, the averaging weight and to skip the
-// missing steps of a short last segment.
+// or K single-step nodes, and a fold node; graph s serves the segments whose
+// recomputed states sit in slot set s, so a node's pre-wait addresses depend
+// on s and on t, the step within the segment, only (with every state stored,
+// on the segment q as well). q comes from a device counter (graph s reads
+// counter s; its fold leaves q - 1 in the other); after the wait it selects
+// the adjoint buffers and the averaging weight and skips the missing steps of
+// a short last segment.
 struct AdjArgs {
     const long long* seg;              // the segment q swept by this replay
     long long* seg_next;               // the fold writes q - 1 here (the other graph's counter)
