@@ -142,3 +142,17 @@ def test_create_without_workspace_fails_cleanly(D):
     with pytest.raises(D.DmrtError) as ei:
         D.dmrt_create(p, None, 0, 0, 0)
     assert ei.value.code == D.DMRT_E_ARG
+
+
+def test_adjoint_workspace_queries_refuse_bad_arguments(D):
+    # The three workspace queries (checkpoints overlapped, alternating, every
+    # state stored) refuse a missing context or a step count below 1 without
+    # touching a GPU; the binding checks its storage-mode argument first.
+    import ctypes
+
+    L = D.load()
+    n = ctypes.c_size_t()
+    for fn in (L.dmrt_adjoint_workspace_size, L.dmrt_adjoint_workspace_min, L.dmrt_adjoint_workspace_all):
+        assert fn(None, 10, ctypes.byref(n)) == D.DMRT_E_ARG
+    with pytest.raises(ValueError):
+        D.Cavity2D.adjoint(object(), 10, 5, store="every")
