@@ -136,14 +136,14 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
     grid_dep_wait();
     grid_dep_launch();
     const bool rec = C.start != nullptr;
-    // Recorded states: in the form for the largest blocks, with rows of a
-    // multiple of 4 floats (16-byte aligned in shared memory; the global pitch
-    // and state stride always are), one lane of the Nusselt-rows warp copies
-    // the block's rows out in bulk after each step's barrier, off the node
-    // warps' path; else every node thread stores its node. (The forms for
-    // smaller blocks keep the stores: the copy code there cost their unrecorded
-    // steps 6-10 % through register allocation.)
-    const bool bulk_rec = MAXT == 1024 && C.record != nullptr && (nx & 3) == 0;
+    // Recorded states: in the form for the largest blocks, when the rows fill
+    // the pitch (a block's rows are then one contiguous run per plane, 16-byte
+    // aligned in shared memory and in global memory), one lane of the
+    // Nusselt-rows warp copies them out in bulk after each step's barrier, off
+    // the node warps' path; else every node thread stores its node. (The forms
+    // for smaller blocks keep the stores: the copy code there cost their
+    // unrecorded steps 6-10 % through register allocation.)
+    const bool bulk_rec = MAXT == 1024 && C.record != nullptr && pitch == nx && (nx & 3) == 0;
     // The state of this block's rows and of the rows next to them, from global
     // buffer `parity` (recompute mode: from `start`); halo rows beyond the
     // cavity's walls read as zero in both buffers (the wall rules replace
@@ -330,15 +330,8 @@ __global__ void __launch_bounds__(MAXT) step_cluster_kernel(const __grid_constan
             float* g = C.record + (size_t)s * C.record_stride + (size_t)r0 * pitch;
             const float* src = Dst + nx;  // local row 0
 #pragma unroll 1
-            for (int p = 0; p < kPlanes; ++p) {
-                if (pitch == nx) {
-                    cluster_bulk_s2g(g + p * PL, src + p * plane_sm, (unsigned)(nr * nx * 4));
-                } else {
-                    for (int r = 0; r < nr; ++r)
-                        cluster_bulk_s2g(g + p * PL + (size_t)r * pitch, src + p * plane_sm + r * nx,
-                                         (unsigned)(nx * 4));
-                }
-            }
+            for (int p = 0; p < kPlanes; ++p)
+                cluster_bulk_s2g(g + p * PL, src + p * plane_sm, (unsigned)(nr * nx * 4));
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
         if (!rec && nu_warp) {
